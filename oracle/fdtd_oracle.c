@@ -1,0 +1,657 @@
+/*
+ * FP64 CPU oracle of the 3-D Yee FDTD step and its discrete adjoint.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; only tests, the smoke check and the CPU-baseline leg of the
+ * benchmark do.  It shares no code, header, table or helper with the CUDA
+ * library: every coefficient below is derived here from the paper's text.
+ *
+ * Plain, slow, single-threaded, full-grid arrays, written so that each line
+ * can be checked against the paper by eye:
+ *   - Eq. (yee)   (Sec. 2.1): E^{n+1} = E^n + S eps^{-1} C^-(H^{n+1/2}) + s^{n+1},
+ *                             H^{n+3/2} = H^{n+1/2} - S C^+(E^{n+1}) + m^{n+3/2};
+ *                 soft sources are added after the update; fields start at 0,
+ *                 E is sampled at (n+1) dt and H at (n+3/2) dt.
+ *   - Sec. 2.2    CPML (Roden-Gedney): one memory variable per transverse
+ *                 derivative in each absorbing face, polynomial kappa/sigma/alpha
+ *                 profiles; PEC holds tangential E at zero on the boundary node;
+ *                 periodic pairs wrap the difference operators (oracle-only).
+ *   - Sec. 2.3    real permittivity per Yee E position (diagonal), Drude/Lorentz
+ *                 poles integrated with the trapezoidal ADE.
+ *   - Sec. 2.4    DFT monitors over a box of cells (plane, patch or point) with the
+ *                 half-step magnetic phase.
+ *   - Sec. 3.1, Eq. (adjoint): reverse recursion, transposed curls, the CPML
+ *                 transpose  psibar_mem = psibar + ybar, Dbar = ybar/kappa + c psibar_mem,
+ *                 psibar_old = b psibar_mem, and the transposed 2x2 pole system;
+ *                 material cotangent w.r.t. eps^{-1}.
+ *
+ * Readings where the paper is silent (all listed with their reasons in the
+ * design notes of the repository):
+ *   units c = eps0 = mu0 = 1, h = 1, dt = S; Yee positions Ex(i+1/2,j,k),
+ *   Ey(i,j+1/2,k), Ez(i,j,k+1/2), Hx(i,j+1/2,k+1/2), Hy(i+1/2,j,k+1/2),
+ *   Hz(i+1/2,j+1/2,k); PEC walls at coordinate 0 and N of a non-periodic axis;
+ *   CPML sigma(rho) = sigma_max (rho/d)^m, kappa = 1 + (kappa_max-1)(rho/d)^m,
+ *   alpha = alpha_max (1 - rho/d), b = exp(-(sigma/kappa + alpha) S),
+ *   c = sigma (b-1) / (sigma kappa + kappa^2 alpha)  (c = 0 when sigma = 0);
+ *   ADE per pole in per-step time: dP/dt = Q, dQ/dt = -gamma Q - a0 P + b1 E,
+ *   Lorentz a0 = w0^2, b1 = deps w0^2; Drude a0 = 0, b1 = wp^2; trapezoidal
+ *   rule on x = (P,Q), D = eps_inf E + sum_p P_p, dD/dt = curl H.
+ *   DFT: F(w) = sum_n f(t_n) exp(+i w t_n), no dt factor.
+ *
+ * Index of a cell: idx = (k*ny + j)*nx + i (x fastest).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdint.h>
+
+#define MAXP 16
+#define MAXSRC 64
+#define MAXMON 16
+
+typedef struct {
+    int comp;            /* 0..2 = Ex..Ez, 3..5 = Hx..Hz */
+    int lo[3], hi[3];    /* half-open box */
+    double *wave;        /* wave[n] is added at forward step n (time n+1 for E, n+3/2 for H) */
+    int n;
+} osrc_t;
+
+typedef struct {
+    int lo[3], hi[3];    /* half-open box of cells (a plane, a patch of a plane, a point) */
+    unsigned mask;       /* bit c set: component c (0..5) recorded */
+    int ncomp, comps[6];
+    int nf;
+    double *omega;       /* rad / step */
+    long ncell;          /* box cells, x fastest */
+    double *acc;         /* [ncomp][nf][ncell] complex (re, im) */
+    double *cot;         /* adjoint source, same layout, or NULL */
+} omon_t;
+
+typedef struct oracle {
+    int N[3];
+    long ncell;
+    double S;
+    int periodic[3];
+    int cpml[6];
+    double m, kappa_max, alpha_max, sigma_max;
+    /* CPML coefficients per axis: E-derivatives at integer nodes, H-derivatives at half nodes */
+    double *eb[3], *ec[3], *ek[3];
+    double *hb[3], *hc[3], *hk[3];
+    /* materials */
+    double *inv_eps[3];
+    int npole;
+    double a0[MAXP], b1[MAXP], gam[MAXP];
+    double M[MAXP][2][2], g[MAXP][2];   /* x^{n+1} = M x^n + g (E^{n+1} + E^n) */
+    unsigned char *mask;
+    /* forward state */
+    double *F[6];                 /* Ex Ey Ez Hx Hy Hz */
+    double *psiE[3][2], *psiH[3][2];
+    double *P[3][MAXP], *Q[3][MAXP];
+    long step;
+    /* sources, monitors, energy */
+    int nsrc; osrc_t src[MAXSRC];
+    int nmon; omon_t mon[MAXMON];
+    int energy_on; long energy_cap; double *energy;
+    /* adjoint state (natural cotangents) */
+    double *A[6];
+    double *apsiE[3][2], *apsiH[3][2];
+    double *aP[3][MAXP], *aQ[3][MAXP];
+    int design_on; int dlo[3], dhi[3]; long dcell; double *grad[3];
+    /* scratch */
+    double *tmpE[3], *curl[3], *tmpH[3];
+} oracle_t;
+
+static long IDX(const oracle_t *o, int i, int j, int k) { return ((long)k * o->N[1] + j) * o->N[0] + i; }
+
+static double *zalloc(long n) { return (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double)); }
+
+/* Value of array a at integer coordinates c (may be one outside the grid):
+ * wraps on a periodic axis, else returns 0 (no node beyond a PEC wall). */
+static double at(const oracle_t *o, const double *a, int c0, int c1, int c2) {
+    int c[3] = {c0, c1, c2};
+    for (int q = 0; q < 3; ++q) {
+        if (c[q] < 0) { if (o->periodic[q]) c[q] += o->N[q]; else return 0.0; }
+        if (c[q] >= o->N[q]) { if (o->periodic[q]) c[q] -= o->N[q]; else return 0.0; }
+    }
+    return a[IDX(o, c[0], c[1], c[2])];
+}
+/* Scatter-add into array a at c (wrap / drop like at()). */
+static void add_at(const oracle_t *o, double *a, int c0, int c1, int c2, double v) {
+    int c[3] = {c0, c1, c2};
+    for (int q = 0; q < 3; ++q) {
+        if (c[q] < 0) { if (o->periodic[q]) c[q] += o->N[q]; else return; }
+        if (c[q] >= o->N[q]) { if (o->periodic[q]) c[q] -= o->N[q]; else return; }
+    }
+    a[IDX(o, c[0], c[1], c[2])] += v;
+}
+
+/* CPML profile at coordinate x (cells) along axis q.  Outside the layer the
+ * derivative is the plain difference: b = 1, c = 0, 1/kappa = 1. */
+static void cpml_coef(const oracle_t *o, int q, double x, double *b, double *c, double *kinv) {
+    int dlo = o->cpml[2 * q], dhi = o->cpml[2 * q + 1];
+    double Nq = (double)o->N[q];
+    double rho = -1.0, d = 1.0;
+    if (dlo > 0 && x < (double)dlo) { rho = (double)dlo - x; d = (double)dlo; }
+    else if (dhi > 0 && x > Nq - (double)dhi) { rho = x - (Nq - (double)dhi); d = (double)dhi; }
+    if (rho < 0.0) { *b = 1.0; *c = 0.0; *kinv = 1.0; return; }
+    if (rho > d) rho = d;
+    double smax = o->sigma_max < 0.0 ? 0.8 * (o->m + 1.0) : o->sigma_max;
+    double r = pow(rho / d, o->m);
+    double sigma = smax * r;
+    double kappa = 1.0 + (o->kappa_max - 1.0) * r;
+    double alpha = o->alpha_max * (1.0 - rho / d);
+    double bb = exp(-(sigma / kappa + alpha) * o->S);
+    double cc = 0.0;
+    if (sigma > 0.0) cc = sigma * (bb - 1.0) / (sigma * kappa + kappa * kappa * alpha);
+    *b = bb; *c = cc; *kinv = 1.0 / kappa;
+}
+
+oracle_t *oracle_create(int nx, int ny, int nz, double S, const int *periodic, const int *cpml,
+                        double m, double kappa_max, double alpha_max, double sigma_max) {
+    oracle_t *o = (oracle_t *)calloc(1, sizeof(oracle_t));
+    o->N[0] = nx; o->N[1] = ny; o->N[2] = nz;
+    o->ncell = (long)nx * ny * nz;
+    o->S = S;
+    for (int q = 0; q < 3; ++q) o->periodic[q] = periodic ? periodic[q] : 0;
+    for (int f = 0; f < 6; ++f) o->cpml[f] = cpml ? cpml[f] : 0;
+    o->m = m; o->kappa_max = kappa_max; o->alpha_max = alpha_max; o->sigma_max = sigma_max;
+    for (int q = 0; q < 3; ++q) {
+        int n = o->N[q];
+        o->eb[q] = zalloc(n); o->ec[q] = zalloc(n); o->ek[q] = zalloc(n);
+        o->hb[q] = zalloc(n); o->hc[q] = zalloc(n); o->hk[q] = zalloc(n);
+        for (int j = 0; j < n; ++j) {
+            cpml_coef(o, q, (double)j, &o->eb[q][j], &o->ec[q][j], &o->ek[q][j]);
+            cpml_coef(o, q, (double)j + 0.5, &o->hb[q][j], &o->hc[q][j], &o->hk[q][j]);
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        o->inv_eps[a] = zalloc(o->ncell);
+        for (long c = 0; c < o->ncell; ++c) o->inv_eps[a][c] = 1.0;
+    }
+    o->mask = (unsigned char *)calloc((size_t)o->ncell, 1);
+    for (int f = 0; f < 6; ++f) { o->F[f] = zalloc(o->ncell); o->A[f] = zalloc(o->ncell); }
+    for (int a = 0; a < 3; ++a)
+        for (int s = 0; s < 2; ++s) {
+            o->psiE[a][s] = zalloc(o->ncell); o->psiH[a][s] = zalloc(o->ncell);
+            o->apsiE[a][s] = zalloc(o->ncell); o->apsiH[a][s] = zalloc(o->ncell);
+        }
+    for (int a = 0; a < 3; ++a) {
+        o->tmpE[a] = zalloc(o->ncell); o->curl[a] = zalloc(o->ncell); o->tmpH[a] = zalloc(o->ncell);
+    }
+    return o;
+}
+
+void oracle_destroy(oracle_t *o) {
+    if (!o) return;
+    for (int q = 0; q < 3; ++q) {
+        free(o->eb[q]); free(o->ec[q]); free(o->ek[q]); free(o->hb[q]); free(o->hc[q]); free(o->hk[q]);
+        free(o->inv_eps[q]); free(o->tmpE[q]); free(o->curl[q]); free(o->tmpH[q]); free(o->grad[q]);
+        for (int s = 0; s < 2; ++s) { free(o->psiE[q][s]); free(o->psiH[q][s]); free(o->apsiE[q][s]); free(o->apsiH[q][s]); }
+        for (int p = 0; p < o->npole; ++p) { free(o->P[q][p]); free(o->Q[q][p]); free(o->aP[q][p]); free(o->aQ[q][p]); }
+    }
+    for (int f = 0; f < 6; ++f) { free(o->F[f]); free(o->A[f]); }
+    free(o->mask);
+    for (int s = 0; s < o->nsrc; ++s) free(o->src[s].wave);
+    for (int s = 0; s < o->nmon; ++s) { free(o->mon[s].omega); free(o->mon[s].acc); free(o->mon[s].cot); }
+    free(o->energy);
+    free(o);
+}
+
+/* 2x2 helpers for the trapezoidal pole update (Sec. 2.3, Okoniewski's ADE). */
+static void mat2_inv(const double A[2][2], double R[2][2]) {
+    double det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    R[0][0] = A[1][1] / det; R[0][1] = -A[0][1] / det;
+    R[1][0] = -A[1][0] / det; R[1][1] = A[0][0] / det;
+}
+static void mat2_mul(const double A[2][2], const double B[2][2], double R[2][2]) {
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) R[r][c] = A[r][0] * B[0][c] + A[r][1] * B[1][c];
+}
+
+/* kinds: 0 = Lorentz (deps, w0, gamma), 1 = Drude (unused, wp, gamma).
+ * Each pole p: x' = A x + bvec E with A = [[0,1],[-a0,-gamma]], bvec = (0,b1).
+ * Trapezoidal: (I - A/2) x^{n+1} = (I + A/2) x^n + (bvec/2)(E^{n+1} + E^n). */
+void oracle_set_material(oracle_t *o, const double *iex, const double *iey, const double *iez,
+                         int npole, const int *kind, const double *deps, const double *w,
+                         const double *gamma, const unsigned char *mask) {
+    const double *ie[3] = {iex, iey, iez};
+    for (int a = 0; a < 3; ++a)
+        if (ie[a]) memcpy(o->inv_eps[a], ie[a], sizeof(double) * (size_t)o->ncell);
+    for (int a = 0; a < 3; ++a)
+        for (int p = 0; p < o->npole; ++p) { free(o->P[a][p]); free(o->Q[a][p]); free(o->aP[a][p]); free(o->aQ[a][p]); }
+    o->npole = npole;
+    for (int p = 0; p < npole; ++p) {
+        if (kind[p] == 0) { o->a0[p] = w[p] * w[p]; o->b1[p] = deps[p] * w[p] * w[p]; }
+        else { o->a0[p] = 0.0; o->b1[p] = w[p] * w[p]; }
+        o->gam[p] = gamma[p];
+        double A[2][2] = {{0.0, 1.0}, {-o->a0[p], -o->gam[p]}};
+        double Im[2][2], Ip[2][2], Iminv[2][2];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) {
+                double id = (r == c) ? 1.0 : 0.0;
+                Im[r][c] = id - 0.5 * A[r][c];
+                Ip[r][c] = id + 0.5 * A[r][c];
+            }
+        mat2_inv(Im, Iminv);
+        mat2_mul(Iminv, Ip, o->M[p]);
+        /* g = (I - A/2)^{-1} bvec / 2 */
+        o->g[p][0] = Iminv[0][1] * o->b1[p] * 0.5;
+        o->g[p][1] = Iminv[1][1] * o->b1[p] * 0.5;
+        for (int a = 0; a < 3; ++a) {
+            o->P[a][p] = zalloc(o->ncell); o->Q[a][p] = zalloc(o->ncell);
+            o->aP[a][p] = zalloc(o->ncell); o->aQ[a][p] = zalloc(o->ncell);
+        }
+    }
+    if (mask) memcpy(o->mask, mask, (size_t)o->ncell);
+    else memset(o->mask, 0, (size_t)o->ncell);
+}
+
+int oracle_add_source(oracle_t *o, int comp, const int *lo, const int *hi, const double *wave, int n) {
+    if (o->nsrc >= MAXSRC) return -1;
+    osrc_t *s = &o->src[o->nsrc];
+    s->comp = comp;
+    for (int q = 0; q < 3; ++q) { s->lo[q] = lo[q]; s->hi[q] = hi[q]; }
+    s->wave = zalloc(n); memcpy(s->wave, wave, sizeof(double) * (size_t)n); s->n = n;
+    return o->nsrc++;
+}
+
+int oracle_add_dft_box(oracle_t *o, const int *lo, const int *hi, unsigned mask, int nf, const double *omega) {
+    if (o->nmon >= MAXMON) return -1;
+    omon_t *m = &o->mon[o->nmon];
+    for (int q = 0; q < 3; ++q) { m->lo[q] = lo[q]; m->hi[q] = hi[q]; }
+    m->mask = mask; m->nf = nf;
+    m->ncomp = 0;
+    for (int c = 0; c < 6; ++c) if (mask & (1u << c)) m->comps[m->ncomp++] = c;
+    m->omega = zalloc(nf); memcpy(m->omega, omega, sizeof(double) * (size_t)nf);
+    m->ncell = (long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+    m->acc = zalloc(2L * m->ncomp * nf * m->ncell);
+    m->cot = NULL;
+    return o->nmon++;
+}
+
+void oracle_enable_energy(oracle_t *o, long cap) {
+    free(o->energy);
+    o->energy = zalloc(cap); o->energy_cap = cap; o->energy_on = 1;
+}
+
+/* Grid cell of the c-th cell of monitor box m (x fastest). */
+static void mon_cell(const omon_t *m, long c, int *i, int *j, int *k) {
+    long bx = m->hi[0] - m->lo[0], by = m->hi[1] - m->lo[1];
+    *i = m->lo[0] + (int)(c % bx);
+    *j = m->lo[1] + (int)((c / bx) % by);
+    *k = m->lo[2] + (int)(c / (bx * by));
+}
+
+/* Accumulate F += f(t) exp(i w t) for the components of one field kind. */
+static void dft_accumulate(oracle_t *o, int magnetic, double t) {
+    for (int s = 0; s < o->nmon; ++s) {
+        omon_t *m = &o->mon[s];
+        for (int ci = 0; ci < m->ncomp; ++ci) {
+            int comp = m->comps[ci];
+            if ((comp >= 3) != magnetic) continue;
+            for (int f = 0; f < m->nf; ++f) {
+                double cr = cos(m->omega[f] * t), si = sin(m->omega[f] * t);
+                double *acc = m->acc + 2L * ((long)ci * m->nf + f) * m->ncell;
+                for (long c = 0; c < m->ncell; ++c) {
+                    int i, j, k; mon_cell(m, c, &i, &j, &k);
+                    double v = o->F[comp][IDX(o, i, j, k)];
+                    acc[2 * c] += v * cr;
+                    acc[2 * c + 1] += v * si;
+                }
+            }
+        }
+    }
+}
+
+static int is_pec_E(const oracle_t *o, int a, const int c[3]) {
+    for (int q = 0; q < 3; ++q)
+        if (q != a && !o->periodic[q] && c[q] == 0) return 1;
+    return 0;
+}
+
+/* E-phase of Eq. (yee): reads E, H, psiE, P, Q; writes Enew (pre-source), psiE_out,
+ * P/Q outputs and the CPML-corrected curl.  Output arrays may alias inputs
+ * because every cell reads only its own E/psi/P/Q and the (unchanged) H. */
+static void e_phase(oracle_t *o, double *const Eout[3], double *const psiout[3][2],
+                    double *const Pout[3][MAXP], double *const Qout[3][MAXP]) {
+    const int nx = o->N[0], ny = o->N[1], nz = o->N[2];
+    for (int a = 0; a < 3; ++a) {
+        int b = (a + 1) % 3, cax = (a + 2) % 3;
+        const double *Hc = o->F[3 + cax], *Hb = o->F[3 + b];
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    int c[3] = {i, j, k};
+                    long id = IDX(o, i, j, k);
+                    if (is_pec_E(o, a, c)) {
+                        Eout[a][id] = o->F[a][id];
+                        o->curl[a][id] = 0.0;
+                        continue;
+                    }
+                    int cb[3] = {i, j, k}; cb[b] -= 1;
+                    int cc[3] = {i, j, k}; cc[cax] -= 1;
+                    double d1 = Hc[id] - at(o, Hc, cb[0], cb[1], cb[2]);   /* dHc/dx_b */
+                    double d2 = Hb[id] - at(o, Hb, cc[0], cc[1], cc[2]);   /* dHb/dx_c */
+                    int pb = c[b], pc = c[cax];
+                    double ps1 = o->eb[b][pb] * o->psiE[a][0][id] + o->ec[b][pb] * d1;
+                    double ps2 = o->eb[cax][pc] * o->psiE[a][1][id] + o->ec[cax][pc] * d2;
+                    double y1 = o->ek[b][pb] * d1 + ps1;
+                    double y2 = o->ek[cax][pc] * d2 + ps2;
+                    double cu = y1 - y2;
+                    psiout[a][0][id] = ps1;
+                    psiout[a][1][id] = ps2;
+                    o->curl[a][id] = cu;
+                    double E = o->F[a][id];
+                    if (o->npole > 0 && o->mask[id]) {
+                        double eps = 1.0 / o->inv_eps[a][id];
+                        double G = 0.0, num = eps * E + o->S * cu;
+                        for (int p = 0; p < o->npole; ++p) {
+                            double Pp = o->P[a][p][id], Qp = o->Q[a][p][id];
+                            double MxP = o->M[p][0][0] * Pp + o->M[p][0][1] * Qp;
+                            num += Pp - MxP - o->g[p][0] * E;
+                            G += o->g[p][0];
+                        }
+                        double En = num / (eps + G);
+                        for (int p = 0; p < o->npole; ++p) {
+                            double Pp = o->P[a][p][id], Qp = o->Q[a][p][id];
+                            double Pn = o->M[p][0][0] * Pp + o->M[p][0][1] * Qp + o->g[p][0] * (En + E);
+                            double Qn = o->M[p][1][0] * Pp + o->M[p][1][1] * Qp + o->g[p][1] * (En + E);
+                            Pout[a][p][id] = Pn; Qout[a][p][id] = Qn;
+                        }
+                        Eout[a][id] = En;
+                    } else {
+                        Eout[a][id] = E + o->S * o->inv_eps[a][id] * cu;
+                        for (int p = 0; p < o->npole; ++p) {
+                            Pout[a][p][id] = o->P[a][p][id]; Qout[a][p][id] = o->Q[a][p][id];
+                        }
+                    }
+                }
+    }
+}
+
+static void add_sources(oracle_t *o, int magnetic, long n) {
+    for (int s = 0; s < o->nsrc; ++s) {
+        osrc_t *sr = &o->src[s];
+        if ((sr->comp >= 3) != magnetic) continue;
+        if (n >= sr->n) continue;
+        double v = sr->wave[n];
+        for (int k = sr->lo[2]; k < sr->hi[2]; ++k)
+            for (int j = sr->lo[1]; j < sr->hi[1]; ++j)
+                for (int i = sr->lo[0]; i < sr->hi[0]; ++i) o->F[sr->comp][IDX(o, i, j, k)] += v;
+    }
+}
+
+/* H-phase of Eq. (yee): H -= S * curl(E) with CPML at half-integer nodes. */
+static void h_phase(oracle_t *o) {
+    const int nx = o->N[0], ny = o->N[1], nz = o->N[2];
+    for (int a = 0; a < 3; ++a) {
+        int b = (a + 1) % 3, cax = (a + 2) % 3;
+        const double *Ec = o->F[cax], *Eb = o->F[b];
+        double *H = o->F[3 + a];
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    int c[3] = {i, j, k};
+                    long id = IDX(o, i, j, k);
+                    int cb[3] = {i, j, k}; cb[b] += 1;
+                    int cc[3] = {i, j, k}; cc[cax] += 1;
+                    double d1 = at(o, Ec, cb[0], cb[1], cb[2]) - Ec[id];   /* dEc/dx_b */
+                    double d2 = at(o, Eb, cc[0], cc[1], cc[2]) - Eb[id];   /* dEb/dx_c */
+                    int pb = c[b], pc = c[cax];
+                    double ps1 = o->hb[b][pb] * o->psiH[a][0][id] + o->hc[b][pb] * d1;
+                    double ps2 = o->hb[cax][pc] * o->psiH[a][1][id] + o->hc[cax][pc] * d2;
+                    o->psiH[a][0][id] = ps1;
+                    o->psiH[a][1][id] = ps2;
+                    double y1 = o->hk[b][pb] * d1 + ps1;
+                    double y2 = o->hk[cax][pc] * d2 + ps2;
+                    o->tmpH[a][id] = H[id];
+                    H[id] = H[id] - o->S * (y1 - y2);
+                }
+    }
+}
+
+static void record_energy(oracle_t *o) {
+    /* W_{n+1} = 1/2 sum eps |E^{n+1}|^2 + 1/2 sum H^{n+1/2} . H^{n+3/2} */
+    double w = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (long c = 0; c < o->ncell; ++c) {
+            w += 0.5 * o->F[a][c] * o->F[a][c] / o->inv_eps[a][c];
+            w += 0.5 * o->tmpH[a][c] * o->F[3 + a][c];
+        }
+    if (o->step < o->energy_cap) o->energy[o->step] = w;
+}
+
+/* One forward step n -> n+1 in the order of Eq. (yee) and Sec. 2.1. */
+static void step_once(oracle_t *o) {
+    long n = o->step;
+    double *Eout[3] = {o->F[0], o->F[1], o->F[2]};
+    e_phase(o, Eout, o->psiE, o->P, o->Q);
+    add_sources(o, 0, n);
+    dft_accumulate(o, 0, (double)(n + 1));
+    h_phase(o);
+    add_sources(o, 1, n);
+    dft_accumulate(o, 1, (double)n + 1.5);
+    if (o->energy_on) record_energy(o);
+    o->step = n + 1;
+}
+
+void oracle_step(oracle_t *o, int n) { for (int s = 0; s < n; ++s) step_once(o); }
+
+/* ---------------- access ---------------- */
+double *oracle_field(oracle_t *o, int comp) { return o->F[comp]; }
+double *oracle_psi(oracle_t *o, int magnetic, int comp, int which) {
+    return magnetic ? o->psiH[comp][which] : o->psiE[comp][which];
+}
+double *oracle_pole(oracle_t *o, int comp, int pole, int which) { return which ? o->Q[comp][pole] : o->P[comp][pole]; }
+double *oracle_dft(oracle_t *o, int mon) { return o->mon[mon].acc; }
+long oracle_dft_len(oracle_t *o, int mon) { return 2L * o->mon[mon].ncomp * o->mon[mon].nf * o->mon[mon].ncell; }
+double *oracle_energy(oracle_t *o) { return o->energy; }
+long oracle_step_count(oracle_t *o) { return o->step; }
+void oracle_set_step(oracle_t *o, long s) { o->step = s; }
+double *oracle_coef(oracle_t *o, int magnetic, int axis, int which) {
+    if (magnetic) return which == 0 ? o->hb[axis] : (which == 1 ? o->hc[axis] : o->hk[axis]);
+    return which == 0 ? o->eb[axis] : (which == 1 ? o->ec[axis] : o->ek[axis]);
+}
+void oracle_pole_coef(oracle_t *o, int p, double *M4, double *g2) {
+    M4[0] = o->M[p][0][0]; M4[1] = o->M[p][0][1]; M4[2] = o->M[p][1][0]; M4[3] = o->M[p][1][1];
+    g2[0] = o->g[p][0]; g2[1] = o->g[p][1];
+}
+
+/* Whole forward state (E, H, psiE, psiH, P, Q) as one vector. */
+long oracle_state_len(oracle_t *o) { return o->ncell * (6 + 12 + 6L * o->npole); }
+static void state_ptrs(oracle_t *o, double **v, int adj) {
+    int n = 0;
+    for (int f = 0; f < 6; ++f) v[n++] = adj ? o->A[f] : o->F[f];
+    for (int a = 0; a < 3; ++a) for (int s = 0; s < 2; ++s) v[n++] = adj ? o->apsiE[a][s] : o->psiE[a][s];
+    for (int a = 0; a < 3; ++a) for (int s = 0; s < 2; ++s) v[n++] = adj ? o->apsiH[a][s] : o->psiH[a][s];
+    for (int a = 0; a < 3; ++a) for (int p = 0; p < o->npole; ++p) {
+        v[n++] = adj ? o->aP[a][p] : o->P[a][p];
+        v[n++] = adj ? o->aQ[a][p] : o->Q[a][p];
+    }
+}
+void oracle_state_get(oracle_t *o, double *buf, int adj) {
+    double *v[18 + 6 * MAXP];
+    state_ptrs(o, v, adj);
+    int nv = 18 + 6 * o->npole;
+    for (int s = 0; s < nv; ++s) memcpy(buf + (long)s * o->ncell, v[s], sizeof(double) * (size_t)o->ncell);
+}
+void oracle_state_set(oracle_t *o, const double *buf, int adj) {
+    double *v[18 + 6 * MAXP];
+    state_ptrs(o, v, adj);
+    int nv = 18 + 6 * o->npole;
+    for (int s = 0; s < nv; ++s) memcpy(v[s], buf + (long)s * o->ncell, sizeof(double) * (size_t)o->ncell);
+}
+void oracle_dft_reset(oracle_t *o) {
+    for (int s = 0; s < o->nmon; ++s) memset(o->mon[s].acc, 0, sizeof(double) * (size_t)oracle_dft_len(o, s));
+}
+
+/* ---------------- discrete adjoint, Sec. 3.1 / Eq. (adjoint) ----------------
+ * Scatter form: every forward assignment y = sum_i c_i x_i becomes
+ * xbar_i += c_i ybar, visited in reverse statement order.  State cotangents
+ * are the natural ones (of E^n, H^{n+1/2}, psi, P, Q after step n).  PEC
+ * nodes are not state: their cotangent is held at zero. */
+void oracle_set_adjoint_source(oracle_t *o, int mon, const double *cot) {
+    omon_t *m = &o->mon[mon];
+    long len = oracle_dft_len(o, mon);
+    free(m->cot);
+    m->cot = NULL;
+    if (!cot) return;
+    m->cot = zalloc(len);
+    memcpy(m->cot, cot, sizeof(double) * (size_t)len);
+}
+
+int oracle_set_design(oracle_t *o, const int *lo, const int *hi) {
+    for (int q = 0; q < 3; ++q) { o->dlo[q] = lo[q]; o->dhi[q] = hi[q]; }
+    o->dcell = (long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+    for (int a = 0; a < 3; ++a) { free(o->grad[a]); o->grad[a] = zalloc(o->dcell); }
+    o->design_on = 1;
+    return 0;
+}
+double *oracle_grad(oracle_t *o, int comp) { return o->grad[comp]; }
+double *oracle_adj_field(oracle_t *o, int comp) { return o->A[comp]; }
+
+void oracle_adj_reset(oracle_t *o) {
+    double *v[18 + 6 * MAXP];
+    state_ptrs(o, v, 1);
+    int nv = 18 + 6 * o->npole;
+    for (int s = 0; s < nv; ++s) memset(v[s], 0, sizeof(double) * (size_t)o->ncell);
+    if (o->design_on) for (int a = 0; a < 3; ++a) memset(o->grad[a], 0, sizeof(double) * (size_t)o->dcell);
+}
+
+/* dJ/df(t) = Re(conj(Fbar) exp(i w t)) for the components of one kind. */
+static void inject(oracle_t *o, int magnetic, double t) {
+    for (int s = 0; s < o->nmon; ++s) {
+        omon_t *m = &o->mon[s];
+        if (!m->cot) continue;
+        for (int ci = 0; ci < m->ncomp; ++ci) {
+            int comp = m->comps[ci];
+            if ((comp >= 3) != magnetic) continue;
+            for (int f = 0; f < m->nf; ++f) {
+                double cr = cos(m->omega[f] * t), si = sin(m->omega[f] * t);
+                const double *cot = m->cot + 2L * ((long)ci * m->nf + f) * m->ncell;
+                for (long c = 0; c < m->ncell; ++c) {
+                    int i, j, k; mon_cell(m, c, &i, &j, &k);
+                    o->A[comp][IDX(o, i, j, k)] += cot[2 * c] * cr + cot[2 * c + 1] * si;
+                }
+            }
+        }
+    }
+}
+
+/* Adjoint of forward step m (u^m -> u^{m+1}).  The forward state held by the
+ * oracle must be u^m: it is read only for the material cotangent. */
+void oracle_adjoint_step(oracle_t *o, long m) {
+    const int nx = o->N[0], ny = o->N[1], nz = o->N[2];
+    /* Forward values of step m needed by the material cotangent: pre-source
+     * E^{m+1} and the curl, recomputed from u^m without touching the state. */
+    if (o->design_on) {
+        double *Pt[3][MAXP], *Qt[3][MAXP], *pst[3][2];
+        for (int a = 0; a < 3; ++a) {
+            for (int p = 0; p < o->npole; ++p) { Pt[a][p] = zalloc(o->ncell); Qt[a][p] = zalloc(o->ncell); }
+            pst[a][0] = zalloc(o->ncell); pst[a][1] = zalloc(o->ncell);
+        }
+        e_phase(o, o->tmpE, pst, Pt, Qt);
+        for (int a = 0; a < 3; ++a) {
+            for (int p = 0; p < o->npole; ++p) { free(Pt[a][p]); free(Qt[a][p]); }
+            free(pst[a][0]); free(pst[a][1]);
+        }
+    }
+    /* reverse of: DFT-H at t = m + 3/2 */
+    inject(o, 1, (double)m + 1.5);
+    /* reverse of the H-phase: H_a -= S (y1 - y2), psi = b psi + c d, y = d/kappa + psi */
+    for (int a = 0; a < 3; ++a) {
+        int b = (a + 1) % 3, cax = (a + 2) % 3;
+        double *Ac = o->A[cax], *Ab = o->A[b];
+        const double *Ha = o->A[3 + a];
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    int c[3] = {i, j, k};
+                    long id = IDX(o, i, j, k);
+                    int pb = c[b], pc = c[cax];
+                    double yb1 = -o->S * Ha[id];
+                    double yb2 = o->S * Ha[id];
+                    double pm1 = o->apsiH[a][0][id] + yb1;
+                    double pm2 = o->apsiH[a][1][id] + yb2;
+                    double db1 = o->hk[b][pb] * yb1 + o->hc[b][pb] * pm1;
+                    double db2 = o->hk[cax][pc] * yb2 + o->hc[cax][pc] * pm2;
+                    o->apsiH[a][0][id] = o->hb[b][pb] * pm1;
+                    o->apsiH[a][1][id] = o->hb[cax][pc] * pm2;
+                    int cb[3] = {i, j, k}; cb[b] += 1;
+                    int cc[3] = {i, j, k}; cc[cax] += 1;
+                    add_at(o, Ac, cb[0], cb[1], cb[2], db1);
+                    Ac[id] -= db1;
+                    add_at(o, Ab, cc[0], cc[1], cc[2], db2);
+                    Ab[id] -= db2;
+                }
+    }
+    /* reverse of: DFT-E at t = m + 1 */
+    inject(o, 0, (double)(m + 1));
+    /* reverse of the E-phase */
+    for (int a = 0; a < 3; ++a) {
+        int b = (a + 1) % 3, cax = (a + 2) % 3;
+        double *Hc = o->A[3 + cax], *Hb = o->A[3 + b];
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    int c[3] = {i, j, k};
+                    long id = IDX(o, i, j, k);
+                    if (is_pec_E(o, a, c)) { o->A[a][id] = 0.0; continue; }
+                    double Etb = o->A[a][id];        /* cotangent of pre-source E^{m+1} */
+                    double Eold_b = 0.0, curl_b;
+                    int indesign = o->design_on && i >= o->dlo[0] && i < o->dhi[0] && j >= o->dlo[1] &&
+                                   j < o->dhi[1] && k >= o->dlo[2] && k < o->dhi[2];
+                    long did = indesign ? ((long)(k - o->dlo[2]) * (o->dhi[1] - o->dlo[1]) + (j - o->dlo[1])) *
+                                              (o->dhi[0] - o->dlo[0]) + (i - o->dlo[0]) : 0;
+                    if (o->npole > 0 && o->mask[id]) {
+                        double eps = 1.0 / o->inv_eps[a][id];
+                        double G = 0.0;
+                        for (int p = 0; p < o->npole; ++p) G += o->g[p][0];
+                        /* x_p^{m+1} = M_p x_p^m + g_p (Et + E^m) */
+                        for (int p = 0; p < o->npole; ++p) {
+                            double xbP = o->aP[a][p][id], xbQ = o->aQ[a][p][id];
+                            double gx = o->g[p][0] * xbP + o->g[p][1] * xbQ;
+                            Etb += gx;
+                            Eold_b += gx;
+                            o->aP[a][p][id] = o->M[p][0][0] * xbP + o->M[p][1][0] * xbQ;
+                            o->aQ[a][p][id] = o->M[p][0][1] * xbP + o->M[p][1][1] * xbQ;
+                        }
+                        /* Et = (eps E + sum_p (P - (M x)_P - g_P E) + S curl) / (eps + G) */
+                        double den = eps + G;
+                        Eold_b += Etb * (eps - G) / den;
+                        for (int p = 0; p < o->npole; ++p) {
+                            o->aP[a][p][id] += Etb * (1.0 - o->M[p][0][0]) / den;
+                            o->aQ[a][p][id] += Etb * (-o->M[p][0][1]) / den;
+                        }
+                        curl_b = Etb * o->S / den;
+                        if (indesign) {
+                            double Eold = o->F[a][id], Et = o->tmpE[a][id];
+                            double eps_b = Etb * (Eold - Et) / den;
+                            o->grad[a][did] += -eps * eps * eps_b;
+                        }
+                    } else {
+                        /* Et = E + S inv_eps curl */
+                        Eold_b = Etb;
+                        curl_b = Etb * o->S * o->inv_eps[a][id];
+                        if (indesign) o->grad[a][did] += Etb * o->S * o->curl[a][id];
+                    }
+                    /* curl = y1 - y2 ; psi = b psi + c d ; y = d/kappa + psi */
+                    int pb = c[b], pc = c[cax];
+                    double yb1 = curl_b, yb2 = -curl_b;
+                    double pm1 = o->apsiE[a][0][id] + yb1;
+                    double pm2 = o->apsiE[a][1][id] + yb2;
+                    double db1 = o->ek[b][pb] * yb1 + o->ec[b][pb] * pm1;
+                    double db2 = o->ek[cax][pc] * yb2 + o->ec[cax][pc] * pm2;
+                    o->apsiE[a][0][id] = o->eb[b][pb] * pm1;
+                    o->apsiE[a][1][id] = o->eb[cax][pc] * pm2;
+                    /* d1 = Hc(r) - Hc(r - e_b), d2 = Hb(r) - Hb(r - e_c) */
+                    int cb[3] = {i, j, k}; cb[b] -= 1;
+                    int cc[3] = {i, j, k}; cc[cax] -= 1;
+                    Hc[id] += db1;
+                    add_at(o, Hc, cb[0], cb[1], cb[2], -db1);
+                    Hb[id] += db2;
+                    add_at(o, Hb, cc[0], cc[1], cc[2], -db2);
+                    o->A[a][id] = Eold_b;
+                }
+    }
+}
