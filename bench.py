@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 FDTD hot path; prints one JSON line.
+
+Workload (one bench step): the 128^3 FP32 forward solve with 10-cell CPML, a central 64^3
+region of blocky random eps in [1, 12], an Ez Gaussian-pulse sheet and running DFT monitors of
+all six components on the z = 64 plane at three frequencies, advanced 2000 time steps (E
+update, sources, DFT-E, H update, DFT-H per step).  value = cells x steps / device time.
+
+Extra keys: roofline of the dominant kernel (algorithmic bytes / event-timed duration against
+the measured HBM copy bandwidth), the FP64 oracle on the host cores (cpu_baseline), the same
+solve end to end through the C ABI with host buffers (e2e), the FP64 path's rate and the
+FP32-vs-FP64 spectral error, and the rate of the transposed (adjoint) step and of a full
+checkpointed gradient evaluation.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on a bounded
+sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS_AXIS = 128
+CPML = 10
+T_STEPS = 2000
+WORKLOAD = ("cpml_blocks_128^3: 128^3 cells, 10-cell CPML (m=3, kappa_max=5, alpha_max=0.05), central 64^3 "
+            "eps_r~U[1,12] in 8^3 blocks, Ez Gaussian-pulse sheet (lambda0=20 cells), 2000 steps, DFT of "
+            "Ex..Hz on z=64 at lambda 18/20/22")
+METRIC = "Gcell-steps/s fwd & adjoint, FP32 vs FP64 at stated error; % of HBM peak"
+
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def scene(steps=T_STEPS):
+    from paper_2609_30039_gb300 import workloads as W
+    return W.cpml_blocks(n=N_CELLS_AXIS, d=CPML, n_steps=steps)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_2609_30039_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(cs, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        ent = d.get(kernel)
+        if ent and ent.get("source_sha") == source_sha():
+            return ent["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"gbfdtd_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    v = [x.strip() for x in line.split(",")]
+                    if len(v) >= 9:
+                        rows.append(v)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        loaded = [s for s in sm if s > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def alg_bytes_per_cell(sc, esz, kind):
+    """Algorithmic bytes of one launch per cell (read once, write once; no temporal blocking):
+    E update: E (3 R + 3 W) + H (3 R) + eps^-1 (1 R isotropic | 3 R) = 10 | 12 words;
+    H update: H (3 R + 3 W) + E (3 R) = 9 words; each CPML slab membership adds 2 psi R + W
+    = 4 words per half-step (averaged over the grid)."""
+    n = sc.shape
+    cells = n[0] * n[1] * n[2]
+    memb = sum((sc.cpml[2 * q] + sc.cpml[2 * q + 1]) / n[q] for q in range(3))
+    iso = sc.inv_eps is not None and len(sc.inv_eps) == 1
+    if kind == "e_update":
+        words = 10 if iso else 12
+    else:
+        words = 9
+    return (words + 4 * memb) * esz, cells
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2609_30039_gb300 import adjoint as ADJ
+    from paper_2609_30039_gb300 import build as B
+    from paper_2609_30039_gb300 import fdtd
+
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    B.build()
+    fdtd.load()
+    sc = scene()
+    cells = sc.cells
+    ctx = fdtd.Context([sc], dtype="f32", device=f"cuda:{local}")
+    stream = ctx.stream
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def solve():
+        fdtd.fdtd_reset(ctx.ctx)
+        fdtd.fdtd_dft_reset(ctx.ctx)
+        fdtd.fdtd_step_forward(ctx.ctx, T_STEPS)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = ctx.launches()
+    times = []
+    prof = None
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))                      # L2 flush between timed iterations
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            last = k == args.steps - 1
+            if last:
+                fdtd.fdtd_profile_begin(ctx.ctx, 8 * T_STEPS + 16)
+            e0.record(stream)
+            solve()
+            e1.record(stream)
+            if last:
+                prof = fdtd.fdtd_profile_end(ctx.ctx)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = ctx.launches() - l0
+    tot_ms = sum(times)
+    if dist:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    value = world * cells * T_STEPS / (ms_per_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (event-timed during the last timed iteration)
+    dom = max(("e_update", "h_update"), key=lambda k: prof[k][0])
+    avg_ms = prof[dom][0] / max(prof[dom][1], 1)
+    bpc, ncell = alg_bytes_per_cell(sc, 4, dom)
+    alg_bytes = bpc * ncell
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    step_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]}
+    share = {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items() if v[1]}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Gcell-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded PCG64 inputs of the workload's shape; no paper scene)",
+        "config": {"workload": WORKLOAD, "cells": cells, "time_steps_per_iter": T_STEPS,
+                   "l2": "flushed between timed iterations (256 MiB write); the ~75 MB state stays L2-resident "
+                         "within an iteration", "parallelism": f"{world} independent replica(s), no collective"},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic(dom),
+                     "alg_bytes_per_launch": int(alg_bytes), "avg_launch_us": round(avg_ms * 1e3, 3),
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                     else "fallback 6.8 TB/s"},
+        "kernel_avg_us": {k: round(v * 1e3, 3) for k, v in step_ms.items()},
+        "kernel_share": share,
+    }
+    clk_s = clk.summary()
+    if clk_s:
+        out["clocks"] = clk_s
+
+    if rank == 0 and not args.quick:
+        out["e2e"] = e2e(ctx, sc, args, dev)
+        out.update(extras(ctx, sc, args, dev))
+        if not args.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def e2e(ctx, sc, args, dev):
+    """Same solve through the public C-ABI calls with host buffers: inv_eps H2D from pinned
+    memory, rebinding, reset, 2000 steps, and the DFT spectra D2H into pinned memory."""
+    import numpy as np
+    import torch
+
+    from paper_2609_30039_gb300 import fdtd
+    host_ie = torch.from_numpy(np.ascontiguousarray(sc.inv_eps[0], dtype=np.float32)).pin_memory()
+    dev_ie = torch.empty_like(host_ie, device=dev)
+    mid = ctx.monitors[0][0]
+    n = fdtd.fdtd_dft_size(ctx.ctx, mid)
+    host_out = torch.empty(2 * n, dtype=torch.float64).pin_memory()
+    stream = ctx.stream
+    ts = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dev_ie.copy_(host_ie, non_blocking=True)
+        ctx.set_inv_eps(0, [dev_ie, dev_ie, dev_ie])
+        fdtd.fdtd_reset(ctx.ctx)
+        fdtd.fdtd_dft_reset(ctx.ctx)
+        fdtd.fdtd_step_forward(ctx.ctx, T_STEPS)
+        fdtd.fdtd_dft_read(ctx.ctx, mid, host_out.data_ptr(), host_out.numel() * 8, 0)
+        stream.synchronize()
+        if k >= args.warmup:
+            ts.append(time.perf_counter() - t0)
+    t = statistics.mean(ts)
+    return {"value": round(sc.cells * T_STEPS / t / 1e9, 3), "unit": "Gcell-steps/s",
+            "h2d_bytes_per_step": int(host_ie.numel() * 4), "d2h_bytes_per_step": int(host_out.numel() * 8),
+            "ms_per_step": round(t * 1e3, 3)}
+
+
+def extras(ctx, sc, args, dev):
+    """FP64 rate and FP32-vs-FP64 spectral error; transposed-step rate; checkpointed gradient."""
+    import numpy as np
+    import torch
+
+    from paper_2609_30039_gb300 import adjoint as ADJ
+    from paper_2609_30039_gb300 import fdtd
+    res = {}
+    # FP32 spectra of the last solve vs an FP64 solve of the same inputs
+    f32 = ctx.dft(0).clone()
+    c64 = fdtd.Context([sc], dtype="f64", device=str(dev))
+    for _ in range(1):
+        c64.step(T_STEPS)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fdtd.fdtd_reset(c64.ctx)
+    fdtd.fdtd_dft_reset(c64.ctx)
+    e0.record(c64.stream)
+    c64.step(T_STEPS)
+    e1.record(c64.stream)
+    e1.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    f64 = c64.dft(0)
+    err = float(torch.linalg.vector_norm(f32 - f64) / torch.linalg.vector_norm(f64))
+    res["fp64"] = {"value": round(sc.cells * T_STEPS / (ms64 * 1e-3) / 1e9, 3), "unit": "Gcell-steps/s",
+                   "fp32_vs_fp64_dft_rel_l2": err, "note": "FP64 GPU path is checked against the FP64 oracle "
+                   "to <= 1e-12 in the parity tests"}
+    c64.close()
+    # transposed steps (no design box: pure transpose rate over the whole grid)
+    fdtd.fdtd_adjoint_begin(ctx.ctx)
+    n_adj = min(T_STEPS, fdtd.fdtd_adjoint_step_count(ctx.ctx))
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    fdtd.fdtd_step_adjoint(ctx.ctx, n_adj)
+    e1.record(ctx.stream)
+    e1.synchronize()
+    ms_adj = e0.elapsed_time(e1)
+    res["adjoint"] = {"value": round(sc.cells * n_adj / (ms_adj * 1e-3) / 1e9, 3), "unit": "Gcell-steps/s",
+                      "what": "transposed steps of the same grid (E and H transposes, CPML), no replay"}
+    # full checkpointed gradient: objective sum |F|^2 on the monitor plane, design = central 64^3
+    from paper_2609_30039_gb300 import workloads as W
+    sg = scene()
+    sg.design = ((32, 32, 32), (96, 96, 96))
+    cg = fdtd.Context([sg], dtype="f32", device=str(dev))
+    runner = ADJ.DesignAdjoint(cg, slots=32)
+
+    def loss(specs):
+        F = specs[0]
+        return float((F.abs() ** 2).sum()), [torch.view_as_real(2.0 * F).contiguous()]
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    (_, _), grads, stats = runner.run(T_STEPS, loss)
+    torch.cuda.synchronize()
+    tg = time.perf_counter() - t0
+    res["gradient"] = {"seconds": round(tg, 4), "checkpoints": 32, "forward_steps_incl_replay": stats["forward_steps"],
+                       "adjoint_steps": stats["adjoint_steps"],
+                       "forward_equiv_gcell_steps_s": round(sg.cells * T_STEPS / tg / 1e9, 3),
+                       "grad_finite": bool(torch.isfinite(grads[0]).all().item())}
+    cg.close()
+    return res
+
+
+def cpu_baseline(sc, seconds):
+    """The FP64 oracle as it stands, single thread, on the first few steps of the same workload."""
+    from oracle.oracle import build as obuild
+    from tests.oracle_adapter import oracle_from_scene
+    obuild()
+    o = oracle_from_scene(sc)
+    t0 = time.perf_counter()
+    o.step(2)
+    est = (time.perf_counter() - t0) / 2
+    n = max(1, min(T_STEPS - 2, int(seconds / max(est, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    return {"value": round(sc.cells * n / dt / 1e9, 6), "unit": "Gcell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"steps 3..{n + 2} of the 2000-step 128^3 workload (FP64 C oracle, one thread, "
+                      f"{dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return
+    from oracle.oracle import build as obuild
+    from tests.oracle_adapter import oracle_from_scene
+    obuild()
+    sc = scene()
+    o = oracle_from_scene(sc)
+    per = max(1, args.ref_steps_per_iter)
+    for _ in range(args.warmup):
+        o.step(1)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.step(per)
+        ts.append(time.perf_counter() - t0)
+    t = sum(ts)
+    value = sc.cells * per * args.steps / t / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gcell-steps/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "cells": sc.cells,
+                      "time_steps_per_iter": per, "note": "each bench step is a bounded sample of the workload"},
+           "cpu_baseline": {"value": round(value, 6), "unit": "Gcell-steps/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{per} time steps of the 128^3 workload per bench step"},
+           "e2e": {"value": round(value, 6), "unit": "Gcell-steps/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip e2e / extras / cpu baseline")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-steps-per-iter", type=int, default=8)
+    ap.add_argument("--profile-case", type=int, default=0,
+                    help="n: run only a short n^3 FP32 forward (ncu captures on a case larger than L2)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.profile_case:
+        profile_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+def profile_case(args):
+    """Short n^3 FP32 forward solve of the same workload family, for ncu captures."""
+    import torch
+
+    from paper_2609_30039_gb300 import build as B
+    from paper_2609_30039_gb300 import fdtd
+    from paper_2609_30039_gb300 import workloads as W
+    B.build()
+    n = args.profile_case
+    sc = W.cpml_blocks(n=n, d=CPML, n_steps=args.steps)
+    ctx = fdtd.Context([sc], dtype="f32")
+    ctx.step(args.warmup + args.steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": n, "steps": args.warmup + args.steps, "cells": sc.cells}))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,277 @@
+/*
+ * gbfdtd — GB300-native differentiable FDTD hot path (C ABI).
+ *
+ * The method is the differentiable FDTD scheme of arxiv 2609.30039 (TorchFDTD):
+ *   Sec. 2.1, Eq. (yee): E^{n+1} = E^n + S eps^{-1} C^-(H^{n+1/2}) + s^{n+1},
+ *                        H^{n+3/2} = H^{n+1/2} - S C^+(E^{n+1}) + m^{n+3/2};
+ *   Sec. 2.2: CPML memories per transverse derivative in absorbing faces, PEC faces;
+ *   Sec. 2.3: permittivity per Yee E position (diagonal), up to 16 Drude/Lorentz poles
+ *             integrated with the trapezoidal ADE, tensor admission rule inside a face;
+ *   Sec. 2.4: soft point/sheet sources, running DFT monitors with the half-step phase;
+ *   Sec. 3.1, Eq. (adjoint): transposed kernel of every update and the material
+ *             cotangent d(objective)/d(eps^-1);
+ *   Sec. 3.2: checkpoint snapshots for replay;
+ *   Sec. 4.1: several independent structures advanced by one launch.
+ *
+ * Conventions (all entry points):
+ *   - Reduced units: lengths in cells, c = eps0 = mu0 = 1; only the Courant number
+ *     S = c dt / dx enters the update.  Arrays of cells are (nz, ny, nx) with x fastest:
+ *     idx = (k*ny + j)*nx + i.  Yee positions: Ex(i+1/2,j,k), Ey(i,j+1/2,k), Ez(i,j,k+1/2),
+ *     Hx(i,j+1/2,k+1/2), Hy(i+1/2,j,k+1/2), Hz(i+1/2,j+1/2,k).  The outer boundary of
+ *     every domain is PEC: tangential E on the planes of coordinate 0 is held at zero and
+ *     nodes at coordinate N do not exist.
+ *   - Component ids: 0..2 = Ex, Ey, Ez; 3..5 = Hx, Hy, Hz.
+ *   - Every function returns an fdtd_status; nothing throws across the ABI.  On error the
+ *     context keeps a message (fdtd_last_error).  After FDTD_ECUDA the context is poisoned:
+ *     every later call except fdtd_destroy / fdtd_last_error returns FDTD_ESTATE.
+ *   - All device work is enqueued on the stream given to fdtd_create (a cudaStream_t passed
+ *     as void*; NULL = legacy default stream).  Calls are asynchronous unless stated.
+ *     A context is not thread-safe.
+ *   - "device" pointers are CUDA global memory; "borrowed" means the caller keeps it alive
+ *     for as long as the context may use it; "copied" means the library copies it before
+ *     returning.
+ *   - Time indexing: fields start at zero (step count 0).  Forward step n (n = 0, 1, ...)
+ *     maps u^n -> u^{n+1}; its electric samples belong to time (n+1) dt and its magnetic
+ *     samples to (n+3/2) dt (Sec. 2.1).
+ */
+#ifndef GBFDTD_FDTD_H
+#define GBFDTD_FDTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FDTD_OK = 0,
+    FDTD_EINVAL = 1,     /* bad argument (sizes, ids, boxes, NULL pointers) */
+    FDTD_ECFL = 2,       /* Courant number violates Eq. (cfl): S sqrt(3) > 0.99 */
+    FDTD_ETENSOR = 3,    /* a CPML cell holds a permittivity rejected by the Sec. 2.3 admission rule */
+    FDTD_ENOMEM = 4,     /* the memory plan exceeds free device memory (nothing allocated) */
+    FDTD_ECUDA = 5,      /* a CUDA call failed; the context is poisoned */
+    FDTD_ESTATE = 6,     /* call not valid in the current state (see each function) */
+    FDTD_ENONFINITE = 7, /* NaN/Inf found by fdtd_check_finite */
+    FDTD_ETIMEOUT = 8    /* a bounded host wait ran out */
+} fdtd_status;
+
+enum { FDTD_F32 = 0, FDTD_F64 = 1 };          /* storage and arithmetic type of fields */
+enum { FDTD_LORENTZ = 0, FDTD_DRUDE = 1 };
+enum { FDTD_CODEC_NATIVE = 0, FDTD_CODEC_BF16 = 1 };   /* snapshot codecs */
+
+typedef struct fdtd_ctx fdtd_ctx;
+
+/* One domain's grid (Sec. 2.1).  dx > 0 and dt only serve the consistency check
+ * dt == courant * dx (dt = 0: derived).  All domains of a context share courant and dtype. */
+typedef struct {
+    int32_t nx, ny, nz;   /* cells per axis, each >= 2 */
+    double dx;
+    double courant;       /* S; Eq. (cfl): 0 < S <= 0.99 / sqrt(3) */
+    double dt;
+    int32_t dtype;        /* FDTD_F32 | FDTD_F64 */
+} fdtd_grid;
+
+/* CPML of one domain (Sec. 2.2, Roden-Gedney).  cells[f] = depth d of face f in
+ * (-x,+x,-y,+y,-z,+z); 0 = bare PEC face.  At depth rho (cells, measured at the node of the
+ * derivative: integer for E updates, half-integer for H updates):
+ *   sigma = sigma_max (rho/d)^m, kappa = 1 + (kappa_max - 1)(rho/d)^m, alpha = alpha_max (1 - rho/d),
+ *   b = exp(-(sigma/kappa + alpha) S), c = sigma (b - 1)/(sigma kappa + kappa^2 alpha) (0 if sigma = 0);
+ *   psi <- b psi + c D,  y = D / kappa + psi.  sigma_max < 0 selects 0.8 (m + 1). */
+typedef struct {
+    int32_t cells[6];
+    double m, kappa_max, alpha_max, sigma_max;
+} fdtd_cpml;
+
+/* One pole (Sec. 2.3).  Per step: dP/dt = Q, dQ/dt = -gamma Q - a0 P + b1 E with
+ * Lorentz a0 = omega^2, b1 = delta_eps omega^2; Drude a0 = 0, b1 = omega^2 (omega = wp dt). */
+typedef struct {
+    int32_t kind;         /* FDTD_LORENTZ | FDTD_DRUDE */
+    double delta_eps;     /* Lorentz strength (unused for Drude) */
+    double omega_dt;      /* rad/step */
+    double gamma_dt;      /* damping per step, >= 0 */
+} fdtd_pole;
+
+/* Materials of one domain (Sec. 2.3).  inv_eps[a]: device, borrowed, dtype of the grid,
+ * nz*ny*nx values of 1/eps (1/eps_inf in dispersive cells) at the Yee position of E_a; the
+ * same pointer three times declares an isotropic medium.  Values must be > 0.
+ * pole_mask: device, borrowed, nz*ny*nx bytes, nonzero = this domain's poles act on all three
+ * E components of the cell; NULL = no dispersion.  poles: host, copied, n_poles <= 16. */
+typedef struct {
+    const void* inv_eps[3];
+    int32_t n_poles;
+    const fdtd_pole* poles;
+    const uint8_t* pole_mask;
+} fdtd_material;
+
+/* Creates a context owning all internal device state (fields, CPML memories, pole states,
+ * adjoint state, monitors, snapshots) for n_domains independent domains (Sec. 4.1); arrays
+ * grids/cpml/materials have n_domains entries.  Checks Eq. (cfl) (FDTD_ECFL), the tensor
+ * admission rule in every CPML cell (FDTD_ETENSOR: with a diagonal tensor the face normal is
+ * a principal axis; the normal eigenvalue must not lie strictly between the other two), and
+ * the memory plan against cudaMemGetInfo before allocating (FDTD_ENOMEM).  Synchronises the
+ * stream.  *out is set only on FDTD_OK. */
+fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cpml* cpml,
+                        const fdtd_material* materials, void* stream, fdtd_ctx** out);
+
+/* Frees everything the context owns.  NULL-safe.  Synchronises the stream. */
+fdtd_status fdtd_destroy(fdtd_ctx* ctx);
+
+/* Message of the last error on this context ("" if none); static text when ctx == NULL. */
+const char* fdtd_last_error(const fdtd_ctx* ctx);
+
+/* Library version string (static). */
+const char* fdtd_version(void);
+
+/* Rebinds domain `domain`'s material (same rules as in fdtd_create; the pole count and the
+ * set of dispersive cells must not grow beyond the box chosen at create: FDTD_EINVAL). */
+fdtd_status fdtd_set_material(fdtd_ctx* ctx, int32_t domain, const fdtd_material* material);
+
+/* Soft source (Sec. 2.4, Eq. (yee) s and m): after the update of `component` in forward
+ * step n, every cell of the half-open box [lo, hi) gets += waveform[n] (no effect for
+ * n >= n_steps).  waveform: host, copied, FP64.  *source_id may be NULL. */
+fdtd_status fdtd_add_source(fdtd_ctx* ctx, int32_t domain, int32_t component, const int32_t lo[3],
+                            const int32_t hi[3], const double* waveform, int32_t n_steps,
+                            int32_t* source_id);
+
+/* Running DFT monitor over the half-open box [lo, hi) (a plane, a patch or a point; Sec. 2.4):
+ * F_c(f, cell) += field_c(cell) * exp(+i omega_dt[f] t) with t = n+1 for E components and
+ * t = n+3/2 for H components in forward step n.  Accumulators are complex FP64, layout
+ * [ncomp][n_freq][box cells (x fastest)], components in increasing id among component_mask
+ * (bit c = component c).  omega_dt: host, copied.  *monitor_id receives the id. */
+fdtd_status fdtd_add_dft_monitor(fdtd_ctx* ctx, int32_t domain, const int32_t lo[3], const int32_t hi[3],
+                                 uint32_t component_mask, int32_t n_freq, const double* omega_dt,
+                                 int32_t* monitor_id);
+
+/* Number of complex FP64 values of a monitor (ncomp * n_freq * box cells). */
+fdtd_status fdtd_dft_size(fdtd_ctx* ctx, int32_t monitor_id, int64_t* n_complex);
+
+/* Copies a monitor's accumulators (interleaved re, im doubles) to dst (bytes >= 16 * size).
+ * dst_on_device = 0: host memory, the call synchronises the stream. */
+fdtd_status fdtd_dft_read(fdtd_ctx* ctx, int32_t monitor_id, void* dst, size_t bytes, int32_t dst_on_device);
+
+/* Zeroes every DFT accumulator. */
+fdtd_status fdtd_dft_reset(fdtd_ctx* ctx);
+
+/* enabled = 0 freezes every DFT accumulator during fdtd_step_forward (used while replaying
+ * forward segments of the adjoint, Sec. 3.2); 1 (default) accumulates. */
+fdtd_status fdtd_dft_enable(fdtd_ctx* ctx, int32_t enabled);
+
+/* Records the discrete energy W_{n+1} = 1/2 sum eps |E^{n+1}|^2 + 1/2 sum H^{n+1/2} . H^{n+3/2}
+ * of every domain at every forward step n < capacity (FP64, per domain). */
+fdtd_status fdtd_enable_energy(fdtd_ctx* ctx, int32_t capacity);
+
+/* Copies n per-step energies of one domain to host memory (synchronises). */
+fdtd_status fdtd_energy_read(fdtd_ctx* ctx, int32_t domain, double* host_dst, int32_t n);
+
+/* Advances every domain by n_steps forward steps (Eq. (yee): E update with CPML, poles and
+ * eps^-1; E sources; E DFT; H update with CPML; H sources; H DFT; energy).  Asynchronous. */
+fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps);
+
+/* Number of forward steps the held state has taken (u^n: returns n). */
+fdtd_status fdtd_step_count(fdtd_ctx* ctx, int64_t* n);
+
+/* Zeroes the forward state (fields, CPML memories, pole states) and sets the step count to 0.
+ * DFT accumulators and energies are left alone (see fdtd_dft_reset). */
+fdtd_status fdtd_reset(fdtd_ctx* ctx);
+
+/* ---- state access (tests, checkpoints held by the caller) ----
+ * A domain's state is a list of parts:
+ *   part 0..5            field Ex..Hz, nz*ny*nx values;
+ *   part 6 + 2a + s      E CPML memory psi of E_a for its s-th curl derivative
+ *                        (s = 0: along axis (a+1)%3, s = 1: along (a+2)%3);
+ *   part 12 + 2a + s     the same for H_a;
+ *   part 18 + 2(a*P + p) + w   pole state (w = 0: P, 1: Q) of pole p for E_a (P = n_poles).
+ * A CPML part of axis q holds the cells whose q-coordinate lies in [0, d_lo) U [N_q - d_hi, N_q)
+ * (the slabs of the two q faces), in (z, y, x) order with x fastest, the q extent replaced by
+ * d_lo + d_hi; it is empty if the axis has no CPML.  A pole part holds the cells of the box
+ * reported by fdtd_ade_box.  Values are in the dtype of the grid.
+ * which = 0: forward state; which = 1: adjoint state in natural form (the cotangent of the
+ * forward part of the same id; reading it completes any pending transposition first). */
+fdtd_status fdtd_part_count(fdtd_ctx* ctx, int32_t domain, int32_t* n_parts);
+fdtd_status fdtd_part_size(fdtd_ctx* ctx, int32_t domain, int32_t part, int64_t* n_values);
+fdtd_status fdtd_get_part(fdtd_ctx* ctx, int32_t domain, int32_t which, int32_t part, void* dst_device);
+fdtd_status fdtd_set_part(fdtd_ctx* ctx, int32_t domain, int32_t which, int32_t part, const void* src_device);
+/* Box [lo, hi) of the pole states of a domain (empty box if it has no dispersive cell). */
+fdtd_status fdtd_ade_box(fdtd_ctx* ctx, int32_t domain, int32_t lo[3], int32_t hi[3]);
+/* Sets the forward step count (after the caller wrote a state with fdtd_set_part). */
+fdtd_status fdtd_set_step_count(fdtd_ctx* ctx, int64_t n);
+
+/* ---- checkpoints (Sec. 3.2) ----
+ * Saves the whole forward state of every domain and its step count into slot `slot` (device
+ * memory owned by the context, allocated on first use of the slot; FDTD_ENOMEM if it does not
+ * fit).  codec FDTD_CODEC_NATIVE copies values exactly; FDTD_CODEC_BF16 stores bf16(x / s)
+ * with one FP32 scale s = max|x| per (part, outermost index) slab (a z-plane for field parts),
+ * s = 0 for an all-zero slab.  restore dequantises into the live state. */
+fdtd_status fdtd_state_save(fdtd_ctx* ctx, int32_t slot, int32_t codec);
+fdtd_status fdtd_state_restore(fdtd_ctx* ctx, int32_t slot);
+/* Device bytes one snapshot of this context takes with a codec. */
+fdtd_status fdtd_snapshot_bytes(fdtd_ctx* ctx, int32_t codec, int64_t* bytes);
+/* Frees every snapshot slot. */
+fdtd_status fdtd_snapshots_free(fdtd_ctx* ctx);
+
+/* ---- discrete adjoint (Sec. 3.1, Eq. (adjoint)) ----
+ * Design box of a domain: the material cotangent d J / d(eps^-1_a) of every cell of [lo, hi)
+ * is accumulated (+=) into grad_device (FP64, borrowed, layout [3][box cells, x fastest]) by
+ * every adjoint step.  The box must lie outside the CPML slabs.  grad_device = NULL removes it. */
+fdtd_status fdtd_set_design(fdtd_ctx* ctx, int32_t domain, const int32_t lo[3], const int32_t hi[3],
+                            double* grad_device);
+
+/* Adjoint source of a monitor: cot_device (borrowed, complex FP64 interleaved, the monitor's
+ * layout) holds dJ/dRe F + i dJ/dIm F.  The adjoint injects dJ/df(t) = Re(conj(cot) exp(i w t))
+ * at the monitor cells.  NULL clears it. */
+fdtd_status fdtd_set_adjoint_source(fdtd_ctx* ctx, int32_t monitor_id, const void* cot_device);
+
+/* Starts an adjoint sweep at the current forward step count N: zeroes the adjoint state
+ * (cotangent of u^N) and injects the magnetic samples of time N + 1/2. */
+fdtd_status fdtd_adjoint_begin(fdtd_ctx* ctx);
+
+/* Transposes n_steps forward steps, m = A-1, A-2, ... where A is the index of the current
+ * adjoint state (N after fdtd_adjoint_begin).  When any design box is set, each transposed
+ * step m needs the forward state u^m (for the material cotangent): then n_steps must be 1 and
+ * the forward step count must equal m (FDTD_ESTATE otherwise); the caller re-creates u^m by
+ * checkpoint replay.  Without a design box any n_steps <= A is allowed. */
+fdtd_status fdtd_step_adjoint(fdtd_ctx* ctx, int32_t n_steps);
+
+/* Index A of the current adjoint state (the cotangent held is that of u^A). */
+fdtd_status fdtd_adjoint_step_count(fdtd_ctx* ctx, int64_t* a);
+
+/* Replaces the adjoint state's step index (after the caller wrote a natural adjoint state
+ * with fdtd_set_part, which = 1). */
+fdtd_status fdtd_set_adjoint_step_count(fdtd_ctx* ctx, int64_t a);
+
+/* ---- health ---- */
+/* Scans the forward state of every domain for NaN/Inf; returns FDTD_ENONFINITE if any
+ * (synchronises). */
+fdtd_status fdtd_check_finite(fdtd_ctx* ctx);
+
+/* Synchronises the context's stream, polling at most timeout_ms milliseconds
+ * (FDTD_ETIMEOUT if the work has not finished by then; the work itself is not cancelled). */
+fdtd_status fdtd_synchronize(fdtd_ctx* ctx, int32_t timeout_ms);
+
+/* Number of kernel launches this context has enqueued since creation (instrumentation). */
+fdtd_status fdtd_launch_count(fdtd_ctx* ctx, int64_t* n);
+
+/* ---- instrumentation: per-kernel device time with CUDA events on the context's stream ----
+ * Kernel classes: */
+enum {
+    FDTD_KERNEL_E = 0,        /* E update (Eq. (yee) first half, CPML, poles) */
+    FDTD_KERNEL_H = 1,        /* H update (second half, CPML, energy) */
+    FDTD_KERNEL_SOURCE = 2,   /* soft sources */
+    FDTD_KERNEL_DFT = 3,      /* running DFT monitors */
+    FDTD_KERNEL_STEP = 4,     /* device step counter */
+    FDTD_KERNEL_ADJ_E = 5,    /* transposed step, E side */
+    FDTD_KERNEL_ADJ_H = 6,    /* transposed step, H side */
+    FDTD_KERNEL_CLASSES = 7
+};
+/* Starts recording an event pair around every kernel launch (at most max_launches launches,
+ * later ones are not timed).  Adds two event records per launch to the stream. */
+fdtd_status fdtd_profile_begin(fdtd_ctx* ctx, int32_t max_launches);
+/* Stops recording, synchronises, and writes per class (FDTD_KERNEL_CLASSES entries each) the
+ * summed device milliseconds and the number of timed launches. */
+fdtd_status fdtd_profile_end(fdtd_ctx* ctx, double* ms_per_class, int64_t* launches_per_class);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBFDTD_FDTD_H */

@@ -1,0 +1,1483 @@
+// C-ABI of the gbfdtd library (declared in include/fdtd.h): context, memory plan, device
+// descriptors, forward stepping, adjoint sweep bookkeeping, snapshots.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "fdtd_internal.cuh"
+
+using namespace gbfdtd;
+
+namespace {
+
+struct DomainHost {
+    int n[3] = {0, 0, 0};
+    long long ncell = 0;
+    int dlo[3] = {0, 0, 0}, dhi[3] = {0, 0, 0}, ns[3] = {0, 0, 0};
+    fdtd_cpml cpml{};
+    const void* ie[3] = {nullptr, nullptr, nullptr};
+    const uint8_t* mask = nullptr;
+    int npole = 0;
+    fdtd_pole poles[kMaxPole];
+    int blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
+    long long bcell = 0;
+    void* F[6] = {};
+    void* A[6] = {};
+    void* psiE[3][2] = {};
+    void* psiH[3][2] = {};
+    void* apsiE[3][2] = {};
+    void* apsiH[3][2] = {};
+    void* cE[3] = {};
+    void* cH[3] = {};
+    void* ade = nullptr;
+    void* aade = nullptr;
+    double* energy = nullptr;
+    int energy_cap = 0;
+    int design = 0;
+    int glo[3] = {0, 0, 0}, ghi[3] = {0, 0, 0};
+    double* grad = nullptr;
+    std::vector<int> mons;
+};
+
+struct MonHost {
+    Mon m{};
+    std::vector<double> omega;
+};
+
+struct SrcHost {
+    Src s{};
+    double* wave = nullptr;
+};
+
+struct Slot {
+    void* buf = nullptr;
+    size_t bytes = 0;
+    int codec = 0;
+    long long step = 0;
+};
+
+}  // namespace
+
+struct fdtd_ctx {
+    int dtype = FDTD_F32;
+    size_t esz = 4;
+    double S = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<DomainHost> doms;
+    void* d_doms = nullptr;
+    std::vector<Tile> tiles;        // every tile (transposed kernels)
+    std::vector<Tile> tiles_gen;    // tiles touching CPML, PEC planes, domain edges or poles
+    std::vector<Tile> tiles_int;    // all other tiles
+    Tile* d_tiles = nullptr;
+    Tile* d_tiles_gen = nullptr;
+    Tile* d_tiles_int = nullptr;
+    int aniso = 0;
+    std::vector<MonHost> mons;
+    Mon* d_mons = nullptr;
+    int* d_entries[2] = {nullptr, nullptr};
+    long long* d_entry_begin[2] = {nullptr, nullptr};
+    int nentries[2] = {0, 0};
+    long long nthreads[2] = {0, 0};
+    std::vector<SrcHost> srcs;
+    Src* d_srcs[2] = {nullptr, nullptr};
+    int nsrc[2] = {0, 0};
+    long long nsrccells[2] = {0, 0};
+    int* d_step = nullptr;
+    int h_step_tmp = 0;
+    long long step = 0;
+    long long adj_step = 0;
+    int adj_pending = 0;
+    int dft_enabled = 1;
+    int energy_on = 0;
+    int phase_cap = 0;
+    long long launches = 0;
+    std::string err;
+    int poisoned = 0;
+    std::map<int, Slot> slots;
+    unsigned long long* d_flag = nullptr;
+    int* d_box = nullptr;
+    std::vector<void*> owned;   // every device allocation of the context
+    // CUDA graphs of kGraphSteps forward steps, keyed by (dft enabled, energy on)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    long long graph_launches[2][2] = {{0, 0}, {0, 0}};
+    int use_graphs = 1;
+    // instrumentation
+    int prof_on = 0;
+    int prof_used = 0;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_kind;
+};
+
+namespace {
+
+fdtd_status fail(fdtd_ctx* c, fdtd_status st, const std::string& msg) {
+    if (c) {
+        c->err = msg;
+        if (st == FDTD_ECUDA) c->poisoned = 1;
+    }
+    return st;
+}
+
+#define CK(ctx, call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail((ctx), FDTD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+
+#define CKL(ctx)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = cudaGetLastError();                                                       \
+        if (e_ != cudaSuccess) return fail((ctx), FDTD_ECUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define GUARD(ctx)                                                                                 \
+    do {                                                                                           \
+        if (!(ctx)) return FDTD_EINVAL;                                                            \
+        if ((ctx)->poisoned) return fail((ctx), FDTD_ESTATE, "context poisoned by an earlier CUDA error"); \
+    } while (0)
+
+fdtd_status dmalloc(fdtd_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return FDTD_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(c, FDTD_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    if (e != cudaSuccess) return fail(c, FDTD_ECUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    c->owned.push_back(*p);
+    CK(c, cudaMemsetAsync(*p, 0, bytes, c->stream));
+    return FDTD_OK;
+}
+
+void dfree(fdtd_ctx* c, void* p) {
+    if (!p) return;
+    for (auto it = c->owned.begin(); it != c->owned.end(); ++it)
+        if (*it == p) {
+            c->owned.erase(it);
+            break;
+        }
+    cudaFree(p);
+}
+
+Launch L(fdtd_ctx* c) { return Launch{c->stream, &c->launches}; }
+
+// CPML profile (Sec. 2.2, reading stated in include/fdtd.h): rows [b | c | 1/kappa] at
+// integer (E derivative) or half-integer (H derivative) nodes.
+void cpml_table(const fdtd_cpml& p, int q, int N, double S, bool half, std::vector<double>& out) {
+    out.assign(3 * (size_t)N, 0.0);
+    const int dlo = p.cells[2 * q], dhi = p.cells[2 * q + 1];
+    const double smax = p.sigma_max < 0 ? 0.8 * (p.m + 1.0) : p.sigma_max;
+    for (int j = 0; j < N; ++j) {
+        const double x = j + (half ? 0.5 : 0.0);
+        double rho = -1.0, d = 1.0;
+        if (dlo > 0 && x < dlo) {
+            rho = dlo - x;
+            d = dlo;
+        } else if (dhi > 0 && x > N - dhi) {
+            rho = x - (N - dhi);
+            d = dhi;
+        }
+        double b = 1.0, cc = 0.0, kinv = 1.0;
+        if (rho >= 0.0) {
+            if (rho > d) rho = d;
+            const double r = std::pow(rho / d, p.m);
+            const double sigma = smax * r;
+            const double kappa = 1.0 + (p.kappa_max - 1.0) * r;
+            const double alpha = p.alpha_max * (1.0 - rho / d);
+            b = std::exp(-(sigma / kappa + alpha) * S);
+            cc = sigma > 0.0 ? sigma * (b - 1.0) / (sigma * kappa + kappa * kappa * alpha) : 0.0;
+            kinv = 1.0 / kappa;
+        }
+        out[j] = b;
+        out[N + j] = cc;
+        out[2 * N + j] = kinv;
+    }
+}
+
+// Trapezoidal pole update (Sec. 2.3), closed form of (I - A/2)^-1 (I + A/2) with
+// A = [[0, 1], [-a0, -g]]:  M = [[1 + g/2 - a0/4, 1], [-a0, 1 - g/2 - a0/4]] / det,
+// det = 1 + g/2 + a0/4;  x-increment vector (b1/(4 det), b1/(2 det)).
+void pole_coef(const fdtd_pole& p, double M[4], double g[2]) {
+    const double w2 = p.omega_dt * p.omega_dt;
+    const double a0 = p.kind == FDTD_LORENTZ ? w2 : 0.0;
+    const double b1 = p.kind == FDTD_LORENTZ ? p.delta_eps * w2 : w2;
+    const double gm = p.gamma_dt;
+    const double det = 1.0 + 0.5 * gm + 0.25 * a0;
+    M[0] = (1.0 + 0.5 * gm - 0.25 * a0) / det;
+    M[1] = 1.0 / det;
+    M[2] = -a0 / det;
+    M[3] = (1.0 - 0.5 * gm - 0.25 * a0) / det;
+    g[0] = b1 / (4.0 * det);
+    g[1] = b1 / (2.0 * det);
+}
+
+long long part_size(const DomainHost& d, int part) {
+    if (part < 6) return d.ncell;
+    if (part < 18) {
+        const int a = ((part - 6) % 6) / 2, s = (part - 6) % 2;
+        const int ax = (a + 1 + s) % 3;
+        return d.ncell / d.n[ax] * d.ns[ax];
+    }
+    return d.bcell;
+}
+
+int part_count(const DomainHost& d) { return 18 + 6 * d.npole; }
+
+void* part_ptr(const DomainHost& d, int which, int part, size_t esz) {
+    if (part < 6) return which ? d.A[part] : d.F[part];
+    if (part < 12) {
+        const int a = (part - 6) / 2, s = (part - 6) % 2;
+        return which ? d.apsiE[a][s] : d.psiE[a][s];
+    }
+    if (part < 18) {
+        const int a = (part - 12) / 2, s = (part - 12) % 2;
+        return which ? d.apsiH[a][s] : d.psiH[a][s];
+    }
+    char* base = (char*)(which ? d.aade : d.ade);
+    if (!base) return nullptr;
+    return base + (size_t)(part - 18) * d.bcell * esz;
+}
+
+// Outermost extent of a part's array (slabs of the BF16 codec).
+long long part_planes(const DomainHost& d, int part) {
+    if (part < 6) return d.n[2];
+    if (part < 18) {
+        const int a = ((part - 6) % 6) / 2, s = (part - 6) % 2;
+        const int ax = (a + 1 + s) % 3;
+        return ax == 2 ? d.ns[2] : d.n[2];
+    }
+    return d.bhi[2] - d.blo[2];
+}
+
+template <typename T>
+void fill_dom(const fdtd_ctx* c, const DomainHost& h, Dom<T>& d) {
+    std::memset(&d, 0, sizeof(d));
+    for (int q = 0; q < 3; ++q) {
+        d.n[q] = h.n[q];
+        d.dlo[q] = h.dlo[q];
+        d.dhi[q] = h.dhi[q];
+        d.ns[q] = h.ns[q];
+        d.blo[q] = h.blo[q];
+        d.bhi[q] = h.bhi[q];
+        d.glo[q] = h.glo[q];
+        d.ghi[q] = h.ghi[q];
+        d.ie[q] = (const T*)h.ie[q];
+        d.cE[q] = (const T*)h.cE[q];
+        d.cH[q] = (const T*)h.cH[q];
+    }
+    d.ncell = h.ncell;
+    for (int f = 0; f < 6; ++f) {
+        d.F[f] = (T*)h.F[f];
+        d.A[f] = (T*)h.A[f];
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int s = 0; s < 2; ++s) {
+            d.psiE[a][s] = (T*)h.psiE[a][s];
+            d.psiH[a][s] = (T*)h.psiH[a][s];
+            d.apsiE[a][s] = (T*)h.apsiE[a][s];
+            d.apsiH[a][s] = (T*)h.apsiH[a][s];
+        }
+    d.mask = h.mask;
+    d.bcell = h.bcell;
+    d.ade = (T*)h.ade;
+    d.aade = (T*)h.aade;
+    d.npole = h.npole;
+    double G = 0.0;
+    for (int p = 0; p < h.npole; ++p) {
+        double M[4], g[2];
+        pole_coef(h.poles[p], M, g);
+        d.M00[p] = (T)M[0];
+        d.M01[p] = (T)M[1];
+        d.M10[p] = (T)M[2];
+        d.M11[p] = (T)M[3];
+        d.g0[p] = (T)g[0];
+        d.g1[p] = (T)g[1];
+        G += g[0];
+    }
+    d.G = (T)G;
+    d.design = h.design;
+    d.grad = h.grad;
+    d.nmon = (int)h.mons.size();
+    for (int i = 0; i < d.nmon; ++i) d.mon[i] = h.mons[i];
+    d.energy = c->energy_on ? h.energy : nullptr;
+    d.energy_cap = h.energy_cap;
+}
+
+template <typename T>
+fdtd_status sync_doms_t(fdtd_ctx* c) {
+    std::vector<Dom<T>> hd(c->doms.size());
+    for (size_t i = 0; i < c->doms.size(); ++i) fill_dom<T>(c, c->doms[i], hd[i]);
+    CK(c, cudaMemcpyAsync(c->d_doms, hd.data(), sizeof(Dom<T>) * hd.size(), cudaMemcpyHostToDevice, c->stream));
+    return FDTD_OK;
+}
+
+fdtd_status sync_doms(fdtd_ctx* c) { return c->dtype == FDTD_F32 ? sync_doms_t<float>(c) : sync_doms_t<double>(c); }
+
+fdtd_status ensure_phase(fdtd_ctx* c, long long need, bool* changed = nullptr) {
+    if (changed) *changed = false;
+    if (need <= c->phase_cap) return FDTD_OK;
+    if (changed) *changed = true;
+    long long cap = c->phase_cap ? c->phase_cap : 1024;
+    while (cap < need) cap *= 2;
+    for (auto& mh : c->mons) {
+        const int nf = mh.m.nf;
+        std::vector<double> tab((size_t)cap * 2 * nf * 2);
+        for (long long n = 0; n < cap; ++n)
+            for (int kind = 0; kind < 2; ++kind) {
+                const double t = (double)n + (kind ? 1.5 : 1.0);
+                for (int f = 0; f < nf; ++f) {
+                    const size_t o = (((size_t)n * 2 + kind) * nf + f) * 2;
+                    tab[o] = std::cos(mh.omega[f] * t);
+                    tab[o + 1] = std::sin(mh.omega[f] * t);
+                }
+            }
+        void* p = nullptr;
+        fdtd_status st = dmalloc(c, &p, tab.size() * sizeof(double));
+        if (st != FDTD_OK) return st;
+        CK(c, cudaMemcpyAsync(p, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        if (mh.m.phase) {
+            CK(c, cudaStreamSynchronize(c->stream));
+            dfree(c, (void*)mh.m.phase);
+        }
+        mh.m.phase = (const double2*)p;
+        mh.m.cap = (int)cap;
+    }
+    c->phase_cap = (int)cap;
+    return FDTD_OK;
+}
+
+void drop_graphs(fdtd_ctx* c);
+
+fdtd_status sync_mons(fdtd_ctx* c) {
+    drop_graphs(c);
+    if (c->d_mons) {
+        CK(c, cudaStreamSynchronize(c->stream));
+        dfree(c, c->d_mons);
+        c->d_mons = nullptr;
+    }
+    for (int kind = 0; kind < 2; ++kind) {
+        if (c->d_entries[kind]) dfree(c, c->d_entries[kind]);
+        if (c->d_entry_begin[kind]) dfree(c, c->d_entry_begin[kind]);
+        c->d_entries[kind] = nullptr;
+        c->d_entry_begin[kind] = nullptr;
+        c->nentries[kind] = 0;
+        c->nthreads[kind] = 0;
+    }
+    if (c->mons.empty()) return FDTD_OK;
+    std::vector<Mon> hm;
+    for (auto& m : c->mons) hm.push_back(m.m);
+    fdtd_status st = dmalloc(c, (void**)&c->d_mons, sizeof(Mon) * hm.size());
+    if (st != FDTD_OK) return st;
+    CK(c, cudaMemcpyAsync(c->d_mons, hm.data(), sizeof(Mon) * hm.size(), cudaMemcpyHostToDevice, c->stream));
+    for (int kind = 0; kind < 2; ++kind) {
+        std::vector<int> ent;
+        std::vector<long long> beg;
+        long long tot = 0;
+        for (size_t mi = 0; mi < c->mons.size(); ++mi) {
+            const Mon& m = c->mons[mi].m;
+            for (int ci = 0; ci < m.ncomp; ++ci) {
+                if ((m.comps[ci] >= 3) != (kind == 1)) continue;
+                ent.push_back((int)mi);
+                ent.push_back(ci);
+                beg.push_back(tot);
+                tot += m.ncell;
+            }
+        }
+        if (ent.empty()) continue;
+        st = dmalloc(c, (void**)&c->d_entries[kind], ent.size() * sizeof(int));
+        if (st != FDTD_OK) return st;
+        st = dmalloc(c, (void**)&c->d_entry_begin[kind], beg.size() * sizeof(long long));
+        if (st != FDTD_OK) return st;
+        CK(c, cudaMemcpyAsync(c->d_entries[kind], ent.data(), ent.size() * sizeof(int), cudaMemcpyHostToDevice,
+                              c->stream));
+        CK(c, cudaMemcpyAsync(c->d_entry_begin[kind], beg.data(), beg.size() * sizeof(long long),
+                              cudaMemcpyHostToDevice, c->stream));
+        c->nentries[kind] = (int)beg.size();
+        c->nthreads[kind] = tot;
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FDTD_OK;
+}
+
+fdtd_status sync_srcs(fdtd_ctx* c) {
+    CK(c, cudaStreamSynchronize(c->stream));
+    drop_graphs(c);
+    for (int kind = 0; kind < 2; ++kind) {
+        if (c->d_srcs[kind]) dfree(c, c->d_srcs[kind]);
+        c->d_srcs[kind] = nullptr;
+        std::vector<Src> hs;
+        long long tot = 0;
+        for (auto& s : c->srcs) {
+            if ((s.s.comp >= 3) != (kind == 1)) continue;
+            Src x = s.s;
+            x.begin = tot;
+            tot += x.ncell;
+            hs.push_back(x);
+        }
+        c->nsrc[kind] = (int)hs.size();
+        c->nsrccells[kind] = tot;
+        if (hs.empty()) continue;
+        fdtd_status st = dmalloc(c, (void**)&c->d_srcs[kind], sizeof(Src) * hs.size());
+        if (st != FDTD_OK) return st;
+        CK(c, cudaMemcpyAsync(c->d_srcs[kind], hs.data(), sizeof(Src) * hs.size(), cudaMemcpyHostToDevice,
+                              c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FDTD_OK;
+}
+
+bool valid_dom(const fdtd_ctx* c, int d) { return d >= 0 && d < (int)c->doms.size(); }
+
+bool valid_box(const DomainHost& d, const int32_t lo[3], const int32_t hi[3]) {
+    for (int q = 0; q < 3; ++q)
+        if (lo[q] < 0 || hi[q] > d.n[q] || lo[q] >= hi[q]) return false;
+    return true;
+}
+
+fdtd_status check_material(fdtd_ctx* c, const fdtd_material& m) {
+    for (int a = 0; a < 3; ++a)
+        if (!m.inv_eps[a]) return fail(c, FDTD_EINVAL, "inv_eps pointer is NULL");
+    if (m.n_poles < 0 || m.n_poles > kMaxPole) return fail(c, FDTD_EINVAL, "n_poles must be in [0, 16]");
+    if (m.n_poles > 0 && (!m.poles || !m.pole_mask)) return fail(c, FDTD_EINVAL, "poles need a table and a mask");
+    for (int p = 0; p < m.n_poles; ++p) {
+        const fdtd_pole& q = m.poles[p];
+        if ((q.kind != FDTD_LORENTZ && q.kind != FDTD_DRUDE) || !(q.gamma_dt >= 0) || !(q.omega_dt >= 0) ||
+            !std::isfinite(q.delta_eps))
+            return fail(c, FDTD_EINVAL, "invalid pole parameters");
+    }
+    return FDTD_OK;
+}
+
+template <typename T>
+fdtd_status admission_t(fdtd_ctx* c, int di) {
+    Dom<T> hd;
+    fill_dom<T>(c, c->doms[di], hd);
+    Dom<T>* dd = nullptr;
+    fdtd_status st = dmalloc(c, (void**)&dd, sizeof(Dom<T>));
+    if (st != FDTD_OK) return st;
+    CK(c, cudaMemcpyAsync(dd, &hd, sizeof(Dom<T>), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned long long), c->stream));
+    launch_admission<T>(L(c), dd, hd, c->d_flag);
+    CKL(c);
+    unsigned long long bad = 0;
+    CK(c, cudaMemcpyAsync(&bad, c->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    dfree(c, dd);
+    if (bad)
+        return fail(c, FDTD_ETENSOR,
+                    "domain " + std::to_string(di) + ": " + std::to_string(bad) +
+                        " CPML cells hold a permittivity whose face-normal eigenvalue is the intermediate one");
+    return FDTD_OK;
+}
+
+fdtd_status admission(fdtd_ctx* c, int di) {
+    const DomainHost& d = c->doms[di];
+    if (d.ie[0] == d.ie[1] && d.ie[1] == d.ie[2]) return FDTD_OK;  // isotropic: always admitted
+    if (d.ns[0] + d.ns[1] + d.ns[2] == 0) return FDTD_OK;
+    return c->dtype == FDTD_F32 ? admission_t<float>(c, di) : admission_t<double>(c, di);
+}
+
+fdtd_status mask_box(fdtd_ctx* c, const uint8_t* mask, const int n[3], int lo[3], int hi[3]) {
+    int init[6] = {n[0], n[1], n[2], 0, 0, 0};
+    CK(c, cudaMemcpyAsync(c->d_box, init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
+    launch_mask_box(L(c), mask, n[0], n[1], n[2], c->d_box);
+    CKL(c);
+    int out[6];
+    CK(c, cudaMemcpyAsync(out, c->d_box, sizeof(out), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (out[3] == 0) {
+        for (int q = 0; q < 3; ++q) lo[q] = hi[q] = 0;
+    } else {
+        for (int q = 0; q < 3; ++q) {
+            lo[q] = out[q];
+            hi[q] = out[3 + q];
+        }
+    }
+    return FDTD_OK;
+}
+
+// Tiles of kTileX x kTileY columns and a z chunk chosen so that the grid holds several blocks
+// per SM.  A tile is "interior" when every cell and its -1 / +1 neighbours along each axis lie
+// strictly inside the domain and outside the CPML slabs and the pole box.
+void build_tiles(fdtd_ctx* c) {
+    c->tiles.clear();
+    c->tiles_gen.clear();
+    c->tiles_int.clear();
+    long long cols = 0, zsum = 0;
+    for (const auto& d : c->doms) {
+        cols += (long long)((d.n[0] + kTileX - 1) / kTileX) * ((d.n[1] + kTileY - 1) / kTileY);
+        zsum += (long long)((d.n[0] + kTileX - 1) / kTileX) * ((d.n[1] + kTileY - 1) / kTileY) * d.n[2];
+    }
+    const long long target = 152 * 8;
+    int zc = (int)(zsum / target);
+    zc = zc < 4 ? 4 : (zc > 32 ? 32 : zc);
+    (void)cols;
+    for (int di = 0; di < (int)c->doms.size(); ++di) {
+        const DomainHost& d = c->doms[di];
+        for (int z0 = 0; z0 < d.n[2]; z0 += zc)
+            for (int y0 = 0; y0 < d.n[1]; y0 += kTileY)
+                for (int x0 = 0; x0 < d.n[0]; x0 += kTileX) {
+                    Tile t;
+                    t.dom = di;
+                    t.x0 = x0;
+                    t.y0 = y0;
+                    t.z0 = z0;
+                    t.z1 = z0 + zc < d.n[2] ? z0 + zc : d.n[2];
+                    const int lo[3] = {x0, y0, z0};
+                    const int hi[3] = {x0 + kTileX < d.n[0] ? x0 + kTileX : d.n[0],
+                                       y0 + kTileY < d.n[1] ? y0 + kTileY : d.n[1], t.z1};
+                    // interior: no cell in a slab or on a PEC plane, the -1 neighbour outside the low
+                    // H slab (the transposed H update carries the H cell's CPML terms to E at +1),
+                    // the +1 neighbour inside the domain
+                    bool inner = true;
+                    for (int q = 0; q < 3; ++q) {
+                        const int a = d.dlo[q] > 0 ? d.dlo[q] + 1 : 1;
+                        const int b = d.n[q] - (d.dhi[q] > 1 ? d.dhi[q] : 1);
+                        if (lo[q] < a || hi[q] > b) inner = false;
+                    }
+                    if (d.npole > 0 && d.bcell > 0) {
+                        bool meet = true;
+                        for (int q = 0; q < 3; ++q)
+                            if (hi[q] <= d.blo[q] || lo[q] >= d.bhi[q]) meet = false;
+                        if (meet) inner = false;
+                    }
+                    c->tiles.push_back(t);
+                    (inner ? c->tiles_int : c->tiles_gen).push_back(t);
+                }
+    }
+}
+
+// Event pair around one launch when profiling (two records on the stream, no work changed).
+struct Prof {
+    fdtd_ctx* c;
+    bool on;
+    Prof(fdtd_ctx* cc, int kind) : c(cc), on(false) {
+        if (!c->prof_on || c->prof_used + 2 > (int)c->prof_ev.size()) return;
+        on = true;
+        c->prof_kind[c->prof_used / 2] = kind;
+        cudaEventRecord(c->prof_ev[c->prof_used], c->stream);
+    }
+    ~Prof() {
+        if (!on) return;
+        cudaEventRecord(c->prof_ev[c->prof_used + 1], c->stream);
+        c->prof_used += 2;
+    }
+};
+
+template <typename T>
+void step_once(fdtd_ctx* c, cudaStream_t st) {
+    const Launch l{st, &c->launches};
+    const Dom<T>* dd = (const Dom<T>*)c->d_doms;
+    const int nt = (int)c->tiles.size();
+    (void)nt;
+    {
+        Prof p(c, FDTD_KERNEL_E);
+        launch_e_update<T>(l, dd, c->d_tiles_int, (int)c->tiles_int.size(), (T)c->S, 0, c->aniso);
+    }
+    {
+        Prof p(c, FDTD_KERNEL_E);
+        launch_e_update<T>(l, dd, c->d_tiles_gen, (int)c->tiles_gen.size(), (T)c->S, 1, 1);
+    }
+    if (c->nsrc[0]) {
+        Prof p(c, FDTD_KERNEL_SOURCE);
+        launch_sources<T>(l, dd, c->d_srcs[0], c->nsrc[0], c->nsrccells[0], c->d_step);
+    }
+    if (c->dft_enabled && c->nentries[0]) {
+        Prof p(c, FDTD_KERNEL_DFT);
+        launch_dft<T>(l, dd, c->d_mons, c->d_entries[0], c->nentries[0], c->nthreads[0], c->d_entry_begin[0],
+                      c->d_step, 0);
+    }
+    {
+        Prof p(c, FDTD_KERNEL_H);
+        launch_h_update<T>(l, dd, c->d_tiles_int, (int)c->tiles_int.size(), (T)c->S, c->d_step, 0, c->energy_on);
+    }
+    {
+        Prof p(c, FDTD_KERNEL_H);
+        launch_h_update<T>(l, dd, c->d_tiles_gen, (int)c->tiles_gen.size(), (T)c->S, c->d_step, 1, c->energy_on);
+    }
+    if (c->nsrc[1]) {
+        Prof p(c, FDTD_KERNEL_SOURCE);
+        launch_sources<T>(l, dd, c->d_srcs[1], c->nsrc[1], c->nsrccells[1], c->d_step);
+    }
+    if (c->dft_enabled && c->nentries[1]) {
+        Prof p(c, FDTD_KERNEL_DFT);
+        launch_dft<T>(l, dd, c->d_mons, c->d_entries[1], c->nentries[1], c->nthreads[1], c->d_entry_begin[1],
+                      c->d_step, 1);
+    }
+    {
+        Prof p(c, FDTD_KERNEL_STEP);
+        launch_advance(l, c->d_step, 1);
+    }
+}
+
+template <typename T>
+void adj_once(fdtd_ctx* c, int m) {
+    const Launch l = L(c);
+    const Dom<T>* dd = (const Dom<T>*)c->d_doms;
+    const int nt = (int)c->tiles.size();
+    (void)nt;
+    {
+        Prof p(c, FDTD_KERNEL_ADJ_E);
+        launch_adj_e<T>(l, dd, c->d_mons, c->d_tiles_int, (int)c->tiles_int.size(), (T)c->S, m, c->adj_pending, 0,
+                        c->aniso);
+    }
+    {
+        Prof p(c, FDTD_KERNEL_ADJ_E);
+        launch_adj_e<T>(l, dd, c->d_mons, c->d_tiles_gen, (int)c->tiles_gen.size(), (T)c->S, m, c->adj_pending, 1, 1);
+    }
+    {
+        Prof p(c, FDTD_KERNEL_ADJ_H);
+        launch_adj_h<T>(l, dd, c->d_mons, c->d_tiles_int, (int)c->tiles_int.size(), (T)c->S, m, 0);
+    }
+    {
+        Prof p(c, FDTD_KERNEL_ADJ_H);
+        launch_adj_h<T>(l, dd, c->d_mons, c->d_tiles_gen, (int)c->tiles_gen.size(), (T)c->S, m, 1);
+    }
+}
+
+constexpr int kGraphSteps = 32;
+
+void drop_graphs(fdtd_ctx* c) {
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            if (c->graph[a][b]) {
+                cudaGraphExecDestroy(c->graph[a][b]);
+                c->graph[a][b] = nullptr;
+            }
+}
+
+// Captures kGraphSteps forward steps on a private stream (the step index, source amplitudes
+// and DFT phases are read from device memory, so one graph serves every replay).
+fdtd_status build_graph(fdtd_ctx* c) {
+    const int a = c->dft_enabled, b = c->energy_on;
+    if (c->graph[a][b]) return FDTD_OK;
+    if (!c->cap_stream) CK(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const long long l0 = c->launches;
+    CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int s = 0; s < kGraphSteps; ++s) {
+        if (c->dtype == FDTD_F32)
+            step_once<float>(c, c->cap_stream);
+        else
+            step_once<double>(c, c->cap_stream);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    c->launches = l0;
+    if (e != cudaSuccess) return fail(c, FDTD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph[a][b], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph[a][b] = nullptr;
+        return fail(c, FDTD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    long long per = 0;
+    {
+        // count the launches of one step without enqueuing anything
+        int tiles_i = c->tiles_int.empty() ? 0 : 1, tiles_g = c->tiles_gen.empty() ? 0 : 1;
+        per = 2 * (tiles_i + tiles_g) + (c->nsrc[0] ? 1 : 0) + (c->nsrc[1] ? 1 : 0) +
+              (c->dft_enabled && c->nentries[0] ? 1 : 0) + (c->dft_enabled && c->nentries[1] ? 1 : 0) + 1;
+    }
+    c->graph_launches[a][b] = per * kGraphSteps;
+    return FDTD_OK;
+}
+
+fdtd_status flush_adjoint(fdtd_ctx* c) {
+    if (!c->adj_pending) return FDTD_OK;
+    if (c->dtype == FDTD_F32)
+        launch_adj_flush<float>(L(c), (const Dom<float>*)c->d_doms, c->d_tiles, (int)c->tiles.size(), (float)c->S);
+    else
+        launch_adj_flush<double>(L(c), (const Dom<double>*)c->d_doms, c->d_tiles, (int)c->tiles.size(), c->S);
+    CKL(c);
+    c->adj_pending = 0;
+    return FDTD_OK;
+}
+
+fdtd_status set_device_step(fdtd_ctx* c, long long s) {
+    c->h_step_tmp = (int)s;
+    CK(c, cudaMemcpyAsync(c->d_step, &c->h_step_tmp, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FDTD_OK;
+}
+
+size_t snapshot_bytes(const fdtd_ctx* c, int codec) {
+    size_t tot = 0;
+    for (const auto& d : c->doms)
+        for (int p = 0; p < part_count(d); ++p) {
+            const long long n = part_size(d, p);
+            if (n == 0) continue;
+            const size_t b = codec == FDTD_CODEC_BF16 ? (size_t)n * 2 + (size_t)part_planes(d, p) * 4 : (size_t)n * c->esz;
+            tot += (b + 255) & ~(size_t)255;
+        }
+    return tot;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fdtd_version(void) { return "gbfdtd 0.1 (sm_103a)"; }
+
+static thread_local std::string g_create_err;
+
+const char* fdtd_last_error(const fdtd_ctx* ctx) {
+    if (!ctx) return g_create_err.c_str();
+    return ctx->err.c_str();
+}
+
+fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cpml* cpml,
+                        const fdtd_material* materials, void* stream, fdtd_ctx** out) {
+    if (!out || n_domains < 1 || !grids || !cpml || !materials) return FDTD_EINVAL;
+    *out = nullptr;
+    fdtd_ctx* c = new fdtd_ctx();
+    c->stream = (cudaStream_t)stream;
+    c->dtype = grids[0].dtype;
+    g_create_err.clear();
+    auto bail = [&](fdtd_status st) {
+        g_create_err = c->err.empty() ? std::string("fdtd_create failed with status ") + std::to_string((int)st) : c->err;
+        c->poisoned = 0;
+        fdtd_destroy(c);
+        return st;
+    };
+    if (c->dtype != FDTD_F32 && c->dtype != FDTD_F64) return bail(FDTD_EINVAL);
+    c->esz = c->dtype == FDTD_F32 ? 4 : 8;
+    c->S = grids[0].courant;
+    for (int di = 0; di < n_domains; ++di) {
+        const fdtd_grid& g = grids[di];
+        if (g.dtype != c->dtype || g.courant != c->S) return bail(FDTD_EINVAL);
+        if (g.nx < 2 || g.ny < 2 || g.nz < 2 || !(g.dx > 0) || !(g.courant > 0)) return bail(FDTD_EINVAL);
+        if ((long long)g.nx * g.ny * g.nz >= (1ll << 40) || g.nx > 65535 || g.ny > 65535) return bail(FDTD_EINVAL);
+        if (g.dt != 0.0 && std::fabs(g.dt - g.courant * g.dx) > 1e-12 * g.courant * g.dx) return bail(FDTD_EINVAL);
+        if (g.courant * std::sqrt(3.0) > 0.99 * (1.0 + 1e-12)) return bail(FDTD_ECFL);
+        const fdtd_cpml& p = cpml[di];
+        for (int q = 0; q < 3; ++q) {
+            const int n = q == 0 ? g.nx : (q == 1 ? g.ny : g.nz);
+            if (p.cells[2 * q] < 0 || p.cells[2 * q + 1] < 0 || p.cells[2 * q] + p.cells[2 * q + 1] > n - 2)
+                return bail(FDTD_EINVAL);
+        }
+        if ((p.cells[0] | p.cells[1] | p.cells[2] | p.cells[3] | p.cells[4] | p.cells[5]) &&
+            (!(p.m >= 0) || !(p.kappa_max >= 1) || !(p.alpha_max >= 0)))
+            return bail(FDTD_EINVAL);
+        if (check_material(c, materials[di]) != FDTD_OK) return bail(FDTD_EINVAL);
+    }
+    // scratch
+    cudaError_t e = cudaMalloc((void**)&c->d_flag, 64);
+    if (e != cudaSuccess) return bail(FDTD_ECUDA);
+    c->owned.push_back(c->d_flag);
+    e = cudaMalloc((void**)&c->d_box, 64);
+    if (e != cudaSuccess) return bail(FDTD_ECUDA);
+    c->owned.push_back(c->d_box);
+    e = cudaMalloc((void**)&c->d_step, 64);
+    if (e != cudaSuccess) return bail(FDTD_ECUDA);
+    c->owned.push_back(c->d_step);
+    if (cudaMemsetAsync(c->d_step, 0, 64, c->stream) != cudaSuccess) return bail(FDTD_ECUDA);
+
+    // domain geometry, pole boxes and the memory plan
+    c->doms.resize(n_domains);
+    size_t plan = 0;
+    for (int di = 0; di < n_domains; ++di) {
+        DomainHost& d = c->doms[di];
+        const fdtd_grid& g = grids[di];
+        d.n[0] = g.nx;
+        d.n[1] = g.ny;
+        d.n[2] = g.nz;
+        d.ncell = (long long)g.nx * g.ny * g.nz;
+        d.cpml = cpml[di];
+        for (int q = 0; q < 3; ++q) {
+            d.dlo[q] = cpml[di].cells[2 * q];
+            d.dhi[q] = cpml[di].cells[2 * q + 1];
+            d.ns[q] = d.dlo[q] + d.dhi[q];
+        }
+        const fdtd_material& m = materials[di];
+        for (int a = 0; a < 3; ++a) d.ie[a] = m.inv_eps[a];
+        d.npole = m.n_poles;
+        for (int p = 0; p < m.n_poles; ++p) d.poles[p] = m.poles[p];
+        d.mask = m.n_poles > 0 ? m.pole_mask : nullptr;
+        if (d.mask) {
+            fdtd_status st = mask_box(c, d.mask, d.n, d.blo, d.bhi);
+            if (st != FDTD_OK) return bail(st);
+        }
+        d.bcell = (long long)(d.bhi[0] - d.blo[0]) * (d.bhi[1] - d.blo[1]) * (d.bhi[2] - d.blo[2]);
+        if (d.bcell == 0) {
+            d.npole = 0;
+            d.mask = nullptr;
+        }
+        plan += 12 * (size_t)d.ncell * c->esz;
+        for (int q = 0; q < 3; ++q) plan += 8 * (size_t)(d.ncell / d.n[q]) * d.ns[q] * c->esz + 6 * d.n[q] * c->esz;
+        plan += 2 * 6 * (size_t)d.npole * d.bcell * c->esz;
+    }
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return bail(FDTD_ECUDA);
+    if (plan + (64ull << 20) > free_b) {
+        c->err = "memory plan " + std::to_string(plan) + " B exceeds free device memory " + std::to_string(free_b) + " B";
+        return bail(FDTD_ENOMEM);
+    }
+    for (int di = 0; di < n_domains; ++di) {
+        DomainHost& d = c->doms[di];
+        const size_t fb = (size_t)d.ncell * c->esz;
+        for (int f = 0; f < 6; ++f) {
+            if (dmalloc(c, &d.F[f], fb) != FDTD_OK) return bail(FDTD_ENOMEM);
+            if (dmalloc(c, &d.A[f], fb) != FDTD_OK) return bail(FDTD_ENOMEM);
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int s = 0; s < 2; ++s) {
+                const int ax = (a + 1 + s) % 3;
+                const size_t sb = (size_t)(d.ncell / d.n[ax]) * d.ns[ax] * c->esz;
+                if (dmalloc(c, &d.psiE[a][s], sb) || dmalloc(c, &d.psiH[a][s], sb) || dmalloc(c, &d.apsiE[a][s], sb) ||
+                    dmalloc(c, &d.apsiH[a][s], sb))
+                    return bail(FDTD_ENOMEM);
+            }
+        for (int q = 0; q < 3; ++q) {
+            std::vector<double> te, th;
+            cpml_table(d.cpml, q, d.n[q], c->S, false, te);
+            cpml_table(d.cpml, q, d.n[q], c->S, true, th);
+            const size_t tb = te.size() * c->esz;
+            if (dmalloc(c, &d.cE[q], tb) || dmalloc(c, &d.cH[q], tb)) return bail(FDTD_ENOMEM);
+            std::vector<float> fe(te.begin(), te.end()), fh(th.begin(), th.end());
+            const void* se = c->dtype == FDTD_F32 ? (const void*)fe.data() : (const void*)te.data();
+            const void* sh = c->dtype == FDTD_F32 ? (const void*)fh.data() : (const void*)th.data();
+            if (cudaMemcpyAsync(d.cE[q], se, tb, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(d.cH[q], sh, tb, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess)
+                return bail(FDTD_ECUDA);
+        }
+        const size_t ab = 6 * (size_t)d.npole * d.bcell * c->esz;
+        if (dmalloc(c, &d.ade, ab) || dmalloc(c, &d.aade, ab)) return bail(FDTD_ENOMEM);
+    }
+    const size_t domb = (c->dtype == FDTD_F32 ? sizeof(Dom<float>) : sizeof(Dom<double>)) * n_domains;
+    if (dmalloc(c, &c->d_doms, domb) != FDTD_OK) return bail(FDTD_ENOMEM);
+    build_tiles(c);
+    for (int di = 0; di < n_domains; ++di) {
+        const DomainHost& d = c->doms[di];
+        if (d.ie[0] != d.ie[1] || d.ie[1] != d.ie[2]) c->aniso = 1;
+    }
+    {
+        std::vector<Tile>* lists[3] = {&c->tiles, &c->tiles_gen, &c->tiles_int};
+        Tile** dst[3] = {&c->d_tiles, &c->d_tiles_gen, &c->d_tiles_int};
+        for (int li = 0; li < 3; ++li) {
+            if (lists[li]->empty()) continue;
+            if (dmalloc(c, (void**)dst[li], sizeof(Tile) * lists[li]->size()) != FDTD_OK) return bail(FDTD_ENOMEM);
+            if (cudaMemcpyAsync(*dst[li], lists[li]->data(), sizeof(Tile) * lists[li]->size(), cudaMemcpyHostToDevice,
+                                c->stream) != cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess)
+                return bail(FDTD_ECUDA);
+        }
+    }
+    if (sync_doms(c) != FDTD_OK) return bail(FDTD_ECUDA);
+    for (int di = 0; di < n_domains; ++di) {
+        fdtd_status st = admission(c, di);
+        if (st != FDTD_OK) return bail(st);
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(FDTD_ECUDA);
+    *out = c;
+    return FDTD_OK;
+}
+
+static void prof_release(fdtd_ctx* ctx);
+
+fdtd_status fdtd_destroy(fdtd_ctx* ctx) {
+    if (!ctx) return FDTD_OK;
+    cudaStreamSynchronize(ctx->stream);
+    prof_release(ctx);
+    drop_graphs(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (void* p : ctx->owned) cudaFree(p);
+    for (auto& s : ctx->slots) cudaFree(s.second.buf);
+    delete ctx;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_material(fdtd_ctx* ctx, int32_t domain, const fdtd_material* m) {
+    GUARD(ctx);
+    if (!valid_dom(ctx, domain) || !m) return fail(ctx, FDTD_EINVAL, "bad domain or material");
+    fdtd_status st = check_material(ctx, *m);
+    if (st != FDTD_OK) return st;
+    DomainHost& d = ctx->doms[domain];
+    if (m->n_poles != d.npole) return fail(ctx, FDTD_EINVAL, "the pole count cannot change after create");
+    if (d.npole > 0) {
+        int lo[3], hi[3];
+        st = mask_box(ctx, m->pole_mask, d.n, lo, hi);
+        if (st != FDTD_OK) return st;
+        for (int q = 0; q < 3; ++q)
+            if (hi[q] > lo[q] && (lo[q] < d.blo[q] || hi[q] > d.bhi[q]))
+                return fail(ctx, FDTD_EINVAL, "dispersive cells outside the pole-state box chosen at create");
+    }
+    const void* old[3] = {d.ie[0], d.ie[1], d.ie[2]};
+    const uint8_t* oldm = d.mask;
+    fdtd_pole oldp[kMaxPole];
+    std::memcpy(oldp, d.poles, sizeof(oldp));
+    for (int a = 0; a < 3; ++a) d.ie[a] = m->inv_eps[a];
+    for (int p = 0; p < m->n_poles; ++p) d.poles[p] = m->poles[p];
+    if (d.npole > 0) d.mask = m->pole_mask;
+    if (d.ie[0] != d.ie[1] || d.ie[1] != d.ie[2]) ctx->aniso = 1;
+    st = admission(ctx, domain);
+    if (st != FDTD_OK) {
+        for (int a = 0; a < 3; ++a) d.ie[a] = old[a];
+        d.mask = oldm;
+        std::memcpy(d.poles, oldp, sizeof(oldp));
+        return st;
+    }
+    return sync_doms(ctx);
+}
+
+fdtd_status fdtd_add_source(fdtd_ctx* ctx, int32_t domain, int32_t component, const int32_t lo[3],
+                            const int32_t hi[3], const double* waveform, int32_t n_steps, int32_t* source_id) {
+    GUARD(ctx);
+    if (!valid_dom(ctx, domain) || component < 0 || component > 5 || !lo || !hi || n_steps < 0 ||
+        (n_steps > 0 && !waveform))
+        return fail(ctx, FDTD_EINVAL, "bad source arguments");
+    const DomainHost& d = ctx->doms[domain];
+    if (!valid_box(d, lo, hi)) return fail(ctx, FDTD_EINVAL, "source box outside the domain");
+    for (auto& s : ctx->srcs) {
+        if (s.s.dom != domain || s.s.comp != component) continue;
+        bool overlap = true;
+        for (int q = 0; q < 3; ++q)
+            if (hi[q] <= s.s.lo[q] || lo[q] >= s.s.hi[q]) overlap = false;
+        if (overlap) return fail(ctx, FDTD_EINVAL, "source boxes of one component must not overlap");
+    }
+    SrcHost sh;
+    sh.s.dom = domain;
+    sh.s.comp = component;
+    for (int q = 0; q < 3; ++q) {
+        sh.s.lo[q] = lo[q];
+        sh.s.hi[q] = hi[q];
+    }
+    sh.s.bx = hi[0] - lo[0];
+    sh.s.by = hi[1] - lo[1];
+    sh.s.ncell = (long long)sh.s.bx * sh.s.by * (hi[2] - lo[2]);
+    sh.s.n = n_steps;
+    fdtd_status st = dmalloc(ctx, (void**)&sh.wave, sizeof(double) * (n_steps > 0 ? n_steps : 1));
+    if (st != FDTD_OK) return st;
+    if (n_steps > 0) {
+        CK(ctx, cudaMemcpyAsync(sh.wave, waveform, sizeof(double) * n_steps, cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    sh.s.wave = sh.wave;
+    ctx->srcs.push_back(sh);
+    if (source_id) *source_id = (int)ctx->srcs.size() - 1;
+    return sync_srcs(ctx);
+}
+
+fdtd_status fdtd_add_dft_monitor(fdtd_ctx* ctx, int32_t domain, const int32_t lo[3], const int32_t hi[3],
+                                 uint32_t component_mask, int32_t n_freq, const double* omega_dt,
+                                 int32_t* monitor_id) {
+    GUARD(ctx);
+    if (!valid_dom(ctx, domain) || !lo || !hi || n_freq < 1 || !omega_dt || (component_mask & ~63u) ||
+        component_mask == 0)
+        return fail(ctx, FDTD_EINVAL, "bad monitor arguments");
+    DomainHost& d = ctx->doms[domain];
+    if (!valid_box(d, lo, hi)) return fail(ctx, FDTD_EINVAL, "monitor box outside the domain");
+    if ((int)d.mons.size() >= kMaxMonPerDom) return fail(ctx, FDTD_EINVAL, "at most 8 monitors per domain");
+    MonHost mh;
+    Mon& m = mh.m;
+    m.dom = domain;
+    for (int q = 0; q < 3; ++q) {
+        m.lo[q] = lo[q];
+        m.hi[q] = hi[q];
+    }
+    m.bx = hi[0] - lo[0];
+    m.by = hi[1] - lo[1];
+    m.ncell = (long long)m.bx * m.by * (hi[2] - lo[2]);
+    m.nf = n_freq;
+    m.mask = component_mask;
+    m.ncomp = 0;
+    for (int cc = 0; cc < 6; ++cc)
+        if (component_mask & (1u << cc)) m.comps[m.ncomp++] = cc;
+    mh.omega.assign(omega_dt, omega_dt + n_freq);
+    fdtd_status st = dmalloc(ctx, (void**)&m.acc, sizeof(double2) * m.ncomp * n_freq * m.ncell);
+    if (st != FDTD_OK) return st;
+    ctx->mons.push_back(mh);
+    const int id = (int)ctx->mons.size() - 1;
+    d.mons.push_back(id);
+    // (re)build phase tables for every monitor at the current capacity
+    const int cap = ctx->phase_cap;
+    ctx->phase_cap = 0;
+    for (auto& x : ctx->mons)
+        if (x.m.phase) {
+            CK(ctx, cudaStreamSynchronize(ctx->stream));
+            dfree(ctx, (void*)x.m.phase);
+            x.m.phase = nullptr;
+        }
+    st = ensure_phase(ctx, cap > 0 ? cap : 1024);
+    if (st != FDTD_OK) return st;
+    if (monitor_id) *monitor_id = id;
+    st = sync_mons(ctx);
+    if (st != FDTD_OK) return st;
+    return sync_doms(ctx);
+}
+
+fdtd_status fdtd_dft_size(fdtd_ctx* ctx, int32_t monitor_id, int64_t* n) {
+    GUARD(ctx);
+    if (monitor_id < 0 || monitor_id >= (int)ctx->mons.size() || !n) return fail(ctx, FDTD_EINVAL, "bad monitor id");
+    const Mon& m = ctx->mons[monitor_id].m;
+    *n = (int64_t)m.ncomp * m.nf * m.ncell;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_dft_read(fdtd_ctx* ctx, int32_t monitor_id, void* dst, size_t bytes, int32_t dst_on_device) {
+    GUARD(ctx);
+    int64_t n = 0;
+    fdtd_status st = fdtd_dft_size(ctx, monitor_id, &n);
+    if (st != FDTD_OK) return st;
+    if (!dst || bytes < (size_t)n * 16) return fail(ctx, FDTD_EINVAL, "destination too small");
+    const Mon& m = ctx->mons[monitor_id].m;
+    CK(ctx, cudaMemcpyAsync(dst, m.acc, (size_t)n * 16, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    if (!dst_on_device) CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_dft_reset(fdtd_ctx* ctx) {
+    GUARD(ctx);
+    for (auto& mh : ctx->mons)
+        CK(ctx, cudaMemsetAsync(mh.m.acc, 0, sizeof(double2) * mh.m.ncomp * mh.m.nf * mh.m.ncell, ctx->stream));
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_dft_enable(fdtd_ctx* ctx, int32_t enabled) {
+    GUARD(ctx);
+    ctx->dft_enabled = enabled ? 1 : 0;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_enable_energy(fdtd_ctx* ctx, int32_t capacity) {
+    GUARD(ctx);
+    if (capacity < 1) return fail(ctx, FDTD_EINVAL, "capacity must be >= 1");
+    for (auto& d : ctx->doms) {
+        if (d.energy) dfree(ctx, d.energy);
+        fdtd_status st = dmalloc(ctx, (void**)&d.energy, sizeof(double) * capacity);
+        if (st != FDTD_OK) return st;
+        d.energy_cap = capacity;
+    }
+    ctx->energy_on = 1;
+    drop_graphs(ctx);
+    return sync_doms(ctx);
+}
+
+fdtd_status fdtd_energy_read(fdtd_ctx* ctx, int32_t domain, double* host_dst, int32_t n) {
+    GUARD(ctx);
+    if (!valid_dom(ctx, domain) || !host_dst || n < 0) return fail(ctx, FDTD_EINVAL, "bad arguments");
+    const DomainHost& d = ctx->doms[domain];
+    if (!d.energy || n > d.energy_cap) return fail(ctx, FDTD_ESTATE, "energy not enabled or n > capacity");
+    CK(ctx, cudaMemcpyAsync(host_dst, d.energy, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
+    GUARD(ctx);
+    if (n_steps < 0) return fail(ctx, FDTD_EINVAL, "n_steps < 0");
+    if (ctx->step + n_steps >= (1ll << 30)) return fail(ctx, FDTD_EINVAL, "step count overflow");
+    if (!ctx->mons.empty()) {
+        bool changed = false;
+        fdtd_status st = ensure_phase(ctx, ctx->step + n_steps + 2, &changed);
+        if (st != FDTD_OK) return st;
+        if (changed) {
+            st = sync_mons(ctx);
+            if (st != FDTD_OK) return st;
+        }
+    }
+    int left = n_steps;
+    if (ctx->use_graphs && !ctx->prof_on && n_steps >= kGraphSteps) {
+        fdtd_status st = build_graph(ctx);
+        if (st != FDTD_OK) return st;
+        cudaGraphExec_t ge = ctx->graph[ctx->dft_enabled][ctx->energy_on];
+        while (left >= kGraphSteps) {
+            CK(ctx, cudaGraphLaunch(ge, ctx->stream));
+            ctx->launches += ctx->graph_launches[ctx->dft_enabled][ctx->energy_on];
+            left -= kGraphSteps;
+        }
+    }
+    for (int s = 0; s < left; ++s) {
+        if (ctx->dtype == FDTD_F32)
+            step_once<float>(ctx, ctx->stream);
+        else
+            step_once<double>(ctx, ctx->stream);
+    }
+    CKL(ctx);
+    ctx->step += n_steps;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_step_count(fdtd_ctx* ctx, int64_t* n) {
+    GUARD(ctx);
+    if (!n) return FDTD_EINVAL;
+    *n = ctx->step;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_step_count(fdtd_ctx* ctx, int64_t n) {
+    GUARD(ctx);
+    if (n < 0 || n >= (1ll << 30)) return fail(ctx, FDTD_EINVAL, "bad step count");
+    ctx->step = n;
+    return set_device_step(ctx, n);
+}
+
+fdtd_status fdtd_reset(fdtd_ctx* ctx) {
+    GUARD(ctx);
+    for (auto& d : ctx->doms)
+        for (int p = 0; p < part_count(d); ++p) {
+            void* ptr = part_ptr(d, 0, p, ctx->esz);
+            const long long n = part_size(d, p);
+            if (ptr && n) CK(ctx, cudaMemsetAsync(ptr, 0, (size_t)n * ctx->esz, ctx->stream));
+        }
+    ctx->step = 0;
+    return set_device_step(ctx, 0);
+}
+
+fdtd_status fdtd_part_count(fdtd_ctx* ctx, int32_t domain, int32_t* n_parts) {
+    GUARD(ctx);
+    if (!valid_dom(ctx, domain) || !n_parts) return fail(ctx, FDTD_EINVAL, "bad domain");
+    *n_parts = part_count(ctx->doms[domain]);
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_part_size(fdtd_ctx* ctx, int32_t domain, int32_t part, int64_t* n_values) {
+    GUARD(ctx);
+    if (!valid_dom(ctx, domain) || !n_values) return fail(ctx, FDTD_EINVAL, "bad domain");
+    const DomainHost& d = ctx->doms[domain];
+    if (part < 0 || part >= part_count(d)) return fail(ctx, FDTD_EINVAL, "bad part id");
+    *n_values = part_size(d, part);
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_get_part(fdtd_ctx* ctx, int32_t domain, int32_t which, int32_t part, void* dst) {
+    GUARD(ctx);
+    if (!valid_dom(ctx, domain) || (which != 0 && which != 1) || !dst) return fail(ctx, FDTD_EINVAL, "bad arguments");
+    const DomainHost& d = ctx->doms[domain];
+    if (part < 0 || part >= part_count(d)) return fail(ctx, FDTD_EINVAL, "bad part id");
+    if (which == 1) {
+        fdtd_status st = flush_adjoint(ctx);
+        if (st != FDTD_OK) return st;
+    }
+    const long long n = part_size(d, part);
+    if (n == 0) return FDTD_OK;
+    CK(ctx, cudaMemcpyAsync(dst, part_ptr(d, which, part, ctx->esz), (size_t)n * ctx->esz, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_part(fdtd_ctx* ctx, int32_t domain, int32_t which, int32_t part, const void* src) {
+    GUARD(ctx);
+    if (!valid_dom(ctx, domain) || (which != 0 && which != 1) || !src) return fail(ctx, FDTD_EINVAL, "bad arguments");
+    const DomainHost& d = ctx->doms[domain];
+    if (part < 0 || part >= part_count(d)) return fail(ctx, FDTD_EINVAL, "bad part id");
+    if (which == 1) {
+        fdtd_status st = flush_adjoint(ctx);
+        if (st != FDTD_OK) return st;
+    }
+    const long long n = part_size(d, part);
+    if (n == 0) return FDTD_OK;
+    CK(ctx, cudaMemcpyAsync(part_ptr(d, which, part, ctx->esz), src, (size_t)n * ctx->esz, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_ade_box(fdtd_ctx* ctx, int32_t domain, int32_t lo[3], int32_t hi[3]) {
+    GUARD(ctx);
+    if (!valid_dom(ctx, domain) || !lo || !hi) return fail(ctx, FDTD_EINVAL, "bad arguments");
+    for (int q = 0; q < 3; ++q) {
+        lo[q] = ctx->doms[domain].blo[q];
+        hi[q] = ctx->doms[domain].bhi[q];
+    }
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_snapshot_bytes(fdtd_ctx* ctx, int32_t codec, int64_t* bytes) {
+    GUARD(ctx);
+    if (!bytes || (codec != FDTD_CODEC_NATIVE && codec != FDTD_CODEC_BF16)) return fail(ctx, FDTD_EINVAL, "bad codec");
+    *bytes = (int64_t)snapshot_bytes(ctx, codec);
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_state_save(fdtd_ctx* ctx, int32_t slot, int32_t codec) {
+    GUARD(ctx);
+    if (slot < 0 || (codec != FDTD_CODEC_NATIVE && codec != FDTD_CODEC_BF16))
+        return fail(ctx, FDTD_EINVAL, "bad slot or codec");
+    const size_t need = snapshot_bytes(ctx, codec);
+    Slot& s = ctx->slots[slot];
+    if (s.bytes < need) {
+        if (s.buf) {
+            CK(ctx, cudaStreamSynchronize(ctx->stream));
+            cudaFree(s.buf);
+            s.buf = nullptr;
+            s.bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&s.buf, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->slots.erase(slot);
+            return fail(ctx, FDTD_ENOMEM, "snapshot slot allocation failed");
+        }
+        s.bytes = need;
+    }
+    s.codec = codec;
+    s.step = ctx->step;
+    char* p = (char*)s.buf;
+    const Launch l = L(ctx);
+    for (const auto& d : ctx->doms)
+        for (int part = 0; part < part_count(d); ++part) {
+            const long long n = part_size(d, part);
+            if (n == 0) continue;
+            const void* src = part_ptr(d, 0, part, ctx->esz);
+            size_t b;
+            if (codec == FDTD_CODEC_NATIVE) {
+                b = (size_t)n * ctx->esz;
+                CK(ctx, cudaMemcpyAsync(p, src, b, cudaMemcpyDeviceToDevice, ctx->stream));
+            } else {
+                const long long np = part_planes(d, part);
+                b = (size_t)n * 2 + (size_t)np * 4;
+                uint16_t* q = (uint16_t*)p;
+                float* sc = (float*)(p + (size_t)n * 2);
+                if (((uintptr_t)sc) & 3) return fail(ctx, FDTD_EINVAL, "internal alignment");
+                if (ctx->dtype == FDTD_F32)
+                    launch_bf16_encode<float>(l, (const float*)src, np, n / np, q, sc);
+                else
+                    launch_bf16_encode<double>(l, (const double*)src, np, n / np, q, sc);
+                CKL(ctx);
+            }
+            p += (b + 255) & ~(size_t)255;
+        }
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_state_restore(fdtd_ctx* ctx, int32_t slot) {
+    GUARD(ctx);
+    auto it = ctx->slots.find(slot);
+    if (it == ctx->slots.end() || !it->second.buf) return fail(ctx, FDTD_ESTATE, "empty snapshot slot");
+    const Slot& s = it->second;
+    const char* p = (const char*)s.buf;
+    const Launch l = L(ctx);
+    for (const auto& d : ctx->doms)
+        for (int part = 0; part < part_count(d); ++part) {
+            const long long n = part_size(d, part);
+            if (n == 0) continue;
+            void* dst = part_ptr(d, 0, part, ctx->esz);
+            size_t b;
+            if (s.codec == FDTD_CODEC_NATIVE) {
+                b = (size_t)n * ctx->esz;
+                CK(ctx, cudaMemcpyAsync(dst, p, b, cudaMemcpyDeviceToDevice, ctx->stream));
+            } else {
+                const long long np = part_planes(d, part);
+                b = (size_t)n * 2 + (size_t)np * 4;
+                const uint16_t* q = (const uint16_t*)p;
+                const float* sc = (const float*)(p + (size_t)n * 2);
+                if (ctx->dtype == FDTD_F32)
+                    launch_bf16_decode<float>(l, q, sc, np, n / np, (float*)dst);
+                else
+                    launch_bf16_decode<double>(l, q, sc, np, n / np, (double*)dst);
+                CKL(ctx);
+            }
+            p += (b + 255) & ~(size_t)255;
+        }
+    ctx->step = s.step;
+    return set_device_step(ctx, s.step);
+}
+
+fdtd_status fdtd_snapshots_free(fdtd_ctx* ctx) {
+    GUARD(ctx);
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto& s : ctx->slots) cudaFree(s.second.buf);
+    ctx->slots.clear();
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_design(fdtd_ctx* ctx, int32_t domain, const int32_t lo[3], const int32_t hi[3], double* grad) {
+    GUARD(ctx);
+    if (!valid_dom(ctx, domain)) return fail(ctx, FDTD_EINVAL, "bad domain");
+    DomainHost& d = ctx->doms[domain];
+    if (!grad) {
+        d.design = 0;
+        d.grad = nullptr;
+        return sync_doms(ctx);
+    }
+    if (!lo || !hi || !valid_box(d, lo, hi)) return fail(ctx, FDTD_EINVAL, "design box outside the domain");
+    for (int q = 0; q < 3; ++q)
+        if (lo[q] < d.dlo[q] || hi[q] > d.n[q] - d.dhi[q])
+            return fail(ctx, FDTD_EINVAL, "design box must lie outside the CPML slabs");
+    d.design = 1;
+    d.grad = grad;
+    for (int q = 0; q < 3; ++q) {
+        d.glo[q] = lo[q];
+        d.ghi[q] = hi[q];
+    }
+    return sync_doms(ctx);
+}
+
+fdtd_status fdtd_set_adjoint_source(fdtd_ctx* ctx, int32_t monitor_id, const void* cot) {
+    GUARD(ctx);
+    if (monitor_id < 0 || monitor_id >= (int)ctx->mons.size()) return fail(ctx, FDTD_EINVAL, "bad monitor id");
+    ctx->mons[monitor_id].m.cot = (const double2*)cot;
+    return sync_mons(ctx);
+}
+
+fdtd_status fdtd_adjoint_begin(fdtd_ctx* ctx) {
+    GUARD(ctx);
+    for (auto& d : ctx->doms)
+        for (int p = 0; p < part_count(d); ++p) {
+            void* ptr = part_ptr(d, 1, p, ctx->esz);
+            const long long n = part_size(d, p);
+            if (ptr && n) CK(ctx, cudaMemsetAsync(ptr, 0, (size_t)n * ctx->esz, ctx->stream));
+        }
+    ctx->adj_step = ctx->step;
+    ctx->adj_pending = 0;
+    if (ctx->step >= 1 && ctx->nentries[1] > 0) {
+        bool changed = false;
+        fdtd_status st = ensure_phase(ctx, ctx->step + 2, &changed);
+        if (st != FDTD_OK) return st;
+        if (changed) {
+            st = sync_mons(ctx);
+            if (st != FDTD_OK) return st;
+        }
+        if (ctx->dtype == FDTD_F32)
+            launch_inject<float>(L(ctx), (const Dom<float>*)ctx->d_doms, ctx->d_mons, ctx->d_entries[1],
+                                 ctx->nentries[1], ctx->nthreads[1], ctx->d_entry_begin[1], (int)ctx->step - 1, 1);
+        else
+            launch_inject<double>(L(ctx), (const Dom<double>*)ctx->d_doms, ctx->d_mons, ctx->d_entries[1],
+                                  ctx->nentries[1], ctx->nthreads[1], ctx->d_entry_begin[1], (int)ctx->step - 1, 1);
+        CKL(ctx);
+    }
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_step_adjoint(fdtd_ctx* ctx, int32_t n_steps) {
+    GUARD(ctx);
+    if (n_steps < 0 || n_steps > ctx->adj_step) return fail(ctx, FDTD_EINVAL, "n_steps out of range");
+    bool design = false;
+    for (auto& d : ctx->doms) design = design || d.design;
+    if (design && n_steps > 0 && (n_steps != 1 || ctx->step != ctx->adj_step - 1))
+        return fail(ctx, FDTD_ESTATE,
+                    "with a design box each adjoint step m needs the forward state u^m (step count " +
+                        std::to_string(ctx->step) + ", adjoint index " + std::to_string(ctx->adj_step) + ")");
+    if (!ctx->mons.empty()) {
+        bool changed = false;
+        fdtd_status st = ensure_phase(ctx, ctx->adj_step + 2, &changed);
+        if (st != FDTD_OK) return st;
+        if (changed) {
+            st = sync_mons(ctx);
+            if (st != FDTD_OK) return st;
+        }
+    }
+    for (int s = 0; s < n_steps; ++s) {
+        const int m = (int)ctx->adj_step - 1;
+        if (ctx->dtype == FDTD_F32)
+            adj_once<float>(ctx, m);
+        else
+            adj_once<double>(ctx, m);
+        ctx->adj_pending = 1;
+        ctx->adj_step = m;
+    }
+    CKL(ctx);
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_adjoint_step_count(fdtd_ctx* ctx, int64_t* a) {
+    GUARD(ctx);
+    if (!a) return FDTD_EINVAL;
+    *a = ctx->adj_step;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_adjoint_step_count(fdtd_ctx* ctx, int64_t a) {
+    GUARD(ctx);
+    if (a < 0 || a >= (1ll << 30)) return fail(ctx, FDTD_EINVAL, "bad adjoint index");
+    fdtd_status st = flush_adjoint(ctx);
+    if (st != FDTD_OK) return st;
+    ctx->adj_step = a;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_check_finite(fdtd_ctx* ctx) {
+    GUARD(ctx);
+    CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(unsigned long long), ctx->stream));
+    for (auto& d : ctx->doms)
+        for (int p = 0; p < part_count(d); ++p) {
+            const void* ptr = part_ptr(d, 0, p, ctx->esz);
+            const long long n = part_size(d, p);
+            if (!ptr || !n) continue;
+            if (ctx->dtype == FDTD_F32)
+                launch_nonfinite<float>(L(ctx), (const float*)ptr, n, ctx->d_flag);
+            else
+                launch_nonfinite<double>(L(ctx), (const double*)ptr, n, ctx->d_flag);
+        }
+    CKL(ctx);
+    unsigned long long bad = 0;
+    CK(ctx, cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (bad) return fail(ctx, FDTD_ENONFINITE, "non-finite values in the forward state");
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_synchronize(fdtd_ctx* ctx, int32_t timeout_ms) {
+    GUARD(ctx);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(ctx->stream);
+        if (e == cudaSuccess) return FDTD_OK;
+        if (e != cudaErrorNotReady) return fail(ctx, FDTD_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+        if (ms.count() >= timeout_ms) return fail(ctx, FDTD_ETIMEOUT, "stream not finished within the timeout");
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+}
+
+fdtd_status fdtd_launch_count(fdtd_ctx* ctx, int64_t* n) {
+    if (!ctx || !n) return FDTD_EINVAL;
+    *n = ctx->launches;
+    return FDTD_OK;
+}
+
+static void prof_release(fdtd_ctx* ctx) {
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    ctx->prof_ev.clear();
+    ctx->prof_kind.clear();
+    ctx->prof_on = 0;
+    ctx->prof_used = 0;
+}
+
+fdtd_status fdtd_profile_begin(fdtd_ctx* ctx, int32_t max_launches) {
+    GUARD(ctx);
+    if (max_launches < 1) return fail(ctx, FDTD_EINVAL, "max_launches must be >= 1");
+    prof_release(ctx);
+    ctx->prof_ev.resize(2 * (size_t)max_launches);
+    ctx->prof_kind.assign(max_launches, 0);
+    for (auto& e : ctx->prof_ev) {
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) {
+            e = nullptr;
+            prof_release(ctx);
+            return fail(ctx, FDTD_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(r));
+        }
+    }
+    ctx->prof_on = 1;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_profile_end(fdtd_ctx* ctx, double* ms, int64_t* launches) {
+    GUARD(ctx);
+    if (!ms || !launches) return fail(ctx, FDTD_EINVAL, "NULL output");
+    for (int k = 0; k < FDTD_KERNEL_CLASSES; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i + 1 < ctx->prof_used; i += 2) {
+        float t = 0.f;
+        CK(ctx, cudaEventElapsedTime(&t, ctx->prof_ev[i], ctx->prof_ev[i + 1]));
+        const int k = ctx->prof_kind[i / 2];
+        ms[k] += t;
+        launches[k] += 1;
+    }
+    prof_release(ctx);
+    return FDTD_OK;
+}
+
+}  // extern "C"

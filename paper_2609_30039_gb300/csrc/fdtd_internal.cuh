@@ -1,0 +1,163 @@
+// Internal device-side types of the gbfdtd library (not part of the ABI).
+//
+// Layout in HBM (per domain, dtype T = float | double):
+//   F[0..5]   forward fields Ex..Hz, full grid (nz, ny, nx), x fastest
+//   A[0..5]   adjoint fields (lagged form during a sweep, see kernels_adj.cu)
+//   psiE[a][s], psiH[a][s]  CPML memories, only over the two slabs of the derivative's axis
+//   ade       pole states [3][npole][2 (P,Q)][ADE box cells]   (bounding box of the pole mask)
+//   cE[q], cH[q]  CPML coefficients along axis q: [b(N) | c(N) | 1/kappa(N)], E at integer
+//                 nodes, H at half nodes (Sec. 2.2)
+// All descriptors live in device memory and are read through the read-only path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fdtd.h"
+
+namespace gbfdtd {
+
+constexpr int kMaxPole = 16;
+constexpr int kMaxMonPerDom = 8;
+constexpr int kTileX = 32;
+constexpr int kTileY = 8;
+
+template <typename T>
+struct Dom {
+    int n[3];                  // nx, ny, nz
+    long long ncell;
+    T* F[6];
+    T* A[6];
+    const T* ie[3];            // 1/eps per E component (borrowed)
+    const uint8_t* mask;       // pole mask (borrowed) or nullptr
+    int dlo[3], dhi[3], ns[3]; // CPML depth per axis (low, high), ns = dlo + dhi
+    T* psiE[3][2];
+    T* psiH[3][2];
+    T* apsiE[3][2];
+    T* apsiH[3][2];
+    const T* cE[3];
+    const T* cH[3];
+    int blo[3], bhi[3];        // pole-state box
+    long long bcell;
+    T* ade;
+    T* aade;
+    int npole;
+    T M00[kMaxPole], M01[kMaxPole], M10[kMaxPole], M11[kMaxPole], g0[kMaxPole], g1[kMaxPole];
+    T G;                       // sum_p g0[p]
+    int design;                // 1 if a design box is set
+    int glo[3], ghi[3];
+    double* grad;              // [3][design cells]
+    int nmon;                  // monitors of this domain (adjoint injection)
+    int mon[kMaxMonPerDom];
+    double* energy;            // per-step energy or nullptr
+    int energy_cap;
+};
+
+// A running DFT monitor (Sec. 2.4).  acc / cot: [ncomp][nf][ncell] double2.
+// phase: [cap][2 (E: t=n+1, H: t=n+3/2)][nf] double2 = exp(i w t).
+struct Mon {
+    int dom;
+    int lo[3], hi[3];
+    int bx, by;
+    long long ncell;
+    int nf;
+    int ncomp;
+    int comps[6];
+    unsigned mask;
+    double2* acc;
+    const double2* cot;
+    const double2* phase;
+    int cap;
+};
+
+struct Src {
+    int dom, comp;
+    int lo[3], hi[3];
+    int bx, by;
+    long long ncell, begin;    // begin: offset of this source in the flattened cell list
+    const double* wave;
+    int n;
+};
+
+// One tile of work: kTileX x kTileY columns of a domain marched over [z0, z1).
+struct Tile {
+    int dom;
+    int x0, y0;
+    int z0, z1;
+};
+
+__host__ __device__ inline long long cidx(const int* n, int i, int j, int k) {
+    return ((long long)k * n[1] + j) * n[0] + i;
+}
+
+// Slab index of coordinate x along an axis with CPML depths (lo, hi) over N nodes, or -1.
+__host__ __device__ inline int slab_of(int x, int lo, int hi, int N) {
+    if (x < lo) return x;
+    if (x >= N - hi) return lo + (x - (N - hi));
+    return -1;
+}
+
+// Offset inside the slab array of axis q for cell (i,j,k) with slab index s.
+__host__ __device__ inline long long slab_off(const int* n, const int* ns, int q, int i, int j, int k, int s) {
+    if (q == 0) return ((long long)k * n[1] + j) * ns[0] + s;
+    if (q == 1) return ((long long)k * ns[1] + s) * n[0] + i;
+    return ((long long)s * n[1] + j) * n[0] + i;
+}
+
+template <typename T>
+__device__ inline bool in_ade_box(const Dom<T>& d, int i, int j, int k) {
+    return i >= d.blo[0] && i < d.bhi[0] && j >= d.blo[1] && j < d.bhi[1] && k >= d.blo[2] && k < d.bhi[2];
+}
+
+template <typename T>
+__device__ inline long long ade_off(const Dom<T>& d, int i, int j, int k) {
+    return ((long long)(k - d.blo[2]) * (d.bhi[1] - d.blo[1]) + (j - d.blo[1])) * (d.bhi[0] - d.blo[0]) + (i - d.blo[0]);
+}
+
+// ---- launch helpers (host) -------------------------------------------------------------
+struct Launch {
+    cudaStream_t stream;
+    long long* counter;   // launches enqueued
+};
+
+// Forward kernels (kernels_fwd.cu)
+template <typename T>
+void launch_e_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, int general, int aniso);
+template <typename T>
+void launch_h_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const int* d_step,
+                     int general, int energy);
+template <typename T>
+void launch_sources(const Launch& L, const Dom<T>* doms, const Src* srcs, int nsrc, long long ncells,
+                    const int* d_step);
+template <typename T>
+void launch_dft(const Launch& L, const Dom<T>* doms, const Mon* mons, const int* entries, int nentries,
+                long long nthreads, const long long* entry_begin, const int* d_step, int kind);
+void launch_advance(const Launch& L, int* d_step, int delta);
+
+// Adjoint kernels (kernels_adj.cu)
+template <typename T>
+void launch_adj_e(const Launch& L, const Dom<T>* doms, const Mon* mons, const Tile* tiles, int ntiles, T S, int m,
+                  int pending, int general, int aniso);
+template <typename T>
+void launch_adj_h(const Launch& L, const Dom<T>* doms, const Mon* mons, const Tile* tiles, int ntiles, T S, int m,
+                  int general);
+template <typename T>
+void launch_adj_flush(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S);
+template <typename T>
+void launch_inject(const Launch& L, const Dom<T>* doms, const Mon* mons, const int* entries, int nentries,
+                   long long nthreads, const long long* entry_begin, int step, int kind);
+
+// Auxiliary kernels (kernels_aux.cu)
+template <typename T>
+void launch_admission(const Launch& L, const Dom<T>* d_dom, const Dom<T>& h_dom, unsigned long long* d_bad);
+void launch_mask_box(const Launch& L, const uint8_t* mask, int nx, int ny, int nz, int* d_box);
+template <typename T>
+void launch_nonfinite(const Launch& L, const T* p, long long n, unsigned long long* d_bad);
+template <typename T>
+void launch_bf16_encode(const Launch& L, const T* src, long long nplanes, long long plane, uint16_t* dst,
+                        float* scales);
+template <typename T>
+void launch_bf16_decode(const Launch& L, const uint16_t* src, const float* scales, long long nplanes,
+                        long long plane, T* dst);
+
+}  // namespace gbfdtd

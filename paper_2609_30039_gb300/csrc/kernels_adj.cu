@@ -1,0 +1,460 @@
+// Transposed (discrete-adjoint) half-steps, arxiv 2609.30039 Sec. 3.1, Eq. (adjoint).
+//
+// Every forward update has a transpose kernel of the same locality:
+//   * k_adj_e  (one thread per E column, like the forward E update) applies the transpose of
+//     the forward H update (Ebar += gathered backward differences of the H cotangent, the
+//     "opposite-direction differences" of Sec. 3.1), injects dJ/dE of the monitors, and
+//     transposes the E update's own-cell part (poles, eps^-1, material cotangent);
+//   * k_adj_h  (one thread per H column) applies the transpose of the forward E update
+//     (Hbar += gathered forward differences) and the H-side CPML recursion.
+// CPML transpose (Sec. 3.1): psibar_mem = psibar + ybar, Dbar = ybar/kappa + c psibar_mem,
+// psibar_old = b psibar_mem.  Pole transpose: the 2x2 trapezoidal system applied to the
+// cotangents with M^T.
+//
+// Gather form needs the cotangent of every neighbour's derivative D while its owner is still
+// updating psibar.  So that no kernel reads a value another thread of the same launch writes,
+// the E-side own-cell part of transposed step m is deferred to the next k_adj_e (m-1):
+// after k_adj_e(m) the E array holds F = S/(eps_inf + G) * Etilde_bar (the cotangent of the
+// curl, which k_adj_h needs at neighbours), and the pole/psi cotangents still hold their step
+// m+1 values.  k_adj_e(m-1) (or k_adj_flush) first completes step m for its own cell:
+//   Ebar^m   = (eps_inf - G)/S * F + sum_p g_p . xbar_p
+//   xbar_p^m = M_p^T xbar_p + ((1 - M00_p) / S, -M01_p / S) F
+//   psibar_E^m = b (psibar_E + (+F | -F))
+// The H side needs no deferral: psibar_H of step m is finished by k_adj_h(m) after
+// k_adj_e(m) has read it.
+#include "fdtd_internal.cuh"
+
+namespace gbfdtd {
+
+// Cotangent of the derivative D read by H_h's s-th derivative at cell (i,j,k):
+// ybar = -S Hbar (s = 0) | +S Hbar (s = 1); Dbar = ybar/kappa + c (psibar + ybar) in the slab.
+template <typename T>
+__device__ __forceinline__ T dbar_h(const Dom<T>& d, int h, int s, int i, int j, int k, T S) {
+    const int c[3] = {i, j, k};
+    const int ax = (h + 1 + s) % 3;
+    const long long id = cidx(d.n, i, j, k);
+    const T yb = (s == 0 ? -S : S) * d.A[3 + h][id];
+    if (d.ns[ax] == 0) return yb;
+    const int x = c[ax];
+    const int sl = slab_of(x, d.dlo[ax], d.dhi[ax], d.n[ax]);
+    if (sl < 0) return yb;
+    const int N = d.n[ax];
+    const T pm = d.apsiH[h][s][slab_off(d.n, d.ns, ax, i, j, k, sl)] + yb;
+    return d.cH[ax][2 * N + x] * yb + d.cH[ax][N + x] * pm;
+}
+
+// Cotangent of the derivative D read by E_e's s-th derivative at cell (i,j,k), from the
+// lagged E state: ybar = +F (s = 0) | -F (s = 1).
+template <typename T>
+__device__ __forceinline__ T dbar_e(const Dom<T>& d, int e, int s, int i, int j, int k) {
+    const int c[3] = {i, j, k};
+    // a PEC node is never updated, so its CPML memory never reaches a curl: no cotangent flows
+    if (c[(e + 1) % 3] == 0 || c[(e + 2) % 3] == 0) return T(0);
+    const int ax = (e + 1 + s) % 3;
+    const long long id = cidx(d.n, i, j, k);
+    const T F = d.A[e][id];
+    const T yb = s == 0 ? F : -F;
+    if (d.ns[ax] == 0) return yb;
+    const int x = c[ax];
+    const int sl = slab_of(x, d.dlo[ax], d.dhi[ax], d.n[ax]);
+    if (sl < 0) return yb;
+    const int N = d.n[ax];
+    const T pm = d.apsiE[e][s][slab_off(d.n, d.ns, ax, i, j, k, sl)] + yb;
+    return d.cE[ax][2 * N + x] * yb + d.cE[ax][N + x] * pm;
+}
+
+// Completes the deferred own-cell transpose of an E update for component a; returns Ebar.
+template <typename T>
+__device__ __forceinline__ T e_deferred(const Dom<T>& d, int a, int i, int j, int k, long long id, bool disp,
+                                        T F, T S) {
+    const int c[3] = {i, j, k};
+    const T ie = d.ie[a][id];
+    T eb;
+    if (disp) {
+        eb = (T(1) / ie - d.G) / S * F;
+        const long long bo = ade_off(d, i, j, k);
+        for (int p = 0; p < d.npole; ++p) {
+            T* pp = d.aade + ((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo;
+            T* pq = d.aade + ((long long)(a * d.npole + p) * 2 + 1) * d.bcell + bo;
+            const T xp = *pp, xq = *pq;
+            eb += d.g0[p] * xp + d.g1[p] * xq;
+            *pp = d.M00[p] * xp + d.M10[p] * xq + (T(1) - d.M00[p]) / S * F;
+            *pq = d.M01[p] * xp + d.M11[p] * xq - d.M01[p] / S * F;
+        }
+    } else {
+        eb = F / (S * ie);
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int ax = (a + 1 + s) % 3;
+        if (d.ns[ax] == 0) continue;
+        const int x = c[ax];
+        const int sl = slab_of(x, d.dlo[ax], d.dhi[ax], d.n[ax]);
+        if (sl < 0) continue;
+        T* p = d.apsiE[a][s] + slab_off(d.n, d.ns, ax, i, j, k, sl);
+        *p = d.cE[ax][x] * (*p + (s == 0 ? F : -F));
+    }
+    return eb;
+}
+
+template <typename T>
+__device__ __forceinline__ double inject_at(const Dom<T>& d, const Mon* __restrict__ mons, int comp, int i, int j,
+                                            int k, long long pidx) {
+    // dJ/df(t) = Re(conj(cot) exp(i w t)), pidx = (step * 2 + kind) of the phase table
+    double acc = 0.0;
+    for (int mm = 0; mm < d.nmon; ++mm) {
+        const Mon& m = mons[d.mon[mm]];
+        if (!m.cot || !((m.mask >> comp) & 1u)) continue;
+        if (i < m.lo[0] || i >= m.hi[0] || j < m.lo[1] || j >= m.hi[1] || k < m.lo[2] || k >= m.hi[2]) continue;
+        int ci = 0;
+        for (int c2 = 0; c2 < comp; ++c2) ci += (m.mask >> c2) & 1u;
+        const long long cell = ((long long)(k - m.lo[2]) * m.by + (j - m.lo[1])) * m.bx + (i - m.lo[0]);
+        const double2* ph = m.phase + pidx * m.nf;
+        const double2* ct = m.cot + (long long)ci * m.nf * m.ncell + cell;
+        for (int f = 0; f < m.nf; ++f) {
+            const double2 c = ct[(long long)f * m.ncell];
+            const double2 p = ph[f];
+            acc += c.x * p.x + c.y * p.y;
+        }
+    }
+    return acc;
+}
+
+// k_adj_e: transposed step m, E side.  Forward state must be u^m when a design box is set.
+template <typename T>
+__global__ void __launch_bounds__(kTileX* kTileY) k_adj_e(const Dom<T>* __restrict__ doms,
+                                                          const Mon* __restrict__ mons,
+                                                          const Tile* __restrict__ tiles, T S, int m, int pending) {
+    const Tile t = tiles[blockIdx.x];
+    const Dom<T>& d = doms[t.dom];
+    const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
+    if (i >= d.n[0] || j >= d.n[1]) return;
+    const long long st[3] = {1, (long long)d.n[0], (long long)d.n[0] * d.n[1]};
+    for (int k = t.z0; k < t.z1; ++k) {
+        const int c[3] = {i, j, k};
+        const long long id = cidx(d.n, i, j, k);
+        const bool dcell = d.npole > 0 && d.mask[id] && in_ade_box(d, i, j, k);
+        const bool gcell = d.design && i >= d.glo[0] && i < d.ghi[0] && j >= d.glo[1] && j < d.ghi[1] &&
+                           k >= d.glo[2] && k < d.ghi[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int b = (a + 1) % 3, q = (a + 2) % 3;
+            if (c[b] == 0 || c[q] == 0) {  // PEC node: not a state variable
+                d.A[a][id] = T(0);
+                continue;
+            }
+            const T Fprev = d.A[a][id];
+            T eb = pending ? e_deferred(d, a, i, j, k, id, dcell, Fprev, S) : Fprev;
+            // transpose of the H update of step m: E_a is read by H_b (1st derivative, along q)
+            // and by H_q (2nd derivative, along b), each at r and r + e
+            int cm[3] = {i, j, k};
+            cm[q] -= 1;
+            eb += dbar_h(d, b, 0, cm[0], cm[1], cm[2], S) - dbar_h(d, b, 0, i, j, k, S);
+            cm[q] += 1;
+            cm[b] -= 1;
+            eb += dbar_h(d, q, 1, cm[0], cm[1], cm[2], S) - dbar_h(d, q, 1, i, j, k, S);
+            // dJ/dE^{m+1}
+            if (d.nmon) eb += (T)inject_at(d, mons, a, i, j, k, (long long)m * 2 + 0);
+            // transpose of the E update of step m (own cell)
+            const T ie = d.ie[a][id];
+            T et = eb;
+            T gdisp = T(0);
+            if (dcell) {
+                const long long bo = ade_off(d, i, j, k);
+                for (int p = 0; p < d.npole; ++p) {
+                    const T xp = d.aade[((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo];
+                    const T xq = d.aade[((long long)(a * d.npole + p) * 2 + 1) * d.bcell + bo];
+                    et += d.g0[p] * xp + d.g1[p] * xq;
+                }
+                gdisp = d.G;
+            }
+            if (gcell) {
+                // d E^{m+1} / d(eps^-1) = Delta (eps_inf / (eps_inf + G))^2,
+                // Delta = S curl(H^{m+1/2}) + sum_p (P - (M x)_P - 2 g_p E^m)  (forward state u^m)
+                const T* Hq = d.F[3 + q];
+                const T* Hb = d.F[3 + b];
+                const T curl = (Hq[id] - Hq[id - st[b]]) - (Hb[id] - Hb[id - st[q]]);
+                double delta = (double)(S * curl);
+                if (dcell) {
+                    const long long bo = ade_off(d, i, j, k);
+                    const T e0 = d.F[a][id];
+                    for (int p = 0; p < d.npole; ++p) {
+                        const T P = d.ade[((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo];
+                        const T Q = d.ade[((long long)(a * d.npole + p) * 2 + 1) * d.bcell + bo];
+                        delta += (double)(P - (d.M00[p] * P + d.M01[p] * Q) - T(2) * d.g0[p] * e0);
+                    }
+                }
+                const double r = 1.0 / (1.0 + (double)ie * (double)gdisp);
+                const long long gi = ((long long)(k - d.glo[2]) * (d.ghi[1] - d.glo[1]) + (j - d.glo[1])) *
+                                         (d.ghi[0] - d.glo[0]) + (i - d.glo[0]);
+                const long long gn = (long long)(d.ghi[0] - d.glo[0]) * (d.ghi[1] - d.glo[1]) * (d.ghi[2] - d.glo[2]);
+                d.grad[a * gn + gi] += (double)et * delta * r * r;
+            }
+            d.A[a][id] = S * ie / (T(1) + ie * gdisp) * et;
+        }
+    }
+}
+
+// k_adj_h: transposed step m, H side.  Injects dJ/dH^{m+1/2} (m >= 1) at the end.
+template <typename T>
+__global__ void __launch_bounds__(kTileX* kTileY) k_adj_h(const Dom<T>* __restrict__ doms,
+                                                          const Mon* __restrict__ mons,
+                                                          const Tile* __restrict__ tiles, T S, int m) {
+    const Tile t = tiles[blockIdx.x];
+    const Dom<T>& d = doms[t.dom];
+    const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
+    if (i >= d.n[0] || j >= d.n[1]) return;
+    for (int k = t.z0; k < t.z1; ++k) {
+        const int c[3] = {i, j, k};
+        const long long id = cidx(d.n, i, j, k);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int b = (a + 1) % 3, q = (a + 2) % 3;
+            const T hb = d.A[3 + a][id];
+            // finish the H-side CPML transpose of step m (k_adj_e(m) has read psibar_H)
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int ax = (a + 1 + s) % 3;
+                if (d.ns[ax] == 0) continue;
+                const int x = c[ax];
+                const int sl = slab_of(x, d.dlo[ax], d.dhi[ax], d.n[ax]);
+                if (sl < 0) continue;
+                T* p = d.apsiH[a][s] + slab_off(d.n, d.ns, ax, i, j, k, sl);
+                *p = d.cH[ax][x] * (*p + (s == 0 ? -S : S) * hb);
+            }
+            // transpose of the E update of step m: H_a is read by E_b (1st derivative, along q)
+            // and by E_q (2nd derivative, along b), each at r and r - e
+            T h = hb;
+            h += dbar_e(d, b, 0, i, j, k);
+            if (c[q] + 1 < d.n[q]) {
+                int cp[3] = {i, j, k};
+                cp[q] += 1;
+                h -= dbar_e(d, b, 0, cp[0], cp[1], cp[2]);
+            }
+            h += dbar_e(d, q, 1, i, j, k);
+            if (c[b] + 1 < d.n[b]) {
+                int cp[3] = {i, j, k};
+                cp[b] += 1;
+                h -= dbar_e(d, q, 1, cp[0], cp[1], cp[2]);
+            }
+            if (d.nmon && m >= 1) h += (T)inject_at(d, mons, 3 + a, i, j, k, (long long)(m - 1) * 2 + 1);
+            d.A[3 + a][id] = h;
+        }
+    }
+}
+
+// Interior fast paths of the two transposed kernels: tiles that touch no CPML slab, PEC plane,
+// domain edge or pole cell.  Without CPML the derivative cotangents reduce to -S Hbar / +S Hbar
+// and +F / -F, so k_adj_e_int is the forward E update with Ebar -= S C^- Hbar and
+// k_adj_h_int is Hbar += C^+ F.  Loads of a plane are issued before its stores; the z-1
+// (z+1) neighbours are carried in registers.  The design-box gradient and the monitor
+// injection keep their per-cell checks.
+template <typename T, bool kAniso>
+__global__ void __launch_bounds__(kTileX* kTileY) k_adj_e_int(const Dom<T>* __restrict__ doms,
+                                                              const Mon* __restrict__ mons,
+                                                              const Tile* __restrict__ tiles, T S, int m,
+                                                              int pending) {
+    const Tile t = tiles[blockIdx.x];
+    const Dom<T>& d = doms[t.dom];
+    const int nx = d.n[0], ny = d.n[1];
+    const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const long long nxy = (long long)nx * ny;
+    T* Fx = d.A[0];
+    T* Fy = d.A[1];
+    T* Fz = d.A[2];
+    const T* Bx = d.A[3];
+    const T* By = d.A[4];
+    const T* Bz = d.A[5];
+    const T* ie0 = d.ie[0];
+    const T* ie1 = d.ie[1];
+    const T* ie2 = d.ie[2];
+    const bool gcol = d.design && i >= d.glo[0] && i < d.ghi[0] && j >= d.glo[1] && j < d.ghi[1];
+    long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
+    T bxz = Bx[id - nxy], byz = By[id - nxy];
+    for (int k = t.z0; k < t.z1; ++k, id += nxy) {
+        const T bx = Bx[id], by = By[id], bz = Bz[id];
+        const T bz_ym = Bz[id - nx], bx_ym = Bx[id - nx];
+        const T bz_xm = Bz[id - 1], by_xm = By[id - 1];
+        const T fx = Fx[id], fy = Fy[id], fz = Fz[id];
+        const T iex = ie0[id];
+        const T iey = kAniso ? ie1[id] : iex;
+        const T iez = kAniso ? ie2[id] : iex;
+        // deferred own-cell transpose of step m+1 (non-dispersive: Ebar = F / (S eps^-1))
+        T ex = pending ? fx / (S * iex) : fx;
+        T ey = pending ? fy / (S * iey) : fy;
+        T ez = pending ? fz / (S * iez) : fz;
+        // transpose of the H update: Ebar -= S C^- Hbar
+        ex += S * ((by - byz) - (bz - bz_ym));
+        ey += S * ((bz - bz_xm) - (bx - bxz));
+        ez += S * ((bx - bx_ym) - (by - by_xm));
+        bxz = bx;
+        byz = by;
+        if (d.nmon) {
+            ex += (T)inject_at(d, mons, 0, i, j, k, (long long)m * 2 + 0);
+            ey += (T)inject_at(d, mons, 1, i, j, k, (long long)m * 2 + 0);
+            ez += (T)inject_at(d, mons, 2, i, j, k, (long long)m * 2 + 0);
+        }
+        if (gcol && k >= d.glo[2] && k < d.ghi[2]) {
+            // d E^{m+1} / d(eps^-1) = S curl(H^{m+1/2}) of the forward state u^m
+            const T* Hx = d.F[3];
+            const T* Hy = d.F[4];
+            const T* Hz = d.F[5];
+            const T cx = (Hz[id] - Hz[id - nx]) - (Hy[id] - Hy[id - nxy]);
+            const T cy = (Hx[id] - Hx[id - nxy]) - (Hz[id] - Hz[id - 1]);
+            const T cz = (Hy[id] - Hy[id - 1]) - (Hx[id] - Hx[id - nx]);
+            const long long gi = ((long long)(k - d.glo[2]) * (d.ghi[1] - d.glo[1]) + (j - d.glo[1])) *
+                                     (d.ghi[0] - d.glo[0]) + (i - d.glo[0]);
+            const long long gn = (long long)(d.ghi[0] - d.glo[0]) * (d.ghi[1] - d.glo[1]) * (d.ghi[2] - d.glo[2]);
+            d.grad[gi] += (double)ex * (double)(S * cx);
+            d.grad[gn + gi] += (double)ey * (double)(S * cy);
+            d.grad[2 * gn + gi] += (double)ez * (double)(S * cz);
+        }
+        Fx[id] = S * iex * ex;
+        Fy[id] = S * iey * ey;
+        Fz[id] = S * iez * ez;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileX* kTileY) k_adj_h_int(const Dom<T>* __restrict__ doms,
+                                                              const Mon* __restrict__ mons,
+                                                              const Tile* __restrict__ tiles, T S, int m) {
+    const Tile t = tiles[blockIdx.x];
+    const Dom<T>& d = doms[t.dom];
+    const int nx = d.n[0], ny = d.n[1];
+    const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const long long nxy = (long long)nx * ny;
+    const T* Fx = d.A[0];
+    const T* Fy = d.A[1];
+    const T* Fz = d.A[2];
+    T* Bx = d.A[3];
+    T* By = d.A[4];
+    T* Bz = d.A[5];
+    long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
+    T fxk = Fx[id], fyk = Fy[id];
+    for (int k = t.z0; k < t.z1; ++k, id += nxy) {
+        const T fxn = Fx[id + nxy], fyn = Fy[id + nxy];
+        const T fz = Fz[id];
+        const T fz_yp = Fz[id + nx], fz_xp = Fz[id + 1];
+        const T fy_xp = Fy[id + 1], fx_yp = Fx[id + nx];
+        T bx = Bx[id], by = By[id], bz = Bz[id];
+        // transpose of the E update: Hbar += C^+ F
+        bx += (fz_yp - fz) - (fyn - fyk);
+        by += (fxn - fxk) - (fz_xp - fz);
+        bz += (fy_xp - fyk) - (fx_yp - fxk);
+        if (d.nmon && m >= 1) {
+            bx += (T)inject_at(d, mons, 3, i, j, k, (long long)(m - 1) * 2 + 1);
+            by += (T)inject_at(d, mons, 4, i, j, k, (long long)(m - 1) * 2 + 1);
+            bz += (T)inject_at(d, mons, 5, i, j, k, (long long)(m - 1) * 2 + 1);
+        }
+        Bx[id] = bx;
+        By[id] = by;
+        Bz[id] = bz;
+        fxk = fxn;
+        fyk = fyn;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileX* kTileY) k_adj_flush(const Dom<T>* __restrict__ doms,
+                                                              const Tile* __restrict__ tiles, T S) {
+    const Tile t = tiles[blockIdx.x];
+    const Dom<T>& d = doms[t.dom];
+    const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
+    if (i >= d.n[0] || j >= d.n[1]) return;
+    for (int k = t.z0; k < t.z1; ++k) {
+        const int c[3] = {i, j, k};
+        const long long id = cidx(d.n, i, j, k);
+        const bool dcell = d.npole > 0 && d.mask[id] && in_ade_box(d, i, j, k);
+        for (int a = 0; a < 3; ++a) {
+            const int b = (a + 1) % 3, q = (a + 2) % 3;
+            if (c[b] == 0 || c[q] == 0) continue;
+            d.A[a][id] = e_deferred(d, a, i, j, k, id, dcell, d.A[a][id], S);
+        }
+    }
+}
+
+// Standalone injection of dJ/df(t) into the adjoint fields (used to start a sweep).
+template <typename T>
+__global__ void k_inject(const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons,
+                         const int* __restrict__ entries, int nentries, long long nthreads,
+                         const long long* __restrict__ entry_begin, int step, int kind) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= nthreads) return;
+    int e = 0;
+    while (e + 1 < nentries && entry_begin[e + 1] <= t) ++e;
+    const int mi = entries[2 * e], ci = entries[2 * e + 1];
+    const Mon& m = mons[mi];
+    if (!m.cot) return;
+    const long long cell = t - entry_begin[e];
+    const int i = m.lo[0] + (int)(cell % m.bx);
+    const int j = m.lo[1] + (int)((cell / m.bx) % m.by);
+    const int k = m.lo[2] + (int)(cell / ((long long)m.bx * m.by));
+    const Dom<T>& d = doms[m.dom];
+    const double2* ph = m.phase + ((long long)step * 2 + kind) * m.nf;
+    const double2* ct = m.cot + (long long)ci * m.nf * m.ncell + cell;
+    double acc = 0.0;
+    for (int f = 0; f < m.nf; ++f) {
+        const double2 c = ct[(long long)f * m.ncell];
+        acc += c.x * ph[f].x + c.y * ph[f].y;
+    }
+    d.A[m.comps[ci]][cidx(d.n, i, j, k)] += (T)acc;
+}
+
+template <typename T>
+void launch_adj_e(const Launch& L, const Dom<T>* doms, const Mon* mons, const Tile* tiles, int ntiles, T S, int m,
+                  int pending, int general, int aniso) {
+    if (ntiles <= 0) return;
+    const dim3 b(kTileX, kTileY);
+    if (general)
+        k_adj_e<T><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m, pending);
+    else if (aniso)
+        k_adj_e_int<T, true><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m, pending);
+    else
+        k_adj_e_int<T, false><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m, pending);
+    ++*L.counter;
+}
+
+template <typename T>
+void launch_adj_h(const Launch& L, const Dom<T>* doms, const Mon* mons, const Tile* tiles, int ntiles, T S, int m,
+                  int general) {
+    if (ntiles <= 0) return;
+    const dim3 b(kTileX, kTileY);
+    if (general)
+        k_adj_h<T><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m);
+    else
+        k_adj_h_int<T><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m);
+    ++*L.counter;
+}
+
+template <typename T>
+void launch_adj_flush(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S) {
+    if (ntiles <= 0) return;
+    k_adj_flush<T><<<ntiles, dim3(kTileX, kTileY), 0, L.stream>>>(doms, tiles, S);
+    ++*L.counter;
+}
+
+template <typename T>
+void launch_inject(const Launch& L, const Dom<T>* doms, const Mon* mons, const int* entries, int nentries,
+                   long long nthreads, const long long* entry_begin, int step, int kind) {
+    if (nentries <= 0 || nthreads <= 0) return;
+    const int bs = 256;
+    k_inject<T><<<(unsigned)((nthreads + bs - 1) / bs), bs, 0, L.stream>>>(doms, mons, entries, nentries, nthreads,
+                                                                           entry_begin, step, kind);
+    ++*L.counter;
+}
+
+#define GBFDTD_INST(T)                                                                                          \
+    template void launch_adj_e<T>(const Launch&, const Dom<T>*, const Mon*, const Tile*, int, T, int, int, int, \
+                                  int);                                                                         \
+    template void launch_adj_h<T>(const Launch&, const Dom<T>*, const Mon*, const Tile*, int, T, int, int);     \
+    template void launch_adj_flush<T>(const Launch&, const Dom<T>*, const Tile*, int, T);                       \
+    template void launch_inject<T>(const Launch&, const Dom<T>*, const Mon*, const int*, int, long long,        \
+                                   const long long*, int, int);
+GBFDTD_INST(float)
+GBFDTD_INST(double)
+#undef GBFDTD_INST
+
+}  // namespace gbfdtd

@@ -1,0 +1,142 @@
+// Auxiliary kernels: the CPML tensor admission rule (Sec. 2.3), the bounding box of the pole
+// mask, a NaN/Inf scan, and the BF16 snapshot codec with one scale per slab (Sec. 3.2).
+#include <cuda_bf16.h>
+
+#include "fdtd_internal.cuh"
+
+namespace gbfdtd {
+
+// Sec. 2.3: inside an absorbing face a tensor is admitted only if the face normal is a principal
+// axis with a non-intermediate eigenvalue.  For a diagonal tensor the normal of a q-face is a
+// principal axis; reject a cell of a q-slab whose eps_qq lies strictly between the other two
+// (the same order test on 1/eps).
+template <typename T>
+__global__ void k_admission(const Dom<T>* __restrict__ dd, unsigned long long* bad) {
+    const Dom<T>& d = *dd;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= d.ncell) return;
+    const int i = (int)(t % d.n[0]);
+    const int j = (int)((t / d.n[0]) % d.n[1]);
+    const int k = (int)(t / ((long long)d.n[0] * d.n[1]));
+    const int c[3] = {i, j, k};
+    const T v[3] = {d.ie[0][t], d.ie[1][t], d.ie[2][t]};
+    for (int q = 0; q < 3; ++q) {
+        if (d.ns[q] == 0 || slab_of(c[q], d.dlo[q], d.dhi[q], d.n[q]) < 0) continue;
+        const T a = v[(q + 1) % 3], b = v[(q + 2) % 3], x = v[q];
+        const T lo = a < b ? a : b, hi = a < b ? b : a;
+        if (x > lo && x < hi) {
+            atomicAdd(bad, 1ull);
+            return;
+        }
+    }
+}
+
+__global__ void k_mask_box(const uint8_t* __restrict__ mask, int nx, int ny, int nz, int* box) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nx * ny * nz) return;
+    if (!mask[t]) return;
+    const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((long long)nx * ny));
+    atomicMin(box + 0, i);
+    atomicMin(box + 1, j);
+    atomicMin(box + 2, k);
+    atomicMax(box + 3, i + 1);
+    atomicMax(box + 4, j + 1);
+    atomicMax(box + 5, k + 1);
+}
+
+template <typename T>
+__global__ void k_nonfinite(const T* __restrict__ p, long long n, unsigned long long* bad) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const T v = p[t];
+        if (!(v == v) || v - v != T(0)) {  // NaN fails v == v; +-Inf gives Inf - Inf = NaN
+            atomicAdd(bad, 1ull);
+            return;
+        }
+    }
+}
+
+// One block per slab: s = max |x| over the slab, then q = bf16_rn(x / s).
+template <typename T>
+__global__ void k_bf16_encode(const T* __restrict__ src, long long plane, __nv_bfloat16* __restrict__ dst,
+                              float* __restrict__ scales) {
+    const long long base = (long long)blockIdx.x * plane;
+    float m = 0.f;
+    for (long long t = threadIdx.x; t < plane; t += blockDim.x) m = fmaxf(m, fabsf((float)src[base + t]));
+    __shared__ float red[32];
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) red[0] = m;
+    }
+    __syncthreads();
+    const float s = red[0];
+    const float inv = s > 0.f ? 1.f / s : 0.f;
+    for (long long t = threadIdx.x; t < plane; t += blockDim.x)
+        dst[base + t] = __float2bfloat16_rn((float)src[base + t] * inv);
+    if (threadIdx.x == 0) scales[blockIdx.x] = s;
+}
+
+template <typename T>
+__global__ void k_bf16_decode(const __nv_bfloat16* __restrict__ src, const float* __restrict__ scales, long long plane,
+                              T* __restrict__ dst) {
+    const long long base = (long long)blockIdx.x * plane;
+    const float s = scales[blockIdx.x];
+    for (long long t = threadIdx.x; t < plane; t += blockDim.x)
+        dst[base + t] = (T)(__bfloat162float(src[base + t]) * s);
+}
+
+template <typename T>
+void launch_admission(const Launch& L, const Dom<T>* d_dom, const Dom<T>& h_dom, unsigned long long* d_bad) {
+    const int bs = 256;
+    k_admission<T><<<(unsigned)((h_dom.ncell + bs - 1) / bs), bs, 0, L.stream>>>(d_dom, d_bad);
+    ++*L.counter;
+}
+
+void launch_mask_box(const Launch& L, const uint8_t* mask, int nx, int ny, int nz, int* d_box) {
+    const int bs = 256;
+    const long long n = (long long)nx * ny * nz;
+    k_mask_box<<<(unsigned)((n + bs - 1) / bs), bs, 0, L.stream>>>(mask, nx, ny, nz, d_box);
+    ++*L.counter;
+}
+
+template <typename T>
+void launch_nonfinite(const Launch& L, const T* p, long long n, unsigned long long* d_bad) {
+    if (n <= 0) return;
+    const int bs = 256;
+    long long blocks = (n + bs - 1) / bs;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_nonfinite<T><<<(unsigned)blocks, bs, 0, L.stream>>>(p, n, d_bad);
+    ++*L.counter;
+}
+
+template <typename T>
+void launch_bf16_encode(const Launch& L, const T* src, long long nplanes, long long plane, uint16_t* dst,
+                        float* scales) {
+    if (nplanes <= 0 || plane <= 0) return;
+    k_bf16_encode<T><<<(unsigned)nplanes, 256, 0, L.stream>>>(src, plane, reinterpret_cast<__nv_bfloat16*>(dst),
+                                                             scales);
+    ++*L.counter;
+}
+
+template <typename T>
+void launch_bf16_decode(const Launch& L, const uint16_t* src, const float* scales, long long nplanes,
+                        long long plane, T* dst) {
+    if (nplanes <= 0 || plane <= 0) return;
+    k_bf16_decode<T><<<(unsigned)nplanes, 256, 0, L.stream>>>(reinterpret_cast<const __nv_bfloat16*>(src), scales,
+                                                             plane, dst);
+    ++*L.counter;
+}
+
+#define GBFDTD_INST(T)                                                                                     \
+    template void launch_admission<T>(const Launch&, const Dom<T>*, const Dom<T>&, unsigned long long*);   \
+    template void launch_nonfinite<T>(const Launch&, const T*, long long, unsigned long long*);             \
+    template void launch_bf16_encode<T>(const Launch&, const T*, long long, long long, uint16_t*, float*); \
+    template void launch_bf16_decode<T>(const Launch&, const uint16_t*, const float*, long long, long long, T*);
+GBFDTD_INST(float)
+GBFDTD_INST(double)
+#undef GBFDTD_INST
+
+}  // namespace gbfdtd

@@ -236,6 +236,12 @@ def random_state_scene(shape=(9, 8, 7), d: int = 2, n_poles: int = 2, aniso: boo
     rng = _rng(seed_index)
     nx, ny, nz = shape
     inv = [1.0 / rng.uniform(1.0, 4.0, size=(nz, ny, nx)) for _ in range(3 if aniso else 1)]
+    if aniso and d > 0:
+        # inside the absorbing slabs the tensor must pass the admission rule: keep it isotropic
+        slab = np.zeros((nz, ny, nx), dtype=bool)
+        slab[:d], slab[nz - d:], slab[:, :d], slab[:, ny - d:], slab[:, :, :d], slab[:, :, nx - d:] = (True,) * 6
+        for a in (1, 2):
+            inv[a][slab] = inv[0][slab]
     poles = tuple((LORENTZ, float(rng.uniform(0.5, 3.0)), float(rng.uniform(0.05, 0.3)),
                    float(rng.uniform(0.01, 0.05))) for _ in range(n_poles))
     mask = np.zeros((nz, ny, nx), dtype=np.uint8)
