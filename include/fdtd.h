@@ -252,6 +252,25 @@ fdtd_status fdtd_synchronize(fdtd_ctx* ctx, int32_t timeout_ms);
 /* Number of kernel launches this context has enqueued since creation (instrumentation). */
 fdtd_status fdtd_launch_count(fdtd_ctx* ctx, int64_t* n);
 
+/* ---- allocation-free health check (no counterpart in the paper) ----
+ * Counts the NaN / Inf values among n values of one device array (dtype FDTD_F32 | FDTD_F64,
+ * e.g. a state part read with fdtd_get_part) into *count (host).  Unlike fdtd_check_finite it
+ * needs no context and allocates nothing: it is for callers that cannot call cudaMalloc, such
+ * as code whose device memory is owned by a framework's caching allocator or a fixed budget,
+ * where an extra allocation may fail or (cudaMalloc synchronises the device) stall other work.
+ * Its scratch is a file-scope device array of 2048 per-block counts plus one total (16 KiB),
+ * which every GPU that loads the library holds until the process exits.  Limit: n <= 33554432
+ * values (2048 blocks x 256 threads x 64 values); larger n returns FDTD_EINVAL before any GPU
+ * work.  The first call on a device looks up that array's device address (cudaGetSymbolAddress,
+ * with that device current) and must come before any stream capture on the device.  Work is
+ * enqueued on `stream` (NULL = legacy default stream) and the call synchronises it.  All calls
+ * share the one scratch array and every call rewrites the slots it reads, so consecutive calls
+ * are independent, but calls that overlap on the GPU (different streams or threads at once)
+ * race and may return wrong counts.  Errors: FDTD_EINVAL (NULL count, negative or too large n,
+ * bad dtype, NULL data with n > 0), FDTD_ECUDA (a CUDA call failed). */
+fdtd_status fdtd_count_nonfinite_noalloc(const void* data_device, int64_t n, int32_t dtype, void* stream,
+                                         int64_t* count);
+
 /* ---- instrumentation: per-kernel device time with CUDA events on the context's stream ----
  * Kernel classes: */
 enum {

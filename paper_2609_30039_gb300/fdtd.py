@@ -103,6 +103,7 @@ _SIGS = {
     "fdtd_check_finite": [_ctx],
     "fdtd_synchronize": [_ctx, C.c_int32],
     "fdtd_launch_count": [_ctx, _i64p],
+    "fdtd_count_nonfinite_noalloc": [_vp, C.c_int64, C.c_int32, _vp, _i64p],
     "fdtd_profile_begin": [_ctx, C.c_int32],
     "fdtd_profile_end": [_ctx, C.POINTER(C.c_double), _i64p],
 }
@@ -199,6 +200,14 @@ def _get_i64(name, ctx, *args):
 
 
 fdtd_profile_begin = _wrap_simple("fdtd_profile_begin")
+
+
+def fdtd_count_nonfinite_noalloc(data_ptr, n, dtype, stream=0):
+    """NaN/Inf count of n values at a device pointer; allocates no device memory (see fdtd.h)."""
+    cnt = C.c_int64()
+    st = load().fdtd_count_nonfinite_noalloc(_vp(data_ptr), int(n), int(dtype), _vp(stream), C.byref(cnt))
+    _check(st, "fdtd_count_nonfinite_noalloc", None)
+    return int(cnt.value)
 
 
 def fdtd_profile_end(ctx):
