@@ -196,7 +196,7 @@ def run_ours(args):
             e1 = torch.cuda.Event(enable_timing=True)
             last = k == args.steps - 1
             if last:
-                fdtd.fdtd_profile_begin(ctx.ctx, 8 * T_STEPS + 16)
+                fdtd.fdtd_profile_begin(ctx.ctx, 8 * T_STEPS + 16)   # event pairs around each launch
             e0.record(stream)
             solve()
             e1.record(stream)
@@ -218,12 +218,22 @@ def run_ours(args):
     value = world * cells * T_STEPS / (ms_per_step * 1e-3) / 1e9
 
     # roofline of the dominant kernel (event-timed during the last timed iteration)
-    dom = max(("e_update", "h_update"), key=lambda k: prof[k][0])
-    avg_ms = prof[dom][0] / max(prof[dom][1], 1)
-    bpc, ncell = alg_bytes_per_cell(sc, 4, dom)
-    alg_bytes = bpc * ncell
     peak, peak_kind = peaks()
-    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    if prof["persistent"][1]:
+        # one persistent launch runs up to 512 whole steps (E and H half-steps)
+        dom = "persistent"
+        bE, ncell = alg_bytes_per_cell(sc, 4, "e_update")
+        bH, _ = alg_bytes_per_cell(sc, 4, "h_update")
+        launches_p = prof["persistent"][1]
+        avg_ms = prof["persistent"][0] / launches_p
+        alg_bytes = (bE + bH) * ncell * T_STEPS / launches_p
+        achieved = (bE + bH) * ncell * T_STEPS / (prof["persistent"][0] * 1e-3) / 1e9
+    else:
+        dom = max(("e_update", "h_update"), key=lambda k: prof[k][0])
+        avg_ms = prof[dom][0] / max(prof[dom][1], 1)
+        bpc, ncell = alg_bytes_per_cell(sc, 4, dom)
+        alg_bytes = bpc * ncell
+        achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     step_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]}
     share = {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items() if v[1]}
 
@@ -417,11 +427,19 @@ def main():
     ap.add_argument("--ref-steps-per-iter", type=int, default=8)
     ap.add_argument("--profile-case", type=int, default=0,
                     help="n: run only a short n^3 FP32 forward (ncu captures on a case larger than L2)")
+    ap.add_argument("--workload", default="cpml128",
+                    choices=["cpml128", "pec32", "batched", "adjoint256", "large640"],
+                    help="cpml128 is the benchmark line; the others measure the remaining workloads")
+    ap.add_argument("--fd-cells", type=int, default=20)
+    ap.add_argument("--launch-mode", type=int, default=1, help="1 persistent cooperative launches, 0 per half-step")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.profile_case:
         profile_case(args)
+    elif args.workload != "cpml128" and args.impl == "ours":
+        {"pec32": measure_pec32, "batched": measure_batched, "adjoint256": measure_adjoint256,
+         "large640": measure_large640}[args.workload](args)
     elif args.impl == "reference":
         run_reference(args)
     else:
@@ -439,10 +457,208 @@ def profile_case(args):
     n = args.profile_case
     sc = W.cpml_blocks(n=n, d=CPML, n_steps=args.steps)
     ctx = fdtd.Context([sc], dtype="f32")
-    ctx.step(args.warmup + args.steps)
-    torch.cuda.synchronize()
-    print(json.dumps({"profile_case": n, "steps": args.warmup + args.steps, "cells": sc.cells}))
+    fdtd.fdtd_set_launch_mode(ctx.ctx, args.launch_mode)
+    ctx.step(args.warmup)
+    t = _timed(lambda: ctx.step(args.steps), ctx.stream) if args.steps else 0.0
+    print(json.dumps({"profile_case": n, "launch_mode": args.launch_mode, "steps": args.warmup + args.steps,
+                      "cells": sc.cells, "gcell_steps_s": round(sc.cells * args.steps / t / 1e9, 3) if t else None}))
     ctx.close()
+
+
+
+# ---------------------------------------------------------------------------------------------
+# measurements of the remaining workloads (one JSON line each; not the benchmark line)
+def _timed(fn, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def measure_pec32(args):
+    """32^3 FP64 PEC vacuum, 200 steps: rate, relative L2 of the six fields against the FP64
+    oracle, and the drift of the discrete energy after the source has decayed."""
+    import numpy as np
+    from oracle.oracle import build as obuild
+    from paper_2609_30039_gb300 import build as B
+    from paper_2609_30039_gb300 import fdtd
+    from paper_2609_30039_gb300 import workloads as W
+    from tests.oracle_adapter import oracle_from_scene
+    B.build()
+    obuild()
+    sc = W.pec_vacuum(32, 200)
+    ctx = fdtd.Context([sc], dtype="f64")
+    for _ in range(args.warmup):
+        fdtd.fdtd_reset(ctx.ctx)
+        ctx.step(sc.n_steps)
+    fdtd.fdtd_reset(ctx.ctx)
+    fdtd.fdtd_enable_energy(ctx.ctx, sc.n_steps + 8)   # fresh (zeroed) per-step energies for the timed run
+    t = _timed(lambda: ctx.step(sc.n_steps), ctx.stream)
+    o = oracle_from_scene(sc)
+    o.step(sc.n_steps)
+    g = np.concatenate([ctx.field(0, c).cpu().numpy().ravel() for c in range(6)])
+    r = np.concatenate([o.field(c).ravel() for c in range(6)])
+    e = ctx.energy(0, sc.n_steps)
+    tail = e[130:]
+    print(json.dumps({"workload": "pec_vacuum_32^3 FP64, 200 steps", "gcell_steps_s": round(sc.cells * 200 / t / 1e9, 3),
+                      "fields_rel_l2_vs_oracle": float(np.linalg.norm(g - r) / np.linalg.norm(r)),
+                      "energy_rel_l2_vs_oracle": float(np.linalg.norm(e - o.energy()) / np.linalg.norm(o.energy())),
+                      "energy_drift_130_200": float((tail.max() - tail.min()) / abs(tail.mean()))}))
+
+
+def measure_batched(args):
+    """64 uneven Lorentz domains (48..96 per axis), 1500 steps, FP32, one launch per tile class
+    and half-step for all domains: rate and the oracle check of the smallest domain's spectra."""
+    import numpy as np
+    import torch
+    from oracle.oracle import build as obuild
+    from paper_2609_30039_gb300 import build as B
+    from paper_2609_30039_gb300 import fdtd
+    from paper_2609_30039_gb300 import workloads as W
+    from tests.oracle_adapter import oracle_from_scene
+    B.build()
+    scs = W.lorentz_batch()
+    cells = sum(sc.cells for sc in scs)
+    ctx = fdtd.Context(scs, dtype="f32")
+    T = scs[0].n_steps
+    for _ in range(max(1, args.warmup - 2)):
+        fdtd.fdtd_reset(ctx.ctx)
+        fdtd.fdtd_dft_reset(ctx.ctx)
+        ctx.step(T)
+    ts = []
+    for _ in range(max(1, args.steps // 3)):
+        fdtd.fdtd_reset(ctx.ctx)
+        fdtd.fdtd_dft_reset(ctx.ctx)
+        ts.append(_timed(lambda: ctx.step(T), ctx.stream))
+    t = statistics.median(ts)
+    small = min(range(len(scs)), key=lambda d: scs[d].cells)
+    out = {"workload": f"lorentz_batch: {len(scs)} domains, {cells} cells, {T} steps, FP32",
+           "gcell_steps_s": round(cells * T / t / 1e9, 3), "seconds": round(t, 4),
+           "launches_per_step": 4, "graph_steps": 32}
+    if not args.no_cpu:
+        obuild()
+        o = oracle_from_scene(scs[small])
+        o.step(T)
+        F = ctx.dft(small).cpu().numpy()
+        R = o.dft(0)
+        out["smallest_domain"] = scs[small].shape
+        out["smallest_domain_dft_rel_l2_vs_oracle"] = float(np.linalg.norm(F - R) / np.linalg.norm(R))
+    print(json.dumps(out))
+
+
+def _fd_gradient_check(sc, n_cells, h, rng_seed, dtype_fd="f64", dtype_adj="f32", slots=32):
+    """d J / d rho at n_cells seeded design cells: checkpointed adjoint (dtype_adj) against
+    central differences of rho (dtype_fd) through the workload's map eps(rho)."""
+    import numpy as np
+    import torch
+    from paper_2609_30039_gb300 import adjoint as ADJ
+    from paper_2609_30039_gb300 import fdtd
+    from paper_2609_30039_gb300 import workloads as W
+    (lx, ly, lz), (hx, hy, hz) = sc.design
+
+    def loss(specs):
+        F = specs[0]
+        return float((F.abs() ** 2).sum()), [torch.view_as_real(2.0 * F).contiguous()]
+
+    ctx = fdtd.Context([sc], dtype=dtype_adj)
+    t0 = time.perf_counter()
+    (J, _), grads, stats = ADJ.DesignAdjoint(ctx, slots=slots).run(sc.n_steps, loss)
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    g = grads[0].view(3, hz - lz, hy - ly, hx - lx).cpu().numpy()
+    ctx.close()
+    # chain to rho: eps = 1 + 11 sigmoid(8 (rho - 0.5)), inv = 1/eps (isotropic: all three components)
+    rho = sc.rho
+    sig = 1.0 / (1.0 + np.exp(-8.0 * (rho - 0.5)))
+    eps = 1.0 + 11.0 * sig
+    dinv_drho = -(11.0 * 8.0 * sig * (1.0 - sig)) / eps ** 2
+    dJdrho = g.sum(axis=0) * dinv_drho
+    rng = np.random.default_rng(rng_seed)
+    shp = rho.shape
+    idx = [np.unravel_index(int(k), shp) for k in rng.choice(rho.size, size=n_cells, replace=False)]
+    fdc = fdtd.Context([W.Scene(**{**sc.__dict__, "design": None})], dtype=dtype_fd)
+
+    def J_of(rho2):
+        inv = sc.inv_eps3()[0].copy()
+        inv[lz:hz, ly:hy, lx:hx] = 1.0 / W.density_to_eps(rho2)
+        t = torch.from_numpy(inv.astype(np.float64 if dtype_fd == "f64" else np.float32)).to(fdc.device)
+        fdc.set_inv_eps(0, [t, t, t])
+        fdtd.fdtd_reset(fdc.ctx)
+        fdtd.fdtd_dft_reset(fdc.ctx)
+        fdc.step(sc.n_steps)
+        F = fdc.dft(0)
+        return float((F.abs() ** 2).sum())
+
+    fd, ad = [], []
+    t0 = time.perf_counter()
+    for c in idx:
+        rp, rm = rho.copy(), rho.copy()
+        rp[c] += h
+        rm[c] -= h
+        fd.append((J_of(rp) - J_of(rm)) / (2 * h))
+        ad.append(dJdrho[c])
+    t_fd = time.perf_counter() - t0
+    fd, ad = np.array(fd), np.array(ad)
+    big = np.abs(fd) >= 1e-2 * np.abs(fd).max()
+    return {"J": J, "gradient_seconds": round(t_grad, 3), "fd_seconds": round(t_fd, 1),
+            "forward_steps_incl_replay": stats["forward_steps"], "adjoint_steps": stats["adjoint_steps"],
+            "vector_rel_l2": float(np.linalg.norm(ad - fd) / np.linalg.norm(fd)),
+            "max_rel_err_large_cells": float(np.max(np.abs(ad[big] - fd[big]) / np.abs(fd[big]))),
+            "n_cells": n_cells, "h": h, "fd_dtype": dtype_fd, "adjoint_dtype": dtype_adj}
+
+
+def measure_adjoint256(args):
+    """256^3 adjoint workload, 3000 steps, 32 checkpoints: FP32 checkpointed gradient against
+    FP64 central differences of rho at seeded design cells (h = 1e-3)."""
+    from paper_2609_30039_gb300 import build as B
+    from paper_2609_30039_gb300 import workloads as W
+    B.build()
+    sc = W.adjoint_design()
+    res = _fd_gradient_check(sc, args.fd_cells, 1e-3, 2609030042)
+    res["workload"] = "adjoint_design_256^3, 3000 steps, C=32"
+    res["gradient_forward_equiv_gcell_steps_s"] = round(sc.cells * sc.n_steps / res["gradient_seconds"] / 1e9, 3)
+    print(json.dumps(res))
+
+
+def measure_large640(args):
+    """640^3 anisotropic two-pole workload, 4000 steps: the checkpointed gradient with BF16
+    snapshots against the same gradient with exact FP32 snapshots."""
+    import numpy as np
+    import torch
+    from paper_2609_30039_gb300 import adjoint as ADJ
+    from paper_2609_30039_gb300 import build as B
+    from paper_2609_30039_gb300 import fdtd
+    from paper_2609_30039_gb300 import workloads as W
+    B.build()
+    n = args.profile_case or 640
+    sc = W.large_adjoint(n=n)
+    (lx, ly, lz), (hx, hy, hz) = sc.design
+
+    def loss(specs):
+        F = specs[0]
+        a = F.abs().clamp_min(1e-30)
+        return float(a.sum()), [torch.view_as_real(F / a).contiguous()]
+
+    res = {"workload": f"large_adjoint_{n}^3, {sc.n_steps} steps", "cells": sc.cells}
+    grads = {}
+    for codec, name in ((fdtd.FDTD_CODEC_NATIVE, "fp32_snapshots"), (fdtd.FDTD_CODEC_BF16, "bf16_snapshots")):
+        ctx = fdtd.Context([sc], dtype="f32")
+        snap = fdtd.fdtd_snapshot_bytes(ctx.ctx, codec)
+        t0 = time.perf_counter()
+        (J, _), g, stats = ADJ.DesignAdjoint(ctx, slots=16, codec=codec).run(sc.n_steps, loss)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        grads[name] = g[0].cpu().numpy()
+        res[name] = {"J": J, "seconds": round(dt, 2), "snapshot_bytes": snap, "slots": 16,
+                     "forward_steps_incl_replay": stats["forward_steps"]}
+        ctx.close()
+    a, b = grads["fp32_snapshots"], grads["bf16_snapshots"]
+    res["bf16_vs_fp32_snapshot_gradient_rel_l2"] = float(np.linalg.norm(b - a) / np.linalg.norm(a))
+    print(json.dumps(res))
 
 
 if __name__ == "__main__":

@@ -165,8 +165,14 @@ fdtd_status fdtd_enable_energy(fdtd_ctx* ctx, int32_t capacity);
 fdtd_status fdtd_energy_read(fdtd_ctx* ctx, int32_t domain, double* host_dst, int32_t n);
 
 /* Advances every domain by n_steps forward steps (Eq. (yee): E update with CPML, poles and
- * eps^-1; E sources; E DFT; H update with CPML; H sources; H DFT; energy).  Asynchronous. */
+ * eps^-1; E sources; E DFT; H update with CPML; H sources; H DFT; energy).  Asynchronous.
+ * Runs as persistent cooperative launches of up to 512 steps (grid-wide barrier between the
+ * half-steps) unless fdtd_set_launch_mode selected per-half-step launches. */
 fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps);
+
+/* mode 0: per-half-step launches (replayed as CUDA graphs); mode 1 (default): persistent
+ * cooperative launches.  Both compute the same values bitwise. */
+fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode);
 
 /* Number of forward steps the held state has taken (u^n: returns n). */
 fdtd_status fdtd_step_count(fdtd_ctx* ctx, int64_t* n);
@@ -281,7 +287,8 @@ enum {
     FDTD_KERNEL_STEP = 4,     /* device step counter */
     FDTD_KERNEL_ADJ_E = 5,    /* transposed step, E side */
     FDTD_KERNEL_ADJ_H = 6,    /* transposed step, H side */
-    FDTD_KERNEL_CLASSES = 7
+    FDTD_KERNEL_PERSISTENT = 7, /* persistent launch of several forward steps (E and H) */
+    FDTD_KERNEL_CLASSES = 8
 };
 /* Starts recording an event pair around every kernel launch (at most max_launches launches,
  * later ones are not timed).  Adds two event records per launch to the stream. */

@@ -1,5 +1,7 @@
 // C-ABI of the gbfdtd library (declared in include/fdtd.h): context, memory plan, device
 // descriptors, forward stepping, adjoint sweep bookkeeping, snapshots.
+#include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -42,6 +44,7 @@ struct DomainHost {
     int glo[3] = {0, 0, 0}, ghi[3] = {0, 0, 0};
     double* grad = nullptr;
     std::vector<int> mons;
+    std::vector<int> srcs;
 };
 
 struct MonHost {
@@ -84,10 +87,13 @@ struct fdtd_ctx {
     int nentries[2] = {0, 0};
     long long nthreads[2] = {0, 0};
     std::vector<SrcHost> srcs;
-    Src* d_srcs[2] = {nullptr, nullptr};
-    int nsrc[2] = {0, 0};
-    long long nsrccells[2] = {0, 0};
+    Src* d_srcs = nullptr;          // every source of every domain
     int* d_step = nullptr;
+    unsigned* d_ticket = nullptr;   // completion ticket of the last H launch of a step
+    GridSync* d_sync = nullptr;     // barrier / ticket of the persistent step kernel
+    Tile* d_tiles_lpt = nullptr;    // general tiles first, then interior (persistent kernel)
+    int use_persistent = 1;
+    int persist_grid = 0;
     int h_step_tmp = 0;
     long long step = 0;
     long long adj_step = 0;
@@ -307,6 +313,8 @@ void fill_dom(const fdtd_ctx* c, const DomainHost& h, Dom<T>& d) {
     d.grad = h.grad;
     d.nmon = (int)h.mons.size();
     for (int i = 0; i < d.nmon; ++i) d.mon[i] = h.mons[i];
+    d.nsrc = (int)h.srcs.size();
+    for (int i = 0; i < d.nsrc; ++i) d.src[i] = h.srcs[i];
     d.energy = c->energy_on ? h.energy : nullptr;
     d.energy_cap = h.energy_cap;
 }
@@ -408,31 +416,28 @@ fdtd_status sync_mons(fdtd_ctx* c) {
     return FDTD_OK;
 }
 
+fdtd_status upload_tiles(fdtd_ctx* c);
+
 fdtd_status sync_srcs(fdtd_ctx* c) {
     CK(c, cudaStreamSynchronize(c->stream));
     drop_graphs(c);
-    for (int kind = 0; kind < 2; ++kind) {
-        if (c->d_srcs[kind]) dfree(c, c->d_srcs[kind]);
-        c->d_srcs[kind] = nullptr;
+    if (c->d_srcs) dfree(c, c->d_srcs);
+    c->d_srcs = nullptr;
+    for (auto& d : c->doms) d.srcs.clear();
+    if (!c->srcs.empty()) {
         std::vector<Src> hs;
-        long long tot = 0;
-        for (auto& s : c->srcs) {
-            if ((s.s.comp >= 3) != (kind == 1)) continue;
-            Src x = s.s;
-            x.begin = tot;
-            tot += x.ncell;
-            hs.push_back(x);
+        for (size_t k = 0; k < c->srcs.size(); ++k) {
+            hs.push_back(c->srcs[k].s);
+            c->doms[c->srcs[k].s.dom].srcs.push_back((int)k);
         }
-        c->nsrc[kind] = (int)hs.size();
-        c->nsrccells[kind] = tot;
-        if (hs.empty()) continue;
-        fdtd_status st = dmalloc(c, (void**)&c->d_srcs[kind], sizeof(Src) * hs.size());
+        fdtd_status st = dmalloc(c, (void**)&c->d_srcs, sizeof(Src) * hs.size());
         if (st != FDTD_OK) return st;
-        CK(c, cudaMemcpyAsync(c->d_srcs[kind], hs.data(), sizeof(Src) * hs.size(), cudaMemcpyHostToDevice,
-                              c->stream));
+        CK(c, cudaMemcpyAsync(c->d_srcs, hs.data(), sizeof(Src) * hs.size(), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
     }
-    CK(c, cudaStreamSynchronize(c->stream));
-    return FDTD_OK;
+    fdtd_status st = upload_tiles(c);
+    if (st != FDTD_OK) return st;
+    return sync_doms(c);
 }
 
 bool valid_dom(const fdtd_ctx* c, int d) { return d >= 0 && d < (int)c->doms.size(); }
@@ -506,54 +511,170 @@ fdtd_status mask_box(fdtd_ctx* c, const uint8_t* mask, const int n[3], int lo[3]
 }
 
 // Tiles of kTileX x kTileY columns and a z chunk chosen so that the grid holds several blocks
-// per SM.  A tile is "interior" when every cell and its -1 / +1 neighbours along each axis lie
-// strictly inside the domain and outside the CPML slabs and the pole box.
+// per SM.  Each domain is split into an interior box and the boundary shell around it; the
+// interior box holds every cell whose update and transpose need no CPML, PEC or domain-edge
+// code: per axis [d_lo + 1, N - max(1, d_hi)) (d_lo + 1 keeps the -1 neighbour out of the low
+// H slab, whose CPML terms the transposed H update carries to E; 1 when there is no CPML).
+// Interior tiles meeting the pole box join the general class.  The shell is cut into six
+// disjoint boxes (z-low, z-high, y-low, y-high, x-low, x-high) of general tiles.
+// Packs a list of disjoint [lo, hi) ranges, in order, into chunks of at most w coordinates that
+// span at most two ranges each: {s0, s1, s2, s3} as in Tile::xs.
+static std::vector<std::array<int, 4>> pack_ranges(const std::vector<std::pair<int, int>>& rs, int w) {
+    std::vector<std::array<int, 4>> out;
+    std::vector<std::pair<int, int>> cur;
+    int used = 0;
+    auto flush = [&]() {
+        if (cur.empty()) return;
+        std::array<int, 4> a;
+        a[0] = cur[0].first;
+        a[1] = cur[0].second;
+        a[2] = cur.size() > 1 ? cur[1].first : cur[0].second;
+        a[3] = cur.size() > 1 ? cur[1].second : cur[0].second;
+        out.push_back(a);
+        cur.clear();
+        used = 0;
+    };
+    for (auto r : rs) {
+        int lo = r.first;
+        while (lo < r.second) {
+            if (cur.size() == 2 || used == w) flush();
+            const int take = std::min(w - used, r.second - lo);
+            cur.push_back({lo, lo + take});
+            used += take;
+            lo += take;
+        }
+    }
+    flush();
+    return out;
+}
+
 void build_tiles(fdtd_ctx* c) {
     c->tiles.clear();
     c->tiles_gen.clear();
     c->tiles_int.clear();
-    long long cols = 0, zsum = 0;
-    for (const auto& d : c->doms) {
-        cols += (long long)((d.n[0] + kTileX - 1) / kTileX) * ((d.n[1] + kTileY - 1) / kTileY);
+    long long zsum = 0;
+    for (const auto& d : c->doms)
         zsum += (long long)((d.n[0] + kTileX - 1) / kTileX) * ((d.n[1] + kTileY - 1) / kTileY) * d.n[2];
-    }
-    const long long target = 152 * 8;
-    int zc = (int)(zsum / target);
+    int zc = (int)(zsum / (152 * 8));
     zc = zc < 4 ? 4 : (zc > 32 ? 32 : zc);
-    (void)cols;
     for (int di = 0; di < (int)c->doms.size(); ++di) {
         const DomainHost& d = c->doms[di];
-        for (int z0 = 0; z0 < d.n[2]; z0 += zc)
-            for (int y0 = 0; y0 < d.n[1]; y0 += kTileY)
-                for (int x0 = 0; x0 < d.n[0]; x0 += kTileX) {
-                    Tile t;
-                    t.dom = di;
-                    t.x0 = x0;
-                    t.y0 = y0;
-                    t.z0 = z0;
-                    t.z1 = z0 + zc < d.n[2] ? z0 + zc : d.n[2];
-                    const int lo[3] = {x0, y0, z0};
-                    const int hi[3] = {x0 + kTileX < d.n[0] ? x0 + kTileX : d.n[0],
-                                       y0 + kTileY < d.n[1] ? y0 + kTileY : d.n[1], t.z1};
-                    // interior: no cell in a slab or on a PEC plane, the -1 neighbour outside the low
-                    // H slab (the transposed H update carries the H cell's CPML terms to E at +1),
-                    // the +1 neighbour inside the domain
-                    bool inner = true;
-                    for (int q = 0; q < 3; ++q) {
-                        const int a = d.dlo[q] > 0 ? d.dlo[q] + 1 : 1;
-                        const int b = d.n[q] - (d.dhi[q] > 1 ? d.dhi[q] : 1);
-                        if (lo[q] < a || hi[q] > b) inner = false;
-                    }
-                    if (d.npole > 0 && d.bcell > 0) {
-                        bool meet = true;
-                        for (int q = 0; q < 3; ++q)
-                            if (hi[q] <= d.blo[q] || lo[q] >= d.bhi[q]) meet = false;
-                        if (meet) inner = false;
-                    }
-                    c->tiles.push_back(t);
-                    (inner ? c->tiles_int : c->tiles_gen).push_back(t);
-                }
+        int a[3], b[3];
+        bool has_int = true;
+        for (int q = 0; q < 3; ++q) {
+            a[q] = d.dlo[q] > 0 ? d.dlo[q] + 1 : 1;
+            b[q] = d.n[q] - (d.dhi[q] > 1 ? d.dhi[q] : 1);
+            if (a[q] >= b[q]) has_int = false;
+        }
+        // xr / yr: column ranges; zr: z ranges; interior decides the class
+        auto emit = [&](const std::vector<std::pair<int, int>>& xr, const std::vector<std::pair<int, int>>& yr,
+                        const std::vector<std::pair<int, int>>& zr, bool interior) {
+            const auto xt = pack_ranges(xr, kTileX);
+            const auto yt = pack_ranges(yr, kTileY);
+            for (auto z : zr)
+                for (int z0 = z.first; z0 < z.second; z0 += zc)
+                    for (const auto& ys : yt)
+                        for (const auto& xs : xt) {
+                            Tile t;
+                            t.dom = di;
+                            for (int k = 0; k < 4; ++k) {
+                                t.xs[k] = xs[k];
+                                t.ys[k] = ys[k];
+                            }
+                            t.x0 = xs[0];
+                            t.y0 = ys[0];
+                            t.z0 = z0;
+                            t.z1 = z0 + zc < z.second ? z0 + zc : z.second;
+                            t.flags = 0;
+                            bool inner = interior;
+                            if (inner && d.npole > 0 && d.bcell > 0) {
+                                const int tl[3] = {xs[0], ys[0], t.z0}, th[3] = {xs[1], ys[1], t.z1};
+                                bool meet = true;
+                                for (int q = 0; q < 3; ++q)
+                                    if (th[q] <= d.blo[q] || tl[q] >= d.bhi[q]) meet = false;
+                                if (meet) inner = false;
+                            }
+                            c->tiles.push_back(t);
+                            (inner ? c->tiles_int : c->tiles_gen).push_back(t);
+                        }
+        };
+        typedef std::vector<std::pair<int, int>> R;
+        const int N[3] = {d.n[0], d.n[1], d.n[2]};
+        if (!has_int) {
+            emit(R{{0, N[0]}}, R{{0, N[1]}}, R{{0, N[2]}}, false);
+            continue;
+        }
+        // z slabs (full xy), y slabs (both sides in one tile row range), x slabs (both sides per warp)
+        emit(R{{0, N[0]}}, R{{0, N[1]}}, R{{0, a[2]}, {b[2], N[2]}}, false);
+        emit(R{{0, N[0]}}, R{{0, a[1]}, {b[1], N[1]}}, R{{a[2], b[2]}}, false);
+        emit(R{{0, a[0]}, {b[0], N[0]}}, R{{a[1], b[1]}}, R{{a[2], b[2]}}, false);
+        emit(R{{a[0], b[0]}}, R{{a[1], b[1]}}, R{{a[2], b[2]}}, true);
     }
+}
+
+// Per-tile flags: which tiles hold cells of a soft source or of a DFT monitor (of E or H).
+void tile_flags(fdtd_ctx* c, Tile& t) {
+    const DomainHost& d = c->doms[t.dom];
+    // a two-segment tile is tested against the hull of its columns (flags may over-select)
+    const int lo[3] = {t.xs[0], t.ys[0], t.z0};
+    const int hi[3] = {t.xs[3] > t.xs[1] ? t.xs[3] : t.xs[1], t.ys[3] > t.ys[1] ? t.ys[3] : t.ys[1], t.z1};
+    auto meets = [&](const int* blo, const int* bhi) {
+        for (int q = 0; q < 3; ++q)
+            if (hi[q] <= blo[q] || lo[q] >= bhi[q]) return false;
+        return true;
+    };
+    t.flags = 0;
+    for (int k : d.srcs) {
+        const Src& s = c->srcs[k].s;
+        if (meets(s.lo, s.hi)) t.flags |= s.comp < 3 ? kTileSrcE : kTileSrcH;
+    }
+    for (int k : d.mons) {
+        const Mon& m = c->mons[k].m;
+        if (!meets(m.lo, m.hi)) continue;
+        if (m.mask & 7u) t.flags |= kTileMonE;
+        if (m.mask & 56u) t.flags |= kTileMonH;
+    }
+}
+
+fdtd_status upload_tiles(fdtd_ctx* c) {
+    drop_graphs(c);
+    std::vector<Tile> lpt;
+    for (auto& t : c->tiles_gen) {
+        tile_flags(c, t);
+        t.flags |= kTileGeneral;
+        lpt.push_back(t);
+    }
+    for (auto& t : c->tiles_int) {
+        tile_flags(c, t);
+        lpt.push_back(t);
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (!lpt.empty()) {
+        if (!c->d_tiles_lpt) {
+            fdtd_status st = dmalloc(c, (void**)&c->d_tiles_lpt, sizeof(Tile) * lpt.size());
+            if (st != FDTD_OK) return st;
+        }
+        CK(c, cudaMemcpyAsync(c->d_tiles_lpt, lpt.data(), sizeof(Tile) * lpt.size(), cudaMemcpyHostToDevice,
+                              c->stream));
+    }
+    std::vector<Tile>* lists[3] = {&c->tiles, &c->tiles_gen, &c->tiles_int};
+    Tile** dst[3] = {&c->d_tiles, &c->d_tiles_gen, &c->d_tiles_int};
+    for (int li = 0; li < 3; ++li) {
+        for (auto& t : *lists[li]) {
+            const int g = t.flags & kTileGeneral;
+            tile_flags(c, t);
+            t.flags |= g;
+        }
+        if (lists[li]->empty()) continue;
+        if (!*dst[li]) {
+            fdtd_status st = dmalloc(c, (void**)dst[li], sizeof(Tile) * lists[li]->size());
+            if (st != FDTD_OK) return st;
+        }
+        CK(c, cudaMemcpyAsync(*dst[li], lists[li]->data(), sizeof(Tile) * lists[li]->size(), cudaMemcpyHostToDevice,
+                              c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FDTD_OK;
 }
 
 // Event pair around one launch when profiling (two records on the stream, no work changed).
@@ -577,45 +698,28 @@ template <typename T>
 void step_once(fdtd_ctx* c, cudaStream_t st) {
     const Launch l{st, &c->launches};
     const Dom<T>* dd = (const Dom<T>*)c->d_doms;
-    const int nt = (int)c->tiles.size();
-    (void)nt;
+    StepArgs a;
+    a.srcs = c->d_srcs;
+    a.mons = c->d_mons;
+    a.d_step = c->d_step;
+    a.d_ticket = c->d_ticket;
+    a.dft_on = c->dft_enabled;
+    const int ng = (int)c->tiles_gen.size(), ni = (int)c->tiles_int.size();
     {
         Prof p(c, FDTD_KERNEL_E);
-        launch_e_update<T>(l, dd, c->d_tiles_int, (int)c->tiles_int.size(), (T)c->S, 0, c->aniso);
+        launch_e_update<T>(l, dd, c->d_tiles_gen, ng, (T)c->S, a, 1, 1);
     }
     {
         Prof p(c, FDTD_KERNEL_E);
-        launch_e_update<T>(l, dd, c->d_tiles_gen, (int)c->tiles_gen.size(), (T)c->S, 1, 1);
-    }
-    if (c->nsrc[0]) {
-        Prof p(c, FDTD_KERNEL_SOURCE);
-        launch_sources<T>(l, dd, c->d_srcs[0], c->nsrc[0], c->nsrccells[0], c->d_step);
-    }
-    if (c->dft_enabled && c->nentries[0]) {
-        Prof p(c, FDTD_KERNEL_DFT);
-        launch_dft<T>(l, dd, c->d_mons, c->d_entries[0], c->nentries[0], c->nthreads[0], c->d_entry_begin[0],
-                      c->d_step, 0);
+        launch_e_update<T>(l, dd, c->d_tiles_int, ni, (T)c->S, a, 0, c->aniso);
     }
     {
         Prof p(c, FDTD_KERNEL_H);
-        launch_h_update<T>(l, dd, c->d_tiles_int, (int)c->tiles_int.size(), (T)c->S, c->d_step, 0, c->energy_on);
+        launch_h_update<T>(l, dd, c->d_tiles_gen, ng, (T)c->S, a, 1, c->energy_on, ni == 0);
     }
     {
         Prof p(c, FDTD_KERNEL_H);
-        launch_h_update<T>(l, dd, c->d_tiles_gen, (int)c->tiles_gen.size(), (T)c->S, c->d_step, 1, c->energy_on);
-    }
-    if (c->nsrc[1]) {
-        Prof p(c, FDTD_KERNEL_SOURCE);
-        launch_sources<T>(l, dd, c->d_srcs[1], c->nsrc[1], c->nsrccells[1], c->d_step);
-    }
-    if (c->dft_enabled && c->nentries[1]) {
-        Prof p(c, FDTD_KERNEL_DFT);
-        launch_dft<T>(l, dd, c->d_mons, c->d_entries[1], c->nentries[1], c->nthreads[1], c->d_entry_begin[1],
-                      c->d_step, 1);
-    }
-    {
-        Prof p(c, FDTD_KERNEL_STEP);
-        launch_advance(l, c->d_step, 1);
+        launch_h_update<T>(l, dd, c->d_tiles_int, ni, (T)c->S, a, 0, c->energy_on, 1);
     }
 }
 
@@ -679,13 +783,8 @@ fdtd_status build_graph(fdtd_ctx* c) {
         c->graph[a][b] = nullptr;
         return fail(c, FDTD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
-    long long per = 0;
-    {
-        // count the launches of one step without enqueuing anything
-        int tiles_i = c->tiles_int.empty() ? 0 : 1, tiles_g = c->tiles_gen.empty() ? 0 : 1;
-        per = 2 * (tiles_i + tiles_g) + (c->nsrc[0] ? 1 : 0) + (c->nsrc[1] ? 1 : 0) +
-              (c->dft_enabled && c->nentries[0] ? 1 : 0) + (c->dft_enabled && c->nentries[1] ? 1 : 0) + 1;
-    }
+    // launches of one step: E and H for each non-empty tile class
+    const long long per = 2 * ((c->tiles_int.empty() ? 0 : 1) + (c->tiles_gen.empty() ? 0 : 1));
     c->graph_launches[a][b] = per * kGraphSteps;
     return FDTD_OK;
 }
@@ -779,6 +878,13 @@ fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cp
     if (e != cudaSuccess) return bail(FDTD_ECUDA);
     c->owned.push_back(c->d_step);
     if (cudaMemsetAsync(c->d_step, 0, 64, c->stream) != cudaSuccess) return bail(FDTD_ECUDA);
+    e = cudaMalloc((void**)&c->d_ticket, 64);
+    if (e != cudaSuccess) return bail(FDTD_ECUDA);
+    c->owned.push_back(c->d_ticket);
+    e = cudaMalloc((void**)&c->d_sync, sizeof(GridSync));
+    if (e != cudaSuccess) return bail(FDTD_ECUDA);
+    c->owned.push_back(c->d_sync);
+    if (cudaMemsetAsync(c->d_ticket, 0, 64, c->stream) != cudaSuccess) return bail(FDTD_ECUDA);
 
     // domain geometry, pole boxes and the memory plan
     c->doms.resize(n_domains);
@@ -859,18 +965,7 @@ fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cp
         const DomainHost& d = c->doms[di];
         if (d.ie[0] != d.ie[1] || d.ie[1] != d.ie[2]) c->aniso = 1;
     }
-    {
-        std::vector<Tile>* lists[3] = {&c->tiles, &c->tiles_gen, &c->tiles_int};
-        Tile** dst[3] = {&c->d_tiles, &c->d_tiles_gen, &c->d_tiles_int};
-        for (int li = 0; li < 3; ++li) {
-            if (lists[li]->empty()) continue;
-            if (dmalloc(c, (void**)dst[li], sizeof(Tile) * lists[li]->size()) != FDTD_OK) return bail(FDTD_ENOMEM);
-            if (cudaMemcpyAsync(*dst[li], lists[li]->data(), sizeof(Tile) * lists[li]->size(), cudaMemcpyHostToDevice,
-                                c->stream) != cudaSuccess ||
-                cudaStreamSynchronize(c->stream) != cudaSuccess)
-                return bail(FDTD_ECUDA);
-        }
-    }
+    if (upload_tiles(c) != FDTD_OK) return bail(FDTD_ECUDA);
     if (sync_doms(c) != FDTD_OK) return bail(FDTD_ECUDA);
     for (int di = 0; di < n_domains; ++di) {
         fdtd_status st = admission(c, di);
@@ -936,6 +1031,11 @@ fdtd_status fdtd_add_source(fdtd_ctx* ctx, int32_t domain, int32_t component, co
         return fail(ctx, FDTD_EINVAL, "bad source arguments");
     const DomainHost& d = ctx->doms[domain];
     if (!valid_box(d, lo, hi)) return fail(ctx, FDTD_EINVAL, "source box outside the domain");
+    if ((int)d.srcs.size() >= kMaxSrcPerDom) return fail(ctx, FDTD_EINVAL, "at most 8 sources per domain");
+    if (component < 3)
+        for (int q = 0; q < 3; ++q)
+            if (q != component && lo[q] == 0)
+                return fail(ctx, FDTD_EINVAL, "an electric source box must not include PEC-held nodes (coordinate 0)");
     for (auto& s : ctx->srcs) {
         if (s.s.dom != domain || s.s.comp != component) continue;
         bool overlap = true;
@@ -1010,6 +1110,8 @@ fdtd_status fdtd_add_dft_monitor(fdtd_ctx* ctx, int32_t domain, const int32_t lo
     if (st != FDTD_OK) return st;
     if (monitor_id) *monitor_id = id;
     st = sync_mons(ctx);
+    if (st != FDTD_OK) return st;
+    st = upload_tiles(ctx);
     if (st != FDTD_OK) return st;
     return sync_doms(ctx);
 }
@@ -1086,7 +1188,32 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
         }
     }
     int left = n_steps;
-    if (ctx->use_graphs && !ctx->prof_on && n_steps >= kGraphSteps) {
+    if (ctx->use_persistent && n_steps > 0) {
+        StepArgs a;
+        a.srcs = ctx->d_srcs;
+        a.mons = ctx->d_mons;
+        a.d_step = ctx->d_step;
+        a.d_ticket = ctx->d_ticket;
+        a.dft_on = ctx->dft_enabled;
+        const int nt = (int)(ctx->tiles_gen.size() + ctx->tiles_int.size());
+        const Launch l{ctx->stream, &ctx->launches};
+        while (left > 0) {
+            const int chunk = left > 512 ? 512 : left;
+            cudaError_t e;
+            {
+                Prof p(ctx, FDTD_KERNEL_PERSISTENT);
+                if (ctx->dtype == FDTD_F32)
+                    e = launch_steps<float>(l, (const Dom<float>*)ctx->d_doms, ctx->d_tiles_lpt, nt, (float)ctx->S, a,
+                                            chunk, ctx->aniso, ctx->energy_on, ctx->d_sync, &ctx->persist_grid);
+                else
+                    e = launch_steps<double>(l, (const Dom<double>*)ctx->d_doms, ctx->d_tiles_lpt, nt, ctx->S, a, chunk,
+                                             ctx->aniso, ctx->energy_on, ctx->d_sync, &ctx->persist_grid);
+            }
+            if (e != cudaSuccess) return fail(ctx, FDTD_ECUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
+            left -= chunk;
+        }
+    }
+    if (ctx->use_graphs && !ctx->prof_on && left >= kGraphSteps) {
         fdtd_status st = build_graph(ctx);
         if (st != FDTD_OK) return st;
         cudaGraphExec_t ge = ctx->graph[ctx->dft_enabled][ctx->energy_on];
@@ -1104,6 +1231,13 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
     }
     CKL(ctx);
     ctx->step += n_steps;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode) {
+    GUARD(ctx);
+    if (mode != 0 && mode != 1) return fail(ctx, FDTD_EINVAL, "launch mode must be 0 or 1");
+    ctx->use_persistent = mode;
     return FDTD_OK;
 }
 
@@ -1421,7 +1555,12 @@ fdtd_status fdtd_synchronize(fdtd_ctx* ctx, int32_t timeout_ms) {
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaStreamQuery(ctx->stream);
-        if (e == cudaSuccess) return FDTD_OK;
+        if (e == cudaSuccess) {
+            GridSync gs;
+            CK(ctx, cudaMemcpy(&gs, ctx->d_sync, sizeof(gs), cudaMemcpyDeviceToHost));
+            if (gs.err) return fail(ctx, FDTD_ETIMEOUT, "a grid barrier of the persistent step kernel ran out");
+            return FDTD_OK;
+        }
         if (e != cudaErrorNotReady) return fail(ctx, FDTD_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
         const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
         if (ms.count() >= timeout_ms) return fail(ctx, FDTD_ETIMEOUT, "stream not finished within the timeout");

@@ -19,6 +19,7 @@ namespace gbfdtd {
 
 constexpr int kMaxPole = 16;
 constexpr int kMaxMonPerDom = 8;
+constexpr int kMaxSrcPerDom = 8;
 constexpr int kTileX = 32;
 constexpr int kTileY = 8;
 
@@ -47,8 +48,10 @@ struct Dom {
     int design;                // 1 if a design box is set
     int glo[3], ghi[3];
     double* grad;              // [3][design cells]
-    int nmon;                  // monitors of this domain (adjoint injection)
+    int nmon;                  // monitors of this domain
     int mon[kMaxMonPerDom];
+    int nsrc;                  // soft sources of this domain
+    int src[kMaxSrcPerDom];
     double* energy;            // per-step energy or nullptr
     int energy_cap;
 };
@@ -80,11 +83,41 @@ struct Src {
 };
 
 // One tile of work: kTileX x kTileY columns of a domain marched over [z0, z1).
+enum : int {
+    kTileSrcE = 1,   // holds a cell of an electric soft source
+    kTileSrcH = 2,   // ... of a magnetic soft source
+    kTileMonE = 4,   // holds a cell of a monitor recording an E component
+    kTileMonH = 8,   // ... an H component
+    kTileGeneral = 16 // needs the CPML / PEC / pole code path
+};
+
+// State of the grid-wide barrier and tile ticket of the persistent step kernel.
+struct GridSync {
+    unsigned arrive;
+    unsigned gen;
+    int err;                  // set when a barrier wait ran out (the launch then stops)
+    int pad;
+    unsigned long long ticket;
+};
+// Columns of a tile: lane tx maps to x in [xs[0], xs[1]) then [xs[2], xs[3]) (two segments let
+// one warp cover both opposite CPML slabs), thread row ty to y likewise with ys; at most
+// kTileX x kTileY columns.  z runs over [z0, z1).
 struct Tile {
     int dom;
-    int x0, y0;
+    int xs[4];
+    int ys[4];
     int z0, z1;
+    int flags;
+    int x0, y0;   // first column (for flag tests)
 };
+
+// Coordinate of lane `l` of a two-segment range, or -1 past its end.
+__host__ __device__ inline int seg_coord(const int* s, int l) {
+    const int n1 = s[1] - s[0];
+    if (l < n1) return s[0] + l;
+    const int x = s[2] + (l - n1);
+    return x < s[3] ? x : -1;
+}
 
 __host__ __device__ inline long long cidx(const int* n, int i, int j, int k) {
     return ((long long)k * n[1] + j) * n[0] + i;
@@ -121,18 +154,27 @@ struct Launch {
 };
 
 // Forward kernels (kernels_fwd.cu)
+// Step context shared by the fused forward kernels: sources, monitors, the device step counter
+// and the grid-completion ticket that advances it.
+struct StepArgs {
+    const Src* srcs;
+    const Mon* mons;
+    int* d_step;
+    unsigned* d_ticket;
+    int dft_on;
+};
+
 template <typename T>
-void launch_e_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, int general, int aniso);
+void launch_e_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
+                     int general, int aniso);
 template <typename T>
-void launch_h_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const int* d_step,
-                     int general, int energy);
-template <typename T>
-void launch_sources(const Launch& L, const Dom<T>* doms, const Src* srcs, int nsrc, long long ncells,
-                    const int* d_step);
-template <typename T>
-void launch_dft(const Launch& L, const Dom<T>* doms, const Mon* mons, const int* entries, int nentries,
-                long long nthreads, const long long* entry_begin, const int* d_step, int kind);
+void launch_h_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
+                     int general, int energy, int advance);
 void launch_advance(const Launch& L, int* d_step, int delta);
+// Persistent cooperative launch advancing nsteps forward steps over all tiles (general first).
+template <typename T>
+cudaError_t launch_steps(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
+                         int nsteps, int aniso, int energy, GridSync* gs, int* grid_used);
 
 // Adjoint kernels (kernels_adj.cu)
 template <typename T>

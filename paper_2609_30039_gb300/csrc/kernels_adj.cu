@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_adj_e(const Dom<T>* __restri
                                                           const Tile* __restrict__ tiles, T S, int m, int pending) {
     const Tile t = tiles[blockIdx.x];
     const Dom<T>& d = doms[t.dom];
-    const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
-    if (i >= d.n[0] || j >= d.n[1]) return;
+    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    if (i < 0 || j < 0) return;
     const long long st[3] = {1, (long long)d.n[0], (long long)d.n[0] * d.n[1]};
     for (int k = t.z0; k < t.z1; ++k) {
         const int c[3] = {i, j, k};
@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_adj_h(const Dom<T>* __restri
                                                           const Tile* __restrict__ tiles, T S, int m) {
     const Tile t = tiles[blockIdx.x];
     const Dom<T>& d = doms[t.dom];
-    const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
-    if (i >= d.n[0] || j >= d.n[1]) return;
+    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    if (i < 0 || j < 0) return;
     for (int k = t.z0; k < t.z1; ++k) {
         const int c[3] = {i, j, k};
         const long long id = cidx(d.n, i, j, k);
@@ -257,8 +257,8 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_adj_e_int(const Dom<T>* __re
     const Tile t = tiles[blockIdx.x];
     const Dom<T>& d = doms[t.dom];
     const int nx = d.n[0], ny = d.n[1];
-    const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
-    if (i >= nx || j >= ny) return;
+    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    if (i < 0 || j < 0) return;
     const long long nxy = (long long)nx * ny;
     T* Fx = d.A[0];
     T* Fy = d.A[1];
@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_adj_h_int(const Dom<T>* __re
     const Tile t = tiles[blockIdx.x];
     const Dom<T>& d = doms[t.dom];
     const int nx = d.n[0], ny = d.n[1];
-    const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
-    if (i >= nx || j >= ny) return;
+    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    if (i < 0 || j < 0) return;
     const long long nxy = (long long)nx * ny;
     const T* Fx = d.A[0];
     const T* Fy = d.A[1];
@@ -362,8 +362,8 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_adj_flush(const Dom<T>* __re
                                                               const Tile* __restrict__ tiles, T S) {
     const Tile t = tiles[blockIdx.x];
     const Dom<T>& d = doms[t.dom];
-    const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
-    if (i >= d.n[0] || j >= d.n[1]) return;
+    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    if (i < 0 || j < 0) return;
     for (int k = t.z0; k < t.z1; ++k) {
         const int c[3] = {i, j, k};
         const long long id = cidx(d.n, i, j, k);

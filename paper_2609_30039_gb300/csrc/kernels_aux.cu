@@ -72,10 +72,11 @@ __global__ void k_bf16_encode(const T* __restrict__ src, long long plane, __nv_b
         if (threadIdx.x == 0) red[0] = m;
     }
     __syncthreads();
+    // divide (not multiply by 1/s): a slab whose max is an FP32 denormal has 1/s = inf, and
+    // 0 * inf would store NaN; x / s stays within [-1, 1]
     const float s = red[0];
-    const float inv = s > 0.f ? 1.f / s : 0.f;
     for (long long t = threadIdx.x; t < plane; t += blockDim.x)
-        dst[base + t] = __float2bfloat16_rn((float)src[base + t] * inv);
+        dst[base + t] = __float2bfloat16_rn(s > 0.f ? (float)src[base + t] / s : 0.f);
     if (threadIdx.x == 0) scales[blockIdx.x] = s;
 }
 

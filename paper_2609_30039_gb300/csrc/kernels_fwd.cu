@@ -2,9 +2,12 @@
 // memories of Sec. 2.2, the trapezoidal Drude/Lorentz update and diagonal eps^-1 of Sec. 2.3,
 // soft sources and running DFT monitors of Sec. 2.4.
 //
-// Work decomposition: a tile is 32 x 4 columns of one domain; each thread owns a column (i, j)
+// Work decomposition: a tile is 32 x 8 columns of one domain; each thread owns a column (i, j)
 // and marches k over the tile's z range, so consecutive planes of the same column stay in L1
-// and every warp reads 32 consecutive floats (128 B) of each array.
+// and every warp reads 32 consecutive floats (128 B) of each array.  Soft sources, the FP64
+// DFT accumulation and the device step counter are fused into the two field kernels (per-tile
+// flags mark the tiles that hold source or monitor cells), so a forward step is two kernels per
+// tile class and a CUDA graph of them replays without host work.
 #include "fdtd_internal.cuh"
 
 namespace gbfdtd {
@@ -63,17 +66,66 @@ __device__ __forceinline__ T ade_update(const Dom<T>& d, int a, long long bo, T 
     return e1;
 }
 
+// Soft source increments of component `comp` at a cell (Eq. (yee): added after the update).
+template <typename T>
+__device__ __forceinline__ T src_add(const Dom<T>& d, const Src* __restrict__ srcs, int comp, int i, int j, int k,
+                                     int step) {
+    T add = T(0);
+    for (int s = 0; s < d.nsrc; ++s) {
+        const Src& sr = srcs[d.src[s]];
+        if (sr.comp != comp || step >= sr.n) continue;
+        if (i < sr.lo[0] || i >= sr.hi[0] || j < sr.lo[1] || j >= sr.hi[1] || k < sr.lo[2] || k >= sr.hi[2]) continue;
+        add += (T)sr.wave[step];
+    }
+    return add;
+}
+
+// Running DFT (Sec. 2.4) of the three E (kind 0, t = n+1) or H (kind 1, t = n+3/2) components of
+// one cell: F += f exp(i w t), accumulated in FP64.
+template <typename T>
+__device__ __forceinline__ void dft_cell(const Dom<T>& d, const Mon* __restrict__ mons, int kind, int i, int j, int k,
+                                         int step, T v0, T v1, T v2) {
+    for (int mm = 0; mm < d.nmon; ++mm) {
+        const Mon& m = mons[d.mon[mm]];
+        if (i < m.lo[0] || i >= m.hi[0] || j < m.lo[1] || j >= m.hi[1] || k < m.lo[2] || k >= m.hi[2]) continue;
+        const long long cell = ((long long)(k - m.lo[2]) * m.by + (j - m.lo[1])) * m.bx + (i - m.lo[0]);
+        const double2* ph = m.phase + ((long long)step * 2 + kind) * m.nf;
+        int ci = 0;
+        for (int c = 0; c < 6; ++c) {
+            if (!((m.mask >> c) & 1u)) continue;
+            if (c / 3 == kind) {
+                const double v = (double)(c % 3 == 0 ? v0 : (c % 3 == 1 ? v1 : v2));
+                double2* acc = m.acc + (long long)ci * m.nf * m.ncell + cell;
+                for (int f = 0; f < m.nf; ++f) {
+                    const double2 p = ph[f];
+                    double2 a = acc[(long long)f * m.ncell];
+                    a.x += v * p.x;
+                    a.y += v * p.y;
+                    acc[(long long)f * m.ncell] = a;
+                }
+            }
+            ++ci;
+        }
+    }
+}
+
+template <typename T>
+constexpr int min_blocks(bool general) {
+    return general ? (sizeof(T) == 4 ? 4 : 2) : (sizeof(T) == 4 ? 5 : 3);
+}
+
 // E half-step (Eq. (yee) first half) of a tile.  kGen = false: the tile touches no CPML slab,
 // PEC plane, domain edge or dispersive cell, so none of that code is compiled in.  Every load of
 // a plane is issued before any store of it; H_x, H_y of plane k-1 stay in registers.
 template <typename T, bool kGen, bool kAniso>
-__global__ void __launch_bounds__(kTileX* kTileY) k_e_update(const Dom<T>* __restrict__ doms,
-                                                             const Tile* __restrict__ tiles, T S) {
-    const Tile t = tiles[blockIdx.x];
+__device__ __forceinline__ void tile_e(const Dom<T>* __restrict__ doms, const Tile& t, T S, const StepArgs& a,
+                                       int step) {
     const Dom<T>& d = doms[t.dom];
     const int nx = d.n[0], ny = d.n[1];
-    const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
-    if (i >= nx || j >= ny) return;
+    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    if (i < 0 || j < 0) return;
+    const bool fsrc = t.flags & kTileSrcE;
+    const bool fmon = a.dft_on && (t.flags & kTileMonE);
     const long long nxy = (long long)nx * ny;
     T* Ex = d.F[0];
     T* Ey = d.F[1];
@@ -144,29 +196,49 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_e_update(const Dom<T>* __res
                 if (!py) ey += S * iey * (yy1 - yy2);
                 if (!pz) ez += S * iez * (yz1 - yz2);
             }
-            if (!px) Ex[id] = ex;
-            if (!py) Ey[id] = ey;
-            if (!pz) Ez[id] = ez;
+            // a PEC-held component keeps its (zero) value and receives no source
         } else {
-            Ex[id] = ex + S * iex * (yx1 - yx2);
-            Ey[id] = ey + S * iey * (yy1 - yy2);
-            Ez[id] = ez + S * iez * (yz1 - yz2);
+            ex += S * iex * (yx1 - yx2);
+            ey += S * iey * (yy1 - yy2);
+            ez += S * iez * (yz1 - yz2);
         }
+        if (fsrc) {
+            ex += src_add(d, a.srcs, 0, i, j, k, step);
+            ey += src_add(d, a.srcs, 1, i, j, k, step);
+            ez += src_add(d, a.srcs, 2, i, j, k, step);
+        }
+        if (kGen) {
+            const bool pk = k == 0;
+            if (!(pj || pk)) Ex[id] = ex;
+            if (!(pi || pk)) Ey[id] = ey;
+            if (!(pi || pj)) Ez[id] = ez;
+        } else {
+            Ex[id] = ex;
+            Ey[id] = ey;
+            Ez[id] = ez;
+        }
+        if (fmon) dft_cell(d, a.mons, 0, i, j, k, step, ex, ey, ez);
     }
+}
+
+template <typename T, bool kGen, bool kAniso>
+__global__ void __launch_bounds__(kTileX* kTileY, min_blocks<T>(kGen))
+    k_e_update(const Dom<T>* __restrict__ doms, const Tile* __restrict__ tiles, T S, const StepArgs a) {
+    tile_e<T, kGen, kAniso>(doms, tiles[blockIdx.x], S, a, *a.d_step);
 }
 
 // H half-step (Eq. (yee) second half) of a tile; E_x, E_y of plane k+1 are carried to the next
 // plane in registers.  kEnergy adds W_{n+1} = 1/2 sum eps |E|^2 + 1/2 sum H^{n+1/2} H^{n+3/2}.
 template <typename T, bool kGen, bool kEnergy>
-__global__ void __launch_bounds__(kTileX* kTileY) k_h_update(const Dom<T>* __restrict__ doms,
-                                                             const Tile* __restrict__ tiles, T S,
-                                                             const int* __restrict__ d_step) {
-    const Tile t = tiles[blockIdx.x];
+__device__ __forceinline__ void tile_h(const Dom<T>* __restrict__ doms, const Tile& t, T S, const StepArgs& a,
+                                       int step) {
     const Dom<T>& d = doms[t.dom];
     const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
-    const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
+    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    const bool fsrc = t.flags & kTileSrcH;
+    const bool fmon = a.dft_on && (t.flags & kTileMonH);
     double w = 0.0;
-    if (i < nx && j < ny) {
+    if (i >= 0 && j >= 0) {
         const long long nxy = (long long)nx * ny;
         const T* Ex = d.F[0];
         const T* Ey = d.F[1];
@@ -215,12 +287,18 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_h_update(const Dom<T>* __res
                     yz2 = cpml_apply(cy, d.psiH[2][1] + o, yz2);
                 }
             }
-            const T hx1 = hx - S * (yx1 - yx2);
-            const T hy1 = hy - S * (yy1 - yy2);
-            const T hz1 = hz - S * (yz1 - yz2);
+            T hx1 = hx - S * (yx1 - yx2);
+            T hy1 = hy - S * (yy1 - yy2);
+            T hz1 = hz - S * (yz1 - yz2);
+            if (fsrc) {
+                hx1 += src_add(d, a.srcs, 3, i, j, k, step);
+                hy1 += src_add(d, a.srcs, 4, i, j, k, step);
+                hz1 += src_add(d, a.srcs, 5, i, j, k, step);
+            }
             Hx[id] = hx1;
             Hy[id] = hy1;
             Hz[id] = hz1;
+            if (fmon) dft_cell(d, a.mons, 1, i, j, k, step, hx1, hy1, hz1);
             if (kEnergy) {
                 w += 0.5 * ((double)hx * hx1 + (double)hy * hy1 + (double)hz * hz1);
                 w += 0.5 * ((double)exk * exk / (double)d.ie[0][id] + (double)eyk * eyk / (double)d.ie[1][id] +
@@ -232,109 +310,170 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_h_update(const Dom<T>* __res
     }
     if (kEnergy) {
         for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        const int step = *d_step;
         if ((threadIdx.x & 31) == 0 && d.energy && step < d.energy_cap) atomicAdd(d.energy + step, w);
     }
 }
 
-template <typename T>
-__global__ void k_sources(const Dom<T>* __restrict__ doms, const Src* __restrict__ srcs, int nsrc, long long ncells,
-                          const int* __restrict__ d_step) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= ncells) return;
-    int s = 0;
-    while (s + 1 < nsrc && srcs[s + 1].begin <= t) ++s;
-    const Src& sr = srcs[s];
-    const int step = *d_step;
-    if (step >= sr.n) return;
-    const long long l = t - sr.begin;
-    const int i = sr.lo[0] + (int)(l % sr.bx);
-    const int j = sr.lo[1] + (int)((l / sr.bx) % sr.by);
-    const int k = sr.lo[2] + (int)(l / ((long long)sr.bx * sr.by));
-    const Dom<T>& d = doms[sr.dom];
-    d.F[sr.comp][cidx(d.n, i, j, k)] += (T)sr.wave[step];
+template <typename T, bool kGen, bool kEnergy>
+__global__ void __launch_bounds__(kTileX* kTileY, min_blocks<T>(kGen))
+    k_h_update(const Dom<T>* __restrict__ doms, const Tile* __restrict__ tiles, T S, const StepArgs a, int advance) {
+    const int step = *a.d_step;
+    tile_h<T, kGen, kEnergy>(doms, tiles[blockIdx.x], S, a, step);
+    if (advance) {
+        // the last block to finish advances the device step counter (every block has read it)
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            __threadfence();
+            const unsigned done = atomicAdd(a.d_ticket, 1u);
+            if (done == gridDim.x - 1) {
+                *a.d_ticket = 0u;
+                *a.d_step = step + 1;
+                __threadfence();
+            }
+        }
+    }
 }
 
-// Running DFT (Sec. 2.4): F += f(t) exp(i w t), FP64 accumulation of the field value.
-template <typename T>
-__global__ void k_dft(const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, const int* __restrict__ entries,
-                      int nentries, long long nthreads, const long long* __restrict__ entry_begin,
-                      const int* __restrict__ d_step, int kind) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= nthreads) return;
-    int e = 0;
-    while (e + 1 < nentries && entry_begin[e + 1] <= t) ++e;
-    const int mi = entries[2 * e], ci = entries[2 * e + 1];
-    const Mon& m = mons[mi];
-    const long long cell = t - entry_begin[e];
-    const int i = m.lo[0] + (int)(cell % m.bx);
-    const int j = m.lo[1] + (int)((cell / m.bx) % m.by);
-    const int k = m.lo[2] + (int)(cell / ((long long)m.bx * m.by));
-    const Dom<T>& d = doms[m.dom];
-    const double v = (double)d.F[m.comps[ci]][cidx(d.n, i, j, k)];
-    const int step = *d_step;
-    const double2* ph = m.phase + ((long long)step * 2 + kind) * m.nf;
-    double2* acc = m.acc + (long long)ci * m.nf * m.ncell + cell;
-    for (int f = 0; f < m.nf; ++f) {
-        const double2 p = ph[f];
-        double2 a = acc[(long long)f * m.ncell];
-        a.x += v * p.x;
-        a.y += v * p.y;
-        acc[(long long)f * m.ncell] = a;
+// ---- persistent step kernel ---------------------------------------------------------------
+// One cooperative launch runs nsteps forward steps: in each half-step the blocks claim tiles from
+// a shared ticket (general tiles first, so the slower ones start early), then meet at a
+// grid-wide barrier.  The barrier wait is bounded; if it runs out the block records an error
+// and every block leaves the loop (a cooperative launch guarantees all blocks are resident, so
+// this only guards against a fault elsewhere).
+constexpr long long kBarrierSpinLimit = 1ll << 26;   // x ~64 ns sleep: a few seconds
+
+__device__ __forceinline__ bool grid_sync(GridSync* gs, unsigned nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        volatile unsigned* vgen = &gs->gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(&gs->arrive, 1u) == nblocks - 1) {
+            gs->arrive = 0u;
+            __threadfence();
+            atomicAdd(&gs->gen, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == g) {
+                if (++it > kBarrierSpinLimit) {
+                    atomicExch(&gs->err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = *((volatile int*)&gs->err) == 0;
     }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ int claim_tile(GridSync* gs, unsigned long long base) {
+    __shared__ int s_t;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_t = (int)(atomicAdd(&gs->ticket, 1ull) - base);
+    __syncthreads();
+    const int t = s_t;
+    __syncthreads();
+    return t;
+}
+
+template <typename T, bool kAniso, bool kEnergy>
+__global__ void __launch_bounds__(kTileX* kTileY, min_blocks<T>(true))
+    k_steps(const Dom<T>* __restrict__ doms, const Tile* __restrict__ tiles, int ntiles, T S, const StepArgs a,
+            int nsteps, GridSync* gs) {
+    const int step0 = *a.d_step;
+    const unsigned long long per_phase = (unsigned long long)ntiles + gridDim.x;
+    unsigned long long base = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        const int step = step0 + s;
+        for (;;) {
+            const int t = claim_tile(gs, base);
+            if (t >= ntiles) break;
+            const Tile tl = tiles[t];
+            if (tl.flags & kTileGeneral)
+                tile_e<T, true, true>(doms, tl, S, a, step);
+            else
+                tile_e<T, false, kAniso>(doms, tl, S, a, step);
+        }
+        base += per_phase;
+        if (!grid_sync(gs, gridDim.x)) return;
+        for (;;) {
+            const int t = claim_tile(gs, base);
+            if (t >= ntiles) break;
+            const Tile tl = tiles[t];
+            if (tl.flags & kTileGeneral)
+                tile_h<T, true, kEnergy>(doms, tl, S, a, step);
+            else
+                tile_h<T, false, kEnergy>(doms, tl, S, a, step);
+        }
+        base += per_phase;
+        if (!grid_sync(gs, gridDim.x)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *a.d_step = step0 + nsteps;
+}
+
+template <typename T>
+cudaError_t launch_steps(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
+                         int nsteps, int aniso, int energy, GridSync* gs, int* grid_used) {
+    void* fn;
+    if (aniso)
+        fn = energy ? (void*)k_steps<T, true, true> : (void*)k_steps<T, true, false>;
+    else
+        fn = energy ? (void*)k_steps<T, false, true> : (void*)k_steps<T, false, false>;
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kTileX * kTileY, 0);
+    if (e != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    int grid = sms * per;
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    e = cudaMemsetAsync(gs, 0, sizeof(GridSync), L.stream);
+    if (e != cudaSuccess) return e;
+    StepArgs aa = a;
+    void* args[] = {(void*)&doms, (void*)&tiles, (void*)&ntiles, (void*)&S, (void*)&aa, (void*)&nsteps, (void*)&gs};
+    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTileX, kTileY), args, 0, L.stream);
+    ++*L.counter;
+    if (grid_used) *grid_used = grid;
+    return e;
 }
 
 __global__ void k_advance(int* d_step, int delta) { *d_step += delta; }
 
 // ---- host launchers --------------------------------------------------------------------------
 template <typename T>
-void launch_e_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, int general, int aniso) {
+void launch_e_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
+                     int general, int aniso) {
     if (ntiles <= 0) return;
     const dim3 b(kTileX, kTileY);
     if (general)
-        k_e_update<T, true, true><<<ntiles, b, 0, L.stream>>>(doms, tiles, S);
+        k_e_update<T, true, true><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a);
     else if (aniso)
-        k_e_update<T, false, true><<<ntiles, b, 0, L.stream>>>(doms, tiles, S);
+        k_e_update<T, false, true><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a);
     else
-        k_e_update<T, false, false><<<ntiles, b, 0, L.stream>>>(doms, tiles, S);
+        k_e_update<T, false, false><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a);
     ++*L.counter;
 }
 
 template <typename T>
-void launch_h_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const int* d_step,
-                     int general, int energy) {
+void launch_h_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
+                     int general, int energy, int advance) {
     if (ntiles <= 0) return;
     const dim3 b(kTileX, kTileY);
     if (general) {
         if (energy)
-            k_h_update<T, true, true><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, d_step);
+            k_h_update<T, true, true><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a, advance);
         else
-            k_h_update<T, true, false><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, d_step);
+            k_h_update<T, true, false><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a, advance);
     } else {
         if (energy)
-            k_h_update<T, false, true><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, d_step);
+            k_h_update<T, false, true><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a, advance);
         else
-            k_h_update<T, false, false><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, d_step);
+            k_h_update<T, false, false><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a, advance);
     }
-    ++*L.counter;
-}
-
-template <typename T>
-void launch_sources(const Launch& L, const Dom<T>* doms, const Src* srcs, int nsrc, long long ncells,
-                    const int* d_step) {
-    if (nsrc <= 0 || ncells <= 0) return;
-    const int bs = 256;
-    k_sources<T><<<(unsigned)((ncells + bs - 1) / bs), bs, 0, L.stream>>>(doms, srcs, nsrc, ncells, d_step);
-    ++*L.counter;
-}
-
-template <typename T>
-void launch_dft(const Launch& L, const Dom<T>* doms, const Mon* mons, const int* entries, int nentries,
-                long long nthreads, const long long* entry_begin, const int* d_step, int kind) {
-    if (nentries <= 0 || nthreads <= 0) return;
-    const int bs = 256;
-    k_dft<T><<<(unsigned)((nthreads + bs - 1) / bs), bs, 0, L.stream>>>(doms, mons, entries, nentries, nthreads,
-                                                                        entry_begin, d_step, kind);
     ++*L.counter;
 }
 
@@ -344,13 +483,15 @@ void launch_advance(const Launch& L, int* d_step, int delta) {
 }
 
 #define GBFDTD_INST(T)                                                                                           \
-    template void launch_e_update<T>(const Launch&, const Dom<T>*, const Tile*, int, T, int, int);               \
-    template void launch_h_update<T>(const Launch&, const Dom<T>*, const Tile*, int, T, const int*, int, int);   \
-    template void launch_sources<T>(const Launch&, const Dom<T>*, const Src*, int, long long, const int*);       \
-    template void launch_dft<T>(const Launch&, const Dom<T>*, const Mon*, const int*, int, long long,            \
-                                const long long*, const int*, int);
+    template void launch_e_update<T>(const Launch&, const Dom<T>*, const Tile*, int, T, const StepArgs&, int, int); \
+    template void launch_h_update<T>(const Launch&, const Dom<T>*, const Tile*, int, T, const StepArgs&, int, int,  \
+                                     int);
 GBFDTD_INST(float)
 GBFDTD_INST(double)
 #undef GBFDTD_INST
+template cudaError_t launch_steps<float>(const Launch&, const Dom<float>*, const Tile*, int, float, const StepArgs&, int,
+                                         int, int, GridSync*, int*);
+template cudaError_t launch_steps<double>(const Launch&, const Dom<double>*, const Tile*, int, double,
+                                          const StepArgs&, int, int, int, GridSync*, int*);
 
 }  // namespace gbfdtd

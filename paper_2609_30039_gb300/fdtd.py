@@ -27,7 +27,7 @@ STATUS_NAMES = ["FDTD_OK", "FDTD_EINVAL", "FDTD_ECFL", "FDTD_ETENSOR", "FDTD_ENO
 FDTD_F32, FDTD_F64 = 0, 1
 FDTD_LORENTZ, FDTD_DRUDE = 0, 1
 FDTD_CODEC_NATIVE, FDTD_CODEC_BF16 = 0, 1
-KERNEL_CLASSES = ["e_update", "h_update", "source", "dft", "step", "adj_e", "adj_h"]
+KERNEL_CLASSES = ["e_update", "h_update", "source", "dft", "step", "adj_e", "adj_h", "persistent"]
 
 
 class fdtd_grid(C.Structure):
@@ -83,6 +83,7 @@ _SIGS = {
     "fdtd_energy_read": [_ctx, C.c_int32, C.POINTER(C.c_double), C.c_int32],
     "fdtd_step_forward": [_ctx, C.c_int32],
     "fdtd_step_count": [_ctx, _i64p],
+    "fdtd_set_launch_mode": [_ctx, C.c_int32],
     "fdtd_reset": [_ctx],
     "fdtd_part_count": [_ctx, C.c_int32, _i32p],
     "fdtd_part_size": [_ctx, C.c_int32, C.c_int32, _i64p],
@@ -180,6 +181,7 @@ fdtd_dft_reset = _wrap_simple("fdtd_dft_reset")
 fdtd_dft_enable = _wrap_simple("fdtd_dft_enable")
 fdtd_enable_energy = _wrap_simple("fdtd_enable_energy")
 fdtd_step_forward = _wrap_simple("fdtd_step_forward")
+fdtd_set_launch_mode = _wrap_simple("fdtd_set_launch_mode")
 fdtd_reset = _wrap_simple("fdtd_reset")
 fdtd_set_step_count = _wrap_simple("fdtd_set_step_count")
 fdtd_state_save = _wrap_simple("fdtd_state_save")

@@ -367,6 +367,24 @@ def test_snapshot_native_roundtrip_bitwise_and_bf16_bound():
         assert torch.all((got - ref).abs() <= s * 2.0 ** -8 + 1e-30)
 
 
+def test_bf16_snapshot_every_part_anisotropic_poles():
+    # CPML memories and pole states too: each restored value within 2^-8 of its slab's max |x|
+    sc = W.large_adjoint(n=48, d=4, n_steps=200, margin=2)
+    ctx = fdtd.Context([sc], dtype="f32")
+    ctx.step(150)
+    saved = [ctx.part(0, p).clone() for p in range(ctx.part_count(0))]
+    fdtd.fdtd_state_save(ctx.ctx, 3, fdtd.FDTD_CODEC_BF16)
+    ctx.step(7)
+    fdtd.fdtd_state_restore(ctx.ctx, 3)
+    for p in range(ctx.part_count(0)):
+        got, ref = ctx.part(0, p), saved[p]
+        if not ref.numel():
+            continue
+        assert torch.isfinite(got).all(), p
+        bound = ref.abs().max() * 2.0 ** -8 + 1e-30
+        assert (got - ref).abs().max() <= bound, (p, float((got - ref).abs().max()), float(bound))
+
+
 # ----------------------------------------------------------------------------- errors
 def _grid(nx=16, courant=W.COURANT, dtype=fdtd.FDTD_F32):
     return fdtd.fdtd_grid(nx, nx, nx, 1.0, courant, 0.0, dtype)
@@ -437,3 +455,43 @@ def test_nonfinite_detection_and_adjoint_state_rules():
         fdtd.fdtd_check_finite(ctx.ctx)
     assert e.value.status == fdtd.FDTD_ENONFINITE
     del runner
+
+
+@pytest.mark.parametrize("which", ["blocks", "batch"])
+def test_persistent_and_per_launch_paths_bitwise_equal(which):
+    scs = [small_blocks(40, 6, 150)] if which == "blocks" else _tiny_batch(3, 150)
+    outs = []
+    for mode in (0, 1):
+        ctx = fdtd.Context(scs, dtype="f32")
+        fdtd.fdtd_set_launch_mode(ctx.ctx, mode)
+        ctx.step(70)
+        ctx.step(80)   # two calls: the device step counter carries across launches
+        assert ctx.step_count == 150
+        outs.append(([ctx.part(d, p).clone() for d in range(len(scs)) for p in range(ctx.part_count(d))],
+                     [ctx.dft(k).clone() for k in range(len(ctx.monitors))]))
+        ctx.close()
+    for a, b in zip(outs[0][0], outs[1][0]):
+        assert torch.equal(a, b)
+    for a, b in zip(outs[0][1], outs[1][1]):
+        assert torch.equal(a, b)
+
+
+def test_bf16_snapshot_denormal_slab_stays_finite():
+    # a slab whose largest value is an FP32 denormal (the leading edge of a wave far from the
+    # source) must round-trip without NaN
+    sc = small_blocks(24, 4, 10)
+    ctx = fdtd.Context([sc], dtype="f32")
+    nx, ny, nz = sc.shape
+    ez = torch.zeros(nz, ny, nx, device="cuda")
+    ez[5, 3, 7] = 1e-40
+    ez[5, 3, 8] = -3e-41
+    ez[9, 2, 2] = 0.75
+    ctx.set_part(0, 2, ez.view(-1))
+    fdtd.fdtd_state_save(ctx.ctx, 0, fdtd.FDTD_CODEC_BF16)
+    ctx.set_part(0, 2, torch.zeros_like(ez).view(-1))
+    fdtd.fdtd_state_restore(ctx.ctx, 0)
+    got = ctx.part(0, 2).view(nz, ny, nx)
+    assert torch.isfinite(got).all()
+    assert abs(float(got[9, 2, 2]) - 0.75) <= 0.75 * 2.0 ** -8
+    assert float(got[5, 3, 7]) > 0 and float(got[5, 3, 8]) < 0
+    assert float(got.abs().sum()) - 0.75 < 1e-3

@@ -1,0 +1,113 @@
+"""The adjoint workloads at reduced size on the GPU.
+
+* The design workload (per-cell densities, eps = 1 + 11 sigmoid(8 (rho - 0.5)), |F_Ex|^2 on a
+  patch) at 64^3: the FP32 checkpointed adjoint gradient d J / d rho against FP64 central
+  differences at 20 seeded cells with h = 1e-3 (vector relative L2 and per-cell bound 1%).
+* The large anisotropic two-pole workload (diagonal eps blocks, Lorentz design layer, sum |F_Ey|
+  on a far plane) at 96^3: replay from exact snapshots is bitwise equal to storing every state;
+  the BF16-snapshot gradient stays close to it.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2609_30039_gb300 import adjoint as ADJ
+from paper_2609_30039_gb300 import build as B
+from paper_2609_30039_gb300 import fdtd
+from paper_2609_30039_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    fdtd.load()
+
+
+def _sq_loss(specs):
+    F = specs[0]
+    return float((F.abs() ** 2).sum()), [torch.view_as_real(2.0 * F).contiguous()]
+
+
+def _abs_loss(specs):
+    F = specs[0]
+    a = F.abs().clamp_min(1e-30)
+    return float(a.sum()), [torch.view_as_real(F / a).contiguous()]
+
+
+def test_design_gradient_fp32_adjoint_vs_fp64_central_differences():
+    sc = W.adjoint_design(n=64, d=8, n_steps=750)
+    (lx, ly, lz), (hx, hy, hz) = sc.design
+    ctx = fdtd.Context([sc], dtype="f32")
+    (J, _), grads, stats = ADJ.DesignAdjoint(ctx, slots=16).run(sc.n_steps, _sq_loss)
+    g = grads[0].view(3, hz - lz, hy - ly, hx - lx).cpu().numpy()
+    rho = sc.rho
+    sig = 1.0 / (1.0 + np.exp(-8.0 * (rho - 0.5)))
+    eps = 1.0 + 11.0 * sig
+    dJdrho = g.sum(axis=0) * (-(88.0 * sig * (1.0 - sig)) / eps ** 2)
+    fd_ctx = fdtd.Context([W.Scene(**{**sc.__dict__, "design": None})], dtype="f64")
+
+    def J_of(r):
+        inv = sc.inv_eps3()[0].copy()
+        inv[lz:hz, ly:hy, lx:hx] = 1.0 / W.density_to_eps(r)
+        t = torch.from_numpy(inv).to("cuda")
+        fd_ctx.set_inv_eps(0, [t, t, t])
+        fdtd.fdtd_reset(fd_ctx.ctx)
+        fdtd.fdtd_dft_reset(fd_ctx.ctx)
+        fd_ctx.step(sc.n_steps)
+        return float((fd_ctx.dft(0).abs() ** 2).sum())
+
+    rng = np.random.default_rng(2609030042)
+    cells = [np.unravel_index(int(k), rho.shape) for k in rng.choice(rho.size, size=20, replace=False)]
+    h = 1e-3
+    fd, ad = [], []
+    for c in cells:
+        rp, rm = rho.copy(), rho.copy()
+        rp[c] += h
+        rm[c] -= h
+        fd.append((J_of(rp) - J_of(rm)) / (2 * h))
+        ad.append(dJdrho[c])
+    fd, ad = np.array(fd), np.array(ad)
+    assert np.linalg.norm(ad - fd) <= 1e-2 * np.linalg.norm(fd), (ad, fd)
+    big = np.abs(fd) >= 1e-2 * np.abs(fd).max()
+    assert np.all(np.abs(ad[big] - fd[big]) <= 1e-2 * np.abs(fd[big]))
+    assert stats["adjoint_steps"] == sc.n_steps
+
+
+def test_large_workload_snapshots_exact_replay_and_bf16_bound():
+    sc = W.large_adjoint(n=96, d=4, n_steps=600, margin=2)
+    grads = {}
+    for name, slots, codec in (("store_all", 601, fdtd.FDTD_CODEC_NATIVE), ("fp32", 8, fdtd.FDTD_CODEC_NATIVE),
+                               ("bf16", 8, fdtd.FDTD_CODEC_BF16)):
+        ctx = fdtd.Context([sc], dtype="f32")
+        (J, _), g, _ = ADJ.DesignAdjoint(ctx, slots=slots, codec=codec).run(sc.n_steps, _abs_loss)
+        grads[name] = g[0].clone()
+        assert np.isfinite(J) and torch.isfinite(g[0]).all()
+        ctx.close()
+    assert torch.equal(grads["fp32"], grads["store_all"])
+    a, b = grads["fp32"], grads["bf16"]
+    err = float(torch.linalg.vector_norm(b - a) / torch.linalg.vector_norm(a))
+    assert err < 5e-2, err
+
+
+def test_large_workload_gradient_matches_oracle_fp64_small():
+    from oracle.oracle import gradient_replay
+    from tests.oracle_adapter import oracle_from_scene
+    sc = W.large_adjoint(n=40, d=3, n_steps=90, margin=1)
+    sc.sources[0].wave = W.gaussian_pulse(90, wavelength=8.0, periods=1.0, delay=3.0)
+    sc.monitors[0].omegas = W.omegas_for((7.0, 9.0))
+    o = oracle_from_scene(sc)
+
+    def obj(orc):
+        F = orc.dft(0)
+        a = np.maximum(np.abs(F), 1e-30)
+        return float(a.sum()), {0: F / a}
+
+    J_ref = gradient_replay(o, sc.n_steps, obj)
+    g_ref = np.stack([o.grad(a) for a in range(3)])
+    ctx = fdtd.Context([sc], dtype="f64")
+    (J, _), grads, _ = ADJ.DesignAdjoint(ctx, slots=10).run(sc.n_steps, _abs_loss)
+    g = grads[0].cpu().numpy().reshape(g_ref.shape)
+    assert abs(J - J_ref) <= 1e-12 * abs(J_ref)
+    assert np.linalg.norm(g - g_ref) <= 1e-10 * np.linalg.norm(g_ref)
