@@ -171,8 +171,16 @@ fdtd_status fdtd_energy_read(fdtd_ctx* ctx, int32_t domain, double* host_dst, in
 fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps);
 
 /* mode 0: per-half-step launches (replayed as CUDA graphs); mode 1 (default): persistent
- * cooperative launches.  Both compute the same values bitwise. */
+ * cooperative launches (4 blocks per SM); mode 2: persistent launches whose interior tiles load
+ * the next z-plane ahead (3 blocks per SM).  All modes compute the same values bitwise. */
 fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode);
+fdtd_status fdtd_get_launch_mode(fdtd_ctx* ctx, int32_t* mode);
+
+/* Autotuner: times each launch mode for n_steps forward steps on the current state and keeps
+ * the fastest.  The state, step count and DFT accumulators are left as they were (the state is
+ * snapshotted and restored; DFT accumulation is off while tuning).  ms_per_mode (3 entries,
+ * may be NULL) receives the measured milliseconds.  Synchronises the stream. */
+fdtd_status fdtd_autotune(fdtd_ctx* ctx, int32_t n_steps, double* ms_per_mode);
 
 /* Number of forward steps the held state has taken (u^n: returns n). */
 fdtd_status fdtd_step_count(fdtd_ctx* ctx, int64_t* n);

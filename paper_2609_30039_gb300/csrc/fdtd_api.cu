@@ -93,6 +93,7 @@ struct fdtd_ctx {
     GridSync* d_sync = nullptr;     // barrier / ticket of the persistent step kernel
     Tile* d_tiles_lpt = nullptr;    // general tiles first, then interior (persistent kernel)
     int use_persistent = 1;
+    int persist_prefetch = 0;
     int persist_grid = 0;
     int h_step_tmp = 0;
     long long step = 0;
@@ -1204,10 +1205,12 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
                 Prof p(ctx, FDTD_KERNEL_PERSISTENT);
                 if (ctx->dtype == FDTD_F32)
                     e = launch_steps<float>(l, (const Dom<float>*)ctx->d_doms, ctx->d_tiles_lpt, nt, (float)ctx->S, a,
-                                            chunk, ctx->aniso, ctx->energy_on, ctx->d_sync, &ctx->persist_grid);
+                                            chunk, ctx->aniso, ctx->energy_on, ctx->persist_prefetch, ctx->d_sync,
+                                            &ctx->persist_grid);
                 else
                     e = launch_steps<double>(l, (const Dom<double>*)ctx->d_doms, ctx->d_tiles_lpt, nt, ctx->S, a, chunk,
-                                             ctx->aniso, ctx->energy_on, ctx->d_sync, &ctx->persist_grid);
+                                             ctx->aniso, ctx->energy_on, ctx->persist_prefetch, ctx->d_sync,
+                                             &ctx->persist_grid);
             }
             if (e != cudaSuccess) return fail(ctx, FDTD_ECUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
             left -= chunk;
@@ -1236,9 +1239,77 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
 
 fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode) {
     GUARD(ctx);
-    if (mode != 0 && mode != 1) return fail(ctx, FDTD_EINVAL, "launch mode must be 0 or 1");
-    ctx->use_persistent = mode;
+    if (mode < 0 || mode > 2) return fail(ctx, FDTD_EINVAL, "launch mode must be 0, 1 or 2");
+    ctx->use_persistent = mode >= 1;
+    ctx->persist_prefetch = mode == 2;
     return FDTD_OK;
+}
+
+fdtd_status fdtd_get_launch_mode(fdtd_ctx* ctx, int32_t* mode) {
+    GUARD(ctx);
+    if (!mode) return FDTD_EINVAL;
+    *mode = ctx->use_persistent ? (ctx->persist_prefetch ? 2 : 1) : 0;
+    return FDTD_OK;
+}
+
+// Times every launch mode for n_steps on the live state (saved to a private snapshot first and
+// restored after each trial, DFT accumulation off) and keeps the fastest.
+static fdtd_status save_slot(fdtd_ctx* ctx, int32_t slot, int32_t codec);
+static fdtd_status restore_slot(fdtd_ctx* ctx, int32_t slot);
+
+fdtd_status fdtd_autotune(fdtd_ctx* ctx, int32_t n_steps, double* ms_per_mode) {
+    GUARD(ctx);
+    if (n_steps < 1) return fail(ctx, FDTD_EINVAL, "n_steps must be >= 1");
+    const int slot = 1 << 30;   // private slot id (public ids are below 2^30)
+    const int dft = ctx->dft_enabled, energy = ctx->energy_on;
+    const long long step0 = ctx->step;
+    ctx->dft_enabled = 0;
+    ctx->energy_on = 0;
+    fdtd_status st = FDTD_OK;
+    double best = 1e30;
+    int best_mode = 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        st = fail(ctx, FDTD_ECUDA, "cudaEventCreate failed");
+    if (st == FDTD_OK) st = save_slot(ctx, slot, FDTD_CODEC_NATIVE);
+    for (int mode = 0; mode < 3 && st == FDTD_OK; ++mode) {
+        fdtd_set_launch_mode(ctx, mode);
+        // warm-up: graph capture, first-touch of the persistent kernel, caches
+        st = fdtd_step_forward(ctx, n_steps < kGraphSteps ? n_steps : kGraphSteps);
+        if (st == FDTD_OK) st = restore_slot(ctx, slot);
+        if (st != FDTD_OK) break;
+        cudaEventRecord(e0, ctx->stream);
+        st = fdtd_step_forward(ctx, n_steps);
+        cudaEventRecord(e1, ctx->stream);
+        if (st != FDTD_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = fail(ctx, FDTD_ECUDA, "autotune event synchronisation failed");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms_per_mode) ms_per_mode[mode] = ms;
+        if (ms < best) {
+            best = ms;
+            best_mode = mode;
+        }
+        st = restore_slot(ctx, slot);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(ctx->stream);
+    auto it = ctx->slots.find(slot);
+    if (it != ctx->slots.end()) {
+        cudaFree(it->second.buf);
+        ctx->slots.erase(it);
+    }
+    ctx->dft_enabled = dft;
+    ctx->energy_on = energy;
+    ctx->step = step0;
+    if (st != FDTD_OK) return st;
+    st = set_device_step(ctx, step0);
+    if (st != FDTD_OK) return st;
+    return fdtd_set_launch_mode(ctx, best_mode);
 }
 
 fdtd_status fdtd_step_count(fdtd_ctx* ctx, int64_t* n) {
@@ -1332,10 +1403,7 @@ fdtd_status fdtd_snapshot_bytes(fdtd_ctx* ctx, int32_t codec, int64_t* bytes) {
     return FDTD_OK;
 }
 
-fdtd_status fdtd_state_save(fdtd_ctx* ctx, int32_t slot, int32_t codec) {
-    GUARD(ctx);
-    if (slot < 0 || (codec != FDTD_CODEC_NATIVE && codec != FDTD_CODEC_BF16))
-        return fail(ctx, FDTD_EINVAL, "bad slot or codec");
+static fdtd_status save_slot(fdtd_ctx* ctx, int32_t slot, int32_t codec) {
     const size_t need = snapshot_bytes(ctx, codec);
     Slot& s = ctx->slots[slot];
     if (s.bytes < need) {
@@ -1383,8 +1451,7 @@ fdtd_status fdtd_state_save(fdtd_ctx* ctx, int32_t slot, int32_t codec) {
     return FDTD_OK;
 }
 
-fdtd_status fdtd_state_restore(fdtd_ctx* ctx, int32_t slot) {
-    GUARD(ctx);
+static fdtd_status restore_slot(fdtd_ctx* ctx, int32_t slot) {
     auto it = ctx->slots.find(slot);
     if (it == ctx->slots.end() || !it->second.buf) return fail(ctx, FDTD_ESTATE, "empty snapshot slot");
     const Slot& s = it->second;
@@ -1414,6 +1481,19 @@ fdtd_status fdtd_state_restore(fdtd_ctx* ctx, int32_t slot) {
         }
     ctx->step = s.step;
     return set_device_step(ctx, s.step);
+}
+
+fdtd_status fdtd_state_save(fdtd_ctx* ctx, int32_t slot, int32_t codec) {
+    GUARD(ctx);
+    if (slot < 0 || slot >= (1 << 30) || (codec != FDTD_CODEC_NATIVE && codec != FDTD_CODEC_BF16))
+        return fail(ctx, FDTD_EINVAL, "bad slot or codec");
+    return save_slot(ctx, slot, codec);
+}
+
+fdtd_status fdtd_state_restore(fdtd_ctx* ctx, int32_t slot) {
+    GUARD(ctx);
+    if (slot < 0 || slot >= (1 << 30)) return fail(ctx, FDTD_EINVAL, "bad slot");
+    return restore_slot(ctx, slot);
 }
 
 fdtd_status fdtd_snapshots_free(fdtd_ctx* ctx) {

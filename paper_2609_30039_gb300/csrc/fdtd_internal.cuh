@@ -174,7 +174,7 @@ void launch_advance(const Launch& L, int* d_step, int delta);
 // Persistent cooperative launch advancing nsteps forward steps over all tiles (general first).
 template <typename T>
 cudaError_t launch_steps(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
-                         int nsteps, int aniso, int energy, GridSync* gs, int* grid_used);
+                         int nsteps, int aniso, int energy, int prefetch, GridSync* gs, int* grid_used);
 
 // Adjoint kernels (kernels_adj.cu)
 template <typename T>

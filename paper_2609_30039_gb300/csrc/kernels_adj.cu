@@ -243,6 +243,304 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_adj_h(const Dom<T>* __restri
     }
 }
 
+// ---- general tiles, hoisted form -------------------------------------------------------------
+// Column constants (CPML coefficients along x and y at this column and its -1 / +1 neighbour)
+// are computed once per thread; along z once per plane.  Per plane every load precedes every
+// store.  The cotangent terms of the z-derivatives are carried from plane to plane.
+
+template <typename T>
+struct CpmlC {   // coefficients of one node: slab index (-1 outside), b, c, 1/kappa
+    int s;
+    T b, c, k;
+};
+
+template <typename T>
+__device__ __forceinline__ CpmlC<T> cpml_c(const Dom<T>& d, const T* coef, int q, int x) {
+    CpmlC<T> r;
+    r.s = (d.ns[q] && x >= 0 && x < d.n[q]) ? slab_of(x, d.dlo[q], d.dhi[q], d.n[q]) : -1;
+    r.b = T(1);
+    r.c = T(0);
+    r.k = T(1);
+    if (r.s >= 0) {
+        const int N = d.n[q];
+        r.b = coef[x];
+        r.c = coef[N + x];
+        r.k = coef[2 * N + x];
+    }
+    return r;
+}
+
+// Dbar of a derivative whose ybar is yb, at a node with coefficients cc and memory cotangent ps.
+template <typename T>
+__device__ __forceinline__ T dbar_c(const CpmlC<T>& cc, T yb, T ps) {
+    return cc.s >= 0 ? cc.k * yb + cc.c * (ps + yb) : yb;
+}
+
+// Offsets of a cell inside the slab arrays of each axis.
+template <typename T>
+__device__ __forceinline__ long long off_x(const Dom<T>& d, int s, int j, int k) {
+    return ((long long)k * d.n[1] + j) * d.ns[0] + s;
+}
+template <typename T>
+__device__ __forceinline__ long long off_y(const Dom<T>& d, int s, int i, int k) {
+    return ((long long)k * d.ns[1] + s) * d.n[0] + i;
+}
+template <typename T>
+__device__ __forceinline__ long long off_z(const Dom<T>& d, int s, int i, int j) {
+    return ((long long)s * d.n[1] + j) * d.n[0] + i;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
+    k_adj_e_gen(const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, const Tile* __restrict__ tiles, T S,
+                int m, int pending) {
+    const Tile t = tiles[blockIdx.x];
+    const Dom<T>& d = doms[t.dom];
+    const int nx = d.n[0], ny = d.n[1];
+    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    if (i < 0 || j < 0) return;
+    const long long nxy = (long long)nx * ny;
+    T* A0 = d.A[0];
+    T* A1 = d.A[1];
+    T* A2 = d.A[2];
+    const T* B0 = d.A[3];
+    const T* B1 = d.A[4];
+    const T* B2 = d.A[5];
+    // E-node coefficients (deferred psibar_E), H-node coefficients at this column and the -1 one
+    const CpmlC<T> xE = cpml_c(d, d.cE[0], 0, i), yE = cpml_c(d, d.cE[1], 1, j);
+    const CpmlC<T> xH = cpml_c(d, d.cH[0], 0, i), xHm = cpml_c(d, d.cH[0], 0, i - 1);
+    const CpmlC<T> yH = cpml_c(d, d.cH[1], 1, j), yHm = cpml_c(d, d.cH[1], 1, j - 1);
+    const bool pi = i == 0, pj = j == 0;
+    const bool gcol = d.design && i >= d.glo[0] && i < d.ghi[0] && j >= d.glo[1] && j < d.ghi[1];
+    const bool mon = d.nmon && (t.flags & kTileMonE);
+    long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
+    // z-derivative terms of H_y (s = 0) and H_x (s = 1) at plane k-1
+    T tyz_m = T(0), txz_m = T(0);
+    if (t.z0 > 0) {
+        const CpmlC<T> zH = cpml_c(d, d.cH[2], 2, t.z0 - 1);
+        const long long o = zH.s >= 0 ? off_z(d, zH.s, i, j) : 0;
+        tyz_m = dbar_c(zH, -S * B1[id - nxy], zH.s >= 0 ? d.apsiH[1][0][o] : T(0));
+        txz_m = dbar_c(zH, S * B0[id - nxy], zH.s >= 0 ? d.apsiH[0][1][o] : T(0));
+    }
+    for (int k = t.z0; k < t.z1; ++k, id += nxy) {
+        const bool pk = k == 0;
+        const bool px = pj || pk, py = pi || pk, pz = pi || pj;
+        const CpmlC<T> zE = cpml_c(d, d.cE[2], 2, k), zH = cpml_c(d, d.cH[2], 2, k);
+        // loads of the plane
+        const T f0 = A0[id], f1 = A1[id], f2 = A2[id];
+        const T b0 = B0[id], b1 = B1[id], b2 = B2[id];
+        const T b2_xm = pi ? T(0) : B2[id - 1], b1_xm = pi ? T(0) : B1[id - 1];
+        const T b2_ym = pj ? T(0) : B2[id - nx], b0_ym = pj ? T(0) : B0[id - nx];
+        const long long oz = zH.s >= 0 ? off_z(d, zH.s, i, j) : 0;
+        const T p10 = zH.s >= 0 ? d.apsiH[1][0][oz] : T(0);   // H_y, d/dz
+        const T p01 = zH.s >= 0 ? d.apsiH[0][1][oz] : T(0);   // H_x, d/dz
+        const T p20 = xH.s >= 0 ? d.apsiH[2][0][off_x(d, xH.s, j, k)] : T(0);                 // H_z, d/dx
+        const T p20m = (!pi && xHm.s >= 0) ? d.apsiH[2][0][off_x(d, xHm.s, j, k)] : T(0);
+        const T p11 = xH.s >= 0 ? d.apsiH[1][1][off_x(d, xH.s, j, k)] : T(0);                 // H_y, d/dx
+        const T p11m = (!pi && xHm.s >= 0) ? d.apsiH[1][1][off_x(d, xHm.s, j, k)] : T(0);
+        const T p21 = yH.s >= 0 ? d.apsiH[2][1][off_y(d, yH.s, i, k)] : T(0);                 // H_z, d/dy
+        const T p21m = (!pj && yHm.s >= 0) ? d.apsiH[2][1][off_y(d, yHm.s, i, k)] : T(0);
+        const T p00 = yH.s >= 0 ? d.apsiH[0][0][off_y(d, yH.s, i, k)] : T(0);                 // H_x, d/dy
+        const T p00m = (!pj && yHm.s >= 0) ? d.apsiH[0][0][off_y(d, yHm.s, i, k)] : T(0);
+        // derivative cotangents of the H update: s = 0 has ybar = -S Hbar, s = 1 has +S Hbar
+        const T tyz = dbar_c(zH, -S * b1, p10), txz = dbar_c(zH, S * b0, p01);
+        const T tzx = dbar_c(xH, -S * b2, p20), tzx_m = pi ? T(0) : dbar_c(xHm, -S * b2_xm, p20m);
+        const T tyx = dbar_c(xH, S * b1, p11), tyx_m = pi ? T(0) : dbar_c(xHm, S * b1_xm, p11m);
+        const T tzy = dbar_c(yH, S * b2, p21), tzy_m = pj ? T(0) : dbar_c(yHm, S * b2_ym, p21m);
+        const T txy = dbar_c(yH, -S * b0, p00), txy_m = pj ? T(0) : dbar_c(yHm, -S * b0_ym, p00m);
+        const bool dcell = d.npole > 0 && i >= d.blo[0] && i < d.bhi[0] && j >= d.blo[1] && j < d.bhi[1] &&
+                           k >= d.blo[2] && k < d.bhi[2] && d.mask[id];
+        const bool gcell = gcol && k >= d.glo[2] && k < d.ghi[2];
+        const T fin[3] = {f0, f1, f2};
+        const T gat[3] = {(tyz_m - tyz) + (tzy_m - tzy), (tzx_m - tzx) + (txz_m - txz), (txy_m - txy) + (tyx_m - tyx)};
+        const bool pec[3] = {px, py, pz};
+        // own-cell CPML nodes of E_a's two derivatives (s = 0 along (a+1)%3, s = 1 along (a+2)%3)
+        const CpmlC<T>* ec[3][2] = {{&yE, &zE}, {&zE, &xE}, {&xE, &yE}};
+        T fout[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (pec[a]) {
+                fout[a] = T(0);
+                continue;
+            }
+            const T ie = d.ie[a][id];
+            const T F = fin[a];
+            T eb;
+            if (pending) {
+                // complete the own-cell transpose of step m+1
+                if (dcell) {
+                    eb = (T(1) / ie - d.G) / S * F;
+                    const long long bo = ade_off(d, i, j, k);
+                    for (int p = 0; p < d.npole; ++p) {
+                        T* pp = d.aade + ((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo;
+                        T* pq = d.aade + ((long long)(a * d.npole + p) * 2 + 1) * d.bcell + bo;
+                        const T xp = *pp, xq = *pq;
+                        eb += d.g0[p] * xp + d.g1[p] * xq;
+                        *pp = d.M00[p] * xp + d.M10[p] * xq + (T(1) - d.M00[p]) / S * F;
+                        *pq = d.M01[p] * xp + d.M11[p] * xq - d.M01[p] / S * F;
+                    }
+                } else {
+                    eb = F / (S * ie);
+                }
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    const CpmlC<T>& cc = *ec[a][s2];
+                    if (cc.s < 0) continue;
+                    const int ax = (a + 1 + s2) % 3;
+                    const long long o = ax == 0 ? off_x(d, cc.s, j, k) : (ax == 1 ? off_y(d, cc.s, i, k) : off_z(d, cc.s, i, j));
+                    T* pp = d.apsiE[a][s2] + o;
+                    *pp = cc.b * (*pp + (s2 == 0 ? F : -F));
+                }
+            } else {
+                eb = F;
+            }
+            eb += gat[a];
+            if (mon) eb += (T)inject_at(d, mons, a, i, j, k, (long long)m * 2 + 0);
+            T et = eb;
+            T gdisp = T(0);
+            if (dcell) {
+                const long long bo = ade_off(d, i, j, k);
+                for (int p = 0; p < d.npole; ++p) {
+                    const T xp = d.aade[((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo];
+                    const T xq = d.aade[((long long)(a * d.npole + p) * 2 + 1) * d.bcell + bo];
+                    et += d.g0[p] * xp + d.g1[p] * xq;
+                }
+                gdisp = d.G;
+            }
+            if (gcell) {
+                const int b = (a + 1) % 3, q = (a + 2) % 3;
+                const long long st[3] = {1, (long long)nx, nxy};
+                const T* Hq = d.F[3 + q];
+                const T* Hb = d.F[3 + b];
+                const T curl = (Hq[id] - Hq[id - st[b]]) - (Hb[id] - Hb[id - st[q]]);
+                double delta = (double)(S * curl);
+                if (dcell) {
+                    const long long bo = ade_off(d, i, j, k);
+                    const T e0 = d.F[a][id];
+                    for (int p = 0; p < d.npole; ++p) {
+                        const T P = d.ade[((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo];
+                        const T Q = d.ade[((long long)(a * d.npole + p) * 2 + 1) * d.bcell + bo];
+                        delta += (double)(P - (d.M00[p] * P + d.M01[p] * Q) - T(2) * d.g0[p] * e0);
+                    }
+                }
+                const double r = 1.0 / (1.0 + (double)ie * (double)gdisp);
+                const long long gi = ((long long)(k - d.glo[2]) * (d.ghi[1] - d.glo[1]) + (j - d.glo[1])) *
+                                         (d.ghi[0] - d.glo[0]) + (i - d.glo[0]);
+                const long long gn = (long long)(d.ghi[0] - d.glo[0]) * (d.ghi[1] - d.glo[1]) * (d.ghi[2] - d.glo[2]);
+                d.grad[a * gn + gi] += (double)et * delta * r * r;
+            }
+            fout[a] = S * ie / (T(1) + ie * gdisp) * et;
+        }
+        A0[id] = fout[0];
+        A1[id] = fout[1];
+        A2[id] = fout[2];
+        tyz_m = tyz;
+        txz_m = txz;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
+    k_adj_h_gen(const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, const Tile* __restrict__ tiles, T S,
+                int m) {
+    const Tile t = tiles[blockIdx.x];
+    const Dom<T>& d = doms[t.dom];
+    const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
+    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    if (i < 0 || j < 0) return;
+    const long long nxy = (long long)nx * ny;
+    const T* A0 = d.A[0];
+    const T* A1 = d.A[1];
+    const T* A2 = d.A[2];
+    T* B0 = d.A[3];
+    T* B1 = d.A[4];
+    T* B2 = d.A[5];
+    const bool xe = i + 1 < nx, ye = j + 1 < ny;
+    // H-node coefficients (own psibar_H); E-node coefficients at this column and the +1 one
+    const CpmlC<T> xH = cpml_c(d, d.cH[0], 0, i), yH = cpml_c(d, d.cH[1], 1, j);
+    const CpmlC<T> xE = cpml_c(d, d.cE[0], 0, i), xEp = cpml_c(d, d.cE[0], 0, i + 1);
+    const CpmlC<T> yE = cpml_c(d, d.cE[1], 1, j), yEp = cpml_c(d, d.cE[1], 1, j + 1);
+    const bool mon = d.nmon && m >= 1 && (t.flags & kTileMonH);
+    long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
+    // z-derivative terms of E_y (s = 0) and E_x (s = 1) at plane k (carried to the next plane)
+    auto zterms = [&](int k, long long idk, T& ty, T& tx) {
+        if (k >= nz) {
+            ty = T(0);
+            tx = T(0);
+            return;
+        }
+        const CpmlC<T> zE = cpml_c(d, d.cE[2], 2, k);
+        const long long o = zE.s >= 0 ? off_z(d, zE.s, i, j) : 0;
+        // E_y is PEC-held where i == 0 or k == 0; E_x where j == 0 or k == 0
+        ty = (i == 0 || k == 0) ? T(0) : dbar_c(zE, A1[idk], zE.s >= 0 ? d.apsiE[1][0][o] : T(0));
+        tx = (j == 0 || k == 0) ? T(0) : dbar_c(zE, -A0[idk], zE.s >= 0 ? d.apsiE[0][1][o] : T(0));
+    };
+    T tyz_k, txz_k;
+    zterms(t.z0, id, tyz_k, txz_k);
+    for (int k = t.z0; k < t.z1; ++k, id += nxy) {
+        T tyz_n, txz_n;
+        zterms(k + 1, id + nxy, tyz_n, txz_n);
+        const bool pk = k == 0;
+        const CpmlC<T> zH = cpml_c(d, d.cH[2], 2, k);
+        const T b0 = B0[id], b1 = B1[id], b2 = B2[id];
+        const T f0 = A0[id], f1 = A1[id], f2 = A2[id];
+        const T f2_xp = xe ? A2[id + 1] : T(0), f1_xp = xe ? A1[id + 1] : T(0);
+        const T f2_yp = ye ? A2[id + nx] : T(0), f0_yp = ye ? A0[id + nx] : T(0);
+        // E-derivative cotangents: E_e's s = 0 has ybar = +F, s = 1 has ybar = -F; PEC nodes give 0
+        // H_x gathers E_y s=0 (z) and E_z s=1 (y); H_y gathers E_z s=0 (x) and E_x s=1 (z);
+        // H_z gathers E_x s=0 (y) and E_y s=1 (x)
+        const T tzy = (i == 0 || j == 0) ? T(0)
+                                         : dbar_c(yE, -f2, yE.s >= 0 ? d.apsiE[2][1][off_y(d, yE.s, i, k)] : T(0));
+        const T tzy_p = (!ye || i == 0) ? T(0)
+                                        : dbar_c(yEp, -f2_yp, yEp.s >= 0 ? d.apsiE[2][1][off_y(d, yEp.s, i, k)] : T(0));
+        const T tzx = (i == 0 || j == 0) ? T(0)
+                                         : dbar_c(xE, f2, xE.s >= 0 ? d.apsiE[2][0][off_x(d, xE.s, j, k)] : T(0));
+        const T tzx_p = (!xe || j == 0) ? T(0)
+                                        : dbar_c(xEp, f2_xp, xEp.s >= 0 ? d.apsiE[2][0][off_x(d, xEp.s, j, k)] : T(0));
+        const T txy = (pk || j == 0) ? T(0)
+                                     : dbar_c(yE, f0, yE.s >= 0 ? d.apsiE[0][0][off_y(d, yE.s, i, k)] : T(0));
+        const T txy_p = (!ye || pk) ? T(0)
+                                    : dbar_c(yEp, f0_yp, yEp.s >= 0 ? d.apsiE[0][0][off_y(d, yEp.s, i, k)] : T(0));
+        const T tyx = (pk || i == 0) ? T(0)
+                                     : dbar_c(xE, -f1, xE.s >= 0 ? d.apsiE[1][1][off_x(d, xE.s, j, k)] : T(0));
+        const T tyx_p = (!xe || pk) ? T(0)
+                                    : dbar_c(xEp, -f1_xp, xEp.s >= 0 ? d.apsiE[1][1][off_x(d, xEp.s, j, k)] : T(0));
+        (void)f1;
+        T h0 = b0 + (tyz_k - tyz_n) + (tzy - tzy_p);
+        T h1 = b1 + (tzx - tzx_p) + (txz_k - txz_n);
+        T h2 = b2 + (txy - txy_p) + (tyx - tyx_p);
+        // finish the H-side CPML transpose of step m (k_adj_e(m) has read psibar_H)
+        if (yH.s >= 0) {
+            T* p = d.apsiH[0][0] + off_y(d, yH.s, i, k);
+            *p = yH.b * (*p - S * b0);
+            T* q = d.apsiH[2][1] + off_y(d, yH.s, i, k);
+            *q = yH.b * (*q + S * b2);
+        }
+        if (zH.s >= 0) {
+            T* p = d.apsiH[0][1] + off_z(d, zH.s, i, j);
+            *p = zH.b * (*p + S * b0);
+            T* q = d.apsiH[1][0] + off_z(d, zH.s, i, j);
+            *q = zH.b * (*q - S * b1);
+        }
+        if (xH.s >= 0) {
+            T* p = d.apsiH[1][1] + off_x(d, xH.s, j, k);
+            *p = xH.b * (*p + S * b1);
+            T* q = d.apsiH[2][0] + off_x(d, xH.s, j, k);
+            *q = xH.b * (*q - S * b2);
+        }
+        if (mon) {
+            h0 += (T)inject_at(d, mons, 3, i, j, k, (long long)(m - 1) * 2 + 1);
+            h1 += (T)inject_at(d, mons, 4, i, j, k, (long long)(m - 1) * 2 + 1);
+            h2 += (T)inject_at(d, mons, 5, i, j, k, (long long)(m - 1) * 2 + 1);
+        }
+        B0[id] = h0;
+        B1[id] = h1;
+        B2[id] = h2;
+        tyz_k = tyz_n;
+        txz_k = txz_n;
+    }
+}
+
 // Interior fast paths of the two transposed kernels: tiles that touch no CPML slab, PEC plane,
 // domain edge or pole cell.  Without CPML the derivative cotangents reduce to -S Hbar / +S Hbar
 // and +F / -F, so k_adj_e_int is the forward E update with Ebar -= S C^- Hbar and
@@ -409,7 +707,7 @@ void launch_adj_e(const Launch& L, const Dom<T>* doms, const Mon* mons, const Ti
     if (ntiles <= 0) return;
     const dim3 b(kTileX, kTileY);
     if (general)
-        k_adj_e<T><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m, pending);
+        k_adj_e_gen<T><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m, pending);
     else if (aniso)
         k_adj_e_int<T, true><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m, pending);
     else
@@ -423,7 +721,7 @@ void launch_adj_h(const Launch& L, const Dom<T>* doms, const Mon* mons, const Ti
     if (ntiles <= 0) return;
     const dim3 b(kTileX, kTileY);
     if (general)
-        k_adj_h<T><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m);
+        k_adj_h_gen<T><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m);
     else
         k_adj_h_int<T><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m);
     ++*L.counter;

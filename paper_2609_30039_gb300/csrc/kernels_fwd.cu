@@ -111,12 +111,160 @@ __device__ __forceinline__ void dft_cell(const Dom<T>& d, const Mon* __restrict_
 
 template <typename T>
 constexpr int min_blocks(bool general) {
-    return general ? (sizeof(T) == 4 ? 4 : 2) : (sizeof(T) == 4 ? 5 : 3);
+    return general ? (sizeof(T) == 4 ? 4 : 2) : (sizeof(T) == 4 ? 4 : 3);
+}
+
+// the persistent kernel holds both code paths; the prefetch variant needs more registers
+template <typename T, bool kPrefetch>
+constexpr int min_blocks_persistent() {
+    return sizeof(T) == 4 ? (kPrefetch ? 3 : 4) : 2;
 }
 
 // E half-step (Eq. (yee) first half) of a tile.  kGen = false: the tile touches no CPML slab,
 // PEC plane, domain edge or dispersive cell, so none of that code is compiled in.  Every load of
 // a plane is issued before any store of it; H_x, H_y of plane k-1 stay in registers.
+// Interior E tile with a one-plane software pipeline: the operands of plane k+1 are loaded
+// before plane k is computed and stored, so every thread keeps two planes of loads in flight.
+template <typename T, bool kAniso>
+__device__ __forceinline__ void tile_e_int(const Dom<T>* __restrict__ doms, const Tile& t, T S, const StepArgs& a,
+                                           int step) {
+    const Dom<T>& d = doms[t.dom];
+    const int nx = d.n[0], ny = d.n[1];
+    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    if (i < 0 || j < 0) return;
+    const bool fsrc = t.flags & kTileSrcE;
+    const bool fmon = a.dft_on && (t.flags & kTileMonE);
+    const long long nxy = (long long)nx * ny;
+    T* Ex = d.F[0];
+    T* Ey = d.F[1];
+    T* Ez = d.F[2];
+    const T* Hx = d.F[3];
+    const T* Hy = d.F[4];
+    const T* Hz = d.F[5];
+    const T* ie0 = d.ie[0];
+    const T* ie1 = d.ie[1];
+    const T* ie2 = d.ie[2];
+    long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
+    T hxz = Hx[id - nxy], hyz = Hy[id - nxy];
+    // operands of the current plane
+    T hx = Hx[id], hy = Hy[id], hz = Hz[id];
+    T hz_ym = Hz[id - nx], hx_ym = Hx[id - nx], hz_xm = Hz[id - 1], hy_xm = Hy[id - 1];
+    T ex = Ex[id], ey = Ey[id], ez = Ez[id];
+    T iex = ie0[id], iey = kAniso ? ie1[id] : iex, iez = kAniso ? ie2[id] : iex;
+    for (int k = t.z0; k < t.z1; ++k, id += nxy) {
+        // prefetch plane k+1 (the tile never ends at the domain's last plane)
+        const long long nid = id + nxy;
+        const bool more = k + 1 < t.z1;
+        T nhx = T(0), nhy = T(0), nhz = T(0), nhz_ym = T(0), nhx_ym = T(0), nhz_xm = T(0), nhy_xm = T(0);
+        T nex = T(0), ney = T(0), nez = T(0), niex = T(0), niey = T(0), niez = T(0);
+        if (more) {
+            nhx = Hx[nid];
+            nhy = Hy[nid];
+            nhz = Hz[nid];
+            nhz_ym = Hz[nid - nx];
+            nhx_ym = Hx[nid - nx];
+            nhz_xm = Hz[nid - 1];
+            nhy_xm = Hy[nid - 1];
+            nex = Ex[nid];
+            ney = Ey[nid];
+            nez = Ez[nid];
+            niex = ie0[nid];
+            niey = kAniso ? ie1[nid] : niex;
+            niez = kAniso ? ie2[nid] : niex;
+        }
+        ex += S * iex * ((hz - hz_ym) - (hy - hyz));
+        ey += S * iey * ((hx - hxz) - (hz - hz_xm));
+        ez += S * iez * ((hy - hy_xm) - (hx - hx_ym));
+        if (fsrc) {
+            ex += src_add(d, a.srcs, 0, i, j, k, step);
+            ey += src_add(d, a.srcs, 1, i, j, k, step);
+            ez += src_add(d, a.srcs, 2, i, j, k, step);
+        }
+        Ex[id] = ex;
+        Ey[id] = ey;
+        Ez[id] = ez;
+        if (fmon) dft_cell(d, a.mons, 0, i, j, k, step, ex, ey, ez);
+        hxz = hx;
+        hyz = hy;
+        hx = nhx; hy = nhy; hz = nhz;
+        hz_ym = nhz_ym; hx_ym = nhx_ym; hz_xm = nhz_xm; hy_xm = nhy_xm;
+        ex = nex; ey = ney; ez = nez;
+        iex = niex; iey = niey; iez = niez;
+    }
+}
+
+// Interior H tile with the same one-plane pipeline (E_x, E_y of plane k+1 are operands of
+// plane k and are carried).
+template <typename T, bool kEnergy>
+__device__ __forceinline__ void tile_h_int(const Dom<T>* __restrict__ doms, const Tile& t, T S, const StepArgs& a,
+                                           int step) {
+    const Dom<T>& d = doms[t.dom];
+    const int nx = d.n[0], ny = d.n[1];
+    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    const bool fsrc = t.flags & kTileSrcH;
+    const bool fmon = a.dft_on && (t.flags & kTileMonH);
+    double w = 0.0;
+    if (i >= 0 && j >= 0) {
+        const long long nxy = (long long)nx * ny;
+        const T* Ex = d.F[0];
+        const T* Ey = d.F[1];
+        const T* Ez = d.F[2];
+        T* Hx = d.F[3];
+        T* Hy = d.F[4];
+        T* Hz = d.F[5];
+        long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
+        T exk = Ex[id], eyk = Ey[id];
+        T exn = Ex[id + nxy], eyn = Ey[id + nxy];
+        T ez = Ez[id], ez_yp = Ez[id + nx], ez_xp = Ez[id + 1], ey_xp = Ey[id + 1], ex_yp = Ex[id + nx];
+        T hx = Hx[id], hy = Hy[id], hz = Hz[id];
+        for (int k = t.z0; k < t.z1; ++k, id += nxy) {
+            const long long nid = id + nxy;
+            const bool more = k + 1 < t.z1;
+            T nexn = T(0), neyn = T(0), nez = T(0), nez_yp = T(0), nez_xp = T(0), ney_xp = T(0), nex_yp = T(0);
+            T nhx = T(0), nhy = T(0), nhz = T(0);
+            if (more) {
+                nexn = Ex[nid + nxy];
+                neyn = Ey[nid + nxy];
+                nez = Ez[nid];
+                nez_yp = Ez[nid + nx];
+                nez_xp = Ez[nid + 1];
+                ney_xp = Ey[nid + 1];
+                nex_yp = Ex[nid + nx];
+                nhx = Hx[nid];
+                nhy = Hy[nid];
+                nhz = Hz[nid];
+            }
+            T hx1 = hx - S * ((ez_yp - ez) - (eyn - eyk));
+            T hy1 = hy - S * ((exn - exk) - (ez_xp - ez));
+            T hz1 = hz - S * ((ey_xp - eyk) - (ex_yp - exk));
+            if (fsrc) {
+                hx1 += src_add(d, a.srcs, 3, i, j, k, step);
+                hy1 += src_add(d, a.srcs, 4, i, j, k, step);
+                hz1 += src_add(d, a.srcs, 5, i, j, k, step);
+            }
+            Hx[id] = hx1;
+            Hy[id] = hy1;
+            Hz[id] = hz1;
+            if (fmon) dft_cell(d, a.mons, 1, i, j, k, step, hx1, hy1, hz1);
+            if (kEnergy) {
+                w += 0.5 * ((double)hx * hx1 + (double)hy * hy1 + (double)hz * hz1);
+                w += 0.5 * ((double)exk * exk / (double)d.ie[0][id] + (double)eyk * eyk / (double)d.ie[1][id] +
+                            (double)ez * ez / (double)d.ie[2][id]);
+            }
+            exk = exn;
+            eyk = eyn;
+            exn = nexn;
+            eyn = neyn;
+            ez = nez; ez_yp = nez_yp; ez_xp = nez_xp; ey_xp = ney_xp; ex_yp = nex_yp;
+            hx = nhx; hy = nhy; hz = nhz;
+        }
+    }
+    if (kEnergy) {
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if ((threadIdx.x & 31) == 0 && d.energy && step < d.energy_cap) atomicAdd(d.energy + step, w);
+    }
+}
+
 template <typename T, bool kGen, bool kAniso>
 __device__ __forceinline__ void tile_e(const Dom<T>* __restrict__ doms, const Tile& t, T S, const StepArgs& a,
                                        int step) {
@@ -224,7 +372,10 @@ __device__ __forceinline__ void tile_e(const Dom<T>* __restrict__ doms, const Ti
 template <typename T, bool kGen, bool kAniso>
 __global__ void __launch_bounds__(kTileX* kTileY, min_blocks<T>(kGen))
     k_e_update(const Dom<T>* __restrict__ doms, const Tile* __restrict__ tiles, T S, const StepArgs a) {
-    tile_e<T, kGen, kAniso>(doms, tiles[blockIdx.x], S, a, *a.d_step);
+    if (kGen)
+        tile_e<T, true, kAniso>(doms, tiles[blockIdx.x], S, a, *a.d_step);
+    else
+        tile_e_int<T, kAniso>(doms, tiles[blockIdx.x], S, a, *a.d_step);
 }
 
 // H half-step (Eq. (yee) second half) of a tile; E_x, E_y of plane k+1 are carried to the next
@@ -318,7 +469,10 @@ template <typename T, bool kGen, bool kEnergy>
 __global__ void __launch_bounds__(kTileX* kTileY, min_blocks<T>(kGen))
     k_h_update(const Dom<T>* __restrict__ doms, const Tile* __restrict__ tiles, T S, const StepArgs a, int advance) {
     const int step = *a.d_step;
-    tile_h<T, kGen, kEnergy>(doms, tiles[blockIdx.x], S, a, step);
+    if (kGen)
+        tile_h<T, true, kEnergy>(doms, tiles[blockIdx.x], S, a, step);
+    else
+        tile_h_int<T, kEnergy>(doms, tiles[blockIdx.x], S, a, step);
     if (advance) {
         // the last block to finish advances the device step counter (every block has read it)
         __syncthreads();
@@ -379,8 +533,8 @@ __device__ __forceinline__ int claim_tile(GridSync* gs, unsigned long long base)
     return t;
 }
 
-template <typename T, bool kAniso, bool kEnergy>
-__global__ void __launch_bounds__(kTileX* kTileY, min_blocks<T>(true))
+template <typename T, bool kAniso, bool kEnergy, bool kPrefetch>
+__global__ void __launch_bounds__(kTileX* kTileY, min_blocks_persistent<T, kPrefetch>())
     k_steps(const Dom<T>* __restrict__ doms, const Tile* __restrict__ tiles, int ntiles, T S, const StepArgs a,
             int nsteps, GridSync* gs) {
     const int step0 = *a.d_step;
@@ -394,6 +548,8 @@ __global__ void __launch_bounds__(kTileX* kTileY, min_blocks<T>(true))
             const Tile tl = tiles[t];
             if (tl.flags & kTileGeneral)
                 tile_e<T, true, true>(doms, tl, S, a, step);
+            else if (kPrefetch)
+                tile_e_int<T, kAniso>(doms, tl, S, a, step);
             else
                 tile_e<T, false, kAniso>(doms, tl, S, a, step);
         }
@@ -405,6 +561,8 @@ __global__ void __launch_bounds__(kTileX* kTileY, min_blocks<T>(true))
             const Tile tl = tiles[t];
             if (tl.flags & kTileGeneral)
                 tile_h<T, true, kEnergy>(doms, tl, S, a, step);
+            else if (kPrefetch)
+                tile_h_int<T, kEnergy>(doms, tl, S, a, step);
             else
                 tile_h<T, false, kEnergy>(doms, tl, S, a, step);
         }
@@ -416,12 +574,19 @@ __global__ void __launch_bounds__(kTileX* kTileY, min_blocks<T>(true))
 
 template <typename T>
 cudaError_t launch_steps(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
-                         int nsteps, int aniso, int energy, GridSync* gs, int* grid_used) {
+                         int nsteps, int aniso, int energy, int prefetch, GridSync* gs, int* grid_used) {
     void* fn;
-    if (aniso)
-        fn = energy ? (void*)k_steps<T, true, true> : (void*)k_steps<T, true, false>;
-    else
-        fn = energy ? (void*)k_steps<T, false, true> : (void*)k_steps<T, false, false>;
+    if (prefetch) {
+        if (aniso)
+            fn = energy ? (void*)k_steps<T, true, true, true> : (void*)k_steps<T, true, false, true>;
+        else
+            fn = energy ? (void*)k_steps<T, false, true, true> : (void*)k_steps<T, false, false, true>;
+    } else {
+        if (aniso)
+            fn = energy ? (void*)k_steps<T, true, true, false> : (void*)k_steps<T, true, false, false>;
+        else
+            fn = energy ? (void*)k_steps<T, false, true, false> : (void*)k_steps<T, false, false, false>;
+    }
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -490,8 +655,8 @@ GBFDTD_INST(float)
 GBFDTD_INST(double)
 #undef GBFDTD_INST
 template cudaError_t launch_steps<float>(const Launch&, const Dom<float>*, const Tile*, int, float, const StepArgs&, int,
-                                         int, int, GridSync*, int*);
+                                         int, int, int, GridSync*, int*);
 template cudaError_t launch_steps<double>(const Launch&, const Dom<double>*, const Tile*, int, double,
-                                          const StepArgs&, int, int, int, GridSync*, int*);
+                                          const StepArgs&, int, int, int, int, GridSync*, int*);
 
 }  // namespace gbfdtd

@@ -84,6 +84,8 @@ _SIGS = {
     "fdtd_step_forward": [_ctx, C.c_int32],
     "fdtd_step_count": [_ctx, _i64p],
     "fdtd_set_launch_mode": [_ctx, C.c_int32],
+    "fdtd_get_launch_mode": [_ctx, _i32p],
+    "fdtd_autotune": [_ctx, C.c_int32, C.POINTER(C.c_double)],
     "fdtd_reset": [_ctx],
     "fdtd_part_count": [_ctx, C.c_int32, _i32p],
     "fdtd_part_size": [_ctx, C.c_int32, C.c_int32, _i64p],
@@ -182,6 +184,19 @@ fdtd_dft_enable = _wrap_simple("fdtd_dft_enable")
 fdtd_enable_energy = _wrap_simple("fdtd_enable_energy")
 fdtd_step_forward = _wrap_simple("fdtd_step_forward")
 fdtd_set_launch_mode = _wrap_simple("fdtd_set_launch_mode")
+
+
+def fdtd_get_launch_mode(ctx):
+    v = C.c_int32()
+    _check(load().fdtd_get_launch_mode(ctx, C.byref(v)), "fdtd_get_launch_mode", ctx)
+    return int(v.value)
+
+
+def fdtd_autotune(ctx, n_steps):
+    """Times the launch modes on the live state, keeps the fastest; returns ms per mode."""
+    ms = (C.c_double * 3)()
+    _check(load().fdtd_autotune(ctx, int(n_steps), ms), "fdtd_autotune", ctx)
+    return [float(v) for v in ms]
 fdtd_reset = _wrap_simple("fdtd_reset")
 fdtd_set_step_count = _wrap_simple("fdtd_set_step_count")
 fdtd_state_save = _wrap_simple("fdtd_state_save")

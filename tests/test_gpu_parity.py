@@ -461,7 +461,7 @@ def test_nonfinite_detection_and_adjoint_state_rules():
 def test_persistent_and_per_launch_paths_bitwise_equal(which):
     scs = [small_blocks(40, 6, 150)] if which == "blocks" else _tiny_batch(3, 150)
     outs = []
-    for mode in (0, 1):
+    for mode in (0, 1, 2):
         ctx = fdtd.Context(scs, dtype="f32")
         fdtd.fdtd_set_launch_mode(ctx.ctx, mode)
         ctx.step(70)
@@ -470,10 +470,11 @@ def test_persistent_and_per_launch_paths_bitwise_equal(which):
         outs.append(([ctx.part(d, p).clone() for d in range(len(scs)) for p in range(ctx.part_count(d))],
                      [ctx.dft(k).clone() for k in range(len(ctx.monitors))]))
         ctx.close()
-    for a, b in zip(outs[0][0], outs[1][0]):
-        assert torch.equal(a, b)
-    for a, b in zip(outs[0][1], outs[1][1]):
-        assert torch.equal(a, b)
+    for other in outs[1:]:
+        for a, b in zip(outs[0][0], other[0]):
+            assert torch.equal(a, b)
+        for a, b in zip(outs[0][1], other[1]):
+            assert torch.equal(a, b)
 
 
 def test_bf16_snapshot_denormal_slab_stays_finite():
@@ -495,3 +496,19 @@ def test_bf16_snapshot_denormal_slab_stays_finite():
     assert abs(float(got[9, 2, 2]) - 0.75) <= 0.75 * 2.0 ** -8
     assert float(got[5, 3, 7]) > 0 and float(got[5, 3, 8]) < 0
     assert float(got.abs().sum()) - 0.75 < 1e-3
+
+
+def test_autotune_keeps_state_and_spectra():
+    sc = small_blocks(40, 6, 120)
+    ref = fdtd.Context([sc], dtype="f32")
+    ref.step(60)
+    ctx = fdtd.Context([sc], dtype="f32")
+    ctx.step(30)
+    ms = fdtd.fdtd_autotune(ctx.ctx, 12)
+    assert len(ms) == 3 and all(m > 0 for m in ms)
+    assert fdtd.fdtd_get_launch_mode(ctx.ctx) in (0, 1, 2)
+    assert ctx.step_count == 30
+    ctx.step(30)
+    for p in range(ctx.part_count(0)):
+        assert torch.equal(ctx.part(0, p), ref.part(0, p))
+    assert torch.equal(ctx.dft(0), ref.dft(0))
