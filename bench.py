@@ -65,15 +65,16 @@ def source_sha():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+def recorded_traffic(kernel, steps_per_launch):
+    """DRAM bytes per launch from the committed ncu summary (bytes per time step x steps per
+    launch), if the summary was taken from the current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
         ent = d.get(kernel)
         if ent and ent.get("source_sha") == source_sha():
-            return ent["dram_bytes_per_launch"]
+            return int(ent["dram_bytes_per_step"] * steps_per_launch)
     except Exception:
         pass
     return None
@@ -159,6 +160,7 @@ def run_ours(args):
     from paper_2609_30039_gb300 import adjoint as ADJ
     from paper_2609_30039_gb300 import build as B
     from paper_2609_30039_gb300 import fdtd
+    from paper_2609_30039_gb300 import sharding
 
     rank, world, local = rank_info()
     torch.cuda.set_device(local)
@@ -214,10 +216,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = ctx.launches() - l0
     tot_ms = sum(times)
-    if dist:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = sharding.max_over_ranks(tot_ms, dist, dev)
     ms_per_step = tot_ms / args.steps
     value = world * cells * T_STEPS / (ms_per_step * 1e-3) / 1e9
 
@@ -238,6 +237,11 @@ def run_ours(args):
         bpc, ncell = alg_bytes_per_cell(sc, 4, dom)
         alg_bytes = bpc * ncell
         achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    # ncu DRAM bytes of the same kernel variant (recorded per time step), or None
+    if dom == "persistent":
+        traffic = recorded_traffic(f"persistent_mode{mode}", T_STEPS / prof["persistent"][1])
+    else:
+        traffic = recorded_traffic(dom, 1)
     step_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]}
     share = {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items() if v[1]}
 
@@ -253,7 +257,7 @@ def run_ours(args):
         "launch_mode": {"chosen": ["per-half-step graphs", "persistent", "persistent+prefetch"][mode],
                         "autotune_ms_per_200_steps": [round(v, 3) for v in tune_ms]},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic(dom),
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                      "alg_bytes_per_launch": int(alg_bytes), "avg_launch_us": round(avg_ms * 1e3, 3),
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.8 TB/s"},
@@ -526,11 +530,23 @@ def measure_batched(args):
     from paper_2609_30039_gb300 import fdtd
     from paper_2609_30039_gb300 import workloads as W
     from tests.oracle_adapter import oracle_from_scene
+    from paper_2609_30039_gb300 import sharding
     B.build()
-    scs = W.lorentz_batch()
+    rank, world, local = rank_info()
+    dist = None
+    all_scs = W.lorentz_batch()
+    T = all_scs[0].n_steps
+    total_cells = sum(sc.cells for sc in all_scs)
+    mine = list(range(len(all_scs)))
+    if world > 1:
+        # independent domains: each rank advances its own share, no data-path collective
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        mine = sharding.shard_domains([sc.cells for sc in all_scs], world)[rank]
+    scs = [all_scs[d] for d in mine]
     cells = sum(sc.cells for sc in scs)
-    ctx = fdtd.Context(scs, dtype="f32")
-    T = scs[0].n_steps
+    ctx = fdtd.Context(scs, dtype="f32", device=f"cuda:{local}")
     for _ in range(max(1, args.warmup - 2)):
         fdtd.fdtd_reset(ctx.ctx)
         fdtd.fdtd_dft_reset(ctx.ctx)
@@ -541,11 +557,15 @@ def measure_batched(args):
         fdtd.fdtd_dft_reset(ctx.ctx)
         ts.append(_timed(lambda: ctx.step(T), ctx.stream))
     t = statistics.median(ts)
+    if dist:
+        dist.barrier()
+        t = sharding.max_over_ranks(t, dist, torch.device("cuda", local))
     small = min(range(len(scs)), key=lambda d: scs[d].cells)
-    out = {"workload": f"lorentz_batch: {len(scs)} domains, {cells} cells, {T} steps, FP32",
-           "gcell_steps_s": round(cells * T / t / 1e9, 3), "seconds": round(t, 4),
+    out = {"workload": f"lorentz_batch: {len(all_scs)} domains, {total_cells} cells, {T} steps, FP32",
+           "gcell_steps_s": round(total_cells * T / t / 1e9, 3), "seconds": round(t, 4),
+           "n_gpus": world, "scaling": "strong (fixed batch, domains sharded over ranks)",
            "launches_per_step": 4, "graph_steps": 32}
-    if not args.no_cpu:
+    if rank == 0 and not args.no_cpu:
         obuild()
         o = oracle_from_scene(scs[small])
         o.step(T)
@@ -553,7 +573,12 @@ def measure_batched(args):
         R = o.dft(0)
         out["smallest_domain"] = scs[small].shape
         out["smallest_domain_dft_rel_l2_vs_oracle"] = float(np.linalg.norm(F - R) / np.linalg.norm(R))
-    print(json.dumps(out))
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def _fd_gradient_check(sc, n_cells, h, rng_seed, dtype_fd="f64", dtype_adj="f32", slots=32):

@@ -1,11 +1,12 @@
 // Transposed (discrete-adjoint) half-steps, arxiv 2609.30039 Sec. 3.1, Eq. (adjoint).
 //
-// Every forward update has a transpose kernel of the same locality:
-//   * k_adj_e  (one thread per E column, like the forward E update) applies the transpose of
+// Every forward update has a transpose kernel of the same locality, in a general form (CPML,
+// PEC, poles: k_adj_e_gen / k_adj_h_gen) and an interior form (k_adj_e_int / k_adj_h_int):
+//   * k_adj_e*  (one thread per E column, like the forward E update) applies the transpose of
 //     the forward H update (Ebar += gathered backward differences of the H cotangent, the
-//     "opposite-direction differences" of Sec. 3.1), injects dJ/dE of the monitors, and
+//     opposite-direction differences of Sec. 3.1), injects dJ/dE of the monitors, and
 //     transposes the E update's own-cell part (poles, eps^-1, material cotangent);
-//   * k_adj_h  (one thread per H column) applies the transpose of the forward E update
+//   * k_adj_h*  (one thread per H column) applies the transpose of the forward E update
 //     (Hbar += gathered forward differences) and the H-side CPML recursion.
 // CPML transpose (Sec. 3.1): psibar_mem = psibar + ybar, Dbar = ybar/kappa + c psibar_mem,
 // psibar_old = b psibar_mem.  Pole transpose: the 2x2 trapezoidal system applied to the
@@ -13,55 +14,18 @@
 //
 // Gather form needs the cotangent of every neighbour's derivative D while its owner is still
 // updating psibar.  So that no kernel reads a value another thread of the same launch writes,
-// the E-side own-cell part of transposed step m is deferred to the next k_adj_e (m-1):
-// after k_adj_e(m) the E array holds F = S/(eps_inf + G) * Etilde_bar (the cotangent of the
+// the E-side own-cell part of transposed step m is deferred to the next k_adj_e* (m-1):
+// after k_adj_e*(m) the E array holds F = S/(eps_inf + G) * Etilde_bar (the cotangent of the
 // curl, which k_adj_h needs at neighbours), and the pole/psi cotangents still hold their step
-// m+1 values.  k_adj_e(m-1) (or k_adj_flush) first completes step m for its own cell:
+// m+1 values.  k_adj_e*(m-1) (or k_adj_flush) first completes step m for its own cell:
 //   Ebar^m   = (eps_inf - G)/S * F + sum_p g_p . xbar_p
 //   xbar_p^m = M_p^T xbar_p + ((1 - M00_p) / S, -M01_p / S) F
 //   psibar_E^m = b (psibar_E + (+F | -F))
-// The H side needs no deferral: psibar_H of step m is finished by k_adj_h(m) after
-// k_adj_e(m) has read it.
+// The H side needs no deferral: psibar_H of step m is finished by k_adj_h*(m) after
+// k_adj_e*(m) has read it.
 #include "fdtd_internal.cuh"
 
 namespace gbfdtd {
-
-// Cotangent of the derivative D read by H_h's s-th derivative at cell (i,j,k):
-// ybar = -S Hbar (s = 0) | +S Hbar (s = 1); Dbar = ybar/kappa + c (psibar + ybar) in the slab.
-template <typename T>
-__device__ __forceinline__ T dbar_h(const Dom<T>& d, int h, int s, int i, int j, int k, T S) {
-    const int c[3] = {i, j, k};
-    const int ax = (h + 1 + s) % 3;
-    const long long id = cidx(d.n, i, j, k);
-    const T yb = (s == 0 ? -S : S) * d.A[3 + h][id];
-    if (d.ns[ax] == 0) return yb;
-    const int x = c[ax];
-    const int sl = slab_of(x, d.dlo[ax], d.dhi[ax], d.n[ax]);
-    if (sl < 0) return yb;
-    const int N = d.n[ax];
-    const T pm = d.apsiH[h][s][slab_off(d.n, d.ns, ax, i, j, k, sl)] + yb;
-    return d.cH[ax][2 * N + x] * yb + d.cH[ax][N + x] * pm;
-}
-
-// Cotangent of the derivative D read by E_e's s-th derivative at cell (i,j,k), from the
-// lagged E state: ybar = +F (s = 0) | -F (s = 1).
-template <typename T>
-__device__ __forceinline__ T dbar_e(const Dom<T>& d, int e, int s, int i, int j, int k) {
-    const int c[3] = {i, j, k};
-    // a PEC node is never updated, so its CPML memory never reaches a curl: no cotangent flows
-    if (c[(e + 1) % 3] == 0 || c[(e + 2) % 3] == 0) return T(0);
-    const int ax = (e + 1 + s) % 3;
-    const long long id = cidx(d.n, i, j, k);
-    const T F = d.A[e][id];
-    const T yb = s == 0 ? F : -F;
-    if (d.ns[ax] == 0) return yb;
-    const int x = c[ax];
-    const int sl = slab_of(x, d.dlo[ax], d.dhi[ax], d.n[ax]);
-    if (sl < 0) return yb;
-    const int N = d.n[ax];
-    const T pm = d.apsiE[e][s][slab_off(d.n, d.ns, ax, i, j, k, sl)] + yb;
-    return d.cE[ax][2 * N + x] * yb + d.cE[ax][N + x] * pm;
-}
 
 // Completes the deferred own-cell transpose of an E update for component a; returns Ebar.
 template <typename T>
@@ -118,129 +82,6 @@ __device__ __forceinline__ double inject_at(const Dom<T>& d, const Mon* __restri
         }
     }
     return acc;
-}
-
-// k_adj_e: transposed step m, E side.  Forward state must be u^m when a design box is set.
-template <typename T>
-__global__ void __launch_bounds__(kTileX* kTileY) k_adj_e(const Dom<T>* __restrict__ doms,
-                                                          const Mon* __restrict__ mons,
-                                                          const Tile* __restrict__ tiles, T S, int m, int pending) {
-    const Tile t = tiles[blockIdx.x];
-    const Dom<T>& d = doms[t.dom];
-    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
-    if (i < 0 || j < 0) return;
-    const long long st[3] = {1, (long long)d.n[0], (long long)d.n[0] * d.n[1]};
-    for (int k = t.z0; k < t.z1; ++k) {
-        const int c[3] = {i, j, k};
-        const long long id = cidx(d.n, i, j, k);
-        const bool dcell = d.npole > 0 && d.mask[id] && in_ade_box(d, i, j, k);
-        const bool gcell = d.design && i >= d.glo[0] && i < d.ghi[0] && j >= d.glo[1] && j < d.ghi[1] &&
-                           k >= d.glo[2] && k < d.ghi[2];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int b = (a + 1) % 3, q = (a + 2) % 3;
-            if (c[b] == 0 || c[q] == 0) {  // PEC node: not a state variable
-                d.A[a][id] = T(0);
-                continue;
-            }
-            const T Fprev = d.A[a][id];
-            T eb = pending ? e_deferred(d, a, i, j, k, id, dcell, Fprev, S) : Fprev;
-            // transpose of the H update of step m: E_a is read by H_b (1st derivative, along q)
-            // and by H_q (2nd derivative, along b), each at r and r + e
-            int cm[3] = {i, j, k};
-            cm[q] -= 1;
-            eb += dbar_h(d, b, 0, cm[0], cm[1], cm[2], S) - dbar_h(d, b, 0, i, j, k, S);
-            cm[q] += 1;
-            cm[b] -= 1;
-            eb += dbar_h(d, q, 1, cm[0], cm[1], cm[2], S) - dbar_h(d, q, 1, i, j, k, S);
-            // dJ/dE^{m+1}
-            if (d.nmon) eb += (T)inject_at(d, mons, a, i, j, k, (long long)m * 2 + 0);
-            // transpose of the E update of step m (own cell)
-            const T ie = d.ie[a][id];
-            T et = eb;
-            T gdisp = T(0);
-            if (dcell) {
-                const long long bo = ade_off(d, i, j, k);
-                for (int p = 0; p < d.npole; ++p) {
-                    const T xp = d.aade[((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo];
-                    const T xq = d.aade[((long long)(a * d.npole + p) * 2 + 1) * d.bcell + bo];
-                    et += d.g0[p] * xp + d.g1[p] * xq;
-                }
-                gdisp = d.G;
-            }
-            if (gcell) {
-                // d E^{m+1} / d(eps^-1) = Delta (eps_inf / (eps_inf + G))^2,
-                // Delta = S curl(H^{m+1/2}) + sum_p (P - (M x)_P - 2 g_p E^m)  (forward state u^m)
-                const T* Hq = d.F[3 + q];
-                const T* Hb = d.F[3 + b];
-                const T curl = (Hq[id] - Hq[id - st[b]]) - (Hb[id] - Hb[id - st[q]]);
-                double delta = (double)(S * curl);
-                if (dcell) {
-                    const long long bo = ade_off(d, i, j, k);
-                    const T e0 = d.F[a][id];
-                    for (int p = 0; p < d.npole; ++p) {
-                        const T P = d.ade[((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo];
-                        const T Q = d.ade[((long long)(a * d.npole + p) * 2 + 1) * d.bcell + bo];
-                        delta += (double)(P - (d.M00[p] * P + d.M01[p] * Q) - T(2) * d.g0[p] * e0);
-                    }
-                }
-                const double r = 1.0 / (1.0 + (double)ie * (double)gdisp);
-                const long long gi = ((long long)(k - d.glo[2]) * (d.ghi[1] - d.glo[1]) + (j - d.glo[1])) *
-                                         (d.ghi[0] - d.glo[0]) + (i - d.glo[0]);
-                const long long gn = (long long)(d.ghi[0] - d.glo[0]) * (d.ghi[1] - d.glo[1]) * (d.ghi[2] - d.glo[2]);
-                d.grad[a * gn + gi] += (double)et * delta * r * r;
-            }
-            d.A[a][id] = S * ie / (T(1) + ie * gdisp) * et;
-        }
-    }
-}
-
-// k_adj_h: transposed step m, H side.  Injects dJ/dH^{m+1/2} (m >= 1) at the end.
-template <typename T>
-__global__ void __launch_bounds__(kTileX* kTileY) k_adj_h(const Dom<T>* __restrict__ doms,
-                                                          const Mon* __restrict__ mons,
-                                                          const Tile* __restrict__ tiles, T S, int m) {
-    const Tile t = tiles[blockIdx.x];
-    const Dom<T>& d = doms[t.dom];
-    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
-    if (i < 0 || j < 0) return;
-    for (int k = t.z0; k < t.z1; ++k) {
-        const int c[3] = {i, j, k};
-        const long long id = cidx(d.n, i, j, k);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int b = (a + 1) % 3, q = (a + 2) % 3;
-            const T hb = d.A[3 + a][id];
-            // finish the H-side CPML transpose of step m (k_adj_e(m) has read psibar_H)
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const int ax = (a + 1 + s) % 3;
-                if (d.ns[ax] == 0) continue;
-                const int x = c[ax];
-                const int sl = slab_of(x, d.dlo[ax], d.dhi[ax], d.n[ax]);
-                if (sl < 0) continue;
-                T* p = d.apsiH[a][s] + slab_off(d.n, d.ns, ax, i, j, k, sl);
-                *p = d.cH[ax][x] * (*p + (s == 0 ? -S : S) * hb);
-            }
-            // transpose of the E update of step m: H_a is read by E_b (1st derivative, along q)
-            // and by E_q (2nd derivative, along b), each at r and r - e
-            T h = hb;
-            h += dbar_e(d, b, 0, i, j, k);
-            if (c[q] + 1 < d.n[q]) {
-                int cp[3] = {i, j, k};
-                cp[q] += 1;
-                h -= dbar_e(d, b, 0, cp[0], cp[1], cp[2]);
-            }
-            h += dbar_e(d, q, 1, i, j, k);
-            if (c[b] + 1 < d.n[b]) {
-                int cp[3] = {i, j, k};
-                cp[b] += 1;
-                h -= dbar_e(d, q, 1, cp[0], cp[1], cp[2]);
-            }
-            if (d.nmon && m >= 1) h += (T)inject_at(d, mons, 3 + a, i, j, k, (long long)(m - 1) * 2 + 1);
-            d.A[3 + a][id] = h;
-        }
-    }
 }
 
 // ---- general tiles, hoisted form -------------------------------------------------------------
