@@ -254,7 +254,7 @@ def run_ours(args):
                    "l2": "flushed between timed iterations (256 MiB write); the ~75 MB state stays L2-resident "
                          "within an iteration", "parallelism": f"{world} independent replica(s), no collective"},
         "gpu_launches": int(launches),
-        "launch_mode": {"chosen": ["per-half-step graphs", "persistent", "persistent+prefetch"][mode],
+        "launch_mode": {"chosen": ["per-half-step graphs", "persistent", "persistent+prefetch", "persistent+TMA"][mode],
                         "autotune_ms_per_200_steps": [round(v, 3) for v in tune_ms]},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -441,7 +441,10 @@ def main():
                     choices=["cpml128", "pec32", "batched", "adjoint256", "large640"],
                     help="cpml128 is the benchmark line; the others measure the remaining workloads")
     ap.add_argument("--fd-cells", type=int, default=20)
-    ap.add_argument("--launch-mode", type=int, default=1, help="0 per half-step launches, 1 persistent, 2 persistent with prefetch")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision of --profile-case")
+    ap.add_argument("--cpml", type=int, default=CPML, help="CPML depth of --profile-case (0: PEC box)")
+    ap.add_argument("--adjoint", action="store_true", help="--profile-case: also time as many transposed steps")
+    ap.add_argument("--launch-mode", type=int, default=1, help="0 per half-step launches, 1 persistent, 2 persistent with prefetch, 3 persistent with TMA staging")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -457,7 +460,8 @@ def main():
 
 
 def profile_case(args):
-    """Short n^3 FP32 forward solve of the same workload family, for ncu captures."""
+    """Short n^3 forward solve of the same workload family (FP32 unless --dtype f64), for ncu
+    captures and launch-mode timings."""
     import torch
 
     from paper_2609_30039_gb300 import build as B
@@ -465,12 +469,20 @@ def profile_case(args):
     from paper_2609_30039_gb300 import workloads as W
     B.build()
     n = args.profile_case
-    sc = W.cpml_blocks(n=n, d=CPML, n_steps=args.steps)
-    ctx = fdtd.Context([sc], dtype="f32")
+    sc = W.cpml_blocks(n=n, d=args.cpml, n_steps=args.steps)
+    for src in sc.sources:   # an electric sheet must stay off the PEC planes of a box without CPML
+        src.lo = tuple(max(v, 1) for v in src.lo)
+    ctx = fdtd.Context([sc], dtype=args.dtype)
     fdtd.fdtd_set_launch_mode(ctx.ctx, args.launch_mode)
     ctx.step(args.warmup)
     t = _timed(lambda: ctx.step(args.steps), ctx.stream) if args.steps else 0.0
-    print(json.dumps({"profile_case": n, "launch_mode": args.launch_mode, "steps": args.warmup + args.steps,
+    adj = None
+    if args.adjoint and args.steps:
+        fdtd.fdtd_adjoint_begin(ctx.ctx)
+        ta = _timed(lambda: fdtd.fdtd_step_adjoint(ctx.ctx, args.steps), ctx.stream)
+        adj = round(sc.cells * args.steps / ta / 1e9, 3)
+    print(json.dumps({"profile_case": n, "cpml": args.cpml, "dtype": args.dtype, "launch_mode": args.launch_mode,
+                      "adjoint_gcell_steps_s": adj, "steps": args.warmup + args.steps,
                       "cells": sc.cells, "gcell_steps_s": round(sc.cells * args.steps / t / 1e9, 3) if t else None}))
     ctx.close()
 

@@ -170,16 +170,26 @@ fdtd_status fdtd_energy_read(fdtd_ctx* ctx, int32_t domain, double* host_dst, in
  * half-steps) unless fdtd_set_launch_mode selected per-half-step launches. */
 fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps);
 
-/* mode 0: per-half-step launches (replayed as CUDA graphs); mode 1 (default): persistent
- * cooperative launches (4 blocks per SM); mode 2: persistent launches whose interior tiles load
- * the next z-plane ahead (3 blocks per SM).  All modes compute the same values bitwise. */
+/* Launch modes (no counterpart in the paper; they change scheduling, not arithmetic):
+ * mode 0: per-half-step launches (replayed as CUDA graphs); mode 1 (default): persistent
+ * cooperative launches (4 blocks per SM in FP32); mode 2: persistent launches whose interior
+ * tiles load the next z-plane ahead into registers (3 blocks per SM); mode 3: persistent
+ * launches whose interior tiles stage whole z-planes in shared memory with tiled bulk tensor
+ * copies (TMA), several planes ahead.  Mode 3 applies to domains whose rows (nx elements) are
+ * a multiple of 16 bytes and whose fields and eps^-1 arrays are 16-byte aligned; other domains
+ * run the mode-1 code.  All modes compute the same values bitwise.  FDTD_EINVAL for another
+ * mode. */
+#define FDTD_LAUNCH_MODES 4
 fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode);
 fdtd_status fdtd_get_launch_mode(fdtd_ctx* ctx, int32_t* mode);
 
-/* Autotuner: times each launch mode for n_steps forward steps on the current state and keeps
- * the fastest.  The state, step count and DFT accumulators are left as they were (the state is
- * snapshotted and restored; DFT accumulation is off while tuning).  ms_per_mode (3 entries,
- * may be NULL) receives the measured milliseconds.  Synchronises the stream. */
+/* Autotuner (no counterpart in the paper): times each launch mode for n_steps forward steps on
+ * the current state, with DFT recording as configured and energy recording off, and keeps the
+ * fastest.  The state, step count, DFT accumulators and energies are left as they were (state
+ * and accumulators are copied aside and restored after every trial).  ms_per_mode
+ * (FDTD_LAUNCH_MODES entries, may be NULL) receives the measured milliseconds.  Needs device
+ * memory for one native snapshot plus the accumulators (FDTD_ENOMEM otherwise).  Synchronises
+ * the stream. */
 fdtd_status fdtd_autotune(fdtd_ctx* ctx, int32_t n_steps, double* ms_per_mode);
 
 /* Number of forward steps the held state has taken (u^n: returns n). */

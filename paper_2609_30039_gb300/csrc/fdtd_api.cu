@@ -11,6 +11,9 @@
 #include <thread>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "fdtd_internal.cuh"
 
 using namespace gbfdtd;
@@ -45,6 +48,8 @@ struct DomainHost {
     double* grad = nullptr;
     std::vector<int> mons;
     std::vector<int> srcs;
+    const void* tmaps = nullptr;   // this domain's kTmaMaps tensor maps in device memory
+    int tma = 0;                   // maps encoded for the current field and eps^-1 pointers
 };
 
 struct MonHost {
@@ -92,8 +97,10 @@ struct fdtd_ctx {
     unsigned* d_ticket = nullptr;   // completion ticket of the last H launch of a step
     GridSync* d_sync = nullptr;     // barrier / ticket of the persistent step kernel
     Tile* d_tiles_lpt = nullptr;    // general tiles first, then interior (persistent kernel)
+    int n_lpt = 0;
     int use_persistent = 1;
-    int persist_prefetch = 0;
+    int persist_variant = 0;        // 0 register path, 1 register prefetch, 2 TMA-staged interior
+    void* d_tmaps = nullptr;        // kTmaMaps CUtensorMap per domain
     int persist_grid = 0;
     int h_step_tmp = 0;
     long long step = 0;
@@ -111,6 +118,13 @@ struct fdtd_ctx {
     std::vector<void*> owned;   // every device allocation of the context
     // CUDA graphs of kGraphSteps forward steps, keyed by (dft enabled, energy on)
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t aux_stream = nullptr;   // interior launches of the per-half-step mode
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t dft_stream = nullptr;   // DFT launches of the per-half-step mode
+    cudaEvent_t ev_e = nullptr, ev_h = nullptr, ev_de = nullptr, ev_dh = nullptr;
+    DftItem* d_dft_items = nullptr;      // 256-cell work items of every monitor
+    int n_dft_items = 0;
+    int* d_base = nullptr;               // first step of the batch being launched (DFT phases)
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     long long graph_launches[2][2] = {{0, 0}, {0, 0}};
     int use_graphs = 1;
@@ -318,6 +332,65 @@ void fill_dom(const fdtd_ctx* c, const DomainHost& h, Dom<T>& d) {
     for (int i = 0; i < d.nsrc; ++i) d.src[i] = h.srcs[i];
     d.energy = c->energy_on ? h.energy : nullptr;
     d.energy_cap = h.energy_cap;
+    d.tmaps = h.tmaps;
+    d.tma = h.tma;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Plane-box tensor maps of one domain (Ex..Hz, eps^-1 x y z), each a 3-D view (nx, ny, nz) with a
+// kTmaBoxX x kTmaBoxY x 1 box.  False when the domain cannot use them: a row of nx elements that
+// is not a multiple of 16 bytes, an operand not 16-byte aligned, or an encoding the driver refuses.
+bool encode_tmaps(const fdtd_ctx* c, const DomainHost& h, CUtensorMap* out) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encoder();
+    if (!enc || !kTmaFits) return false;
+    const size_t esz = c->esz;
+    if (((size_t)h.n[0] * esz) % 16 != 0) return false;
+    const void* ptr[kTmaMaps] = {h.F[0], h.F[1], h.F[2], h.F[3], h.F[4], h.F[5], h.ie[0], h.ie[1], h.ie[2]};
+    const cuuint64_t dim[3] = {(cuuint64_t)h.n[0], (cuuint64_t)h.n[1], (cuuint64_t)h.n[2]};
+    const cuuint64_t str[2] = {(cuuint64_t)h.n[0] * esz, (cuuint64_t)h.n[0] * h.n[1] * esz};
+    const cuuint32_t box[3] = {(cuuint32_t)kTmaBoxX, (cuuint32_t)kTmaBoxY, 1u};
+    const cuuint32_t es[3] = {1u, 1u, 1u};
+    for (int b = 0; b < kTmaMaps; ++b) {
+        if (!ptr[b] || ((uintptr_t)ptr[b] & 15u)) return false;
+        const CUresult r = enc(&out[b], esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                               const_cast<void*>(ptr[b]), dim, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    return true;
+}
+
+// (Re-)encodes every domain's maps for the current pointers and uploads them.
+fdtd_status sync_tmaps(fdtd_ctx* c) {
+    if (!c->d_tmaps) return FDTD_OK;
+    std::vector<CUtensorMap> maps(c->doms.size() * kTmaMaps);
+    for (size_t di = 0; di < c->doms.size(); ++di) {
+        DomainHost& h = c->doms[di];
+        h.tmaps = (const char*)c->d_tmaps + di * kTmaMaps * sizeof(CUtensorMap);
+        h.tma = encode_tmaps(c, h, &maps[di * kTmaMaps]) ? 1 : 0;
+    }
+    CK(c, cudaMemcpyAsync(c->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FDTD_OK;
 }
 
 template <typename T>
@@ -328,7 +401,11 @@ fdtd_status sync_doms_t(fdtd_ctx* c) {
     return FDTD_OK;
 }
 
-fdtd_status sync_doms(fdtd_ctx* c) { return c->dtype == FDTD_F32 ? sync_doms_t<float>(c) : sync_doms_t<double>(c); }
+fdtd_status sync_doms(fdtd_ctx* c) {
+    fdtd_status st = sync_tmaps(c);
+    if (st != FDTD_OK) return st;
+    return c->dtype == FDTD_F32 ? sync_doms_t<float>(c) : sync_doms_t<double>(c);
+}
 
 fdtd_status ensure_phase(fdtd_ctx* c, long long need, bool* changed = nullptr) {
     if (changed) *changed = false;
@@ -381,9 +458,22 @@ fdtd_status sync_mons(fdtd_ctx* c) {
         c->nentries[kind] = 0;
         c->nthreads[kind] = 0;
     }
+    if (c->d_dft_items) dfree(c, c->d_dft_items);
+    c->d_dft_items = nullptr;
+    c->n_dft_items = 0;
     if (c->mons.empty()) return FDTD_OK;
     std::vector<Mon> hm;
     for (auto& m : c->mons) hm.push_back(m.m);
+    {
+        std::vector<DftItem> items;
+        for (size_t mi = 0; mi < c->mons.size(); ++mi)
+            for (long long b = 0; b < c->mons[mi].m.ncell; b += kTileX * kTileY) items.push_back({(int)mi, (int)b});
+        fdtd_status st = dmalloc(c, (void**)&c->d_dft_items, sizeof(DftItem) * items.size());
+        if (st != FDTD_OK) return st;
+        CK(c, cudaMemcpyAsync(c->d_dft_items, items.data(), sizeof(DftItem) * items.size(), cudaMemcpyHostToDevice,
+                              c->stream));
+        c->n_dft_items = (int)items.size();
+    }
     fdtd_status st = dmalloc(c, (void**)&c->d_mons, sizeof(Mon) * hm.size());
     if (st != FDTD_OK) return st;
     CK(c, cudaMemcpyAsync(c->d_mons, hm.data(), sizeof(Mon) * hm.size(), cudaMemcpyHostToDevice, c->stream));
@@ -556,8 +646,14 @@ void build_tiles(fdtd_ctx* c) {
     long long zsum = 0;
     for (const auto& d : c->doms)
         zsum += (long long)((d.n[0] + kTileX - 1) / kTileX) * ((d.n[1] + kTileY - 1) / kTileY) * d.n[2];
-    int zc = (int)(zsum / (152 * 8));
-    zc = zc < 4 ? 4 : (zc > 32 ? 32 : zc);
+#ifndef GBFDTD_TILES_PER_SM
+#define GBFDTD_TILES_PER_SM 8
+#endif
+#ifndef GBFDTD_ZCHUNK_MIN
+#define GBFDTD_ZCHUNK_MIN 4
+#endif
+    int zc = (int)(zsum / (152 * GBFDTD_TILES_PER_SM));
+    zc = zc < GBFDTD_ZCHUNK_MIN ? GBFDTD_ZCHUNK_MIN : (zc > 32 ? 32 : zc);
     for (int di = 0; di < (int)c->doms.size(); ++di) {
         const DomainHost& d = c->doms[di];
         int a[3], b[3];
@@ -570,8 +666,11 @@ void build_tiles(fdtd_ctx* c) {
         // xr / yr: column ranges; zr: z ranges; interior decides the class
         auto emit = [&](const std::vector<std::pair<int, int>>& xr, const std::vector<std::pair<int, int>>& yr,
                         const std::vector<std::pair<int, int>>& zr, bool interior) {
-            const auto xt = pack_ranges(xr, kTileX);
-            const auto yt = pack_ranges(yr, kTileY);
+            const int tw = interior ? kIntX : kTileX;
+            const auto xt = pack_ranges(xr, tw);
+            const auto yt = pack_ranges(yr, kTileX * kTileY / tw);
+            int lw = 0;
+            while ((1 << lw) < tw) ++lw;
             for (auto z : zr)
                 for (int z0 = z.first; z0 < z.second; z0 += zc)
                     for (const auto& ys : yt)
@@ -587,6 +686,7 @@ void build_tiles(fdtd_ctx* c) {
                             t.z0 = z0;
                             t.z1 = z0 + zc < z.second ? z0 + zc : z.second;
                             t.flags = 0;
+                            t.lw = lw;
                             bool inner = interior;
                             if (inner && d.npole > 0 && d.bcell > 0) {
                                 const int tl[3] = {xs[0], ys[0], t.z0}, th[3] = {xs[1], ys[1], t.z1};
@@ -639,6 +739,7 @@ void tile_flags(fdtd_ctx* c, Tile& t) {
 
 fdtd_status upload_tiles(fdtd_ctx* c) {
     drop_graphs(c);
+    // work list of the persistent kernel: general tiles first (the slower class), then interior
     std::vector<Tile> lpt;
     for (auto& t : c->tiles_gen) {
         tile_flags(c, t);
@@ -651,6 +752,10 @@ fdtd_status upload_tiles(fdtd_ctx* c) {
     }
     CK(c, cudaStreamSynchronize(c->stream));
     if (!lpt.empty()) {
+        if (c->d_tiles_lpt && c->n_lpt < (int)lpt.size()) {
+            dfree(c, c->d_tiles_lpt);
+            c->d_tiles_lpt = nullptr;
+        }
         if (!c->d_tiles_lpt) {
             fdtd_status st = dmalloc(c, (void**)&c->d_tiles_lpt, sizeof(Tile) * lpt.size());
             if (st != FDTD_OK) return st;
@@ -658,6 +763,7 @@ fdtd_status upload_tiles(fdtd_ctx* c) {
         CK(c, cudaMemcpyAsync(c->d_tiles_lpt, lpt.data(), sizeof(Tile) * lpt.size(), cudaMemcpyHostToDevice,
                               c->stream));
     }
+    c->n_lpt = (int)lpt.size();
     std::vector<Tile>* lists[3] = {&c->tiles, &c->tiles_gen, &c->tiles_int};
     Tile** dst[3] = {&c->d_tiles, &c->d_tiles_gen, &c->d_tiles_int};
     for (int li = 0; li < 3; ++li) {
@@ -666,13 +772,14 @@ fdtd_status upload_tiles(fdtd_ctx* c) {
             tile_flags(c, t);
             t.flags |= g;
         }
-        if (lists[li]->empty()) continue;
+        const std::vector<Tile>& up = *lists[li];
+        if (up.empty()) continue;
         if (!*dst[li]) {
-            fdtd_status st = dmalloc(c, (void**)dst[li], sizeof(Tile) * lists[li]->size());
+            fdtd_status st = dmalloc(c, (void**)dst[li], sizeof(Tile) * up.size());
             if (st != FDTD_OK) return st;
         }
-        CK(c, cudaMemcpyAsync(*dst[li], lists[li]->data(), sizeof(Tile) * lists[li]->size(), cudaMemcpyHostToDevice,
-                              c->stream));
+        CK(c, cudaMemcpyAsync(*dst[li], up.data(), sizeof(Tile) * up.size(), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
     }
     CK(c, cudaStreamSynchronize(c->stream));
     return FDTD_OK;
@@ -695,8 +802,11 @@ struct Prof {
     }
 };
 
+// One forward step as per-half-step launches on stream st.  offset: position of this step in the
+// launched batch (its DFT phase index is *d_base + offset); first / last: first and last step of
+// the batch (no wait on DFT work of an earlier batch; the DFT stream is joined back at the end).
 template <typename T>
-void step_once(fdtd_ctx* c, cudaStream_t st) {
+void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) {
     const Launch l{st, &c->launches};
     const Dom<T>* dd = (const Dom<T>*)c->d_doms;
     StepArgs a;
@@ -705,22 +815,72 @@ void step_once(fdtd_ctx* c, cudaStream_t st) {
     a.d_step = c->d_step;
     a.d_ticket = c->d_ticket;
     a.dft_on = c->dft_enabled;
+    a.dft_items = c->d_dft_items;
+    a.ndft = c->n_dft_items;
     const int ng = (int)c->tiles_gen.size(), ni = (int)c->tiles_int.size();
+    // The general and interior launches of a half-step touch disjoint cells: they run
+    // concurrently (interior on the auxiliary stream, forked and joined with events, also inside
+    // a graph capture) so the high-occupancy interior blocks fill the SMs around the general
+    // ones.  Under per-launch profiling they run one after the other on st.
+    const bool fork = c->aux_stream && !c->prof_on && ng > 0 && ni > 0;
+    const Launch la{fork ? c->aux_stream : st, &c->launches};
+    // The DFT of E (step n) runs on its own stream beside the H update, the DFT of H beside the
+    // next E update; a half-step waits only for the DFT of the field it overwrites.
+    const int nd = c->dft_enabled ? c->n_dft_items : 0;
+    const bool dstream = nd > 0 && !c->prof_on;
+    const Launch ld{dstream ? c->dft_stream : st, &c->launches};
+    const unsigned adv = (unsigned)(ng + ni);
+    auto fork_int = [&]() {
+        if (!fork) return;
+        cudaEventRecord(c->ev_fork, st);
+        cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0);
+    };
+    auto join_int = [&]() {
+        if (!fork) return;
+        cudaEventRecord(c->ev_join, c->aux_stream);
+        cudaStreamWaitEvent(st, c->ev_join, 0);
+    };
+    if (nd > 0 && first) launch_copy_int(l, c->d_step, c->d_base);
+    if (dstream && !first) cudaStreamWaitEvent(st, c->ev_de, 0);   // DFT of E^n done before E changes
+    fork_int();
     {
         Prof p(c, FDTD_KERNEL_E);
         launch_e_update<T>(l, dd, c->d_tiles_gen, ng, (T)c->S, a, 1, 1);
     }
     {
         Prof p(c, FDTD_KERNEL_E);
-        launch_e_update<T>(l, dd, c->d_tiles_int, ni, (T)c->S, a, 0, c->aniso);
+        launch_e_update<T>(la, dd, c->d_tiles_int, ni, (T)c->S, a, 0, c->aniso);
+    }
+    join_int();
+    if (nd > 0) {
+        if (dstream) {
+            cudaEventRecord(c->ev_e, st);
+            cudaStreamWaitEvent(c->dft_stream, c->ev_e, 0);
+        }
+        Prof p(c, FDTD_KERNEL_DFT);
+        launch_dft<T>(ld, dd, c->d_mons, c->d_dft_items, nd, 0, c->d_base, offset);
+        if (dstream) cudaEventRecord(c->ev_de, c->dft_stream);
+    }
+    if (dstream && !first) cudaStreamWaitEvent(st, c->ev_dh, 0);   // DFT of H^{n-1/2} done
+    fork_int();
+    {
+        Prof p(c, FDTD_KERNEL_H);
+        launch_h_update<T>(l, dd, c->d_tiles_gen, ng, (T)c->S, a, 1, c->energy_on, adv);
     }
     {
         Prof p(c, FDTD_KERNEL_H);
-        launch_h_update<T>(l, dd, c->d_tiles_gen, ng, (T)c->S, a, 1, c->energy_on, ni == 0);
+        launch_h_update<T>(la, dd, c->d_tiles_int, ni, (T)c->S, a, 0, c->energy_on, adv);
     }
-    {
-        Prof p(c, FDTD_KERNEL_H);
-        launch_h_update<T>(l, dd, c->d_tiles_int, ni, (T)c->S, a, 0, c->energy_on, 1);
+    join_int();
+    if (nd > 0) {
+        if (dstream) {
+            cudaEventRecord(c->ev_h, st);
+            cudaStreamWaitEvent(c->dft_stream, c->ev_h, 0);
+        }
+        Prof p(c, FDTD_KERNEL_DFT);
+        launch_dft<T>(ld, dd, c->d_mons, c->d_dft_items, nd, 1, c->d_base, offset);
+        if (dstream) cudaEventRecord(c->ev_dh, c->dft_stream);
+        if (dstream && last) cudaStreamWaitEvent(st, c->ev_dh, 0);
     }
 }
 
@@ -728,25 +888,40 @@ template <typename T>
 void adj_once(fdtd_ctx* c, int m) {
     const Launch l = L(c);
     const Dom<T>* dd = (const Dom<T>*)c->d_doms;
-    const int nt = (int)c->tiles.size();
-    (void)nt;
+    const int ng = (int)c->tiles_gen.size(), ni = (int)c->tiles_int.size();
+    // as in step_once: the interior launches run on the auxiliary stream next to the general ones
+    const bool fork = c->aux_stream && !c->prof_on && ng > 0 && ni > 0;
+    const Launch la{fork ? c->aux_stream : c->stream, &c->launches};
+    auto fork_here = [&]() {
+        if (!fork) return;
+        cudaEventRecord(c->ev_fork, c->stream);
+        cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0);
+    };
+    auto join_here = [&]() {
+        if (!fork) return;
+        cudaEventRecord(c->ev_join, c->aux_stream);
+        cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    };
+    fork_here();
     {
         Prof p(c, FDTD_KERNEL_ADJ_E);
-        launch_adj_e<T>(l, dd, c->d_mons, c->d_tiles_int, (int)c->tiles_int.size(), (T)c->S, m, c->adj_pending, 0,
-                        c->aniso);
+        launch_adj_e<T>(la, dd, c->d_mons, c->d_tiles_int, ni, (T)c->S, m, c->adj_pending, 0, c->aniso);
     }
     {
         Prof p(c, FDTD_KERNEL_ADJ_E);
-        launch_adj_e<T>(l, dd, c->d_mons, c->d_tiles_gen, (int)c->tiles_gen.size(), (T)c->S, m, c->adj_pending, 1, 1);
+        launch_adj_e<T>(l, dd, c->d_mons, c->d_tiles_gen, ng, (T)c->S, m, c->adj_pending, 1, 1);
+    }
+    join_here();
+    fork_here();
+    {
+        Prof p(c, FDTD_KERNEL_ADJ_H);
+        launch_adj_h<T>(la, dd, c->d_mons, c->d_tiles_int, ni, (T)c->S, m, 0);
     }
     {
         Prof p(c, FDTD_KERNEL_ADJ_H);
-        launch_adj_h<T>(l, dd, c->d_mons, c->d_tiles_int, (int)c->tiles_int.size(), (T)c->S, m, 0);
+        launch_adj_h<T>(l, dd, c->d_mons, c->d_tiles_gen, ng, (T)c->S, m, 1);
     }
-    {
-        Prof p(c, FDTD_KERNEL_ADJ_H);
-        launch_adj_h<T>(l, dd, c->d_mons, c->d_tiles_gen, (int)c->tiles_gen.size(), (T)c->S, m, 1);
-    }
+    join_here();
 }
 
 constexpr int kGraphSteps = 32;
@@ -770,9 +945,9 @@ fdtd_status build_graph(fdtd_ctx* c) {
     CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int s = 0; s < kGraphSteps; ++s) {
         if (c->dtype == FDTD_F32)
-            step_once<float>(c, c->cap_stream);
+            step_once<float>(c, c->cap_stream, s, s == 0, s == kGraphSteps - 1);
         else
-            step_once<double>(c, c->cap_stream);
+            step_once<double>(c, c->cap_stream, s, s == 0, s == kGraphSteps - 1);
     }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
@@ -784,9 +959,11 @@ fdtd_status build_graph(fdtd_ctx* c) {
         c->graph[a][b] = nullptr;
         return fail(c, FDTD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
-    // launches of one step: E and H for each non-empty tile class
-    const long long per = 2 * ((c->tiles_int.empty() ? 0 : 1) + (c->tiles_gen.empty() ? 0 : 1));
-    c->graph_launches[a][b] = per * kGraphSteps;
+    // launches of one step: E and H for each non-empty tile class, the two DFT launches, and
+    // one step-base copy per graph
+    const int nd = c->dft_enabled && c->n_dft_items > 0;
+    const long long per = 2 * ((c->tiles_int.empty() ? 0 : 1) + (c->tiles_gen.empty() ? 0 : 1) + nd);
+    c->graph_launches[a][b] = per * kGraphSteps + nd;
     return FDTD_OK;
 }
 
@@ -882,6 +1059,18 @@ fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cp
     e = cudaMalloc((void**)&c->d_ticket, 64);
     if (e != cudaSuccess) return bail(FDTD_ECUDA);
     c->owned.push_back(c->d_ticket);
+    if (cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->dft_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_e, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_h, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_de, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_dh, cudaEventDisableTiming) != cudaSuccess)
+        return bail(FDTD_ECUDA);
+    e = cudaMalloc((void**)&c->d_base, 64);
+    if (e != cudaSuccess) return bail(FDTD_ECUDA);
+    c->owned.push_back(c->d_base);
     e = cudaMalloc((void**)&c->d_sync, sizeof(GridSync));
     if (e != cudaSuccess) return bail(FDTD_ECUDA);
     c->owned.push_back(c->d_sync);
@@ -961,6 +1150,7 @@ fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cp
     }
     const size_t domb = (c->dtype == FDTD_F32 ? sizeof(Dom<float>) : sizeof(Dom<double>)) * n_domains;
     if (dmalloc(c, &c->d_doms, domb) != FDTD_OK) return bail(FDTD_ENOMEM);
+    if (dmalloc(c, &c->d_tmaps, sizeof(CUtensorMap) * kTmaMaps * n_domains) != FDTD_OK) return bail(FDTD_ENOMEM);
     build_tiles(c);
     for (int di = 0; di < n_domains; ++di) {
         const DomainHost& d = c->doms[di];
@@ -985,6 +1175,12 @@ fdtd_status fdtd_destroy(fdtd_ctx* ctx) {
     prof_release(ctx);
     drop_graphs(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->dft_stream) cudaStreamDestroy(ctx->dft_stream);
+    for (cudaEvent_t e : {ctx->ev_e, ctx->ev_h, ctx->ev_de, ctx->ev_dh})
+        if (e) cudaEventDestroy(e);
     for (void* p : ctx->owned) cudaFree(p);
     for (auto& s : ctx->slots) cudaFree(s.second.buf);
     delete ctx;
@@ -1196,7 +1392,9 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
         a.d_step = ctx->d_step;
         a.d_ticket = ctx->d_ticket;
         a.dft_on = ctx->dft_enabled;
-        const int nt = (int)(ctx->tiles_gen.size() + ctx->tiles_int.size());
+        a.dft_items = ctx->d_dft_items;
+        a.ndft = ctx->n_dft_items;
+        const int nt = ctx->n_lpt;
         const Launch l{ctx->stream, &ctx->launches};
         while (left > 0) {
             const int chunk = left > 512 ? 512 : left;
@@ -1205,11 +1403,11 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
                 Prof p(ctx, FDTD_KERNEL_PERSISTENT);
                 if (ctx->dtype == FDTD_F32)
                     e = launch_steps<float>(l, (const Dom<float>*)ctx->d_doms, ctx->d_tiles_lpt, nt, (float)ctx->S, a,
-                                            chunk, ctx->aniso, ctx->energy_on, ctx->persist_prefetch, ctx->d_sync,
+                                            chunk, ctx->aniso, ctx->energy_on, ctx->persist_variant, ctx->d_sync,
                                             &ctx->persist_grid);
                 else
                     e = launch_steps<double>(l, (const Dom<double>*)ctx->d_doms, ctx->d_tiles_lpt, nt, ctx->S, a, chunk,
-                                             ctx->aniso, ctx->energy_on, ctx->persist_prefetch, ctx->d_sync,
+                                             ctx->aniso, ctx->energy_on, ctx->persist_variant, ctx->d_sync,
                                              &ctx->persist_grid);
             }
             if (e != cudaSuccess) return fail(ctx, FDTD_ECUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
@@ -1228,9 +1426,9 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
     }
     for (int s = 0; s < left; ++s) {
         if (ctx->dtype == FDTD_F32)
-            step_once<float>(ctx, ctx->stream);
+            step_once<float>(ctx, ctx->stream, s, s == 0, s == left - 1);
         else
-            step_once<double>(ctx, ctx->stream);
+            step_once<double>(ctx, ctx->stream, s, s == 0, s == left - 1);
     }
     CKL(ctx);
     ctx->step += n_steps;
@@ -1239,16 +1437,16 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
 
 fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode) {
     GUARD(ctx);
-    if (mode < 0 || mode > 2) return fail(ctx, FDTD_EINVAL, "launch mode must be 0, 1 or 2");
+    if (mode < 0 || mode >= FDTD_LAUNCH_MODES) return fail(ctx, FDTD_EINVAL, "launch mode must be 0, 1, 2 or 3");
     ctx->use_persistent = mode >= 1;
-    ctx->persist_prefetch = mode == 2;
+    ctx->persist_variant = mode >= 1 ? mode - 1 : 0;
     return FDTD_OK;
 }
 
 fdtd_status fdtd_get_launch_mode(fdtd_ctx* ctx, int32_t* mode) {
     GUARD(ctx);
     if (!mode) return FDTD_EINVAL;
-    *mode = ctx->use_persistent ? (ctx->persist_prefetch ? 2 : 1) : 0;
+    *mode = ctx->use_persistent ? 1 + ctx->persist_variant : 0;
     return FDTD_OK;
 }
 
@@ -1261,18 +1459,35 @@ fdtd_status fdtd_autotune(fdtd_ctx* ctx, int32_t n_steps, double* ms_per_mode) {
     GUARD(ctx);
     if (n_steps < 1) return fail(ctx, FDTD_EINVAL, "n_steps must be >= 1");
     const int slot = 1 << 30;   // private slot id (public ids are below 2^30)
-    const int dft = ctx->dft_enabled, energy = ctx->energy_on;
+    const int energy = ctx->energy_on;
     const long long step0 = ctx->step;
-    ctx->dft_enabled = 0;
     ctx->energy_on = 0;
     fdtd_status st = FDTD_OK;
     double best = 1e30;
     int best_mode = 1;
+    // the trials run with DFT recording as configured (its cost shapes the ranking); the monitor
+    // accumulators are copied aside first and put back after every trial
+    std::vector<std::pair<void*, size_t>> saved;
+    auto put_back = [&]() -> fdtd_status {
+        for (size_t q = 0; q < saved.size(); ++q)
+            CK(ctx, cudaMemcpyAsync(ctx->mons[q].m.acc, saved[q].first, saved[q].second, cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
+        return FDTD_OK;
+    };
+    for (auto& mh : ctx->mons) {
+        const size_t bytes = (size_t)mh.m.ncomp * mh.m.nf * mh.m.ncell * sizeof(double2);
+        void* p = nullptr;
+        if (st == FDTD_OK) st = dmalloc(ctx, &p, bytes);
+        if (st == FDTD_OK)
+            if (cudaMemcpyAsync(p, mh.m.acc, bytes, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+                st = fail(ctx, FDTD_ECUDA, "saving the DFT accumulators failed");
+        saved.push_back({p, bytes});
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    if (st == FDTD_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = fail(ctx, FDTD_ECUDA, "cudaEventCreate failed");
     if (st == FDTD_OK) st = save_slot(ctx, slot, FDTD_CODEC_NATIVE);
-    for (int mode = 0; mode < 3 && st == FDTD_OK; ++mode) {
+    for (int mode = 0; mode < FDTD_LAUNCH_MODES && st == FDTD_OK; ++mode) {
         fdtd_set_launch_mode(ctx, mode);
         // warm-up: graph capture, first-touch of the persistent kernel, caches
         st = fdtd_step_forward(ctx, n_steps < kGraphSteps ? n_steps : kGraphSteps);
@@ -1295,15 +1510,16 @@ fdtd_status fdtd_autotune(fdtd_ctx* ctx, int32_t n_steps, double* ms_per_mode) {
         }
         st = restore_slot(ctx, slot);
     }
+    if (st == FDTD_OK) st = put_back();
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaStreamSynchronize(ctx->stream);
+    for (auto& sv : saved) dfree(ctx, sv.first);
     auto it = ctx->slots.find(slot);
     if (it != ctx->slots.end()) {
         cudaFree(it->second.buf);
         ctx->slots.erase(it);
     }
-    ctx->dft_enabled = dft;
     ctx->energy_on = energy;
     ctx->step = step0;
     if (st != FDTD_OK) return st;
@@ -1638,7 +1854,8 @@ fdtd_status fdtd_synchronize(fdtd_ctx* ctx, int32_t timeout_ms) {
         if (e == cudaSuccess) {
             GridSync gs;
             CK(ctx, cudaMemcpy(&gs, ctx->d_sync, sizeof(gs), cudaMemcpyDeviceToHost));
-            if (gs.err) return fail(ctx, FDTD_ETIMEOUT, "a grid barrier of the persistent step kernel ran out");
+            if (gs.err == 1) return fail(ctx, FDTD_ETIMEOUT, "a grid barrier of the persistent step kernel ran out");
+            if (gs.err) return fail(ctx, FDTD_ETIMEOUT, "a staged plane copy of the persistent step kernel never completed");
             return FDTD_OK;
         }
         if (e != cudaErrorNotReady) return fail(ctx, FDTD_ECUDA, std::string("stream: ") + cudaGetErrorString(e));

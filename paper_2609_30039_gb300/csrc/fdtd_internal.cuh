@@ -20,8 +20,24 @@ namespace gbfdtd {
 constexpr int kMaxPole = 16;
 constexpr int kMaxMonPerDom = 8;
 constexpr int kMaxSrcPerDom = 8;
-constexpr int kTileX = 32;
+constexpr int kTileX = 32;    // block shape (threads): one warp per row of a 32-wide tile
 constexpr int kTileY = 8;
+// Interior tiles may be wider than a warp (same 256 threads, kIntX x kIntY columns): rows of
+// kIntX consecutive x give the DRAM longer contiguous runs per array and plane.
+#ifndef GBFDTD_INT_X
+#define GBFDTD_INT_X 32
+#endif
+constexpr int kIntX = GBFDTD_INT_X;
+constexpr int kIntY = kTileX * kTileY / kIntX;
+// Plane box of the TMA-staged interior tiles: one array, one z-plane, kTmaBoxX x kTmaBoxY
+// elements.  x starts at the tile's first column minus one, rounded down to a 16-byte
+// boundary (at most 4 elements earlier), so kIntX + 4 columns cover the tile, its -1 / +1 halo
+// and the round-down; kIntY + 1 rows cover the tile and its -1 (E update) or +1 (H update) halo
+// row.  A box row is at most 256 elements, so the widest interior tiles cannot be staged.
+constexpr int kTmaBoxX = kIntX + 4;
+constexpr int kTmaBoxY = kIntY + 1;
+constexpr bool kTmaFits = kTmaBoxX <= 256;
+constexpr int kTmaMaps = 9;   // Ex Ey Ez Hx Hy Hz, eps^-1 x y z
 
 template <typename T>
 struct Dom {
@@ -54,6 +70,8 @@ struct Dom {
     int src[kMaxSrcPerDom];
     double* energy;            // per-step energy or nullptr
     int energy_cap;
+    const void* tmaps;         // kTmaMaps CUtensorMap (device memory) or nullptr
+    int tma;                   // 1 if the maps are valid (the TMA-staged interior path may run)
 };
 
 // A running DFT monitor (Sec. 2.4).  acc / cot: [ncomp][nf][ncell] double2.
@@ -73,6 +91,12 @@ struct Mon {
     int cap;
 };
 
+// A DFT work item: cells [begin, begin + 256) of monitor `mon` (one thread per cell).
+struct DftItem {
+    int mon;
+    int begin;
+};
+
 struct Src {
     int dom, comp;
     int lo[3], hi[3];
@@ -86,7 +110,7 @@ struct Src {
 enum : int {
     kTileSrcE = 1,   // holds a cell of an electric soft source
     kTileSrcH = 2,   // ... of a magnetic soft source
-    kTileMonE = 4,   // holds a cell of a monitor recording an E component
+    kTileMonE = 4,   // holds a cell of a monitor recording an E component (objective injection)
     kTileMonH = 8,   // ... an H component
     kTileGeneral = 16 // needs the CPML / PEC / pole code path
 };
@@ -109,6 +133,7 @@ struct Tile {
     int z0, z1;
     int flags;
     int x0, y0;   // first column (for flag tests)
+    int lw;       // log2 of the row width in threads (5: 32 x 8 tiles; interior tiles: log2 kIntX)
 };
 
 // Coordinate of lane `l` of a two-segment range, or -1 past its end.
@@ -117,6 +142,14 @@ __host__ __device__ inline int seg_coord(const int* s, int l) {
     if (l < n1) return s[0] + l;
     const int x = s[2] + (l - n1);
     return x < s[3] ? x : -1;
+}
+
+// Column (i, j) of this thread in tile t (-1 where the thread has no column): thread number
+// tid = threadIdx.y * kTileX + threadIdx.x, lane tid mod 2^lw along x, row tid / 2^lw along y.
+__device__ __forceinline__ void tile_coords(const Tile& t, int& i, int& j) {
+    const int tid = threadIdx.y * kTileX + threadIdx.x;
+    i = seg_coord(t.xs, tid & ((1 << t.lw) - 1));
+    j = seg_coord(t.ys, tid >> t.lw);
 }
 
 __host__ __device__ inline long long cidx(const int* n, int i, int j, int k) {
@@ -162,19 +195,29 @@ struct StepArgs {
     int* d_step;
     unsigned* d_ticket;
     int dft_on;
+    const DftItem* dft_items;   // DFT work items of every monitor (persistent kernel)
+    int ndft;
 };
 
 template <typename T>
 void launch_e_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
                      int general, int aniso);
+// advance: total blocks of the step's H launches that count towards advancing the step counter
+// (0: this launch does not advance it)
 template <typename T>
 void launch_h_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
-                     int general, int energy, int advance);
+                     int general, int energy, unsigned advance);
 void launch_advance(const Launch& L, int* d_step, int delta);
+// DFT of one kind (0: E, 1: H) for every monitor work item, at step *d_base + offset.
+template <typename T>
+void launch_dft(const Launch& L, const Dom<T>* doms, const Mon* mons, const DftItem* items, int nitems, int kind,
+                const int* d_base, int offset);
+void launch_copy_int(const Launch& L, const int* src, int* dst);
 // Persistent cooperative launch advancing nsteps forward steps over all tiles (general first).
+// variant: 0 register path, 1 one-plane register prefetch, 2 TMA-staged interior tiles.
 template <typename T>
 cudaError_t launch_steps(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
-                         int nsteps, int aniso, int energy, int prefetch, GridSync* gs, int* grid_used);
+                         int nsteps, int aniso, int energy, int variant, GridSync* gs, int* grid_used);
 
 // Adjoint kernels (kernels_adj.cu)
 template <typename T>

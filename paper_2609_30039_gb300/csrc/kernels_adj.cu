@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
     const Tile t = tiles[blockIdx.x];
     const Dom<T>& d = doms[t.dom];
     const int nx = d.n[0], ny = d.n[1];
-    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    int i, j;
+    tile_coords(t, i, j);
     if (i < 0 || j < 0) return;
     const long long nxy = (long long)nx * ny;
     T* A0 = d.A[0];
@@ -287,7 +288,8 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
     const Tile t = tiles[blockIdx.x];
     const Dom<T>& d = doms[t.dom];
     const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
-    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    int i, j;
+    tile_coords(t, i, j);
     if (i < 0 || j < 0) return;
     const long long nxy = (long long)nx * ny;
     const T* A0 = d.A[0];
@@ -388,15 +390,26 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
 // k_adj_h_int is Hbar += C^+ F.  Loads of a plane are issued before its stores; the z-1
 // (z+1) neighbours are carried in registers.  The design-box gradient and the monitor
 // injection keep their per-cell checks.
+// Interior transposed kernels: bounded so that 4 (FP32) / 3 (FP64) blocks of 256 threads fit an
+// SM; left unbounded they take ~140 registers (one block per SM) and starve the memory system.
+#ifndef GBFDTD_ADJ_INT_BLOCKS_F32
+#define GBFDTD_ADJ_INT_BLOCKS_F32 4
+#endif
+template <typename T>
+constexpr int adj_int_blocks() {
+    return sizeof(T) == 4 ? GBFDTD_ADJ_INT_BLOCKS_F32 : 3;
+}
+
 template <typename T, bool kAniso>
-__global__ void __launch_bounds__(kTileX* kTileY) k_adj_e_int(const Dom<T>* __restrict__ doms,
+__global__ void __launch_bounds__(kTileX* kTileY, adj_int_blocks<T>()) k_adj_e_int(const Dom<T>* __restrict__ doms,
                                                               const Mon* __restrict__ mons,
                                                               const Tile* __restrict__ tiles, T S, int m,
                                                               int pending) {
     const Tile t = tiles[blockIdx.x];
     const Dom<T>& d = doms[t.dom];
     const int nx = d.n[0], ny = d.n[1];
-    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    int i, j;
+    tile_coords(t, i, j);
     if (i < 0 || j < 0) return;
     const long long nxy = (long long)nx * ny;
     T* Fx = d.A[0];
@@ -456,13 +469,14 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_adj_e_int(const Dom<T>* __re
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTileX* kTileY) k_adj_h_int(const Dom<T>* __restrict__ doms,
+__global__ void __launch_bounds__(kTileX* kTileY, adj_int_blocks<T>()) k_adj_h_int(const Dom<T>* __restrict__ doms,
                                                               const Mon* __restrict__ mons,
                                                               const Tile* __restrict__ tiles, T S, int m) {
     const Tile t = tiles[blockIdx.x];
     const Dom<T>& d = doms[t.dom];
     const int nx = d.n[0], ny = d.n[1];
-    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    int i, j;
+    tile_coords(t, i, j);
     if (i < 0 || j < 0) return;
     const long long nxy = (long long)nx * ny;
     const T* Fx = d.A[0];
@@ -501,7 +515,8 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_adj_flush(const Dom<T>* __re
                                                               const Tile* __restrict__ tiles, T S) {
     const Tile t = tiles[blockIdx.x];
     const Dom<T>& d = doms[t.dom];
-    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    int i, j;
+    tile_coords(t, i, j);
     if (i < 0 || j < 0) return;
     for (int k = t.z0; k < t.z1; ++k) {
         const int c[3] = {i, j, k};

@@ -9,6 +9,7 @@
 // flags mark the tiles that hold source or monitor cells), so a forward step is two kernels per
 // tile class and a CUDA graph of them replays without host work.
 #include "fdtd_internal.cuh"
+#include "tma_ptx.cuh"
 
 namespace gbfdtd {
 
@@ -80,44 +81,85 @@ __device__ __forceinline__ T src_add(const Dom<T>& d, const Src* __restrict__ sr
     return add;
 }
 
-// Running DFT (Sec. 2.4) of the three E (kind 0, t = n+1) or H (kind 1, t = n+3/2) components of
-// one cell: F += f exp(i w t), accumulated in FP64.
+// Running DFT (Sec. 2.4), F += f exp(i w t) accumulated in FP64, of one work item: up to 256
+// consecutive cells of one monitor (one per thread), for the recorded components of one kind
+// (0: E at t = n+1, 1: H at t = n+3/2).  It runs beside the field updates, never on their
+// critical path: the E part of step n while H is updated, the H part while E of step n+1 is (each
+// only reads the field the other half-step leaves alone).  A cell's accumulators are updated in
+// batches of four, loads before stores, one memory round trip per batch.
 template <typename T>
-__device__ __forceinline__ void dft_cell(const Dom<T>& d, const Mon* __restrict__ mons, int kind, int i, int j, int k,
-                                         int step, T v0, T v1, T v2) {
-    for (int mm = 0; mm < d.nmon; ++mm) {
-        const Mon& m = mons[d.mon[mm]];
-        if (i < m.lo[0] || i >= m.hi[0] || j < m.lo[1] || j >= m.hi[1] || k < m.lo[2] || k >= m.hi[2]) continue;
-        const long long cell = ((long long)(k - m.lo[2]) * m.by + (j - m.lo[1])) * m.bx + (i - m.lo[0]);
-        const double2* ph = m.phase + ((long long)step * 2 + kind) * m.nf;
-        int ci = 0;
-        for (int c = 0; c < 6; ++c) {
-            if (!((m.mask >> c) & 1u)) continue;
-            if (c / 3 == kind) {
-                const double v = (double)(c % 3 == 0 ? v0 : (c % 3 == 1 ? v1 : v2));
-                double2* acc = m.acc + (long long)ci * m.nf * m.ncell + cell;
-                for (int f = 0; f < m.nf; ++f) {
-                    const double2 p = ph[f];
-                    double2 a = acc[(long long)f * m.ncell];
-                    a.x += v * p.x;
-                    a.y += v * p.y;
-                    acc[(long long)f * m.ncell] = a;
+__device__ __forceinline__ void dft_item(const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons,
+                                         const DftItem& it, int kind, int step) {
+    const Mon& m = mons[it.mon];
+    const long long cell = it.begin + threadIdx.y * kTileX + threadIdx.x;
+    if (cell >= m.ncell) return;
+    const int i = m.lo[0] + (int)(cell % m.bx);
+    const int j = m.lo[1] + (int)((cell / m.bx) % m.by);
+    const int k = m.lo[2] + (int)(cell / ((long long)m.bx * m.by));
+    const Dom<T>& d = doms[m.dom];
+    const long long id = cidx(d.n, i, j, k);
+    const double2* ph = m.phase + ((long long)step * 2 + kind) * m.nf;
+    const int nf = m.nf;
+    int ci = 0;
+    for (int c = 0; c < 6; ++c) {
+        if (!((m.mask >> c) & 1u)) continue;
+        if (c / 3 == kind) {
+            const double v = (double)d.F[c][id];
+            double2* acc = m.acc + (long long)ci * nf * m.ncell + cell;
+            for (int f0 = 0; f0 < nf; f0 += 4) {
+                double2 x[4], p[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int f = f0 + q < nf ? f0 + q : f0;
+                    x[q] = acc[(long long)f * m.ncell];
+                    p[q] = ph[f];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (f0 + q >= nf) break;
+                    x[q].x += v * p[q].x;
+                    x[q].y += v * p[q].y;
+                    acc[(long long)(f0 + q) * m.ncell] = x[q];
                 }
             }
-            ++ci;
         }
+        ++ci;
     }
 }
 
+// Per-half-step DFT launch: one block per work item; the step is *d_base + offset (the first
+// step of the launched batch plus this launch's position in it, so a captured graph replays).
 template <typename T>
-constexpr int min_blocks(bool general) {
-    return general ? (sizeof(T) == 4 ? 4 : 2) : (sizeof(T) == 4 ? 4 : 3);
+__global__ void __launch_bounds__(kTileX* kTileY)
+    k_dft(const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, const DftItem* __restrict__ items, int kind,
+          const int* __restrict__ d_base, int offset) {
+    dft_item(doms, mons, items[blockIdx.x], kind, *d_base + offset);
 }
 
-// the persistent kernel holds both code paths; the prefetch variant needs more registers
-template <typename T, bool kPrefetch>
+__global__ void k_copy_int(const int* __restrict__ src, int* __restrict__ dst) { *dst = *src; }
+
+// Blocks per SM the per-launch kernels are compiled for.  Interior tiles run the plain register
+// path at full occupancy (8 blocks of 256 threads in FP32, at most 32 registers): the warps in
+// flight are what keeps enough loads outstanding to approach the DRAM bandwidth.
+#ifndef GBFDTD_INT_BLOCKS_F32
+#define GBFDTD_INT_BLOCKS_F32 8
+#endif
+template <typename T>
+constexpr int min_blocks(bool general) {
+    return general ? (sizeof(T) == 4 ? 4 : 2) : (sizeof(T) == 4 ? GBFDTD_INT_BLOCKS_F32 : 4);
+}
+
+#ifndef GBFDTD_TMA_STAGES_F32
+#define GBFDTD_TMA_STAGES_F32 4
+#endif
+#ifndef GBFDTD_TMA_BLOCKS_F32
+#define GBFDTD_TMA_BLOCKS_F32 4
+#endif
+// the persistent kernel holds both code paths; the prefetch variant (1) needs more registers,
+// the TMA variant (2) ~51 KB (FP32) / ~71 KB (FP64) of shared memory per block
+template <typename T, int kVar>
 constexpr int min_blocks_persistent() {
-    return sizeof(T) == 4 ? (kPrefetch ? 3 : 4) : 2;
+    return sizeof(T) == 4 ? (kVar == 1 ? 3 : (kVar == 2 ? GBFDTD_TMA_BLOCKS_F32 : 4)) : 2;
 }
 
 // E half-step (Eq. (yee) first half) of a tile.  kGen = false: the tile touches no CPML slab,
@@ -130,10 +172,10 @@ __device__ __forceinline__ void tile_e_int(const Dom<T>* __restrict__ doms, cons
                                            int step) {
     const Dom<T>& d = doms[t.dom];
     const int nx = d.n[0], ny = d.n[1];
-    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    int i, j;
+    tile_coords(t, i, j);
     if (i < 0 || j < 0) return;
     const bool fsrc = t.flags & kTileSrcE;
-    const bool fmon = a.dft_on && (t.flags & kTileMonE);
     const long long nxy = (long long)nx * ny;
     T* Ex = d.F[0];
     T* Ey = d.F[1];
@@ -183,7 +225,6 @@ __device__ __forceinline__ void tile_e_int(const Dom<T>* __restrict__ doms, cons
         Ex[id] = ex;
         Ey[id] = ey;
         Ez[id] = ez;
-        if (fmon) dft_cell(d, a.mons, 0, i, j, k, step, ex, ey, ez);
         hxz = hx;
         hyz = hy;
         hx = nhx; hy = nhy; hz = nhz;
@@ -200,9 +241,9 @@ __device__ __forceinline__ void tile_h_int(const Dom<T>* __restrict__ doms, cons
                                            int step) {
     const Dom<T>& d = doms[t.dom];
     const int nx = d.n[0], ny = d.n[1];
-    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    int i, j;
+    tile_coords(t, i, j);
     const bool fsrc = t.flags & kTileSrcH;
-    const bool fmon = a.dft_on && (t.flags & kTileMonH);
     double w = 0.0;
     if (i >= 0 && j >= 0) {
         const long long nxy = (long long)nx * ny;
@@ -245,7 +286,6 @@ __device__ __forceinline__ void tile_h_int(const Dom<T>* __restrict__ doms, cons
             Hx[id] = hx1;
             Hy[id] = hy1;
             Hz[id] = hz1;
-            if (fmon) dft_cell(d, a.mons, 1, i, j, k, step, hx1, hy1, hz1);
             if (kEnergy) {
                 w += 0.5 * ((double)hx * hx1 + (double)hy * hy1 + (double)hz * hz1);
                 w += 0.5 * ((double)exk * exk / (double)d.ie[0][id] + (double)eyk * eyk / (double)d.ie[1][id] +
@@ -270,10 +310,10 @@ __device__ __forceinline__ void tile_e(const Dom<T>* __restrict__ doms, const Ti
                                        int step) {
     const Dom<T>& d = doms[t.dom];
     const int nx = d.n[0], ny = d.n[1];
-    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    int i, j;
+    tile_coords(t, i, j);
     if (i < 0 || j < 0) return;
     const bool fsrc = t.flags & kTileSrcE;
-    const bool fmon = a.dft_on && (t.flags & kTileMonE);
     const long long nxy = (long long)nx * ny;
     T* Ex = d.F[0];
     T* Ey = d.F[1];
@@ -365,17 +405,13 @@ __device__ __forceinline__ void tile_e(const Dom<T>* __restrict__ doms, const Ti
             Ey[id] = ey;
             Ez[id] = ez;
         }
-        if (fmon) dft_cell(d, a.mons, 0, i, j, k, step, ex, ey, ez);
     }
 }
 
 template <typename T, bool kGen, bool kAniso>
 __global__ void __launch_bounds__(kTileX* kTileY, min_blocks<T>(kGen))
     k_e_update(const Dom<T>* __restrict__ doms, const Tile* __restrict__ tiles, T S, const StepArgs a) {
-    if (kGen)
-        tile_e<T, true, kAniso>(doms, tiles[blockIdx.x], S, a, *a.d_step);
-    else
-        tile_e_int<T, kAniso>(doms, tiles[blockIdx.x], S, a, *a.d_step);
+    tile_e<T, kGen, kAniso>(doms, tiles[blockIdx.x], S, a, *a.d_step);
 }
 
 // H half-step (Eq. (yee) second half) of a tile; E_x, E_y of plane k+1 are carried to the next
@@ -385,9 +421,9 @@ __device__ __forceinline__ void tile_h(const Dom<T>* __restrict__ doms, const Ti
                                        int step) {
     const Dom<T>& d = doms[t.dom];
     const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
-    const int i = seg_coord(t.xs, threadIdx.x), j = seg_coord(t.ys, threadIdx.y);
+    int i, j;
+    tile_coords(t, i, j);
     const bool fsrc = t.flags & kTileSrcH;
-    const bool fmon = a.dft_on && (t.flags & kTileMonH);
     double w = 0.0;
     if (i >= 0 && j >= 0) {
         const long long nxy = (long long)nx * ny;
@@ -449,7 +485,6 @@ __device__ __forceinline__ void tile_h(const Dom<T>* __restrict__ doms, const Ti
             Hx[id] = hx1;
             Hy[id] = hy1;
             Hz[id] = hz1;
-            if (fmon) dft_cell(d, a.mons, 1, i, j, k, step, hx1, hy1, hz1);
             if (kEnergy) {
                 w += 0.5 * ((double)hx * hx1 + (double)hy * hy1 + (double)hz * hz1);
                 w += 0.5 * ((double)exk * exk / (double)d.ie[0][id] + (double)eyk * eyk / (double)d.ie[1][id] +
@@ -467,25 +502,228 @@ __device__ __forceinline__ void tile_h(const Dom<T>* __restrict__ doms, const Ti
 
 template <typename T, bool kGen, bool kEnergy>
 __global__ void __launch_bounds__(kTileX* kTileY, min_blocks<T>(kGen))
-    k_h_update(const Dom<T>* __restrict__ doms, const Tile* __restrict__ tiles, T S, const StepArgs a, int advance) {
+    k_h_update(const Dom<T>* __restrict__ doms, const Tile* __restrict__ tiles, T S, const StepArgs a,
+               unsigned advance_blocks) {
     const int step = *a.d_step;
-    if (kGen)
-        tile_h<T, true, kEnergy>(doms, tiles[blockIdx.x], S, a, step);
-    else
-        tile_h_int<T, kEnergy>(doms, tiles[blockIdx.x], S, a, step);
-    if (advance) {
-        // the last block to finish advances the device step counter (every block has read it)
+    tile_h<T, kGen, kEnergy>(doms, tiles[blockIdx.x], S, a, step);
+    if (advance_blocks) {
+        // the H launches of a step (general and interior, possibly running concurrently) hold
+        // advance_blocks blocks together; the last of them to finish advances the device step
+        // counter (every block has read it)
         __syncthreads();
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             __threadfence();
             const unsigned done = atomicAdd(a.d_ticket, 1u);
-            if (done == gridDim.x - 1) {
+            if (done == advance_blocks - 1) {
                 *a.d_ticket = 0u;
                 *a.d_step = step + 1;
                 __threadfence();
             }
         }
     }
+}
+
+// ---- TMA-staged interior tiles ---------------------------------------------------------------
+// One elected thread copies every operand array of a z-plane of the tile (a kTmaBoxX x kTmaBoxY
+// box per array, see fdtd_internal.cuh) into a ring of kStages shared-memory stages with tiled
+// bulk tensor copies; each stage completes on its own mbarrier.  While the block computes plane
+// k, planes k+1 .. k+kStages-1 are in flight, so the memory-level parallelism no longer depends
+// on registers or on the number of resident warps.  A stage is refilled only after a block
+// barrier has shown that every thread is done with it.  `seq` counts the planes this block has
+// staged so far: stage = seq % kStages and the mbarrier phase parity = (seq / kStages) & 1.
+template <typename T>
+constexpr int tma_stages() {
+    return sizeof(T) == 4 ? GBFDTD_TMA_STAGES_F32 : 3;
+}
+template <typename T>
+constexpr int tma_box_bytes() {
+    return kTmaBoxX * kTmaBoxY * (int)sizeof(T);
+}
+template <typename T>
+constexpr int tma_slot_elems() {   // one box slot, padded to 128 bytes
+    return ((tma_box_bytes<T>() + 127) / 128 * 128) / (int)sizeof(T);
+}
+template <typename T>
+constexpr int tma_smem_bytes() {   // stages, their mbarriers, and the alignment slack
+    return tma_stages<T>() * kTmaMaps * tma_slot_elems<T>() * (int)sizeof(T) + 8 * tma_stages<T>() + 128;
+}
+
+struct TmaRing {
+    unsigned smem;   // shared address of stage 0, slot 0
+    unsigned bar0;   // shared address of the first mbarrier (8 bytes each)
+    unsigned seq;    // planes staged so far by this block
+};
+
+// Copies plane z of `nbox` arrays (maps 0 .. nbox-1) into the stage of sequence number g.
+template <typename T>
+__device__ __forceinline__ void tma_issue_plane(const TmaRing& r, const void* maps, int nbox, unsigned g, int x, int y,
+                                                int z) {
+    constexpr int NS = tma_stages<T>();
+    const unsigned s = g % NS;
+    const unsigned bar = r.bar0 + 8u * s;
+    const unsigned base = r.smem + s * (unsigned)(kTmaMaps * tma_slot_elems<T>() * sizeof(T));
+    mbar_arrive_expect(bar, (unsigned)(nbox * tma_box_bytes<T>()));
+    const char* m = (const char*)maps;
+    for (int b = 0; b < nbox; ++b)
+        tma_load_3d(base + (unsigned)(b * tma_slot_elems<T>() * sizeof(T)), m + 128 * b, x, y, z, bar);
+}
+
+// After a wait ran out: give the copies issued but not yet seen complete (sequence numbers
+// [from, to)) a bounded chance to land before the block leaves.
+template <typename T>
+__device__ __forceinline__ void tma_drain(const TmaRing& r, unsigned from, unsigned to) {
+    constexpr int NS = tma_stages<T>();
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        for (unsigned g = from; g < to; ++g) mbar_wait(r.bar0 + 8u * (g % NS), (g / NS) & 1u);
+    __syncthreads();
+}
+
+// E half-step of an interior tile with staged planes.  Box origin (bx, y0 - 1, k): the thread of
+// column (i, j) = (x0 + tx, y0 + ty) finds its cell at box row ty + 1, column i - bx, and the
+// -x / -y neighbours one element / one row before it.  Returns false if a stage never completed.
+template <typename T, bool kAniso>
+__device__ __forceinline__ bool tile_e_tma(const Dom<T>& d, const Tile& t, T S, const StepArgs& a, int step,
+                                           TmaRing& r) {
+    constexpr int NS = tma_stages<T>();
+    constexpr int P = tma_slot_elems<T>();
+    const int nx = d.n[0], ny = d.n[1];
+    const int tid = threadIdx.y * kTileX + threadIdx.x;
+    const int tx = tid % kIntX, ty = tid / kIntX;   // interior tiles are kIntX x kIntY columns
+    const int i = t.xs[0] + tx, j = t.ys[0] + ty;
+    const bool act = i < t.xs[1] && j < t.ys[1];
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    const int bx = (t.xs[0] - 1) & ~3, by = t.ys[0] - 1;
+    const int np = t.z1 - t.z0;
+    const int nbox = kAniso ? 9 : 7;
+    const bool fsrc = t.flags & kTileSrcE;
+    const long long nxy = (long long)nx * ny;
+    const unsigned g0 = r.seq;
+    if (lead) {
+        fence_proxy_async_global();
+        for (int p = 0; p < NS && p < np; ++p) tma_issue_plane<T>(r, d.tmaps, nbox, g0 + p, bx, by, t.z0 + p);
+    }
+    T hxz = T(0), hyz = T(0);
+    long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
+    if (act) {
+        hxz = d.F[3][id - nxy];
+        hyz = d.F[4][id - nxy];
+    }
+    const int c = (ty + 1) * kTmaBoxX + (i - bx);
+    const T* stage0 = (const T*)__cvta_shared_to_generic(r.smem);
+    for (int p = 0; p < np; ++p, id += nxy) {
+        const unsigned g = g0 + p;
+        const bool got = mbar_wait(r.bar0 + 8u * (g % NS), (g / NS) & 1u);
+        if (act && got) {
+            const T* st = stage0 + (size_t)(g % NS) * kTmaMaps * P;
+            const T* sEx = st;
+            const T* sEy = st + P;
+            const T* sEz = st + 2 * P;
+            const T* sHx = st + 3 * P;
+            const T* sHy = st + 4 * P;
+            const T* sHz = st + 5 * P;
+            const T hx = sHx[c], hy = sHy[c], hz = sHz[c];
+            const T iex = st[6 * P + c];
+            const T iey = kAniso ? st[7 * P + c] : iex;
+            const T iez = kAniso ? st[8 * P + c] : iex;
+            const int k = t.z0 + p;
+            T ex = sEx[c] + S * iex * ((hz - sHz[c - kTmaBoxX]) - (hy - hyz));
+            T ey = sEy[c] + S * iey * ((hx - hxz) - (hz - sHz[c - 1]));
+            T ez = sEz[c] + S * iez * ((hy - sHy[c - 1]) - (hx - sHx[c - kTmaBoxX]));
+            if (fsrc) {
+                ex += src_add(d, a.srcs, 0, i, j, k, step);
+                ey += src_add(d, a.srcs, 1, i, j, k, step);
+                ez += src_add(d, a.srcs, 2, i, j, k, step);
+            }
+            d.F[0][id] = ex;
+            d.F[1][id] = ey;
+            d.F[2][id] = ez;
+            hxz = hx;
+            hyz = hy;
+        }
+        if (__syncthreads_or(!got)) {
+            tma_drain<T>(r, g, g0 + (np < p + NS ? np : p + NS));   // planes issued so far
+            r.seq = g0 + np;
+            return false;
+        }
+        if (lead && p + NS < np) tma_issue_plane<T>(r, d.tmaps, nbox, g + NS, bx, by, t.z0 + p + NS);
+    }
+    r.seq = g0 + np;
+    return true;
+}
+
+// H half-step of an interior tile with staged planes.  Box origin (bx, y0, k): the cell sits at
+// box row ty, column i - bx; the +x / +y neighbours one element / one row after it.  Planes
+// z0 .. z1 are staged (plane k+1 supplies E_x, E_y of the z-differences), six arrays each.
+template <typename T, bool kEnergy>
+__device__ __forceinline__ bool tile_h_tma(const Dom<T>& d, const Tile& t, T S, const StepArgs& a, int step,
+                                           TmaRing& r) {
+    constexpr int NS = tma_stages<T>();
+    constexpr int P = tma_slot_elems<T>();
+    const int nx = d.n[0], ny = d.n[1];
+    const int tid = threadIdx.y * kTileX + threadIdx.x;
+    const int tx = tid % kIntX, ty = tid / kIntX;   // interior tiles are kIntX x kIntY columns
+    const int i = t.xs[0] + tx, j = t.ys[0] + ty;
+    const bool act = i < t.xs[1] && j < t.ys[1];
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    const int bx = t.xs[0] & ~3, by = t.ys[0];
+    const int nz = t.z1 - t.z0;       // planes computed
+    const int np = nz + 1;            // planes staged
+    const bool fsrc = t.flags & kTileSrcH;
+    const long long nxy = (long long)nx * ny;
+    const unsigned g0 = r.seq;
+    if (lead) {
+        fence_proxy_async_global();
+        for (int p = 0; p < NS && p < np; ++p) tma_issue_plane<T>(r, d.tmaps, 6, g0 + p, bx, by, t.z0 + p);
+    }
+    const int c = ty * kTmaBoxX + (i - bx);
+    const T* stage0 = (const T*)__cvta_shared_to_generic(r.smem);
+    long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
+    double w = 0.0;
+    bool ok = true;
+    for (int p = 0; p < nz; ++p, id += nxy) {
+        const unsigned g = g0 + p;
+        bool got = mbar_wait(r.bar0 + 8u * (g % NS), (g / NS) & 1u);
+        got = got && mbar_wait(r.bar0 + 8u * ((g + 1) % NS), ((g + 1) / NS) & 1u);
+        if (act && got) {
+            const T* st = stage0 + (size_t)(g % NS) * kTmaMaps * P;
+            const T* sn = stage0 + (size_t)((g + 1) % NS) * kTmaMaps * P;
+            const T* sEx = st;
+            const T* sEy = st + P;
+            const T* sEz = st + 2 * P;
+            const T exk = sEx[c], eyk = sEy[c], ez = sEz[c];
+            const T hx = st[3 * P + c], hy = st[4 * P + c], hz = st[5 * P + c];
+            const T exn = sn[c], eyn = sn[P + c];
+            const int k = t.z0 + p;
+            T hx1 = hx - S * ((sEz[c + kTmaBoxX] - ez) - (eyn - eyk));
+            T hy1 = hy - S * ((exn - exk) - (sEz[c + 1] - ez));
+            T hz1 = hz - S * ((sEy[c + 1] - eyk) - (sEx[c + kTmaBoxX] - exk));
+            if (fsrc) {
+                hx1 += src_add(d, a.srcs, 3, i, j, k, step);
+                hy1 += src_add(d, a.srcs, 4, i, j, k, step);
+                hz1 += src_add(d, a.srcs, 5, i, j, k, step);
+            }
+            d.F[3][id] = hx1;
+            d.F[4][id] = hy1;
+            d.F[5][id] = hz1;
+            if (kEnergy) {
+                w += 0.5 * ((double)hx * hx1 + (double)hy * hy1 + (double)hz * hz1);
+                w += 0.5 * ((double)exk * exk / (double)d.ie[0][id] + (double)eyk * eyk / (double)d.ie[1][id] +
+                            (double)ez * ez / (double)d.ie[2][id]);
+            }
+        }
+        if (__syncthreads_or(!got)) {
+            tma_drain<T>(r, g, g0 + (np < p + NS ? np : p + NS));   // planes issued so far
+            ok = false;
+            break;
+        }
+        if (lead && p + NS < np) tma_issue_plane<T>(r, d.tmaps, 6, g + NS, bx, by, t.z0 + p + NS);
+    }
+    r.seq = g0 + np;
+    if (kEnergy) {
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if ((threadIdx.x & 31) == 0 && d.energy && step < d.energy_cap) atomicAdd(d.energy + step, w);
+    }
+    return ok;
 }
 
 // ---- persistent step kernel ---------------------------------------------------------------
@@ -533,64 +771,112 @@ __device__ __forceinline__ int claim_tile(GridSync* gs, unsigned long long base)
     return t;
 }
 
-template <typename T, bool kAniso, bool kEnergy, bool kPrefetch>
-__global__ void __launch_bounds__(kTileX* kTileY, min_blocks_persistent<T, kPrefetch>())
+template <typename T, bool kAniso, bool kEnergy, int kVar>
+__global__ void __launch_bounds__(kTileX* kTileY, min_blocks_persistent<T, kVar>())
     k_steps(const Dom<T>* __restrict__ doms, const Tile* __restrict__ tiles, int ntiles, T S, const StepArgs a,
             int nsteps, GridSync* gs) {
+    extern __shared__ unsigned char smem_dyn[];
+    TmaRing ring{0u, 0u, 0u};
+    if (kVar == 2) {
+        constexpr int NS = tma_stages<T>();
+        const unsigned base = (smem_u32(smem_dyn) + 127u) & ~127u;
+        ring.smem = base;
+        ring.bar0 = base + (unsigned)(NS * kTmaMaps * tma_slot_elems<T>() * sizeof(T));
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            for (int q = 0; q < NS; ++q) mbar_init(ring.bar0 + 8u * q, 1u);
+            mbar_init_fence();
+        }
+        __syncthreads();
+    }
     const int step0 = *a.d_step;
-    const unsigned long long per_phase = (unsigned long long)ntiles + gridDim.x;
+    // each phase claims the field tiles, then the DFT items of the field the phase leaves alone:
+    // the E phase of step s records H of step s-1, the H phase E of step s; a tail phase records
+    // H of the last step
+    const int ndft = a.dft_on ? a.ndft : 0;
+    const int nwork = ntiles + ndft;
+    const unsigned long long per_phase = (unsigned long long)nwork + gridDim.x;
     unsigned long long base = 0;
+    bool ok = true;
     for (int s = 0; s < nsteps; ++s) {
         const int step = step0 + s;
-        for (;;) {
+        while (ok) {
             const int t = claim_tile(gs, base);
-            if (t >= ntiles) break;
+            if (t >= nwork) break;
+            if (t >= ntiles) {
+                if (s > 0) dft_item(doms, a.mons, a.dft_items[t - ntiles], 1, step - 1);
+                continue;
+            }
             const Tile tl = tiles[t];
             if (tl.flags & kTileGeneral)
                 tile_e<T, true, true>(doms, tl, S, a, step);
-            else if (kPrefetch)
+            else if (kVar == 1)
                 tile_e_int<T, kAniso>(doms, tl, S, a, step);
+            else if (kVar == 2 && doms[tl.dom].tma)
+                ok = tile_e_tma<T, kAniso>(doms[tl.dom], tl, S, a, step, ring);
             else
                 tile_e<T, false, kAniso>(doms, tl, S, a, step);
         }
+        if (!ok && threadIdx.x == 0 && threadIdx.y == 0) atomicExch(&gs->err, 2);
+        if (kVar == 2) fence_proxy_async_global();   // these stores are TMA sources of the next phase
         base += per_phase;
         if (!grid_sync(gs, gridDim.x)) return;
-        for (;;) {
+        while (ok) {
             const int t = claim_tile(gs, base);
-            if (t >= ntiles) break;
+            if (t >= nwork) break;
+            if (t >= ntiles) {
+                dft_item(doms, a.mons, a.dft_items[t - ntiles], 0, step);
+                continue;
+            }
             const Tile tl = tiles[t];
             if (tl.flags & kTileGeneral)
                 tile_h<T, true, kEnergy>(doms, tl, S, a, step);
-            else if (kPrefetch)
+            else if (kVar == 1)
                 tile_h_int<T, kEnergy>(doms, tl, S, a, step);
+            else if (kVar == 2 && doms[tl.dom].tma)
+                ok = tile_h_tma<T, kEnergy>(doms[tl.dom], tl, S, a, step, ring);
             else
                 tile_h<T, false, kEnergy>(doms, tl, S, a, step);
         }
+        if (!ok && threadIdx.x == 0 && threadIdx.y == 0) atomicExch(&gs->err, 2);
+        if (kVar == 2) fence_proxy_async_global();
         base += per_phase;
         if (!grid_sync(gs, gridDim.x)) return;
+    }
+    while (ndft > 0 && nsteps > 0) {
+        const int t = claim_tile(gs, base);
+        if (t >= ndft) break;
+        dft_item(doms, a.mons, a.dft_items[t], 1, step0 + nsteps - 1);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *a.d_step = step0 + nsteps;
 }
 
+template <typename T, int kVar>
+static cudaError_t steps_fn(int aniso, int energy, void** fn) {
+    if (aniso)
+        *fn = energy ? (void*)k_steps<T, true, true, kVar> : (void*)k_steps<T, true, false, kVar>;
+    else
+        *fn = energy ? (void*)k_steps<T, false, true, kVar> : (void*)k_steps<T, false, false, kVar>;
+    const int smem = kVar == 2 ? tma_smem_bytes<T>() : 0;
+    return smem > 48 * 1024 ? cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) : cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_steps(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
-                         int nsteps, int aniso, int energy, int prefetch, GridSync* gs, int* grid_used) {
-    void* fn;
-    if (prefetch) {
-        if (aniso)
-            fn = energy ? (void*)k_steps<T, true, true, true> : (void*)k_steps<T, true, false, true>;
-        else
-            fn = energy ? (void*)k_steps<T, false, true, true> : (void*)k_steps<T, false, false, true>;
-    } else {
-        if (aniso)
-            fn = energy ? (void*)k_steps<T, true, true, false> : (void*)k_steps<T, true, false, false>;
-        else
-            fn = energy ? (void*)k_steps<T, false, true, false> : (void*)k_steps<T, false, false, false>;
-    }
+                         int nsteps, int aniso, int energy, int variant, GridSync* gs, int* grid_used) {
+    void* fn = nullptr;
+    cudaError_t e;
+    if (variant == 2)
+        e = steps_fn<T, 2>(aniso, energy, &fn);
+    else if (variant == 1)
+        e = steps_fn<T, 1>(aniso, energy, &fn);
+    else
+        e = steps_fn<T, 0>(aniso, energy, &fn);
+    if (e != cudaSuccess) return e;
+    const int smem = variant == 2 ? tma_smem_bytes<T>() : 0;
     int dev = 0, sms = 0, per = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kTileX * kTileY, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kTileX * kTileY, smem);
     if (e != cudaSuccess) return e;
     if (per < 1) return cudaErrorInvalidConfiguration;
     int grid = sms * per;
@@ -600,7 +886,7 @@ cudaError_t launch_steps(const Launch& L, const Dom<T>* doms, const Tile* tiles,
     if (e != cudaSuccess) return e;
     StepArgs aa = a;
     void* args[] = {(void*)&doms, (void*)&tiles, (void*)&ntiles, (void*)&S, (void*)&aa, (void*)&nsteps, (void*)&gs};
-    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTileX, kTileY), args, 0, L.stream);
+    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTileX, kTileY), args, (size_t)smem, L.stream);
     ++*L.counter;
     if (grid_used) *grid_used = grid;
     return e;
@@ -616,29 +902,36 @@ void launch_e_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int
     const dim3 b(kTileX, kTileY);
     if (general)
         k_e_update<T, true, true><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a);
-    else if (aniso)
-        k_e_update<T, false, true><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a);
     else
-        k_e_update<T, false, false><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a);
+        (aniso ? k_e_update<T, false, true> : k_e_update<T, false, false>)<<<ntiles, b, 0, L.stream>>>(doms, tiles, S,
+                                                                                                     a);
     ++*L.counter;
 }
 
 template <typename T>
 void launch_h_update(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
-                     int general, int energy, int advance) {
+                     int general, int energy, unsigned advance) {
     if (ntiles <= 0) return;
     const dim3 b(kTileX, kTileY);
-    if (general) {
-        if (energy)
-            k_h_update<T, true, true><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a, advance);
-        else
-            k_h_update<T, true, false><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a, advance);
-    } else {
-        if (energy)
-            k_h_update<T, false, true><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a, advance);
-        else
-            k_h_update<T, false, false><<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a, advance);
-    }
+    if (general)
+        (energy ? k_h_update<T, true, true> : k_h_update<T, true, false>)<<<ntiles, b, 0, L.stream>>>(doms, tiles, S, a,
+                                                                                                    advance);
+    else
+        (energy ? k_h_update<T, false, true> : k_h_update<T, false, false>)<<<ntiles, b, 0, L.stream>>>(
+            doms, tiles, S, a, advance);
+    ++*L.counter;
+}
+
+template <typename T>
+void launch_dft(const Launch& L, const Dom<T>* doms, const Mon* mons, const DftItem* items, int nitems, int kind,
+                const int* d_base, int offset) {
+    if (nitems <= 0) return;
+    k_dft<T><<<nitems, dim3(kTileX, kTileY), 0, L.stream>>>(doms, mons, items, kind, d_base, offset);
+    ++*L.counter;
+}
+
+void launch_copy_int(const Launch& L, const int* src, int* dst) {
+    k_copy_int<<<1, 1, 0, L.stream>>>(src, dst);
     ++*L.counter;
 }
 
@@ -650,10 +943,14 @@ void launch_advance(const Launch& L, int* d_step, int delta) {
 #define GBFDTD_INST(T)                                                                                           \
     template void launch_e_update<T>(const Launch&, const Dom<T>*, const Tile*, int, T, const StepArgs&, int, int); \
     template void launch_h_update<T>(const Launch&, const Dom<T>*, const Tile*, int, T, const StepArgs&, int, int,  \
-                                     int);
+                                     unsigned);
 GBFDTD_INST(float)
 GBFDTD_INST(double)
 #undef GBFDTD_INST
+template void launch_dft<float>(const Launch&, const Dom<float>*, const Mon*, const DftItem*, int, int, const int*,
+                                int);
+template void launch_dft<double>(const Launch&, const Dom<double>*, const Mon*, const DftItem*, int, int, const int*,
+                                 int);
 template cudaError_t launch_steps<float>(const Launch&, const Dom<float>*, const Tile*, int, float, const StepArgs&, int,
                                          int, int, int, GridSync*, int*);
 template cudaError_t launch_steps<double>(const Launch&, const Dom<double>*, const Tile*, int, double,

@@ -27,6 +27,7 @@ STATUS_NAMES = ["FDTD_OK", "FDTD_EINVAL", "FDTD_ECFL", "FDTD_ETENSOR", "FDTD_ENO
 FDTD_F32, FDTD_F64 = 0, 1
 FDTD_LORENTZ, FDTD_DRUDE = 0, 1
 FDTD_CODEC_NATIVE, FDTD_CODEC_BF16 = 0, 1
+LAUNCH_MODES = 4   # FDTD_LAUNCH_MODES: per-half-step, persistent, +register prefetch, +TMA staging
 KERNEL_CLASSES = ["e_update", "h_update", "source", "dft", "step", "adj_e", "adj_h", "persistent"]
 
 
@@ -194,7 +195,7 @@ def fdtd_get_launch_mode(ctx):
 
 def fdtd_autotune(ctx, n_steps):
     """Times the launch modes on the live state, keeps the fastest; returns ms per mode."""
-    ms = (C.c_double * 3)()
+    ms = (C.c_double * LAUNCH_MODES)()
     _check(load().fdtd_autotune(ctx, int(n_steps), ms), "fdtd_autotune", ctx)
     return [float(v) for v in ms]
 fdtd_reset = _wrap_simple("fdtd_reset")

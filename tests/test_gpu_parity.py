@@ -457,12 +457,20 @@ def test_nonfinite_detection_and_adjoint_state_rules():
     del runner
 
 
-@pytest.mark.parametrize("which", ["blocks", "batch"])
-def test_persistent_and_per_launch_paths_bitwise_equal(which):
-    scs = [small_blocks(40, 6, 150)] if which == "blocks" else _tiny_batch(3, 150)
+@pytest.mark.parametrize("which,dtype", [("blocks", "f32"), ("batch", "f32"), ("blocks", "f64"), ("rows42", "f32")])
+def test_persistent_and_per_launch_paths_bitwise_equal(which, dtype):
+    # every launch mode (per-half-step, persistent, register prefetch, TMA-staged planes) runs the
+    # same arithmetic per cell, so the states and spectra must agree bit for bit; 42-cell rows
+    # (168 B, not a multiple of 16 B) cannot be staged by TMA and take the register path
+    if which == "blocks":
+        scs = [small_blocks(40, 6, 150)]
+    elif which == "rows42":
+        scs = [small_blocks(42, 6, 150)]
+    else:
+        scs = _tiny_batch(3, 150)
     outs = []
-    for mode in (0, 1, 2):
-        ctx = fdtd.Context(scs, dtype="f32")
+    for mode in range(fdtd.LAUNCH_MODES):
+        ctx = fdtd.Context(scs, dtype=dtype)
         fdtd.fdtd_set_launch_mode(ctx.ctx, mode)
         ctx.step(70)
         ctx.step(80)   # two calls: the device step counter carries across launches
@@ -505,8 +513,8 @@ def test_autotune_keeps_state_and_spectra():
     ctx = fdtd.Context([sc], dtype="f32")
     ctx.step(30)
     ms = fdtd.fdtd_autotune(ctx.ctx, 12)
-    assert len(ms) == 3 and all(m > 0 for m in ms)
-    assert fdtd.fdtd_get_launch_mode(ctx.ctx) in (0, 1, 2)
+    assert len(ms) == fdtd.LAUNCH_MODES and all(m > 0 for m in ms)
+    assert fdtd.fdtd_get_launch_mode(ctx.ctx) in range(fdtd.LAUNCH_MODES)
     assert ctx.step_count == 30
     ctx.step(30)
     for p in range(ctx.part_count(0)):
