@@ -254,7 +254,7 @@ def run_ours(args):
                    "l2": "flushed between timed iterations (256 MiB write); the ~75 MB state stays L2-resident "
                          "within an iteration", "parallelism": f"{world} independent replica(s), no collective"},
         "gpu_launches": int(launches),
-        "launch_mode": {"chosen": ["per-half-step graphs", "persistent", "persistent+prefetch", "persistent+TMA"][mode],
+        "launch_mode": {"chosen": ["per-half-step graphs", "persistent", "persistent+prefetch", "persistent+TMA", "per-cell graphs"][mode],
                         "autotune_ms_per_200_steps": [round(v, 3) for v in tune_ms]},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -444,7 +444,7 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision of --profile-case")
     ap.add_argument("--cpml", type=int, default=CPML, help="CPML depth of --profile-case (0: PEC box)")
     ap.add_argument("--adjoint", action="store_true", help="--profile-case: also time as many transposed steps")
-    ap.add_argument("--launch-mode", type=int, default=1, help="0 per half-step launches, 1 persistent, 2 persistent with prefetch, 3 persistent with TMA staging")
+    ap.add_argument("--launch-mode", type=int, default=1, help="0 per half-step tile launches, 1 persistent, 2 persistent with prefetch, 3 persistent with TMA staging, 4 per-cell launches")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

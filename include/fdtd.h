@@ -177,9 +177,10 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps);
  * launches whose interior tiles stage whole z-planes in shared memory with tiled bulk tensor
  * copies (TMA), several planes ahead.  Mode 3 applies to domains whose rows (nx elements) are
  * a multiple of 16 bytes and whose fields and eps^-1 arrays are 16-byte aligned; other domains
- * run the mode-1 code.  All modes compute the same values bitwise.  FDTD_EINVAL for another
- * mode. */
-#define FDTD_LAUNCH_MODES 4
+ * run the mode-1 code.  Mode 4: per-half-step launches (CUDA graphs) of per-cell kernels, one
+ * thread per cell over every cell of a domain (with an energy record it runs the mode-0 code).
+ * All modes compute the same values bitwise.  FDTD_EINVAL for another mode. */
+#define FDTD_LAUNCH_MODES 5
 fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode);
 fdtd_status fdtd_get_launch_mode(fdtd_ctx* ctx, int32_t* mode);
 

@@ -99,6 +99,7 @@ struct fdtd_ctx {
     Tile* d_tiles_lpt = nullptr;    // general tiles first, then interior (persistent kernel)
     int n_lpt = 0;
     int use_persistent = 1;
+    int cell_mode = 0;              // per-half-step launches of the per-cell streaming kernels
     int persist_variant = 0;        // 0 register path, 1 register prefetch, 2 TMA-staged interior
     void* d_tmaps = nullptr;        // kTmaMaps CUtensorMap per domain
     int persist_grid = 0;
@@ -842,16 +843,30 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
     };
     if (nd > 0 && first) launch_copy_int(l, c->d_step, c->d_base);
     if (dstream && !first) cudaStreamWaitEvent(st, c->ev_de, 0);   // DFT of E^n done before E changes
-    fork_int();
-    {
+    // per-cell streaming mode (no energy record): one launch per domain and half-step
+    const bool cell = c->cell_mode && !c->energy_on;
+    unsigned cell_blocks = 0;
+    if (cell)
+        for (const auto& h : c->doms)
+            cell_blocks += (unsigned)((h.n[0] + kTileX - 1) / kTileX) * ((h.n[1] + kTileY - 1) / kTileY) * h.n[2];
+    if (cell) {
         Prof p(c, FDTD_KERNEL_E);
-        launch_e_update<T>(l, dd, c->d_tiles_gen, ng, (T)c->S, a, 1, 1);
+        for (int di = 0; di < (int)c->doms.size(); ++di) {
+            const DomainHost& h = c->doms[di];
+            launch_e_cell<T>(l, dd, di, h.n, (T)c->S, a, c->aniso, h.npole > 0 && h.bcell > 0);
+        }
+    } else {
+        fork_int();
+        {
+            Prof p(c, FDTD_KERNEL_E);
+            launch_e_update<T>(l, dd, c->d_tiles_gen, ng, (T)c->S, a, 1, 1);
+        }
+        {
+            Prof p(c, FDTD_KERNEL_E);
+            launch_e_update<T>(la, dd, c->d_tiles_int, ni, (T)c->S, a, 0, c->aniso);
+        }
+        join_int();
     }
-    {
-        Prof p(c, FDTD_KERNEL_E);
-        launch_e_update<T>(la, dd, c->d_tiles_int, ni, (T)c->S, a, 0, c->aniso);
-    }
-    join_int();
     if (nd > 0) {
         if (dstream) {
             cudaEventRecord(c->ev_e, st);
@@ -862,16 +877,22 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
         if (dstream) cudaEventRecord(c->ev_de, c->dft_stream);
     }
     if (dstream && !first) cudaStreamWaitEvent(st, c->ev_dh, 0);   // DFT of H^{n-1/2} done
-    fork_int();
-    {
+    if (cell) {
         Prof p(c, FDTD_KERNEL_H);
-        launch_h_update<T>(l, dd, c->d_tiles_gen, ng, (T)c->S, a, 1, c->energy_on, adv);
+        for (int di = 0; di < (int)c->doms.size(); ++di)
+            launch_h_cell<T>(l, dd, di, c->doms[di].n, (T)c->S, a, cell_blocks);
+    } else {
+        fork_int();
+        {
+            Prof p(c, FDTD_KERNEL_H);
+            launch_h_update<T>(l, dd, c->d_tiles_gen, ng, (T)c->S, a, 1, c->energy_on, adv);
+        }
+        {
+            Prof p(c, FDTD_KERNEL_H);
+            launch_h_update<T>(la, dd, c->d_tiles_int, ni, (T)c->S, a, 0, c->energy_on, adv);
+        }
+        join_int();
     }
-    {
-        Prof p(c, FDTD_KERNEL_H);
-        launch_h_update<T>(la, dd, c->d_tiles_int, ni, (T)c->S, a, 0, c->energy_on, adv);
-    }
-    join_int();
     if (nd > 0) {
         if (dstream) {
             cudaEventRecord(c->ev_h, st);
@@ -962,7 +983,9 @@ fdtd_status build_graph(fdtd_ctx* c) {
     // launches of one step: E and H for each non-empty tile class, the two DFT launches, and
     // one step-base copy per graph
     const int nd = c->dft_enabled && c->n_dft_items > 0;
-    const long long per = 2 * ((c->tiles_int.empty() ? 0 : 1) + (c->tiles_gen.empty() ? 0 : 1) + nd);
+    const long long per = c->cell_mode && !c->energy_on
+                              ? 2 * ((long long)c->doms.size() + nd)
+                              : 2 * ((c->tiles_int.empty() ? 0 : 1) + (c->tiles_gen.empty() ? 0 : 1) + nd);
     c->graph_launches[a][b] = per * kGraphSteps + nd;
     return FDTD_OK;
 }
@@ -1437,16 +1460,18 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
 
 fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode) {
     GUARD(ctx);
-    if (mode < 0 || mode >= FDTD_LAUNCH_MODES) return fail(ctx, FDTD_EINVAL, "launch mode must be 0, 1, 2 or 3");
-    ctx->use_persistent = mode >= 1;
-    ctx->persist_variant = mode >= 1 ? mode - 1 : 0;
+    if (mode < 0 || mode >= FDTD_LAUNCH_MODES) return fail(ctx, FDTD_EINVAL, "launch mode must be in [0, 4]");
+    if (mode != ctx->cell_mode * 4) drop_graphs(ctx);   // graphs hold the launches of one mode
+    ctx->use_persistent = mode >= 1 && mode <= 3;
+    ctx->persist_variant = ctx->use_persistent ? mode - 1 : 0;
+    ctx->cell_mode = mode == 4;
     return FDTD_OK;
 }
 
 fdtd_status fdtd_get_launch_mode(fdtd_ctx* ctx, int32_t* mode) {
     GUARD(ctx);
     if (!mode) return FDTD_EINVAL;
-    *mode = ctx->use_persistent ? 1 + ctx->persist_variant : 0;
+    *mode = ctx->cell_mode ? 4 : (ctx->use_persistent ? 1 + ctx->persist_variant : 0);
     return FDTD_OK;
 }
 

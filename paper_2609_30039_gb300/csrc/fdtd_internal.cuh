@@ -213,6 +213,13 @@ template <typename T>
 void launch_dft(const Launch& L, const Dom<T>* doms, const Mon* mons, const DftItem* items, int nitems, int kind,
                 const int* d_base, int offset);
 void launch_copy_int(const Launch& L, const int* src, int* dst);
+// One thread per cell over all cells of domain `dom` (per-cell streaming launch mode).
+template <typename T>
+void launch_e_cell(const Launch& L, const Dom<T>* doms, int dom, const int* n, T S, const StepArgs& a, int aniso,
+                   int poles);
+template <typename T>
+void launch_h_cell(const Launch& L, const Dom<T>* doms, int dom, const int* n, T S, const StepArgs& a,
+                   unsigned advance);
 // Persistent cooperative launch advancing nsteps forward steps over all tiles (general first).
 // variant: 0 register path, 1 one-plane register prefetch, 2 TMA-staged interior tiles.
 template <typename T>

@@ -13,6 +13,10 @@
 
 namespace gbfdtd {
 
+// Fused multiply-add with one rounding, spelled out where several kernels must agree bit for bit.
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // CPML coefficients of one node along one axis: y = D/kappa + psi, psi <- b psi + c D.
 template <typename T>
 struct Cpml1 {
@@ -36,33 +40,43 @@ __device__ __forceinline__ Cpml1<T> cpml_at(const Dom<T>& d, const T* coef, int 
     return r;
 }
 
-// In-slab CPML correction of one derivative: psi updated first, then y = D/kappa + psi.
+// In-slab CPML correction of one derivative: psi <- b psi + c D first, then y = D/kappa + psi
+// (c D rounded, then two fused multiply-adds).
+
+template <typename T>
+__device__ __forceinline__ T cpml_rec(T b, T c, T kinv, T* psi, T D) {
+    const T cd = c * D;
+    const T ps = fma_t(b, *psi, cd);
+    *psi = ps;
+    return fma_t(kinv, D, ps);
+}
+
 template <typename T>
 __device__ __forceinline__ T cpml_apply(const Cpml1<T>& q, T* psi, T D) {
-    const T ps = q.b * (*psi) + q.c * D;
-    *psi = ps;
-    return q.k * D + ps;
+    return cpml_rec(q.b, q.c, q.k, psi, D);
 }
 
 // Trapezoidal pole update of one E component (Sec. 2.3):
 // (eps_inf + G) E^{n+1} = (eps_inf + G) E^n + Delta,
 // Delta = S curl + sum_p (P_p - (M_p x_p)_P - 2 g_p E^n);  x_p <- M_p x_p + g_p (E^{n+1} + E^n).
+// (Multiply-adds are written as explicit fused operations so every kernel rounds alike.)
 template <typename T>
 __device__ __forceinline__ T ade_update(const Dom<T>& d, int a, long long bo, T e0, T ie, T scurl) {
     T delta = scurl;
     T* base = d.ade + (long long)a * d.npole * 2 * d.bcell + bo;
     for (int p = 0; p < d.npole; ++p) {
         const T P = base[(2 * p) * d.bcell], Q = base[(2 * p + 1) * d.bcell];
-        delta += P - (d.M00[p] * P + d.M01[p] * Q) - T(2) * d.g0[p] * e0;
+        const T mp = fma_t(d.M00[p], P, d.M01[p] * Q);
+        delta = delta + fma_t(-T(2) * d.g0[p], e0, P - mp);
     }
-    const T e1 = e0 + ie / (T(1) + ie * d.G) * delta;
+    const T e1 = fma_t(ie / fma_t(ie, d.G, T(1)), delta, e0);
     const T es = e1 + e0;
     for (int p = 0; p < d.npole; ++p) {
         T* pp = base + (2 * p) * d.bcell;
         T* pq = base + (2 * p + 1) * d.bcell;
         const T P = *pp, Q = *pq;
-        *pp = d.M00[p] * P + d.M01[p] * Q + d.g0[p] * es;
-        *pq = d.M10[p] * P + d.M11[p] * Q + d.g1[p] * es;
+        *pp = fma_t(d.g0[p], es, fma_t(d.M00[p], P, d.M01[p] * Q));
+        *pq = fma_t(d.g1[p], es, fma_t(d.M10[p], P, d.M11[p] * Q));
     }
     return e1;
 }
@@ -214,9 +228,9 @@ __device__ __forceinline__ void tile_e_int(const Dom<T>* __restrict__ doms, cons
             niey = kAniso ? ie1[nid] : niex;
             niez = kAniso ? ie2[nid] : niex;
         }
-        ex += S * iex * ((hz - hz_ym) - (hy - hyz));
-        ey += S * iey * ((hx - hxz) - (hz - hz_xm));
-        ez += S * iez * ((hy - hy_xm) - (hx - hx_ym));
+        ex = fma_t(S * iex, ((hz - hz_ym) - (hy - hyz)), ex);
+        ey = fma_t(S * iey, ((hx - hxz) - (hz - hz_xm)), ey);
+        ez = fma_t(S * iez, ((hy - hy_xm) - (hx - hx_ym)), ez);
         if (fsrc) {
             ex += src_add(d, a.srcs, 0, i, j, k, step);
             ey += src_add(d, a.srcs, 1, i, j, k, step);
@@ -275,9 +289,9 @@ __device__ __forceinline__ void tile_h_int(const Dom<T>* __restrict__ doms, cons
                 nhy = Hy[nid];
                 nhz = Hz[nid];
             }
-            T hx1 = hx - S * ((ez_yp - ez) - (eyn - eyk));
-            T hy1 = hy - S * ((exn - exk) - (ez_xp - ez));
-            T hz1 = hz - S * ((ey_xp - eyk) - (ex_yp - exk));
+            T hx1 = fma_t(-S, ((ez_yp - ez) - (eyn - eyk)), hx);
+            T hy1 = fma_t(-S, ((exn - exk) - (ez_xp - ez)), hy);
+            T hz1 = fma_t(-S, ((ey_xp - eyk) - (ex_yp - exk)), hz);
             if (fsrc) {
                 hx1 += src_add(d, a.srcs, 3, i, j, k, step);
                 hy1 += src_add(d, a.srcs, 4, i, j, k, step);
@@ -380,15 +394,15 @@ __device__ __forceinline__ void tile_e(const Dom<T>* __restrict__ doms, const Ti
                 if (!py) ey = ade_update(d, 1, bo, ey, iey, S * (yy1 - yy2));
                 if (!pz) ez = ade_update(d, 2, bo, ez, iez, S * (yz1 - yz2));
             } else {
-                if (!px) ex += S * iex * (yx1 - yx2);
-                if (!py) ey += S * iey * (yy1 - yy2);
-                if (!pz) ez += S * iez * (yz1 - yz2);
+                if (!px) ex = fma_t(S * iex, (yx1 - yx2), ex);
+                if (!py) ey = fma_t(S * iey, (yy1 - yy2), ey);
+                if (!pz) ez = fma_t(S * iez, (yz1 - yz2), ez);
             }
             // a PEC-held component keeps its (zero) value and receives no source
         } else {
-            ex += S * iex * (yx1 - yx2);
-            ey += S * iey * (yy1 - yy2);
-            ez += S * iez * (yz1 - yz2);
+            ex = fma_t(S * iex, (yx1 - yx2), ex);
+            ey = fma_t(S * iey, (yy1 - yy2), ey);
+            ez = fma_t(S * iez, (yz1 - yz2), ez);
         }
         if (fsrc) {
             ex += src_add(d, a.srcs, 0, i, j, k, step);
@@ -474,9 +488,9 @@ __device__ __forceinline__ void tile_h(const Dom<T>* __restrict__ doms, const Ti
                     yz2 = cpml_apply(cy, d.psiH[2][1] + o, yz2);
                 }
             }
-            T hx1 = hx - S * (yx1 - yx2);
-            T hy1 = hy - S * (yy1 - yy2);
-            T hz1 = hz - S * (yz1 - yz2);
+            T hx1 = fma_t(-S, (yx1 - yx2), hx);
+            T hy1 = fma_t(-S, (yy1 - yy2), hy);
+            T hz1 = fma_t(-S, (yz1 - yz2), hz);
             if (fsrc) {
                 hx1 += src_add(d, a.srcs, 3, i, j, k, step);
                 hy1 += src_add(d, a.srcs, 4, i, j, k, step);
@@ -521,6 +535,184 @@ __global__ void __launch_bounds__(kTileX* kTileY, min_blocks<T>(kGen))
             }
         }
     }
+}
+
+// ---- per-cell streaming kernels -------------------------------------------------------------
+// One thread per cell, every cell of a domain in one launch: no z-march, no tile classes.  All
+// loads of a thread are independent (the z-1 / z+1 neighbour comes from L2 instead of a carried
+// register), so with few registers and full occupancy the SMs keep many loads in flight; the
+// CPML, PEC and pole work is decided per cell (warps diverge only where a slab edge or a pole
+// boundary crosses them).  Arithmetic per cell is the same as in tile_e / tile_h.
+#ifndef GBFDTD_CELL_BLOCKS_F32
+#define GBFDTD_CELL_BLOCKS_F32 6
+#endif
+template <typename T>
+constexpr int cell_blocks() {
+    return sizeof(T) == 4 ? GBFDTD_CELL_BLOCKS_F32 : 4;
+}
+
+template <typename T>
+__device__ __forceinline__ T cpml_cell(const T* coef, int N, int x, T* psi, T D) {
+    return cpml_rec(coef[x], coef[N + x], coef[2 * N + x], psi, D);
+}
+
+template <typename T, bool kAniso, bool kPoles>
+__global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
+    k_e_cell(const Dom<T>* __restrict__ doms, int dom, T S, const StepArgs a) {
+    const Dom<T>& d = doms[dom];
+    const int nx = d.n[0], ny = d.n[1];
+    const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const int step = *a.d_step;
+    const long long nxy = (long long)nx * ny;
+    const long long id = ((long long)k * ny + j) * nx + i;
+    const T* Hx = d.F[3];
+    const T* Hy = d.F[4];
+    const T* Hz = d.F[5];
+    const T hx = Hx[id], hy = Hy[id], hz = Hz[id];
+    T yx1 = hz - (j > 0 ? Hz[id - nx] : T(0)), yx2 = hy - (k > 0 ? Hy[id - nxy] : T(0));  // Ex: dHz/dy, dHy/dz
+    T yy1 = hx - (k > 0 ? Hx[id - nxy] : T(0)), yy2 = hz - (i > 0 ? Hz[id - 1] : T(0));   // Ey: dHx/dz, dHz/dx
+    T yz1 = hy - (i > 0 ? Hy[id - 1] : T(0)), yz2 = hx - (j > 0 ? Hx[id - nx] : T(0));    // Ez: dHy/dx, dHx/dy
+    T ex = d.F[0][id], ey = d.F[1][id], ez = d.F[2][id];
+    const T iex = d.ie[0][id];
+    const T iey = kAniso ? d.ie[1][id] : iex;
+    const T iez = kAniso ? d.ie[2][id] : iex;
+    const bool px = j == 0 || k == 0, py = i == 0 || k == 0, pz = i == 0 || j == 0;   // PEC-held
+    if (d.ns[2]) {
+        const int sl = slab_of(k, d.dlo[2], d.dhi[2], d.n[2]);
+        if (sl >= 0) {
+            const long long o = ((long long)sl * ny + j) * nx + i;
+            if (!px) yx2 = cpml_cell(d.cE[2], d.n[2], k, d.psiE[0][1] + o, yx2);
+            if (!py) yy1 = cpml_cell(d.cE[2], d.n[2], k, d.psiE[1][0] + o, yy1);
+        }
+    }
+    if (d.ns[0]) {
+        const int sl = slab_of(i, d.dlo[0], d.dhi[0], nx);
+        if (sl >= 0) {
+            const long long o = ((long long)k * ny + j) * d.ns[0] + sl;
+            if (!py) yy2 = cpml_cell(d.cE[0], nx, i, d.psiE[1][1] + o, yy2);
+            if (!pz) yz1 = cpml_cell(d.cE[0], nx, i, d.psiE[2][0] + o, yz1);
+        }
+    }
+    if (d.ns[1]) {
+        const int sl = slab_of(j, d.dlo[1], d.dhi[1], ny);
+        if (sl >= 0) {
+            const long long o = ((long long)k * d.ns[1] + sl) * nx + i;
+            if (!px) yx1 = cpml_cell(d.cE[1], ny, j, d.psiE[0][0] + o, yx1);
+            if (!pz) yz2 = cpml_cell(d.cE[1], ny, j, d.psiE[2][1] + o, yz2);
+        }
+    }
+    if (kPoles && d.npole > 0 && in_ade_box(d, i, j, k) && d.mask[id]) {
+        const long long bo = ade_off(d, i, j, k);
+        if (!px) ex = ade_update(d, 0, bo, ex, iex, S * (yx1 - yx2));
+        if (!py) ey = ade_update(d, 1, bo, ey, iey, S * (yy1 - yy2));
+        if (!pz) ez = ade_update(d, 2, bo, ez, iez, S * (yz1 - yz2));
+    } else {
+        if (!px) ex = fma_t(S * iex, (yx1 - yx2), ex);
+        if (!py) ey = fma_t(S * iey, (yy1 - yy2), ey);
+        if (!pz) ez = fma_t(S * iez, (yz1 - yz2), ez);
+    }
+    if (d.nsrc) {
+        ex += src_add(d, a.srcs, 0, i, j, k, step);
+        ey += src_add(d, a.srcs, 1, i, j, k, step);
+        ez += src_add(d, a.srcs, 2, i, j, k, step);
+    }
+    if (!px) d.F[0][id] = ex;
+    if (!py) d.F[1][id] = ey;
+    if (!pz) d.F[2][id] = ez;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
+    k_h_cell(const Dom<T>* __restrict__ doms, int dom, T S, const StepArgs a, unsigned advance_blocks) {
+    const Dom<T>& d = doms[dom];
+    const int step = *a.d_step;
+    const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
+    const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
+    if (i < nx && j < ny) {
+        const long long nxy = (long long)nx * ny;
+        const long long id = ((long long)k * ny + j) * nx + i;
+        const T* Ex = d.F[0];
+        const T* Ey = d.F[1];
+        const T* Ez = d.F[2];
+        const bool xe = i + 1 < nx, ye = j + 1 < ny, ze = k + 1 < nz;   // the + neighbour exists
+        const T exk = Ex[id], eyk = Ey[id], ez = Ez[id];
+        T yx1 = (ye ? Ez[id + nx] : T(0)) - ez, yx2 = (ze ? Ey[id + nxy] : T(0)) - eyk;   // Hx: dEz/dy, dEy/dz
+        T yy1 = (ze ? Ex[id + nxy] : T(0)) - exk, yy2 = (xe ? Ez[id + 1] : T(0)) - ez;     // Hy: dEx/dz, dEz/dx
+        T yz1 = (xe ? Ey[id + 1] : T(0)) - eyk, yz2 = (ye ? Ex[id + nx] : T(0)) - exk;     // Hz: dEy/dx, dEx/dy
+        const T hx = d.F[3][id], hy = d.F[4][id], hz = d.F[5][id];
+        if (d.ns[2]) {
+            const int sl = slab_of(k, d.dlo[2], d.dhi[2], nz);
+            if (sl >= 0) {
+                const long long o = ((long long)sl * ny + j) * nx + i;
+                yx2 = cpml_cell(d.cH[2], nz, k, d.psiH[0][1] + o, yx2);
+                yy1 = cpml_cell(d.cH[2], nz, k, d.psiH[1][0] + o, yy1);
+            }
+        }
+        if (d.ns[0]) {
+            const int sl = slab_of(i, d.dlo[0], d.dhi[0], nx);
+            if (sl >= 0) {
+                const long long o = ((long long)k * ny + j) * d.ns[0] + sl;
+                yy2 = cpml_cell(d.cH[0], nx, i, d.psiH[1][1] + o, yy2);
+                yz1 = cpml_cell(d.cH[0], nx, i, d.psiH[2][0] + o, yz1);
+            }
+        }
+        if (d.ns[1]) {
+            const int sl = slab_of(j, d.dlo[1], d.dhi[1], ny);
+            if (sl >= 0) {
+                const long long o = ((long long)k * d.ns[1] + sl) * nx + i;
+                yx1 = cpml_cell(d.cH[1], ny, j, d.psiH[0][0] + o, yx1);
+                yz2 = cpml_cell(d.cH[1], ny, j, d.psiH[2][1] + o, yz2);
+            }
+        }
+        T hx1 = fma_t(-S, (yx1 - yx2), hx);
+        T hy1 = fma_t(-S, (yy1 - yy2), hy);
+        T hz1 = fma_t(-S, (yz1 - yz2), hz);
+        if (d.nsrc) {
+            hx1 += src_add(d, a.srcs, 3, i, j, k, step);
+            hy1 += src_add(d, a.srcs, 4, i, j, k, step);
+            hz1 += src_add(d, a.srcs, 5, i, j, k, step);
+        }
+        d.F[3][id] = hx1;
+        d.F[4][id] = hy1;
+        d.F[5][id] = hz1;
+    }
+    if (advance_blocks) {
+        // the last block of the step's H launches (all domains) advances the step counter
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            __threadfence();
+            const unsigned done = atomicAdd(a.d_ticket, 1u);
+            if (done == advance_blocks - 1) {
+                *a.d_ticket = 0u;
+                *a.d_step = step + 1;
+                __threadfence();
+            }
+        }
+    }
+}
+
+// grid: (x chunks of kTileX, y chunks of kTileY, z planes)
+inline dim3 cell_grid(const int* n) {
+    return dim3((unsigned)((n[0] + kTileX - 1) / kTileX), (unsigned)((n[1] + kTileY - 1) / kTileY), (unsigned)n[2]);
+}
+
+template <typename T>
+void launch_e_cell(const Launch& L, const Dom<T>* doms, int dom, const int* n, T S, const StepArgs& a, int aniso,
+                   int poles) {
+    const dim3 g = cell_grid(n), b(kTileX, kTileY);
+    if (poles)
+        (aniso ? k_e_cell<T, true, true> : k_e_cell<T, false, true>)<<<g, b, 0, L.stream>>>(doms, dom, S, a);
+    else
+        (aniso ? k_e_cell<T, true, false> : k_e_cell<T, false, false>)<<<g, b, 0, L.stream>>>(doms, dom, S, a);
+    ++*L.counter;
+}
+
+template <typename T>
+void launch_h_cell(const Launch& L, const Dom<T>* doms, int dom, const int* n, T S, const StepArgs& a,
+                   unsigned advance) {
+    k_h_cell<T><<<cell_grid(n), dim3(kTileX, kTileY), 0, L.stream>>>(doms, dom, S, a, advance);
+    ++*L.counter;
 }
 
 // ---- TMA-staged interior tiles ---------------------------------------------------------------
@@ -626,9 +818,9 @@ __device__ __forceinline__ bool tile_e_tma(const Dom<T>& d, const Tile& t, T S, 
             const T iey = kAniso ? st[7 * P + c] : iex;
             const T iez = kAniso ? st[8 * P + c] : iex;
             const int k = t.z0 + p;
-            T ex = sEx[c] + S * iex * ((hz - sHz[c - kTmaBoxX]) - (hy - hyz));
-            T ey = sEy[c] + S * iey * ((hx - hxz) - (hz - sHz[c - 1]));
-            T ez = sEz[c] + S * iez * ((hy - sHy[c - 1]) - (hx - sHx[c - kTmaBoxX]));
+            T ex = fma_t(S * iex, ((hz - sHz[c - kTmaBoxX]) - (hy - hyz)), sEx[c]);
+            T ey = fma_t(S * iey, ((hx - hxz) - (hz - sHz[c - 1])), sEy[c]);
+            T ez = fma_t(S * iez, ((hy - sHy[c - 1]) - (hx - sHx[c - kTmaBoxX])), sEz[c]);
             if (fsrc) {
                 ex += src_add(d, a.srcs, 0, i, j, k, step);
                 ey += src_add(d, a.srcs, 1, i, j, k, step);
@@ -694,9 +886,9 @@ __device__ __forceinline__ bool tile_h_tma(const Dom<T>& d, const Tile& t, T S, 
             const T hx = st[3 * P + c], hy = st[4 * P + c], hz = st[5 * P + c];
             const T exn = sn[c], eyn = sn[P + c];
             const int k = t.z0 + p;
-            T hx1 = hx - S * ((sEz[c + kTmaBoxX] - ez) - (eyn - eyk));
-            T hy1 = hy - S * ((exn - exk) - (sEz[c + 1] - ez));
-            T hz1 = hz - S * ((sEy[c + 1] - eyk) - (sEx[c + kTmaBoxX] - exk));
+            T hx1 = fma_t(-S, ((sEz[c + kTmaBoxX] - ez) - (eyn - eyk)), hx);
+            T hy1 = fma_t(-S, ((exn - exk) - (sEz[c + 1] - ez)), hy);
+            T hz1 = fma_t(-S, ((sEy[c + 1] - eyk) - (sEx[c + kTmaBoxX] - exk)), hz);
             if (fsrc) {
                 hx1 += src_add(d, a.srcs, 3, i, j, k, step);
                 hy1 += src_add(d, a.srcs, 4, i, j, k, step);
@@ -951,6 +1143,12 @@ template void launch_dft<float>(const Launch&, const Dom<float>*, const Mon*, co
                                 int);
 template void launch_dft<double>(const Launch&, const Dom<double>*, const Mon*, const DftItem*, int, int, const int*,
                                  int);
+template void launch_e_cell<float>(const Launch&, const Dom<float>*, int, const int*, float, const StepArgs&, int, int);
+template void launch_e_cell<double>(const Launch&, const Dom<double>*, int, const int*, double, const StepArgs&, int,
+                                    int);
+template void launch_h_cell<float>(const Launch&, const Dom<float>*, int, const int*, float, const StepArgs&, unsigned);
+template void launch_h_cell<double>(const Launch&, const Dom<double>*, int, const int*, double, const StepArgs&,
+                                    unsigned);
 template cudaError_t launch_steps<float>(const Launch&, const Dom<float>*, const Tile*, int, float, const StepArgs&, int,
                                          int, int, int, GridSync*, int*);
 template cudaError_t launch_steps<double>(const Launch&, const Dom<double>*, const Tile*, int, double,

@@ -27,7 +27,7 @@ STATUS_NAMES = ["FDTD_OK", "FDTD_EINVAL", "FDTD_ECFL", "FDTD_ETENSOR", "FDTD_ENO
 FDTD_F32, FDTD_F64 = 0, 1
 FDTD_LORENTZ, FDTD_DRUDE = 0, 1
 FDTD_CODEC_NATIVE, FDTD_CODEC_BF16 = 0, 1
-LAUNCH_MODES = 4   # FDTD_LAUNCH_MODES: per-half-step, persistent, +register prefetch, +TMA staging
+LAUNCH_MODES = 5   # FDTD_LAUNCH_MODES: per-half-step tiles, persistent, +register prefetch, +TMA staging, per-cell
 KERNEL_CLASSES = ["e_update", "h_update", "source", "dft", "step", "adj_e", "adj_h", "persistent"]
 
 
