@@ -849,11 +849,30 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
     if (cell)
         for (const auto& h : c->doms)
             cell_blocks += (unsigned)((h.n[0] + kTileX - 1) / kTileX) * ((h.n[1] + kTileY - 1) / kTileY) * h.n[2];
+    auto cell_args = [&](int di, bool e_side) {
+        const DomainHost& h = c->doms[di];
+        CellArgs<T> ca;
+        std::memset(&ca, 0, sizeof(ca));
+        for (int f = 0; f < 6; ++f) ca.F[f] = (T*)h.F[f];
+        for (int q = 0; q < 3; ++q) {
+            ca.ie[q] = (const T*)h.ie[q];
+            ca.coef[q] = (const T*)(e_side ? h.cE[q] : h.cH[q]);
+            ca.n[q] = h.n[q];
+            ca.dlo[q] = h.dlo[q];
+            ca.dhi[q] = h.dhi[q];
+            ca.ns[q] = h.ns[q];
+            for (int s2 = 0; s2 < 2; ++s2) ca.psi[q][s2] = (T*)(e_side ? h.psiE[q][s2] : h.psiH[q][s2]);
+        }
+        ca.nsrc = (int)h.srcs.size();
+        for (int q = 0; q < ca.nsrc && q < kMaxSrcPerDom; ++q) ca.src[q] = h.srcs[q];
+        ca.dom = di;
+        return ca;
+    };
     if (cell) {
         Prof p(c, FDTD_KERNEL_E);
         for (int di = 0; di < (int)c->doms.size(); ++di) {
             const DomainHost& h = c->doms[di];
-            launch_e_cell<T>(l, dd, di, h.n, (T)c->S, a, c->aniso, h.npole > 0 && h.bcell > 0);
+            launch_e_cell<T>(l, cell_args(di, true), dd, (T)c->S, a, c->aniso, h.npole > 0 && h.bcell > 0);
         }
     } else {
         fork_int();
@@ -880,7 +899,7 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
     if (cell) {
         Prof p(c, FDTD_KERNEL_H);
         for (int di = 0; di < (int)c->doms.size(); ++di)
-            launch_h_cell<T>(l, dd, di, c->doms[di].n, (T)c->S, a, cell_blocks);
+            launch_h_cell<T>(l, cell_args(di, false), (T)c->S, a, cell_blocks);
     } else {
         fork_int();
         {

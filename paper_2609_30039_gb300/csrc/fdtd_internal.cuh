@@ -213,13 +213,27 @@ template <typename T>
 void launch_dft(const Launch& L, const Dom<T>* doms, const Mon* mons, const DftItem* items, int nitems, int kind,
                 const int* d_base, int offset);
 void launch_copy_int(const Launch& L, const int* src, int* dst);
-// One thread per cell over all cells of domain `dom` (per-cell streaming launch mode).
+// One domain's operands for the per-cell kernels, passed by value (kernel parameter space) so
+// the first field loads need no descriptor load before them.  psi / coef: the CPML memories and
+// coefficient rows of the half-step (E or H).
 template <typename T>
-void launch_e_cell(const Launch& L, const Dom<T>* doms, int dom, const int* n, T S, const StepArgs& a, int aniso,
+struct CellArgs {
+    T* F[6];
+    const T* ie[3];
+    T* psi[3][2];
+    const T* coef[3];
+    int n[3], dlo[3], dhi[3], ns[3];
+    int nsrc;
+    int src[kMaxSrcPerDom];
+    int dom;
+};
+
+// One thread per cell over all cells of one domain (per-cell streaming launch mode).
+template <typename T>
+void launch_e_cell(const Launch& L, const CellArgs<T>& c, const Dom<T>* doms, T S, const StepArgs& a, int aniso,
                    int poles);
 template <typename T>
-void launch_h_cell(const Launch& L, const Dom<T>* doms, int dom, const int* n, T S, const StepArgs& a,
-                   unsigned advance);
+void launch_h_cell(const Launch& L, const CellArgs<T>& c, T S, const StepArgs& a, unsigned advance);
 // Persistent cooperative launch advancing nsteps forward steps over all tiles (general first).
 // variant: 0 register path, 1 one-plane register prefetch, 2 TMA-staged interior tiles.
 template <typename T>

@@ -82,9 +82,9 @@ __device__ __forceinline__ T ade_update(const Dom<T>& d, int a, long long bo, T 
 }
 
 // Soft source increments of component `comp` at a cell (Eq. (yee): added after the update).
-template <typename T>
-__device__ __forceinline__ T src_add(const Dom<T>& d, const Src* __restrict__ srcs, int comp, int i, int j, int k,
-                                     int step) {
+template <typename T, typename D>
+__device__ __forceinline__ T src_add_t(const D& d, const Src* __restrict__ srcs, int comp, int i, int j, int k,
+                                       int step) {
     T add = T(0);
     for (int s = 0; s < d.nsrc; ++s) {
         const Src& sr = srcs[d.src[s]];
@@ -93,6 +93,12 @@ __device__ __forceinline__ T src_add(const Dom<T>& d, const Src* __restrict__ sr
         add += (T)sr.wave[step];
     }
     return add;
+}
+
+template <typename T>
+__device__ __forceinline__ T src_add(const Dom<T>& d, const Src* __restrict__ srcs, int comp, int i, int j, int k,
+                                     int step) {
+    return src_add_t<T>(d, srcs, comp, i, j, k, step);
 }
 
 // Running DFT (Sec. 2.4), F += f exp(i w t) accumulated in FP64, of one work item: up to 256
@@ -538,17 +544,20 @@ __global__ void __launch_bounds__(kTileX* kTileY, min_blocks<T>(kGen))
 }
 
 // ---- per-cell streaming kernels -------------------------------------------------------------
-// One thread per cell, every cell of a domain in one launch: no z-march, no tile classes.  All
-// loads of a thread are independent (the z-1 / z+1 neighbour comes from L2 instead of a carried
-// register), so with few registers and full occupancy the SMs keep many loads in flight; the
-// CPML, PEC and pole work is decided per cell (warps diverge only where a slab edge or a pole
-// boundary crosses them).  Arithmetic per cell is the same as in tile_e / tile_h.
+// One thread per cell, every cell of a domain in one launch (grid: x chunks, y chunks, z planes,
+// so no index division): no z-march, no tile classes.  All loads of a thread are independent
+// (the z-1 / z+1 neighbour comes from L2 instead of a carried register) and the domain's
+// pointers arrive as a kernel parameter, so the first loads issue at once; with 32 registers and
+// full occupancy the SMs keep many loads in flight.  CPML, PEC and pole work is decided per cell
+// (warps diverge only where a slab edge or a pole boundary crosses them).  Arithmetic per cell is
+// the same as in tile_e / tile_h.
 #ifndef GBFDTD_CELL_BLOCKS_F32
-#define GBFDTD_CELL_BLOCKS_F32 6
+#define GBFDTD_CELL_BLOCKS_F32 8
 #endif
-template <typename T>
+// FP32: full occupancy (32 registers) except with poles (their update needs more registers)
+template <typename T, bool kPoles = false>
 constexpr int cell_blocks() {
-    return sizeof(T) == 4 ? GBFDTD_CELL_BLOCKS_F32 : 4;
+    return sizeof(T) == 4 ? (kPoles ? 6 : GBFDTD_CELL_BLOCKS_F32) : 4;
 }
 
 template <typename T>
@@ -557,130 +566,135 @@ __device__ __forceinline__ T cpml_cell(const T* coef, int N, int x, T* psi, T D)
 }
 
 template <typename T, bool kAniso, bool kPoles>
-__global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
-    k_e_cell(const Dom<T>* __restrict__ doms, int dom, T S, const StepArgs a) {
-    const Dom<T>& d = doms[dom];
-    const int nx = d.n[0], ny = d.n[1];
+__global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
+    k_e_cell(const CellArgs<T> c, const Dom<T>* __restrict__ doms, T S, const StepArgs a) {
+    const int nx = c.n[0], ny = c.n[1];
     const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
     if (i >= nx || j >= ny) return;
-    const int step = *a.d_step;
     const long long nxy = (long long)nx * ny;
     const long long id = ((long long)k * ny + j) * nx + i;
-    const T* Hx = d.F[3];
-    const T* Hy = d.F[4];
-    const T* Hz = d.F[5];
+    const T* Hx = c.F[3];
+    const T* Hy = c.F[4];
+    const T* Hz = c.F[5];
     const T hx = Hx[id], hy = Hy[id], hz = Hz[id];
     T yx1 = hz - (j > 0 ? Hz[id - nx] : T(0)), yx2 = hy - (k > 0 ? Hy[id - nxy] : T(0));  // Ex: dHz/dy, dHy/dz
     T yy1 = hx - (k > 0 ? Hx[id - nxy] : T(0)), yy2 = hz - (i > 0 ? Hz[id - 1] : T(0));   // Ey: dHx/dz, dHz/dx
     T yz1 = hy - (i > 0 ? Hy[id - 1] : T(0)), yz2 = hx - (j > 0 ? Hx[id - nx] : T(0));    // Ez: dHy/dx, dHx/dy
-    T ex = d.F[0][id], ey = d.F[1][id], ez = d.F[2][id];
-    const T iex = d.ie[0][id];
-    const T iey = kAniso ? d.ie[1][id] : iex;
-    const T iez = kAniso ? d.ie[2][id] : iex;
+    T ex = c.F[0][id], ey = c.F[1][id], ez = c.F[2][id];
+    const T iex = c.ie[0][id];
+    const T iey = kAniso ? c.ie[1][id] : iex;
+    const T iez = kAniso ? c.ie[2][id] : iex;
     const bool px = j == 0 || k == 0, py = i == 0 || k == 0, pz = i == 0 || j == 0;   // PEC-held
-    if (d.ns[2]) {
-        const int sl = slab_of(k, d.dlo[2], d.dhi[2], d.n[2]);
+    if (c.ns[2]) {
+        const int sl = slab_of(k, c.dlo[2], c.dhi[2], c.n[2]);
         if (sl >= 0) {
             const long long o = ((long long)sl * ny + j) * nx + i;
-            if (!px) yx2 = cpml_cell(d.cE[2], d.n[2], k, d.psiE[0][1] + o, yx2);
-            if (!py) yy1 = cpml_cell(d.cE[2], d.n[2], k, d.psiE[1][0] + o, yy1);
+            if (!px) yx2 = cpml_cell(c.coef[2], c.n[2], k, c.psi[0][1] + o, yx2);
+            if (!py) yy1 = cpml_cell(c.coef[2], c.n[2], k, c.psi[1][0] + o, yy1);
         }
     }
-    if (d.ns[0]) {
-        const int sl = slab_of(i, d.dlo[0], d.dhi[0], nx);
+    if (c.ns[0]) {
+        const int sl = slab_of(i, c.dlo[0], c.dhi[0], nx);
         if (sl >= 0) {
-            const long long o = ((long long)k * ny + j) * d.ns[0] + sl;
-            if (!py) yy2 = cpml_cell(d.cE[0], nx, i, d.psiE[1][1] + o, yy2);
-            if (!pz) yz1 = cpml_cell(d.cE[0], nx, i, d.psiE[2][0] + o, yz1);
+            const long long o = ((long long)k * ny + j) * c.ns[0] + sl;
+            if (!py) yy2 = cpml_cell(c.coef[0], nx, i, c.psi[1][1] + o, yy2);
+            if (!pz) yz1 = cpml_cell(c.coef[0], nx, i, c.psi[2][0] + o, yz1);
         }
     }
-    if (d.ns[1]) {
-        const int sl = slab_of(j, d.dlo[1], d.dhi[1], ny);
+    if (c.ns[1]) {
+        const int sl = slab_of(j, c.dlo[1], c.dhi[1], ny);
         if (sl >= 0) {
-            const long long o = ((long long)k * d.ns[1] + sl) * nx + i;
-            if (!px) yx1 = cpml_cell(d.cE[1], ny, j, d.psiE[0][0] + o, yx1);
-            if (!pz) yz2 = cpml_cell(d.cE[1], ny, j, d.psiE[2][1] + o, yz2);
+            const long long o = ((long long)k * c.ns[1] + sl) * nx + i;
+            if (!px) yx1 = cpml_cell(c.coef[1], ny, j, c.psi[0][0] + o, yx1);
+            if (!pz) yz2 = cpml_cell(c.coef[1], ny, j, c.psi[2][1] + o, yz2);
         }
     }
-    if (kPoles && d.npole > 0 && in_ade_box(d, i, j, k) && d.mask[id]) {
-        const long long bo = ade_off(d, i, j, k);
-        if (!px) ex = ade_update(d, 0, bo, ex, iex, S * (yx1 - yx2));
-        if (!py) ey = ade_update(d, 1, bo, ey, iey, S * (yy1 - yy2));
-        if (!pz) ez = ade_update(d, 2, bo, ez, iez, S * (yz1 - yz2));
-    } else {
+    bool disp = false;
+    if (kPoles) {
+        const Dom<T>& d = doms[c.dom];
+        disp = d.npole > 0 && in_ade_box(d, i, j, k) && d.mask[id];
+        if (disp) {
+            const long long bo = ade_off(d, i, j, k);
+            if (!px) ex = ade_update(d, 0, bo, ex, iex, S * (yx1 - yx2));
+            if (!py) ey = ade_update(d, 1, bo, ey, iey, S * (yy1 - yy2));
+            if (!pz) ez = ade_update(d, 2, bo, ez, iez, S * (yz1 - yz2));
+        }
+    }
+    if (!disp) {
         if (!px) ex = fma_t(S * iex, (yx1 - yx2), ex);
         if (!py) ey = fma_t(S * iey, (yy1 - yy2), ey);
         if (!pz) ez = fma_t(S * iez, (yz1 - yz2), ez);
     }
-    if (d.nsrc) {
-        ex += src_add(d, a.srcs, 0, i, j, k, step);
-        ey += src_add(d, a.srcs, 1, i, j, k, step);
-        ez += src_add(d, a.srcs, 2, i, j, k, step);
+    if (c.nsrc) {
+        const int step = *a.d_step;
+        ex += src_add_t<T>(c, a.srcs, 0, i, j, k, step);
+        ey += src_add_t<T>(c, a.srcs, 1, i, j, k, step);
+        ez += src_add_t<T>(c, a.srcs, 2, i, j, k, step);
     }
-    if (!px) d.F[0][id] = ex;
-    if (!py) d.F[1][id] = ey;
-    if (!pz) d.F[2][id] = ez;
+    if (!px) c.F[0][id] = ex;
+    if (!py) c.F[1][id] = ey;
+    if (!pz) c.F[2][id] = ez;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
-    k_h_cell(const Dom<T>* __restrict__ doms, int dom, T S, const StepArgs a, unsigned advance_blocks) {
-    const Dom<T>& d = doms[dom];
-    const int step = *a.d_step;
-    const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
+    k_h_cell(const CellArgs<T> c, T S, const StepArgs a, unsigned advance_blocks) {
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
     const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
     if (i < nx && j < ny) {
         const long long nxy = (long long)nx * ny;
         const long long id = ((long long)k * ny + j) * nx + i;
-        const T* Ex = d.F[0];
-        const T* Ey = d.F[1];
-        const T* Ez = d.F[2];
+        const T* Ex = c.F[0];
+        const T* Ey = c.F[1];
+        const T* Ez = c.F[2];
         const bool xe = i + 1 < nx, ye = j + 1 < ny, ze = k + 1 < nz;   // the + neighbour exists
         const T exk = Ex[id], eyk = Ey[id], ez = Ez[id];
         T yx1 = (ye ? Ez[id + nx] : T(0)) - ez, yx2 = (ze ? Ey[id + nxy] : T(0)) - eyk;   // Hx: dEz/dy, dEy/dz
         T yy1 = (ze ? Ex[id + nxy] : T(0)) - exk, yy2 = (xe ? Ez[id + 1] : T(0)) - ez;     // Hy: dEx/dz, dEz/dx
         T yz1 = (xe ? Ey[id + 1] : T(0)) - eyk, yz2 = (ye ? Ex[id + nx] : T(0)) - exk;     // Hz: dEy/dx, dEx/dy
-        const T hx = d.F[3][id], hy = d.F[4][id], hz = d.F[5][id];
-        if (d.ns[2]) {
-            const int sl = slab_of(k, d.dlo[2], d.dhi[2], nz);
+        const T hx = c.F[3][id], hy = c.F[4][id], hz = c.F[5][id];
+        if (c.ns[2]) {
+            const int sl = slab_of(k, c.dlo[2], c.dhi[2], nz);
             if (sl >= 0) {
                 const long long o = ((long long)sl * ny + j) * nx + i;
-                yx2 = cpml_cell(d.cH[2], nz, k, d.psiH[0][1] + o, yx2);
-                yy1 = cpml_cell(d.cH[2], nz, k, d.psiH[1][0] + o, yy1);
+                yx2 = cpml_cell(c.coef[2], nz, k, c.psi[0][1] + o, yx2);
+                yy1 = cpml_cell(c.coef[2], nz, k, c.psi[1][0] + o, yy1);
             }
         }
-        if (d.ns[0]) {
-            const int sl = slab_of(i, d.dlo[0], d.dhi[0], nx);
+        if (c.ns[0]) {
+            const int sl = slab_of(i, c.dlo[0], c.dhi[0], nx);
             if (sl >= 0) {
-                const long long o = ((long long)k * ny + j) * d.ns[0] + sl;
-                yy2 = cpml_cell(d.cH[0], nx, i, d.psiH[1][1] + o, yy2);
-                yz1 = cpml_cell(d.cH[0], nx, i, d.psiH[2][0] + o, yz1);
+                const long long o = ((long long)k * ny + j) * c.ns[0] + sl;
+                yy2 = cpml_cell(c.coef[0], nx, i, c.psi[1][1] + o, yy2);
+                yz1 = cpml_cell(c.coef[0], nx, i, c.psi[2][0] + o, yz1);
             }
         }
-        if (d.ns[1]) {
-            const int sl = slab_of(j, d.dlo[1], d.dhi[1], ny);
+        if (c.ns[1]) {
+            const int sl = slab_of(j, c.dlo[1], c.dhi[1], ny);
             if (sl >= 0) {
-                const long long o = ((long long)k * d.ns[1] + sl) * nx + i;
-                yx1 = cpml_cell(d.cH[1], ny, j, d.psiH[0][0] + o, yx1);
-                yz2 = cpml_cell(d.cH[1], ny, j, d.psiH[2][1] + o, yz2);
+                const long long o = ((long long)k * c.ns[1] + sl) * nx + i;
+                yx1 = cpml_cell(c.coef[1], ny, j, c.psi[0][0] + o, yx1);
+                yz2 = cpml_cell(c.coef[1], ny, j, c.psi[2][1] + o, yz2);
             }
         }
         T hx1 = fma_t(-S, (yx1 - yx2), hx);
         T hy1 = fma_t(-S, (yy1 - yy2), hy);
         T hz1 = fma_t(-S, (yz1 - yz2), hz);
-        if (d.nsrc) {
-            hx1 += src_add(d, a.srcs, 3, i, j, k, step);
-            hy1 += src_add(d, a.srcs, 4, i, j, k, step);
-            hz1 += src_add(d, a.srcs, 5, i, j, k, step);
+        if (c.nsrc) {
+            const int step = *a.d_step;
+            hx1 += src_add_t<T>(c, a.srcs, 3, i, j, k, step);
+            hy1 += src_add_t<T>(c, a.srcs, 4, i, j, k, step);
+            hz1 += src_add_t<T>(c, a.srcs, 5, i, j, k, step);
         }
-        d.F[3][id] = hx1;
-        d.F[4][id] = hy1;
-        d.F[5][id] = hz1;
+        c.F[3][id] = hx1;
+        c.F[4][id] = hy1;
+        c.F[5][id] = hz1;
     }
     if (advance_blocks) {
         // the last block of the step's H launches (all domains) advances the step counter
         __syncthreads();
         if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const int step = *a.d_step;
             __threadfence();
             const unsigned done = atomicAdd(a.d_ticket, 1u);
             if (done == advance_blocks - 1) {
@@ -698,20 +712,19 @@ inline dim3 cell_grid(const int* n) {
 }
 
 template <typename T>
-void launch_e_cell(const Launch& L, const Dom<T>* doms, int dom, const int* n, T S, const StepArgs& a, int aniso,
+void launch_e_cell(const Launch& L, const CellArgs<T>& c, const Dom<T>* doms, T S, const StepArgs& a, int aniso,
                    int poles) {
-    const dim3 g = cell_grid(n), b(kTileX, kTileY);
+    const dim3 g = cell_grid(c.n), b(kTileX, kTileY);
     if (poles)
-        (aniso ? k_e_cell<T, true, true> : k_e_cell<T, false, true>)<<<g, b, 0, L.stream>>>(doms, dom, S, a);
+        (aniso ? k_e_cell<T, true, true> : k_e_cell<T, false, true>)<<<g, b, 0, L.stream>>>(c, doms, S, a);
     else
-        (aniso ? k_e_cell<T, true, false> : k_e_cell<T, false, false>)<<<g, b, 0, L.stream>>>(doms, dom, S, a);
+        (aniso ? k_e_cell<T, true, false> : k_e_cell<T, false, false>)<<<g, b, 0, L.stream>>>(c, doms, S, a);
     ++*L.counter;
 }
 
 template <typename T>
-void launch_h_cell(const Launch& L, const Dom<T>* doms, int dom, const int* n, T S, const StepArgs& a,
-                   unsigned advance) {
-    k_h_cell<T><<<cell_grid(n), dim3(kTileX, kTileY), 0, L.stream>>>(doms, dom, S, a, advance);
+void launch_h_cell(const Launch& L, const CellArgs<T>& c, T S, const StepArgs& a, unsigned advance) {
+    k_h_cell<T><<<cell_grid(c.n), dim3(kTileX, kTileY), 0, L.stream>>>(c, S, a, advance);
     ++*L.counter;
 }
 
@@ -1143,12 +1156,12 @@ template void launch_dft<float>(const Launch&, const Dom<float>*, const Mon*, co
                                 int);
 template void launch_dft<double>(const Launch&, const Dom<double>*, const Mon*, const DftItem*, int, int, const int*,
                                  int);
-template void launch_e_cell<float>(const Launch&, const Dom<float>*, int, const int*, float, const StepArgs&, int, int);
-template void launch_e_cell<double>(const Launch&, const Dom<double>*, int, const int*, double, const StepArgs&, int,
-                                    int);
-template void launch_h_cell<float>(const Launch&, const Dom<float>*, int, const int*, float, const StepArgs&, unsigned);
-template void launch_h_cell<double>(const Launch&, const Dom<double>*, int, const int*, double, const StepArgs&,
-                                    unsigned);
+template void launch_e_cell<float>(const Launch&, const CellArgs<float>&, const Dom<float>*, float, const StepArgs&,
+                                   int, int);
+template void launch_e_cell<double>(const Launch&, const CellArgs<double>&, const Dom<double>*, double,
+                                    const StepArgs&, int, int);
+template void launch_h_cell<float>(const Launch&, const CellArgs<float>&, float, const StepArgs&, unsigned);
+template void launch_h_cell<double>(const Launch&, const CellArgs<double>&, double, const StepArgs&, unsigned);
 template cudaError_t launch_steps<float>(const Launch&, const Dom<float>*, const Tile*, int, float, const StepArgs&, int,
                                          int, int, int, GridSync*, int*);
 template cudaError_t launch_steps<double>(const Launch&, const Dom<double>*, const Tile*, int, double,
