@@ -166,19 +166,20 @@ fdtd_status fdtd_energy_read(fdtd_ctx* ctx, int32_t domain, double* host_dst, in
 
 /* Advances every domain by n_steps forward steps (Eq. (yee): E update with CPML, poles and
  * eps^-1; E sources; E DFT; H update with CPML; H sources; H DFT; energy).  Asynchronous.
- * Runs as persistent cooperative launches of up to 512 steps (grid-wide barrier between the
- * half-steps) unless fdtd_set_launch_mode selected per-half-step launches. */
+ * How the steps are launched is set by fdtd_set_launch_mode (default: per-cell kernels replayed
+ * as CUDA graphs of 32 steps). */
 fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps);
 
 /* Launch modes (no counterpart in the paper; they change scheduling, not arithmetic):
- * mode 0: per-half-step launches (replayed as CUDA graphs); mode 1 (default): persistent
+ * mode 0: per-half-step launches (replayed as CUDA graphs); mode 1: persistent
  * cooperative launches (4 blocks per SM in FP32); mode 2: persistent launches whose interior
  * tiles load the next z-plane ahead into registers (3 blocks per SM); mode 3: persistent
  * launches whose interior tiles stage whole z-planes in shared memory with tiled bulk tensor
  * copies (TMA), several planes ahead.  Mode 3 applies to domains whose rows (nx elements) are
  * a multiple of 16 bytes and whose fields and eps^-1 arrays are 16-byte aligned; other domains
- * run the mode-1 code.  Mode 4: per-half-step launches (CUDA graphs) of per-cell kernels, one
- * thread per cell over every cell of a domain (with an energy record it runs the mode-0 code).
+ * run the mode-1 code.  Mode 4 (default): per-half-step launches (CUDA graphs) of per-cell
+ * kernels, one thread per cell over every cell of a domain (with an energy record it runs the
+ * mode-0 code).
  * All modes compute the same values bitwise.  FDTD_EINVAL for another mode. */
 #define FDTD_LAUNCH_MODES 5
 fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode);

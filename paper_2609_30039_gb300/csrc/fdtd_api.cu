@@ -98,8 +98,8 @@ struct fdtd_ctx {
     GridSync* d_sync = nullptr;     // barrier / ticket of the persistent step kernel
     Tile* d_tiles_lpt = nullptr;    // general tiles first, then interior (persistent kernel)
     int n_lpt = 0;
-    int use_persistent = 1;
-    int cell_mode = 0;              // per-half-step launches of the per-cell streaming kernels
+    int use_persistent = 0;
+    int cell_mode = 1;              // per-half-step launches of the per-cell streaming kernels
     int persist_variant = 0;        // 0 register path, 1 register prefetch, 2 TMA-staged interior
     void* d_tmaps = nullptr;        // kTmaMaps CUtensorMap per domain
     int persist_grid = 0;
@@ -402,7 +402,12 @@ fdtd_status sync_doms_t(fdtd_ctx* c) {
     return FDTD_OK;
 }
 
+void drop_graphs(fdtd_ctx* c);
+
 fdtd_status sync_doms(fdtd_ctx* c) {
+    // captured graphs of the per-cell mode hold the domains' pointers as kernel parameters:
+    // any descriptor change (materials, sources, monitors, design) invalidates them
+    drop_graphs(c);
     fdtd_status st = sync_tmaps(c);
     if (st != FDTD_OK) return st;
     return c->dtype == FDTD_F32 ? sync_doms_t<float>(c) : sync_doms_t<double>(c);
@@ -967,6 +972,10 @@ void adj_once(fdtd_ctx* c, int m) {
 constexpr int kGraphSteps = 32;
 
 void drop_graphs(fdtd_ctx* c) {
+    bool any = false;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) any = any || c->graph[a][b];
+    if (any) cudaStreamSynchronize(c->stream);   // no replay of a graph in flight when it goes
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             if (c->graph[a][b]) {

@@ -520,3 +520,24 @@ def test_autotune_keeps_state_and_spectra():
     for p in range(ctx.part_count(0)):
         assert torch.equal(ctx.part(0, p), ref.part(0, p))
     assert torch.equal(ctx.dft(0), ref.dft(0))
+
+
+@pytest.mark.parametrize("mode", [0, 4])
+def test_new_material_after_graph_capture(mode):
+    # graphs captured before a material change must not keep the old eps^-1 arrays
+    sc = small_blocks(40, 6, 80)
+    ctx = fdtd.Context([sc], dtype="f32")
+    fdtd.fdtd_set_launch_mode(ctx.ctx, mode)
+    ctx.step(64)                                   # two graph replays captured with the old material
+    inv = torch.from_numpy(np.ascontiguousarray(sc.inv_eps3()[0])).to(device=ctx.device, dtype=torch.float32) * 0.5
+    ctx.set_inv_eps(0, [inv, inv, inv])
+    fdtd.fdtd_reset(ctx.ctx)
+    fdtd.fdtd_dft_reset(ctx.ctx)
+    ctx.step(64)
+    ref = fdtd.Context([sc], dtype="f32")
+    fdtd.fdtd_set_launch_mode(ref.ctx, mode)
+    ref.set_inv_eps(0, [inv.clone(), inv.clone(), inv.clone()])
+    ref.step(64)
+    for p in range(ctx.part_count(0)):
+        assert torch.equal(ctx.part(0, p), ref.part(0, p))
+    assert torch.equal(ctx.dft(0), ref.dft(0))
