@@ -127,6 +127,14 @@ const char* fdtd_version(void);
  * set of dispersive cells must not grow beyond the box chosen at create: FDTD_EINVAL). */
 fdtd_status fdtd_set_material(fdtd_ctx* ctx, int32_t domain, const fdtd_material* material);
 
+/* Periodic boundaries (Sec. 2.2: periodic/Bloch lateral boundaries, here with zero Bloch
+ * phase) on the x and/or y axis of one domain: the neighbour beyond the last node is the first
+ * one and vice versa, and the coordinate-0 plane of that axis is no PEC wall.  periodic[3] are
+ * flags for x, y, z; z must be 0, and a periodic axis must have no CPML cells on either face and
+ * at least 2 cells (FDTD_EINVAL otherwise).  Applies to the forward and transposed steps in every
+ * launch mode. */
+fdtd_status fdtd_set_periodic(fdtd_ctx* ctx, int32_t domain, const int32_t periodic[3]);
+
 /* Soft source (Sec. 2.4, Eq. (yee) s and m): after the update of `component` in forward
  * step n, every cell of the half-open box [lo, hi) gets += waveform[n] (no effect for
  * n >= n_steps).  waveform: host, copied, FP64.  *source_id may be NULL. */

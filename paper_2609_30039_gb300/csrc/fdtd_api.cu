@@ -48,6 +48,7 @@ struct DomainHost {
     double* grad = nullptr;
     std::vector<int> mons;
     std::vector<int> srcs;
+    int per[3] = {0, 0, 0};        // periodic axes (x, y)
     const void* tmaps = nullptr;   // this domain's kTmaMaps tensor maps in device memory
     int tma = 0;                   // maps encoded for the current field and eps^-1 pointers
 };
@@ -287,6 +288,7 @@ void fill_dom(const fdtd_ctx* c, const DomainHost& h, Dom<T>& d) {
         d.dlo[q] = h.dlo[q];
         d.dhi[q] = h.dhi[q];
         d.ns[q] = h.ns[q];
+        d.per[q] = h.per[q];
         d.blo[q] = h.blo[q];
         d.bhi[q] = h.bhi[q];
         d.glo[q] = h.glo[q];
@@ -866,6 +868,7 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
             ca.dlo[q] = h.dlo[q];
             ca.dhi[q] = h.dhi[q];
             ca.ns[q] = h.ns[q];
+            ca.per[q] = h.per[q];
             for (int s2 = 0; s2 < 2; ++s2) ca.psi[q][s2] = (T*)(e_side ? h.psiE[q][s2] : h.psiH[q][s2]);
         }
         ca.nsrc = (int)h.srcs.size();
@@ -1236,6 +1239,18 @@ fdtd_status fdtd_destroy(fdtd_ctx* ctx) {
     for (auto& s : ctx->slots) cudaFree(s.second.buf);
     delete ctx;
     return FDTD_OK;
+}
+
+fdtd_status fdtd_set_periodic(fdtd_ctx* ctx, int32_t domain, const int32_t periodic[3]) {
+    GUARD(ctx);
+    if (!valid_dom(ctx, domain) || !periodic) return fail(ctx, FDTD_EINVAL, "bad domain or periodic flags");
+    DomainHost& d = ctx->doms[domain];
+    if (periodic[2]) return fail(ctx, FDTD_EINVAL, "z cannot be periodic (x and y only)");
+    for (int q = 0; q < 2; ++q)
+        if (periodic[q] && (d.dlo[q] || d.dhi[q] || d.n[q] < 2))
+            return fail(ctx, FDTD_EINVAL, "a periodic axis needs no CPML on its faces and at least 2 cells");
+    for (int q = 0; q < 3; ++q) d.per[q] = periodic[q] ? 1 : 0;
+    return sync_doms(ctx);
 }
 
 fdtd_status fdtd_set_material(fdtd_ctx* ctx, int32_t domain, const fdtd_material* m) {

@@ -48,6 +48,7 @@ struct Dom {
     const T* ie[3];            // 1/eps per E component (borrowed)
     const uint8_t* mask;       // pole mask (borrowed) or nullptr
     int dlo[3], dhi[3], ns[3]; // CPML depth per axis (low, high), ns = dlo + dhi
+    int per[3];                // 1: periodic axis (x, y only): neighbours wrap, no PEC plane
     T* psiE[3][2];
     T* psiH[3][2];
     T* apsiE[3][2];
@@ -152,6 +153,26 @@ __device__ __forceinline__ void tile_coords(const Tile& t, int& i, int& j) {
     j = seg_coord(t.ys, tid >> t.lw);
 }
 
+// Offset from cell (x along axis q, element stride st) to its -1 / +1 neighbour along q, or 0
+// with *exists = false where the neighbour is absent (beyond a PEC wall or the domain edge); on a
+// periodic axis the neighbour wraps around.
+__host__ __device__ inline long long nb_minus(int x, int N, long long st, int per, bool* exists) {
+    if (x > 0) {
+        *exists = true;
+        return -st;
+    }
+    *exists = per != 0;
+    return per ? (long long)(N - 1) * st : 0;
+}
+__host__ __device__ inline long long nb_plus(int x, int N, long long st, int per, bool* exists) {
+    if (x + 1 < N) {
+        *exists = true;
+        return st;
+    }
+    *exists = per != 0;
+    return per ? -(long long)(N - 1) * st : 0;
+}
+
 __host__ __device__ inline long long cidx(const int* n, int i, int j, int k) {
     return ((long long)k * n[1] + j) * n[0] + i;
 }
@@ -223,6 +244,7 @@ struct CellArgs {
     T* psi[3][2];
     const T* coef[3];
     int n[3], dlo[3], dhi[3], ns[3];
+    int per[3];
     int nsrc;
     int src[kMaxSrcPerDom];
     int dom;

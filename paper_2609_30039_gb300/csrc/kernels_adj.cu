@@ -152,7 +152,10 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
     const CpmlC<T> xE = cpml_c(d, d.cE[0], 0, i), yE = cpml_c(d, d.cE[1], 1, j);
     const CpmlC<T> xH = cpml_c(d, d.cH[0], 0, i), xHm = cpml_c(d, d.cH[0], 0, i - 1);
     const CpmlC<T> yH = cpml_c(d, d.cH[1], 1, j), yHm = cpml_c(d, d.cH[1], 1, j - 1);
-    const bool pi = i == 0, pj = j == 0;
+    const bool pi = i == 0 && !d.per[0], pj = j == 0 && !d.per[1];   // PEC plane at this column
+    bool hasx, hasy;                                                   // -x / -y neighbour exists
+    const long long oxm = nb_minus(i, nx, 1, d.per[0], &hasx);
+    const long long oym = nb_minus(j, ny, nx, d.per[1], &hasy);
     const bool gcol = d.design && i >= d.glo[0] && i < d.ghi[0] && j >= d.glo[1] && j < d.ghi[1];
     const bool mon = d.nmon && (t.flags & kTileMonE);
     long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
@@ -171,25 +174,25 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
         // loads of the plane
         const T f0 = A0[id], f1 = A1[id], f2 = A2[id];
         const T b0 = B0[id], b1 = B1[id], b2 = B2[id];
-        const T b2_xm = pi ? T(0) : B2[id - 1], b1_xm = pi ? T(0) : B1[id - 1];
-        const T b2_ym = pj ? T(0) : B2[id - nx], b0_ym = pj ? T(0) : B0[id - nx];
+        const T b2_xm = hasx ? B2[id + oxm] : T(0), b1_xm = hasx ? B1[id + oxm] : T(0);
+        const T b2_ym = hasy ? B2[id + oym] : T(0), b0_ym = hasy ? B0[id + oym] : T(0);
         const long long oz = zH.s >= 0 ? off_z(d, zH.s, i, j) : 0;
         const T p10 = zH.s >= 0 ? d.apsiH[1][0][oz] : T(0);   // H_y, d/dz
         const T p01 = zH.s >= 0 ? d.apsiH[0][1][oz] : T(0);   // H_x, d/dz
         const T p20 = xH.s >= 0 ? d.apsiH[2][0][off_x(d, xH.s, j, k)] : T(0);                 // H_z, d/dx
-        const T p20m = (!pi && xHm.s >= 0) ? d.apsiH[2][0][off_x(d, xHm.s, j, k)] : T(0);
+        const T p20m = (hasx && xHm.s >= 0) ? d.apsiH[2][0][off_x(d, xHm.s, j, k)] : T(0);
         const T p11 = xH.s >= 0 ? d.apsiH[1][1][off_x(d, xH.s, j, k)] : T(0);                 // H_y, d/dx
-        const T p11m = (!pi && xHm.s >= 0) ? d.apsiH[1][1][off_x(d, xHm.s, j, k)] : T(0);
+        const T p11m = (hasx && xHm.s >= 0) ? d.apsiH[1][1][off_x(d, xHm.s, j, k)] : T(0);
         const T p21 = yH.s >= 0 ? d.apsiH[2][1][off_y(d, yH.s, i, k)] : T(0);                 // H_z, d/dy
-        const T p21m = (!pj && yHm.s >= 0) ? d.apsiH[2][1][off_y(d, yHm.s, i, k)] : T(0);
+        const T p21m = (hasy && yHm.s >= 0) ? d.apsiH[2][1][off_y(d, yHm.s, i, k)] : T(0);
         const T p00 = yH.s >= 0 ? d.apsiH[0][0][off_y(d, yH.s, i, k)] : T(0);                 // H_x, d/dy
-        const T p00m = (!pj && yHm.s >= 0) ? d.apsiH[0][0][off_y(d, yHm.s, i, k)] : T(0);
+        const T p00m = (hasy && yHm.s >= 0) ? d.apsiH[0][0][off_y(d, yHm.s, i, k)] : T(0);
         // derivative cotangents of the H update: s = 0 has ybar = -S Hbar, s = 1 has +S Hbar
         const T tyz = dbar_c(zH, -S * b1, p10), txz = dbar_c(zH, S * b0, p01);
-        const T tzx = dbar_c(xH, -S * b2, p20), tzx_m = pi ? T(0) : dbar_c(xHm, -S * b2_xm, p20m);
-        const T tyx = dbar_c(xH, S * b1, p11), tyx_m = pi ? T(0) : dbar_c(xHm, S * b1_xm, p11m);
-        const T tzy = dbar_c(yH, S * b2, p21), tzy_m = pj ? T(0) : dbar_c(yHm, S * b2_ym, p21m);
-        const T txy = dbar_c(yH, -S * b0, p00), txy_m = pj ? T(0) : dbar_c(yHm, -S * b0_ym, p00m);
+        const T tzx = dbar_c(xH, -S * b2, p20), tzx_m = hasx ? dbar_c(xHm, -S * b2_xm, p20m) : T(0);
+        const T tyx = dbar_c(xH, S * b1, p11), tyx_m = hasx ? dbar_c(xHm, S * b1_xm, p11m) : T(0);
+        const T tzy = dbar_c(yH, S * b2, p21), tzy_m = hasy ? dbar_c(yHm, S * b2_ym, p21m) : T(0);
+        const T txy = dbar_c(yH, -S * b0, p00), txy_m = hasy ? dbar_c(yHm, -S * b0_ym, p00m) : T(0);
         const bool dcell = d.npole > 0 && i >= d.blo[0] && i < d.bhi[0] && j >= d.blo[1] && j < d.bhi[1] &&
                            k >= d.blo[2] && k < d.bhi[2] && d.mask[id];
         const bool gcell = gcol && k >= d.glo[2] && k < d.ghi[2];
@@ -251,10 +254,12 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
             }
             if (gcell) {
                 const int b = (a + 1) % 3, q = (a + 2) % 3;
-                const long long st[3] = {1, (long long)nx, nxy};
+                // -1 neighbours along b and q (this component is not PEC-held, so they exist,
+                // wrapping on a periodic axis)
+                const long long om[3] = {oxm, oym, -nxy};
                 const T* Hq = d.F[3 + q];
                 const T* Hb = d.F[3 + b];
-                const T curl = (Hq[id] - Hq[id - st[b]]) - (Hb[id] - Hb[id - st[q]]);
+                const T curl = (Hq[id] - Hq[id + om[b]]) - (Hb[id] - Hb[id + om[q]]);
                 double delta = (double)(S * curl);
                 if (dcell) {
                     const long long bo = ade_off(d, i, j, k);
@@ -298,7 +303,10 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
     T* B0 = d.A[3];
     T* B1 = d.A[4];
     T* B2 = d.A[5];
-    const bool xe = i + 1 < nx, ye = j + 1 < ny;
+    bool xe, ye;   // the +x / +y neighbour exists (wraps on a periodic axis)
+    const long long oxp = nb_plus(i, nx, 1, d.per[0], &xe);
+    const long long oyp = nb_plus(j, ny, nx, d.per[1], &ye);
+    const bool pi = i == 0 && !d.per[0], pj = j == 0 && !d.per[1];   // PEC plane at this column
     // H-node coefficients (own psibar_H); E-node coefficients at this column and the +1 one
     const CpmlC<T> xH = cpml_c(d, d.cH[0], 0, i), yH = cpml_c(d, d.cH[1], 1, j);
     const CpmlC<T> xE = cpml_c(d, d.cE[0], 0, i), xEp = cpml_c(d, d.cE[0], 0, i + 1);
@@ -315,8 +323,8 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
         const CpmlC<T> zE = cpml_c(d, d.cE[2], 2, k);
         const long long o = zE.s >= 0 ? off_z(d, zE.s, i, j) : 0;
         // E_y is PEC-held where i == 0 or k == 0; E_x where j == 0 or k == 0
-        ty = (i == 0 || k == 0) ? T(0) : dbar_c(zE, A1[idk], zE.s >= 0 ? d.apsiE[1][0][o] : T(0));
-        tx = (j == 0 || k == 0) ? T(0) : dbar_c(zE, -A0[idk], zE.s >= 0 ? d.apsiE[0][1][o] : T(0));
+        ty = (pi || k == 0) ? T(0) : dbar_c(zE, A1[idk], zE.s >= 0 ? d.apsiE[1][0][o] : T(0));
+        tx = (pj || k == 0) ? T(0) : dbar_c(zE, -A0[idk], zE.s >= 0 ? d.apsiE[0][1][o] : T(0));
     };
     T tyz_k, txz_k;
     zterms(t.z0, id, tyz_k, txz_k);
@@ -327,24 +335,25 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
         const CpmlC<T> zH = cpml_c(d, d.cH[2], 2, k);
         const T b0 = B0[id], b1 = B1[id], b2 = B2[id];
         const T f0 = A0[id], f1 = A1[id], f2 = A2[id];
-        const T f2_xp = xe ? A2[id + 1] : T(0), f1_xp = xe ? A1[id + 1] : T(0);
-        const T f2_yp = ye ? A2[id + nx] : T(0), f0_yp = ye ? A0[id + nx] : T(0);
+        const T f2_xp = xe ? A2[id + oxp] : T(0), f1_xp = xe ? A1[id + oxp] : T(0);
+        const T f2_yp = ye ? A2[id + oyp] : T(0), f0_yp = ye ? A0[id + oyp] : T(0);
         // E-derivative cotangents: E_e's s = 0 has ybar = +F, s = 1 has ybar = -F; PEC nodes give 0
         // H_x gathers E_y s=0 (z) and E_z s=1 (y); H_y gathers E_z s=0 (x) and E_x s=1 (z);
         // H_z gathers E_x s=0 (y) and E_y s=1 (x)
-        const T tzy = (i == 0 || j == 0) ? T(0)
-                                         : dbar_c(yE, -f2, yE.s >= 0 ? d.apsiE[2][1][off_y(d, yE.s, i, k)] : T(0));
-        const T tzy_p = (!ye || i == 0) ? T(0)
-                                        : dbar_c(yEp, -f2_yp, yEp.s >= 0 ? d.apsiE[2][1][off_y(d, yEp.s, i, k)] : T(0));
-        const T tzx = (i == 0 || j == 0) ? T(0)
-                                         : dbar_c(xE, f2, xE.s >= 0 ? d.apsiE[2][0][off_x(d, xE.s, j, k)] : T(0));
-        const T tzx_p = (!xe || j == 0) ? T(0)
-                                        : dbar_c(xEp, f2_xp, xEp.s >= 0 ? d.apsiE[2][0][off_x(d, xEp.s, j, k)] : T(0));
-        const T txy = (pk || j == 0) ? T(0)
-                                     : dbar_c(yE, f0, yE.s >= 0 ? d.apsiE[0][0][off_y(d, yE.s, i, k)] : T(0));
+        // (a +1 neighbour reached by wrapping lies at coordinate 0 of a periodic axis: no PEC)
+        const T tzy = (pi || pj) ? T(0)
+                                 : dbar_c(yE, -f2, yE.s >= 0 ? d.apsiE[2][1][off_y(d, yE.s, i, k)] : T(0));
+        const T tzy_p = (!ye || pi) ? T(0)
+                                    : dbar_c(yEp, -f2_yp, yEp.s >= 0 ? d.apsiE[2][1][off_y(d, yEp.s, i, k)] : T(0));
+        const T tzx = (pi || pj) ? T(0)
+                                 : dbar_c(xE, f2, xE.s >= 0 ? d.apsiE[2][0][off_x(d, xE.s, j, k)] : T(0));
+        const T tzx_p = (!xe || pj) ? T(0)
+                                    : dbar_c(xEp, f2_xp, xEp.s >= 0 ? d.apsiE[2][0][off_x(d, xEp.s, j, k)] : T(0));
+        const T txy = (pk || pj) ? T(0)
+                                 : dbar_c(yE, f0, yE.s >= 0 ? d.apsiE[0][0][off_y(d, yE.s, i, k)] : T(0));
         const T txy_p = (!ye || pk) ? T(0)
                                     : dbar_c(yEp, f0_yp, yEp.s >= 0 ? d.apsiE[0][0][off_y(d, yEp.s, i, k)] : T(0));
-        const T tyx = (pk || i == 0) ? T(0)
+        const T tyx = (pk || pi) ? T(0)
                                      : dbar_c(xE, -f1, xE.s >= 0 ? d.apsiE[1][1][off_x(d, xE.s, j, k)] : T(0));
         const T tyx_p = (!xe || pk) ? T(0)
                                     : dbar_c(xEp, -f1_xp, xEp.s >= 0 ? d.apsiE[1][1][off_x(d, xEp.s, j, k)] : T(0));
@@ -524,7 +533,7 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_adj_flush(const Dom<T>* __re
         const bool dcell = d.npole > 0 && d.mask[id] && in_ade_box(d, i, j, k);
         for (int a = 0; a < 3; ++a) {
             const int b = (a + 1) % 3, q = (a + 2) % 3;
-            if (c[b] == 0 || c[q] == 0) continue;
+            if ((c[b] == 0 && !d.per[b]) || (c[q] == 0 && !d.per[q])) continue;   // PEC-held
             d.A[a][id] = e_deferred(d, a, i, j, k, id, dcell, d.A[a][id], S);
         }
     }

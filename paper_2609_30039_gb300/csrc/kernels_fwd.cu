@@ -345,12 +345,16 @@ __device__ __forceinline__ void tile_e(const Dom<T>* __restrict__ doms, const Ti
     const T* ie1 = d.ie[1];
     const T* ie2 = d.ie[2];
     Cpml1<T> cx, cy;
-    bool pi = false, pj = false;
+    bool pi = false, pj = false;              // PEC plane at this column's x / y
+    bool hasx = true, hasy = true;            // the -x / -y neighbour exists (wraps if periodic)
+    long long oxm = -1, oym = -(long long)nx;
     if (kGen) {
         cx = cpml_at(d, d.cE[0], 0, i);
         cy = cpml_at(d, d.cE[1], 1, j);
-        pi = i == 0;
-        pj = j == 0;
+        pi = i == 0 && !d.per[0];
+        pj = j == 0 && !d.per[1];
+        oxm = nb_minus(i, nx, 1, d.per[0], &hasx);
+        oym = nb_minus(j, ny, nx, d.per[1], &hasy);
     }
     long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
     T hxz = T(0), hyz = T(0);
@@ -360,10 +364,10 @@ __device__ __forceinline__ void tile_e(const Dom<T>* __restrict__ doms, const Ti
     }
     for (int k = t.z0; k < t.z1; ++k, id += nxy) {
         const T hx = Hx[id], hy = Hy[id], hz = Hz[id];
-        const T hz_ym = (!kGen || !pj) ? Hz[id - nx] : T(0);
-        const T hx_ym = (!kGen || !pj) ? Hx[id - nx] : T(0);
-        const T hz_xm = (!kGen || !pi) ? Hz[id - 1] : T(0);
-        const T hy_xm = (!kGen || !pi) ? Hy[id - 1] : T(0);
+        const T hz_ym = (!kGen || hasy) ? Hz[id + oym] : T(0);
+        const T hx_ym = (!kGen || hasy) ? Hx[id + oym] : T(0);
+        const T hz_xm = (!kGen || hasx) ? Hz[id + oxm] : T(0);
+        const T hy_xm = (!kGen || hasx) ? Hy[id + oxm] : T(0);
         T ex = Ex[id], ey = Ey[id], ez = Ez[id];
         const T iex = ie0[id];
         const T iey = kAniso ? ie1[id] : iex;
@@ -454,12 +458,13 @@ __device__ __forceinline__ void tile_h(const Dom<T>* __restrict__ doms, const Ti
         T* Hy = d.F[4];
         T* Hz = d.F[5];
         Cpml1<T> cx, cy;
-        bool xe = true, ye = true;  // the +x / +y neighbour node exists
+        bool xe = true, ye = true;  // the +x / +y neighbour node exists (wraps if periodic)
+        long long oxp = 1, oyp = nx;
         if (kGen) {
             cx = cpml_at(d, d.cH[0], 0, i);
             cy = cpml_at(d, d.cH[1], 1, j);
-            xe = i + 1 < nx;
-            ye = j + 1 < ny;
+            oxp = nb_plus(i, nx, 1, d.per[0], &xe);
+            oyp = nb_plus(j, ny, nx, d.per[1], &ye);
         }
         long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
         T exk = Ex[id], eyk = Ey[id];
@@ -468,10 +473,10 @@ __device__ __forceinline__ void tile_h(const Dom<T>* __restrict__ doms, const Ti
             const T exn = ze ? Ex[id + nxy] : T(0);
             const T eyn = ze ? Ey[id + nxy] : T(0);
             const T ez = Ez[id];
-            const T ez_yp = ye ? Ez[id + nx] : T(0);
-            const T ez_xp = xe ? Ez[id + 1] : T(0);
-            const T ey_xp = xe ? Ey[id + 1] : T(0);
-            const T ex_yp = ye ? Ex[id + nx] : T(0);
+            const T ez_yp = ye ? Ez[id + oyp] : T(0);
+            const T ez_xp = xe ? Ez[id + oxp] : T(0);
+            const T ey_xp = xe ? Ey[id + oxp] : T(0);
+            const T ex_yp = ye ? Ex[id + oyp] : T(0);
             const T hx = Hx[id], hy = Hy[id], hz = Hz[id];
             T yx1 = ez_yp - ez, yx2 = eyn - eyk;  // Hx: dEz/dy, dEy/dz
             T yy1 = exn - exk, yy2 = ez_xp - ez;  // Hy: dEx/dz, dEz/dx
@@ -565,7 +570,7 @@ __device__ __forceinline__ T cpml_cell(const T* coef, int N, int x, T* psi, T D)
     return cpml_rec(coef[x], coef[N + x], coef[2 * N + x], psi, D);
 }
 
-template <typename T, bool kAniso, bool kPoles>
+template <typename T, bool kAniso, bool kPoles, bool kPer>
 __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
     k_e_cell(const CellArgs<T> c, const Dom<T>* __restrict__ doms, T S, const StepArgs a) {
     const int nx = c.n[0], ny = c.n[1];
@@ -573,18 +578,24 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
     if (i >= nx || j >= ny) return;
     const long long nxy = (long long)nx * ny;
     const long long id = ((long long)k * ny + j) * nx + i;
+    // -1 neighbours (wrapping on a periodic axis); a PEC plane holds tangential E at coordinate 0
+    bool hx_, hy_, hz_;
+    const long long ox = nb_minus(i, nx, 1, kPer && c.per[0], &hx_);
+    const long long oy = nb_minus(j, ny, nx, kPer && c.per[1], &hy_);
+    const long long oz = nb_minus(k, c.n[2], nxy, 0, &hz_);
     const T* Hx = c.F[3];
     const T* Hy = c.F[4];
     const T* Hz = c.F[5];
     const T hx = Hx[id], hy = Hy[id], hz = Hz[id];
-    T yx1 = hz - (j > 0 ? Hz[id - nx] : T(0)), yx2 = hy - (k > 0 ? Hy[id - nxy] : T(0));  // Ex: dHz/dy, dHy/dz
-    T yy1 = hx - (k > 0 ? Hx[id - nxy] : T(0)), yy2 = hz - (i > 0 ? Hz[id - 1] : T(0));   // Ey: dHx/dz, dHz/dx
-    T yz1 = hy - (i > 0 ? Hy[id - 1] : T(0)), yz2 = hx - (j > 0 ? Hx[id - nx] : T(0));    // Ez: dHy/dx, dHx/dy
+    T yx1 = hz - (hy_ ? Hz[id + oy] : T(0)), yx2 = hy - (hz_ ? Hy[id + oz] : T(0));  // Ex: dHz/dy, dHy/dz
+    T yy1 = hx - (hz_ ? Hx[id + oz] : T(0)), yy2 = hz - (hx_ ? Hz[id + ox] : T(0));  // Ey: dHx/dz, dHz/dx
+    T yz1 = hy - (hx_ ? Hy[id + ox] : T(0)), yz2 = hx - (hy_ ? Hx[id + oy] : T(0));  // Ez: dHy/dx, dHx/dy
     T ex = c.F[0][id], ey = c.F[1][id], ez = c.F[2][id];
     const T iex = c.ie[0][id];
     const T iey = kAniso ? c.ie[1][id] : iex;
     const T iez = kAniso ? c.ie[2][id] : iex;
-    const bool px = j == 0 || k == 0, py = i == 0 || k == 0, pz = i == 0 || j == 0;   // PEC-held
+    const bool pi = i == 0 && !(kPer && c.per[0]), pj = j == 0 && !(kPer && c.per[1]), pk = k == 0;
+    const bool px = pj || pk, py = pi || pk, pz = pi || pj;   // PEC-held
     if (c.ns[2]) {
         const int sl = slab_of(k, c.dlo[2], c.dhi[2], c.n[2]);
         if (sl >= 0) {
@@ -636,7 +647,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
     if (!pz) c.F[2][id] = ez;
 }
 
-template <typename T>
+template <typename T, bool kPer>
 __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
     k_h_cell(const CellArgs<T> c, T S, const StepArgs a, unsigned advance_blocks) {
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
@@ -647,11 +658,14 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
         const T* Ex = c.F[0];
         const T* Ey = c.F[1];
         const T* Ez = c.F[2];
-        const bool xe = i + 1 < nx, ye = j + 1 < ny, ze = k + 1 < nz;   // the + neighbour exists
+        bool xe, ye, ze;   // the + neighbour exists (wraps on a periodic axis)
+        const long long ox = nb_plus(i, nx, 1, kPer && c.per[0], &xe);
+        const long long oy = nb_plus(j, ny, nx, kPer && c.per[1], &ye);
+        const long long oz = nb_plus(k, nz, nxy, 0, &ze);
         const T exk = Ex[id], eyk = Ey[id], ez = Ez[id];
-        T yx1 = (ye ? Ez[id + nx] : T(0)) - ez, yx2 = (ze ? Ey[id + nxy] : T(0)) - eyk;   // Hx: dEz/dy, dEy/dz
-        T yy1 = (ze ? Ex[id + nxy] : T(0)) - exk, yy2 = (xe ? Ez[id + 1] : T(0)) - ez;     // Hy: dEx/dz, dEz/dx
-        T yz1 = (xe ? Ey[id + 1] : T(0)) - eyk, yz2 = (ye ? Ex[id + nx] : T(0)) - exk;     // Hz: dEy/dx, dEx/dy
+        T yx1 = (ye ? Ez[id + oy] : T(0)) - ez, yx2 = (ze ? Ey[id + oz] : T(0)) - eyk;   // Hx: dEz/dy, dEy/dz
+        T yy1 = (ze ? Ex[id + oz] : T(0)) - exk, yy2 = (xe ? Ez[id + ox] : T(0)) - ez;   // Hy: dEx/dz, dEz/dx
+        T yz1 = (xe ? Ey[id + ox] : T(0)) - eyk, yz2 = (ye ? Ex[id + oy] : T(0)) - exk;  // Hz: dEy/dx, dEx/dy
         const T hx = c.F[3][id], hy = c.F[4][id], hz = c.F[5][id];
         if (c.ns[2]) {
             const int sl = slab_of(k, c.dlo[2], c.dhi[2], nz);
@@ -711,20 +725,34 @@ inline dim3 cell_grid(const int* n) {
     return dim3((unsigned)((n[0] + kTileX - 1) / kTileX), (unsigned)((n[1] + kTileY - 1) / kTileY), (unsigned)n[2]);
 }
 
+template <typename T, bool kPer>
+static void launch_e_cell_t(const Launch& L, const CellArgs<T>& c, const Dom<T>* doms, T S, const StepArgs& a,
+                            int aniso, int poles) {
+    const dim3 g = cell_grid(c.n), b(kTileX, kTileY);
+    if (poles)
+        (aniso ? k_e_cell<T, true, true, kPer> : k_e_cell<T, false, true, kPer>)<<<g, b, 0, L.stream>>>(c, doms, S, a);
+    else
+        (aniso ? k_e_cell<T, true, false, kPer> : k_e_cell<T, false, false, kPer>)<<<g, b, 0, L.stream>>>(c, doms, S,
+                                                                                                         a);
+}
+
 template <typename T>
 void launch_e_cell(const Launch& L, const CellArgs<T>& c, const Dom<T>* doms, T S, const StepArgs& a, int aniso,
                    int poles) {
-    const dim3 g = cell_grid(c.n), b(kTileX, kTileY);
-    if (poles)
-        (aniso ? k_e_cell<T, true, true> : k_e_cell<T, false, true>)<<<g, b, 0, L.stream>>>(c, doms, S, a);
+    if (c.per[0] || c.per[1])
+        launch_e_cell_t<T, true>(L, c, doms, S, a, aniso, poles);
     else
-        (aniso ? k_e_cell<T, true, false> : k_e_cell<T, false, false>)<<<g, b, 0, L.stream>>>(c, doms, S, a);
+        launch_e_cell_t<T, false>(L, c, doms, S, a, aniso, poles);
     ++*L.counter;
 }
 
 template <typename T>
 void launch_h_cell(const Launch& L, const CellArgs<T>& c, T S, const StepArgs& a, unsigned advance) {
-    k_h_cell<T><<<cell_grid(c.n), dim3(kTileX, kTileY), 0, L.stream>>>(c, S, a, advance);
+    const dim3 g = cell_grid(c.n), b(kTileX, kTileY);
+    if (c.per[0] || c.per[1])
+        k_h_cell<T, true><<<g, b, 0, L.stream>>>(c, S, a, advance);
+    else
+        k_h_cell<T, false><<<g, b, 0, L.stream>>>(c, S, a, advance);
     ++*L.counter;
 }
 

@@ -73,6 +73,7 @@ _SIGS = {
     "fdtd_last_error": [_ctx],
     "fdtd_version": [],
     "fdtd_set_material": [_ctx, C.c_int32, C.POINTER(fdtd_material)],
+    "fdtd_set_periodic": [_ctx, C.c_int32, _i32p],
     "fdtd_add_source": [_ctx, C.c_int32, C.c_int32, _i32p, _i32p, C.POINTER(C.c_double), C.c_int32, _i32p],
     "fdtd_add_dft_monitor": [_ctx, C.c_int32, _i32p, _i32p, C.c_uint32, C.c_int32, C.POINTER(C.c_double),
                              _i32p],
@@ -267,6 +268,11 @@ def fdtd_part_count(ctx, domain):
     return int(v.value)
 
 
+def fdtd_set_periodic(ctx, domain, periodic):
+    arr = (C.c_int32 * 3)(*[int(v) for v in periodic])
+    _check(load().fdtd_set_periodic(ctx, int(domain), arr), "fdtd_set_periodic", ctx)
+
+
 def fdtd_set_material(ctx, domain, material):
     _check(load().fdtd_set_material(ctx, int(domain), C.byref(material)), "fdtd_set_material", ctx)
 
@@ -361,6 +367,8 @@ class Context:
         self.monitors = []
         self.sources = []
         for d, sc in enumerate(self.scenes):
+            if any(sc.periodic):
+                fdtd_set_periodic(self.ctx, d, sc.periodic)
             for s in sc.sources:
                 self.sources.append(fdtd_add_source(self.ctx, d, s.comp, s.lo, s.hi, s.wave))
             for m in sc.monitors:

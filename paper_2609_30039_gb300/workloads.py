@@ -61,6 +61,7 @@ class Scene:
     rho: Optional[np.ndarray] = None            # design densities
     energy: bool = False
     name: str = ""
+    periodic: Tuple[int, int, int] = (0, 0, 0)   # periodic x / y (z must be 0)
 
     @property
     def cells(self) -> int:

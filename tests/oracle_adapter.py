@@ -4,7 +4,9 @@ import numpy as np
 from oracle.oracle import Oracle
 
 
-def oracle_from_scene(sc, with_sources=True, with_monitors=True, periodic=(0, 0, 0)):
+def oracle_from_scene(sc, with_sources=True, with_monitors=True, periodic=None):
+    if periodic is None:
+        periodic = getattr(sc, "periodic", (0, 0, 0))
     o = Oracle(sc.shape, sc.courant, periodic=periodic, cpml=sc.cpml, m=sc.cpml_m,
                kappa_max=sc.kappa_max, alpha_max=sc.alpha_max, sigma_max=sc.sigma_max)
     o.set_material(sc.inv_eps3(), poles=sc.poles, mask=sc.pole_mask)

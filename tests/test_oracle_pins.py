@@ -10,7 +10,10 @@ method (Sec. 2-3 of arxiv 2609.30039) or by the mathematics of the Yee scheme:
   * the half-step DFT time offsets (Sec. 2.1, 2.4);
   * dot-product transpose identity and central finite differences with a quadratic
     Taylor remainder for the discrete adjoint (Sec. 3.1, Eq. (adjoint); Sec. 5.2);
-  * checkpoint replay is bitwise equal to store-all (Sec. 3.2).
+  * checkpoint replay is bitwise equal to store-all (Sec. 3.2);
+  * plane-monitor flux (Sec. 2.4) through a slab in a periodic cell (Sec. 2.2) against an
+    independent frequency-domain solve of the same 1-D lattice, energy balance R + T = 1, the
+    continuum Fabry-Perot formula within its O(k h) error, and lossless vacuum propagation.
 A plausible slip anywhere in the oracle (a dropped term, a sign, an index, a transposed
 coefficient) fails at least one of these.
 """
@@ -348,3 +351,77 @@ def test_replay_segments_bitwise_equal_store_all():
     for gg in grads[1:]:
         for a in range(3):
             assert np.array_equal(gg[a], grads[0][a])
+
+
+# ---- plane flux and periodic cells (Sec. 2.2 periodic faces, Sec. 2.4 plane monitors) ----------
+def _slab_runs(n_idx=1.5, L=20, steps=3000):
+    """Quasi-1-D run: a 2 x 2 periodic cell (a plane wave), CPML on both z faces, an Ex sheet,
+    a reflection plane between sheet and slab and a transmission plane beyond it."""
+    from oracle.flux import plane_flux_z
+    S = W.COURANT
+    nz, d, z1, zs, zr, zt = 260, 16, 140, 26, 60, 200
+    lams = np.array([30.0, 40.0, 50.0, 60.0])
+    om = W.omegas_for(lams)
+    wave = W.gaussian_pulse(steps, wavelength=40.0, periods=1.0, delay=3.0)
+    out = {}
+    for slab in (False, True):
+        o = Oracle((2, 2, nz), S, periodic=(1, 1, 0), cpml=(0, 0, 0, 0, d, d), m=3.0, kappa_max=1.0, alpha_max=0.0)
+        ie = np.ones((nz, 2, 2))
+        if slab:
+            ie[z1:z1 + L] = 1.0 / n_idx ** 2
+        o.set_material([ie, ie, ie])
+        o.add_source(0, (0, 0, zs), (2, 2, zs + 1), wave)
+        o.add_dft_box((0, 0, zr), (2, 2, zr + 2), (0, 1, 3, 4), om)
+        o.add_dft_box((0, 0, zt), (2, 2, zt + 2), (0, 1, 3, 4), om)
+        o.step(steps)
+        out[slab] = (plane_flux_z(o.dft(0), (0, 1, 3, 4)), plane_flux_z(o.dft(1), (0, 1, 3, 4)))
+    T = out[True][1] / out[False][1]
+    R = 1.0 - out[True][0] / out[False][0]
+    return T, R, om, S, n_idx, L
+
+
+def test_slab_transmission_matches_exact_lattice_solution():
+    # time stepping + running DFT + Yee-interpolated flux against an independent frequency-domain
+    # solve of the same lattice (transfer relations marched node by node); the residual is the
+    # CPML reflection and the pulse tail, far below the continuum formula's O(k h) interface error
+    from oracle.flux import lattice_transmission, slab_transmission
+    T, R, om, S, n_idx, L = _slab_runs()
+    T_ex, R_ex = lattice_transmission(np.full(L, 1.0 / n_idx ** 2), om, S, reflection=True)
+    assert np.max(np.abs(T - T_ex)) < 2e-5
+    assert np.max(np.abs(R - R_ex)) < 2e-5
+    # energy balance of a lossless slab: the flux weights E and H correctly
+    assert np.max(np.abs(R + T - 1.0)) < 3e-5
+    # and the continuum Fabry-Perot formula within its O(k h) interface error
+    T_fp = slab_transmission(n_idx, L, 2.0 * np.pi * S / om, courant=S)
+    assert np.max(np.abs(T - T_fp)) < 4e-3
+
+
+def test_lattice_transmission_limits():
+    from oracle.flux import lattice_transmission, slab_transmission
+    S = W.COURANT
+    # vacuum "slab": total transmission; a very long wavelength: the continuum formula
+    assert np.allclose(lattice_transmission(np.ones(30), np.array([0.1, 0.3]), S), 1.0, atol=1e-12)
+    om = np.array([2 * np.pi * S / 4000.0])
+    T = lattice_transmission(np.full(10, 1 / 4.0), om, S)
+    assert abs(T[0] - slab_transmission(2.0, 10, 4000.0)) < 1e-6
+    # a quarter-wave-thick layer at its design wavelength on the lattice: minimum transmission
+    T, R = lattice_transmission(np.full(10, 1 / 2.25), np.array([0.05, 0.2]), S, reflection=True)
+    assert np.allclose(R + T, 1.0, atol=1e-12)
+
+
+def test_periodic_plane_flux_is_uniform_in_z_for_vacuum():
+    # lossless vacuum propagation: the same flux crosses two planes
+    from oracle.flux import plane_flux_z
+    S = W.COURANT
+    nz, d, steps = 200, 16, 2500
+    om = W.omegas_for([30.0, 45.0])
+    wave = W.gaussian_pulse(steps, wavelength=40.0, periods=1.0, delay=3.0)
+    o = Oracle((2, 2, nz), S, periodic=(1, 1, 0), cpml=(0, 0, 0, 0, d, d), m=3.0, kappa_max=1.0, alpha_max=0.0)
+    o.set_material([np.ones((nz, 2, 2))] * 3)
+    o.add_source(0, (0, 0, 30), (2, 2, 31), wave)
+    o.add_dft_box((0, 0, 80), (2, 2, 82), (0, 1, 3, 4), om)
+    o.add_dft_box((0, 0, 150), (2, 2, 152), (0, 1, 3, 4), om)
+    o.step(steps)
+    p1 = plane_flux_z(o.dft(0), (0, 1, 3, 4))
+    p2 = plane_flux_z(o.dft(1), (0, 1, 3, 4))
+    assert np.all(p1 > 0) and np.max(np.abs(p2 / p1 - 1.0)) < 1e-5
