@@ -127,6 +127,16 @@ const char* fdtd_version(void);
  * set of dispersive cells must not grow beyond the box chosen at create: FDTD_EINVAL). */
 fdtd_status fdtd_set_material(fdtd_ctx* ctx, int32_t domain, const fdtd_material* material);
 
+/* Net Poynting flux along +z (Sec. 2.4: plane monitors form the signed Poynting flux from
+ * Yee-interpolated spectra) through the plane z = k + 1/2 of a monitor spanning the two z-planes
+ * [k, k+2): P(w) = 1/2 Re sum over the monitor's x-y cells of
+ *   (Ex(k) + Ex(k+1))/2 conj(Hy(k)) - (Ey(k) + Ey(k+1))/2 conj(Hx(k)),
+ * which puts each product at one Yee point (Hy and Hx live on z = k + 1/2).  Spectra carry
+ * their own sample times (E: t = n+1, H: t = n+3/2), so the magnetic half step is already in
+ * their phases.  The monitor must record Ex, Ey, Hx and Hy (FDTD_EINVAL otherwise).
+ * flux_host: n_freq doubles (host).  Synchronises. */
+fdtd_status fdtd_dft_flux(fdtd_ctx* ctx, int32_t monitor, double* flux_host);
+
 /* Periodic boundaries (Sec. 2.2: periodic/Bloch lateral boundaries, here with zero Bloch
  * phase) on the x and/or y axis of one domain: the neighbour beyond the last node is the first
  * one and vice versa, and the coordinate-0 plane of that axis is no PEC wall.  periodic[3] are
@@ -137,7 +147,9 @@ fdtd_status fdtd_set_periodic(fdtd_ctx* ctx, int32_t domain, const int32_t perio
 
 /* Soft source (Sec. 2.4, Eq. (yee) s and m): after the update of `component` in forward
  * step n, every cell of the half-open box [lo, hi) gets += waveform[n] (no effect for
- * n >= n_steps).  waveform: host, copied, FP64.  *source_id may be NULL. */
+ * n >= n_steps).  waveform: host, copied, FP64.  *source_id may be NULL.  An electric source
+ * box may not hold PEC-held nodes (coordinate 0 of a non-periodic axis other than the
+ * component's own: FDTD_EINVAL), so mark periodic axes before adding a source on their seam. */
 fdtd_status fdtd_add_source(fdtd_ctx* ctx, int32_t domain, int32_t component, const int32_t lo[3],
                             const int32_t hi[3], const double* waveform, int32_t n_steps,
                             int32_t* source_id);

@@ -1241,6 +1241,31 @@ fdtd_status fdtd_destroy(fdtd_ctx* ctx) {
     return FDTD_OK;
 }
 
+fdtd_status fdtd_dft_flux(fdtd_ctx* ctx, int32_t monitor, double* flux_host) {
+    GUARD(ctx);
+    if (monitor < 0 || monitor >= (int)ctx->mons.size() || !flux_host)
+        return fail(ctx, FDTD_EINVAL, "bad monitor or output");
+    const Mon& m = ctx->mons[monitor].m;
+    if (m.hi[2] - m.lo[2] != 2) return fail(ctx, FDTD_EINVAL, "a flux monitor spans exactly two z-planes");
+    int slots[4] = {-1, -1, -1, -1};
+    const int want[4] = {0, 1, 3, 4};   // Ex, Ey, Hx, Hy
+    for (int ci = 0; ci < m.ncomp; ++ci)
+        for (int q = 0; q < 4; ++q)
+            if (m.comps[ci] == want[q]) slots[q] = ci;
+    for (int q = 0; q < 4; ++q)
+        if (slots[q] < 0) return fail(ctx, FDTD_EINVAL, "a flux monitor records Ex, Ey, Hx and Hy");
+    double* d_out = nullptr;
+    fdtd_status st = dmalloc(ctx, (void**)&d_out, sizeof(double) * m.nf);
+    if (st != FDTD_OK) return st;
+    launch_flux(L(ctx), ctx->d_mons + monitor, m.nf, slots, d_out);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(flux_host, d_out, sizeof(double) * m.nf, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, d_out);
+    if (e != cudaSuccess) return fail(ctx, FDTD_ECUDA, std::string("flux: ") + cudaGetErrorString(e));
+    return FDTD_OK;
+}
+
 fdtd_status fdtd_set_periodic(fdtd_ctx* ctx, int32_t domain, const int32_t periodic[3]) {
     GUARD(ctx);
     if (!valid_dom(ctx, domain) || !periodic) return fail(ctx, FDTD_EINVAL, "bad domain or periodic flags");
@@ -1297,7 +1322,7 @@ fdtd_status fdtd_add_source(fdtd_ctx* ctx, int32_t domain, int32_t component, co
     if ((int)d.srcs.size() >= kMaxSrcPerDom) return fail(ctx, FDTD_EINVAL, "at most 8 sources per domain");
     if (component < 3)
         for (int q = 0; q < 3; ++q)
-            if (q != component && lo[q] == 0)
+            if (q != component && lo[q] == 0 && !d.per[q])
                 return fail(ctx, FDTD_EINVAL, "an electric source box must not include PEC-held nodes (coordinate 0)");
     for (auto& s : ctx->srcs) {
         if (s.s.dom != domain || s.s.comp != component) continue;

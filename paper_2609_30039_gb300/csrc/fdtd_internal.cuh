@@ -276,6 +276,8 @@ void launch_inject(const Launch& L, const Dom<T>* doms, const Mon* mons, const i
                    long long nthreads, const long long* entry_begin, int step, int kind);
 
 // Auxiliary kernels (kernels_aux.cu)
+// Flux through the H plane of a two-plane monitor; slots: accumulator slots of Ex, Ey, Hx, Hy.
+void launch_flux(const Launch& L, const Mon* mon, int nf, const int* slots, double* out);
 template <typename T>
 void launch_admission(const Launch& L, const Dom<T>* d_dom, const Dom<T>& h_dom, unsigned long long* d_bad);
 void launch_mask_box(const Launch& L, const uint8_t* mask, int nx, int ny, int nz, int* d_box);

@@ -89,6 +89,43 @@ __global__ void k_bf16_decode(const __nv_bfloat16* __restrict__ src, const float
         dst[base + t] = (T)(__bfloat162float(src[base + t]) * s);
 }
 
+// Net Poynting flux along +z through the H plane of a two-plane monitor (Sec. 2.4), one block
+// per frequency: P = 1/2 Re sum [ (Ex(k) + Ex(k+1))/2 conj(Hy(k)) - (Ey(k) + Ey(k+1))/2 conj(Hx(k)) ]
+// over the monitor's x-y cells.  sEx..sHy: accumulator slots of the four components.
+__global__ void __launch_bounds__(256) k_flux(const Mon* __restrict__ mon, int sEx, int sEy, int sHx, int sHy,
+                                              double* __restrict__ out) {
+    const Mon& m = *mon;
+    const int f = blockIdx.x;
+    const long long plane = (long long)m.bx * m.by;
+    const double2* ex = m.acc + ((long long)sEx * m.nf + f) * m.ncell;
+    const double2* ey = m.acc + ((long long)sEy * m.nf + f) * m.ncell;
+    const double2* hx = m.acc + ((long long)sHx * m.nf + f) * m.ncell;
+    const double2* hy = m.acc + ((long long)sHy * m.nf + f) * m.ncell;
+    double sum = 0.0;
+    for (long long c = threadIdx.x; c < plane; c += blockDim.x) {
+        const double2 a0 = ex[c], a1 = ex[c + plane], b0 = ey[c], b1 = ey[c + plane];
+        const double2 gx = hx[c], gy = hy[c];
+        const double exr = 0.5 * (a0.x + a1.x), exi = 0.5 * (a0.y + a1.y);
+        const double eyr = 0.5 * (b0.x + b1.x), eyi = 0.5 * (b0.y + b1.y);
+        // Re(E conj(H)) = Er Hr + Ei Hi
+        sum += 0.5 * ((exr * gy.x + exi * gy.y) - (eyr * gx.x + eyi * gx.y));
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[f] = red[0];
+}
+
+void launch_flux(const Launch& L, const Mon* mon, int nf, const int* slots, double* out) {
+    if (nf <= 0) return;
+    k_flux<<<nf, 256, 0, L.stream>>>(mon, slots[0], slots[1], slots[2], slots[3], out);
+    ++*L.counter;
+}
+
 template <typename T>
 void launch_admission(const Launch& L, const Dom<T>* d_dom, const Dom<T>& h_dom, unsigned long long* d_bad) {
     const int bs = 256;

@@ -74,6 +74,7 @@ _SIGS = {
     "fdtd_version": [],
     "fdtd_set_material": [_ctx, C.c_int32, C.POINTER(fdtd_material)],
     "fdtd_set_periodic": [_ctx, C.c_int32, _i32p],
+    "fdtd_dft_flux": [_ctx, C.c_int32, C.POINTER(C.c_double)],
     "fdtd_add_source": [_ctx, C.c_int32, C.c_int32, _i32p, _i32p, C.POINTER(C.c_double), C.c_int32, _i32p],
     "fdtd_add_dft_monitor": [_ctx, C.c_int32, _i32p, _i32p, C.c_uint32, C.c_int32, C.POINTER(C.c_double),
                              _i32p],
@@ -266,6 +267,13 @@ def fdtd_part_count(ctx, domain):
     v = C.c_int32()
     _check(load().fdtd_part_count(ctx, int(domain), C.byref(v)), "fdtd_part_count", ctx)
     return int(v.value)
+
+
+def fdtd_dft_flux(ctx, monitor, n_freq):
+    """Net +z Poynting flux per frequency through a two-plane monitor (numpy array)."""
+    out = np.zeros(int(n_freq), dtype=np.float64)
+    _check(load().fdtd_dft_flux(ctx, int(monitor), out.ctypes.data_as(C.POINTER(C.c_double))), "fdtd_dft_flux", ctx)
+    return out
 
 
 def fdtd_set_periodic(ctx, domain, periodic):

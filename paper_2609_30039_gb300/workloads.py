@@ -231,24 +231,67 @@ def large_adjoint(n: int = 640, d: int = 16, n_steps: int = 4000, seed_index: in
 
 
 def random_state_scene(shape=(9, 8, 7), d: int = 2, n_poles: int = 2, aniso: bool = True,
-                       seed_index: int = 11) -> Scene:
-    """Tiny grid with CPML on every face, anisotropic eps and a dispersive box: the operator
-    under the dot-product (transpose) tests."""
+                       seed_index: int = 11, periodic: bool = False) -> Scene:
+    """Tiny grid with CPML on every face (periodic: x and y periodic, CPML on the z faces only),
+    anisotropic eps and a dispersive box: the operator under the dot-product (transpose) tests."""
     rng = _rng(seed_index)
     nx, ny, nz = shape
     inv = [1.0 / rng.uniform(1.0, 4.0, size=(nz, ny, nx)) for _ in range(3 if aniso else 1)]
     if aniso and d > 0:
         # inside the absorbing slabs the tensor must pass the admission rule: keep it isotropic
         slab = np.zeros((nz, ny, nx), dtype=bool)
-        slab[:d], slab[nz - d:], slab[:, :d], slab[:, ny - d:], slab[:, :, :d], slab[:, :, nx - d:] = (True,) * 6
+        slab[:d], slab[nz - d:] = True, True
+        if not periodic:
+            slab[:, :d], slab[:, ny - d:], slab[:, :, :d], slab[:, :, nx - d:] = (True,) * 4
         for a in (1, 2):
             inv[a][slab] = inv[0][slab]
     poles = tuple((LORENTZ, float(rng.uniform(0.5, 3.0)), float(rng.uniform(0.05, 0.3)),
                    float(rng.uniform(0.01, 0.05))) for _ in range(n_poles))
     mask = np.zeros((nz, ny, nx), dtype=np.uint8)
     mask[nz // 3: nz - 1, 1: ny - 2, nx // 2: nx] = 1 if n_poles else 0
-    return Scene(shape=shape, n_steps=10, cpml=(d,) * 6, kappa_max=3.0, alpha_max=0.05,
-                 inv_eps=inv, poles=poles, pole_mask=mask, name="random_state")
+    cpml = (0, 0, 0, 0, d, d) if periodic else (d,) * 6
+    return Scene(shape=shape, n_steps=10, cpml=cpml, kappa_max=3.0, alpha_max=0.05,
+                 inv_eps=inv, poles=poles, pole_mask=mask, name="random_state",
+                 periodic=(1, 1, 0) if periodic else (0, 0, 0))
+
+
+def periodic_cell(shape=(24, 20, 48), d: int = 8, n_steps: int = 300, layer=(18, 30), block: int = 4,
+                  seed_index: int = 12, wavelengths=(9.0, 10.0, 11.0)) -> Scene:
+    """Periodic unit cell (x and y periodic, CPML on both z faces): eps_r ~ U[1, 6] per block of
+    block^2 columns in the layer z in [layer), an Ex sheet below it, a two-plane flux monitor
+    (Ex, Ey, Hx, Hy) above it and a plane monitor of all six components inside it."""
+    rng = _rng(seed_index)
+    nx, ny, nz = shape
+    inv = np.ones((nz, ny, nx))
+    bx, by = -(-nx // block), -(-ny // block)
+    eps = rng.uniform(1.0, 6.0, size=(by, bx))
+    inv[layer[0]:layer[1]] = 1.0 / np.repeat(np.repeat(eps, block, 0), block, 1)[:ny, :nx]
+    zs, zt = d + 2, layer[1] + 4
+    src = Source(EX, (0, 0, zs), (nx, ny, zs + 1), gaussian_pulse(n_steps, wavelength=wavelengths[1], periods=1.0,
+                                                                    delay=3.0))
+    om = omegas_for(wavelengths)
+    flux = Monitor((0, 0, zt), (nx, ny, zt + 2), (EX, EY, HX, HY), om)
+    plane = Monitor((0, 0, (layer[0] + layer[1]) // 2), (nx, ny, (layer[0] + layer[1]) // 2 + 1), (0, 1, 2, 3, 4, 5),
+                    om)
+    return Scene(shape=shape, n_steps=n_steps, cpml=(0, 0, 0, 0, d, d), kappa_max=3.0, alpha_max=0.05,
+                 inv_eps=[inv], sources=[src], monitors=[flux, plane], periodic=(1, 1, 0), name="periodic_cell")
+
+
+def slab_cell(n_index: float = 1.5, thickness: int = 20, nz: int = 260, d: int = 16, n_steps: int = 3000,
+              wavelengths=(30.0, 40.0, 50.0, 60.0), with_slab: bool = True) -> Scene:
+    """Normal incidence on a lossless slab: a 2 x 2 periodic cell (a plane wave), CPML on both z
+    faces, an Ex sheet, a reflection flux monitor between sheet and slab and a transmission flux
+    monitor beyond it (the reference run is the same cell with with_slab=False)."""
+    z1, zs, zr, zt = 140, d + 10, 60, 200
+    inv = np.ones((nz, 2, 2))
+    if with_slab:
+        inv[z1:z1 + thickness] = 1.0 / n_index ** 2
+    om = omegas_for(wavelengths)
+    src = Source(EX, (0, 0, zs), (2, 2, zs + 1), gaussian_pulse(n_steps, wavelength=40.0, periods=1.0, delay=3.0))
+    mons = [Monitor((0, 0, zr), (2, 2, zr + 2), (EX, EY, HX, HY), om),
+            Monitor((0, 0, zt), (2, 2, zt + 2), (EX, EY, HX, HY), om)]
+    return Scene(shape=(2, 2, nz), n_steps=n_steps, cpml=(0, 0, 0, 0, d, d), kappa_max=1.0, alpha_max=0.0,
+                 inv_eps=[inv], sources=[src], monitors=mons, periodic=(1, 1, 0), name="slab_cell")
 
 
 def random_state(rng: np.random.Generator, n: int) -> np.ndarray:

@@ -1,0 +1,126 @@
+"""Periodic x-y cells and the plane Poynting flux on the GPU (Sec. 2.2 periodic faces, Sec. 2.4
+plane monitors), through the C ABI, against the FP64 oracle and its pinned flux."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.flux import lattice_transmission, plane_flux_z
+from oracle.oracle import gradient_replay
+from paper_2609_30039_gb300 import adjoint as ADJ
+from paper_2609_30039_gb300 import fdtd
+from paper_2609_30039_gb300 import workloads as W
+from tests.oracle_adapter import oracle_from_scene
+from tests.test_gpu_parity import _gpu_loss, _oracle_objective, _random_parts, _set_parts, compare_state, gpu_parts, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("mode", list(range(5)))
+def test_periodic_cell_fp64_matches_oracle_in_every_launch_mode(mode):
+    sc = W.periodic_cell(n_steps=90)
+    o = oracle_from_scene(sc)
+    o.step(sc.n_steps)
+    ctx = fdtd.Context([sc], dtype="f64")
+    fdtd.fdtd_set_launch_mode(ctx.ctx, mode)
+    ctx.step(40)
+    ctx.step(50)
+    compare_state(ctx, o, sc, tol=1e-12)
+    for k in range(2):
+        assert rel(ctx.dft(k).cpu().numpy(), o.dft(k)) < 1e-12
+
+
+def test_periodic_cell_launch_modes_bitwise_equal_fp32():
+    sc = W.periodic_cell(n_steps=80)
+    outs = []
+    for mode in range(fdtd.LAUNCH_MODES):
+        ctx = fdtd.Context([sc], dtype="f32")
+        fdtd.fdtd_set_launch_mode(ctx.ctx, mode)
+        ctx.step(80)
+        outs.append([ctx.part(0, p).clone() for p in range(ctx.part_count(0))] + [ctx.dft(0).clone()])
+        ctx.close()
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert torch.equal(a, b)
+
+
+def test_periodic_rejects_cpml_on_a_periodic_axis_and_z():
+    sc = W.cpml_blocks(n=24, d=4, n_steps=10, block=4, region=(6, 18), wavelengths=(9.0, 10.0, 11.0))
+    ctx = fdtd.Context([sc], dtype="f32")
+    with pytest.raises(fdtd.FdtdError) as e:
+        fdtd.fdtd_set_periodic(ctx.ctx, 0, (1, 0, 0))
+    assert e.value.status == fdtd.FDTD_EINVAL
+    sc2 = W.periodic_cell(n_steps=10)
+    ctx2 = fdtd.Context([sc2], dtype="f32")
+    with pytest.raises(fdtd.FdtdError):
+        fdtd.fdtd_set_periodic(ctx2.ctx, 0, (1, 1, 1))
+
+
+@pytest.mark.parametrize("nsteps", [1, 7])
+def test_periodic_adjoint_dot_product_fp64(nsteps):
+    # <A x, y> = <x, A^T y> with the wrapped stencils on both sides
+    sc = W.random_state_scene(shape=(10, 9, 12), d=2, n_poles=2, aniso=True, periodic=True)
+    ctx = fdtd.Context([sc], dtype="f64")
+    rng = np.random.default_rng(7 + nsteps)
+    x = _random_parts(ctx, sc, rng)
+    y = _random_parts(ctx, sc, rng)
+    _set_parts(ctx, x, 0)
+    ctx.step(nsteps)
+    fx = gpu_parts(ctx, 0, 0)
+    fdtd.fdtd_adjoint_begin(ctx.ctx)
+    _set_parts(ctx, y, 1)
+    fdtd.fdtd_step_adjoint(ctx.ctx, nsteps)
+    fty = gpu_parts(ctx, 0, 1)
+    lhs = sum(float(a @ b) for a, b in zip(fx, y))
+    rhs = sum(float(a @ b) for a, b in zip(x, fty))
+    scale = np.sqrt(sum(float(a @ a) for a in fx) * sum(float(b @ b) for b in y))
+    assert abs(lhs - rhs) <= 1e-10 * scale, (lhs, rhs)
+
+
+def test_periodic_gradient_across_the_seam_matches_oracle_fp64():
+    # a design box that straddles the x = 0 seam of the periodic cell: the material cotangent
+    # there needs the wrapped -x neighbour of the transposed stencil
+    sc = W.periodic_cell(shape=(12, 10, 30), d=5, n_steps=60, layer=(12, 18), block=3)
+    sc.design = ((0, 2, 12), (5, 8, 18))
+    sc.monitors = [W.Monitor((0, 0, 22), (12, 10, 23), (W.EX,), W.omegas_for((9.0, 10.0)))]
+    o = oracle_from_scene(sc)
+    J_ref = gradient_replay(o, sc.n_steps, _oracle_objective)
+    g_ref = np.stack([o.grad(a) for a in range(3)])
+    ctx = fdtd.Context([sc], dtype="f64")
+    (J, _), grads, _ = ADJ.DesignAdjoint(ctx, slots=8).run(sc.n_steps, _gpu_loss)
+    assert abs(J - J_ref) <= 1e-12 * abs(J_ref)
+    g = grads[0].cpu().numpy().reshape(g_ref.shape)
+    assert rel(g, g_ref) < 1e-10, rel(g, g_ref)
+
+
+def test_flux_fp64_matches_oracle_and_fp32_slab_transmission_matches_lattice():
+    fluxes = {}
+    for slab in (False, True):
+        sc = W.slab_cell(with_slab=slab)
+        nf = len(sc.monitors[0].omegas)
+        o = oracle_from_scene(sc)
+        o.step(sc.n_steps)
+        ctx = fdtd.Context([sc], dtype="f64")
+        ctx.step(sc.n_steps)
+        for k in range(2):
+            got = fdtd.fdtd_dft_flux(ctx.ctx, ctx.monitors[k][0], nf)
+            ref = plane_flux_z(o.dft(k), (0, 1, 3, 4))
+            assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref)), (got, ref)
+        c32 = fdtd.Context([sc], dtype="f32")
+        c32.step(sc.n_steps)
+        fluxes[slab] = [fdtd.fdtd_dft_flux(c32.ctx, c32.monitors[k][0], nf) for k in range(2)]
+    sc = W.slab_cell()
+    T = fluxes[True][1] / fluxes[False][1]
+    R = 1.0 - fluxes[True][0] / fluxes[False][0]
+    T_ex, R_ex = lattice_transmission(np.full(20, 1.0 / 1.5 ** 2), sc.monitors[0].omegas, sc.courant,
+                                      reflection=True)
+    assert np.max(np.abs(T - T_ex)) < 2e-4, (T, T_ex)
+    assert np.max(np.abs(R - R_ex)) < 2e-4, (R, R_ex)
+
+
+def test_flux_rejects_monitors_it_cannot_use():
+    sc = W.periodic_cell(n_steps=10)
+    ctx = fdtd.Context([sc], dtype="f32")
+    with pytest.raises(fdtd.FdtdError) as e:
+        fdtd.fdtd_dft_flux(ctx.ctx, ctx.monitors[1][0], 3)   # one plane thick
+    assert e.value.status == fdtd.FDTD_EINVAL
