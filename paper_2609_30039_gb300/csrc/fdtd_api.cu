@@ -825,6 +825,8 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
     a.dft_on = c->dft_enabled;
     a.dft_items = c->d_dft_items;
     a.ndft = c->n_dft_items;
+    a.d_base = c->d_base;
+    a.offset = offset;
     const int ng = (int)c->tiles_gen.size(), ni = (int)c->tiles_int.size();
     // The general and interior launches of a half-step touch disjoint cells: they run
     // concurrently (interior on the auxiliary stream, forked and joined with events, also inside
@@ -848,14 +850,11 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
         cudaEventRecord(c->ev_join, c->aux_stream);
         cudaStreamWaitEvent(st, c->ev_join, 0);
     };
-    if (nd > 0 && first) launch_copy_int(l, c->d_step, c->d_base);
-    if (dstream && !first) cudaStreamWaitEvent(st, c->ev_de, 0);   // DFT of E^n done before E changes
-    // per-cell streaming mode (no energy record): one launch per domain and half-step
+    // per-cell mode (no energy record): the kernels take their step from the batch base, and
+    // the step counter advances once, after the batch's last step
     const bool cell = c->cell_mode && !c->energy_on;
-    unsigned cell_blocks = 0;
-    if (cell)
-        for (const auto& h : c->doms)
-            cell_blocks += (unsigned)((h.n[0] + kTileX - 1) / kTileX) * ((h.n[1] + kTileY - 1) / kTileY) * h.n[2];
+    if ((nd > 0 || cell) && first) launch_copy_int(l, c->d_step, c->d_base);
+    if (dstream && !first) cudaStreamWaitEvent(st, c->ev_de, 0);   // DFT of E^n done before E changes
     auto cell_args = [&](int di, bool e_side) {
         const DomainHost& h = c->doms[di];
         CellArgs<T> ca;
@@ -873,6 +872,17 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
         }
         ca.nsrc = (int)h.srcs.size();
         for (int q = 0; q < ca.nsrc && q < kMaxSrcPerDom; ++q) ca.src[q] = h.srcs[q];
+        // bounding box of this half-step's sources (cells outside it skip the source loop)
+        bool any = false;
+        for (int q = 0; q < ca.nsrc && q < kMaxSrcPerDom; ++q) {
+            const Src& sr = c->srcs[h.srcs[q]].s;
+            if ((sr.comp < 3) != e_side) continue;
+            for (int ax = 0; ax < 3; ++ax) {
+                ca.src_lo[ax] = any ? std::min(ca.src_lo[ax], sr.lo[ax]) : sr.lo[ax];
+                ca.src_hi[ax] = any ? std::max(ca.src_hi[ax], sr.hi[ax]) : sr.hi[ax];
+            }
+            any = true;
+        }
         ca.dom = di;
         return ca;
     };
@@ -906,8 +916,8 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
     if (dstream && !first) cudaStreamWaitEvent(st, c->ev_dh, 0);   // DFT of H^{n-1/2} done
     if (cell) {
         Prof p(c, FDTD_KERNEL_H);
-        for (int di = 0; di < (int)c->doms.size(); ++di)
-            launch_h_cell<T>(l, cell_args(di, false), (T)c->S, a, cell_blocks);
+        for (int di = 0; di < (int)c->doms.size(); ++di) launch_h_cell<T>(l, cell_args(di, false), (T)c->S, a);
+        if (last) launch_advance(l, c->d_step, offset + 1);
     } else {
         fork_int();
         {
@@ -1014,10 +1024,11 @@ fdtd_status build_graph(fdtd_ctx* c) {
     // launches of one step: E and H for each non-empty tile class, the two DFT launches, and
     // one step-base copy per graph
     const int nd = c->dft_enabled && c->n_dft_items > 0;
-    const long long per = c->cell_mode && !c->energy_on
-                              ? 2 * ((long long)c->doms.size() + nd)
-                              : 2 * ((c->tiles_int.empty() ? 0 : 1) + (c->tiles_gen.empty() ? 0 : 1) + nd);
-    c->graph_launches[a][b] = per * kGraphSteps + nd;
+    const bool cell = c->cell_mode && !c->energy_on;
+    const long long per = cell ? 2 * ((long long)c->doms.size() + nd)
+                               : 2 * ((c->tiles_int.empty() ? 0 : 1) + (c->tiles_gen.empty() ? 0 : 1) + nd);
+    // plus the step-base copy (DFT or per-cell) and, per-cell, the counter advance
+    c->graph_launches[a][b] = per * kGraphSteps + ((nd || cell) ? 1 : 0) + (cell ? 1 : 0);
     return FDTD_OK;
 }
 
@@ -1485,6 +1496,8 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
         a.dft_on = ctx->dft_enabled;
         a.dft_items = ctx->d_dft_items;
         a.ndft = ctx->n_dft_items;
+        a.d_base = nullptr;   // the persistent kernel counts its steps itself
+        a.offset = 0;
         const int nt = ctx->n_lpt;
         const Launch l{ctx->stream, &ctx->launches};
         while (left > 0) {

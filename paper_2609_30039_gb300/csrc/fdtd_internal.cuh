@@ -218,6 +218,8 @@ struct StepArgs {
     int dft_on;
     const DftItem* dft_items;   // DFT work items of every monitor (persistent kernel)
     int ndft;
+    const int* d_base;          // per-cell mode: first step of the launched batch ...
+    int offset;                 // ... and this step's position in it (step = *d_base + offset)
 };
 
 template <typename T>
@@ -247,6 +249,7 @@ struct CellArgs {
     int per[3];
     int nsrc;
     int src[kMaxSrcPerDom];
+    int src_lo[3], src_hi[3];   // bounding box of this half-step's sources (empty: lo = hi = 0)
     int dom;
 };
 
@@ -255,7 +258,7 @@ template <typename T>
 void launch_e_cell(const Launch& L, const CellArgs<T>& c, const Dom<T>* doms, T S, const StepArgs& a, int aniso,
                    int poles);
 template <typename T>
-void launch_h_cell(const Launch& L, const CellArgs<T>& c, T S, const StepArgs& a, unsigned advance);
+void launch_h_cell(const Launch& L, const CellArgs<T>& c, T S, const StepArgs& a);
 // Persistent cooperative launch advancing nsteps forward steps over all tiles (general first).
 // variant: 0 register path, 1 one-plane register prefetch, 2 TMA-staged interior tiles.
 template <typename T>

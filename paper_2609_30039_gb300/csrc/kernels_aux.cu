@@ -55,38 +55,52 @@ __global__ void k_nonfinite(const T* __restrict__ p, long long n, unsigned long 
     }
 }
 
-// One block per slab: s = max |x| over the slab, then q = bf16_rn(x / s).
+// BF16 snapshot codec, one FP32 scale per slab (outermost index): s = max |x| over the slab,
+// q = bf16_rn(x / s), x' = float(q) * s.  Grids are (blocks per slab, slabs): many blocks per slab
+// and no index division.  The scale is reduced with an atomic max on the float's bits (valid for
+// non-negative values; NaN is ignored by fmaxf, as in a sequential max).
 template <typename T>
-__global__ void k_bf16_encode(const T* __restrict__ src, long long plane, __nv_bfloat16* __restrict__ dst,
-                              float* __restrict__ scales) {
-    const long long base = (long long)blockIdx.x * plane;
+__global__ void __launch_bounds__(256) k_slab_absmax(const T* __restrict__ src, long long plane,
+                                                     unsigned* __restrict__ scale_bits) {
+    const long long base = (long long)blockIdx.y * plane;
     float m = 0.f;
-    for (long long t = threadIdx.x; t < plane; t += blockDim.x) m = fmaxf(m, fabsf((float)src[base + t]));
-    __shared__ float red[32];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < plane; t += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf((float)src[base + t]));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float red[8];
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (threadIdx.x == 0) red[0] = m;
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+        atomicMax(scale_bits + blockIdx.y, __float_as_uint(m));
     }
-    __syncthreads();
-    // divide (not multiply by 1/s): a slab whose max is an FP32 denormal has 1/s = inf, and
-    // 0 * inf would store NaN; x / s stays within [-1, 1]
-    const float s = red[0];
-    for (long long t = threadIdx.x; t < plane; t += blockDim.x)
-        dst[base + t] = __float2bfloat16_rn(s > 0.f ? (float)src[base + t] / s : 0.f);
-    if (threadIdx.x == 0) scales[blockIdx.x] = s;
 }
 
 template <typename T>
-__global__ void k_bf16_decode(const __nv_bfloat16* __restrict__ src, const float* __restrict__ scales, long long plane,
-                              T* __restrict__ dst) {
-    const long long base = (long long)blockIdx.x * plane;
-    const float s = scales[blockIdx.x];
-    for (long long t = threadIdx.x; t < plane; t += blockDim.x)
+__global__ void __launch_bounds__(256) k_bf16_quant(const T* __restrict__ src, long long plane,
+                                                    const float* __restrict__ scales, __nv_bfloat16* __restrict__ dst) {
+    // divide (not multiply by 1/s): a slab whose max is an FP32 denormal has 1/s = inf, and
+    // 0 * inf would store NaN; x / s stays within [-1, 1]
+    const float s = scales[blockIdx.y];
+    const long long base = (long long)blockIdx.y * plane;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < plane; t += (long long)gridDim.x * blockDim.x)
+        dst[base + t] = __float2bfloat16_rn(s > 0.f ? (float)src[base + t] / s : 0.f);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bf16_decode(const __nv_bfloat16* __restrict__ src,
+                                                     const float* __restrict__ scales, long long plane,
+                                                     T* __restrict__ dst) {
+    const float s = scales[blockIdx.y];
+    const long long base = (long long)blockIdx.y * plane;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < plane; t += (long long)gridDim.x * blockDim.x)
         dst[base + t] = (T)(__bfloat162float(src[base + t]) * s);
+}
+
+// blocks per slab: about 8 elements per thread, at most 64 blocks
+inline unsigned codec_blocks(long long plane) {
+    const long long b = (plane + 256 * 8 - 1) / (256 * 8);
+    return (unsigned)(b < 1 ? 1 : (b > 64 ? 64 : b));
 }
 
 // Net Poynting flux along +z through the H plane of a two-plane monitor (Sec. 2.4), one block
@@ -154,17 +168,19 @@ template <typename T>
 void launch_bf16_encode(const Launch& L, const T* src, long long nplanes, long long plane, uint16_t* dst,
                         float* scales) {
     if (nplanes <= 0 || plane <= 0) return;
-    k_bf16_encode<T><<<(unsigned)nplanes, 256, 0, L.stream>>>(src, plane, reinterpret_cast<__nv_bfloat16*>(dst),
-                                                             scales);
-    ++*L.counter;
+    const dim3 g(codec_blocks(plane), (unsigned)nplanes);
+    cudaMemsetAsync(scales, 0, sizeof(float) * nplanes, L.stream);
+    k_slab_absmax<T><<<g, 256, 0, L.stream>>>(src, plane, reinterpret_cast<unsigned*>(scales));
+    k_bf16_quant<T><<<g, 256, 0, L.stream>>>(src, plane, scales, reinterpret_cast<__nv_bfloat16*>(dst));
+    *L.counter += 2;
 }
 
 template <typename T>
 void launch_bf16_decode(const Launch& L, const uint16_t* src, const float* scales, long long nplanes,
                         long long plane, T* dst) {
     if (nplanes <= 0 || plane <= 0) return;
-    k_bf16_decode<T><<<(unsigned)nplanes, 256, 0, L.stream>>>(reinterpret_cast<const __nv_bfloat16*>(src), scales,
-                                                             plane, dst);
+    const dim3 g(codec_blocks(plane), (unsigned)nplanes);
+    k_bf16_decode<T><<<g, 256, 0, L.stream>>>(reinterpret_cast<const __nv_bfloat16*>(src), scales, plane, dst);
     ++*L.counter;
 }
 

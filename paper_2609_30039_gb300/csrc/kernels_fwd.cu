@@ -636,8 +636,9 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
         if (!py) ey = fma_t(S * iey, (yy1 - yy2), ey);
         if (!pz) ez = fma_t(S * iez, (yz1 - yz2), ez);
     }
-    if (c.nsrc) {
-        const int step = *a.d_step;
+    if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && k >= c.src_lo[2] &&
+        k < c.src_hi[2]) {
+        const int step = *a.d_base + a.offset;
         ex += src_add_t<T>(c, a.srcs, 0, i, j, k, step);
         ey += src_add_t<T>(c, a.srcs, 1, i, j, k, step);
         ez += src_add_t<T>(c, a.srcs, 2, i, j, k, step);
@@ -649,7 +650,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
 
 template <typename T, bool kPer>
 __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
-    k_h_cell(const CellArgs<T> c, T S, const StepArgs a, unsigned advance_blocks) {
+    k_h_cell(const CellArgs<T> c, T S, const StepArgs a) {
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
     const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
     if (i < nx && j < ny) {
@@ -694,8 +695,9 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
         T hx1 = fma_t(-S, (yx1 - yx2), hx);
         T hy1 = fma_t(-S, (yy1 - yy2), hy);
         T hz1 = fma_t(-S, (yz1 - yz2), hz);
-        if (c.nsrc) {
-            const int step = *a.d_step;
+        if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && k >= c.src_lo[2] &&
+            k < c.src_hi[2]) {
+            const int step = *a.d_base + a.offset;
             hx1 += src_add_t<T>(c, a.srcs, 3, i, j, k, step);
             hy1 += src_add_t<T>(c, a.srcs, 4, i, j, k, step);
             hz1 += src_add_t<T>(c, a.srcs, 5, i, j, k, step);
@@ -703,20 +705,6 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
         c.F[3][id] = hx1;
         c.F[4][id] = hy1;
         c.F[5][id] = hz1;
-    }
-    if (advance_blocks) {
-        // the last block of the step's H launches (all domains) advances the step counter
-        __syncthreads();
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            const int step = *a.d_step;
-            __threadfence();
-            const unsigned done = atomicAdd(a.d_ticket, 1u);
-            if (done == advance_blocks - 1) {
-                *a.d_ticket = 0u;
-                *a.d_step = step + 1;
-                __threadfence();
-            }
-        }
     }
 }
 
@@ -747,12 +735,12 @@ void launch_e_cell(const Launch& L, const CellArgs<T>& c, const Dom<T>* doms, T 
 }
 
 template <typename T>
-void launch_h_cell(const Launch& L, const CellArgs<T>& c, T S, const StepArgs& a, unsigned advance) {
+void launch_h_cell(const Launch& L, const CellArgs<T>& c, T S, const StepArgs& a) {
     const dim3 g = cell_grid(c.n), b(kTileX, kTileY);
     if (c.per[0] || c.per[1])
-        k_h_cell<T, true><<<g, b, 0, L.stream>>>(c, S, a, advance);
+        k_h_cell<T, true><<<g, b, 0, L.stream>>>(c, S, a);
     else
-        k_h_cell<T, false><<<g, b, 0, L.stream>>>(c, S, a, advance);
+        k_h_cell<T, false><<<g, b, 0, L.stream>>>(c, S, a);
     ++*L.counter;
 }
 
@@ -1188,8 +1176,8 @@ template void launch_e_cell<float>(const Launch&, const CellArgs<float>&, const 
                                    int, int);
 template void launch_e_cell<double>(const Launch&, const CellArgs<double>&, const Dom<double>*, double,
                                     const StepArgs&, int, int);
-template void launch_h_cell<float>(const Launch&, const CellArgs<float>&, float, const StepArgs&, unsigned);
-template void launch_h_cell<double>(const Launch&, const CellArgs<double>&, double, const StepArgs&, unsigned);
+template void launch_h_cell<float>(const Launch&, const CellArgs<float>&, float, const StepArgs&);
+template void launch_h_cell<double>(const Launch&, const CellArgs<double>&, double, const StepArgs&);
 template cudaError_t launch_steps<float>(const Launch&, const Dom<float>*, const Tile*, int, float, const StepArgs&, int,
                                          int, int, int, GridSync*, int*);
 template cudaError_t launch_steps<double>(const Launch&, const Dom<double>*, const Tile*, int, double,
