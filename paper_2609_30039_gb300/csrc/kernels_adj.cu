@@ -131,16 +131,12 @@ __device__ __forceinline__ long long off_z(const Dom<T>& d, int s, int i, int j)
     return ((long long)s * d.n[1] + j) * d.n[0] + i;
 }
 
+// Transposed E step of column (i, j) over planes [z0, z1) in general form (CPML, PEC, poles,
+// periodic wrap); `flags` tells whether monitor injection can apply.
 template <typename T>
-__global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
-    k_adj_e_gen(const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, const Tile* __restrict__ tiles, T S,
-                int m, int pending) {
-    const Tile t = tiles[blockIdx.x];
-    const Dom<T>& d = doms[t.dom];
+__device__ __forceinline__ void adj_e_column(const Dom<T>& d, const Mon* __restrict__ mons, int i, int j, int z0,
+                                             int z1, int flags, T S, int m, int pending) {
     const int nx = d.n[0], ny = d.n[1];
-    int i, j;
-    tile_coords(t, i, j);
-    if (i < 0 || j < 0) return;
     const long long nxy = (long long)nx * ny;
     T* A0 = d.A[0];
     T* A1 = d.A[1];
@@ -157,17 +153,17 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
     const long long oxm = nb_minus(i, nx, 1, d.per[0], &hasx);
     const long long oym = nb_minus(j, ny, nx, d.per[1], &hasy);
     const bool gcol = d.design && i >= d.glo[0] && i < d.ghi[0] && j >= d.glo[1] && j < d.ghi[1];
-    const bool mon = d.nmon && (t.flags & kTileMonE);
-    long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
+    const bool mon = d.nmon && (flags & kTileMonE);
+    long long id = (long long)z0 * nxy + (long long)j * nx + i;
     // z-derivative terms of H_y (s = 0) and H_x (s = 1) at plane k-1
     T tyz_m = T(0), txz_m = T(0);
-    if (t.z0 > 0) {
-        const CpmlC<T> zH = cpml_c(d, d.cH[2], 2, t.z0 - 1);
+    if (z0 > 0) {
+        const CpmlC<T> zH = cpml_c(d, d.cH[2], 2, z0 - 1);
         const long long o = zH.s >= 0 ? off_z(d, zH.s, i, j) : 0;
         tyz_m = dbar_c(zH, -S * B1[id - nxy], zH.s >= 0 ? d.apsiH[1][0][o] : T(0));
         txz_m = dbar_c(zH, S * B0[id - nxy], zH.s >= 0 ? d.apsiH[0][1][o] : T(0));
     }
-    for (int k = t.z0; k < t.z1; ++k, id += nxy) {
+    for (int k = z0; k < z1; ++k, id += nxy) {
         const bool pk = k == 0;
         const bool px = pj || pk, py = pi || pk, pz = pi || pj;
         const CpmlC<T> zE = cpml_c(d, d.cE[2], 2, k), zH = cpml_c(d, d.cH[2], 2, k);
@@ -288,14 +284,20 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
 
 template <typename T>
 __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
-    k_adj_h_gen(const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, const Tile* __restrict__ tiles, T S,
-                int m) {
+    k_adj_e_gen(const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, const Tile* __restrict__ tiles, T S,
+                int m, int pending) {
     const Tile t = tiles[blockIdx.x];
-    const Dom<T>& d = doms[t.dom];
-    const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
     int i, j;
     tile_coords(t, i, j);
     if (i < 0 || j < 0) return;
+    adj_e_column(doms[t.dom], mons, i, j, t.z0, t.z1, t.flags, S, m, pending);
+}
+
+// Transposed H step of column (i, j) over planes [z0, z1) in general form.
+template <typename T>
+__device__ __forceinline__ void adj_h_column(const Dom<T>& d, const Mon* __restrict__ mons, int i, int j, int z0,
+                                             int z1, int flags, T S, int m) {
+    const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
     const long long nxy = (long long)nx * ny;
     const T* A0 = d.A[0];
     const T* A1 = d.A[1];
@@ -311,8 +313,8 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
     const CpmlC<T> xH = cpml_c(d, d.cH[0], 0, i), yH = cpml_c(d, d.cH[1], 1, j);
     const CpmlC<T> xE = cpml_c(d, d.cE[0], 0, i), xEp = cpml_c(d, d.cE[0], 0, i + 1);
     const CpmlC<T> yE = cpml_c(d, d.cE[1], 1, j), yEp = cpml_c(d, d.cE[1], 1, j + 1);
-    const bool mon = d.nmon && m >= 1 && (t.flags & kTileMonH);
-    long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
+    const bool mon = d.nmon && m >= 1 && (flags & kTileMonH);
+    long long id = (long long)z0 * nxy + (long long)j * nx + i;
     // z-derivative terms of E_y (s = 0) and E_x (s = 1) at plane k (carried to the next plane)
     auto zterms = [&](int k, long long idk, T& ty, T& tx) {
         if (k >= nz) {
@@ -327,8 +329,8 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
         tx = (pj || k == 0) ? T(0) : dbar_c(zE, -A0[idk], zE.s >= 0 ? d.apsiE[0][1][o] : T(0));
     };
     T tyz_k, txz_k;
-    zterms(t.z0, id, tyz_k, txz_k);
-    for (int k = t.z0; k < t.z1; ++k, id += nxy) {
+    zterms(z0, id, tyz_k, txz_k);
+    for (int k = z0; k < z1; ++k, id += nxy) {
         T tyz_n, txz_n;
         zterms(k + 1, id + nxy, tyz_n, txz_n);
         const bool pk = k == 0;
@@ -391,6 +393,17 @@ __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
         tyz_k = tyz_n;
         txz_k = txz_n;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
+    k_adj_h_gen(const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, const Tile* __restrict__ tiles, T S,
+                int m) {
+    const Tile t = tiles[blockIdx.x];
+    int i, j;
+    tile_coords(t, i, j);
+    if (i < 0 || j < 0) return;
+    adj_h_column(doms[t.dom], mons, i, j, t.z0, t.z1, t.flags, S, m);
 }
 
 // Interior fast paths of the two transposed kernels: tiles that touch no CPML slab, PEC plane,
