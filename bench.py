@@ -185,9 +185,15 @@ def run_ours(args):
         fdtd.fdtd_dft_reset(ctx.ctx)
         fdtd.fdtd_step_forward(ctx.ctx, T_STEPS)
 
-    # pick the launch mode on this workload (state, spectra and step count are left unchanged)
+    # pick the launch mode on this workload (state, spectra and step count are left unchanged);
+    # --launch-mode fixes it instead (e.g. under a profiler, whose per-launch serialisation
+    # would distort the autotuner's timings)
     fdtd.fdtd_step_forward(ctx.ctx, 300)
-    tune_ms = fdtd.fdtd_autotune(ctx.ctx, 200)
+    if args.launch_mode is None:
+        tune_ms = fdtd.fdtd_autotune(ctx.ctx, 200)
+    else:
+        tune_ms = []
+        fdtd.fdtd_set_launch_mode(ctx.ctx, args.launch_mode)
     mode = fdtd.fdtd_get_launch_mode(ctx.ctx)
     for _ in range(args.warmup):
         solve()
@@ -259,8 +265,9 @@ def run_ours(args):
                    "l2": "flushed between timed iterations (256 MiB write); the ~75 MB state stays L2-resident "
                          "within an iteration", "parallelism": f"{world} independent replica(s), no collective"},
         "gpu_launches": int(launches),
-        "launch_mode": {"chosen": ["per-half-step graphs", "persistent", "persistent+prefetch", "persistent+TMA", "per-cell graphs"][mode],
-                        "autotune_ms_per_200_steps": [round(v, 3) for v in tune_ms]},
+        "launch_mode": {"chosen": ["per-half-step graphs", "persistent", "persistent+prefetch", "persistent+TMA",
+                                   "per-cell graphs"][mode],
+                        "autotune_ms_per_200_steps": [round(v, 3) for v in tune_ms] if tune_ms else "fixed"},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                      "alg_bytes_per_launch": int(alg_bytes), "avg_launch_us": round(avg_ms * 1e3, 3),
@@ -449,7 +456,10 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision of --profile-case")
     ap.add_argument("--cpml", type=int, default=CPML, help="CPML depth of --profile-case (0: PEC box)")
     ap.add_argument("--adjoint", action="store_true", help="--profile-case: also time as many transposed steps")
-    ap.add_argument("--launch-mode", type=int, default=1, help="0 per half-step tile launches, 1 persistent, 2 persistent with prefetch, 3 persistent with TMA staging, 4 per-cell launches")
+    ap.add_argument("--launch-mode", type=int, default=None,
+                    help="0 per half-step tile launches, 1 persistent, 2 persistent with prefetch, 3 persistent "
+                         "with TMA staging, 4 per-cell launches; default: autotuned (the bench line), 4 "
+                         "(--profile-case)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -478,7 +488,7 @@ def profile_case(args):
     for src in sc.sources:   # an electric sheet must stay off the PEC planes of a box without CPML
         src.lo = tuple(max(v, 1) for v in src.lo)
     ctx = fdtd.Context([sc], dtype=args.dtype)
-    fdtd.fdtd_set_launch_mode(ctx.ctx, args.launch_mode)
+    fdtd.fdtd_set_launch_mode(ctx.ctx, 4 if args.launch_mode is None else args.launch_mode)
     ctx.step(args.warmup)
     t = _timed(lambda: ctx.step(args.steps), ctx.stream) if args.steps else 0.0
     adj = None
@@ -486,7 +496,8 @@ def profile_case(args):
         fdtd.fdtd_adjoint_begin(ctx.ctx)
         ta = _timed(lambda: fdtd.fdtd_step_adjoint(ctx.ctx, args.steps), ctx.stream)
         adj = round(sc.cells * args.steps / ta / 1e9, 3)
-    print(json.dumps({"profile_case": n, "cpml": args.cpml, "dtype": args.dtype, "launch_mode": args.launch_mode,
+    print(json.dumps({"profile_case": n, "cpml": args.cpml, "dtype": args.dtype,
+                      "launch_mode": fdtd.fdtd_get_launch_mode(ctx.ctx),
                       "adjoint_gcell_steps_s": adj, "steps": args.warmup + args.steps,
                       "cells": sc.cells, "gcell_steps_s": round(sc.cells * args.steps / t / 1e9, 3) if t else None}))
     ctx.close()
