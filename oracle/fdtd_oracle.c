@@ -437,6 +437,72 @@ static void step_once(oracle_t *o) {
 
 void oracle_step(oracle_t *o, int n) { for (int s = 0; s < n; ++s) step_once(o); }
 
+/* Reversible reconstruction (Sec. 3.2: lossless nondispersive problems step Eq. (yee)
+ * backward): one backward step u^{n+1} -> u^n undoes the forward step n in reverse order,
+ *   H^{n+1/2} = (H^{n+3/2} - m^n) + S curl E^{n+1},
+ *   E^n       = (E^{n+1} - s^n) - S eps^-1 curl H^{n+1/2},
+ * with the plain differences of Eq. (yee) (no CPML memory, no pole state: the caller must
+ * hold a domain without CPML layers and without poles; returns -1 otherwise).  DFT monitors
+ * and energies are not touched.  PEC-held E nodes stay as they are. */
+static void sub_sources(oracle_t *o, int magnetic, long n) {
+    for (int s = 0; s < o->nsrc; ++s) {
+        osrc_t *sr = &o->src[s];
+        if ((sr->comp >= 3) != magnetic) continue;
+        if (n >= sr->n) continue;
+        double v = sr->wave[n];
+        for (int k = sr->lo[2]; k < sr->hi[2]; ++k)
+            for (int j = sr->lo[1]; j < sr->hi[1]; ++j)
+                for (int i = sr->lo[0]; i < sr->hi[0]; ++i) o->F[sr->comp][IDX(o, i, j, k)] -= v;
+    }
+}
+
+int oracle_step_backward(oracle_t *o, int n) {
+    for (int q = 0; q < 3; ++q)
+        if (o->cpml[2 * q] || o->cpml[2 * q + 1]) return -1;
+    if (o->npole > 0) return -1;
+    const int nx = o->N[0], ny = o->N[1], nz = o->N[2];
+    for (int s = 0; s < n && o->step > 0; ++s) {
+        const long m = o->step - 1;
+        /* H: every H node reads E^{n+1} only, so the whole H update can be done in place */
+        sub_sources(o, 1, m);
+        for (int a = 0; a < 3; ++a) {
+            int b = (a + 1) % 3, cax = (a + 2) % 3;
+            const double *Ec = o->F[cax], *Eb = o->F[b];
+            double *H = o->F[3 + a];
+            for (int k = 0; k < nz; ++k)
+                for (int j = 0; j < ny; ++j)
+                    for (int i = 0; i < nx; ++i) {
+                        long id = IDX(o, i, j, k);
+                        int cb[3] = {i, j, k}; cb[b] += 1;
+                        int cc[3] = {i, j, k}; cc[cax] += 1;
+                        double d1 = at(o, Ec, cb[0], cb[1], cb[2]) - Ec[id];   /* dEc/dx_b */
+                        double d2 = at(o, Eb, cc[0], cc[1], cc[2]) - Eb[id];   /* dEb/dx_c */
+                        H[id] = H[id] + o->S * (d1 - d2);
+                    }
+        }
+        /* E: reads the reconstructed H only */
+        sub_sources(o, 0, m);
+        for (int a = 0; a < 3; ++a) {
+            int b = (a + 1) % 3, cax = (a + 2) % 3;
+            const double *Hc = o->F[3 + cax], *Hb = o->F[3 + b];
+            for (int k = 0; k < nz; ++k)
+                for (int j = 0; j < ny; ++j)
+                    for (int i = 0; i < nx; ++i) {
+                        int c[3] = {i, j, k};
+                        long id = IDX(o, i, j, k);
+                        if (is_pec_E(o, a, c)) continue;
+                        int cb[3] = {i, j, k}; cb[b] -= 1;
+                        int cc[3] = {i, j, k}; cc[cax] -= 1;
+                        double d1 = Hc[id] - at(o, Hc, cb[0], cb[1], cb[2]);   /* dHc/dx_b */
+                        double d2 = Hb[id] - at(o, Hb, cc[0], cc[1], cc[2]);   /* dHb/dx_c */
+                        o->F[a][id] = o->F[a][id] - o->S * o->inv_eps[a][id] * (d1 - d2);
+                    }
+        }
+        o->step = m;
+    }
+    return 0;
+}
+
 /* ---------------- access ---------------- */
 double *oracle_field(oracle_t *o, int comp) { return o->F[comp]; }
 double *oracle_psi(oracle_t *o, int magnetic, int comp, int which) {

@@ -8,7 +8,8 @@ compiles it with gcc, marshals arguments and exposes numpy views.
 Paper passages followed (arxiv 2609.30039): Sec. 2.1 Eq. (yee) and the half-step time
 bookkeeping; Sec. 2.2 CPML and PEC; Sec. 2.3 diagonal permittivity and trapezoidal
 Drude/Lorentz poles; Sec. 2.4 plane DFT monitors; Sec. 3.1 Eq. (adjoint) and the CPML /
-pole transposes; Sec. 3.2 checkpoint replay (here a plain two-level store-all replay).
+pole transposes; Sec. 3.2 checkpoint replay (here a plain two-level store-all replay) and the
+reversible reconstruction (backward steps of Eq. (yee)).
 """
 from __future__ import annotations
 
@@ -57,6 +58,7 @@ def _load():
             "oracle_add_dft_box": (C.c_int, [vp, _ip, _ip, C.c_uint, C.c_int, _dp]),
             "oracle_enable_energy": (None, [vp, C.c_long]),
             "oracle_step": (None, [vp, C.c_int]),
+            "oracle_step_backward": (C.c_int, [vp, C.c_int]),
             "oracle_field": (_dp, [vp, C.c_int]),
             "oracle_psi": (_dp, [vp, C.c_int, C.c_int, C.c_int]),
             "oracle_pole": (_dp, [vp, C.c_int, C.c_int, C.c_int]),
@@ -183,6 +185,13 @@ class Oracle:
     # -- stepping and access ----------------------------------------------------------
     def step(self, n=1):
         self.lib.oracle_step(self.h, int(n))
+
+    def step_backward(self, n=1):
+        """Undoes n forward steps by stepping Eq. (yee) backward (lossless, nondispersive
+        domains only: no CPML layers, no poles; Sec. 3.2 reversible reconstruction)."""
+        r = self.lib.oracle_step_backward(self.h, int(n))
+        if r != 0:
+            raise ValueError("backward stepping needs a domain without CPML layers and without poles")
 
     @property
     def step_count(self):

@@ -13,7 +13,8 @@ method (Sec. 2-3 of arxiv 2609.30039) or by the mathematics of the Yee scheme:
   * checkpoint replay is bitwise equal to store-all (Sec. 3.2);
   * plane-monitor flux (Sec. 2.4) through a slab in a periodic cell (Sec. 2.2) against an
     independent frequency-domain solve of the same 1-D lattice, energy balance R + T = 1, the
-    continuum Fabry-Perot formula within its O(k h) error, and lossless vacuum propagation.
+    continuum Fabry-Perot formula within its O(k h) error, and lossless vacuum propagation;
+  * the backward step of the reversible reconstruction inverts the forward step (Sec. 3.2).
 A plausible slip anywhere in the oracle (a dropped term, a sign, an index, a transposed
 coefficient) fails at least one of these.
 """
@@ -425,3 +426,46 @@ def test_periodic_plane_flux_is_uniform_in_z_for_vacuum():
     p1 = plane_flux_z(o.dft(0), (0, 1, 3, 4))
     p2 = plane_flux_z(o.dft(1), (0, 1, 3, 4))
     assert np.all(p1 > 0) and np.max(np.abs(p2 / p1 - 1.0)) < 1e-5
+
+
+# ---- reversible reconstruction (Sec. 3.2): backward steps of Eq. (yee) ------------------------
+def _lossless_box(periodic=(1, 0, 0)):
+    shape = (12, 10, 9)
+    S = W.COURANT
+    o = Oracle(shape, S, periodic=periodic)
+    rng = np.random.default_rng(2609)
+    nx, ny, nz = shape
+    o.set_material([1.0 / rng.uniform(1.0, 4.0, size=(nz, ny, nx)) for _ in range(3)])
+    o.add_source(2, (3, 2, 2), (5, 4, 3), np.sin(0.3 * np.arange(80)))
+    o.add_source(4, (6, 5, 4), (7, 6, 6), np.cos(0.2 * np.arange(80)))
+    st = rng.standard_normal(o.state_len)
+    st[6 * nx * ny * nz:] = 0.0          # no CPML layers: the memory arrays of a physical state are 0
+    o.set_state(st)
+    # PEC-held E nodes hold zero in a physical state
+    for a, m in enumerate(pec_mask_E(shape, periodic)):
+        o.field(a)[m] = 0.0
+    return o
+
+
+def test_backward_steps_invert_forward_steps():
+    # the backward step is the algebraic inverse of the forward step (same difference operators,
+    # reverse order, sources subtracted): forward 50 then backward 50 returns the initial state,
+    # and backward 20 lands on the forward state after 30 steps (a sign or order slip breaks both)
+    o = _lossless_box()
+    u0 = o.get_state().copy()
+    o.step(30)
+    u30 = o.get_state().copy()
+    o.step(20)
+    o.step_backward(20)
+    assert o.step_count == 30
+    assert np.linalg.norm(o.get_state() - u30) <= 1e-12 * np.linalg.norm(u30)
+    o.step_backward(30)
+    assert o.step_count == 0
+    assert np.linalg.norm(o.get_state() - u0) <= 1e-12 * np.linalg.norm(u0)
+
+
+def test_backward_steps_refuse_lossy_domains():
+    o = Oracle((8, 8, 8), W.COURANT, cpml=(0, 0, 0, 0, 3, 3))
+    o.step(2)
+    with pytest.raises(ValueError):
+        o.step_backward(1)
