@@ -190,6 +190,16 @@ fdtd_status fdtd_energy_read(fdtd_ctx* ctx, int32_t domain, double* host_dst, in
  * as CUDA graphs of 32 steps). */
 fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps);
 
+/* Reversible reconstruction (Sec. 3.2: for lossless nondispersive problems the forward fields
+ * are rebuilt by stepping Eq. (yee) backward instead of replaying from checkpoints): undoes the
+ * last n_steps forward steps, each in reverse order,
+ *   H^{n+1/2} = (H^{n+3/2} - m^n) + S curl E^{n+1},  E^n = (E^{n+1} - s^n) - S eps^-1 curl H^{n+1/2}.
+ * Every domain must be lossless: no CPML cells on any face and no poles (FDTD_EINVAL);
+ * FDTD_ESTATE when n_steps exceeds the held step count.  DFT accumulators and energies are not
+ * touched; the step count decreases by n_steps.  In floating point the reconstruction differs
+ * from the forward states by accumulated rounding.  Asynchronous. */
+fdtd_status fdtd_step_backward(fdtd_ctx* ctx, int32_t n_steps);
+
 /* Launch modes (no counterpart in the paper; they change scheduling, not arithmetic):
  * mode 0: per-half-step launches (replayed as CUDA graphs); mode 1: persistent
  * cooperative launches (4 blocks per SM in FP32); mode 2: persistent launches whose interior

@@ -172,6 +172,38 @@ class DesignAdjoint:
         return out, self.grads, replay_stats(acts)
 
 
+class ReversibleAdjoint(DesignAdjoint):
+    """The same gradient without checkpoints, for lossless nondispersive domains (Sec. 3.2:
+    the forward fields are rebuilt by stepping Eq. (yee) backward): one forward sweep, then for
+    m = n-1 .. 0 a backward step (u^(m+1) -> u^m) and the transposed step m.  Memory: the state
+    alone; work: one extra step per transposed step instead of the binomial replays."""
+
+    def __init__(self, ctx: "F.Context"):
+        super().__init__(ctx, slots=1)
+
+    def run(self, n_steps: int, loss_of_spectra: Callable):
+        ctx = self.ctx
+        c = ctx.ctx
+        F.fdtd_step_forward(c, n_steps)
+        specs = [ctx.dft(k) for k in range(len(ctx.monitors))]
+        J, cots = loss_of_spectra(specs)
+        keep = [ct.contiguous() if ct is not None else None for ct in cots]
+        for k, ct in enumerate(keep):
+            F.fdtd_set_adjoint_source(c, ctx.monitors[k][0], ct.data_ptr() if ct is not None else None)
+        for g in self.grads:
+            if g is not None:
+                g.zero_()
+        F.fdtd_adjoint_begin(c)
+        F.fdtd_dft_enable(c, 0)
+        for _ in range(n_steps):
+            F.fdtd_step_backward(c, 1)
+            F.fdtd_step_adjoint(c, 1)
+        F.fdtd_dft_enable(c, 1)
+        ctx.synchronize()
+        return (J, specs), self.grads, {"forward_steps": n_steps, "backward_steps": n_steps,
+                                        "adjoint_steps": n_steps}
+
+
 def _make_function():
     import torch
 

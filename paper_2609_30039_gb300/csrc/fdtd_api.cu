@@ -810,6 +810,40 @@ struct Prof {
     }
 };
 
+// Per-cell kernel arguments of domain di for the E (e_side) or H half-step.
+template <typename T>
+CellArgs<T> make_cell_args(const fdtd_ctx* c, int di, bool e_side) {
+    const DomainHost& h = c->doms[di];
+    CellArgs<T> ca;
+    std::memset(&ca, 0, sizeof(ca));
+    for (int f = 0; f < 6; ++f) ca.F[f] = (T*)h.F[f];
+    for (int q = 0; q < 3; ++q) {
+        ca.ie[q] = (const T*)h.ie[q];
+        ca.coef[q] = (const T*)(e_side ? h.cE[q] : h.cH[q]);
+        ca.n[q] = h.n[q];
+        ca.dlo[q] = h.dlo[q];
+        ca.dhi[q] = h.dhi[q];
+        ca.ns[q] = h.ns[q];
+        ca.per[q] = h.per[q];
+        for (int s2 = 0; s2 < 2; ++s2) ca.psi[q][s2] = (T*)(e_side ? h.psiE[q][s2] : h.psiH[q][s2]);
+    }
+    ca.nsrc = (int)h.srcs.size();
+    for (int q = 0; q < ca.nsrc && q < kMaxSrcPerDom; ++q) ca.src[q] = h.srcs[q];
+    // bounding box of this half-step's sources (cells outside it skip the source loop)
+    bool any = false;
+    for (int q = 0; q < ca.nsrc && q < kMaxSrcPerDom; ++q) {
+        const Src& sr = c->srcs[h.srcs[q]].s;
+        if ((sr.comp < 3) != e_side) continue;
+        for (int ax = 0; ax < 3; ++ax) {
+            ca.src_lo[ax] = any ? std::min(ca.src_lo[ax], sr.lo[ax]) : sr.lo[ax];
+            ca.src_hi[ax] = any ? std::max(ca.src_hi[ax], sr.hi[ax]) : sr.hi[ax];
+        }
+        any = true;
+    }
+    ca.dom = di;
+    return ca;
+}
+
 // One forward step as per-half-step launches on stream st.  offset: position of this step in the
 // launched batch (its DFT phase index is *d_base + offset); first / last: first and last step of
 // the batch (no wait on DFT work of an earlier batch; the DFT stream is joined back at the end).
@@ -855,37 +889,7 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
     const bool cell = c->cell_mode && !c->energy_on;
     if ((nd > 0 || cell) && first) launch_copy_int(l, c->d_step, c->d_base);
     if (dstream && !first) cudaStreamWaitEvent(st, c->ev_de, 0);   // DFT of E^n done before E changes
-    auto cell_args = [&](int di, bool e_side) {
-        const DomainHost& h = c->doms[di];
-        CellArgs<T> ca;
-        std::memset(&ca, 0, sizeof(ca));
-        for (int f = 0; f < 6; ++f) ca.F[f] = (T*)h.F[f];
-        for (int q = 0; q < 3; ++q) {
-            ca.ie[q] = (const T*)h.ie[q];
-            ca.coef[q] = (const T*)(e_side ? h.cE[q] : h.cH[q]);
-            ca.n[q] = h.n[q];
-            ca.dlo[q] = h.dlo[q];
-            ca.dhi[q] = h.dhi[q];
-            ca.ns[q] = h.ns[q];
-            ca.per[q] = h.per[q];
-            for (int s2 = 0; s2 < 2; ++s2) ca.psi[q][s2] = (T*)(e_side ? h.psiE[q][s2] : h.psiH[q][s2]);
-        }
-        ca.nsrc = (int)h.srcs.size();
-        for (int q = 0; q < ca.nsrc && q < kMaxSrcPerDom; ++q) ca.src[q] = h.srcs[q];
-        // bounding box of this half-step's sources (cells outside it skip the source loop)
-        bool any = false;
-        for (int q = 0; q < ca.nsrc && q < kMaxSrcPerDom; ++q) {
-            const Src& sr = c->srcs[h.srcs[q]].s;
-            if ((sr.comp < 3) != e_side) continue;
-            for (int ax = 0; ax < 3; ++ax) {
-                ca.src_lo[ax] = any ? std::min(ca.src_lo[ax], sr.lo[ax]) : sr.lo[ax];
-                ca.src_hi[ax] = any ? std::max(ca.src_hi[ax], sr.hi[ax]) : sr.hi[ax];
-            }
-            any = true;
-        }
-        ca.dom = di;
-        return ca;
-    };
+    auto cell_args = [&](int di, bool e_side) { return make_cell_args<T>(c, di, e_side); };
     if (cell) {
         Prof p(c, FDTD_KERNEL_E);
         for (int di = 0; di < (int)c->doms.size(); ++di) {
@@ -1536,6 +1540,42 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
     }
     CKL(ctx);
     ctx->step += n_steps;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_step_backward(fdtd_ctx* ctx, int32_t n_steps) {
+    GUARD(ctx);
+    if (n_steps < 0) return fail(ctx, FDTD_EINVAL, "n_steps must be >= 0");
+    for (const auto& d : ctx->doms) {
+        if (d.ns[0] || d.ns[1] || d.ns[2] || d.npole > 0)
+            return fail(ctx, FDTD_EINVAL, "backward steps need lossless domains: no CPML layers and no poles");
+        if (d.ie[0] == nullptr) return fail(ctx, FDTD_EINVAL, "no material");
+    }
+    if (n_steps > ctx->step) return fail(ctx, FDTD_ESTATE, "cannot step back past step 0");
+    if (n_steps == 0) return FDTD_OK;
+    const Launch l = L(ctx);
+    StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.srcs = ctx->d_srcs;
+    a.mons = ctx->d_mons;
+    a.d_step = ctx->d_step;
+    a.d_ticket = ctx->d_ticket;
+    a.d_base = ctx->d_base;
+    launch_copy_int(l, ctx->d_step, ctx->d_base);
+    for (int q = 0; q < n_steps; ++q) {
+        a.offset = -1 - q;   // undoes forward step (step - 1 - q)
+        for (int di = 0; di < (int)ctx->doms.size(); ++di) {
+            if (ctx->dtype == FDTD_F32)
+                launch_back_cell<float>(l, make_cell_args<float>(ctx, di, true), make_cell_args<float>(ctx, di, false),
+                                        (float)ctx->S, a, ctx->aniso);
+            else
+                launch_back_cell<double>(l, make_cell_args<double>(ctx, di, true),
+                                         make_cell_args<double>(ctx, di, false), ctx->S, a, ctx->aniso);
+        }
+    }
+    launch_advance(l, ctx->d_step, -n_steps);
+    CKL(ctx);
+    ctx->step -= n_steps;
     return FDTD_OK;
 }
 

@@ -259,6 +259,11 @@ void launch_e_cell(const Launch& L, const CellArgs<T>& c, const Dom<T>* doms, T 
                    int poles);
 template <typename T>
 void launch_h_cell(const Launch& L, const CellArgs<T>& c, T S, const StepArgs& a);
+// One backward step (reversible reconstruction) of a lossless domain: ce / ch hold the E / H
+// half-step's sources; the step index is *a.d_base + a.offset.
+template <typename T>
+void launch_back_cell(const Launch& L, const CellArgs<T>& ce, const CellArgs<T>& ch, T S, const StepArgs& a,
+                      int aniso);
 // Persistent cooperative launch advancing nsteps forward steps over all tiles (general first).
 // variant: 0 register path, 1 one-plane register prefetch, 2 TMA-staged interior tiles.
 template <typename T>

@@ -570,7 +570,9 @@ __device__ __forceinline__ T cpml_cell(const T* coef, int N, int x, T* psi, T D)
     return cpml_rec(coef[x], coef[N + x], coef[2 * N + x], psi, D);
 }
 
-template <typename T, bool kAniso, bool kPoles, bool kPer>
+// kBack: the backward step of the reversible reconstruction (Sec. 3.2) for a lossless domain,
+// E^n = (E^{n+1} - s^n) - S eps^-1 curl H^{n+1/2}, called with S negated (no CPML, no poles).
+template <typename T, bool kAniso, bool kPoles, bool kPer, bool kBack = false>
 __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
     k_e_cell(const CellArgs<T> c, const Dom<T>* __restrict__ doms, T S, const StepArgs a) {
     const int nx = c.n[0], ny = c.n[1];
@@ -596,6 +598,20 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
     const T iez = kAniso ? c.ie[2][id] : iex;
     const bool pi = i == 0 && !(kPer && c.per[0]), pj = j == 0 && !(kPer && c.per[1]), pk = k == 0;
     const bool px = pj || pk, py = pi || pk, pz = pi || pj;   // PEC-held
+    if (kBack) {
+        T sx = T(0), sy = T(0), sz = T(0);
+        if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && k >= c.src_lo[2] &&
+            k < c.src_hi[2]) {
+            const int step = *a.d_base + a.offset;
+            sx = src_add_t<T>(c, a.srcs, 0, i, j, k, step);
+            sy = src_add_t<T>(c, a.srcs, 1, i, j, k, step);
+            sz = src_add_t<T>(c, a.srcs, 2, i, j, k, step);
+        }
+        if (!px) c.F[0][id] = fma_t(S * iex, (yx1 - yx2), ex - sx);
+        if (!py) c.F[1][id] = fma_t(S * iey, (yy1 - yy2), ey - sy);
+        if (!pz) c.F[2][id] = fma_t(S * iez, (yz1 - yz2), ez - sz);
+        return;
+    }
     if (c.ns[2]) {
         const int sl = slab_of(k, c.dlo[2], c.dhi[2], c.n[2]);
         if (sl >= 0) {
@@ -648,7 +664,8 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
     if (!pz) c.F[2][id] = ez;
 }
 
-template <typename T, bool kPer>
+// kBack: backward H step, H^{n+1/2} = (H^{n+3/2} - m^n) + S curl E^{n+1}, called with S negated.
+template <typename T, bool kPer, bool kBack = false>
 __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
     k_h_cell(const CellArgs<T> c, T S, const StepArgs a) {
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
@@ -668,6 +685,20 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
         T yy1 = (ze ? Ex[id + oz] : T(0)) - exk, yy2 = (xe ? Ez[id + ox] : T(0)) - ez;   // Hy: dEx/dz, dEz/dx
         T yz1 = (xe ? Ey[id + ox] : T(0)) - eyk, yz2 = (ye ? Ex[id + oy] : T(0)) - exk;  // Hz: dEy/dx, dEx/dy
         const T hx = c.F[3][id], hy = c.F[4][id], hz = c.F[5][id];
+        if (kBack) {
+            T mx = T(0), my = T(0), mz = T(0);
+            if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && k >= c.src_lo[2] &&
+                k < c.src_hi[2]) {
+                const int step = *a.d_base + a.offset;
+                mx = src_add_t<T>(c, a.srcs, 3, i, j, k, step);
+                my = src_add_t<T>(c, a.srcs, 4, i, j, k, step);
+                mz = src_add_t<T>(c, a.srcs, 5, i, j, k, step);
+            }
+            c.F[3][id] = fma_t(-S, (yx1 - yx2), hx - mx);
+            c.F[4][id] = fma_t(-S, (yy1 - yy2), hy - my);
+            c.F[5][id] = fma_t(-S, (yz1 - yz2), hz - mz);
+            return;
+        }
         if (c.ns[2]) {
             const int sl = slab_of(k, c.dlo[2], c.dhi[2], nz);
             if (sl >= 0) {
@@ -732,6 +763,25 @@ void launch_e_cell(const Launch& L, const CellArgs<T>& c, const Dom<T>* doms, T 
     else
         launch_e_cell_t<T, false>(L, c, doms, S, a, aniso, poles);
     ++*L.counter;
+}
+
+// Backward step of a lossless domain: the H kernel first (it reads E^{n+1}), then the E kernel.
+template <typename T>
+void launch_back_cell(const Launch& L, const CellArgs<T>& ce, const CellArgs<T>& ch, T S, const StepArgs& a,
+                      int aniso) {
+    const dim3 g = cell_grid(ce.n), b(kTileX, kTileY);
+    const bool per = ce.per[0] || ce.per[1];
+    if (per)
+        k_h_cell<T, true, true><<<g, b, 0, L.stream>>>(ch, -S, a);
+    else
+        k_h_cell<T, false, true><<<g, b, 0, L.stream>>>(ch, -S, a);
+    if (aniso)
+        (per ? k_e_cell<T, true, false, true, true> : k_e_cell<T, true, false, false, true>)<<<g, b, 0, L.stream>>>(
+            ce, nullptr, -S, a);
+    else
+        (per ? k_e_cell<T, false, false, true, true> : k_e_cell<T, false, false, false, true>)<<<g, b, 0, L.stream>>>(
+            ce, nullptr, -S, a);
+    *L.counter += 2;
 }
 
 template <typename T>
@@ -1176,6 +1226,10 @@ template void launch_e_cell<float>(const Launch&, const CellArgs<float>&, const 
                                    int, int);
 template void launch_e_cell<double>(const Launch&, const CellArgs<double>&, const Dom<double>*, double,
                                     const StepArgs&, int, int);
+template void launch_back_cell<float>(const Launch&, const CellArgs<float>&, const CellArgs<float>&, float,
+                                      const StepArgs&, int);
+template void launch_back_cell<double>(const Launch&, const CellArgs<double>&, const CellArgs<double>&, double,
+                                       const StepArgs&, int);
 template void launch_h_cell<float>(const Launch&, const CellArgs<float>&, float, const StepArgs&);
 template void launch_h_cell<double>(const Launch&, const CellArgs<double>&, double, const StepArgs&);
 template cudaError_t launch_steps<float>(const Launch&, const Dom<float>*, const Tile*, int, float, const StepArgs&, int,

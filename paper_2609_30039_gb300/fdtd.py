@@ -75,6 +75,7 @@ _SIGS = {
     "fdtd_set_material": [_ctx, C.c_int32, C.POINTER(fdtd_material)],
     "fdtd_set_periodic": [_ctx, C.c_int32, _i32p],
     "fdtd_dft_flux": [_ctx, C.c_int32, C.POINTER(C.c_double)],
+    "fdtd_step_backward": [_ctx, C.c_int32],
     "fdtd_add_source": [_ctx, C.c_int32, C.c_int32, _i32p, _i32p, C.POINTER(C.c_double), C.c_int32, _i32p],
     "fdtd_add_dft_monitor": [_ctx, C.c_int32, _i32p, _i32p, C.c_uint32, C.c_int32, C.POINTER(C.c_double),
                              _i32p],
@@ -274,6 +275,9 @@ def fdtd_dft_flux(ctx, monitor, n_freq):
     out = np.zeros(int(n_freq), dtype=np.float64)
     _check(load().fdtd_dft_flux(ctx, int(monitor), out.ctypes.data_as(C.POINTER(C.c_double))), "fdtd_dft_flux", ctx)
     return out
+
+
+fdtd_step_backward = _wrap_simple("fdtd_step_backward")
 
 
 def fdtd_set_periodic(ctx, domain, periodic):
