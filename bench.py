@@ -375,6 +375,7 @@ def extras(ctx, sc, args, dev):
         F = specs[0]
         return float((F.abs() ** 2).sum()), [torch.view_as_real(2.0 * F).contiguous()]
 
+    _warm_loss(loss, dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     (_, _), grads, stats = runner.run(T_STEPS, loss)
@@ -450,7 +451,7 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0,
                     help="n: run only a short n^3 FP32 forward (ncu captures on a case larger than L2)")
     ap.add_argument("--workload", default="cpml128",
-                    choices=["cpml128", "pec32", "batched", "adjoint256", "large640"],
+                    choices=["cpml128", "pec32", "batched", "adjoint256", "large640", "reversible256"],
                     help="cpml128 is the benchmark line; the others measure the remaining workloads")
     ap.add_argument("--fd-cells", type=int, default=20)
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision of --profile-case")
@@ -467,7 +468,7 @@ def main():
         profile_case(args)
     elif args.workload != "cpml128" and args.impl == "ours":
         {"pec32": measure_pec32, "batched": measure_batched, "adjoint256": measure_adjoint256,
-         "large640": measure_large640}[args.workload](args)
+         "large640": measure_large640, "reversible256": measure_reversible256}[args.workload](args)
     elif args.impl == "reference":
         run_reference(args)
     else:
@@ -612,6 +613,15 @@ def measure_batched(args):
         dist.destroy_process_group()
 
 
+def _warm_loss(loss, device):
+    """Calls a spectra loss once on a small complex tensor so that torch's one-time set-up of its
+    complex-number kernels (seconds on a fresh process) stays out of the timed gradients."""
+    import torch
+    z = torch.ones(2, 3, dtype=torch.complex128, device=device)
+    loss([z])
+    torch.cuda.synchronize()
+
+
 def _fd_gradient_check(sc, n_cells, h, rng_seed, dtype_fd="f64", dtype_adj="f32", slots=32):
     """d J / d rho at n_cells seeded design cells: checkpointed adjoint (dtype_adj) against
     central differences of rho (dtype_fd) through the workload's map eps(rho)."""
@@ -627,6 +637,7 @@ def _fd_gradient_check(sc, n_cells, h, rng_seed, dtype_fd="f64", dtype_adj="f32"
         return float((F.abs() ** 2).sum()), [torch.view_as_real(2.0 * F).contiguous()]
 
     ctx = fdtd.Context([sc], dtype=dtype_adj)
+    _warm_loss(loss, ctx.device)
     t0 = time.perf_counter()
     (J, _), grads, stats = ADJ.DesignAdjoint(ctx, slots=slots).run(sc.n_steps, loss)
     torch.cuda.synchronize()
@@ -686,6 +697,51 @@ def measure_adjoint256(args):
     print(json.dumps(res))
 
 
+def measure_reversible256(args):
+    """Lossless 256^3 box (periodic x, PEC y / z), 2000 steps, FP32: the checkpoint-free gradient
+    (backward steps, Sec. 3.2) against the 32-slot checkpointed one, and the periodic forward rate."""
+    import numpy as np
+    import torch
+    from paper_2609_30039_gb300 import adjoint as ADJ
+    from paper_2609_30039_gb300 import build as B
+    from paper_2609_30039_gb300 import fdtd
+    from paper_2609_30039_gb300 import workloads as W
+    B.build()
+    n = args.profile_case or 256
+    sc = W.lossless_design(n=n)
+
+    def loss(specs):
+        F = specs[0]
+        return float((F.abs() ** 2).sum()), [torch.view_as_real(2.0 * F).contiguous()]
+
+    res = {"workload": f"lossless_design_{n}^3 (periodic x, PEC y/z), {sc.n_steps} steps, FP32", "cells": sc.cells}
+    _warm_loss(loss, torch.device("cuda"))
+    ctx = fdtd.Context([sc], dtype="f32")
+    ctx.step(32)
+    fdtd.fdtd_reset(ctx.ctx)
+    fdtd.fdtd_dft_reset(ctx.ctx)
+    t = _timed(lambda: ctx.step(sc.n_steps), ctx.stream)
+    res["forward_gcell_steps_s"] = round(sc.cells * sc.n_steps / t / 1e9, 3)
+    ctx.close()
+    grads = {}
+    for name, make in (("reversible", lambda c: ADJ.ReversibleAdjoint(c)),
+                       ("checkpointed_32", lambda c: ADJ.DesignAdjoint(c, slots=32))):
+        ctx = fdtd.Context([sc], dtype="f32")
+        runner = make(ctx)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        (J, _), g, stats = runner.run(sc.n_steps, loss)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        grads[name] = g[0].cpu().numpy().copy()
+        res[name] = {"J": J, "seconds": round(dt, 3), **{k: int(v) for k, v in stats.items()}}
+        ctx.close()
+    a, b = grads["reversible"], grads["checkpointed_32"]
+    res["reversible_vs_checkpointed_gradient_rel_l2"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    res["speedup"] = round(res["checkpointed_32"]["seconds"] / res["reversible"]["seconds"], 3)
+    print(json.dumps(res))
+
+
 def measure_large640(args):
     """640^3 anisotropic two-pole workload, 4000 steps: the checkpointed gradient with BF16
     snapshots against the same gradient with exact FP32 snapshots."""
@@ -706,6 +762,7 @@ def measure_large640(args):
         return float(a.sum()), [torch.view_as_real(F / a).contiguous()]
 
     res = {"workload": f"large_adjoint_{n}^3, {sc.n_steps} steps", "cells": sc.cells}
+    _warm_loss(loss, torch.device("cuda"))
     grads = {}
     for codec, name in ((fdtd.FDTD_CODEC_NATIVE, "fp32_snapshots"), (fdtd.FDTD_CODEC_BF16, "bf16_snapshots")):
         ctx = fdtd.Context([sc], dtype="f32")

@@ -255,6 +255,25 @@ def random_state_scene(shape=(9, 8, 7), d: int = 2, n_poles: int = 2, aniso: boo
                  periodic=(1, 1, 0) if periodic else (0, 0, 0))
 
 
+def lossless_design(n: int = 256, n_steps: int = 2000, seed_index: int = 13,
+                    wavelengths=(18.0, 20.0, 22.0)) -> Scene:
+    """Lossless nondispersive n^3 box for the reversible gradient: periodic in x, PEC in y and z
+    (no CPML), eps_r ~ U[1, 6] in 8^3 blocks, an Ez sheet at z = n/8, a design box against the
+    x = 0 seam (x in [0, n/8), y in [3n/8, 5n/8), z in [7n/16, 9n/16)) and an Ex DFT patch."""
+    rng = _rng(seed_index)
+    b = 8
+    eps = rng.uniform(1.0, 6.0, size=(n // b, n // b, n // b))
+    inv = 1.0 / np.repeat(np.repeat(np.repeat(eps, b, 0), b, 1), b, 2)
+    zs = n // 8
+    src = Source(EZ, (0, 1, zs), (n, n, zs + 1), gaussian_pulse(n_steps))
+    zt = (3 * n) // 4
+    c, hw = n // 2, max(1, n // 32)
+    mon = Monitor((c - hw, c - hw, zt), (c + hw, c + hw, zt + 1), (EX,), omegas_for(wavelengths))
+    design = ((0, (3 * n) // 8, (7 * n) // 16), (n // 8, (5 * n) // 8, (9 * n) // 16))
+    return Scene(shape=(n, n, n), n_steps=n_steps, cpml=(0,) * 6, inv_eps=[inv], sources=[src], monitors=[mon],
+                 design=design, periodic=(1, 0, 0), name=f"lossless_design_{n}^3")
+
+
 def periodic_cell(shape=(24, 20, 48), d: int = 8, n_steps: int = 300, layer=(18, 30), block: int = 4,
                   seed_index: int = 12, wavelengths=(9.0, 10.0, 11.0)) -> Scene:
     """Periodic unit cell (x and y periodic, CPML on both z faces): eps_r ~ U[1, 6] per block of
