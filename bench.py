@@ -451,9 +451,12 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0,
                     help="n: run only a short n^3 FP32 forward (ncu captures on a case larger than L2)")
     ap.add_argument("--workload", default="cpml128",
-                    choices=["cpml128", "pec32", "batched", "adjoint256", "large640", "reversible256"],
+                    choices=["cpml128", "pec32", "batched", "adjoint256", "large640", "reversible256", "streamed"],
                     help="cpml128 is the benchmark line; the others measure the remaining workloads")
     ap.add_argument("--fd-cells", type=int, default=20)
+    ap.add_argument("--stream-n", type=int, default=768, help="--workload streamed: grid edge")
+    ap.add_argument("--slab", type=int, default=128, help="--workload streamed: owned planes per slab")
+    ap.add_argument("--halo", type=int, default=16, help="--workload streamed: halo planes (steps per batch)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision of --profile-case")
     ap.add_argument("--cpml", type=int, default=CPML, help="CPML depth of --profile-case (0: PEC box)")
     ap.add_argument("--adjoint", action="store_true", help="--profile-case: also time as many transposed steps")
@@ -468,7 +471,8 @@ def main():
         profile_case(args)
     elif args.workload != "cpml128" and args.impl == "ours":
         {"pec32": measure_pec32, "batched": measure_batched, "adjoint256": measure_adjoint256,
-         "large640": measure_large640, "reversible256": measure_reversible256}[args.workload](args)
+         "large640": measure_large640, "reversible256": measure_reversible256,
+         "streamed": measure_streamed}[args.workload](args)
     elif args.impl == "reference":
         run_reference(args)
     else:
@@ -777,6 +781,46 @@ def measure_large640(args):
         ctx.close()
     a, b = grads["fp32_snapshots"], grads["bf16_snapshots"]
     res["bf16_vs_fp32_snapshot_gradient_rel_l2"] = float(np.linalg.norm(b - a) / np.linalg.norm(a))
+    print(json.dumps(res))
+
+
+def measure_streamed(args):
+    """Host-streamed forward (Sec. 4.2): an n^3 FP32 domain (CPML on every face, uniform eps, a point
+    source and a point monitor) whose state lives in pinned host memory and is stepped in z-slabs
+    with halos, against the resident context on the same domain: rates, device bytes held and
+    bitwise equality of the six fields after the same steps."""
+    import numpy as np
+    import torch
+    from paper_2609_30039_gb300 import build as B
+    from paper_2609_30039_gb300 import fdtd
+    from paper_2609_30039_gb300 import workloads as W
+    B.build()
+    n, slab, halo = args.stream_n, args.slab, args.halo
+    steps = 4 * halo
+    c = n // 2
+    sc = W.Scene(shape=(n, n, n), n_steps=(args.warmup + 1) * steps, cpml=(CPML,) * 6, kappa_max=5.0,
+                 alpha_max=0.05, inv_eps=[np.ones((n, n, n), dtype=np.float32)],
+                 sources=[W.Source(W.EZ, (c, c, c), (c + 1, c + 1, c + 1),
+                                   W.gaussian_pulse((args.warmup + 1) * steps, 20.0))],
+                 monitors=[W.Monitor((c + 9, c, c), (c + 10, c + 1, c + 1), (W.EZ,), W.omegas_for((18.0, 20.0)))],
+                 name=f"streamed_{n}^3")
+    res = {"workload": f"host-streamed forward {n}^3 FP32, CPML {CPML}, uniform eps, point source and monitor",
+           "slab": slab, "halo": halo, "timed_steps": steps, "cells": sc.cells}
+    out = {}
+    for kind in ("streamed", "resident"):
+        torch.cuda.synchronize()
+        f0 = torch.cuda.mem_get_info()[0]
+        ctx = fdtd.Context([sc], dtype="f32", streamed=(slab, halo) if kind == "streamed" else None)
+        torch.cuda.synchronize()
+        res[f"{kind}_device_bytes"] = int(f0 - torch.cuda.mem_get_info()[0])
+        for _ in range(args.warmup):
+            ctx.step(steps)
+        t = _timed(lambda: ctx.step(steps), ctx.stream)
+        res[f"{kind}_gcell_steps_s"] = round(sc.cells * steps / t / 1e9, 2)
+        out[kind] = [ctx.part(0, f) for f in range(6)] + [ctx.dft(0)]
+        ctx.close()
+    res["streamed_over_resident_time"] = round(res["resident_gcell_steps_s"] / res["streamed_gcell_steps_s"], 3)
+    res["bitwise_equal_fields_and_spectra"] = all(torch.equal(a, b) for a, b in zip(out["streamed"], out["resident"]))
     print(json.dumps(res))
 
 

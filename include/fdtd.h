@@ -11,7 +11,8 @@
  *   Sec. 3.1, Eq. (adjoint): transposed kernel of every update and the material
  *             cotangent d(objective)/d(eps^-1);
  *   Sec. 3.2: checkpoint snapshots for replay;
- *   Sec. 4.1: several independent structures advanced by one launch.
+ *   Sec. 4.1: several independent structures advanced by one launch;
+ *   Sec. 4.2: host-streamed slabs (state in host memory, stepped slab by slab with halos).
  *
  * Conventions (all entry points):
  *   - Reduced units: lengths in cells, c = eps0 = mu0 = 1; only the Courant number
@@ -113,6 +114,24 @@ typedef struct {
  * stream.  *out is set only on FDTD_OK. */
 fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cpml* cpml,
                         const fdtd_material* materials, void* stream, fdtd_ctx** out);
+
+/* Creates a host-streamed context of one domain (Sec. 4.2).  The fields, CPML memories and pole
+ * states live in pinned host memory owned by the context; material->inv_eps[a] and
+ * material->pole_mask must be pinned host memory (cudaHostAlloc / cudaHostRegister; borrowed,
+ * same layout as in fdtd_create).  The domain is cut along z (the slowest axis) into slabs of
+ * `slab` owned planes.  fdtd_step_forward advances in batches of at most `halo` steps: each slab's
+ * window (its planes plus up to `halo` planes on each side) is copied into one of three device
+ * workspaces, stepped by the per-cell kernels, and its owned planes are copied back, with the
+ * copies of neighbouring slabs overlapping the stepping on two copy streams.  The owned planes then
+ * hold exactly the values that a resident context (fdtd_create) computes, bit for bit.  The device
+ * holds the three windows of min(nz, slab + 2 halo) planes plus the monitors, not the domain.
+ * Requires 1 <= halo <= slab (FDTD_EINVAL).  Supported on a streamed context: stepping, sources,
+ * DFT monitors and flux, periodic x / y, materials (pinned host), get/set of state parts (which =
+ * 0; the copy may involve device or host memory), reset, step counters, fdtd_check_finite.  Not
+ * supported (FDTD_EINVAL): the adjoint and design calls, snapshots, energy records, the backward
+ * step, autotuning, profiling, and launch modes other than 4. */
+fdtd_status fdtd_create_streamed(const fdtd_grid* grid, const fdtd_cpml* cpml, const fdtd_material* material,
+                                 int32_t slab, int32_t halo, void* stream, fdtd_ctx** out);
 
 /* Frees everything the context owns.  NULL-safe.  Synchronises the stream. */
 fdtd_status fdtd_destroy(fdtd_ctx* ctx);
@@ -243,11 +262,12 @@ fdtd_status fdtd_reset(fdtd_ctx* ctx);
  * d_lo + d_hi; it is empty if the axis has no CPML.  A pole part holds the cells of the box
  * reported by fdtd_ade_box.  Values are in the dtype of the grid.
  * which = 0: forward state; which = 1: adjoint state in natural form (the cotangent of the
- * forward part of the same id; reading it completes any pending transposition first). */
+ * forward part of the same id; reading it completes any pending transposition first).
+ * dst / src: device or pinned host memory of part_size values (copied on the context's stream). */
 fdtd_status fdtd_part_count(fdtd_ctx* ctx, int32_t domain, int32_t* n_parts);
 fdtd_status fdtd_part_size(fdtd_ctx* ctx, int32_t domain, int32_t part, int64_t* n_values);
-fdtd_status fdtd_get_part(fdtd_ctx* ctx, int32_t domain, int32_t which, int32_t part, void* dst_device);
-fdtd_status fdtd_set_part(fdtd_ctx* ctx, int32_t domain, int32_t which, int32_t part, const void* src_device);
+fdtd_status fdtd_get_part(fdtd_ctx* ctx, int32_t domain, int32_t which, int32_t part, void* dst);
+fdtd_status fdtd_set_part(fdtd_ctx* ctx, int32_t domain, int32_t which, int32_t part, const void* src);
 /* Box [lo, hi) of the pole states of a domain (empty box if it has no dispersive cell). */
 fdtd_status fdtd_ade_box(fdtd_ctx* ctx, int32_t domain, int32_t lo[3], int32_t hi[3]);
 /* Sets the forward step count (after the caller wrote a state with fdtd_set_part). */

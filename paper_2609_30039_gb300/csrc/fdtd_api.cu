@@ -130,6 +130,27 @@ struct fdtd_ctx {
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     long long graph_launches[2][2] = {{0, 0}, {0, 0}};
     int use_graphs = 1;
+    // host streaming (Sec. 4.2): the one domain's fields, CPML memories, pole state and materials
+    // live in pinned host memory; each batch of up to sk steps runs z-slab by z-slab (sw owned
+    // planes plus sk halo planes on each side) in a ring of three device workspaces
+    int streamed = 0;
+    int sw = 0, sk = 0;
+    std::vector<void*> host_owned;            // pinned host allocations of the context
+    struct Workspace {
+        void* F[6] = {};
+        void* ie[3] = {};
+        void* psiE[3][2] = {};
+        void* psiH[3][2] = {};
+        void* ade = nullptr;
+        void* mask = nullptr;
+    } ws[3];
+    cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+    cudaEvent_t ws_done[3] = {}, ws_free[3] = {};
+    std::vector<cudaEvent_t> ev_in, ev_out;   // per slab: its window copied in / its planes copied out
+    void* d_sdoms = nullptr;                  // one descriptor per slab (workspace pointers, local box)
+    DftItem* d_sitems = nullptr;              // DFT items of the owned planes of every slab
+    std::vector<int> sitem_begin, sitem_count;
+    int stream_dirty = 1;
     // instrumentation
     int prof_on = 0;
     int prof_used = 0;
@@ -166,6 +187,11 @@ fdtd_status fail(fdtd_ctx* c, fdtd_status st, const std::string& msg) {
         if ((ctx)->poisoned) return fail((ctx), FDTD_ESTATE, "context poisoned by an earlier CUDA error"); \
     } while (0)
 
+#define NOT_STREAMED(ctx)                                                                          \
+    do {                                                                                           \
+        if ((ctx)->streamed) return fail((ctx), FDTD_EINVAL, "not available on a host-streamed context"); \
+    } while (0)
+
 fdtd_status dmalloc(fdtd_ctx* c, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return FDTD_OK;
@@ -177,6 +203,21 @@ fdtd_status dmalloc(fdtd_ctx* c, void** p, size_t bytes) {
     if (e != cudaSuccess) return fail(c, FDTD_ECUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     c->owned.push_back(*p);
     CK(c, cudaMemsetAsync(*p, 0, bytes, c->stream));
+    return FDTD_OK;
+}
+
+// Pinned host allocation (host-streamed contexts), zero-filled, owned by the context.
+fdtd_status hmalloc(fdtd_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return FDTD_OK;
+    cudaError_t e = cudaHostAlloc(p, bytes, cudaHostAllocDefault);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(c, FDTD_ENOMEM, "cudaHostAlloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    if (e != cudaSuccess) return fail(c, FDTD_ECUDA, std::string("cudaHostAlloc: ") + cudaGetErrorString(e));
+    c->host_owned.push_back(*p);
+    std::memset(*p, 0, bytes);
     return FDTD_OK;
 }
 
@@ -410,6 +451,7 @@ fdtd_status sync_doms(fdtd_ctx* c) {
     // captured graphs of the per-cell mode hold the domains' pointers as kernel parameters:
     // any descriptor change (materials, sources, monitors, design) invalidates them
     drop_graphs(c);
+    c->stream_dirty = 1;
     fdtd_status st = sync_tmaps(c);
     if (st != FDTD_OK) return st;
     return c->dtype == FDTD_F32 ? sync_doms_t<float>(c) : sync_doms_t<double>(c);
@@ -453,6 +495,7 @@ void drop_graphs(fdtd_ctx* c);
 
 fdtd_status sync_mons(fdtd_ctx* c) {
     drop_graphs(c);
+    c->stream_dirty = 1;
     if (c->d_mons) {
         CK(c, cudaStreamSynchronize(c->stream));
         dfree(c, c->d_mons);
@@ -475,7 +518,8 @@ fdtd_status sync_mons(fdtd_ctx* c) {
     {
         std::vector<DftItem> items;
         for (size_t mi = 0; mi < c->mons.size(); ++mi)
-            for (long long b = 0; b < c->mons[mi].m.ncell; b += kTileX * kTileY) items.push_back({(int)mi, (int)b});
+            for (long long b = 0; b < c->mons[mi].m.ncell; b += kTileX * kTileY) items.push_back({(int)mi, (int)b, (int)std::min<long long>(b + kTileX * kTileY, c->mons[mi].m.ncell),
+                                 c->mons[mi].m.dom, 0});
         fdtd_status st = dmalloc(c, (void**)&c->d_dft_items, sizeof(DftItem) * items.size());
         if (st != FDTD_OK) return st;
         CK(c, cudaMemcpyAsync(c->d_dft_items, items.data(), sizeof(DftItem) * items.size(), cudaMemcpyHostToDevice,
@@ -841,6 +885,8 @@ CellArgs<T> make_cell_args(const fdtd_ctx* c, int di, bool e_side) {
         any = true;
     }
     ca.dom = di;
+    ca.kz0 = 0;
+    ca.nzg = h.n[2];
     return ca;
 }
 
@@ -944,6 +990,300 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
         if (dstream) cudaEventRecord(c->ev_dh, c->dft_stream);
         if (dstream && last) cudaStreamWaitEvent(st, c->ev_dh, 0);
     }
+}
+
+// ---- host streaming (Sec. 4.2) ------------------------------------------------------------------
+// The one domain is cut into z-slabs of sw owned planes.  A batch of kb <= sk steps advances every
+// slab in turn: its window (owned planes plus up to sk planes on each side) is copied from the
+// host state into a device workspace, stepped kb times with the resident per-cell kernels (the
+// global plane offset picks the CPML z profile and the sources), and its owned planes are copied
+// back.  Each step spoils one more plane at each cut edge of the window (a cut edge is stepped as
+// if it were a PEC / open end), so after kb <= sk steps the owned planes hold exactly the values
+// the resident stepper computes.  z is the slowest axis of every per-cell array, so a window is one
+// contiguous range per array.
+struct SlabWin {
+    int zs, ze;     // owned planes [zs, ze)
+    int wlo, whi;   // window [wlo, whi)
+    int zb0, zb1;   // window part of the pole-state box
+};
+
+SlabWin slab_win(const fdtd_ctx* c, int s) {
+    const DomainHost& h = c->doms[0];
+    const int nz = h.n[2];
+    SlabWin w;
+    w.zs = s * c->sw;
+    w.ze = std::min(nz, w.zs + c->sw);
+    w.wlo = std::max(0, w.zs - c->sk);
+    w.whi = std::min(nz, w.ze + c->sk);
+    w.zb0 = std::max(w.wlo, h.blo[2]);
+    w.zb1 = std::min(w.whi, h.bhi[2]);
+    if (h.npole == 0 || h.bcell == 0 || w.zb1 <= w.zb0) w.zb0 = w.zb1 = 0;
+    return w;
+}
+
+int slab_count(const fdtd_ctx* c) { return (c->doms[0].n[2] + c->sw - 1) / c->sw; }
+
+// Elements per z-plane of CPML memory (a, s) (axis (a + 1 + s) % 3; 0 when that axis has none);
+// the z-axis memories are indexed by CPML plane, not by grid plane.
+long long psi_plane(const DomainHost& h, int a, int s) {
+    const int ax = (a + 1 + s) % 3;
+    if (h.ns[ax] == 0) return 0;
+    if (ax == 0) return (long long)h.n[1] * h.ns[0];
+    if (ax == 1) return (long long)h.ns[1] * h.n[0];
+    return (long long)h.n[0] * h.n[1];
+}
+
+// Per-slab descriptors (workspace pointers, local pole box) and the DFT items of its owned planes.
+template <typename T>
+fdtd_status stream_prepare(fdtd_ctx* c) {
+    if (!c->stream_dirty) return FDTD_OK;
+    CK(c, cudaStreamSynchronize(c->stream));
+    const DomainHost& h = c->doms[0];
+    const int nsl = slab_count(c);
+    const long long nxy = (long long)h.n[0] * h.n[1];
+    std::vector<Dom<T>> hd(nsl);
+    std::vector<DftItem> items;
+    c->sitem_begin.assign(nsl, 0);
+    c->sitem_count.assign(nsl, 0);
+    for (int s = 0; s < nsl; ++s) {
+        const SlabWin w = slab_win(c, s);
+        const fdtd_ctx::Workspace& ws = c->ws[s % 3];
+        Dom<T>& d = hd[s];
+        fill_dom<T>(c, h, d);
+        d.n[2] = w.whi - w.wlo;
+        d.ncell = nxy * d.n[2];
+        for (int f = 0; f < 6; ++f) {
+            d.F[f] = (T*)ws.F[f];
+            d.A[f] = nullptr;
+        }
+        for (int a = 0; a < 3; ++a) {
+            // distinct eps^-1 arrays get distinct workspace copies
+            int src = a;
+            for (int b = 0; b < a; ++b)
+                if (h.ie[b] == h.ie[a]) {
+                    src = b;
+                    break;
+                }
+            d.ie[a] = (const T*)ws.ie[src];
+            for (int s2 = 0; s2 < 2; ++s2) {
+                d.psiE[a][s2] = (T*)ws.psiE[a][s2];
+                d.psiH[a][s2] = (T*)ws.psiH[a][s2];
+                d.apsiE[a][s2] = d.apsiH[a][s2] = nullptr;
+            }
+        }
+        d.mask = (const uint8_t*)ws.mask;
+        d.aade = nullptr;
+        d.ade = (T*)ws.ade;
+        d.grad = nullptr;
+        d.design = 0;
+        d.energy = nullptr;
+        if (w.zb1 > w.zb0) {
+            d.blo[2] = w.zb0 - w.wlo;
+            d.bhi[2] = w.zb1 - w.wlo;
+            d.bcell = (long long)(h.bhi[0] - h.blo[0]) * (h.bhi[1] - h.blo[1]) * (w.zb1 - w.zb0);
+        } else {
+            for (int q = 0; q < 3; ++q) d.blo[q] = d.bhi[q] = 0;
+            d.bcell = 0;
+        }
+        // DFT: monitor cells of the owned planes (cells are numbered x fastest, z slowest)
+        c->sitem_begin[s] = (int)items.size();
+        for (size_t mi = 0; mi < c->mons.size(); ++mi) {
+            const Mon& m = c->mons[mi].m;
+            const int za = std::max(w.zs, m.lo[2]), zb = std::min(w.ze, m.hi[2]);
+            if (zb <= za) continue;
+            const long long per = (long long)m.bx * m.by;
+            const long long c0 = (za - m.lo[2]) * per, c1 = (zb - m.lo[2]) * per;
+            for (long long b = c0; b < c1; b += kTileX * kTileY)
+                items.push_back({(int)mi, (int)b, (int)std::min<long long>(b + kTileX * kTileY, c1), s, w.wlo});
+        }
+        c->sitem_count[s] = (int)items.size() - c->sitem_begin[s];
+    }
+    if (!c->d_sdoms) {
+        fdtd_status st = dmalloc(c, &c->d_sdoms, sizeof(Dom<T>) * nsl);
+        if (st != FDTD_OK) return st;
+    }
+    CK(c, cudaMemcpyAsync(c->d_sdoms, hd.data(), sizeof(Dom<T>) * nsl, cudaMemcpyHostToDevice, c->stream));
+    if (c->d_sitems) dfree(c, c->d_sitems);
+    c->d_sitems = nullptr;
+    if (!items.empty()) {
+        fdtd_status st = dmalloc(c, (void**)&c->d_sitems, sizeof(DftItem) * items.size());
+        if (st != FDTD_OK) return st;
+        CK(c, cudaMemcpyAsync(c->d_sitems, items.data(), sizeof(DftItem) * items.size(), cudaMemcpyHostToDevice,
+                              c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->stream_dirty = 0;
+    return FDTD_OK;
+}
+
+// Copies window or owned planes between the host state and workspace r (to_dev: host -> device
+// of the window; otherwise device -> host of the owned planes).
+fdtd_status stream_copy(fdtd_ctx* c, const SlabWin& w, int r, bool to_dev, cudaStream_t st) {
+    const DomainHost& h = c->doms[0];
+    fdtd_ctx::Workspace& ws = c->ws[r];
+    const size_t esz = c->esz;
+    const long long nxy = (long long)h.n[0] * h.n[1];
+    const int nz = h.n[2];
+    const int lo = to_dev ? w.wlo : w.zs, hi = to_dev ? w.whi : w.ze;   // global planes moved
+    const cudaMemcpyKind kind = to_dev ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    // planes [lo, hi) of an array of `per` elements per plane; the workspace holds the window
+    auto planes = [&](void* home, void* dev, long long per, size_t el) -> cudaError_t {
+        if (per == 0 || hi <= lo) return cudaSuccess;
+        char* hp = (char*)home + (size_t)lo * per * el;
+        char* dp = (char*)dev + (size_t)(lo - w.wlo) * per * el;
+        const size_t bytes = (size_t)(hi - lo) * per * el;
+        return to_dev ? cudaMemcpyAsync(dp, hp, bytes, kind, st) : cudaMemcpyAsync(hp, dp, bytes, kind, st);
+    };
+    for (int f = 0; f < 6; ++f) CK(c, planes(h.F[f], ws.F[f], nxy, esz));
+    if (to_dev) {
+        for (int a = 0; a < 3; ++a) {
+            bool dup = false;
+            for (int b = 0; b < a; ++b) dup = dup || h.ie[b] == h.ie[a];
+            if (!dup) CK(c, planes(const_cast<void*>(h.ie[a]), ws.ie[a], nxy, esz));
+        }
+        if (h.npole > 0 && h.mask) CK(c, planes(const_cast<uint8_t*>(h.mask), ws.mask, nxy, 1));
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int s = 0; s < 2; ++s) {
+            const long long per = psi_plane(h, a, s);
+            if (per == 0) continue;
+            void* home[2] = {h.psiE[a][s], h.psiH[a][s]};
+            void* dev[2] = {ws.psiE[a][s], ws.psiH[a][s]};
+            if ((a + 1 + s) % 3 != 2) {
+                for (int e = 0; e < 2; ++e) CK(c, planes(home[e], dev[e], per, esz));
+                continue;
+            }
+            // z memories: CPML planes [0, dlo) are grid planes [0, dlo), planes [dlo, ns) are grid
+            // planes [nz - dhi, nz); the workspace keeps the whole array at the same offsets
+            const int dlo = h.dlo[2], dhi = h.dhi[2];
+            const int r0[2] = {lo, std::max(lo, nz - dhi)}, r1[2] = {std::min(hi, dlo), hi};
+            for (int part = 0; part < 2; ++part) {
+                if (r1[part] <= r0[part]) continue;
+                const long long p0 = part == 0 ? r0[0] : dlo + (r0[1] - (nz - dhi));
+                const size_t off = (size_t)p0 * per * esz, bytes = (size_t)(r1[part] - r0[part]) * per * esz;
+                for (int e = 0; e < 2; ++e) {
+                    char* hp = (char*)home[e] + off;
+                    char* dp = (char*)dev[e] + off;
+                    CK(c, to_dev ? cudaMemcpyAsync(dp, hp, bytes, kind, st) : cudaMemcpyAsync(hp, dp, bytes, kind, st));
+                }
+            }
+        }
+    // pole state: chunks [component][pole][P / Q] of the box, z slowest inside a chunk
+    if (w.zb1 > w.zb0) {
+        const long long bxy = (long long)(h.bhi[0] - h.blo[0]) * (h.bhi[1] - h.blo[1]);
+        const long long lb = bxy * (w.zb1 - w.zb0);
+        const int z0 = std::max(lo, w.zb0), z1 = std::min(hi, w.zb1);
+        if (z1 > z0) {
+            const size_t bytes = (size_t)(z1 - z0) * bxy * esz;
+            for (int q = 0; q < 6 * h.npole; ++q) {
+                char* hp = (char*)h.ade + ((size_t)q * h.bcell + (size_t)(z0 - h.blo[2]) * bxy) * esz;
+                char* dp = (char*)ws.ade + ((size_t)q * lb + (size_t)(z0 - w.zb0) * bxy) * esz;
+                CK(c, to_dev ? cudaMemcpyAsync(dp, hp, bytes, kind, st) : cudaMemcpyAsync(hp, dp, bytes, kind, st));
+            }
+        }
+    }
+    return FDTD_OK;
+}
+
+template <typename T>
+CellArgs<T> stream_cell_args(const fdtd_ctx* c, int s, bool e_side) {
+    const SlabWin w = slab_win(c, s);
+    const fdtd_ctx::Workspace& ws = c->ws[s % 3];
+    const DomainHost& h = c->doms[0];
+    CellArgs<T> ca = make_cell_args<T>(c, 0, e_side);
+    for (int f = 0; f < 6; ++f) ca.F[f] = (T*)ws.F[f];
+    for (int a = 0; a < 3; ++a) {
+        int src = a;
+        for (int b = 0; b < a; ++b)
+            if (h.ie[b] == h.ie[a]) {
+                src = b;
+                break;
+            }
+        ca.ie[a] = (const T*)ws.ie[src];
+        for (int s2 = 0; s2 < 2; ++s2) ca.psi[a][s2] = (T*)(e_side ? ws.psiE[a][s2] : ws.psiH[a][s2]);
+    }
+    ca.n[2] = w.whi - w.wlo;
+    ca.kz0 = w.wlo;
+    ca.nzg = h.n[2];
+    ca.dom = s;
+    return ca;
+}
+
+// n_steps forward steps of a host-streamed context, in batches of at most sk steps.
+template <typename T>
+fdtd_status stream_forward(fdtd_ctx* c, int n_steps) {
+    fdtd_status st = stream_prepare<T>(c);
+    if (st != FDTD_OK) return st;
+    const DomainHost& h = c->doms[0];
+    const int nsl = slab_count(c);
+    const Launch l{c->stream, &c->launches};
+    const Dom<T>* sd = (const Dom<T>*)c->d_sdoms;
+    StepArgs a;
+    a.srcs = c->d_srcs;
+    a.mons = c->d_mons;
+    a.d_step = c->d_step;
+    a.d_ticket = c->d_ticket;
+    a.dft_on = c->dft_enabled;
+    a.dft_items = nullptr;
+    a.ndft = 0;
+    a.d_base = c->d_base;
+    a.offset = 0;
+    // the host state may have been written on the caller's stream (set_part, reset)
+    CK(c, cudaEventRecord(c->ev_fork, c->stream));
+    CK(c, cudaStreamWaitEvent(c->h2d_stream, c->ev_fork, 0));
+    auto copy_in = [&](int s) -> fdtd_status {
+        const int r = s % 3;
+        // the workspace is free once its last slab has been copied out; the window's host planes
+        // hold the batch's start state once the previous batch copied out slab s + 1 (in order
+        // after slabs s - 1 and s)
+        CK(c, cudaStreamWaitEvent(c->h2d_stream, c->ws_free[r], 0));
+        CK(c, cudaStreamWaitEvent(c->h2d_stream, c->ev_out[std::min(s + 1, nsl - 1)], 0));
+        fdtd_status e = stream_copy(c, slab_win(c, s), r, true, c->h2d_stream);
+        if (e != FDTD_OK) return e;
+        CK(c, cudaEventRecord(c->ev_in[s], c->h2d_stream));
+        return FDTD_OK;
+    };
+    int left = n_steps;
+    while (left > 0) {
+        const int kb = std::min(left, c->sk);
+        st = copy_in(0);
+        if (st != FDTD_OK) return st;
+        for (int s = 0; s < nsl; ++s) {
+            const int r = s % 3;
+            // the next window is read before this slab's owned planes are written back
+            if (s + 1 < nsl) {
+                st = copy_in(s + 1);
+                if (st != FDTD_OK) return st;
+            }
+            CK(c, cudaStreamWaitEvent(c->stream, c->ev_in[s], 0));
+            if (s == 0) launch_copy_int(l, c->d_step, c->d_base);
+            const CellArgs<T> ce = stream_cell_args<T>(c, s, true), ch = stream_cell_args<T>(c, s, false);
+            const SlabWin w = slab_win(c, s);
+            const int poles = h.npole > 0 && w.zb1 > w.zb0;
+            const int nd = c->dft_enabled ? c->sitem_count[s] : 0;
+            const DftItem* items = c->d_sitems ? c->d_sitems + c->sitem_begin[s] : nullptr;
+            for (int o = 0; o < kb; ++o) {
+                a.offset = o;
+                launch_e_cell<T>(l, ce, sd, (T)c->S, a, c->aniso, poles);
+                if (nd > 0) launch_dft<T>(l, sd, c->d_mons, items, nd, 0, c->d_base, o);
+                launch_h_cell<T>(l, ch, (T)c->S, a);
+                if (nd > 0) launch_dft<T>(l, sd, c->d_mons, items, nd, 1, c->d_base, o);
+            }
+            if (s == nsl - 1) launch_advance(l, c->d_step, kb);
+            CK(c, cudaEventRecord(c->ws_done[r], c->stream));
+            CK(c, cudaStreamWaitEvent(c->d2h_stream, c->ws_done[r], 0));
+            if (s + 1 < nsl) CK(c, cudaStreamWaitEvent(c->d2h_stream, c->ev_in[s + 1], 0));
+            st = stream_copy(c, w, r, false, c->d2h_stream);
+            if (st != FDTD_OK) return st;
+            CK(c, cudaEventRecord(c->ev_out[s], c->d2h_stream));
+            CK(c, cudaEventRecord(c->ws_free[r], c->d2h_stream));
+        }
+        left -= kb;
+    }
+    // later work on the caller's stream sees the final host state
+    CK(c, cudaStreamWaitEvent(c->stream, c->ev_out[nsl - 1], 0));
+    CKL(c);
+    return FDTD_OK;
 }
 
 template <typename T>
@@ -1066,6 +1406,62 @@ size_t snapshot_bytes(const fdtd_ctx* c, int codec) {
     return tot;
 }
 
+// True when every array of a material is in pinned (page-locked) host memory.
+bool host_material(const fdtd_material& m) {
+    auto pinned = [](const void* p) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return at.type == cudaMemoryTypeHost;
+    };
+    for (int a = 0; a < 3; ++a)
+        if (!pinned(m.inv_eps[a])) return false;
+    return m.n_poles == 0 || pinned(m.pole_mask);
+}
+
+// Device workspaces, copy streams and events of a host-streamed context.
+fdtd_status stream_alloc(fdtd_ctx* c) {
+    const DomainHost& d = c->doms[0];
+    const long long nxy = (long long)d.n[0] * d.n[1];
+    const int nw = std::min(d.n[2], c->sw + 2 * c->sk);
+    const size_t fb = (size_t)nw * nxy * c->esz;
+    for (int r = 0; r < 3; ++r) {
+        fdtd_ctx::Workspace& w = c->ws[r];
+        for (int f = 0; f < 6; ++f)
+            if (dmalloc(c, &w.F[f], fb) != FDTD_OK) return FDTD_ENOMEM;
+        for (int a = 0; a < 3; ++a)
+            if (dmalloc(c, &w.ie[a], fb) != FDTD_OK) return FDTD_ENOMEM;
+        for (int a = 0; a < 3; ++a)
+            for (int s = 0; s < 2; ++s) {
+                const long long per = psi_plane(d, a, s);
+                const size_t sb = (size_t)per * ((a + 1 + s) % 3 == 2 ? d.ns[2] : nw) * c->esz;
+                if (dmalloc(c, &w.psiE[a][s], sb) || dmalloc(c, &w.psiH[a][s], sb)) return FDTD_ENOMEM;
+            }
+        if (d.npole > 0 && d.bcell > 0) {
+            if (dmalloc(c, &w.mask, (size_t)nw * nxy) != FDTD_OK) return FDTD_ENOMEM;
+            const size_t ab = 6 * (size_t)d.npole * (d.bhi[0] - d.blo[0]) * (d.bhi[1] - d.blo[1]) *
+                              std::min(d.bhi[2] - d.blo[2], nw) * c->esz;
+            if (dmalloc(c, &w.ade, ab) != FDTD_OK) return FDTD_ENOMEM;
+        }
+    }
+    CK(c, cudaStreamCreateWithFlags(&c->h2d_stream, cudaStreamNonBlocking));
+    CK(c, cudaStreamCreateWithFlags(&c->d2h_stream, cudaStreamNonBlocking));
+    for (int r = 0; r < 3; ++r) {
+        CK(c, cudaEventCreateWithFlags(&c->ws_done[r], cudaEventDisableTiming));
+        CK(c, cudaEventCreateWithFlags(&c->ws_free[r], cudaEventDisableTiming));
+    }
+    const int nsl = slab_count(c);
+    c->ev_in.assign(nsl, nullptr);
+    c->ev_out.assign(nsl, nullptr);
+    for (int s = 0; s < nsl; ++s) {
+        CK(c, cudaEventCreateWithFlags(&c->ev_in[s], cudaEventDisableTiming));
+        CK(c, cudaEventCreateWithFlags(&c->ev_out[s], cudaEventDisableTiming));
+    }
+    return FDTD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1079,12 +1475,16 @@ const char* fdtd_last_error(const fdtd_ctx* ctx) {
     return ctx->err.c_str();
 }
 
-fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cpml* cpml,
-                        const fdtd_material* materials, void* stream, fdtd_ctx** out) {
+static fdtd_status create_impl(int32_t n_domains, const fdtd_grid* grids, const fdtd_cpml* cpml,
+                               const fdtd_material* materials, void* stream, fdtd_ctx** out, int streamed, int sw,
+                               int sk) {
     if (!out || n_domains < 1 || !grids || !cpml || !materials) return FDTD_EINVAL;
     *out = nullptr;
     fdtd_ctx* c = new fdtd_ctx();
     c->stream = (cudaStream_t)stream;
+    c->streamed = streamed;
+    c->sw = sw;
+    c->sk = sk;
     c->dtype = grids[0].dtype;
     g_create_err.clear();
     auto bail = [&](fdtd_status st) {
@@ -1113,6 +1513,10 @@ fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cp
             (!(p.m >= 0) || !(p.kappa_max >= 1) || !(p.alpha_max >= 0)))
             return bail(FDTD_EINVAL);
         if (check_material(c, materials[di]) != FDTD_OK) return bail(FDTD_EINVAL);
+        if (streamed && !host_material(materials[di])) {
+            c->err = "a host-streamed context needs its eps^-1 arrays and pole mask in pinned host memory";
+            return bail(FDTD_EINVAL);
+        }
     }
     // scratch
     cudaError_t e = cudaMalloc((void**)&c->d_flag, 64);
@@ -1175,6 +1579,19 @@ fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cp
             d.npole = 0;
             d.mask = nullptr;
         }
+        if (streamed) {
+            // three workspaces of one window each (fields, eps^-1, CPML memories, mask, pole state)
+            const long long nxy = (long long)d.n[0] * d.n[1];
+            const int nw = std::min(d.n[2], sw + 2 * sk);
+            size_t ws = (size_t)nw * nxy * (9 * c->esz + (d.npole > 0 ? 1 : 0));
+            ws += 4 * ((size_t)nw * d.n[1] * d.ns[0] + (size_t)nw * d.ns[1] * d.n[0] + (size_t)d.ns[2] * nxy) * c->esz;
+            if (d.bcell > 0)
+                ws += 6 * (size_t)d.npole * (d.bhi[0] - d.blo[0]) * (d.bhi[1] - d.blo[1]) *
+                      std::min(d.bhi[2] - d.blo[2], nw) * c->esz;
+            plan += 3 * ws;
+            for (int q = 0; q < 3; ++q) plan += 6 * d.n[q] * c->esz;
+            continue;
+        }
         plan += 12 * (size_t)d.ncell * c->esz;
         for (int q = 0; q < 3; ++q) plan += 8 * (size_t)(d.ncell / d.n[q]) * d.ns[q] * c->esz + 6 * d.n[q] * c->esz;
         plan += 2 * 6 * (size_t)d.npole * d.bcell * c->esz;
@@ -1188,11 +1605,22 @@ fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cp
     for (int di = 0; di < n_domains; ++di) {
         DomainHost& d = c->doms[di];
         const size_t fb = (size_t)d.ncell * c->esz;
-        for (int f = 0; f < 6; ++f) {
+        if (streamed) {
+            // the state lives in pinned host memory; no adjoint arrays
+            for (int f = 0; f < 6; ++f)
+                if (hmalloc(c, &d.F[f], fb) != FDTD_OK) return bail(FDTD_ENOMEM);
+            for (int a = 0; a < 3; ++a)
+                for (int s = 0; s < 2; ++s) {
+                    const int ax = (a + 1 + s) % 3;
+                    const size_t sb = (size_t)(d.ncell / d.n[ax]) * d.ns[ax] * c->esz;
+                    if (hmalloc(c, &d.psiE[a][s], sb) || hmalloc(c, &d.psiH[a][s], sb)) return bail(FDTD_ENOMEM);
+                }
+        }
+        for (int f = 0; f < 6 && !streamed; ++f) {
             if (dmalloc(c, &d.F[f], fb) != FDTD_OK) return bail(FDTD_ENOMEM);
             if (dmalloc(c, &d.A[f], fb) != FDTD_OK) return bail(FDTD_ENOMEM);
         }
-        for (int a = 0; a < 3; ++a)
+        for (int a = 0; a < 3 && !streamed; ++a)
             for (int s = 0; s < 2; ++s) {
                 const int ax = (a + 1 + s) % 3;
                 const size_t sb = (size_t)(d.ncell / d.n[ax]) * d.ns[ax] * c->esz;
@@ -1215,11 +1643,20 @@ fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cp
                 return bail(FDTD_ECUDA);
         }
         const size_t ab = 6 * (size_t)d.npole * d.bcell * c->esz;
-        if (dmalloc(c, &d.ade, ab) || dmalloc(c, &d.aade, ab)) return bail(FDTD_ENOMEM);
+        if (streamed) {
+            if (hmalloc(c, &d.ade, ab)) return bail(FDTD_ENOMEM);
+        } else if (dmalloc(c, &d.ade, ab) || dmalloc(c, &d.aade, ab)) {
+            return bail(FDTD_ENOMEM);
+        }
+    }
+    if (streamed) {
+        fdtd_status st = stream_alloc(c);
+        if (st != FDTD_OK) return bail(st);
     }
     const size_t domb = (c->dtype == FDTD_F32 ? sizeof(Dom<float>) : sizeof(Dom<double>)) * n_domains;
     if (dmalloc(c, &c->d_doms, domb) != FDTD_OK) return bail(FDTD_ENOMEM);
-    if (dmalloc(c, &c->d_tmaps, sizeof(CUtensorMap) * kTmaMaps * n_domains) != FDTD_OK) return bail(FDTD_ENOMEM);
+    if (!streamed && dmalloc(c, &c->d_tmaps, sizeof(CUtensorMap) * kTmaMaps * n_domains) != FDTD_OK)
+        return bail(FDTD_ENOMEM);
     build_tiles(c);
     for (int di = 0; di < n_domains; ++di) {
         const DomainHost& d = c->doms[di];
@@ -1236,6 +1673,23 @@ fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cp
     return FDTD_OK;
 }
 
+fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cpml* cpml,
+                        const fdtd_material* materials, void* stream, fdtd_ctx** out) {
+    return create_impl(n_domains, grids, cpml, materials, stream, out, 0, 0, 0);
+}
+
+fdtd_status fdtd_create_streamed(const fdtd_grid* grid, const fdtd_cpml* cpml, const fdtd_material* material,
+                                 int32_t slab, int32_t halo, void* stream, fdtd_ctx** out) {
+    if (!out) return FDTD_EINVAL;
+    *out = nullptr;
+    g_create_err.clear();
+    if (halo < 1 || slab < halo) {
+        g_create_err = "host streaming needs halo >= 1 and slab >= halo";
+        return FDTD_EINVAL;
+    }
+    return create_impl(1, grid, cpml, material, stream, out, 1, slab, halo);
+}
+
 static void prof_release(fdtd_ctx* ctx);
 
 fdtd_status fdtd_destroy(fdtd_ctx* ctx) {
@@ -1250,7 +1704,19 @@ fdtd_status fdtd_destroy(fdtd_ctx* ctx) {
     if (ctx->dft_stream) cudaStreamDestroy(ctx->dft_stream);
     for (cudaEvent_t e : {ctx->ev_e, ctx->ev_h, ctx->ev_de, ctx->ev_dh})
         if (e) cudaEventDestroy(e);
+    for (cudaStream_t st : {ctx->h2d_stream, ctx->d2h_stream})
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+    for (int r = 0; r < 3; ++r)
+        for (cudaEvent_t e : {ctx->ws_done[r], ctx->ws_free[r]})
+            if (e) cudaEventDestroy(e);
+    for (auto* v : {&ctx->ev_in, &ctx->ev_out})
+        for (cudaEvent_t e : *v)
+            if (e) cudaEventDestroy(e);
     for (void* p : ctx->owned) cudaFree(p);
+    for (void* p : ctx->host_owned) cudaFreeHost(p);
     for (auto& s : ctx->slots) cudaFree(s.second.buf);
     delete ctx;
     return FDTD_OK;
@@ -1298,6 +1764,8 @@ fdtd_status fdtd_set_material(fdtd_ctx* ctx, int32_t domain, const fdtd_material
     if (!valid_dom(ctx, domain) || !m) return fail(ctx, FDTD_EINVAL, "bad domain or material");
     fdtd_status st = check_material(ctx, *m);
     if (st != FDTD_OK) return st;
+    if (ctx->streamed && !host_material(*m))
+        return fail(ctx, FDTD_EINVAL, "a host-streamed context needs its materials in pinned host memory");
     DomainHost& d = ctx->doms[domain];
     if (m->n_poles != d.npole) return fail(ctx, FDTD_EINVAL, "the pole count cannot change after create");
     if (d.npole > 0) {
@@ -1455,6 +1923,7 @@ fdtd_status fdtd_dft_enable(fdtd_ctx* ctx, int32_t enabled) {
 
 fdtd_status fdtd_enable_energy(fdtd_ctx* ctx, int32_t capacity) {
     GUARD(ctx);
+    NOT_STREAMED(ctx);
     if (capacity < 1) return fail(ctx, FDTD_EINVAL, "capacity must be >= 1");
     for (auto& d : ctx->doms) {
         if (d.energy) dfree(ctx, d.energy);
@@ -1489,6 +1958,12 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
             st = sync_mons(ctx);
             if (st != FDTD_OK) return st;
         }
+    }
+    if (ctx->streamed) {
+        fdtd_status st = ctx->dtype == FDTD_F32 ? stream_forward<float>(ctx, n_steps) : stream_forward<double>(ctx, n_steps);
+        if (st != FDTD_OK) return st;
+        ctx->step += n_steps;
+        return FDTD_OK;
     }
     int left = n_steps;
     if (ctx->use_persistent && n_steps > 0) {
@@ -1545,6 +2020,7 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
 
 fdtd_status fdtd_step_backward(fdtd_ctx* ctx, int32_t n_steps) {
     GUARD(ctx);
+    NOT_STREAMED(ctx);
     if (n_steps < 0) return fail(ctx, FDTD_EINVAL, "n_steps must be >= 0");
     for (const auto& d : ctx->doms) {
         if (d.ns[0] || d.ns[1] || d.ns[2] || d.npole > 0)
@@ -1581,6 +2057,7 @@ fdtd_status fdtd_step_backward(fdtd_ctx* ctx, int32_t n_steps) {
 
 fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode) {
     GUARD(ctx);
+    if (ctx->streamed && mode != 4) return fail(ctx, FDTD_EINVAL, "a host-streamed context steps per cell (mode 4)");
     if (mode < 0 || mode >= FDTD_LAUNCH_MODES) return fail(ctx, FDTD_EINVAL, "launch mode must be in [0, 4]");
     if (mode != ctx->cell_mode * 4) drop_graphs(ctx);   // graphs hold the launches of one mode
     ctx->use_persistent = mode >= 1 && mode <= 3;
@@ -1603,6 +2080,7 @@ static fdtd_status restore_slot(fdtd_ctx* ctx, int32_t slot);
 
 fdtd_status fdtd_autotune(fdtd_ctx* ctx, int32_t n_steps, double* ms_per_mode) {
     GUARD(ctx);
+    NOT_STREAMED(ctx);
     if (n_steps < 1) return fail(ctx, FDTD_EINVAL, "n_steps must be >= 1");
     const int slot = 1 << 30;   // private slot id (public ids are below 2^30)
     const int energy = ctx->energy_on;
@@ -1690,6 +2168,19 @@ fdtd_status fdtd_set_step_count(fdtd_ctx* ctx, int64_t n) {
 
 fdtd_status fdtd_reset(fdtd_ctx* ctx) {
     GUARD(ctx);
+    if (ctx->streamed) {
+        // host state: cleared by the host once the streams are idle
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->d2h_stream));
+        const DomainHost& d = ctx->doms[0];
+        for (int p = 0; p < part_count(d); ++p) {
+            void* ptr = part_ptr(d, 0, p, ctx->esz);
+            const long long n = part_size(d, p);
+            if (ptr && n) std::memset(ptr, 0, (size_t)n * ctx->esz);
+        }
+        ctx->step = 0;
+        return set_device_step(ctx, 0);
+    }
     for (auto& d : ctx->doms)
         for (int p = 0; p < part_count(d); ++p) {
             void* ptr = part_ptr(d, 0, p, ctx->esz);
@@ -1721,13 +2212,14 @@ fdtd_status fdtd_get_part(fdtd_ctx* ctx, int32_t domain, int32_t which, int32_t 
     if (!valid_dom(ctx, domain) || (which != 0 && which != 1) || !dst) return fail(ctx, FDTD_EINVAL, "bad arguments");
     const DomainHost& d = ctx->doms[domain];
     if (part < 0 || part >= part_count(d)) return fail(ctx, FDTD_EINVAL, "bad part id");
+    if (which == 1 && ctx->streamed) return fail(ctx, FDTD_EINVAL, "a host-streamed context has no adjoint state");
     if (which == 1) {
         fdtd_status st = flush_adjoint(ctx);
         if (st != FDTD_OK) return st;
     }
     const long long n = part_size(d, part);
     if (n == 0) return FDTD_OK;
-    CK(ctx, cudaMemcpyAsync(dst, part_ptr(d, which, part, ctx->esz), (size_t)n * ctx->esz, cudaMemcpyDeviceToDevice,
+    CK(ctx, cudaMemcpyAsync(dst, part_ptr(d, which, part, ctx->esz), (size_t)n * ctx->esz, cudaMemcpyDefault,
                             ctx->stream));
     return FDTD_OK;
 }
@@ -1737,13 +2229,14 @@ fdtd_status fdtd_set_part(fdtd_ctx* ctx, int32_t domain, int32_t which, int32_t 
     if (!valid_dom(ctx, domain) || (which != 0 && which != 1) || !src) return fail(ctx, FDTD_EINVAL, "bad arguments");
     const DomainHost& d = ctx->doms[domain];
     if (part < 0 || part >= part_count(d)) return fail(ctx, FDTD_EINVAL, "bad part id");
+    if (which == 1 && ctx->streamed) return fail(ctx, FDTD_EINVAL, "a host-streamed context has no adjoint state");
     if (which == 1) {
         fdtd_status st = flush_adjoint(ctx);
         if (st != FDTD_OK) return st;
     }
     const long long n = part_size(d, part);
     if (n == 0) return FDTD_OK;
-    CK(ctx, cudaMemcpyAsync(part_ptr(d, which, part, ctx->esz), src, (size_t)n * ctx->esz, cudaMemcpyDeviceToDevice,
+    CK(ctx, cudaMemcpyAsync(part_ptr(d, which, part, ctx->esz), src, (size_t)n * ctx->esz, cudaMemcpyDefault,
                             ctx->stream));
     return FDTD_OK;
 }
@@ -1760,6 +2253,7 @@ fdtd_status fdtd_ade_box(fdtd_ctx* ctx, int32_t domain, int32_t lo[3], int32_t h
 
 fdtd_status fdtd_snapshot_bytes(fdtd_ctx* ctx, int32_t codec, int64_t* bytes) {
     GUARD(ctx);
+    NOT_STREAMED(ctx);
     if (!bytes || (codec != FDTD_CODEC_NATIVE && codec != FDTD_CODEC_BF16)) return fail(ctx, FDTD_EINVAL, "bad codec");
     *bytes = (int64_t)snapshot_bytes(ctx, codec);
     return FDTD_OK;
@@ -1847,6 +2341,7 @@ static fdtd_status restore_slot(fdtd_ctx* ctx, int32_t slot) {
 
 fdtd_status fdtd_state_save(fdtd_ctx* ctx, int32_t slot, int32_t codec) {
     GUARD(ctx);
+    NOT_STREAMED(ctx);
     if (slot < 0 || slot >= (1 << 30) || (codec != FDTD_CODEC_NATIVE && codec != FDTD_CODEC_BF16))
         return fail(ctx, FDTD_EINVAL, "bad slot or codec");
     return save_slot(ctx, slot, codec);
@@ -1854,6 +2349,7 @@ fdtd_status fdtd_state_save(fdtd_ctx* ctx, int32_t slot, int32_t codec) {
 
 fdtd_status fdtd_state_restore(fdtd_ctx* ctx, int32_t slot) {
     GUARD(ctx);
+    NOT_STREAMED(ctx);
     if (slot < 0 || slot >= (1 << 30)) return fail(ctx, FDTD_EINVAL, "bad slot");
     return restore_slot(ctx, slot);
 }
@@ -1868,6 +2364,7 @@ fdtd_status fdtd_snapshots_free(fdtd_ctx* ctx) {
 
 fdtd_status fdtd_set_design(fdtd_ctx* ctx, int32_t domain, const int32_t lo[3], const int32_t hi[3], double* grad) {
     GUARD(ctx);
+    NOT_STREAMED(ctx);
     if (!valid_dom(ctx, domain)) return fail(ctx, FDTD_EINVAL, "bad domain");
     DomainHost& d = ctx->doms[domain];
     if (!grad) {
@@ -1890,6 +2387,7 @@ fdtd_status fdtd_set_design(fdtd_ctx* ctx, int32_t domain, const int32_t lo[3], 
 
 fdtd_status fdtd_set_adjoint_source(fdtd_ctx* ctx, int32_t monitor_id, const void* cot) {
     GUARD(ctx);
+    NOT_STREAMED(ctx);
     if (monitor_id < 0 || monitor_id >= (int)ctx->mons.size()) return fail(ctx, FDTD_EINVAL, "bad monitor id");
     ctx->mons[monitor_id].m.cot = (const double2*)cot;
     return sync_mons(ctx);
@@ -1897,6 +2395,7 @@ fdtd_status fdtd_set_adjoint_source(fdtd_ctx* ctx, int32_t monitor_id, const voi
 
 fdtd_status fdtd_adjoint_begin(fdtd_ctx* ctx) {
     GUARD(ctx);
+    NOT_STREAMED(ctx);
     for (auto& d : ctx->doms)
         for (int p = 0; p < part_count(d); ++p) {
             void* ptr = part_ptr(d, 1, p, ctx->esz);
@@ -1926,6 +2425,7 @@ fdtd_status fdtd_adjoint_begin(fdtd_ctx* ctx) {
 
 fdtd_status fdtd_step_adjoint(fdtd_ctx* ctx, int32_t n_steps) {
     GUARD(ctx);
+    NOT_STREAMED(ctx);
     if (n_steps < 0 || n_steps > ctx->adj_step) return fail(ctx, FDTD_EINVAL, "n_steps out of range");
     bool design = false;
     for (auto& d : ctx->doms) design = design || d.design;
@@ -2027,6 +2527,7 @@ static void prof_release(fdtd_ctx* ctx) {
 
 fdtd_status fdtd_profile_begin(fdtd_ctx* ctx, int32_t max_launches) {
     GUARD(ctx);
+    NOT_STREAMED(ctx);
     if (max_launches < 1) return fail(ctx, FDTD_EINVAL, "max_launches must be >= 1");
     prof_release(ctx);
     ctx->prof_ev.resize(2 * (size_t)max_launches);

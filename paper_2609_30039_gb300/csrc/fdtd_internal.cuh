@@ -92,10 +92,15 @@ struct Mon {
     int cap;
 };
 
-// A DFT work item: cells [begin, begin + 256) of monitor `mon` (one thread per cell).
+// A DFT work item: cells [begin, min(begin + 256, end)) of monitor `mon` (one thread per cell),
+// read from domain descriptor `dom` whose plane k holds global plane k + kz0 (a host-streamed slab;
+// resident items have dom = the monitor's domain, kz0 = 0).
 struct DftItem {
     int mon;
     int begin;
+    int end;
+    int dom;
+    int kz0;
 };
 
 struct Src {
@@ -251,6 +256,10 @@ struct CellArgs {
     int src[kMaxSrcPerDom];
     int src_lo[3], src_hi[3];   // bounding box of this half-step's sources (empty: lo = hi = 0)
     int dom;
+    // z window of a host-streamed slab: local plane k is global plane k + kz0 of a domain of nzg
+    // planes (the CPML z profile, its memory index and the source boxes use global planes); a
+    // resident domain has kz0 = 0, nzg = n[2]
+    int kz0, nzg;
 };
 
 // One thread per cell over all cells of one domain (per-cell streaming launch mode).

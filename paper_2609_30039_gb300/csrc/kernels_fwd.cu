@@ -112,11 +112,11 @@ __device__ __forceinline__ void dft_item(const Dom<T>* __restrict__ doms, const 
                                          const DftItem& it, int kind, int step) {
     const Mon& m = mons[it.mon];
     const long long cell = it.begin + threadIdx.y * kTileX + threadIdx.x;
-    if (cell >= m.ncell) return;
+    if (cell >= it.end) return;
     const int i = m.lo[0] + (int)(cell % m.bx);
     const int j = m.lo[1] + (int)((cell / m.bx) % m.by);
-    const int k = m.lo[2] + (int)(cell / ((long long)m.bx * m.by));
-    const Dom<T>& d = doms[m.dom];
+    const int k = m.lo[2] + (int)(cell / ((long long)m.bx * m.by)) - it.kz0;
+    const Dom<T>& d = doms[it.dom];
     const long long id = cidx(d.n, i, j, k);
     const double2* ph = m.phase + ((long long)step * 2 + kind) * m.nf;
     const int nf = m.nf;
@@ -577,6 +577,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
     k_e_cell(const CellArgs<T> c, const Dom<T>* __restrict__ doms, T S, const StepArgs a) {
     const int nx = c.n[0], ny = c.n[1];
     const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
+    const int kg = k + c.kz0;   // global plane (CPML z profile, sources)
     if (i >= nx || j >= ny) return;
     const long long nxy = (long long)nx * ny;
     const long long id = ((long long)k * ny + j) * nx + i;
@@ -600,12 +601,12 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
     const bool px = pj || pk, py = pi || pk, pz = pi || pj;   // PEC-held
     if (kBack) {
         T sx = T(0), sy = T(0), sz = T(0);
-        if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && k >= c.src_lo[2] &&
-            k < c.src_hi[2]) {
+        if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && kg >= c.src_lo[2] &&
+            kg < c.src_hi[2]) {
             const int step = *a.d_base + a.offset;
-            sx = src_add_t<T>(c, a.srcs, 0, i, j, k, step);
-            sy = src_add_t<T>(c, a.srcs, 1, i, j, k, step);
-            sz = src_add_t<T>(c, a.srcs, 2, i, j, k, step);
+            sx = src_add_t<T>(c, a.srcs, 0, i, j, kg, step);
+            sy = src_add_t<T>(c, a.srcs, 1, i, j, kg, step);
+            sz = src_add_t<T>(c, a.srcs, 2, i, j, kg, step);
         }
         if (!px) c.F[0][id] = fma_t(S * iex, (yx1 - yx2), ex - sx);
         if (!py) c.F[1][id] = fma_t(S * iey, (yy1 - yy2), ey - sy);
@@ -613,11 +614,11 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
         return;
     }
     if (c.ns[2]) {
-        const int sl = slab_of(k, c.dlo[2], c.dhi[2], c.n[2]);
+        const int sl = slab_of(kg, c.dlo[2], c.dhi[2], c.nzg);
         if (sl >= 0) {
             const long long o = ((long long)sl * ny + j) * nx + i;
-            if (!px) yx2 = cpml_cell(c.coef[2], c.n[2], k, c.psi[0][1] + o, yx2);
-            if (!py) yy1 = cpml_cell(c.coef[2], c.n[2], k, c.psi[1][0] + o, yy1);
+            if (!px) yx2 = cpml_cell(c.coef[2], c.nzg, kg, c.psi[0][1] + o, yx2);
+            if (!py) yy1 = cpml_cell(c.coef[2], c.nzg, kg, c.psi[1][0] + o, yy1);
         }
     }
     if (c.ns[0]) {
@@ -652,12 +653,12 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
         if (!py) ey = fma_t(S * iey, (yy1 - yy2), ey);
         if (!pz) ez = fma_t(S * iez, (yz1 - yz2), ez);
     }
-    if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && k >= c.src_lo[2] &&
-        k < c.src_hi[2]) {
+    if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && kg >= c.src_lo[2] &&
+        kg < c.src_hi[2]) {
         const int step = *a.d_base + a.offset;
-        ex += src_add_t<T>(c, a.srcs, 0, i, j, k, step);
-        ey += src_add_t<T>(c, a.srcs, 1, i, j, k, step);
-        ez += src_add_t<T>(c, a.srcs, 2, i, j, k, step);
+        ex += src_add_t<T>(c, a.srcs, 0, i, j, kg, step);
+        ey += src_add_t<T>(c, a.srcs, 1, i, j, kg, step);
+        ez += src_add_t<T>(c, a.srcs, 2, i, j, kg, step);
     }
     if (!px) c.F[0][id] = ex;
     if (!py) c.F[1][id] = ey;
@@ -670,6 +671,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
     k_h_cell(const CellArgs<T> c, T S, const StepArgs a) {
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
     const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
+    const int kg = k + c.kz0;   // global plane (CPML z profile, sources)
     if (i < nx && j < ny) {
         const long long nxy = (long long)nx * ny;
         const long long id = ((long long)k * ny + j) * nx + i;
@@ -687,12 +689,12 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
         const T hx = c.F[3][id], hy = c.F[4][id], hz = c.F[5][id];
         if (kBack) {
             T mx = T(0), my = T(0), mz = T(0);
-            if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && k >= c.src_lo[2] &&
-                k < c.src_hi[2]) {
+            if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && kg >= c.src_lo[2] &&
+                kg < c.src_hi[2]) {
                 const int step = *a.d_base + a.offset;
-                mx = src_add_t<T>(c, a.srcs, 3, i, j, k, step);
-                my = src_add_t<T>(c, a.srcs, 4, i, j, k, step);
-                mz = src_add_t<T>(c, a.srcs, 5, i, j, k, step);
+                mx = src_add_t<T>(c, a.srcs, 3, i, j, kg, step);
+                my = src_add_t<T>(c, a.srcs, 4, i, j, kg, step);
+                mz = src_add_t<T>(c, a.srcs, 5, i, j, kg, step);
             }
             c.F[3][id] = fma_t(-S, (yx1 - yx2), hx - mx);
             c.F[4][id] = fma_t(-S, (yy1 - yy2), hy - my);
@@ -700,11 +702,11 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
             return;
         }
         if (c.ns[2]) {
-            const int sl = slab_of(k, c.dlo[2], c.dhi[2], nz);
+            const int sl = slab_of(kg, c.dlo[2], c.dhi[2], c.nzg);
             if (sl >= 0) {
                 const long long o = ((long long)sl * ny + j) * nx + i;
-                yx2 = cpml_cell(c.coef[2], nz, k, c.psi[0][1] + o, yx2);
-                yy1 = cpml_cell(c.coef[2], nz, k, c.psi[1][0] + o, yy1);
+                yx2 = cpml_cell(c.coef[2], c.nzg, kg, c.psi[0][1] + o, yx2);
+                yy1 = cpml_cell(c.coef[2], c.nzg, kg, c.psi[1][0] + o, yy1);
             }
         }
         if (c.ns[0]) {
@@ -726,12 +728,12 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
         T hx1 = fma_t(-S, (yx1 - yx2), hx);
         T hy1 = fma_t(-S, (yy1 - yy2), hy);
         T hz1 = fma_t(-S, (yz1 - yz2), hz);
-        if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && k >= c.src_lo[2] &&
-            k < c.src_hi[2]) {
+        if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && kg >= c.src_lo[2] &&
+            kg < c.src_hi[2]) {
             const int step = *a.d_base + a.offset;
-            hx1 += src_add_t<T>(c, a.srcs, 3, i, j, k, step);
-            hy1 += src_add_t<T>(c, a.srcs, 4, i, j, k, step);
-            hz1 += src_add_t<T>(c, a.srcs, 5, i, j, k, step);
+            hx1 += src_add_t<T>(c, a.srcs, 3, i, j, kg, step);
+            hy1 += src_add_t<T>(c, a.srcs, 4, i, j, kg, step);
+            hz1 += src_add_t<T>(c, a.srcs, 5, i, j, kg, step);
         }
         c.F[3][id] = hx1;
         c.F[4][id] = hy1;

@@ -69,6 +69,8 @@ _ctx = C.c_void_p
 _SIGS = {
     "fdtd_create": [C.c_int32, C.POINTER(fdtd_grid), C.POINTER(fdtd_cpml), C.POINTER(fdtd_material), _vp,
                     C.POINTER(_ctx)],
+    "fdtd_create_streamed": [C.POINTER(fdtd_grid), C.POINTER(fdtd_cpml), C.POINTER(fdtd_material), C.c_int32,
+                             C.c_int32, _vp, C.POINTER(_ctx)],
     "fdtd_destroy": [_ctx],
     "fdtd_last_error": [_ctx],
     "fdtd_version": [],
@@ -168,6 +170,16 @@ def fdtd_create(grids, cpmls, materials, stream=0):
     out = _ctx()
     st = lib.fdtd_create(n, ga, ca, ma, _vp(stream), C.byref(out))
     _check(st, "fdtd_create", None)
+    return out
+
+
+def fdtd_create_streamed(grid, cpml, material, slab, halo, stream=0):
+    """Host-streamed context of one domain (Sec. 4.2): state in pinned host memory, stepped in
+    z-slabs of `slab` planes with `halo` halo planes (batches of at most `halo` steps)."""
+    out = _ctx()
+    st = load().fdtd_create_streamed(C.byref(grid), C.byref(cpml), C.byref(material), int(slab), int(halo),
+                                     _vp(stream), C.byref(out))
+    _check(st, "fdtd_create_streamed", None)
     return out
 
 
@@ -349,12 +361,17 @@ class Context:
     """Owns one fdtd_ctx built from workload Scenes (one per domain) and the torch tensors the
     library borrows (inv_eps, pole masks, gradient buffers, adjoint sources)."""
 
-    def __init__(self, scenes, dtype: str = "f32", device: str = "cuda:0", stream=None):
+    def __init__(self, scenes, dtype: str = "f32", device: str = "cuda:0", stream=None, streamed=None):
+        """streamed: None (state in device memory) or (slab, halo) for a host-streamed context of
+        one domain (Sec. 4.2), whose materials are then kept in pinned host memory."""
         import torch
         self.torch = torch
         if not isinstance(scenes, (list, tuple)):
             scenes = [scenes]
         self.scenes = list(scenes)
+        self.streamed = tuple(int(v) for v in streamed) if streamed is not None else None
+        if self.streamed is not None and len(self.scenes) != 1:
+            raise ValueError("a host-streamed context holds one domain")
         self.tdtype = torch.float32 if dtype == "f32" else torch.float64
         self.npdtype = np.float32 if dtype == "f32" else np.float64
         self.code = FDTD_F32 if dtype == "f32" else FDTD_F64
@@ -375,7 +392,11 @@ class Context:
             ie = self._material_tensors(sc)
             self.inv_eps.append(ie)
             mats.append(self._material_struct(sc, ie))
-        self.ctx = fdtd_create(grids, cpmls, mats, stream=self.stream.cuda_stream)
+        if self.streamed is not None:
+            self.ctx = fdtd_create_streamed(grids[0], cpmls[0], mats[0], self.streamed[0], self.streamed[1],
+                                            stream=self.stream.cuda_stream)
+        else:
+            self.ctx = fdtd_create(grids, cpmls, mats, stream=self.stream.cuda_stream)
         self.monitors = []
         self.sources = []
         for d, sc in enumerate(self.scenes):
@@ -393,13 +414,17 @@ class Context:
             if sc.energy:
                 fdtd_enable_energy(self.ctx, sc.n_steps + 8)
 
+    def _place(self, t):
+        """Material arrays live on the device, or in pinned host memory for a streamed context."""
+        return t.pin_memory() if self.streamed is not None else t.to(self.device)
+
     def _material_tensors(self, sc):
         torch = self.torch
         arrs = sc.inv_eps3()
         if arrs[0] is arrs[1] and arrs[1] is arrs[2]:
-            t = torch.from_numpy(np.ascontiguousarray(arrs[0], dtype=self.npdtype)).to(self.device)
+            t = self._place(torch.from_numpy(np.ascontiguousarray(arrs[0], dtype=self.npdtype)))
             return [t, t, t]
-        return [torch.from_numpy(np.ascontiguousarray(a, dtype=self.npdtype)).to(self.device) for a in arrs]
+        return [self._place(torch.from_numpy(np.ascontiguousarray(a, dtype=self.npdtype))) for a in arrs]
 
     def _material_struct(self, sc, ie, mask_tensor=None):
         torch = self.torch
@@ -412,8 +437,8 @@ class Context:
             arr = (fdtd_pole * npole)(*[fdtd_pole(int(k), float(de), float(w), float(g)) for k, de, w, g in sc.poles])
             self._keep.append(arr)
             m.poles = C.cast(arr, C.POINTER(fdtd_pole))
-            mk = mask_tensor if mask_tensor is not None else torch.from_numpy(
-                np.ascontiguousarray(sc.pole_mask, dtype=np.uint8)).to(self.device)
+            mk = mask_tensor if mask_tensor is not None else self._place(torch.from_numpy(
+                np.ascontiguousarray(sc.pole_mask, dtype=np.uint8)))
             self.masks.append(mk)
             m.pole_mask = mk.data_ptr()
         else:
@@ -425,6 +450,12 @@ class Context:
         """Rebinds domain's eps^-1 to the given device tensors (kept alive here)."""
         sc = self.scenes[domain]
         ie = [t.contiguous() for t in ie_tensors]
+        if self.streamed is not None:
+            pinned = {}
+            for t in ie:   # the same tensor three times stays one (isotropic) array
+                if id(t) not in pinned:
+                    pinned[id(t)] = t if t.is_pinned() else t.cpu().pin_memory()
+            ie = [pinned[id(t)] for t in ie]
         self.inv_eps[domain] = ie
         mk = None
         if sc.pole_mask is not None and len(sc.poles):
