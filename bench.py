@@ -455,8 +455,8 @@ def main():
                     help="cpml128 is the benchmark line; the others measure the remaining workloads")
     ap.add_argument("--fd-cells", type=int, default=20)
     ap.add_argument("--stream-n", type=int, default=768, help="--workload streamed: grid edge")
-    ap.add_argument("--slab", type=int, default=128, help="--workload streamed: owned planes per slab")
-    ap.add_argument("--halo", type=int, default=16, help="--workload streamed: halo planes (steps per batch)")
+    ap.add_argument("--slab", type=int, default=256, help="--workload streamed: owned planes per slab")
+    ap.add_argument("--halo", type=int, default=32, help="--workload streamed: halo planes (steps per batch)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision of --profile-case")
     ap.add_argument("--cpml", type=int, default=CPML, help="CPML depth of --profile-case (0: PEC box)")
     ap.add_argument("--adjoint", action="store_true", help="--profile-case: also time as many transposed steps")

@@ -23,7 +23,9 @@
  *   - Sec. 3.1, Eq. (adjoint): reverse recursion, transposed curls, the CPML
  *                 transpose  psibar_mem = psibar + ybar, Dbar = ybar/kappa + c psibar_mem,
  *                 psibar_old = b psibar_mem, and the transposed 2x2 pole system;
- *                 material cotangent w.r.t. eps^{-1}.
+ *                 material cotangent w.r.t. eps^{-1}; pole-parameter cotangents
+ *                 (d J / d(deps, w, gamma) of each pole) through the transposed
+ *                 dispersion update.
  *
  * Readings where the paper is silent (all listed with their reasons in the
  * design notes of the repository):
@@ -81,7 +83,11 @@ typedef struct oracle {
     double *inv_eps[3];
     int npole;
     double a0[MAXP], b1[MAXP], gam[MAXP];
+    int pkind[MAXP]; double pdeps[MAXP], pw[MAXP];   /* the pole parameters as given */
     double M[MAXP][2][2], g[MAXP][2];   /* x^{n+1} = M x^n + g (E^{n+1} + E^n) */
+    /* cotangents of (M00, M01, M10, M11, g0, g1) of each pole, summed over the
+     * dispersive cells, components and adjoint steps since the last adj_reset */
+    double pgc[MAXP][6];
     unsigned char *mask;
     /* forward state */
     double *F[6];                 /* Ex Ey Ez Hx Hy Hz */
@@ -221,6 +227,7 @@ void oracle_set_material(oracle_t *o, const double *iex, const double *iey, cons
         for (int p = 0; p < o->npole; ++p) { free(o->P[a][p]); free(o->Q[a][p]); free(o->aP[a][p]); free(o->aQ[a][p]); }
     o->npole = npole;
     for (int p = 0; p < npole; ++p) {
+        o->pkind[p] = kind[p]; o->pdeps[p] = deps[p]; o->pw[p] = w[p];
         if (kind[p] == 0) { o->a0[p] = w[p] * w[p]; o->b1[p] = deps[p] * w[p] * w[p]; }
         else { o->a0[p] = 0.0; o->b1[p] = w[p] * w[p]; }
         o->gam[p] = gamma[p];
@@ -582,6 +589,50 @@ void oracle_adj_reset(oracle_t *o) {
     int nv = 18 + 6 * o->npole;
     for (int s = 0; s < nv; ++s) memset(v[s], 0, sizeof(double) * (size_t)o->ncell);
     if (o->design_on) for (int a = 0; a < 3; ++a) memset(o->grad[a], 0, sizeof(double) * (size_t)o->dcell);
+    memset(o->pgc, 0, sizeof(o->pgc));
+}
+
+/* d J / d(deps, w, gamma) of each pole (out[3p + 0..2]; a Drude pole has no deps) from the
+ * coefficient cotangents, by differentiating the trapezoidal construction: with
+ * B = I - A/2, M = B^-1 (I + A/2) and g = B^-1 bvec / 2,
+ *   dM = B^-1 (dA/2) (M + I),   dg = B^-1 (dA/2) g + B^-1 dbvec / 2,
+ * A = [[0, 1], [-a0, -gamma]], bvec = (0, b1); Lorentz a0 = w^2, b1 = deps w^2; Drude a0 = 0,
+ * b1 = w^2. */
+void oracle_pole_grad(oracle_t *o, double *out) {
+    for (int p = 0; p < o->npole; ++p) {
+        double A[2][2] = {{0.0, 1.0}, {-o->a0[p], -o->gam[p]}};
+        double B[2][2], Binv[2][2];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) B[r][c] = (r == c ? 1.0 : 0.0) - 0.5 * A[r][c];
+        mat2_inv(B, Binv);
+        const int lor = o->pkind[p] == 0;
+        const double w = o->pw[p], de = o->pdeps[p];
+        /* (d a0, d b1, d gamma) per parameter */
+        const double dpar[3][3] = {{0.0, lor ? w * w : 0.0, 0.0},
+                                   {lor ? 2.0 * w : 0.0, lor ? 2.0 * de * w : 2.0 * w, 0.0},
+                                   {0.0, 0.0, 1.0}};
+        for (int t = 0; t < 3; ++t) {
+            double dA[2][2] = {{0.0, 0.0}, {-dpar[t][0], -dpar[t][2]}};
+            double hdA[2][2], MI[2][2], T1[2][2], dM[2][2];
+            for (int r = 0; r < 2; ++r)
+                for (int c = 0; c < 2; ++c) { hdA[r][c] = 0.5 * dA[r][c]; MI[r][c] = o->M[p][r][c] + (r == c ? 1.0 : 0.0); }
+            mat2_mul(hdA, MI, T1);
+            mat2_mul(Binv, T1, dM);
+            /* dg = B^-1 (hdA g + dbvec / 2) */
+            double v0 = hdA[0][0] * o->g[p][0] + hdA[0][1] * o->g[p][1];
+            double v1 = hdA[1][0] * o->g[p][0] + hdA[1][1] * o->g[p][1] + 0.5 * dpar[t][1];
+            double dg0 = Binv[0][0] * v0 + Binv[0][1] * v1;
+            double dg1 = Binv[1][0] * v0 + Binv[1][1] * v1;
+            out[3 * p + t] = o->pgc[p][0] * dM[0][0] + o->pgc[p][1] * dM[0][1] + o->pgc[p][2] * dM[1][0] +
+                             o->pgc[p][3] * dM[1][1] + o->pgc[p][4] * dg0 + o->pgc[p][5] * dg1;
+        }
+    }
+}
+
+/* The coefficient cotangents themselves: out[6p + 0..5] for (M00, M01, M10, M11, g0, g1). */
+void oracle_pole_coef_grad(oracle_t *o, double *out) {
+    for (int p = 0; p < o->npole; ++p)
+        for (int q = 0; q < 6; ++q) out[6 * p + q] = o->pgc[p][q];
 }
 
 /* dJ/df(t) = Re(conj(Fbar) exp(i w t)) for the components of one kind. */
@@ -610,7 +661,7 @@ void oracle_adjoint_step(oracle_t *o, long m) {
     const int nx = o->N[0], ny = o->N[1], nz = o->N[2];
     /* Forward values of step m needed by the material cotangent: pre-source
      * E^{m+1} and the curl, recomputed from u^m without touching the state. */
-    if (o->design_on) {
+    if (o->design_on || o->npole > 0) {
         double *Pt[3][MAXP], *Qt[3][MAXP], *pst[3][2];
         for (int a = 0; a < 3; ++a) {
             for (int p = 0; p < o->npole; ++p) { Pt[a][p] = zalloc(o->ncell); Qt[a][p] = zalloc(o->ncell); }
@@ -673,6 +724,26 @@ void oracle_adjoint_step(oracle_t *o, long m) {
                         double eps = 1.0 / o->inv_eps[a][id];
                         double G = 0.0;
                         for (int p = 0; p < o->npole; ++p) G += o->g[p][0];
+                        double den = eps + G;
+                        /* pole-parameter cotangents: Et depends on M00, M01 and g0 (through
+                         * num and den), x^{m+1} on all six coefficients; Etot is the total
+                         * cotangent of Et (its own plus the path through x^{m+1}) */
+                        {
+                            double Etot = Etb;
+                            for (int p = 0; p < o->npole; ++p)
+                                Etot += o->g[p][0] * o->aP[a][p][id] + o->g[p][1] * o->aQ[a][p][id];
+                            double Eold = o->F[a][id], Et = o->tmpE[a][id], es = Et + Eold;
+                            for (int p = 0; p < o->npole; ++p) {
+                                double Pp = o->P[a][p][id], Qp = o->Q[a][p][id];
+                                double xbP = o->aP[a][p][id], xbQ = o->aQ[a][p][id];
+                                o->pgc[p][0] += xbP * Pp - Etot * Pp / den;
+                                o->pgc[p][1] += xbP * Qp - Etot * Qp / den;
+                                o->pgc[p][2] += xbQ * Pp;
+                                o->pgc[p][3] += xbQ * Qp;
+                                o->pgc[p][4] += xbP * es - Etot * es / den;
+                                o->pgc[p][5] += xbQ * es;
+                            }
+                        }
                         /* x_p^{m+1} = M_p x_p^m + g_p (Et + E^m) */
                         for (int p = 0; p < o->npole; ++p) {
                             double xbP = o->aP[a][p][id], xbQ = o->aQ[a][p][id];
@@ -683,7 +754,6 @@ void oracle_adjoint_step(oracle_t *o, long m) {
                             o->aQ[a][p][id] = o->M[p][0][1] * xbP + o->M[p][1][1] * xbQ;
                         }
                         /* Et = (eps E + sum_p (P - (M x)_P - g_P E) + S curl) / (eps + G) */
-                        double den = eps + G;
                         Eold_b += Etb * (eps - G) / den;
                         for (int p = 0; p < o->npole; ++p) {
                             o->aP[a][p][id] += Etb * (1.0 - o->M[p][0][0]) / den;

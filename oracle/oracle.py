@@ -79,6 +79,8 @@ def _load():
             "oracle_adj_field": (_dp, [vp, C.c_int]),
             "oracle_adj_reset": (None, [vp]),
             "oracle_adjoint_step": (None, [vp, C.c_long]),
+            "oracle_pole_grad": (None, [vp, _dp]),
+            "oracle_pole_coef_grad": (None, [vp, _dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -292,6 +294,22 @@ class Oracle:
     def adjoint_step(self, m):
         """Adjoint of forward step m; the held forward state must be u^m."""
         self.lib.oracle_adjoint_step(self.h, int(m))
+
+    def pole_grad(self):
+        """d J / d(deps, omega_dt, gamma_dt) of each pole, (n_poles, 3), accumulated by the
+        adjoint steps since adj_reset (Sec. 3.1: pole parameters through the transposed
+        dispersion update)."""
+        n = self.npole
+        out = np.zeros(3 * max(n, 1))
+        self.lib.oracle_pole_grad(self.h, _d(out))
+        return out[: 3 * n].reshape(n, 3)
+
+    def pole_coef_grad(self):
+        """Cotangents of (M00, M01, M10, M11, g0, g1) of each pole, (n_poles, 6)."""
+        n = self.npole
+        out = np.zeros(6 * max(n, 1))
+        self.lib.oracle_pole_coef_grad(self.h, _d(out))
+        return out[: 6 * n].reshape(n, 6)
 
 
 def gradient_replay(orc: Oracle, n_steps: int, objective, segment: int = 0):

@@ -1033,12 +1033,28 @@ long long psi_plane(const DomainHost& h, int a, int s) {
     return (long long)h.n[0] * h.n[1];
 }
 
+// First E component whose eps^-1 array is the same as that of component a.
+int ie_first(const DomainHost& h, int a) {
+    for (int b = 0; b < a; ++b)
+        if (h.ie[b] == h.ie[a]) return b;
+    return a;
+}
+
 // Per-slab descriptors (workspace pointers, local pole box) and the DFT items of its owned planes.
 template <typename T>
 fdtd_status stream_prepare(fdtd_ctx* c) {
     if (!c->stream_dirty) return FDTD_OK;
     CK(c, cudaStreamSynchronize(c->stream));
     const DomainHost& h = c->doms[0];
+    {
+        const size_t fb = (size_t)std::min(h.n[2], c->sw + 2 * c->sk) * h.n[0] * h.n[1] * c->esz;
+        for (int r = 0; r < 3; ++r)
+            for (int a = 0; a < 3; ++a)
+                if (ie_first(h, a) == a && !c->ws[r].ie[a]) {
+                    fdtd_status st = dmalloc(c, &c->ws[r].ie[a], fb);
+                    if (st != FDTD_OK) return st;
+                }
+    }
     const int nsl = slab_count(c);
     const long long nxy = (long long)h.n[0] * h.n[1];
     std::vector<Dom<T>> hd(nsl);
@@ -1057,14 +1073,7 @@ fdtd_status stream_prepare(fdtd_ctx* c) {
             d.A[f] = nullptr;
         }
         for (int a = 0; a < 3; ++a) {
-            // distinct eps^-1 arrays get distinct workspace copies
-            int src = a;
-            for (int b = 0; b < a; ++b)
-                if (h.ie[b] == h.ie[a]) {
-                    src = b;
-                    break;
-                }
-            d.ie[a] = (const T*)ws.ie[src];
+            d.ie[a] = (const T*)ws.ie[ie_first(h, a)];   // distinct arrays, distinct windows
             for (int s2 = 0; s2 < 2; ++s2) {
                 d.psiE[a][s2] = (T*)ws.psiE[a][s2];
                 d.psiH[a][s2] = (T*)ws.psiH[a][s2];
@@ -1136,11 +1145,8 @@ fdtd_status stream_copy(fdtd_ctx* c, const SlabWin& w, int r, bool to_dev, cudaS
     };
     for (int f = 0; f < 6; ++f) CK(c, planes(h.F[f], ws.F[f], nxy, esz));
     if (to_dev) {
-        for (int a = 0; a < 3; ++a) {
-            bool dup = false;
-            for (int b = 0; b < a; ++b) dup = dup || h.ie[b] == h.ie[a];
-            if (!dup) CK(c, planes(const_cast<void*>(h.ie[a]), ws.ie[a], nxy, esz));
-        }
+        for (int a = 0; a < 3; ++a)
+            if (ie_first(h, a) == a) CK(c, planes(const_cast<void*>(h.ie[a]), ws.ie[a], nxy, esz));
         if (h.npole > 0 && h.mask) CK(c, planes(const_cast<uint8_t*>(h.mask), ws.mask, nxy, 1));
     }
     for (int a = 0; a < 3; ++a)
@@ -1193,13 +1199,7 @@ CellArgs<T> stream_cell_args(const fdtd_ctx* c, int s, bool e_side) {
     CellArgs<T> ca = make_cell_args<T>(c, 0, e_side);
     for (int f = 0; f < 6; ++f) ca.F[f] = (T*)ws.F[f];
     for (int a = 0; a < 3; ++a) {
-        int src = a;
-        for (int b = 0; b < a; ++b)
-            if (h.ie[b] == h.ie[a]) {
-                src = b;
-                break;
-            }
-        ca.ie[a] = (const T*)ws.ie[src];
+        ca.ie[a] = (const T*)ws.ie[ie_first(h, a)];
         for (int s2 = 0; s2 < 2; ++s2) ca.psi[a][s2] = (T*)(e_side ? ws.psiE[a][s2] : ws.psiH[a][s2]);
     }
     ca.n[2] = w.whi - w.wlo;
@@ -1431,8 +1431,10 @@ fdtd_status stream_alloc(fdtd_ctx* c) {
         fdtd_ctx::Workspace& w = c->ws[r];
         for (int f = 0; f < 6; ++f)
             if (dmalloc(c, &w.F[f], fb) != FDTD_OK) return FDTD_ENOMEM;
+        // one eps^-1 window per distinct array (an isotropic medium needs one; a later material
+        // with more distinct arrays gets the others in stream_prepare)
         for (int a = 0; a < 3; ++a)
-            if (dmalloc(c, &w.ie[a], fb) != FDTD_OK) return FDTD_ENOMEM;
+            if (ie_first(d, a) == a && dmalloc(c, &w.ie[a], fb) != FDTD_OK) return FDTD_ENOMEM;
         for (int a = 0; a < 3; ++a)
             for (int s = 0; s < 2; ++s) {
                 const long long per = psi_plane(d, a, s);
@@ -1583,7 +1585,8 @@ static fdtd_status create_impl(int32_t n_domains, const fdtd_grid* grids, const 
             // three workspaces of one window each (fields, eps^-1, CPML memories, mask, pole state)
             const long long nxy = (long long)d.n[0] * d.n[1];
             const int nw = std::min(d.n[2], sw + 2 * sk);
-            size_t ws = (size_t)nw * nxy * (9 * c->esz + (d.npole > 0 ? 1 : 0));
+            const int nie = d.ie[0] == d.ie[1] && d.ie[1] == d.ie[2] ? 1 : 3;
+            size_t ws = (size_t)nw * nxy * ((6 + nie) * c->esz + (d.npole > 0 ? 1 : 0));
             ws += 4 * ((size_t)nw * d.n[1] * d.ns[0] + (size_t)nw * d.ns[1] * d.n[0] + (size_t)d.ns[2] * nxy) * c->esz;
             if (d.bcell > 0)
                 ws += 6 * (size_t)d.npole * (d.bhi[0] - d.blo[0]) * (d.bhi[1] - d.blo[1]) *

@@ -342,6 +342,56 @@ def test_gradient_matches_central_differences(dispersive):
     assert 3.6 < r1 / r2 < 4.4, (r1, r2)
 
 
+def _J_poles(sc, poles):
+    sc2 = W.Scene(**{**sc.__dict__, "poles": tuple(poles)})
+    sc2.design = None
+    o = oracle_from_scene(sc2)
+    o.step(sc.n_steps)
+    return _objective(o)[0]
+
+
+def test_pole_parameter_gradient_matches_central_differences():
+    # Sec. 3.1: pole parameters differentiate through the transposed dispersion update.  The
+    # adjoint's d J / d(deps, omega_dt, gamma_dt) of a Lorentz and a Drude pole against central
+    # differences of J through the forward recursion (h = 1e-5 |theta|: truncation and rounding
+    # both below 1e-9 relative here)
+    sc = _small_design_scene(True)
+    sc.design = None
+    o = oracle_from_scene(sc)
+    J0 = gradient_replay(o, sc.n_steps, _objective)
+    g = o.pole_grad()
+    assert g.shape == (2, 3)
+    assert g[1, 0] == 0.0            # a Drude pole has no strength parameter
+    for p in range(2):
+        for t in range(3):
+            if sc.poles[p][0] == DRUDE and t == 0:
+                continue
+            base = list(sc.poles[p])
+            val = base[1 + t]
+            h = 1e-5 * max(abs(val), 1e-2)
+
+            def J_h(step):
+                q = list(sc.poles)
+                b = list(base)
+                b[1 + t] = val + step
+                q[p] = tuple(b)
+                return _J_poles(sc, q)
+
+            fd = (J_h(h) - J_h(-h)) / (2 * h)
+            assert abs(fd - g[p, t]) <= 1e-7 * abs(g[p, t]), (p, t, fd, g[p, t])
+    # the Taylor remainder of the first-order model in omega_dt of the Lorentz pole is quadratic
+    w = sc.poles[0][2]
+
+    def J_w(step):
+        q = list(sc.poles)
+        q[0] = (q[0][0], q[0][1], w + step, q[0][3])
+        return _J_poles(sc, q)
+
+    r1 = abs(J_w(1e-3) - J0 - 1e-3 * g[0, 1])
+    r2 = abs(J_w(5e-4) - J0 - 5e-4 * g[0, 1])
+    assert 3.6 < r1 / r2 < 4.4, (r1, r2)
+
+
 def test_replay_segments_bitwise_equal_store_all():
     sc = _small_design_scene(True, n=14, steps=30)
     grads = []
