@@ -451,7 +451,7 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0,
                     help="n: run only a short n^3 FP32 forward (ncu captures on a case larger than L2)")
     ap.add_argument("--workload", default="cpml128",
-                    choices=["cpml128", "pec32", "batched", "adjoint256", "large640", "reversible256", "streamed"],
+                    choices=["cpml128", "pec32", "batched", "adjoint256", "large640", "reversible256", "streamed", "poles"],
                     help="cpml128 is the benchmark line; the others measure the remaining workloads")
     ap.add_argument("--fd-cells", type=int, default=20)
     ap.add_argument("--stream-n", type=int, default=768, help="--workload streamed: grid edge")
@@ -472,7 +472,7 @@ def main():
     elif args.workload != "cpml128" and args.impl == "ours":
         {"pec32": measure_pec32, "batched": measure_batched, "adjoint256": measure_adjoint256,
          "large640": measure_large640, "reversible256": measure_reversible256,
-         "streamed": measure_streamed}[args.workload](args)
+         "streamed": measure_streamed, "poles": measure_poles}[args.workload](args)
     elif args.impl == "reference":
         run_reference(args)
     else:
@@ -821,6 +821,80 @@ def measure_streamed(args):
         ctx.close()
     res["streamed_over_resident_time"] = round(res["resident_gcell_steps_s"] / res["streamed_gcell_steps_s"], 3)
     res["bitwise_equal_fields_and_spectra"] = all(torch.equal(a, b) for a, b in zip(out["streamed"], out["resident"]))
+    print(json.dumps(res))
+
+
+def measure_poles(args):
+    """Pole-parameter gradients (Sec. 3.1) on the anisotropic two-pole workload: the checkpointed
+    FP32 gradient at n^3 (1000 steps, 16 slots) with and without the pole cotangents, and on a 64^3
+    replica the FP32 / FP64 adjoint d J / d(omega_dt, gamma_dt) against FP64 central differences
+    of J through the GPU forward."""
+    import numpy as np
+    import torch
+    from paper_2609_30039_gb300 import adjoint as ADJ
+    from paper_2609_30039_gb300 import build as B
+    from paper_2609_30039_gb300 import fdtd
+    from paper_2609_30039_gb300 import workloads as W
+    B.build()
+
+    def loss(specs):
+        F = specs[0]
+        return float((F.abs() ** 2).sum()), [torch.view_as_real(2.0 * F).contiguous()]
+
+    _warm_loss(loss, torch.device("cuda"))
+    n = args.profile_case or 256
+    sc = W.large_adjoint(n=n, n_steps=1000)
+    res = {"workload": f"large_adjoint_{n}^3 (two Lorentz poles in a {sc.design[1][0] - sc.design[0][0]}^2 x "
+                       f"{sc.design[1][2] - sc.design[0][2]} layer), 1000 steps, FP32, 16 slots"}
+    for on in (False, True):
+        ctx = fdtd.Context([sc], dtype="f32")
+        adj = ADJ.DesignAdjoint(ctx, slots=16, pole_grads=on)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        adj.run(sc.n_steps, loss)
+        torch.cuda.synchronize()
+        res["gradient_seconds_" + ("with_pole_grads" if on else "eps_only")] = round(time.perf_counter() - t0, 3)
+        if on:
+            res["pole_grads"] = adj.pole_grads[0].tolist()
+        ctx.close()
+    # central differences on a small replica
+    small = W.large_adjoint(n=64, d=8, n_steps=400, layer=((12, 12, 26), (52, 52, 32)))
+    small.design = None
+
+    def J_of(poles):
+        s2 = W.Scene(**{**small.__dict__, "poles": tuple(poles)})
+        c = fdtd.Context([s2], dtype="f64")
+        c.step(s2.n_steps)
+        F = c.dft(0)
+        J = float((F.abs() ** 2).sum())
+        c.close()
+        return J
+
+    adj_pg = {}
+    for dt in ("f32", "f64"):
+        ctx = fdtd.Context([small], dtype=dt)
+        adj = ADJ.DesignAdjoint(ctx, slots=16, pole_grads=True)
+        adj.run(small.n_steps, loss)
+        adj_pg[dt] = adj.pole_grads[0]
+        ctx.close()
+    fd = {}
+    for p, t in ((0, 1), (1, 2), (0, 0)):
+        base = list(small.poles[p])
+        val = base[1 + t]
+        h = 1e-5 * abs(val)
+        Js = []
+        for sgn in (1, -1):
+            q = list(small.poles)
+            b = list(base)
+            b[1 + t] = val + sgn * h
+            q[p] = tuple(b)
+            Js.append(J_of(q))
+        d = (Js[0] - Js[1]) / (2 * h)
+        name = f"pole{p}_{('deps', 'omega_dt', 'gamma_dt')[t]}"
+        fd[name] = {"central_difference_fp64": d,
+                    "adjoint_fp64_rel_err": abs(adj_pg["f64"][p, t] - d) / abs(d),
+                    "adjoint_fp32_rel_err": abs(adj_pg["f32"][p, t] - d) / abs(d)}
+    res["fd_check_64^3_400_steps"] = fd
     print(json.dumps(res))
 
 

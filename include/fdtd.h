@@ -293,6 +293,19 @@ fdtd_status fdtd_snapshots_free(fdtd_ctx* ctx);
 fdtd_status fdtd_set_design(fdtd_ctx* ctx, int32_t domain, const int32_t lo[3], const int32_t hi[3],
                             double* grad_device);
 
+/* Pole-parameter gradients (Sec. 3.1: Drude and Lorentz pole parameters differentiate through the
+ * transposed dispersion update).  enabled != 0: every later transposed step sums, over the domain's
+ * dispersive cells and E components, the cotangents of each pole's trapezoidal coefficients
+ * (M00, M01, M10, M11, g0, g1; FP64 device accumulator owned by the context, zeroed here and by
+ * fdtd_adjoint_begin).  Needs poles and a pole-state box outside the CPML slabs (FDTD_EINVAL).
+ * enabled = 0 stops collecting. */
+fdtd_status fdtd_set_pole_grad(fdtd_ctx* ctx, int32_t domain, int32_t enabled);
+/* d J / d(delta_eps, omega_dt, gamma_dt) of each pole of the domain, host_out[3 p + 0..2]
+ * (n_poles * 3 doubles; a Drude pole's delta_eps entry is 0), from the coefficient cotangents
+ * collected since fdtd_adjoint_begin and the exact derivatives of the coefficients' closed form.
+ * Synchronises the stream.  FDTD_EINVAL if the domain does not collect them. */
+fdtd_status fdtd_pole_grad(fdtd_ctx* ctx, int32_t domain, double* host_out);
+
 /* Adjoint source of a monitor: cot_device (borrowed, complex FP64 interleaved, the monitor's
  * layout) holds dJ/dRe F + i dJ/dIm F.  The adjoint injects dJ/df(t) = Re(conj(cot) exp(i w t))
  * at the monitor cells.  NULL clears it. */

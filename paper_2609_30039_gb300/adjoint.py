@@ -134,11 +134,21 @@ class DesignAdjoint:
     """Gradient of a real objective of the monitor spectra w.r.t. eps^-1 in each domain's design
     box, by one forward sweep and one checkpointed transposed sweep on the GPU."""
 
-    def __init__(self, ctx: "F.Context", slots: int = 32, codec: int = F.FDTD_CODEC_NATIVE):
+    def __init__(self, ctx: "F.Context", slots: int = 32, codec: int = F.FDTD_CODEC_NATIVE,
+                 pole_grads: bool = False):
+        """pole_grads: also collect d J / d(delta_eps, omega_dt, gamma_dt) of the poles of every
+        dispersive domain (read from self.pole_grads after run)."""
         self.ctx = ctx
         self.slots = slots
         self.codec = codec
         torch = ctx.torch
+        self.pole_domains = []
+        if pole_grads:
+            for d, sc in enumerate(ctx.scenes):
+                if sc.pole_mask is not None and len(sc.poles):
+                    F.fdtd_set_pole_grad(ctx.ctx, d, 1)
+                    self.pole_domains.append(d)
+        self.pole_grads = {}
         self.grads = []
         for d, sc in enumerate(ctx.scenes):
             if sc.design is None:
@@ -169,6 +179,7 @@ class DesignAdjoint:
 
         out = run_schedule(ctx, acts, objective, self.codec)
         ctx.synchronize()
+        self.pole_grads = {d: F.fdtd_pole_grad(ctx.ctx, d, len(ctx.scenes[d].poles)) for d in self.pole_domains}
         return out, self.grads, replay_stats(acts)
 
 

@@ -49,6 +49,8 @@ struct DomainHost {
     std::vector<int> mons;
     std::vector<int> srcs;
     int per[3] = {0, 0, 0};        // periodic axes (x, y)
+    double* pgc = nullptr;         // pole-coefficient cotangents [npole][6] (device, owned)
+    int pgc_on = 0;                // collected by the transposed steps
     const void* tmaps = nullptr;   // this domain's kTmaMaps tensor maps in device memory
     int tma = 0;                   // maps encoded for the current field and eps^-1 pointers
 };
@@ -283,6 +285,36 @@ void pole_coef(const fdtd_pole& p, double M[4], double g[2]) {
     g[1] = b1 / (2.0 * det);
 }
 
+// Derivatives of the pole coefficients (M00, M01, M10, M11, g0, g1) of pole_coef with respect to
+// parameter `wrt` (0 delta_eps, 1 omega_dt, 2 gamma_dt): the same closed form evaluated on dual
+// numbers (value, derivative).
+struct Dual {
+    double v, d;
+};
+inline Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+inline Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+inline Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+inline Dual operator/(Dual a, Dual b) { return {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)}; }
+inline Dual cst(double x) { return {x, 0.0}; }
+
+void pole_coef_deriv(const fdtd_pole& p, int wrt, double dc[6]) {
+    const Dual de = {p.delta_eps, wrt == 0 ? 1.0 : 0.0};
+    const Dual w = {p.omega_dt, wrt == 1 ? 1.0 : 0.0};
+    const Dual gm = {p.gamma_dt, wrt == 2 ? 1.0 : 0.0};
+    const bool lor = p.kind == FDTD_LORENTZ;
+    const Dual w2 = w * w;
+    const Dual a0 = lor ? w2 : cst(0.0);
+    const Dual b1 = lor ? de * w2 : w2;
+    const Dual det = cst(1.0) + cst(0.5) * gm + cst(0.25) * a0;
+    const Dual c[6] = {(cst(1.0) + cst(0.5) * gm - cst(0.25) * a0) / det,
+                       cst(1.0) / det,
+                       (cst(0.0) - a0) / det,
+                       (cst(1.0) - cst(0.5) * gm - cst(0.25) * a0) / det,
+                       b1 / (cst(4.0) * det),
+                       b1 / (cst(2.0) * det)};
+    for (int q = 0; q < 6; ++q) dc[q] = c[q].d;
+}
+
 long long part_size(const DomainHost& d, int part) {
     if (part < 6) return d.ncell;
     if (part < 18) {
@@ -351,6 +383,7 @@ void fill_dom(const fdtd_ctx* c, const DomainHost& h, Dom<T>& d) {
             d.apsiH[a][s] = (T*)h.apsiH[a][s];
         }
     d.mask = h.mask;
+    d.pgc = h.pgc_on ? h.pgc : nullptr;
     d.bcell = h.bcell;
     d.ade = (T*)h.ade;
     d.aade = (T*)h.aade;
@@ -1290,6 +1323,8 @@ template <typename T>
 void adj_once(fdtd_ctx* c, int m) {
     const Launch l = L(c);
     const Dom<T>* dd = (const Dom<T>*)c->d_doms;
+    int pgrad = 0;   // some domain collects pole-coefficient cotangents
+    for (const auto& h : c->doms) pgrad |= h.pgc_on;
     const int ng = (int)c->tiles_gen.size(), ni = (int)c->tiles_int.size();
     // as in step_once: the interior launches run on the auxiliary stream next to the general ones
     const bool fork = c->aux_stream && !c->prof_on && ng > 0 && ni > 0;
@@ -1307,11 +1342,11 @@ void adj_once(fdtd_ctx* c, int m) {
     fork_here();
     {
         Prof p(c, FDTD_KERNEL_ADJ_E);
-        launch_adj_e<T>(la, dd, c->d_mons, c->d_tiles_int, ni, (T)c->S, m, c->adj_pending, 0, c->aniso);
+        launch_adj_e<T>(la, dd, c->d_mons, c->d_tiles_int, ni, (T)c->S, m, c->adj_pending, 0, c->aniso, 0);
     }
     {
         Prof p(c, FDTD_KERNEL_ADJ_E);
-        launch_adj_e<T>(l, dd, c->d_mons, c->d_tiles_gen, ng, (T)c->S, m, c->adj_pending, 1, 1);
+        launch_adj_e<T>(l, dd, c->d_mons, c->d_tiles_gen, ng, (T)c->S, m, c->adj_pending, 1, 1, pgrad);
     }
     join_here();
     fork_here();
@@ -2388,6 +2423,48 @@ fdtd_status fdtd_set_design(fdtd_ctx* ctx, int32_t domain, const int32_t lo[3], 
     return sync_doms(ctx);
 }
 
+fdtd_status fdtd_set_pole_grad(fdtd_ctx* ctx, int32_t domain, int32_t enabled) {
+    GUARD(ctx);
+    NOT_STREAMED(ctx);
+    if (!valid_dom(ctx, domain)) return fail(ctx, FDTD_EINVAL, "bad domain");
+    DomainHost& d = ctx->doms[domain];
+    if (!enabled) {
+        d.pgc_on = 0;
+        return sync_doms(ctx);
+    }
+    if (d.npole == 0 || d.bcell == 0) return fail(ctx, FDTD_EINVAL, "the domain has no dispersive cell");
+    for (int q = 0; q < 3; ++q)
+        if (d.blo[q] < d.dlo[q] || d.bhi[q] > d.n[q] - d.dhi[q])
+            return fail(ctx, FDTD_EINVAL, "pole-parameter gradients need the pole-state box outside the CPML slabs");
+    if (!d.pgc) {
+        fdtd_status st = dmalloc(ctx, (void**)&d.pgc, sizeof(double) * 6 * kMaxPole);
+        if (st != FDTD_OK) return st;
+    }
+    CK(ctx, cudaMemsetAsync(d.pgc, 0, sizeof(double) * 6 * kMaxPole, ctx->stream));
+    d.pgc_on = 1;
+    return sync_doms(ctx);
+}
+
+fdtd_status fdtd_pole_grad(fdtd_ctx* ctx, int32_t domain, double* host_out) {
+    GUARD(ctx);
+    NOT_STREAMED(ctx);
+    if (!valid_dom(ctx, domain) || !host_out) return fail(ctx, FDTD_EINVAL, "bad arguments");
+    const DomainHost& d = ctx->doms[domain];
+    if (!d.pgc_on) return fail(ctx, FDTD_EINVAL, "pole-parameter gradients are not collected for this domain");
+    double pgc[6 * kMaxPole];
+    CK(ctx, cudaMemcpyAsync(pgc, d.pgc, sizeof(pgc), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int p = 0; p < d.npole; ++p)
+        for (int t = 0; t < 3; ++t) {
+            double dc[6];
+            pole_coef_deriv(d.poles[p], t, dc);
+            double acc = 0.0;
+            for (int q = 0; q < 6; ++q) acc += pgc[6 * p + q] * dc[q];
+            host_out[3 * p + t] = acc;
+        }
+    return FDTD_OK;
+}
+
 fdtd_status fdtd_set_adjoint_source(fdtd_ctx* ctx, int32_t monitor_id, const void* cot) {
     GUARD(ctx);
     NOT_STREAMED(ctx);
@@ -2405,6 +2482,8 @@ fdtd_status fdtd_adjoint_begin(fdtd_ctx* ctx) {
             const long long n = part_size(d, p);
             if (ptr && n) CK(ctx, cudaMemsetAsync(ptr, 0, (size_t)n * ctx->esz, ctx->stream));
         }
+    for (auto& d : ctx->doms)
+        if (d.pgc_on) CK(ctx, cudaMemsetAsync(d.pgc, 0, sizeof(double) * 6 * kMaxPole, ctx->stream));
     ctx->adj_step = ctx->step;
     ctx->adj_pending = 0;
     if (ctx->step >= 1 && ctx->nentries[1] > 0) {

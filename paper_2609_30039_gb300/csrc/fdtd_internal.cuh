@@ -65,6 +65,7 @@ struct Dom {
     int design;                // 1 if a design box is set
     int glo[3], ghi[3];
     double* grad;              // [3][design cells]
+    double* pgc;               // pole-coefficient cotangents [npole][6] or nullptr (not collected)
     int nmon;                  // monitors of this domain
     int mon[kMaxMonPerDom];
     int nsrc;                  // soft sources of this domain
@@ -282,7 +283,8 @@ cudaError_t launch_steps(const Launch& L, const Dom<T>* doms, const Tile* tiles,
 // Adjoint kernels (kernels_adj.cu)
 template <typename T>
 void launch_adj_e(const Launch& L, const Dom<T>* doms, const Mon* mons, const Tile* tiles, int ntiles, T S, int m,
-                  int pending, int general, int aniso);
+                  int pending, int general, int aniso,
+                  int pole_grad);
 template <typename T>
 void launch_adj_h(const Launch& L, const Dom<T>* doms, const Mon* mons, const Tile* tiles, int ntiles, T S, int m,
                   int general);

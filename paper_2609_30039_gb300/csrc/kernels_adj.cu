@@ -132,10 +132,11 @@ __device__ __forceinline__ long long off_z(const Dom<T>& d, int s, int i, int j)
 }
 
 // Transposed E step of column (i, j) over planes [z0, z1) in general form (CPML, PEC, poles,
-// periodic wrap); `flags` tells whether monitor injection can apply.
+// periodic wrap); `flags` tells whether monitor injection can apply.  pacc (or nullptr): this
+// thread's sums of the pole-coefficient cotangents [pole][M00, M01, M10, M11, g0, g1].
 template <typename T>
 __device__ __forceinline__ void adj_e_column(const Dom<T>& d, const Mon* __restrict__ mons, int i, int j, int z0,
-                                             int z1, int flags, T S, int m, int pending) {
+                                             int z1, int flags, T S, int m, int pending, double* pacc) {
     const int nx = d.n[0], ny = d.n[1];
     const long long nxy = (long long)nx * ny;
     T* A0 = d.A[0];
@@ -248,29 +249,59 @@ __device__ __forceinline__ void adj_e_column(const Dom<T>& d, const Mon* __restr
                 }
                 gdisp = d.G;
             }
-            if (gcell) {
+            const bool pcell = pacc && dcell;
+            if (gcell || pcell) {
                 const int b = (a + 1) % 3, q = (a + 2) % 3;
                 // -1 neighbours along b and q (this component is not PEC-held, so they exist,
-                // wrapping on a periodic axis)
+                // wrapping on a periodic axis); the cell lies outside the CPML slabs, so the
+                // forward update used the plain curl
                 const long long om[3] = {oxm, oym, -nxy};
                 const T* Hq = d.F[3 + q];
                 const T* Hb = d.F[3 + b];
                 const T curl = (Hq[id] - Hq[id + om[b]]) - (Hb[id] - Hb[id + om[q]]);
                 double delta = (double)(S * curl);
+                const T e0 = d.F[a][id];
+                const long long bo = dcell ? ade_off(d, i, j, k) : 0;
                 if (dcell) {
-                    const long long bo = ade_off(d, i, j, k);
-                    const T e0 = d.F[a][id];
                     for (int p = 0; p < d.npole; ++p) {
                         const T P = d.ade[((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo];
                         const T Q = d.ade[((long long)(a * d.npole + p) * 2 + 1) * d.bcell + bo];
                         delta += (double)(P - (d.M00[p] * P + d.M01[p] * Q) - T(2) * d.g0[p] * e0);
                     }
                 }
+                // E^{m+1} = E^m + rho delta with rho = eps^-1 / (1 + eps^-1 G)
                 const double r = 1.0 / (1.0 + (double)ie * (double)gdisp);
-                const long long gi = ((long long)(k - d.glo[2]) * (d.ghi[1] - d.glo[1]) + (j - d.glo[1])) *
-                                         (d.ghi[0] - d.glo[0]) + (i - d.glo[0]);
-                const long long gn = (long long)(d.ghi[0] - d.glo[0]) * (d.ghi[1] - d.glo[1]) * (d.ghi[2] - d.glo[2]);
-                d.grad[a * gn + gi] += (double)et * delta * r * r;
+                if (gcell) {
+                    const long long gi = ((long long)(k - d.glo[2]) * (d.ghi[1] - d.glo[1]) + (j - d.glo[1])) *
+                                             (d.ghi[0] - d.glo[0]) + (i - d.glo[0]);
+                    const long long gn =
+                        (long long)(d.ghi[0] - d.glo[0]) * (d.ghi[1] - d.glo[1]) * (d.ghi[2] - d.glo[2]);
+                    d.grad[a * gn + gi] += (double)et * delta * r * r;
+                }
+                if (pcell) {
+                    // x_p^{m+1} = M_p x_p^m + g_p es with es = E^m + E^{m+1}; E^{m+1} depends on
+                    // M00, M01 (through delta) and on g0 (through delta and G): with et the total
+                    // cotangent of E^{m+1} and u = xbar_P - rho et,
+                    //   M00 += u P, M01 += u Q, M10 += xbar_Q P, M11 += xbar_Q Q,
+                    //   g0 += u es,  g1 += xbar_Q es
+                    const double rho = (double)ie * r;
+                    const double es = 2.0 * (double)e0 + rho * delta;
+                    const double etr = (double)et * rho;
+                    for (int p = 0; p < d.npole; ++p) {
+                        const long long o0 = ((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo;
+                        const long long o1 = o0 + d.bcell;
+                        const double P = (double)d.ade[o0], Q = (double)d.ade[o1];
+                        const double xq = (double)d.aade[o1];
+                        const double u = (double)d.aade[o0] - etr;
+                        double* pa = pacc + 6 * p;
+                        pa[0] += u * P;
+                        pa[1] += u * Q;
+                        pa[2] += xq * P;
+                        pa[3] += xq * Q;
+                        pa[4] += u * es;
+                        pa[5] += xq * es;
+                    }
+                }
             }
             fout[a] = S * ie / (T(1) + ie * gdisp) * et;
         }
@@ -282,15 +313,32 @@ __device__ __forceinline__ void adj_e_column(const Dom<T>& d, const Mon* __restr
     }
 }
 
-template <typename T>
+// kPG: also sums the pole-coefficient cotangents of domains that collect them (Sec. 3.1: pole
+// parameters through the transposed dispersion update): per thread over its column, then one
+// warp sum and one FP64 atomic per warp and coefficient into the domain's accumulator.
+template <typename T, bool kPG>
 __global__ void __launch_bounds__(kTileX* kTileY, sizeof(T) == 4 ? 3 : 2)
     k_adj_e_gen(const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, const Tile* __restrict__ tiles, T S,
                 int m, int pending) {
     const Tile t = tiles[blockIdx.x];
     int i, j;
     tile_coords(t, i, j);
-    if (i < 0 || j < 0) return;
-    adj_e_column(doms[t.dom], mons, i, j, t.z0, t.z1, t.flags, S, m, pending);
+    const Dom<T>& d = doms[t.dom];
+    if (!kPG) {
+        if (i < 0 || j < 0) return;
+        adj_e_column(d, mons, i, j, t.z0, t.z1, t.flags, S, m, pending, (double*)nullptr);
+        return;
+    }
+    // every lane of a warp reaches the shuffles below (the domain, hence np, is the block's)
+    const int np = d.pgc ? d.npole : 0;
+    double acc[kMaxPole * 6];
+    for (int q = 0; q < np * 6; ++q) acc[q] = 0.0;
+    if (i >= 0 && j >= 0) adj_e_column(d, mons, i, j, t.z0, t.z1, t.flags, S, m, pending, np ? acc : nullptr);
+    for (int q = 0; q < np * 6; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(d.pgc + q, v);
+    }
 }
 
 // Transposed H step of column (i, j) over planes [z0, z1) in general form.
@@ -581,11 +629,13 @@ __global__ void k_inject(const Dom<T>* __restrict__ doms, const Mon* __restrict_
 
 template <typename T>
 void launch_adj_e(const Launch& L, const Dom<T>* doms, const Mon* mons, const Tile* tiles, int ntiles, T S, int m,
-                  int pending, int general, int aniso) {
+                  int pending, int general, int aniso, int pole_grad) {
     if (ntiles <= 0) return;
     const dim3 b(kTileX, kTileY);
-    if (general)
-        k_adj_e_gen<T><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m, pending);
+    if (general && pole_grad)
+        k_adj_e_gen<T, true><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m, pending);
+    else if (general)
+        k_adj_e_gen<T, false><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m, pending);
     else if (aniso)
         k_adj_e_int<T, true><<<ntiles, b, 0, L.stream>>>(doms, mons, tiles, S, m, pending);
     else
@@ -624,7 +674,7 @@ void launch_inject(const Launch& L, const Dom<T>* doms, const Mon* mons, const i
 
 #define GBFDTD_INST(T)                                                                                          \
     template void launch_adj_e<T>(const Launch&, const Dom<T>*, const Mon*, const Tile*, int, T, int, int, int, \
-                                  int);                                                                         \
+                                  int, int);                                                                    \
     template void launch_adj_h<T>(const Launch&, const Dom<T>*, const Mon*, const Tile*, int, T, int, int);     \
     template void launch_adj_flush<T>(const Launch&, const Dom<T>*, const Tile*, int, T);                       \
     template void launch_inject<T>(const Launch&, const Dom<T>*, const Mon*, const int*, int, long long,        \

@@ -72,6 +72,8 @@ _SIGS = {
     "fdtd_create_streamed": [C.POINTER(fdtd_grid), C.POINTER(fdtd_cpml), C.POINTER(fdtd_material), C.c_int32,
                              C.c_int32, _vp, C.POINTER(_ctx)],
     "fdtd_destroy": [_ctx],
+    "fdtd_set_pole_grad": [_ctx, C.c_int32, C.c_int32],
+    "fdtd_pole_grad": [_ctx, C.c_int32, C.POINTER(C.c_double)],
     "fdtd_last_error": [_ctx],
     "fdtd_version": [],
     "fdtd_set_material": [_ctx, C.c_int32, C.POINTER(fdtd_material)],
@@ -181,6 +183,17 @@ def fdtd_create_streamed(grid, cpml, material, slab, halo, stream=0):
                                      _vp(stream), C.byref(out))
     _check(st, "fdtd_create_streamed", None)
     return out
+
+
+def fdtd_set_pole_grad(ctx, domain, enabled):
+    _check(load().fdtd_set_pole_grad(ctx, int(domain), int(bool(enabled))), "fdtd_set_pole_grad", ctx)
+
+
+def fdtd_pole_grad(ctx, domain, n_poles):
+    """d J / d(delta_eps, omega_dt, gamma_dt) of each pole of a domain, shape (n_poles, 3)."""
+    out = np.zeros(3 * max(int(n_poles), 1))
+    _check(load().fdtd_pole_grad(ctx, int(domain), out.ctypes.data_as(C.POINTER(C.c_double))), "fdtd_pole_grad", ctx)
+    return out[: 3 * int(n_poles)].reshape(int(n_poles), 3)
 
 
 def fdtd_destroy(ctx):
