@@ -817,6 +817,14 @@ def measure_streamed(args):
             ctx.step(steps)
         t = _timed(lambda: ctx.step(steps), ctx.stream)
         res[f"{kind}_gcell_steps_s"] = round(sc.cells * steps / t / 1e9, 2)
+        if kind == "streamed":
+            # host-link bytes of the timed batches: each window's six fields and eps^-1 in, each
+            # slab's six owned field planes out (the CPML memories add < 1%)
+            plane = n * n * 4
+            win = sum(min(n, z + slab + halo) - max(0, z - halo) for z in range(0, n, slab))
+            per_batch = win * plane * 7 + n * plane * 6
+            res["host_link_gb_s"] = round(per_batch * (steps // halo) / t / 1e9, 1)
+            res["halo_overhead"] = round(win / n, 3)
         out[kind] = [ctx.part(0, f) for f in range(6)] + [ctx.dft(0)]
         ctx.close()
     res["streamed_over_resident_time"] = round(res["resident_gcell_steps_s"] / res["streamed_gcell_steps_s"], 3)
