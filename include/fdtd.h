@@ -281,6 +281,20 @@ fdtd_status fdtd_set_step_count(fdtd_ctx* ctx, int64_t n);
  * s = 0 for an all-zero slab.  restore dequantises into the live state. */
 fdtd_status fdtd_state_save(fdtd_ctx* ctx, int32_t slot, int32_t codec);
 fdtd_status fdtd_state_restore(fdtd_ctx* ctx, int32_t slot);
+/* Native executor of a checkpoint-replay schedule (Sec. 3.2).  actions holds n_actions pairs
+ * (kind, arg): FDTD_ACT_SAVE (fdtd_state_save of slot arg with `codec`), FDTD_ACT_RESTORE (slot
+ * arg), FDTD_ACT_ADVANCE (arg forward steps), FDTD_ACT_ADJOINT (arg transposed steps),
+ * FDTD_ACT_STOP (return, so that the caller evaluates its objective, registers adjoint sources and
+ * calls fdtd_adjoint_begin before resuming after it).  *executed = actions consumed, the STOP
+ * included.  Stops at the first failing action and returns its status (*executed counts the
+ * actions before it).  Host memory: actions (read only). */
+#define FDTD_ACT_SAVE 0
+#define FDTD_ACT_RESTORE 1
+#define FDTD_ACT_ADVANCE 2
+#define FDTD_ACT_ADJOINT 3
+#define FDTD_ACT_STOP 4
+fdtd_status fdtd_run_schedule(fdtd_ctx* ctx, const int32_t* actions, int32_t n_actions, int32_t codec,
+                              int32_t* executed);
 /* Device bytes one snapshot of this context takes with a codec. */
 fdtd_status fdtd_snapshot_bytes(fdtd_ctx* ctx, int32_t codec, int64_t* bytes);
 /* Frees every snapshot slot. */

@@ -12,6 +12,7 @@ Only scheduling lives here; every forward and transposed step runs in libgbfdtd'
 from __future__ import annotations
 
 from math import comb
+import numpy as np
 from typing import Callable, Dict, List, Tuple
 
 from . import fdtd as F
@@ -100,27 +101,43 @@ def schedule(n: int, slots: int) -> List[Tuple]:
     return acts
 
 
-def run_schedule(ctx: "F.Context", acts, objective: Callable, codec: int = F.FDTD_CODEC_NATIVE):
-    """Executes a schedule on a Context whose forward state is u^0.  `objective(ctx)` is called
-    once the forward sweep reaches step n and must register adjoint sources and design
-    buffers; it returns what run_schedule returns."""
-    c = ctx.ctx
-    result = None
+def encode(acts) -> np.ndarray:
+    """The schedule as (kind, arg) int32 rows for the native executor (fdtd_run_schedule)."""
+    rows = []
     for a in acts:
         kind = a[0]
         if kind == "save":
-            F.fdtd_state_save(c, a[1], codec)
+            rows.append((F.FDTD_ACT_SAVE, a[1]))
         elif kind == "restore":
-            F.fdtd_state_restore(c, a[1])
+            rows.append((F.FDTD_ACT_RESTORE, a[1]))
         elif kind == "advance":
-            F.fdtd_step_forward(c, a[1])
+            rows.append((F.FDTD_ACT_ADVANCE, a[1]))
         elif kind == "adjoint":
-            F.fdtd_step_adjoint(c, 1)
+            rows.append((F.FDTD_ACT_ADJOINT, 1))
         elif kind == "forward_done":
-            result = objective(ctx)
-            F.fdtd_adjoint_begin(c)
-            F.fdtd_dft_enable(c, 0)
-    F.fdtd_dft_enable(c, 1)
+            rows.append((F.FDTD_ACT_STOP, 0))
+        else:
+            raise ValueError(f"unknown action {kind}")
+    return np.asarray(rows, dtype=np.int32).reshape(-1, 2)
+
+
+def run_schedule(ctx: "F.Context", acts, objective: Callable, codec: int = F.FDTD_CODEC_NATIVE):
+    """Executes a schedule on a Context whose forward state is u^0, in the library's native
+    executor (two calls: the forward sweep up to its end, then the reversal).  `objective(ctx)` is
+    called in between and must register adjoint sources and design buffers; it returns what
+    run_schedule returns."""
+    c = ctx.ctx
+    rows = encode(acts)
+    nxt = F.fdtd_run_schedule(c, rows, 0, codec)
+    result = None
+    if nxt > 0 and rows[nxt - 1, 0] == F.FDTD_ACT_STOP:
+        result = objective(ctx)
+        F.fdtd_adjoint_begin(c)
+        F.fdtd_dft_enable(c, 0)
+        try:
+            F.fdtd_run_schedule(c, rows, nxt, codec)
+        finally:
+            F.fdtd_dft_enable(c, 1)
     return result
 
 
@@ -273,13 +290,8 @@ class Runner:
         F.fdtd_reset(ctx.ctx)
         F.fdtd_dft_reset(ctx.ctx)
         self.acts = schedule(n_steps, self.slots)
-        cut = next(i for i, a in enumerate(self.acts) if a[0] == "forward_done")
-        for a in self.acts[:cut]:
-            if a[0] == "save":
-                F.fdtd_state_save(ctx.ctx, a[1], self.codec)
-            elif a[0] == "advance":
-                F.fdtd_step_forward(ctx.ctx, a[1])
-        self.cut = cut
+        self.rows = encode(self.acts)
+        self.cut = F.fdtd_run_schedule(ctx.ctx, self.rows, 0, self.codec)   # up to the STOP
         return [ctx.dft(k).clone() for k in range(len(ctx.monitors))]
 
     def backward(self, grad_specs):
@@ -294,15 +306,7 @@ class Runner:
         F.fdtd_adjoint_begin(ctx.ctx)
         F.fdtd_dft_enable(ctx.ctx, 0)
         try:
-            for a in self.acts[self.cut + 1:]:
-                if a[0] == "save":
-                    F.fdtd_state_save(ctx.ctx, a[1], self.codec)
-                elif a[0] == "restore":
-                    F.fdtd_state_restore(ctx.ctx, a[1])
-                elif a[0] == "advance":
-                    F.fdtd_step_forward(ctx.ctx, a[1])
-                elif a[0] == "adjoint":
-                    F.fdtd_step_adjoint(ctx.ctx, 1)
+            F.fdtd_run_schedule(ctx.ctx, self.rows, self.cut, self.codec)
         finally:
             F.fdtd_dft_enable(ctx.ctx, 1)
         ctx.synchronize()

@@ -2537,6 +2537,28 @@ fdtd_status fdtd_step_adjoint(fdtd_ctx* ctx, int32_t n_steps) {
     return FDTD_OK;
 }
 
+fdtd_status fdtd_run_schedule(fdtd_ctx* ctx, const int32_t* actions, int32_t n_actions, int32_t codec,
+                              int32_t* executed) {
+    GUARD(ctx);
+    if (!actions || n_actions < 0 || !executed) return fail(ctx, FDTD_EINVAL, "bad arguments");
+    *executed = 0;
+    for (int32_t i = 0; i < n_actions; ++i) {
+        const int32_t kind = actions[2 * i], arg = actions[2 * i + 1];
+        fdtd_status st;
+        switch (kind) {
+            case FDTD_ACT_SAVE: st = fdtd_state_save(ctx, arg, codec); break;
+            case FDTD_ACT_RESTORE: st = fdtd_state_restore(ctx, arg); break;
+            case FDTD_ACT_ADVANCE: st = fdtd_step_forward(ctx, arg); break;
+            case FDTD_ACT_ADJOINT: st = fdtd_step_adjoint(ctx, arg); break;
+            case FDTD_ACT_STOP: *executed = i + 1; return FDTD_OK;
+            default: return fail(ctx, FDTD_EINVAL, "unknown schedule action " + std::to_string(kind));
+        }
+        if (st != FDTD_OK) return st;
+        *executed = i + 1;
+    }
+    return FDTD_OK;
+}
+
 fdtd_status fdtd_adjoint_step_count(fdtd_ctx* ctx, int64_t* a) {
     GUARD(ctx);
     if (!a) return FDTD_EINVAL;

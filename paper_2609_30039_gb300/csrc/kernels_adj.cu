@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_int_blocks<T>()) k_adj_e_i
         ez += S * ((bx - bx_ym) - (by - by_xm));
         bxz = bx;
         byz = by;
-        if (d.nmon) {
+        if (d.nmon && (t.flags & kTileMonE)) {
             ex += (T)inject_at(d, mons, 0, i, j, k, (long long)m * 2 + 0);
             ey += (T)inject_at(d, mons, 1, i, j, k, (long long)m * 2 + 0);
             ez += (T)inject_at(d, mons, 2, i, j, k, (long long)m * 2 + 0);
@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_int_blocks<T>()) k_adj_h_i
         bx += (fz_yp - fz) - (fyn - fyk);
         by += (fxn - fxk) - (fz_xp - fz);
         bz += (fy_xp - fyk) - (fx_yp - fxk);
-        if (d.nmon && m >= 1) {
+        if (d.nmon && m >= 1 && (t.flags & kTileMonH)) {
             bx += (T)inject_at(d, mons, 3, i, j, k, (long long)(m - 1) * 2 + 1);
             by += (T)inject_at(d, mons, 4, i, j, k, (long long)(m - 1) * 2 + 1);
             bz += (T)inject_at(d, mons, 5, i, j, k, (long long)(m - 1) * 2 + 1);

@@ -72,6 +72,7 @@ _SIGS = {
     "fdtd_create_streamed": [C.POINTER(fdtd_grid), C.POINTER(fdtd_cpml), C.POINTER(fdtd_material), C.c_int32,
                              C.c_int32, _vp, C.POINTER(_ctx)],
     "fdtd_destroy": [_ctx],
+    "fdtd_run_schedule": [_ctx, C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.POINTER(C.c_int32)],
     "fdtd_set_pole_grad": [_ctx, C.c_int32, C.c_int32],
     "fdtd_pole_grad": [_ctx, C.c_int32, C.POINTER(C.c_double)],
     "fdtd_last_error": [_ctx],
@@ -194,6 +195,23 @@ def fdtd_pole_grad(ctx, domain, n_poles):
     out = np.zeros(3 * max(int(n_poles), 1))
     _check(load().fdtd_pole_grad(ctx, int(domain), out.ctypes.data_as(C.POINTER(C.c_double))), "fdtd_pole_grad", ctx)
     return out[: 3 * int(n_poles)].reshape(int(n_poles), 3)
+
+
+FDTD_ACT_SAVE, FDTD_ACT_RESTORE, FDTD_ACT_ADVANCE, FDTD_ACT_ADJOINT, FDTD_ACT_STOP = 0, 1, 2, 3, 4
+
+
+def fdtd_run_schedule(ctx, actions, start, codec):
+    """Runs the (kind, arg) int32 rows actions[start:] natively until a STOP or the end; returns
+    the index of the next action to run."""
+    a = np.ascontiguousarray(actions, dtype=np.int32).reshape(-1, 2)
+    n = a.shape[0] - int(start)
+    if n <= 0:
+        return int(start)
+    done = C.c_int32(0)
+    ptr = a[int(start):].ctypes.data_as(C.POINTER(C.c_int32))
+    st = load().fdtd_run_schedule(ctx, ptr, n, int(codec), C.byref(done))
+    _check(st, "fdtd_run_schedule", ctx)
+    return int(start) + done.value
 
 
 def fdtd_destroy(ctx):

@@ -47,3 +47,24 @@ def test_repetition_numbers_of_the_workloads():
 def test_spine_is_increasing():
     sp = spine(3000, 31)
     assert sp == sorted(sp) and len(set(sp)) == len(sp) and sp[-1] < 3000
+
+
+@pytest.mark.parametrize("n,slots", [(1, 1), (17, 3), (200, 8)])
+def test_encoded_schedule_rows(n, slots):
+    # the native executor's rows carry the same actions: one STOP after the forward sweep, one
+    # transposed step per adjoint action, slots and step counts unchanged
+    from paper_2609_30039_gb300 import fdtd as F
+    from paper_2609_30039_gb300.adjoint import encode
+    acts = schedule(n, slots)
+    rows = encode(acts)
+    assert rows.dtype.name == "int32" and rows.shape == (len(acts), 2)
+    kinds = {"save": F.FDTD_ACT_SAVE, "restore": F.FDTD_ACT_RESTORE, "advance": F.FDTD_ACT_ADVANCE,
+             "adjoint": F.FDTD_ACT_ADJOINT, "forward_done": F.FDTD_ACT_STOP}
+    for a, r in zip(acts, rows):
+        assert r[0] == kinds[a[0]]
+        if a[0] in ("save", "restore", "advance"):
+            assert r[1] == a[1]
+        if a[0] == "adjoint":
+            assert r[1] == 1
+    assert int((rows[:, 0] == F.FDTD_ACT_STOP).sum()) == 1
+    assert int((rows[:, 0] == F.FDTD_ACT_ADJOINT).sum()) == n

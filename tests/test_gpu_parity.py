@@ -316,6 +316,45 @@ def test_gradient_matches_oracle_fp64(dispersive, slots):
     assert stats["adjoint_steps"] == sc.n_steps
 
 
+def test_native_schedule_executor_matches_per_action_calls():
+    # the same schedule run action by action through the ABI and by fdtd_run_schedule: same bits
+    sc = _design_scene(True)
+    out = []
+    for native in (False, True):
+        ctx = fdtd.Context([sc], dtype="f32")
+        runner = ADJ.DesignAdjoint(ctx, slots=6, pole_grads=True)
+        if native:
+            (J, _), grads, _ = runner.run(sc.n_steps, _gpu_loss)
+        else:
+            c = ctx.ctx
+            for a in ADJ.schedule(sc.n_steps, 6):
+                if a[0] == "save":
+                    fdtd.fdtd_state_save(c, a[1], fdtd.FDTD_CODEC_NATIVE)
+                elif a[0] == "restore":
+                    fdtd.fdtd_state_restore(c, a[1])
+                elif a[0] == "advance":
+                    fdtd.fdtd_step_forward(c, a[1])
+                elif a[0] == "adjoint":
+                    fdtd.fdtd_step_adjoint(c, 1)
+                else:
+                    specs = [ctx.dft(k) for k in range(len(ctx.monitors))]
+                    J, cots = _gpu_loss(specs)
+                    keep = [ct.contiguous() for ct in cots]
+                    fdtd.fdtd_set_adjoint_source(c, ctx.monitors[0][0], keep[0].data_ptr())
+                    fdtd.fdtd_adjoint_begin(c)
+                    fdtd.fdtd_dft_enable(c, 0)
+            fdtd.fdtd_dft_enable(c, 1)
+            ctx.synchronize()
+            grads = runner.grads
+            runner.pole_grads = {0: fdtd.fdtd_pole_grad(c, 0, 2)}
+        out.append((J, grads[0].clone(), runner.pole_grads[0].copy()))
+        ctx.close()
+    assert out[0][0] == out[1][0]
+    assert torch.equal(out[0][1], out[1][1])
+    # the pole cotangents are FP64 atomic sums over warps, whose order varies between runs
+    assert np.max(np.abs(out[0][2] - out[1][2])) <= 1e-12 * np.max(np.abs(out[0][2]))
+
+
 def test_gradient_fp32_close_to_oracle():
     sc = _design_scene(False)
     o = oracle_from_scene(sc)
