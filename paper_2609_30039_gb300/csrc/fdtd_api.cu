@@ -132,6 +132,9 @@ struct fdtd_ctx {
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     long long graph_launches[2][2] = {{0, 0}, {0, 0}};
     int use_graphs = 1;
+    SnapSeg* d_snapsegs = nullptr;   // the state parts of a native snapshot (one copy launch)
+    int n_snapsegs = 0;
+    long long snap_max = 0;
     // host streaming (Sec. 4.2): the one domain's fields, CPML memories, pole state and materials
     // live in pinned host memory; each batch of up to sk steps runs z-slab by z-slab (sw owned
     // planes plus sk halo planes on each side) in a ring of three device workspaces
@@ -2297,6 +2300,30 @@ fdtd_status fdtd_snapshot_bytes(fdtd_ctx* ctx, int32_t codec, int64_t* bytes) {
     return FDTD_OK;
 }
 
+// Segment table of a native snapshot (built once: part arrays and sizes are fixed at create).
+static fdtd_status snap_segments(fdtd_ctx* ctx) {
+    if (ctx->d_snapsegs) return FDTD_OK;
+    std::vector<SnapSeg> segs;
+    long long off = 0;
+    for (const auto& d : ctx->doms)
+        for (int part = 0; part < part_count(d); ++part) {
+            const long long n = part_size(d, part);
+            if (n == 0) continue;
+            const long long b = n * (long long)ctx->esz;
+            segs.push_back({(char*)part_ptr(d, 0, part, ctx->esz), off, b});
+            ctx->snap_max = std::max(ctx->snap_max, b);
+            off += (b + 255) & ~255ll;
+        }
+    if (segs.size() > 65535) return fail(ctx, FDTD_EINVAL, "too many state parts for one snapshot launch");
+    if (segs.empty()) return FDTD_OK;
+    fdtd_status st = dmalloc(ctx, (void**)&ctx->d_snapsegs, sizeof(SnapSeg) * segs.size());
+    if (st != FDTD_OK) return st;
+    CK(ctx, cudaMemcpyAsync(ctx->d_snapsegs, segs.data(), sizeof(SnapSeg) * segs.size(), cudaMemcpyHostToDevice,
+                            ctx->stream));
+    ctx->n_snapsegs = (int)segs.size();
+    return FDTD_OK;
+}
+
 static fdtd_status save_slot(fdtd_ctx* ctx, int32_t slot, int32_t codec) {
     const size_t need = snapshot_bytes(ctx, codec);
     Slot& s = ctx->slots[slot];
@@ -2319,27 +2346,28 @@ static fdtd_status save_slot(fdtd_ctx* ctx, int32_t slot, int32_t codec) {
     s.step = ctx->step;
     char* p = (char*)s.buf;
     const Launch l = L(ctx);
+    if (codec == FDTD_CODEC_NATIVE) {
+        fdtd_status st = snap_segments(ctx);
+        if (st != FDTD_OK) return st;
+        launch_snapshot_copy(l, ctx->d_snapsegs, ctx->n_snapsegs, ctx->snap_max, s.buf, 1);
+        CKL(ctx);
+        return FDTD_OK;
+    }
     for (const auto& d : ctx->doms)
         for (int part = 0; part < part_count(d); ++part) {
             const long long n = part_size(d, part);
             if (n == 0) continue;
             const void* src = part_ptr(d, 0, part, ctx->esz);
-            size_t b;
-            if (codec == FDTD_CODEC_NATIVE) {
-                b = (size_t)n * ctx->esz;
-                CK(ctx, cudaMemcpyAsync(p, src, b, cudaMemcpyDeviceToDevice, ctx->stream));
-            } else {
-                const long long np = part_planes(d, part);
-                b = (size_t)n * 2 + (size_t)np * 4;
-                uint16_t* q = (uint16_t*)p;
-                float* sc = (float*)(p + (size_t)n * 2);
-                if (((uintptr_t)sc) & 3) return fail(ctx, FDTD_EINVAL, "internal alignment");
-                if (ctx->dtype == FDTD_F32)
-                    launch_bf16_encode<float>(l, (const float*)src, np, n / np, q, sc);
-                else
-                    launch_bf16_encode<double>(l, (const double*)src, np, n / np, q, sc);
-                CKL(ctx);
-            }
+            const long long np = part_planes(d, part);
+            const size_t b = (size_t)n * 2 + (size_t)np * 4;
+            uint16_t* q = (uint16_t*)p;
+            float* sc = (float*)(p + (size_t)n * 2);
+            if (((uintptr_t)sc) & 3) return fail(ctx, FDTD_EINVAL, "internal alignment");
+            if (ctx->dtype == FDTD_F32)
+                launch_bf16_encode<float>(l, (const float*)src, np, n / np, q, sc);
+            else
+                launch_bf16_encode<double>(l, (const double*)src, np, n / np, q, sc);
+            CKL(ctx);
             p += (b + 255) & ~(size_t)255;
         }
     return FDTD_OK;
@@ -2351,26 +2379,28 @@ static fdtd_status restore_slot(fdtd_ctx* ctx, int32_t slot) {
     const Slot& s = it->second;
     const char* p = (const char*)s.buf;
     const Launch l = L(ctx);
+    if (s.codec == FDTD_CODEC_NATIVE) {
+        fdtd_status st = snap_segments(ctx);
+        if (st != FDTD_OK) return st;
+        launch_snapshot_copy(l, ctx->d_snapsegs, ctx->n_snapsegs, ctx->snap_max, s.buf, 0);
+        CKL(ctx);
+        ctx->step = s.step;
+        return set_device_step(ctx, s.step);
+    }
     for (const auto& d : ctx->doms)
         for (int part = 0; part < part_count(d); ++part) {
             const long long n = part_size(d, part);
             if (n == 0) continue;
             void* dst = part_ptr(d, 0, part, ctx->esz);
-            size_t b;
-            if (s.codec == FDTD_CODEC_NATIVE) {
-                b = (size_t)n * ctx->esz;
-                CK(ctx, cudaMemcpyAsync(dst, p, b, cudaMemcpyDeviceToDevice, ctx->stream));
-            } else {
-                const long long np = part_planes(d, part);
-                b = (size_t)n * 2 + (size_t)np * 4;
-                const uint16_t* q = (const uint16_t*)p;
-                const float* sc = (const float*)(p + (size_t)n * 2);
-                if (ctx->dtype == FDTD_F32)
-                    launch_bf16_decode<float>(l, q, sc, np, n / np, (float*)dst);
-                else
-                    launch_bf16_decode<double>(l, q, sc, np, n / np, (double*)dst);
-                CKL(ctx);
-            }
+            const long long np = part_planes(d, part);
+            const size_t b = (size_t)n * 2 + (size_t)np * 4;
+            const uint16_t* q = (const uint16_t*)p;
+            const float* sc = (const float*)(p + (size_t)n * 2);
+            if (ctx->dtype == FDTD_F32)
+                launch_bf16_decode<float>(l, q, sc, np, n / np, (float*)dst);
+            else
+                launch_bf16_decode<double>(l, q, sc, np, n / np, (double*)dst);
+            CKL(ctx);
             p += (b + 255) & ~(size_t)255;
         }
     ctx->step = s.step;

@@ -302,6 +302,16 @@ void launch_admission(const Launch& L, const Dom<T>* d_dom, const Dom<T>& h_dom,
 void launch_mask_box(const Launch& L, const uint8_t* mask, int nx, int ny, int nz, int* d_box);
 template <typename T>
 void launch_nonfinite(const Launch& L, const T* p, long long n, unsigned long long* d_bad);
+// One state part of a native snapshot: the live array, its byte offset in the slot, its size.
+struct SnapSeg {
+    char* state;
+    long long off;
+    long long bytes;
+};
+// Copies every segment live -> slot (to_slot) or slot -> live in one launch (gridDim.y = nseg <=
+// 65535); max_bytes: the largest segment.
+void launch_snapshot_copy(const Launch& L, const SnapSeg* segs, int nseg, long long max_bytes, void* slot,
+                          int to_slot);
 template <typename T>
 void launch_bf16_encode(const Launch& L, const T* src, long long nplanes, long long plane, uint16_t* dst,
                         float* scales);

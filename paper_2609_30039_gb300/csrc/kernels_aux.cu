@@ -184,6 +184,42 @@ void launch_bf16_decode(const Launch& L, const uint16_t* src, const float* scale
     ++*L.counter;
 }
 
+// ---- native snapshots ----------------------------------------------------------------------
+// One launch moves every state part between the live arrays and a snapshot slot: block row y
+// copies segment y, grid-stride along x.  Slot offsets are 256-byte aligned; a part array starts
+// on a 256-byte boundary (fields, CPML memories) or at least on its element size (pole-state parts
+// inside one allocation), and its size is a whole number of elements of >= 4 bytes.  16-byte
+// vectors where both ends are 16-byte aligned (the last bytes % 16 bytes by lanes of block x = 0),
+// 4-byte words otherwise.
+__global__ void k_snapshot_copy(const SnapSeg* __restrict__ segs, char* __restrict__ slot, int to_slot) {
+    const SnapSeg sg = segs[blockIdx.y];
+    const char* src = to_slot ? sg.state : slot + sg.off;
+    char* dst = to_slot ? slot + sg.off : sg.state;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, dt = (long long)gridDim.x * blockDim.x;
+    if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+        const long long nv = sg.bytes >> 4;
+        const int4* s4 = reinterpret_cast<const int4*>(src);
+        int4* d4 = reinterpret_cast<int4*>(dst);
+        for (long long v = t0; v < nv; v += dt) d4[v] = s4[v];
+        const int tail = (int)(sg.bytes & 15);
+        if (blockIdx.x == 0 && (int)threadIdx.x < tail) dst[(nv << 4) + threadIdx.x] = src[(nv << 4) + threadIdx.x];
+    } else {
+        const long long nw = sg.bytes >> 2;
+        const unsigned* s1 = reinterpret_cast<const unsigned*>(src);
+        unsigned* d1 = reinterpret_cast<unsigned*>(dst);
+        for (long long v = t0; v < nw; v += dt) d1[v] = s1[v];
+    }
+}
+
+void launch_snapshot_copy(const Launch& L, const SnapSeg* segs, int nseg, long long max_bytes, void* slot,
+                          int to_slot) {
+    if (nseg <= 0) return;
+    long long bx = ((max_bytes >> 4) + 256 * 8 - 1) / (256 * 8);   // <= 8 vectors per thread
+    bx = bx < 1 ? 1 : (bx > 1024 ? 1024 : bx);
+    k_snapshot_copy<<<dim3((unsigned)bx, (unsigned)nseg), 256, 0, L.stream>>>(segs, (char*)slot, to_slot);
+    ++*L.counter;
+}
+
 #define GBFDTD_INST(T)                                                                                     \
     template void launch_admission<T>(const Launch&, const Dom<T>*, const Dom<T>&, unsigned long long*);   \
     template void launch_nonfinite<T>(const Launch&, const T*, long long, unsigned long long*);             \
