@@ -519,3 +519,97 @@ def test_backward_steps_refuse_lossy_domains():
     o.step(2)
     with pytest.raises(ValueError):
         o.step_backward(1)
+
+
+# ---- dispersive slabs at normal incidence: second-order convergence (Sec. 5.1) -----------------
+def _golden_dispersive():
+    import os
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "dispersive_slab_convergence.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                mat, mesh, err = line.split()
+                rows[(mat, int(mesh))] = float(err)
+    return rows
+
+
+def _slab_reference(eps, k0d):
+    """Airy closed form of a homogeneous slab of permittivity eps (time factor exp(-i w t)) and
+    optical thickness k0 d in vacuum: R = |r|^2, T = |t|^2."""
+    n = np.sqrt(eps + 0j)
+    n = np.where(n.imag < 0, -n, n)
+    r12 = (1 - n) / (1 + n)
+    ph = np.exp(2j * n * k0d)
+    r = r12 * (1 - ph) / (1 - r12 ** 2 * ph)
+    t = (1 - r12 ** 2) * np.exp(1j * n * k0d) / (1 - r12 ** 2 * ph)
+    return np.abs(r) ** 2, np.abs(t) ** 2
+
+
+def _eps_continuum(w, einf, poles):
+    e = einf + 0j
+    for kind, de, w0, g in poles:
+        e += -w0 ** 2 / (w ** 2 + 1j * g * w) if kind == DRUDE else de * w0 ** 2 / (w0 ** 2 - w ** 2 - 1j * g * w)
+    return e
+
+
+def _dispersive_slab_error(h, einf, poles, d_um, lams, t_um=70.0):
+    """Largest |error| of R, T, A of the oracle's slab (lengths in um, c = 1, mesh h, dt = S h):
+    a 2 x 2 periodic cell, CPML on both z faces, an Ex sheet, flux planes before and after the
+    slab, each normalised by the same cell without the slab."""
+    from oracle.flux import plane_flux_z
+    S = W.COURANT
+    dt = S * h
+    d = 16
+    zs = d + 5
+    zr = zs + int(round(0.4 / h))
+    z1 = zs + int(round(1.5 / h))
+    L = int(round(d_um / h))
+    zt = z1 + L + int(round(0.4 / h))
+    nz = zt + 2 + int(round(1.0 / h)) + d
+    n_steps = int(round(t_um / dt))
+    om = 2 * np.pi * dt / lams                     # rad per step
+    step_poles = tuple((k, de, w0 * dt, g * dt) for k, de, w0, g in poles)
+    flux = []
+    for with_slab in (False, True):
+        o = Oracle((2, 2, nz), S, periodic=(1, 1, 0), cpml=(0, 0, 0, 0, d, d), m=3.0, kappa_max=1.0,
+                   alpha_max=0.0)
+        ie = np.ones((nz, 2, 2))
+        mask = np.zeros((nz, 2, 2), dtype=np.uint8)
+        if with_slab:
+            ie[z1:z1 + L] = 1.0 / einf
+            mask[z1:z1 + L] = 1
+        o.set_material([ie, ie, ie], poles=step_poles, mask=mask)
+        o.add_source(0, (0, 0, zs), (2, 2, zs + 1),
+                     W.gaussian_pulse(n_steps, wavelength=1.55 / h, periods=0.6, delay=4.0))
+        o.add_dft_box((0, 0, zr), (2, 2, zr + 2), (0, 1, 3, 4), om)
+        o.add_dft_box((0, 0, zt), (2, 2, zt + 2), (0, 1, 3, 4), om)
+        o.step(n_steps)
+        flux.append((plane_flux_z(o.dft(0), (0, 1, 3, 4)), plane_flux_z(o.dft(1), (0, 1, 3, 4))))
+    T = flux[1][1] / flux[0][1]
+    R = 1.0 - flux[1][0] / flux[0][0]
+    w = 2 * np.pi / lams
+    Re, Te = _slab_reference(_eps_continuum(w, einf, poles), w * d_um)
+    return max(np.max(np.abs(R - Re)), np.max(np.abs(T - Te)), np.max(np.abs((1 - R - T) - (1 - Re - Te))))
+
+
+@pytest.mark.parametrize("material", ["drude", "lorentz"])
+def test_dispersive_slab_converges_at_second_order_like_the_paper(material):
+    # the trapezoidal ADE, the CPML and the flux planes against the continuum transfer matrix of
+    # the poles' permittivity: halving the mesh lowers the largest R / T / A error by the factor
+    # the paper prints (about four), at errors of the printed order.  Slabs of the printed
+    # thicknesses; pole parameters (per um of c t) chosen here, since the paper prints none:
+    # Drude eps_inf 1, lambda_p 0.9 um, gamma 2 pi 0.05; two Lorentz poles on eps_inf 1.5,
+    # (deps 1.0, lambda_0 1.2 um, gamma 2 pi 0.06) and (0.5, 2.5 um, 2 pi 0.08).
+    golden = _golden_dispersive()
+    lams = np.linspace(1.3, 1.8, 21)
+    if material == "drude":
+        einf, poles, d_um = 1.0, ((DRUDE, 0.0, 2 * np.pi / 0.9, 2 * np.pi * 0.05),), 0.1
+    else:
+        einf, d_um = 1.5, 0.5
+        poles = ((LORENTZ, 1.0, 2 * np.pi / 1.2, 2 * np.pi * 0.06), (LORENTZ, 0.5, 2 * np.pi / 2.5, 2 * np.pi * 0.08))
+    e20 = _dispersive_slab_error(0.02, einf, poles, d_um, lams)
+    e10 = _dispersive_slab_error(0.01, einf, poles, d_um, lams)
+    paper_ratio = golden[(material, 20)] / golden[(material, 10)]
+    assert 0.8 * paper_ratio < e20 / e10 < 1.25 * paper_ratio, (e20, e10, paper_ratio)
+    for mesh, e in ((20, e20), (10, e10)):
+        assert e < 5.0 * golden[(material, mesh)], (mesh, e)
