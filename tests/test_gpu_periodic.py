@@ -124,3 +124,41 @@ def test_flux_rejects_monitors_it_cannot_use():
     with pytest.raises(fdtd.FdtdError) as e:
         fdtd.fdtd_dft_flux(ctx.ctx, ctx.monitors[1][0], 3)   # one plane thick
     assert e.value.status == fdtd.FDTD_EINVAL
+
+
+def test_fp32_slab_error_against_the_continuum_formula_is_the_printed_one():
+    # Sec. 5.1: the 8-cell slab of index 1.5 on a 25 nm mesh; the CUDA path's FP32 flux spectra
+    # deviate from Eq. (slab) by the discrete response the paper prints (tests/golden)
+    import os
+    golden = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "slab_transmission_errors.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                golden[k] = float(v)
+    S, n_idx, L, h = W.COURANT, 1.5, 8, 0.025
+    lams = np.linspace(1.3, 1.8, 31)
+    om = 2 * np.pi * S * h / lams
+    T_cont = 1.0 / (1.0 + ((n_idx ** 2 - 1) / (2 * n_idx)) ** 2 * np.sin(2 * np.pi * n_idx * 0.2 / lams) ** 2)
+    nz, zs, zr, z1, zt, steps = 300, 26, 70, 140, 200, 5000
+    flux = []
+    for slab in (False, True):
+        inv = np.ones((nz, 2, 2))
+        if slab:
+            inv[z1:z1 + L] = 1.0 / n_idx ** 2
+        src = W.Source(W.EX, (0, 0, zs), (2, 2, zs + 1),
+                       W.gaussian_pulse(steps, wavelength=1.55 / h, periods=0.6, delay=4.0))
+        mons = [W.Monitor((0, 0, zr), (2, 2, zr + 2), (W.EX, W.EY, W.HX, W.HY), om),
+                W.Monitor((0, 0, zt), (2, 2, zt + 2), (W.EX, W.EY, W.HX, W.HY), om)]
+        sc = W.Scene(shape=(2, 2, nz), n_steps=steps, cpml=(0, 0, 0, 0, 16, 16), kappa_max=1.0, alpha_max=0.0,
+                     inv_eps=[inv], sources=[src], monitors=mons, periodic=(1, 1, 0))
+        ctx = fdtd.Context([sc], dtype="f32")
+        ctx.step(steps)
+        flux.append([fdtd.fdtd_dft_flux(ctx.ctx, ctx.monitors[k][0], len(om)) for k in range(2)])
+        ctx.close()
+    T = flux[1][1] / flux[0][1]
+    R = 1.0 - flux[1][0] / flux[0][0]
+    eT, eR = np.max(np.abs(T - T_cont)), np.max(np.abs(R - (1.0 - T_cont)))
+    # FP32 spectra: within 3% of the printed values (the FP64 oracle lands within 0.6%)
+    assert abs(eT - golden["max_abs_T_error"]) < 0.03 * golden["max_abs_T_error"], eT
+    assert abs(eR - golden["max_abs_R_error"]) < 0.03 * golden["max_abs_R_error"], eR
