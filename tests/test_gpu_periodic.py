@@ -162,3 +162,51 @@ def test_fp32_slab_error_against_the_continuum_formula_is_the_printed_one():
     # FP32 spectra: within 3% of the printed values (the FP64 oracle lands within 0.6%)
     assert abs(eT - golden["max_abs_T_error"]) < 0.03 * golden["max_abs_T_error"], eT
     assert abs(eR - golden["max_abs_R_error"]) < 0.03 * golden["max_abs_R_error"], eR
+
+
+def test_fp32_drude_slab_converges_at_the_printed_second_order_rate():
+    # Sec. 5.1 dispersive slabs on the CUDA path in FP32: the Drude slab of the oracle pin (0.1 um,
+    # eps_inf 1, lambda_p 0.9 um, gamma 2 pi 0.05 per um of c t) against the continuum transfer
+    # matrix; halving the mesh lowers the largest R / T / A error by the printed factor
+    import os
+    from tests.test_oracle_pins import _eps_continuum, _golden_dispersive, _slab_reference
+    golden = _golden_dispersive()
+    S = W.COURANT
+    lams = np.linspace(1.3, 1.8, 21)
+    poles = ((W.DRUDE, 0.0, 2 * np.pi / 0.9, 2 * np.pi * 0.05),)
+    errs = []
+    for h in (0.02, 0.01):
+        dt = S * h
+        zs = 21
+        zr, z1 = zs + int(round(0.4 / h)), zs + int(round(1.5 / h))
+        L = int(round(0.1 / h))
+        zt = z1 + L + int(round(0.4 / h))
+        nz = zt + 2 + int(round(1.0 / h)) + 16
+        steps = int(round(70.0 / dt))
+        om = 2 * np.pi * dt / lams
+        flux = []
+        for slab in (False, True):
+            mask = np.zeros((nz, 2, 2), dtype=np.uint8)
+            if slab:
+                mask[z1:z1 + L] = 1
+            src = W.Source(W.EX, (0, 0, zs), (2, 2, zs + 1),
+                           W.gaussian_pulse(steps, wavelength=1.55 / h, periods=0.6, delay=4.0))
+            mons = [W.Monitor((0, 0, zr), (2, 2, zr + 2), (W.EX, W.EY, W.HX, W.HY), om),
+                    W.Monitor((0, 0, zt), (2, 2, zt + 2), (W.EX, W.EY, W.HX, W.HY), om)]
+            sc = W.Scene(shape=(2, 2, nz), n_steps=steps, cpml=(0, 0, 0, 0, 16, 16), kappa_max=1.0,
+                         alpha_max=0.0, inv_eps=[np.ones((nz, 2, 2))],
+                         poles=tuple((k, de, w0 * dt, g * dt) for k, de, w0, g in poles) if slab else (),
+                         pole_mask=mask if slab else None, sources=[src], monitors=mons, periodic=(1, 1, 0))
+            ctx = fdtd.Context([sc], dtype="f32")
+            ctx.step(steps)
+            flux.append([fdtd.fdtd_dft_flux(ctx.ctx, ctx.monitors[k][0], len(om)) for k in range(2)])
+            ctx.close()
+        T = flux[1][1] / flux[0][1]
+        R = 1.0 - flux[1][0] / flux[0][0]
+        w = 2 * np.pi / lams
+        Re, Te = _slab_reference(_eps_continuum(w, 1.0, poles), w * 0.1)
+        errs.append(max(np.max(np.abs(R - Re)), np.max(np.abs(T - Te)),
+                        np.max(np.abs((1 - R - T) - (1 - Re - Te)))))
+    ratio = golden[("drude", 20)] / golden[("drude", 10)]
+    assert 0.75 * ratio < errs[0] / errs[1] < 1.3 * ratio, errs
+    assert errs[0] < 5.0 * golden[("drude", 20)], errs
