@@ -168,7 +168,6 @@ def test_fp32_drude_slab_converges_at_the_printed_second_order_rate():
     # Sec. 5.1 dispersive slabs on the CUDA path in FP32: the Drude slab of the oracle pin (0.1 um,
     # eps_inf 1, lambda_p 0.9 um, gamma 2 pi 0.05 per um of c t) against the continuum transfer
     # matrix; halving the mesh lowers the largest R / T / A error by the printed factor
-    import os
     from tests.test_oracle_pins import _eps_continuum, _golden_dispersive, _slab_reference
     golden = _golden_dispersive()
     S = W.COURANT
