@@ -728,3 +728,95 @@ def test_streamed_slab_schedule_reproduces_the_resident_oracle(slab, halo):
     # the emulation adds each batch's partial DFT sums from separate window runs: rounding order only
     for k in range(len(sc.monitors)):
         assert np.max(np.abs(spectra[k] - ref.dft(k))) <= 1e-13 * np.max(np.abs(ref.dft(k)))
+
+
+def _streamed_adjoint_by_windows(sc, slab, halo, cots, ckpt):
+    """The transposed sweep of the streamed schedule with the oracle: batches in reverse; per slab
+    the window replays the batch's forward steps from the checkpoint at the batch start, then runs
+    the transposed steps from the adjoint state at the batch end (adjoint sources injected over the
+    whole window), writes back its owned planes and adds the material cotangent of its owned cells
+    (design box cut to them).  Returns the adjoint state at step 0 and the gradient."""
+    nx, ny, nz = sc.shape
+    inv = [np.asarray(a) for a in sc.inv_eps3()]
+    (gx0, gy0, gz0), (gx1, gy1, gz1) = sc.design
+    grad = np.zeros((3, gz1 - gz0, gy1 - gy0, gx1 - gx0))
+    A = None
+    starts = sorted(ckpt)
+    for t0 in reversed(starts):
+        kb = min(halo, sc.n_steps - t0)
+        newA = None
+        for zs in range(0, nz, slab):
+            ze = min(nz, zs + slab)
+            lo, hi = max(0, zs - halo), min(nz, ze + halo)
+            cp = list(sc.cpml)
+            cp[4] = cp[4] if lo == 0 else 0
+            cp[5] = cp[5] if hi == nz else 0
+            o = Oracle((nx, ny, hi - lo), sc.courant, periodic=sc.periodic, cpml=cp, m=sc.cpml_m,
+                       kappa_max=sc.kappa_max, alpha_max=sc.alpha_max, sigma_max=sc.sigma_max)
+            o.set_material([a[lo:hi] for a in inv], poles=sc.poles,
+                           mask=sc.pole_mask[lo:hi] if sc.pole_mask is not None else None)
+            for s in sc.sources:
+                if s.hi[2] > lo and s.lo[2] < hi:
+                    o.add_source(s.comp, (s.lo[0], s.lo[1], max(s.lo[2], lo) - lo),
+                                 (s.hi[0], s.hi[1], min(s.hi[2], hi) - lo), s.wave)
+            q = 0
+            for k, m in enumerate(sc.monitors):
+                za, zb = max(m.lo[2], lo), min(m.hi[2], hi)
+                if zb > za:
+                    o.add_dft_box((m.lo[0], m.lo[1], za - lo), (m.hi[0], m.hi[1], zb - lo), m.comps, m.omegas)
+                    o.set_adjoint_source(q, cots[k][:, :, za - m.lo[2]:zb - m.lo[2]])
+                    q += 1
+            da, db = max(gz0, zs), min(gz1, ze)
+            if db > da:
+                o.set_design((gx0, gy0, da - lo), (gx1, gy1, db - lo))
+            nv = o.state_len // (nx * ny * (hi - lo))
+            full = ckpt[t0].reshape(nv, nz, ny, nx)
+            o.set_state(full[:, lo:hi].reshape(-1), step=t0)
+            fw = []
+            for j in range(kb):
+                fw.append(o.get_state())
+                o.step(1)
+            if A is None:
+                A = np.zeros((nv, nz, ny, nx))
+            if newA is None:
+                newA = A.copy()
+            o.set_state(A[:, lo:hi].reshape(-1), adjoint=True)
+            for j in reversed(range(kb)):
+                o.set_state(fw[j], step=t0 + j)
+                o.adjoint_step(t0 + j)
+            newA[:, zs:ze] = o.get_state(adjoint=True).reshape(nv, hi - lo, ny, nx)[:, zs - lo:ze - lo]
+            if db > da:
+                for a in range(3):
+                    grad[a, da - gz0:db - gz0] += o.grad(a)
+        A = newA
+    return A, grad
+
+
+@pytest.mark.parametrize("slab,halo", [(8, 3), (9, 6)])
+def test_streamed_transposed_sweep_reproduces_the_resident_gradient(slab, halo):
+    # Sec. 4.2: the transposed sweep runs the slab tiling in reverse.  Emulated with the oracle
+    # (CPML on every face, a diagonal tensor, two poles, a design box and a monitor crossing slab
+    # edges, 20 steps): the adjoint state at step 0 matches the resident sweep bit for bit, and
+    # the material cotangent to rounding order (each window sums its own steps first)
+    sc = W.random_state_scene(shape=(9, 8, 40), d=3, n_poles=2, aniso=True)
+    sc.n_steps = 20
+    wave = W.gaussian_pulse(20, 8.0, periods=1, delay=2)
+    sc.sources = [W.Source(W.EY, (4, 3, 5), (5, 5, 6), wave), W.Source(W.EX, (3, 4, 30), (4, 5, 31), -wave)]
+    sc.monitors = [W.Monitor((2, 2, 12), (7, 6, 27), (0, 1, 2, 3, 4, 5), W.omegas_for((7.0, 9.0)))]
+    sc.design = ((3, 3, 6), (6, 5, 34))
+    # resident forward with checkpoints at the batch starts, then the resident gradient
+    o = oracle_from_scene(sc)
+    ckpt = {}
+    for t in range(sc.n_steps):
+        if t % halo == 0:
+            ckpt[t] = o.get_state()
+        o.step(1)
+    F = o.dft(0)
+    cots = [2.0 * F]
+    ref = oracle_from_scene(sc)
+    gradient_replay(ref, sc.n_steps, lambda r: (float((np.abs(r.dft(0)) ** 2).sum()), {0: 2.0 * r.dft(0)}))
+    g_ref = np.stack([ref.grad(a) for a in range(3)])
+    ref_adj = ref.get_state(adjoint=True)
+    A, g = _streamed_adjoint_by_windows(sc, slab, halo, cots, ckpt)
+    assert np.array_equal(A.reshape(-1), ref_adj), np.max(np.abs(A.reshape(-1) - ref_adj))
+    assert np.max(np.abs(g - g_ref)) <= 1e-13 * np.max(np.abs(g_ref)), np.max(np.abs(g - g_ref))
