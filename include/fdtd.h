@@ -153,8 +153,9 @@ fdtd_status fdtd_set_material(fdtd_ctx* ctx, int32_t domain, const fdtd_material
  * which puts each product at one Yee point (Hy and Hx live on z = k + 1/2).  Spectra carry
  * their own sample times (E: t = n+1, H: t = n+3/2), so the magnetic half step is already in
  * their phases.  The monitor must record Ex, Ey, Hx and Hy (FDTD_EINVAL otherwise).
- * flux_host: n_freq doubles (host).  Synchronises. */
-fdtd_status fdtd_dft_flux(fdtd_ctx* ctx, int32_t monitor, double* flux_host);
+ * flux_host: n_freq doubles (host); n_freq must equal the monitor's frequency count (FDTD_EINVAL
+ * otherwise, nothing written).  Synchronises. */
+fdtd_status fdtd_dft_flux(fdtd_ctx* ctx, int32_t monitor, double* flux_host, int32_t n_freq);
 
 /* Periodic boundaries (Sec. 2.2: periodic/Bloch lateral boundaries, here with zero Bloch
  * phase) on the x and/or y axis of one domain: the neighbour beyond the last node is the first

@@ -1763,11 +1763,12 @@ fdtd_status fdtd_destroy(fdtd_ctx* ctx) {
     return FDTD_OK;
 }
 
-fdtd_status fdtd_dft_flux(fdtd_ctx* ctx, int32_t monitor, double* flux_host) {
+fdtd_status fdtd_dft_flux(fdtd_ctx* ctx, int32_t monitor, double* flux_host, int32_t n_freq) {
     GUARD(ctx);
     if (monitor < 0 || monitor >= (int)ctx->mons.size() || !flux_host)
         return fail(ctx, FDTD_EINVAL, "bad monitor or output");
     const Mon& m = ctx->mons[monitor].m;
+    if (n_freq != m.nf) return fail(ctx, FDTD_EINVAL, "n_freq differs from the monitor's frequency count");
     if (m.hi[2] - m.lo[2] != 2) return fail(ctx, FDTD_EINVAL, "a flux monitor spans exactly two z-planes");
     int slots[4] = {-1, -1, -1, -1};
     const int want[4] = {0, 1, 3, 4};   // Ex, Ey, Hx, Hy

@@ -79,7 +79,7 @@ _SIGS = {
     "fdtd_version": [],
     "fdtd_set_material": [_ctx, C.c_int32, C.POINTER(fdtd_material)],
     "fdtd_set_periodic": [_ctx, C.c_int32, _i32p],
-    "fdtd_dft_flux": [_ctx, C.c_int32, C.POINTER(C.c_double)],
+    "fdtd_dft_flux": [_ctx, C.c_int32, C.POINTER(C.c_double), C.c_int32],
     "fdtd_step_backward": [_ctx, C.c_int32],
     "fdtd_add_source": [_ctx, C.c_int32, C.c_int32, _i32p, _i32p, C.POINTER(C.c_double), C.c_int32, _i32p],
     "fdtd_add_dft_monitor": [_ctx, C.c_int32, _i32p, _i32p, C.c_uint32, C.c_int32, C.POINTER(C.c_double),
@@ -190,9 +190,15 @@ def fdtd_set_pole_grad(ctx, domain, enabled):
     _check(load().fdtd_set_pole_grad(ctx, int(domain), int(bool(enabled))), "fdtd_set_pole_grad", ctx)
 
 
+MAX_POLES = 16
+
+
 def fdtd_pole_grad(ctx, domain, n_poles):
-    """d J / d(delta_eps, omega_dt, gamma_dt) of each pole of a domain, shape (n_poles, 3)."""
-    out = np.zeros(3 * max(int(n_poles), 1))
+    """d J / d(delta_eps, omega_dt, gamma_dt) of each pole of a domain, shape (n_poles, 3).  The
+    library writes 3 values per pole of the domain, so the buffer holds the largest pole count."""
+    if not 0 <= int(n_poles) <= MAX_POLES:
+        raise ValueError("n_poles must be in [0, 16]")
+    out = np.zeros(3 * MAX_POLES)
     _check(load().fdtd_pole_grad(ctx, int(domain), out.ctypes.data_as(C.POINTER(C.c_double))), "fdtd_pole_grad", ctx)
     return out[: 3 * int(n_poles)].reshape(int(n_poles), 3)
 
@@ -315,9 +321,10 @@ def fdtd_part_count(ctx, domain):
 
 def fdtd_dft_flux(ctx, monitor, n_freq):
     """Net +z Poynting flux per frequency through a two-plane monitor (numpy array)."""
-    out = np.zeros(int(n_freq), dtype=np.float64)
-    _check(load().fdtd_dft_flux(ctx, int(monitor), out.ctypes.data_as(C.POINTER(C.c_double))), "fdtd_dft_flux", ctx)
-    return out
+    out = np.zeros(max(int(n_freq), 1), dtype=np.float64)
+    _check(load().fdtd_dft_flux(ctx, int(monitor), out.ctypes.data_as(C.POINTER(C.c_double)), int(n_freq)),
+           "fdtd_dft_flux", ctx)
+    return out[: int(n_freq)]
 
 
 fdtd_step_backward = _wrap_simple("fdtd_step_backward")

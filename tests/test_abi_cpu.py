@@ -41,6 +41,24 @@ def test_binding_covers_header():
         assert hasattr(fdtd, n), n
 
 
+def _declared_arity():
+    txt = open(os.path.join(ROOT, "include", "fdtd.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(fdtd_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.S):
+        params = " ".join(params.split())
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_header():
+    # every ctypes signature has as many arguments as the C declaration
+    arity = _declared_arity()
+    assert set(arity) == set(declared())
+    for name, n in arity.items():
+        assert len(fdtd._SIGS[name]) == n, (name, len(fdtd._SIGS[name]), n)
+
+
 def test_version_and_null_context_calls():
     fdtd.load()
     assert "sm_103a" in fdtd.fdtd_version()

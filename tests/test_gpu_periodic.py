@@ -122,7 +122,10 @@ def test_flux_rejects_monitors_it_cannot_use():
     sc = W.periodic_cell(n_steps=10)
     ctx = fdtd.Context([sc], dtype="f32")
     with pytest.raises(fdtd.FdtdError) as e:
-        fdtd.fdtd_dft_flux(ctx.ctx, ctx.monitors[1][0], 3)   # one plane thick
+        fdtd.fdtd_dft_flux(ctx.ctx, ctx.monitors[1][0], len(sc.monitors[1].omegas))   # one plane thick
+    assert e.value.status == fdtd.FDTD_EINVAL
+    with pytest.raises(fdtd.FdtdError) as e:   # a buffer size that is not the frequency count
+        fdtd.fdtd_dft_flux(ctx.ctx, ctx.monitors[0][0], len(sc.monitors[0].omegas) + 1)
     assert e.value.status == fdtd.FDTD_EINVAL
 
 
