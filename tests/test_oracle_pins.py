@@ -820,3 +820,39 @@ def test_streamed_transposed_sweep_reproduces_the_resident_gradient(slab, halo):
     A, g = _streamed_adjoint_by_windows(sc, slab, halo, cots, ckpt)
     assert np.array_equal(A.reshape(-1), ref_adj), np.max(np.abs(A.reshape(-1) - ref_adj))
     assert np.max(np.abs(g - g_ref)) <= 1e-13 * np.max(np.abs(g_ref)), np.max(np.abs(g - g_ref))
+
+
+def test_birefringent_slab_each_polarisation_is_its_own_lattice_slab():
+    # Sec. 2.3 diagonal tensors: at normal incidence an Ex-polarised wave sees eps_xx only and an
+    # Ey-polarised one eps_yy only, so each polarisation of a slab with principal indices 1.5 and
+    # 2.0 transmits exactly like an isotropic lattice slab of that index, with no cross-polarised
+    # field (the other component's eps may not leak into the update)
+    from oracle.flux import lattice_transmission, plane_flux_z
+    S = W.COURANT
+    nz, d, L, z1, zs, zr, zt, steps = 260, 16, 20, 140, 26, 60, 200, 3000
+    om = W.omegas_for([30.0, 40.0, 50.0])
+    idx = {0: 1.5, 1: 2.0}
+    for comp in (0, 1):
+        flux = []
+        for slab in (False, True):
+            o = Oracle((2, 2, nz), S, periodic=(1, 1, 0), cpml=(0, 0, 0, 0, d, d), m=3.0, kappa_max=1.0,
+                       alpha_max=0.0)
+            ie = [np.ones((nz, 2, 2)) for _ in range(3)]
+            if slab:
+                ie[0][z1:z1 + L] = 1.0 / idx[0] ** 2
+                ie[1][z1:z1 + L] = 1.0 / idx[1] ** 2
+                ie[2][z1:z1 + L] = 1.0 / 1.7 ** 2
+            o.set_material(ie)
+            o.add_source(comp, (0, 0, zs), (2, 2, zs + 1), W.gaussian_pulse(steps, wavelength=40.0, periods=1.0,
+                                                                            delay=3.0))
+            o.add_dft_box((0, 0, zr), (2, 2, zr + 2), (0, 1, 3, 4), om)
+            o.add_dft_box((0, 0, zt), (2, 2, zt + 2), (0, 1, 3, 4), om)
+            o.step(steps)
+            flux.append((plane_flux_z(o.dft(0), (0, 1, 3, 4)), plane_flux_z(o.dft(1), (0, 1, 3, 4))))
+            other = 1 - comp
+            assert np.max(np.abs(o.field(other))) == 0.0     # no cross-polarised E
+        T = flux[1][1] / flux[0][1]
+        T_ex = lattice_transmission(np.full(L, 1.0 / idx[comp] ** 2), om, S)
+        T_wrong = lattice_transmission(np.full(L, 1.0 / idx[1 - comp] ** 2), om, S)
+        assert np.max(np.abs(T - T_ex)) < 2e-5, (comp, T, T_ex)
+        assert np.max(np.abs(T_ex - T_wrong)) > 1e-2      # the two indices are distinguishable
