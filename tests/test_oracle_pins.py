@@ -856,3 +856,20 @@ def test_birefringent_slab_each_polarisation_is_its_own_lattice_slab():
         T_wrong = lattice_transmission(np.full(L, 1.0 / idx[1 - comp] ** 2), om, S)
         assert np.max(np.abs(T - T_ex)) < 2e-5, (comp, T, T_ex)
         assert np.max(np.abs(T_ex - T_wrong)) > 1e-2      # the two indices are distinguishable
+
+
+def test_degenerate_runs_zero_steps_and_no_sources():
+    # zero steps leave a random state and the spectra untouched; with no source the zero state
+    # stays exactly zero through CPML, poles and a tensor (nothing is injected by the boundary or
+    # the dispersion updates)
+    sc = W.random_state_scene(shape=(9, 8, 7), d=2, n_poles=2, aniso=True)
+    sc.monitors = [W.Monitor((1, 1, 1), (8, 7, 6), (0, 1, 2, 3, 4, 5), W.omegas_for((7.0,)))]
+    o = oracle_from_scene(sc, with_sources=False)
+    st = np.random.default_rng(3).standard_normal(o.state_len)
+    o.set_state(st)
+    o.step(0)
+    assert np.array_equal(o.get_state(), st)
+    assert np.array_equal(o.dft(0), np.zeros_like(o.dft(0)))
+    z = oracle_from_scene(sc, with_sources=False)
+    z.step(25)
+    assert not np.any(z.get_state()) and not np.any(z.dft(0))
