@@ -873,3 +873,93 @@ def test_degenerate_runs_zero_steps_and_no_sources():
     z = oracle_from_scene(sc, with_sources=False)
     z.step(25)
     assert not np.any(z.get_state()) and not np.any(z.dft(0))
+
+
+# ---- Bloch phase (Sec. 2.2): complex-field oracle ----------------------------------------------
+def _bloch_cell(shape=(7, 6, 9), kx=0.37, ky=-0.21, seed=1):
+    from oracle.bloch import BlochOracle
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    ie = [1.0 / rng.uniform(1.0, 4.0, size=(nz, ny, nx)) for _ in range(3)]
+    return BlochOracle(shape, W.COURANT, kx=kx, ky=ky, inv_eps=ie), rng
+
+
+def test_bloch_oracle_at_zero_phase_is_the_periodic_oracle():
+    # p = 1: real and imaginary parts step independently with the real periodic cell of the main
+    # oracle (x, y periodic, PEC z faces)
+    bo, rng = _bloch_cell(kx=0.0, ky=0.0)
+    shape = (bo.nx, bo.ny, bo.nz)
+    ref = Oracle(shape, W.COURANT, periodic=(1, 1, 0))
+    ref.set_material(bo.ie)
+    n = bo.nx * bo.ny * bo.nz
+    x = rng.standard_normal(6 * n)
+    pec = pec_mask_E(shape, (1, 1, 0))
+    for a in range(3):
+        v = x[a * n:(a + 1) * n].reshape(bo.nz, bo.ny, bo.nx)
+        v[pec[a]] = 0.0
+    st = np.zeros(ref.state_len)
+    st[:6 * n] = x
+    ref.set_state(st)
+    bo.set_state(x + 0j)
+    ref.step(9)
+    bo.step(9)
+    assert np.max(np.abs(bo.state().imag)) == 0.0
+    assert np.max(np.abs(bo.state().real - ref.get_state()[:6 * n])) <= 1e-13
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_bloch_cavity_mode_follows_the_discrete_dispersion(axis):
+    # one Bloch wavenumber k along x (Ey mode) or y (Ex mode) times a PEC standing wave sin(kz z):
+    # from H = 0 the state holds the +-omega eigenmodes only, so any field sample obeys
+    # y_{n+1} + y_{n-1} = 2 cos(omega) y_n with sin^2(omega/2) = S^2 (sin^2(k/2) + sin^2(kz/2))
+    from oracle.bloch import BlochOracle
+    nx, ny, nz, k, m = 8, 7, 10, 0.61, 2
+    kx, ky = (k, 0.0) if axis == 0 else (0.0, k)
+    bo = BlochOracle((nx, ny, nz), W.COURANT, kx=kx, ky=ky)
+    kz = m * np.pi / nz
+    i, j, kk = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    mode = (np.exp(1j * (kx * i + ky * j)) * np.sin(kz * kk)).transpose(2, 1, 0)
+    comp = 1 if axis == 0 else 0          # the E component transverse to k and z
+    bo.E[comp] = mode.astype(np.complex128)
+    S = W.COURANT
+    cos_w = 1.0 - 2.0 * S ** 2 * (np.sin(k / 2) ** 2 + np.sin(kz / 2) ** 2)
+    ys = []
+    for _ in range(60):
+        ys.append(bo.E[comp][3, 2, 5])
+        bo.step(1)
+    ys = np.array(ys)
+    res = ys[2:] + ys[:-2] - 2.0 * cos_w * ys[1:-1]
+    assert np.max(np.abs(res)) <= 1e-12 * np.max(np.abs(ys)), np.max(np.abs(res))
+    # and a neighbouring wavenumber's frequency does not fit
+    cos_bad = 1.0 - 2.0 * S ** 2 * (np.sin((k + 0.05) / 2) ** 2 + np.sin(kz / 2) ** 2)
+    assert np.max(np.abs(ys[2:] + ys[:-2] - 2.0 * cos_bad * ys[1:-1])) > 1e-3 * np.max(np.abs(ys))
+
+
+def test_bloch_step_conserves_the_discrete_energy_and_transposes_with_conjugate_seams():
+    # lossless cell: W_n = sum eps |E^n|^2 + Re sum conj(H^{n-1/2}) H^{n+1/2} is constant, which
+    # needs the forward difference to be minus the adjoint of the backward one seam included; and
+    # the transposed step is the adjoint of the step: <y, A x> = <A^H y, x>
+    bo, rng = _bloch_cell()
+    n = bo.nx * bo.ny * bo.nz
+    x = rng.standard_normal(6 * n) + 1j * rng.standard_normal(6 * n)
+    bo.set_state(x)
+    for a in range(3):
+        bo.E[a] = np.where(bo.pec[a], 0.0, bo.E[a])
+    x = bo.state()
+    Ws = []
+    for _ in range(40):
+        H_old = [h.copy() for h in bo.H]
+        bo.step(1)
+        # energy at the E time of this step: E^{n+1} with H^{n+1/2} (old) and H^{n+3/2} (new)
+        Ws.append(bo.electric_energy() + sum(float(np.real(np.vdot(H_old[a], bo.H[a]))) for a in range(3)))
+    Ws = np.array(Ws)
+    assert np.max(np.abs(Ws - Ws[0])) <= 1e-12 * abs(Ws[0]), (Ws.min(), Ws.max())
+    bo.set_state(x)
+    bo.step(3)
+    Ax = bo.state()
+    y = rng.standard_normal(6 * n) + 1j * rng.standard_normal(6 * n)
+    bo.set_state(y)
+    bo.adjoint_step(3)
+    Aty = bo.state()
+    lhs, rhs = np.vdot(y, Ax), np.vdot(Aty, x)
+    assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(Ax) * np.linalg.norm(y)
