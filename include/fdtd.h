@@ -23,8 +23,9 @@
  *     nodes at coordinate N do not exist.
  *   - Component ids: 0..2 = Ex, Ey, Ez; 3..5 = Hx, Hy, Hz.
  *   - Every function returns an fdtd_status; nothing throws across the ABI.  On error the
- *     context keeps a message (fdtd_last_error).  After FDTD_ECUDA the context is poisoned:
- *     every later call except fdtd_destroy / fdtd_last_error returns FDTD_ESTATE.
+ *     context keeps a message (fdtd_last_error).  After FDTD_ECUDA, or FDTD_ETIMEOUT reporting a
+ *     device-side wait that ran out, the context is poisoned: every later call except
+ *     fdtd_destroy / fdtd_last_error returns FDTD_ESTATE.
  *   - All device work is enqueued on the stream given to fdtd_create (a cudaStream_t passed
  *     as void*; NULL = legacy default stream).  Calls are asynchronous unless stated.
  *     A context is not thread-safe.
@@ -54,7 +55,7 @@ typedef enum {
     FDTD_ECUDA = 5,      /* a CUDA call failed; the context is poisoned */
     FDTD_ESTATE = 6,     /* call not valid in the current state (see each function) */
     FDTD_ENONFINITE = 7, /* NaN/Inf found by fdtd_check_finite */
-    FDTD_ETIMEOUT = 8    /* a bounded host wait ran out */
+    FDTD_ETIMEOUT = 8    /* a bounded host wait, or a bounded device-side wait, ran out */
 } fdtd_status;
 
 enum { FDTD_F32 = 0, FDTD_F64 = 1 };          /* storage and arithmetic type of fields */
@@ -350,8 +351,23 @@ fdtd_status fdtd_set_adjoint_step_count(fdtd_ctx* ctx, int64_t a);
 fdtd_status fdtd_check_finite(fdtd_ctx* ctx);
 
 /* Synchronises the context's stream, polling at most timeout_ms milliseconds
- * (FDTD_ETIMEOUT if the work has not finished by then; the work itself is not cancelled). */
+ * (FDTD_ETIMEOUT if the work has not finished by then; the work itself is not cancelled, and the
+ * context stays usable).  Once the stream has drained it reads the persistent kernel's sticky error
+ * word: if a device-side wait of a persistent launch (a grid barrier, or a staged plane copy of
+ * launch mode 3) gave up, it returns FDTD_ETIMEOUT and poisons the context.  Every later
+ * persistent launch of the context returns at its first instruction once the word is set, so no
+ * further step runs on a state that is no longer the result of the requested steps.
+ * fdtd_dft_read to host memory and fdtd_check_finite read the same word after they synchronise. */
 fdtd_status fdtd_synchronize(fdtd_ctx* ctx, int32_t timeout_ms);
+
+/* Wait bound of the persistent launches (modes 1-3; no counterpart in the paper): a grid-barrier
+ * wait gives up after `polls` polls of ~64 ns each (default 2^26, a few seconds), records the
+ * error and leaves the launch.  extra_arrivals (0 or 1; default 0) is a test hook: with 1 every
+ * barrier waits for one block more than the launch has, so no barrier can complete and every
+ * block gives up after at most `polls` polls -- the bounded failure path, exercised without any
+ * block that hangs or faults.  Synchronises the stream.  FDTD_EINVAL for polls < 1 or another
+ * extra_arrivals. */
+fdtd_status fdtd_set_wait_limit(fdtd_ctx* ctx, int64_t polls, int32_t extra_arrivals);
 
 /* Number of kernel launches this context has enqueued since creation (instrumentation). */
 fdtd_status fdtd_launch_count(fdtd_ctx* ctx, int64_t* n);
@@ -365,8 +381,10 @@ fdtd_status fdtd_launch_count(fdtd_ctx* ctx, int64_t* n);
  * Its scratch is a file-scope device array of 2048 per-block counts plus one total (16 KiB),
  * which every GPU that loads the library holds until the process exits.  Limit: n <= 33554432
  * values (2048 blocks x 256 threads x 64 values); larger n returns FDTD_EINVAL before any GPU
- * work.  The first call on a device looks up that array's device address (cudaGetSymbolAddress,
- * with that device current) and must come before any stream capture on the device.  Work is
+ * work.  Every call looks up that array's device address on the current device
+ * (cudaGetSymbolAddress), so the address stays right after the device's context was reset; the
+ * first call on a device also loads the library's device code there and should come before any
+ * stream capture on that device.  Work is
  * enqueued on `stream` (NULL = legacy default stream) and the call synchronises it.  All calls
  * share the one scratch array and every call rewrites the slots it reads, so consecutive calls
  * are independent, but calls that overlap on the GPU (different streams or threads at once)

@@ -6,8 +6,13 @@
  * benchmark do.  It shares no code, header, table or helper with the CUDA
  * library: every coefficient below is derived here from the paper's text.
  *
- * Plain, slow, single-threaded, full-grid arrays, written so that each line
- * can be checked against the paper by eye:
+ * Plain, slow, full-grid arrays, written so that each line can be checked
+ * against the paper by eye.  Single-threaded by default; oracle_set_threads(n)
+ * lets an OpenMP team share the k-planes of the E and H phases and the cells of
+ * the DFT accumulation, where every cell reads only values no other cell of the
+ * same loop writes, so each cell's arithmetic (and hence every result, bit for
+ * bit) is the same for any thread count.  The energy sum and the adjoint
+ * (scatter form) always run on one thread.
  *   - Eq. (yee)   (Sec. 2.1): E^{n+1} = E^n + S eps^{-1} C^-(H^{n+1/2}) + s^{n+1},
  *                             H^{n+3/2} = H^{n+1/2} - S C^+(E^{n+1}) + m^{n+3/2};
  *                 soft sources are added after the update; fields start at 0,
@@ -105,6 +110,7 @@ typedef struct oracle {
     int design_on; int dlo[3], dhi[3]; long dcell; double *grad[3];
     /* scratch */
     double *tmpE[3], *curl[3], *tmpH[3];
+    int threads;                  /* OpenMP team size of the cell loops (1: serial) */
 } oracle_t;
 
 static long IDX(const oracle_t *o, int i, int j, int k) { return ((long)k * o->N[1] + j) * o->N[0] + i; }
@@ -158,6 +164,7 @@ oracle_t *oracle_create(int nx, int ny, int nz, double S, const int *periodic, c
     o->N[0] = nx; o->N[1] = ny; o->N[2] = nz;
     o->ncell = (long)nx * ny * nz;
     o->S = S;
+    o->threads = 1;
     for (int q = 0; q < 3; ++q) o->periodic[q] = periodic ? periodic[q] : 0;
     for (int f = 0; f < 6; ++f) o->cpml[f] = cpml ? cpml[f] : 0;
     o->m = m; o->kappa_max = kappa_max; o->alpha_max = alpha_max; o->sigma_max = sigma_max;
@@ -299,6 +306,7 @@ static void dft_accumulate(oracle_t *o, int magnetic, double t) {
             for (int f = 0; f < m->nf; ++f) {
                 double cr = cos(m->omega[f] * t), si = sin(m->omega[f] * t);
                 double *acc = m->acc + 2L * ((long)ci * m->nf + f) * m->ncell;
+#pragma omp parallel for num_threads(o->threads) if (o->threads > 1 && m->ncell >= 4096)
                 for (long c = 0; c < m->ncell; ++c) {
                     int i, j, k; mon_cell(m, c, &i, &j, &k);
                     double v = o->F[comp][IDX(o, i, j, k)];
@@ -325,6 +333,7 @@ static void e_phase(oracle_t *o, double *const Eout[3], double *const psiout[3][
     for (int a = 0; a < 3; ++a) {
         int b = (a + 1) % 3, cax = (a + 2) % 3;
         const double *Hc = o->F[3 + cax], *Hb = o->F[3 + b];
+#pragma omp parallel for num_threads(o->threads) if (o->threads > 1)
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
@@ -395,6 +404,7 @@ static void h_phase(oracle_t *o) {
         int b = (a + 1) % 3, cax = (a + 2) % 3;
         const double *Ec = o->F[cax], *Eb = o->F[b];
         double *H = o->F[3 + a];
+#pragma omp parallel for num_threads(o->threads) if (o->threads > 1)
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
@@ -443,6 +453,10 @@ static void step_once(oracle_t *o) {
 }
 
 void oracle_step(oracle_t *o, int n) { for (int s = 0; s < n; ++s) step_once(o); }
+
+/* Team size of the cell loops of the forward step (values < 1 mean 1).  Results do not
+ * depend on it. */
+void oracle_set_threads(oracle_t *o, int n) { o->threads = n < 1 ? 1 : n; }
 
 /* Reversible reconstruction (Sec. 3.2: lossless nondispersive problems step Eq. (yee)
  * backward): one backward step u^{n+1} -> u^n undoes the forward step n in reverse order,

@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py``; the product path never imports it.  The arithmetic lives
-in ``fdtd_oracle.c`` (plain C, single thread, full-grid FP64 arrays); this module only
-compiles it with gcc, marshals arguments and exposes numpy views.
+in ``fdtd_oracle.c`` (plain C, full-grid FP64 arrays, one thread unless a team is asked for);
+this module only compiles it with gcc, marshals arguments and exposes numpy views.
 
 Paper passages followed (arxiv 2609.30039): Sec. 2.1 Eq. (yee) and the half-step time
 bookkeeping; Sec. 2.2 CPML and PEC; Sec. 2.3 diagonal permittivity and trapezoidal
@@ -32,11 +32,17 @@ _ip = C.POINTER(C.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, portable: no -march flags)."""
+    """Compile the oracle with gcc: -O3, ISO C99 (so no multiply-add contraction: every
+    operation rounds on its own, on x86 and Arm alike), portable (no -march flags), with OpenMP
+    for the optional cell-loop team (see Oracle.set_threads); without libgomp it builds serial."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O3", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -58,6 +64,7 @@ def _load():
             "oracle_add_dft_box": (C.c_int, [vp, _ip, _ip, C.c_uint, C.c_int, _dp]),
             "oracle_enable_energy": (None, [vp, C.c_long]),
             "oracle_step": (None, [vp, C.c_int]),
+            "oracle_set_threads": (None, [vp, C.c_int]),
             "oracle_step_backward": (C.c_int, [vp, C.c_int]),
             "oracle_field": (_dp, [vp, C.c_int]),
             "oracle_psi": (_dp, [vp, C.c_int, C.c_int, C.c_int]),
@@ -187,6 +194,11 @@ class Oracle:
     # -- stepping and access ----------------------------------------------------------
     def step(self, n=1):
         self.lib.oracle_step(self.h, int(n))
+
+    def set_threads(self, n):
+        """OpenMP team size of the forward step's cell loops (1 = serial, the default).  Every
+        cell's arithmetic is the same for any team size, so results are identical bit for bit."""
+        self.lib.oracle_set_threads(self.h, int(n))
 
     def step_backward(self, n=1):
         """Undoes n forward steps by stepping Eq. (yee) backward (lossless, nondispersive

@@ -1425,6 +1425,18 @@ fdtd_status flush_adjoint(fdtd_ctx* c) {
     return FDTD_OK;
 }
 
+// Reads the sticky error word of the persistent kernel after the stream has drained (the caller
+// synchronised it).  A wait that ran out poisons the context: its state is no longer the
+// result of the requested steps.
+fdtd_status device_error(fdtd_ctx* c) {
+    int err = 0;
+    CK(c, cudaMemcpy(&err, &c->d_sync->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!err) return FDTD_OK;
+    c->poisoned = 1;
+    if (err == 1) return fail(c, FDTD_ETIMEOUT, "a grid barrier of the persistent step kernel ran out");
+    return fail(c, FDTD_ETIMEOUT, "a staged plane copy of the persistent step kernel never completed");
+}
+
 fdtd_status set_device_step(fdtd_ctx* c, long long s) {
     c->h_step_tmp = (int)s;
     CK(c, cudaMemcpyAsync(c->d_step, &c->h_step_tmp, sizeof(int), cudaMemcpyHostToDevice, c->stream));
@@ -1432,13 +1444,18 @@ fdtd_status set_device_step(fdtd_ctx* c, long long s) {
     return FDTD_OK;
 }
 
+// Layout of one part in a BF16 snapshot: n bf16 codes, then (from the next 4-byte boundary, so
+// that parts of odd size keep their scales aligned) one FP32 scale per plane.
+size_t bf16_scale_off(long long n) { return ((size_t)n * 2 + 3) & ~(size_t)3; }
+size_t bf16_part_bytes(long long n, long long planes) { return bf16_scale_off(n) + (size_t)planes * 4; }
+
 size_t snapshot_bytes(const fdtd_ctx* c, int codec) {
     size_t tot = 0;
     for (const auto& d : c->doms)
         for (int p = 0; p < part_count(d); ++p) {
             const long long n = part_size(d, p);
             if (n == 0) continue;
-            const size_t b = codec == FDTD_CODEC_BF16 ? (size_t)n * 2 + (size_t)part_planes(d, p) * 4 : (size_t)n * c->esz;
+            const size_t b = codec == FDTD_CODEC_BF16 ? bf16_part_bytes(n, part_planes(d, p)) : (size_t)n * c->esz;
             tot += (b + 255) & ~(size_t)255;
         }
     return tot;
@@ -1588,6 +1605,12 @@ static fdtd_status create_impl(int32_t n_domains, const fdtd_grid* grids, const 
     if (e != cudaSuccess) return bail(FDTD_ECUDA);
     c->owned.push_back(c->d_sync);
     if (cudaMemsetAsync(c->d_ticket, 0, 64, c->stream) != cudaSuccess) return bail(FDTD_ECUDA);
+    {
+        // the only place the sticky error word is cleared
+        GridSync gs0{};
+        gs0.spin_limit = kDefaultSpinLimit;
+        if (cudaMemcpy(c->d_sync, &gs0, sizeof(gs0), cudaMemcpyHostToDevice) != cudaSuccess) return bail(FDTD_ECUDA);
+    }
 
     // domain geometry, pole boxes and the memory plan
     c->doms.resize(n_domains);
@@ -1946,7 +1969,10 @@ fdtd_status fdtd_dft_read(fdtd_ctx* ctx, int32_t monitor_id, void* dst, size_t b
     const Mon& m = ctx->mons[monitor_id].m;
     CK(ctx, cudaMemcpyAsync(dst, m.acc, (size_t)n * 16, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                             ctx->stream));
-    if (!dst_on_device) CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!dst_on_device) {
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        return device_error(ctx);
+    }
     return FDTD_OK;
 }
 
@@ -2360,10 +2386,9 @@ static fdtd_status save_slot(fdtd_ctx* ctx, int32_t slot, int32_t codec) {
             if (n == 0) continue;
             const void* src = part_ptr(d, 0, part, ctx->esz);
             const long long np = part_planes(d, part);
-            const size_t b = (size_t)n * 2 + (size_t)np * 4;
+            const size_t b = bf16_part_bytes(n, np);
             uint16_t* q = (uint16_t*)p;
-            float* sc = (float*)(p + (size_t)n * 2);
-            if (((uintptr_t)sc) & 3) return fail(ctx, FDTD_EINVAL, "internal alignment");
+            float* sc = (float*)(p + bf16_scale_off(n));
             if (ctx->dtype == FDTD_F32)
                 launch_bf16_encode<float>(l, (const float*)src, np, n / np, q, sc);
             else
@@ -2394,9 +2419,9 @@ static fdtd_status restore_slot(fdtd_ctx* ctx, int32_t slot) {
             if (n == 0) continue;
             void* dst = part_ptr(d, 0, part, ctx->esz);
             const long long np = part_planes(d, part);
-            const size_t b = (size_t)n * 2 + (size_t)np * 4;
+            const size_t b = bf16_part_bytes(n, np);
             const uint16_t* q = (const uint16_t*)p;
-            const float* sc = (const float*)(p + (size_t)n * 2);
+            const float* sc = (const float*)(p + bf16_scale_off(n));
             if (ctx->dtype == FDTD_F32)
                 launch_bf16_decode<float>(l, q, sc, np, n / np, (float*)dst);
             else
@@ -2623,6 +2648,8 @@ fdtd_status fdtd_check_finite(fdtd_ctx* ctx) {
     unsigned long long bad = 0;
     CK(ctx, cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    fdtd_status st = device_error(ctx);
+    if (st != FDTD_OK) return st;
     if (bad) return fail(ctx, FDTD_ENONFINITE, "non-finite values in the forward state");
     return FDTD_OK;
 }
@@ -2632,18 +2659,23 @@ fdtd_status fdtd_synchronize(fdtd_ctx* ctx, int32_t timeout_ms) {
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaStreamQuery(ctx->stream);
-        if (e == cudaSuccess) {
-            GridSync gs;
-            CK(ctx, cudaMemcpy(&gs, ctx->d_sync, sizeof(gs), cudaMemcpyDeviceToHost));
-            if (gs.err == 1) return fail(ctx, FDTD_ETIMEOUT, "a grid barrier of the persistent step kernel ran out");
-            if (gs.err) return fail(ctx, FDTD_ETIMEOUT, "a staged plane copy of the persistent step kernel never completed");
-            return FDTD_OK;
-        }
+        if (e == cudaSuccess) return device_error(ctx);
         if (e != cudaErrorNotReady) return fail(ctx, FDTD_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
         const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
         if (ms.count() >= timeout_ms) return fail(ctx, FDTD_ETIMEOUT, "stream not finished within the timeout");
         std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
+}
+
+fdtd_status fdtd_set_wait_limit(fdtd_ctx* ctx, int64_t polls, int32_t extra_arrivals) {
+    GUARD(ctx);
+    if (polls < 1 || extra_arrivals < 0 || extra_arrivals > 1) return fail(ctx, FDTD_EINVAL, "bad wait limit");
+    const long long lim = polls;
+    const int extra = extra_arrivals;
+    CK(ctx, cudaStreamSynchronize(ctx->stream));   // no launch in flight reads the words being changed
+    CK(ctx, cudaMemcpy(&ctx->d_sync->spin_limit, &lim, sizeof(lim), cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(&ctx->d_sync->extra, &extra, sizeof(extra), cudaMemcpyHostToDevice));
+    return FDTD_OK;
 }
 
 fdtd_status fdtd_launch_count(fdtd_ctx* ctx, int64_t* n) {

@@ -122,14 +122,19 @@ enum : int {
     kTileGeneral = 16 // needs the CPML / PEC / pole code path
 };
 
-// State of the grid-wide barrier and tile ticket of the persistent step kernel.
+// State of the grid-wide barrier and tile ticket of the persistent step kernel.  arrive, gen and
+// ticket are cleared before every launch; err is sticky: it is cleared only when the context is
+// created, so an error of one launch stops every later launch at its first instruction and stays
+// visible until the host reads it.
 struct GridSync {
     unsigned arrive;
     unsigned gen;
-    int err;                  // set when a barrier wait ran out (the launch then stops)
-    int pad;
+    int err;                  // 1: a barrier wait ran out; 2: a staged plane copy never completed
+    int extra;                // added to the arrivals a barrier waits for (0; a test hook, see fdtd.h)
     unsigned long long ticket;
+    long long spin_limit;     // polls (~64 ns each) a barrier wait may take before it gives up
 };
+constexpr long long kDefaultSpinLimit = 1ll << 26;   // a few seconds
 // Columns of a tile: lane tx maps to x in [xs[0], xs[1]) then [xs[2], xs[3]) (two segments let
 // one warp cover both opposite CPML slabs), thread row ty to y likewise with ys; at most
 // kTileX x kTileY columns.  z runs over [z0, z1).

@@ -1002,10 +1002,11 @@ __device__ __forceinline__ bool tile_h_tma(const Dom<T>& d, const Tile& t, T S, 
 // ---- persistent step kernel ---------------------------------------------------------------
 // One cooperative launch runs nsteps forward steps: in each half-step the blocks claim tiles from
 // a shared ticket (general tiles first, so the slower ones start early), then meet at a
-// grid-wide barrier.  The barrier wait is bounded; if it runs out the block records an error
-// and every block leaves the loop (a cooperative launch guarantees all blocks are resident, so
-// this only guards against a fault elsewhere).
-constexpr long long kBarrierSpinLimit = 1ll << 26;   // x ~64 ns sleep: a few seconds
+// grid-wide barrier.  The barrier wait is bounded (gs->spin_limit polls); if it runs out the
+// block records an error and every block leaves the loop (a cooperative launch guarantees all
+// blocks are resident, so this only guards against a fault elsewhere).  A block whose wait ran
+// out leaves its arrival counted, so the blocks still inside reach no later barrier either: each
+// of them also gives up after at most spin_limit polls, and the launch ends in bounded time.
 
 __device__ __forceinline__ bool grid_sync(GridSync* gs, unsigned nblocks) {
     __shared__ int s_ok;
@@ -1013,15 +1014,17 @@ __device__ __forceinline__ bool grid_sync(GridSync* gs, unsigned nblocks) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         volatile unsigned* vgen = &gs->gen;
         const unsigned g = *vgen;
+        const long long limit = *((volatile long long*)&gs->spin_limit);
+        const unsigned need = nblocks + (unsigned)*((volatile int*)&gs->extra);
         __threadfence();
-        if (atomicAdd(&gs->arrive, 1u) == nblocks - 1) {
+        if (atomicAdd(&gs->arrive, 1u) == need - 1) {
             gs->arrive = 0u;
             __threadfence();
             atomicAdd(&gs->gen, 1u);
         } else {
             long long it = 0;
             while (*vgen == g) {
-                if (++it > kBarrierSpinLimit) {
+                if (++it > limit) {
                     atomicExch(&gs->err, 1);
                     break;
                 }
@@ -1061,6 +1064,8 @@ __global__ void __launch_bounds__(kTileX* kTileY, min_blocks_persistent<T, kVar>
         }
         __syncthreads();
     }
+    // an earlier launch of this context gave up a wait: do nothing (the error stays set)
+    if (*((volatile int*)&gs->err) != 0) return;
     const int step0 = *a.d_step;
     // each phase claims the field tiles, then the DFT items of the field the phase leaves alone:
     // the E phase of step s records H of step s-1, the H phase E of step s; a tail phase records
@@ -1155,7 +1160,9 @@ cudaError_t launch_steps(const Launch& L, const Dom<T>* doms, const Tile* tiles,
     int grid = sms * per;
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
-    e = cudaMemsetAsync(gs, 0, sizeof(GridSync), L.stream);
+    // clear the barrier and the ticket, not the sticky error word or the limits
+    e = cudaMemsetAsync(&gs->arrive, 0, 2 * sizeof(unsigned), L.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&gs->ticket, 0, sizeof(unsigned long long), L.stream);
     if (e != cudaSuccess) return e;
     StepArgs aa = a;
     void* args[] = {(void*)&doms, (void*)&tiles, (void*)&ntiles, (void*)&S, (void*)&aa, (void*)&nsteps, (void*)&gs};

@@ -5,12 +5,12 @@
 // Scratch: one file-scope __device__ array of kNoallocPartials per-block counts plus one total.
 // Every process that loads the library holds it on every GPU it touches until exit.  Host code
 // must not pass the symbol itself to a kernel (on the host it is only a stand-in): its device
-// address is looked up once per device with cudaGetSymbolAddress, with that device current,
-// on the first call made on that device.
+// address is looked up with cudaGetSymbolAddress, with the caller's device current, on every
+// call.  The lookup costs little next to the synchronisation each call ends with, and an address
+// kept from an earlier call could point at released memory once the device's context has been
+// torn down and recreated (cudaDeviceReset), when the array may have moved.
 #include <cuda_runtime.h>
 #include <stdint.h>
-
-#include <mutex>
 
 #include "fdtd.h"
 
@@ -20,12 +20,8 @@ constexpr int kNoallocPartials = 2048;   // per-block partial counts held in the
 constexpr int kNoallocThreads = 256;
 constexpr long long kNoallocPerThread = 64;
 constexpr long long kNoallocMaxValues = (long long)kNoallocPartials * kNoallocThreads * kNoallocPerThread;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoallocPartials + 1];
-
-std::mutex g_mutex;
-unsigned long long* g_scratch_addr[kMaxDevices] = {};
 
 template <typename T>
 __global__ void k_count_nonfinite_partial(const T* __restrict__ p, long long n, unsigned long long* partial) {
@@ -67,18 +63,10 @@ extern "C" fdtd_status fdtd_count_nonfinite_noalloc(const void* data, int64_t n,
     if (n > kNoallocMaxValues) return FDTD_EINVAL;   // needs more than kNoallocPartials partial counts
     *count = 0;
     if (n == 0) return FDTD_OK;
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FDTD_ECUDA;
-    unsigned long long* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mutex);
-        if (!g_scratch_addr[dev]) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FDTD_ECUDA;
-            g_scratch_addr[dev] = (unsigned long long*)p;
-        }
-        scratch = g_scratch_addr[dev];
-    }
+    // the scratch array's address on the current device (see the file comment)
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FDTD_ECUDA;
+    unsigned long long* scratch = (unsigned long long*)p;
     const cudaStream_t st = (cudaStream_t)stream;
     long long blocks = (n + kNoallocThreads * kNoallocPerThread - 1) / (kNoallocThreads * kNoallocPerThread);
     if (blocks < 1) blocks = 1;

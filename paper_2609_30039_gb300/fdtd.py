@@ -114,6 +114,7 @@ _SIGS = {
     "fdtd_set_adjoint_step_count": [_ctx, C.c_int64],
     "fdtd_check_finite": [_ctx],
     "fdtd_synchronize": [_ctx, C.c_int32],
+    "fdtd_set_wait_limit": [_ctx, C.c_int64, C.c_int32],
     "fdtd_launch_count": [_ctx, _i64p],
     "fdtd_count_nonfinite_noalloc": [_vp, C.c_int64, C.c_int32, _vp, _i64p],
     "fdtd_profile_begin": [_ctx, C.c_int32],
@@ -260,6 +261,7 @@ fdtd_step_adjoint = _wrap_simple("fdtd_step_adjoint")
 fdtd_set_adjoint_step_count = _wrap_simple("fdtd_set_adjoint_step_count")
 fdtd_check_finite = _wrap_simple("fdtd_check_finite")
 fdtd_synchronize = _wrap_simple("fdtd_synchronize")
+fdtd_set_wait_limit = _wrap_simple("fdtd_set_wait_limit")
 
 
 def _get_i64(name, ctx, *args):
@@ -547,8 +549,10 @@ class Context:
     def launches(self):
         return fdtd_launch_count(self.ctx)
 
-    def synchronize(self):
-        self.stream.synchronize()
+    def synchronize(self, timeout_ms: int = 600000):
+        """Waits for the context's work and reports a device-side wait that gave up (FdtdError
+        with FDTD_ETIMEOUT; the context is then poisoned)."""
+        fdtd_synchronize(self.ctx, int(timeout_ms))
 
     def close(self):
         if getattr(self, "ctx", None):

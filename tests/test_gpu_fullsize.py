@@ -1,0 +1,88 @@
+"""The stated precision gates at the workloads' full sizes: the CUDA path through the C ABI
+against the FP64 oracle on the same seeded inputs.
+
+* 128^3 cells, 10-cell CPML (m = 3, kappa_max = 5, alpha_max = 0.05), central 64^3 of blocky
+  eps_r ~ U[1, 12], Ez Gaussian-pulse sheet, 2000 steps, DFT of the six components on the z = 64
+  plane at three frequencies: FP32 spectra within 1e-4 relative L2 of the oracle's (over every
+  complex entry: 6 components x 3 frequencies x 128^2 cells), FP64 spectra and the six FP64
+  fields after step 2000 within 1e-12.
+* 64 uneven two-pole Lorentz domains (48..96 cells per axis, 8-cell CPML), 1500 steps, stepped
+  together in one batched context: every domain's FP32 monitor spectra within 1e-4 of its own
+  oracle run.
+
+The oracle runs with an OpenMP team over its cell loops (results do not depend on the team
+size), so the 4.2e9 oracle cell-steps of the first case take well under a minute on the host.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2609_30039_gb300 import build as B
+from paper_2609_30039_gb300 import fdtd
+from paper_2609_30039_gb300 import workloads as W
+from tests.oracle_adapter import oracle_from_scene
+
+pytestmark = pytest.mark.gpu
+
+THREADS = max(1, os.cpu_count() or 1)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    fdtd.load()
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def cpml128_oracle():
+    sc = W.cpml_blocks(n=128, d=10, n_steps=2000)
+    o = oracle_from_scene(sc)
+    o.set_threads(THREADS)
+    o.step(sc.n_steps)
+    return sc, o.dft(0).copy(), [o.field(c).copy() for c in range(6)]
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", 1e-4), ("f64", 1e-12)])
+def test_cpml128_2000_steps_spectra_match_the_oracle(cpml128_oracle, dtype, tol):
+    sc, ref, ref_fields = cpml128_oracle
+    ctx = fdtd.Context([sc], dtype=dtype)
+    ctx.step(sc.n_steps)
+    F = ctx.dft(0).cpu().numpy()
+    assert F.shape == ref.shape
+    err = rel(F, ref)
+    # per (component, frequency): each must also be close on its own scale
+    per = [[rel(F[c, f], ref[c, f]) for f in range(ref.shape[1])] for c in range(ref.shape[0])]
+    print(f"\n{dtype}: spectra rel-L2 vs oracle {err:.3e}; per component/frequency max {np.max(per):.3e}")
+    assert err <= tol, (dtype, err)
+    assert np.max(per) <= 10 * tol, (dtype, per)
+    if dtype == "f64":
+        g = np.concatenate([ctx.field(0, c).cpu().numpy().ravel() for c in range(6)])
+        r = np.concatenate([f.ravel() for f in ref_fields])
+        ferr = rel(g, r)
+        print(f"f64: six fields after step {sc.n_steps} rel-L2 vs oracle {ferr:.3e}")
+        assert ferr <= 1e-12, ferr
+    ctx.close()
+
+
+def test_lorentz_batch_every_domain_fp32_matches_its_oracle():
+    scs = W.lorentz_batch()
+    ctx = fdtd.Context(scs, dtype="f32")
+    ctx.step(scs[0].n_steps)
+    torch.cuda.synchronize()
+    errs = []
+    for d, sc in enumerate(scs):
+        o = oracle_from_scene(sc)
+        o.set_threads(min(THREADS, 8))
+        o.step(sc.n_steps)
+        errs.append(rel(ctx.dft(d).cpu().numpy(), o.dft(0)))
+    print(f"\nlorentz batch: {len(scs)} domains, FP32 spectra rel-L2 vs oracle: max {max(errs):.3e}, "
+          f"median {np.median(errs):.3e}")
+    assert max(errs) <= 1e-4, errs
+    ctx.close()

@@ -424,6 +424,34 @@ def test_bf16_snapshot_every_part_anisotropic_poles():
         assert (got - ref).abs().max() <= bound, (p, float((got - ref).abs().max()), float(bound))
 
 
+def test_bf16_snapshot_on_a_grid_with_odd_extents():
+    """Parts of odd size (33 x 35 x 37 fields, odd CPML slab arrays): each part's scales follow its
+    codes at the next 4-byte boundary, so save and restore work and stay within the BF16 bound."""
+    sc = W.cpml_blocks(n=33, d=5, n_steps=120, block=3, region=(9, 24), wavelengths=(8.0, 10.0))
+    sc.shape = (33, 35, 37)
+    inv = np.ones((37, 35, 33))
+    inv[9:24, 9:24, 9:24] = sc.inv_eps[0][9:24, 9:24, 9:24]
+    sc.inv_eps = [inv]
+    sc.sources[0] = W.Source(W.EZ, (10, 5, 5), (11, 30, 32), W.gaussian_pulse(120, wavelength=10.0, periods=1.0,
+                                                                               delay=3.0))
+    sc.monitors = [W.Monitor((0, 0, 18), (33, 35, 19), (0, 1, 2), sc.monitors[0].omegas)]
+    ctx = fdtd.Context([sc], dtype="f32")
+    ctx.step(70)
+    sizes = [fdtd.fdtd_part_size(ctx.ctx, 0, p) for p in range(ctx.part_count(0))]
+    assert any(n % 2 for n in sizes if n)
+    saved = [ctx.part(0, p).clone() for p in range(ctx.part_count(0))]
+    fdtd.fdtd_state_save(ctx.ctx, 5, fdtd.FDTD_CODEC_BF16)
+    ctx.step(9)
+    fdtd.fdtd_state_restore(ctx.ctx, 5)
+    assert ctx.step_count == 70
+    for p in range(ctx.part_count(0)):
+        got, ref = ctx.part(0, p), saved[p]
+        if not ref.numel():
+            continue
+        assert torch.isfinite(got).all(), p
+        assert (got - ref).abs().max() <= ref.abs().max() * 2.0 ** -8 + 1e-30, p
+
+
 # ----------------------------------------------------------------------------- errors
 def _grid(nx=16, courant=W.COURANT, dtype=fdtd.FDTD_F32):
     return fdtd.fdtd_grid(nx, nx, nx, 1.0, courant, 0.0, dtype)
