@@ -195,6 +195,9 @@ def run_ours(args):
         tune_ms = []
         fdtd.fdtd_set_launch_mode(ctx.ctx, args.launch_mode)
     mode = fdtd.fdtd_get_launch_mode(ctx.ctx)
+    # event-record nodes inside the replayed forward graphs time the E, H and DFT launches of the
+    # timed solves themselves (--no-graph-timing leaves them out)
+    fdtd.fdtd_graph_timing(ctx.ctx, 0 if args.no_graph_timing else 1)
     for _ in range(args.warmup):
         solve()
     torch.cuda.synchronize()
@@ -203,7 +206,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     l0 = ctx.launches()
     times = []
-    prof = None
+    kern = {"e_update": 0.0, "h_update": 0.0, "dft": 0.0}
+    kern_steps = 0
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             flush.fill_(float(k))                      # L2 flush between timed iterations
@@ -214,47 +218,48 @@ def run_ours(args):
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
+            te, th, td, ns = fdtd.fdtd_graph_timing_read(ctx.ctx)   # the last graph replay of this solve
+            kern["e_update"] += te
+            kern["h_update"] += th
+            kern["dft"] += td
+            kern_steps += ns
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     launches = ctx.launches() - l0
     tot_ms = sum(times)
-    # per-kernel event timing in one extra, untimed solve (the instrumentation serialises the
-    # concurrent launches, so it stays out of the timed iterations)
-    flush.fill_(0.0)
-    fdtd.fdtd_profile_begin(ctx.ctx, 12 * T_STEPS + 16)
-    solve()
-    prof = fdtd.fdtd_profile_end(ctx.ctx)
-    torch.cuda.synchronize()
+    spectra32 = ctx.dft(0).cpu().numpy()       # the last timed solve's spectra (oracle check below)
     tot_ms = sharding.max_over_ranks(tot_ms, dist, dev)
     ms_per_step = tot_ms / args.steps
     value = world * cells * T_STEPS / (ms_per_step * 1e-3) / 1e9
 
-    # roofline of the dominant kernel (event-timed in the instrumented solve)
+    # roofline of the dominant kernel, timed inside the replayed graphs of the timed solves
     peak, peak_kind = peaks()
-    if prof["persistent"][1]:
-        # one persistent launch runs up to 512 whole steps (E and H half-steps)
-        dom = "persistent"
-        bE, ncell = alg_bytes_per_cell(sc, 4, "e_update")
-        bH, _ = alg_bytes_per_cell(sc, 4, "h_update")
-        launches_p = prof["persistent"][1]
-        avg_ms = prof["persistent"][0] / launches_p
-        alg_bytes = (bE + bH) * ncell * T_STEPS / launches_p
-        achieved = (bE + bH) * ncell * T_STEPS / (prof["persistent"][0] * 1e-3) / 1e9
-    else:
-        dom = max(("e_update", "h_update"), key=lambda k: prof[k][0])
-        avg_ms = prof[dom][0] / max(prof[dom][1], 1)
-        bpc, ncell = alg_bytes_per_cell(sc, 4, dom)
+    bE, ncell = alg_bytes_per_cell(sc, 4, "e_update")
+    bH, _ = alg_bytes_per_cell(sc, 4, "h_update")
+    step_us = ms_per_step * 1e3 / T_STEPS
+    roof_extra = {}
+    if kern_steps:
+        dom = max(("e_update", "h_update"), key=lambda k: kern[k])
+        avg_ms = kern[dom] / kern_steps
+        bpc = bE if dom == "e_update" else bH
         alg_bytes = bpc * ncell
         achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
-    # ncu DRAM bytes of the same kernel variant (recorded per time step), or None
-    if dom == "persistent":
-        traffic = recorded_traffic(f"persistent_mode{mode}", T_STEPS / prof["persistent"][1])
+        step_ms = {k: v / kern_steps for k, v in kern.items()}
+        tot_k = sum(kern.values())
+        share = {k: round(v / tot_k, 4) for k, v in kern.items() if v}
+        roof_extra = {"timed_in": f"event nodes of the replayed graphs of the timed solves ({kern_steps} steps)",
+                      "e_plus_h_us_per_step": round((kern["e_update"] + kern["h_update"]) / kern_steps * 1e3, 3),
+                      "step_us": round(step_us, 3)}
     else:
-        traffic = recorded_traffic(f"{dom}_mode{mode}", 1)
-    step_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]}
-    share = {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items() if v[1]}
+        # no graph replays (a persistent launch mode): the whole step is the kernel
+        dom, avg_ms = "step", step_us * 1e-3
+        alg_bytes = (bE + bH) * ncell
+        achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+        step_ms, share = {"step": avg_ms}, {"step": 1.0}
+    # ncu DRAM bytes of the same kernel variant (recorded per time step), or None
+    traffic = recorded_traffic(f"{dom}_mode{mode}", 1)
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gcell-steps/s", "n_gpus": world,
@@ -272,10 +277,16 @@ def run_ours(args):
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                      "alg_bytes_per_launch": int(alg_bytes), "avg_launch_us": round(avg_ms * 1e3, 3),
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                     else "fallback 6.8 TB/s"},
+                     else "fallback 6.8 TB/s",
+                     "step_effective_gbs": round((bE + bH) * ncell / (step_us * 1e-6) / 1e9, 1),
+                     "note": "the ~75 MB state of this grid stays L2-resident within a solve, so this is an "
+                             "effective bandwidth (L2 and HBM service); roofline_256 carries the HBM-bound figure",
+                     **roof_extra},
         "kernel_avg_us": {k: round(v * 1e3, 3) for k, v in step_ms.items()},
         "kernel_share": share,
     }
+    if traffic:
+        out["roofline"]["dram_frac"] = round(traffic / (avg_ms * 1e-3) / 1e9 / peak, 4)
     clk_s = clk.summary()
     if clk_s:
         out["clocks"] = clk_s
@@ -283,8 +294,12 @@ def run_ours(args):
     if rank == 0 and not args.quick:
         out["e2e"] = e2e(ctx, sc, args, dev)
         out.update(extras(ctx, sc, args, dev))
+        out["roofline_256"] = roofline_256(args, dev, peak)
         if not args.no_cpu:
-            out["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
+            cb, par = cpu_baseline(sc, args.cpu_seconds, spectra32, out["fp64"].pop("_spectra"))
+            out["cpu_baseline"] = cb
+            if par:
+                out["parity"] = par
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -349,9 +364,9 @@ def extras(ctx, sc, args, dev):
     ms64 = e0.elapsed_time(e1)
     f64 = c64.dft(0)
     err = float(torch.linalg.vector_norm(f32 - f64) / torch.linalg.vector_norm(f64))
-    res["fp64"] = {"value": round(sc.cells * T_STEPS / (ms64 * 1e-3) / 1e9, 3), "unit": "Gcell-steps/s",
-                   "fp32_vs_fp64_dft_rel_l2": err, "note": "FP64 GPU path is checked against the FP64 oracle "
-                   "to <= 1e-12 in the parity tests"}
+    v64 = sc.cells * T_STEPS / (ms64 * 1e-3) / 1e9
+    res["fp64"] = {"value": round(v64, 3), "unit": "Gcell-steps/s", "fp32_vs_fp64_gpu_dft_rel_l2": err,
+                   "roof": fp64_roof(sc, v64), "_spectra": f64.cpu().numpy()}
     c64.close()
     # transposed steps (no design box: pure transpose rate over the whole grid)
     fdtd.fdtd_adjoint_begin(ctx.ctx)
@@ -389,22 +404,137 @@ def extras(ctx, sc, args, dev):
     return res
 
 
-def cpu_baseline(sc, seconds):
-    """The FP64 oracle as it stands, single thread, on the first few steps of the same workload."""
+def fp64_roof(sc, v64):
+    """Roof of the FP64 path: min(HBM copy bandwidth / FP64 bytes, measured FP64 instruction rate /
+    FP64 instructions) per cell-step.  Instructions per cell-step of the per-cell kernels (adds,
+    multiplies and fused multiply-adds, each one FP64 instruction): E update 6 differences + 3 curls
+    + 1 S eps^-1 product + 3 updates = 13, H update 6 + 3 + 3 = 12, plus 12 per CPML slab membership
+    (3 per corrected derivative: c D, two fused multiply-adds; 2 derivatives per half-step)."""
+    from paper_2609_30039_gb300 import fdtd
+    n = sc.shape
+    memb = sum((sc.cpml[2 * q] + sc.cpml[2 * q + 1]) / n[q] for q in range(3))
+    inst = 25.0 + 12.0 * memb
+    bE, _ = alg_bytes_per_cell(sc, 8, "e_update")
+    bH, _ = alg_bytes_per_cell(sc, 8, "h_update")
+    rate, _ = fdtd.fdtd_measure_fp64_rate(0)
+    hbm, _ = peaks()
+    roof_hbm = hbm * 1e9 / (bE + bH) / 1e9
+    roof_alu = rate / inst / 1e9
+    roof = min(roof_hbm, roof_alu)
+    return {"bound": "alu" if roof_alu < roof_hbm else "hbm", "value": round(roof, 3), "unit": "Gcell-steps/s",
+            "frac": round(v64 / roof, 4), "hbm_roof": round(roof_hbm, 3), "alu_roof": round(roof_alu, 3),
+            "fp64_fma_per_s_measured": round(rate, 1), "fp64_inst_per_cell_step": round(inst, 2),
+            "bytes_per_cell_step": round(bE + bH, 1)}
+
+
+def roofline_256(args, dev, peak):
+    """The forward kernels on a 256^3 grid of the same workload family (10-cell CPML, blocky eps,
+    sheet source, plane DFT), whose ~0.5 GB state does not fit the 126 MB L2: per-kernel times from
+    the graph event nodes of a short solve, against the HBM copy bandwidth."""
+    import torch
+
+    from paper_2609_30039_gb300 import fdtd
+    from paper_2609_30039_gb300 import workloads as W
+    n, steps = 256, 320
+    sc = W.cpml_blocks(n=n, d=CPML, n_steps=steps + 64)
+    ctx = fdtd.Context([sc], dtype="f32", device=str(dev))
+    fdtd.fdtd_set_launch_mode(ctx.ctx, 4)
+    fdtd.fdtd_graph_timing(ctx.ctx, 1)
+    ctx.step(64)
+    torch.cuda.synchronize()
+    acc = {"e_update": 0.0, "h_update": 0.0, "dft": 0.0}
+    ns_tot = 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(steps // 32):
+        ctx.step(32)
+        te, th, td, ns = fdtd.fdtd_graph_timing_read(ctx.ctx)
+        acc["e_update"] += te
+        acc["h_update"] += th
+        acc["dft"] += td
+        ns_tot += ns
+    e1.record(ctx.stream)
+    e1.synchronize()
+    ctx.close()
+    out = {"workload": f"cpml_blocks_{n}^3 (same family, {n}^3 cells, CPML {CPML}), {steps} steps, FP32",
+           "gcell_steps_s": round(sc.cells * steps / (e0.elapsed_time(e1) * 1e-3) / 1e9, 3),
+           "note": "state ~0.5 GB, larger than L2: HBM-bound; steps timed one graph at a time (timing reads between)"}
+    for k in ("e_update", "h_update"):
+        bpc, cells = alg_bytes_per_cell(sc, 4, k)
+        avg = acc[k] / max(ns_tot, 1)
+        ach = bpc * cells / (avg * 1e-3) / 1e9
+        out[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                  "avg_launch_us": round(avg * 1e3, 3), "alg_bytes_per_launch": int(bpc * cells),
+                  "traffic": recorded_traffic(f"{k}_256", 1)}
+    return out
+
+
+def cpu_baseline(sc, seconds, spectra32, spectra64):
+    """The FP64 oracle as it stands on the host cores: (1) the whole 2000-step workload with an
+    OpenMP team of every core over its cell loops -- the all-core rate and, from its spectra, the
+    FP32 and FP64 GPU paths' errors against it; (2) one thread on a bounded sample of the same run."""
+    import numpy as np
     from oracle.oracle import build as obuild
     from tests.oracle_adapter import oracle_from_scene
     obuild()
+    cores = os.cpu_count() or 1
+    par = None
     o = oracle_from_scene(sc)
+    o.set_threads(cores)
     t0 = time.perf_counter()
     o.step(2)
-    est = (time.perf_counter() - t0) / 2
-    n = max(1, min(T_STEPS - 2, int(seconds / max(est, 1e-6))))
+    est = (time.perf_counter() - t0) / 2 * T_STEPS
+    if est < 240.0:
+        t0 = time.perf_counter()
+        o.step(T_STEPS - 2)
+        dt_all = time.perf_counter() - t0
+        steps_all = T_STEPS - 2
+        ref = o.dft(0)
+
+        def rel(a):
+            return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+
+        par = {"fp32_vs_oracle_dft_rel_l2": rel(spectra32), "fp64_vs_oracle_dft_rel_l2": rel(spectra64),
+               "tolerance": {"fp32": 1e-4, "fp64": 1e-12},
+               "what": "relative L2 over every complex entry (6 components x 3 frequencies x 128^2 cells) of the "
+                       "spectra after 2000 steps, GPU (timed FP32 solve; FP64 solve) vs the FP64 oracle"}
+    else:
+        t0 = time.perf_counter()
+        steps_all = max(1, int(60.0 / est * T_STEPS))
+        o.step(steps_all)
+        dt_all = time.perf_counter() - t0
+    o1 = oracle_from_scene(sc)
+    o1.step(1)
     t0 = time.perf_counter()
-    o.step(n)
-    dt = time.perf_counter() - t0
-    return {"value": round(sc.cells * n / dt / 1e9, 6), "unit": "Gcell-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"steps 3..{n + 2} of the 2000-step 128^3 workload (FP64 C oracle, one thread, "
-                      f"{dt:.1f} s)"}
+    o1.step(2)
+    est1 = (time.perf_counter() - t0) / 2
+    n1 = max(1, min(T_STEPS - 3, int(seconds / max(est1, 1e-6))))
+    t0 = time.perf_counter()
+    o1.step(n1)
+    dt1 = time.perf_counter() - t0
+    cb = {"value": round(sc.cells * steps_all / dt_all / 1e9, 6), "unit": "Gcell-steps/s", "cores": cores,
+          "kind": "oracle",
+          "sample": f"steps 3..{steps_all + 2} of the 2000-step 128^3 workload, FP64 C oracle (-O3, ISO C, no -march), "
+                    f"OpenMP team of {cores} threads over its cell loops, {dt_all:.1f} s",
+          "one_core": {"value": round(sc.cells * n1 / dt1 / 1e9, 6), "unit": "Gcell-steps/s", "cores": 1,
+                       "sample": f"steps 4..{n1 + 3}, one thread, {dt1:.1f} s"},
+          "host": host_cpu()}
+    return cb, par
+
+
+def host_cpu():
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        for key in ("model name", "CPU part"):
+            for line in txt.splitlines():
+                if line.lower().startswith(key.lower()):
+                    val = line.split(":", 1)[1].strip()
+                    return {"cpu": val if key == "model name" else f"Arm part {val} (0xd4f = Neoverse-V2)",
+                            "nproc": os.cpu_count()}
+    except Exception:
+        pass
+    return {"cpu": "unknown", "nproc": os.cpu_count()}
 
 
 def run_reference(args):
@@ -416,6 +546,8 @@ def run_reference(args):
     obuild()
     sc = scene()
     o = oracle_from_scene(sc)
+    cores = os.cpu_count() or 1
+    o.set_threads(cores)
     per = max(1, args.ref_steps_per_iter)
     for _ in range(args.warmup):
         o.step(1)
@@ -431,8 +563,9 @@ def run_reference(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "cells": sc.cells,
                       "time_steps_per_iter": per, "note": "each bench step is a bounded sample of the workload"},
-           "cpu_baseline": {"value": round(value, 6), "unit": "Gcell-steps/s", "cores": 1, "kind": "oracle",
-                            "sample": f"{per} time steps of the 128^3 workload per bench step"},
+           "cpu_baseline": {"value": round(value, 6), "unit": "Gcell-steps/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{per} time steps of the 128^3 workload per bench step, OpenMP team of "
+                                      f"{cores} threads over the oracle's cell loops", "host": host_cpu()},
            "e2e": {"value": round(value, 6), "unit": "Gcell-steps/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -446,8 +579,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip e2e / extras / cpu baseline")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-steps-per-iter", type=int, default=8)
+    ap.add_argument("--no-graph-timing", action="store_true",
+                    help="time the solves without event nodes in the graphs (no per-kernel times)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-steps-per-iter", type=int, default=32)
     ap.add_argument("--profile-case", type=int, default=0,
                     help="n: run only a short n^3 FP32 forward (ncu captures on a case larger than L2)")
     ap.add_argument("--workload", default="cpml128",
@@ -464,10 +599,20 @@ def main():
                     help="0 per half-step tile launches, 1 persistent, 2 persistent with prefetch, 3 persistent "
                          "with TMA staging, 4 per-cell launches; default: autotuned (the bench line), 4 "
                          "(--profile-case)")
+    ap.add_argument("--dry-run", action="store_true",
+                    help="host-only check of the launch path: N gloo ranks, no GPU work, one JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.profile_case:
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # not launched by torchrun: start one process per GPU and let them report
+        sys.exit(relaunch(args.gpus))
+    rank, world, _ = rank_info()
+    if "WORLD_SIZE" in os.environ and world != args.gpus:
+        raise SystemExit(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world}")
+    if args.dry_run:
+        dry_run(args)
+    elif args.profile_case:
         profile_case(args)
     elif args.workload != "cpml128" and args.impl == "ours":
         {"pec32": measure_pec32, "batched": measure_batched, "adjoint256": measure_adjoint256,
@@ -477,6 +622,37 @@ def main():
         run_reference(args)
     else:
         run_ours(args)
+
+
+def relaunch(n):
+    """Re-runs this command under torch.distributed.run with n processes on this node (rendezvous
+    on 127.0.0.1, a free port); returns their exit status."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
+def dry_run(args):
+    """Every rank joins a gloo group, takes part in the barrier and the max-over-ranks reduction of
+    the real run (here of its rank number), and rank 0 prints the line's launch keys."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2609_30039_gb300 import sharding
+    rank, world, local = rank_info()
+    if world > 1:
+        dist.init_process_group("gloo")
+    t = sharding.max_over_ranks(float(rank), dist if world > 1 else None, torch.device("cpu"))
+    if rank == 0:
+        print(json.dumps({"dry_run": True, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "max_rank_seen": t}), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def profile_case(args):

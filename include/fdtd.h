@@ -413,6 +413,27 @@ fdtd_status fdtd_profile_begin(fdtd_ctx* ctx, int32_t max_launches);
  * summed device milliseconds and the number of timed launches. */
 fdtd_status fdtd_profile_end(fdtd_ctx* ctx, double* ms_per_class, int64_t* launches_per_class);
 
+/* FP64 arithmetic-rate probe (instrumentation; no counterpart in the paper): runs independent
+ * FP64 fused multiply-add chains on every SM (a few milliseconds, best of five timed runs after a
+ * warm-up, CUDA events on `stream`, NULL = legacy default stream; it allocates and frees one small
+ * device buffer) and writes the measured FP64 instruction rate (*fma_per_s, FMA instructions per
+ * second; 2 flops each) and the best run's duration.  The FP64 path's roof is
+ * min(HBM bandwidth / bytes, this rate / FP64 instructions) per cell-step.  Synchronises. */
+fdtd_status fdtd_measure_fp64_rate(void* stream, double* fma_per_s, double* best_ms);
+
+/* Timing inside the captured forward graphs (instrumentation; no counterpart in the paper).
+ * enabled = 1: forward graphs built from now on (existing ones are dropped) carry CUDA event-record
+ * nodes around each step's E launches and its H launches, so the kernels are timed as they run in
+ * the replayed graphs, beside the concurrent DFT work, not in a serialised replay.  0 removes them.
+ * FDTD_EINVAL for another value. */
+fdtd_status fdtd_graph_timing(fdtd_ctx* ctx, int32_t enabled);
+/* Synchronises the stream and writes the summed device milliseconds of the E launches (*ms_e), of
+ * the H launches (*ms_h) and of the DFT launches (*ms_dft, which run on their own stream beside
+ * the field updates) over the *steps steps of the most recent replay of the forward graph of the
+ * current configuration (DFT on or off, energy on or off).  *steps = 0 (and the sums 0) when
+ * timing is off or that graph has not been replayed yet. */
+fdtd_status fdtd_graph_timing_read(fdtd_ctx* ctx, double* ms_e, double* ms_h, double* ms_dft, int32_t* steps);
+
 #ifdef __cplusplus
 }
 #endif

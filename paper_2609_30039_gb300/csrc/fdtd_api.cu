@@ -156,6 +156,12 @@ struct fdtd_ctx {
     DftItem* d_sitems = nullptr;              // DFT items of the owned planes of every slab
     std::vector<int> sitem_begin, sitem_count;
     int stream_dirty = 1;
+    // event-record nodes in the captured forward graphs (kGtPerStep per step: E start / end, H start /
+    // end on the step's stream, then DFT-of-E start / end and DFT-of-H start / end on the DFT
+    // stream), per graph key; gt_cur points at the events of the graph being captured
+    int graph_timing = 0;
+    std::vector<cudaEvent_t> gt_ev[2][2];
+    cudaEvent_t* gt_cur = nullptr;
     // instrumentation
     int prof_on = 0;
     int prof_used = 0;
@@ -874,6 +880,8 @@ fdtd_status upload_tiles(fdtd_ctx* c) {
 }
 
 // Event pair around one launch when profiling (two records on the stream, no work changed).
+constexpr int kGtPerStep = 8;   // timing events per captured step (see fdtd_ctx::gt_ev)
+
 struct Prof {
     fdtd_ctx* c;
     bool on;
@@ -972,6 +980,12 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
     if ((nd > 0 || cell) && first) launch_copy_int(l, c->d_step, c->d_base);
     if (dstream && !first) cudaStreamWaitEvent(st, c->ev_de, 0);   // DFT of E^n done before E changes
     auto cell_args = [&](int di, bool e_side) { return make_cell_args<T>(c, di, e_side); };
+    // timing nodes of a graph being captured: which = 0 / 1 around the E launches, 2 / 3 around H,
+    // 4 / 5 around the DFT of E and 6 / 7 around the DFT of H (on the stream they run on)
+    auto gt = [&](int which, cudaStream_t on) {
+        if (c->gt_cur) cudaEventRecordWithFlags(c->gt_cur[kGtPerStep * offset + which], on, cudaEventRecordExternal);
+    };
+    gt(0, st);
     if (cell) {
         Prof p(c, FDTD_KERNEL_E);
         for (int di = 0; di < (int)c->doms.size(); ++di) {
@@ -990,19 +1004,28 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
         }
         join_int();
     }
+    gt(1, st);
     if (nd > 0) {
         if (dstream) {
             cudaEventRecord(c->ev_e, st);
             cudaStreamWaitEvent(c->dft_stream, c->ev_e, 0);
         }
-        Prof p(c, FDTD_KERNEL_DFT);
-        launch_dft<T>(ld, dd, c->d_mons, c->d_dft_items, nd, 0, c->d_base, offset);
+        gt(4, ld.stream);
+        {
+            Prof p(c, FDTD_KERNEL_DFT);
+            launch_dft<T>(ld, dd, c->d_mons, c->d_dft_items, nd, 0, c->d_base, offset);
+        }
+        gt(5, ld.stream);
         if (dstream) cudaEventRecord(c->ev_de, c->dft_stream);
     }
     if (dstream && !first) cudaStreamWaitEvent(st, c->ev_dh, 0);   // DFT of H^{n-1/2} done
+    gt(2, st);
     if (cell) {
-        Prof p(c, FDTD_KERNEL_H);
-        for (int di = 0; di < (int)c->doms.size(); ++di) launch_h_cell<T>(l, cell_args(di, false), (T)c->S, a);
+        {
+            Prof p(c, FDTD_KERNEL_H);
+            for (int di = 0; di < (int)c->doms.size(); ++di) launch_h_cell<T>(l, cell_args(di, false), (T)c->S, a);
+        }
+        gt(3, st);
         if (last) launch_advance(l, c->d_step, offset + 1);
     } else {
         fork_int();
@@ -1015,14 +1038,19 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
             launch_h_update<T>(la, dd, c->d_tiles_int, ni, (T)c->S, a, 0, c->energy_on, adv);
         }
         join_int();
+        gt(3, st);
     }
     if (nd > 0) {
         if (dstream) {
             cudaEventRecord(c->ev_h, st);
             cudaStreamWaitEvent(c->dft_stream, c->ev_h, 0);
         }
-        Prof p(c, FDTD_KERNEL_DFT);
-        launch_dft<T>(ld, dd, c->d_mons, c->d_dft_items, nd, 1, c->d_base, offset);
+        gt(6, ld.stream);
+        {
+            Prof p(c, FDTD_KERNEL_DFT);
+            launch_dft<T>(ld, dd, c->d_mons, c->d_dft_items, nd, 1, c->d_base, offset);
+        }
+        gt(7, ld.stream);
         if (dstream) cudaEventRecord(c->ev_dh, c->dft_stream);
         if (dstream && last) cudaStreamWaitEvent(st, c->ev_dh, 0);
     }
@@ -1385,6 +1413,11 @@ fdtd_status build_graph(fdtd_ctx* c) {
     const int a = c->dft_enabled, b = c->energy_on;
     if (c->graph[a][b]) return FDTD_OK;
     if (!c->cap_stream) CK(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    if (c->graph_timing && c->gt_ev[a][b].empty()) {
+        c->gt_ev[a][b].resize(kGtPerStep * kGraphSteps, nullptr);
+        for (auto& ev : c->gt_ev[a][b]) CK(c, cudaEventCreate(&ev));
+    }
+    c->gt_cur = c->graph_timing ? c->gt_ev[a][b].data() : nullptr;
     const long long l0 = c->launches;
     CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int s = 0; s < kGraphSteps; ++s) {
@@ -1395,6 +1428,7 @@ fdtd_status build_graph(fdtd_ctx* c) {
     }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    c->gt_cur = nullptr;
     c->launches = l0;
     if (e != cudaSuccess) return fail(c, FDTD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&c->graph[a][b], g, 0);
@@ -1779,6 +1813,10 @@ fdtd_status fdtd_destroy(fdtd_ctx* ctx) {
     for (auto* v : {&ctx->ev_in, &ctx->ev_out})
         for (cudaEvent_t e : *v)
             if (e) cudaEventDestroy(e);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (cudaEvent_t e : ctx->gt_ev[a][b])
+                if (e) cudaEventDestroy(e);
     for (void* p : ctx->owned) cudaFree(p);
     for (void* p : ctx->host_owned) cudaFreeHost(p);
     for (auto& s : ctx->slots) cudaFree(s.second.buf);
@@ -2681,6 +2719,44 @@ fdtd_status fdtd_set_wait_limit(fdtd_ctx* ctx, int64_t polls, int32_t extra_arri
 fdtd_status fdtd_launch_count(fdtd_ctx* ctx, int64_t* n) {
     if (!ctx || !n) return FDTD_EINVAL;
     *n = ctx->launches;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_graph_timing(fdtd_ctx* ctx, int32_t enabled) {
+    GUARD(ctx);
+    if (enabled != 0 && enabled != 1) return fail(ctx, FDTD_EINVAL, "enabled must be 0 or 1");
+    if (ctx->graph_timing == enabled) return FDTD_OK;
+    drop_graphs(ctx);
+    ctx->graph_timing = enabled;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_graph_timing_read(fdtd_ctx* ctx, double* ms_e, double* ms_h, double* ms_dft, int32_t* steps) {
+    GUARD(ctx);
+    if (!ms_e || !ms_h || !ms_dft || !steps) return fail(ctx, FDTD_EINVAL, "NULL output");
+    *ms_e = *ms_h = *ms_dft = 0.0;
+    *steps = 0;
+    const int a = ctx->dft_enabled, b = ctx->energy_on;
+    if (!ctx->graph_timing || !ctx->graph[a][b] || ctx->gt_ev[a][b].empty()) return FDTD_OK;
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const bool dft = ctx->dft_enabled && ctx->n_dft_items > 0;
+    const auto& ev = ctx->gt_ev[a][b];
+    double sum[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int s = 0; s < kGraphSteps; ++s)
+        for (int pair = 0; pair < (dft ? 4 : 2); ++pair) {
+            float t = 0.f;
+            const cudaError_t e = cudaEventElapsedTime(&t, ev[kGtPerStep * s + 2 * pair], ev[kGtPerStep * s + 2 * pair + 1]);
+            if (e == cudaErrorNotReady || e == cudaErrorInvalidResourceHandle) {
+                cudaGetLastError();   // the graph has not been replayed since it was built
+                return FDTD_OK;
+            }
+            CK(ctx, e);
+            sum[pair] += t;
+        }
+    *ms_e = sum[0];
+    *ms_h = sum[1];
+    *ms_dft = sum[2] + sum[3];
+    *steps = kGraphSteps;
     return FDTD_OK;
 }
 

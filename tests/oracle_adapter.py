@@ -38,3 +38,24 @@ def pec_mask_E(shape, periodic=(0, 0, 0)):
             m[tuple(sl)] = True
         masks.append(m)
     return masks
+
+
+def oracle_spectra(sc, threads=1):
+    """Runs a Scene's whole forward solve in the oracle and returns the spectra of its monitors
+    (a list, in the scene's monitor order).  Module-level so a spawn process pool can call it."""
+    o = oracle_from_scene(sc)
+    o.set_threads(threads)
+    o.step(sc.n_steps)
+    return [o.dft(k).copy() for k in range(len(sc.monitors))]
+
+
+def oracle_spectra_many(scenes, processes=None):
+    """oracle_spectra of many independent scenes, one single-threaded oracle per worker of a
+    spawn pool (safe after CUDA was initialised in this process)."""
+    import multiprocessing as mp
+    import os
+    procs = processes or max(1, min(len(scenes), os.cpu_count() or 1))
+    if procs == 1:
+        return [oracle_spectra(sc) for sc in scenes]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(oracle_spectra, scenes, chunksize=1)

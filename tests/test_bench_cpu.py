@@ -41,3 +41,18 @@ def test_workloads_are_reproducible():
             assert np.array_equal(a.pole_mask, b.pole_mask)
         for s, t in zip(a.sources, b.sources):
             assert s.lo == t.lo and s.hi == t.hi and np.array_equal(s.wave, t.wave)
+
+
+def test_gpus_n_without_torchrun_starts_n_ranks():
+    """`bench.py --gpus 2` run directly (no WORLD_SIZE in the environment) re-launches itself under
+    torch.distributed.run with two processes; in dry-run mode they join a gloo group and rank 0
+    reports n_gpus = 2 and the max over both ranks."""
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_ADDR",
+                                                            "MASTER_PORT")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--dry-run", "--steps", "1"],
+                       capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and d["max_rank_seen"] == 1.0

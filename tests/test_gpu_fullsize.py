@@ -7,8 +7,8 @@ against the FP64 oracle on the same seeded inputs.
   complex entry: 6 components x 3 frequencies x 128^2 cells), FP64 spectra and the six FP64
   fields after step 2000 within 1e-12.
 * 64 uneven two-pole Lorentz domains (48..96 cells per axis, 8-cell CPML), 1500 steps, stepped
-  together in one batched context: every domain's FP32 monitor spectra within 1e-4 of its own
-  oracle run.
+  together in one batched context: every domain's FP64 spectra within 1e-12 of its own oracle
+  run, the FP32 batch within 1e-4 (see the test for the normalisation).
 
 The oracle runs with an OpenMP team over its cell loops (results do not depend on the team
 size), so the 4.2e9 oracle cell-steps of the first case take well under a minute on the host.
@@ -22,7 +22,7 @@ import torch
 from paper_2609_30039_gb300 import build as B
 from paper_2609_30039_gb300 import fdtd
 from paper_2609_30039_gb300 import workloads as W
-from tests.oracle_adapter import oracle_from_scene
+from tests.oracle_adapter import oracle_from_scene, oracle_spectra_many
 
 pytestmark = pytest.mark.gpu
 
@@ -71,18 +71,31 @@ def test_cpml128_2000_steps_spectra_match_the_oracle(cpml128_oracle, dtype, tol)
     ctx.close()
 
 
-def test_lorentz_batch_every_domain_fp32_matches_its_oracle():
+def test_lorentz_batch_every_domain_matches_its_oracle():
+    """Every domain of the batch against its own oracle run.  FP64: each domain's spectra within
+    1e-12.  FP32: the batch's spectra taken together within 1e-4 relative L2 (the analogue of the
+    plane criterion above: a monitor result judged against its own norm), and each domain's error
+    within 1e-4 of the batch's RMS domain-spectrum norm.  A point monitor can sit where the spectrum
+    at the monitored frequencies is four orders below the batch's typical level; FP32 rounding
+    error is set by the field scale, not by that local level, so a per-domain relative bound there
+    would measure the monitor's placement, not the arithmetic (the FP64 check rules out a wrong
+    update in that domain)."""
     scs = W.lorentz_batch()
-    ctx = fdtd.Context(scs, dtype="f32")
-    ctx.step(scs[0].n_steps)
-    torch.cuda.synchronize()
-    errs = []
-    for d, sc in enumerate(scs):
-        o = oracle_from_scene(sc)
-        o.set_threads(min(THREADS, 8))
-        o.step(sc.n_steps)
-        errs.append(rel(ctx.dft(d).cpu().numpy(), o.dft(0)))
-    print(f"\nlorentz batch: {len(scs)} domains, FP32 spectra rel-L2 vs oracle: max {max(errs):.3e}, "
-          f"median {np.median(errs):.3e}")
-    assert max(errs) <= 1e-4, errs
-    ctx.close()
+    ref = [r[0] for r in oracle_spectra_many(scs)]
+    got = {}
+    for dt in ("f32", "f64"):
+        ctx = fdtd.Context(scs, dtype=dt)
+        ctx.step(scs[0].n_steps)
+        got[dt] = [ctx.dft(d).cpu().numpy() for d in range(len(scs))]
+        ctx.close()
+    e64 = [rel(got["f64"][d], ref[d]) for d in range(len(scs))]
+    e32 = [rel(got["f32"][d], ref[d]) for d in range(len(scs))]
+    norms = np.array([np.linalg.norm(r) for r in ref])
+    rms = float(np.sqrt(np.mean(norms ** 2)))
+    e32_scaled = [float(np.linalg.norm(got["f32"][d] - ref[d])) / rms for d in range(len(scs))]
+    batch32 = rel(np.concatenate([g.ravel() for g in got["f32"]]), np.concatenate([r.ravel() for r in ref]))
+    print(f"\nlorentz batch, {len(scs)} domains: FP64 max {max(e64):.3e}; FP32 batch {batch32:.3e}, per domain "
+          f"(own norm) max {max(e32):.3e} median {np.median(e32):.3e}, (batch RMS norm) max {max(e32_scaled):.3e}")
+    assert max(e64) <= 1e-12, e64
+    assert batch32 <= 1e-4, batch32
+    assert max(e32_scaled) <= 1e-4, e32_scaled
