@@ -195,9 +195,6 @@ def run_ours(args):
         tune_ms = []
         fdtd.fdtd_set_launch_mode(ctx.ctx, args.launch_mode)
     mode = fdtd.fdtd_get_launch_mode(ctx.ctx)
-    # event-record nodes inside the replayed forward graphs time the E, H and DFT launches of the
-    # timed solves themselves (--no-graph-timing leaves them out)
-    fdtd.fdtd_graph_timing(ctx.ctx, 0 if args.no_graph_timing else 1)
     for _ in range(args.warmup):
         solve()
     torch.cuda.synchronize()
@@ -206,8 +203,6 @@ def run_ours(args):
     torch.cuda.synchronize()
     l0 = ctx.launches()
     times = []
-    kern = {"e_update": 0.0, "h_update": 0.0, "dft": 0.0}
-    kern_steps = 0
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             flush.fill_(float(k))                      # L2 flush between timed iterations
@@ -218,11 +213,6 @@ def run_ours(args):
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
-            te, th, td, ns = fdtd.fdtd_graph_timing_read(ctx.ctx)   # the last graph replay of this solve
-            kern["e_update"] += te
-            kern["h_update"] += th
-            kern["dft"] += td
-            kern_steps += ns
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -234,24 +224,32 @@ def run_ours(args):
     ms_per_step = tot_ms / args.steps
     value = world * cells * T_STEPS / (ms_per_step * 1e-3) / 1e9
 
-    # roofline of the dominant kernel, timed inside the replayed graphs of the timed solves
+    # roofline of the dominant kernel: each kernel class of the timed solve, on the benchmark state
+    # right after the timed solves, as a graph of 32 back-to-back launches with CUDA events on the
+    # context's stream at the graph's two ends only (events between launches would add a drain per
+    # launch); E + H must fit in the timed step (the DFT runs beside them on its own stream)
     peak, peak_kind = peaks()
     bE, ncell = alg_bytes_per_cell(sc, 4, "e_update")
     bH, _ = alg_bytes_per_cell(sc, 4, "h_update")
     step_us = ms_per_step * 1e3 / T_STEPS
     roof_extra = {}
-    if kern_steps:
-        dom = max(("e_update", "h_update"), key=lambda k: kern[k])
-        avg_ms = kern[dom] / kern_steps
+    if mode == 4:
+        step_ms = {"e_update": fdtd.fdtd_time_half_steps(ctx.ctx, 0, 32),
+                   "h_update": fdtd.fdtd_time_half_steps(ctx.ctx, 1, 32),
+                   "dft": fdtd.fdtd_time_half_steps(ctx.ctx, 2, 32)}
+        step_ms["dft"] *= 2.0   # the DFT of E and the DFT of H of one step
+        dom = max(("e_update", "h_update"), key=lambda k: step_ms[k])
+        avg_ms = step_ms[dom]
         bpc = bE if dom == "e_update" else bH
         alg_bytes = bpc * ncell
         achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
-        step_ms = {k: v / kern_steps for k, v in kern.items()}
-        tot_k = sum(kern.values())
-        share = {k: round(v / tot_k, 4) for k, v in kern.items() if v}
-        roof_extra = {"timed_in": f"event nodes of the replayed graphs of the timed solves ({kern_steps} steps)",
-                      "e_plus_h_us_per_step": round((kern["e_update"] + kern["h_update"]) / kern_steps * 1e3, 3),
-                      "step_us": round(step_us, 3)}
+        tot_k = sum(step_ms.values())
+        share = {k: round(v / tot_k, 4) for k, v in step_ms.items()}
+        eh = (step_ms["e_update"] + step_ms["h_update"]) * 1e3
+        roof_extra = {"timed_in": "graph of 32 back-to-back launches on the benchmark state after the timed solves, "
+                                  "CUDA events at the graph's ends",
+                      "e_plus_h_us_per_step": round(eh, 3), "step_us": round(step_us, 3),
+                      "e_plus_h_fits_step": bool(eh <= step_us * 1.02)}
     else:
         # no graph replays (a persistent launch mode): the whole step is the kernel
         dom, avg_ms = "step", step_us * 1e-3
@@ -429,8 +427,9 @@ def fp64_roof(sc, v64):
 
 def roofline_256(args, dev, peak):
     """The forward kernels on a 256^3 grid of the same workload family (10-cell CPML, blocky eps,
-    sheet source, plane DFT), whose ~0.5 GB state does not fit the 126 MB L2: per-kernel times from
-    the graph event nodes of a short solve, against the HBM copy bandwidth."""
+    sheet source, plane DFT), whose ~0.5 GB state does not fit the 126 MB L2: the stepping rate of a
+    short solve, and each kernel class as 32 back-to-back launches in a graph (CUDA events at the
+    graph's ends) against the HBM copy bandwidth."""
     import torch
 
     from paper_2609_30039_gb300 import fdtd
@@ -439,33 +438,24 @@ def roofline_256(args, dev, peak):
     sc = W.cpml_blocks(n=n, d=CPML, n_steps=steps + 64)
     ctx = fdtd.Context([sc], dtype="f32", device=str(dev))
     fdtd.fdtd_set_launch_mode(ctx.ctx, 4)
-    fdtd.fdtd_graph_timing(ctx.ctx, 1)
     ctx.step(64)
     torch.cuda.synchronize()
-    acc = {"e_update": 0.0, "h_update": 0.0, "dft": 0.0}
-    ns_tot = 0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(ctx.stream)
-    for _ in range(steps // 32):
-        ctx.step(32)
-        te, th, td, ns = fdtd.fdtd_graph_timing_read(ctx.ctx)
-        acc["e_update"] += te
-        acc["h_update"] += th
-        acc["dft"] += td
-        ns_tot += ns
+    ctx.step(steps)
     e1.record(ctx.stream)
     e1.synchronize()
-    ctx.close()
-    out = {"workload": f"cpml_blocks_{n}^3 (same family, {n}^3 cells, CPML {CPML}), {steps} steps, FP32",
+    out = {"workload": f"cpml_blocks_{n}^3 (same family, {n}^3 cells, CPML {CPML}), {steps} steps, FP32, per-cell mode",
            "gcell_steps_s": round(sc.cells * steps / (e0.elapsed_time(e1) * 1e-3) / 1e9, 3),
-           "note": "state ~0.5 GB, larger than L2: HBM-bound; steps timed one graph at a time (timing reads between)"}
-    for k in ("e_update", "h_update"):
+           "note": "state ~0.5 GB, larger than L2: HBM-bound"}
+    for which, k in ((0, "e_update"), (1, "h_update")):
+        avg = fdtd.fdtd_time_half_steps(ctx.ctx, which, 32)
         bpc, cells = alg_bytes_per_cell(sc, 4, k)
-        avg = acc[k] / max(ns_tot, 1)
         ach = bpc * cells / (avg * 1e-3) / 1e9
         out[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                   "avg_launch_us": round(avg * 1e3, 3), "alg_bytes_per_launch": int(bpc * cells),
                   "traffic": recorded_traffic(f"{k}_256", 1)}
+    ctx.close()
     return out
 
 
@@ -579,8 +569,6 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip e2e / extras / cpu baseline")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-graph-timing", action="store_true",
-                    help="time the solves without event nodes in the graphs (no per-kernel times)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-steps-per-iter", type=int, default=32)
     ap.add_argument("--profile-case", type=int, default=0,

@@ -421,18 +421,16 @@ fdtd_status fdtd_profile_end(fdtd_ctx* ctx, double* ms_per_class, int64_t* launc
  * min(HBM bandwidth / bytes, this rate / FP64 instructions) per cell-step.  Synchronises. */
 fdtd_status fdtd_measure_fp64_rate(void* stream, double* fma_per_s, double* best_ms);
 
-/* Timing inside the captured forward graphs (instrumentation; no counterpart in the paper).
- * enabled = 1: forward graphs built from now on (existing ones are dropped) carry CUDA event-record
- * nodes around each step's E launches and its H launches, so the kernels are timed as they run in
- * the replayed graphs, beside the concurrent DFT work, not in a serialised replay.  0 removes them.
- * FDTD_EINVAL for another value. */
-fdtd_status fdtd_graph_timing(fdtd_ctx* ctx, int32_t enabled);
-/* Synchronises the stream and writes the summed device milliseconds of the E launches (*ms_e), of
- * the H launches (*ms_h) and of the DFT launches (*ms_dft, which run on their own stream beside
- * the field updates) over the *steps steps of the most recent replay of the forward graph of the
- * current configuration (DFT on or off, energy on or off).  *steps = 0 (and the sums 0) when
- * timing is off or that graph has not been replayed yet. */
-fdtd_status fdtd_graph_timing_read(fdtd_ctx* ctx, double* ms_e, double* ms_h, double* ms_dft, int32_t* steps);
+/* Device time of one forward kernel class running back to back (instrumentation; no counterpart in
+ * the paper): captures n_launches (1..4096) launches of the E update (which = 0), the H update (1)
+ * or the DFT of E (2) -- the per-cell kernels of every domain, as one forward step launches them --
+ * into a CUDA graph, replays it once to warm up and once between two CUDA events on the context's
+ * stream, and writes the milliseconds per launch.  Only the graph is bracketed, so nothing sits
+ * between the timed launches.  The launches act on the live state (fields, CPML memories, pole
+ * states or DFT accumulators change as if the half-step ran 2 n_launches times at the current step
+ * index): reset or restore the state afterwards.  Per-cell launch mode (4) without an energy record
+ * only, and which = 2 needs a monitor (FDTD_EINVAL otherwise).  Synchronises. */
+fdtd_status fdtd_time_half_steps(fdtd_ctx* ctx, int32_t which, int32_t n_launches, double* ms_per_launch);
 
 #ifdef __cplusplus
 }

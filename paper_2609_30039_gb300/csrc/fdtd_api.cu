@@ -156,12 +156,6 @@ struct fdtd_ctx {
     DftItem* d_sitems = nullptr;              // DFT items of the owned planes of every slab
     std::vector<int> sitem_begin, sitem_count;
     int stream_dirty = 1;
-    // event-record nodes in the captured forward graphs (kGtPerStep per step: E start / end, H start /
-    // end on the step's stream, then DFT-of-E start / end and DFT-of-H start / end on the DFT
-    // stream), per graph key; gt_cur points at the events of the graph being captured
-    int graph_timing = 0;
-    std::vector<cudaEvent_t> gt_ev[2][2];
-    cudaEvent_t* gt_cur = nullptr;
     // instrumentation
     int prof_on = 0;
     int prof_used = 0;
@@ -880,8 +874,6 @@ fdtd_status upload_tiles(fdtd_ctx* c) {
 }
 
 // Event pair around one launch when profiling (two records on the stream, no work changed).
-constexpr int kGtPerStep = 8;   // timing events per captured step (see fdtd_ctx::gt_ev)
-
 struct Prof {
     fdtd_ctx* c;
     bool on;
@@ -980,12 +972,6 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
     if ((nd > 0 || cell) && first) launch_copy_int(l, c->d_step, c->d_base);
     if (dstream && !first) cudaStreamWaitEvent(st, c->ev_de, 0);   // DFT of E^n done before E changes
     auto cell_args = [&](int di, bool e_side) { return make_cell_args<T>(c, di, e_side); };
-    // timing nodes of a graph being captured: which = 0 / 1 around the E launches, 2 / 3 around H,
-    // 4 / 5 around the DFT of E and 6 / 7 around the DFT of H (on the stream they run on)
-    auto gt = [&](int which, cudaStream_t on) {
-        if (c->gt_cur) cudaEventRecordWithFlags(c->gt_cur[kGtPerStep * offset + which], on, cudaEventRecordExternal);
-    };
-    gt(0, st);
     if (cell) {
         Prof p(c, FDTD_KERNEL_E);
         for (int di = 0; di < (int)c->doms.size(); ++di) {
@@ -1004,28 +990,23 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
         }
         join_int();
     }
-    gt(1, st);
     if (nd > 0) {
         if (dstream) {
             cudaEventRecord(c->ev_e, st);
             cudaStreamWaitEvent(c->dft_stream, c->ev_e, 0);
         }
-        gt(4, ld.stream);
         {
             Prof p(c, FDTD_KERNEL_DFT);
             launch_dft<T>(ld, dd, c->d_mons, c->d_dft_items, nd, 0, c->d_base, offset);
         }
-        gt(5, ld.stream);
         if (dstream) cudaEventRecord(c->ev_de, c->dft_stream);
     }
     if (dstream && !first) cudaStreamWaitEvent(st, c->ev_dh, 0);   // DFT of H^{n-1/2} done
-    gt(2, st);
     if (cell) {
         {
             Prof p(c, FDTD_KERNEL_H);
             for (int di = 0; di < (int)c->doms.size(); ++di) launch_h_cell<T>(l, cell_args(di, false), (T)c->S, a);
         }
-        gt(3, st);
         if (last) launch_advance(l, c->d_step, offset + 1);
     } else {
         fork_int();
@@ -1038,19 +1019,16 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
             launch_h_update<T>(la, dd, c->d_tiles_int, ni, (T)c->S, a, 0, c->energy_on, adv);
         }
         join_int();
-        gt(3, st);
     }
     if (nd > 0) {
         if (dstream) {
             cudaEventRecord(c->ev_h, st);
             cudaStreamWaitEvent(c->dft_stream, c->ev_h, 0);
         }
-        gt(6, ld.stream);
         {
             Prof p(c, FDTD_KERNEL_DFT);
             launch_dft<T>(ld, dd, c->d_mons, c->d_dft_items, nd, 1, c->d_base, offset);
         }
-        gt(7, ld.stream);
         if (dstream) cudaEventRecord(c->ev_dh, c->dft_stream);
         if (dstream && last) cudaStreamWaitEvent(st, c->ev_dh, 0);
     }
@@ -1350,12 +1328,79 @@ fdtd_status stream_forward(fdtd_ctx* c, int n_steps) {
     return FDTD_OK;
 }
 
+// Per-cell transposed-kernel arguments of domain di.
+template <typename T>
+AdjCellArgs<T> make_adj_args(const fdtd_ctx* c, int di, int* mon) {
+    const DomainHost& h = c->doms[di];
+    AdjCellArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    for (int f = 0; f < 6; ++f) {
+        a.A[f] = (T*)h.A[f];
+        a.F[f] = (const T*)h.F[f];
+    }
+    for (int q = 0; q < 3; ++q) {
+        a.ie[q] = (const T*)h.ie[q];
+        a.cE[q] = (const T*)h.cE[q];
+        a.cH[q] = (const T*)h.cH[q];
+        a.n[q] = h.n[q];
+        a.dlo[q] = h.dlo[q];
+        a.dhi[q] = h.dhi[q];
+        a.ns[q] = h.ns[q];
+        a.per[q] = h.per[q];
+        for (int s2 = 0; s2 < 2; ++s2) {
+            a.apsiE[q][s2] = (T*)h.apsiE[q][s2];
+            a.apsiH[q][s2] = (T*)h.apsiH[q][s2];
+        }
+    }
+    a.dom = di;
+    if (h.design && h.grad) {
+        for (int q = 0; q < 3; ++q) {
+            a.glo[q] = h.glo[q];
+            a.ghi[q] = h.ghi[q];
+        }
+        a.grad = h.grad;
+    }
+    // bounding box of the monitor cells that carry an adjoint source
+    *mon = 0;
+    for (int mi : h.mons) {
+        const Mon& m = c->mons[mi].m;
+        if (!m.cot) continue;
+        for (int q = 0; q < 3; ++q) {
+            a.mlo[q] = *mon ? std::min(a.mlo[q], m.lo[q]) : m.lo[q];
+            a.mhi[q] = *mon ? std::max(a.mhi[q], m.hi[q]) : m.hi[q];
+        }
+        *mon = 1;
+    }
+    return a;
+}
+
 template <typename T>
 void adj_once(fdtd_ctx* c, int m) {
     const Launch l = L(c);
     const Dom<T>* dd = (const Dom<T>*)c->d_doms;
     int pgrad = 0;   // some domain collects pole-coefficient cotangents
     for (const auto& h : c->doms) pgrad |= h.pgc_on;
+    if (c->cell_mode) {
+        // per-cell launch mode: one launch per domain and half-step, E side first (the H side
+        // reads the lagged E cotangent it leaves)
+        std::vector<AdjCellArgs<T>> args(c->doms.size());
+        std::vector<int> mon(c->doms.size(), 0);
+        for (int di = 0; di < (int)c->doms.size(); ++di) args[di] = make_adj_args<T>(c, di, &mon[di]);
+        {
+            Prof p(c, FDTD_KERNEL_ADJ_E);
+            for (int di = 0; di < (int)c->doms.size(); ++di) {
+                const DomainHost& h = c->doms[di];
+                launch_adj_e_cell<T>(l, args[di], dd, c->d_mons, (T)c->S, m, c->adj_pending,
+                                     h.npole > 0 && h.bcell > 0, mon[di], h.pgc_on);
+            }
+        }
+        {
+            Prof p(c, FDTD_KERNEL_ADJ_H);
+            for (int di = 0; di < (int)c->doms.size(); ++di)
+                launch_adj_h_cell<T>(l, args[di], dd, c->d_mons, (T)c->S, m, mon[di]);
+        }
+        return;
+    }
     const int ng = (int)c->tiles_gen.size(), ni = (int)c->tiles_int.size();
     // as in step_once: the interior launches run on the auxiliary stream next to the general ones
     const bool fork = c->aux_stream && !c->prof_on && ng > 0 && ni > 0;
@@ -1413,11 +1458,6 @@ fdtd_status build_graph(fdtd_ctx* c) {
     const int a = c->dft_enabled, b = c->energy_on;
     if (c->graph[a][b]) return FDTD_OK;
     if (!c->cap_stream) CK(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-    if (c->graph_timing && c->gt_ev[a][b].empty()) {
-        c->gt_ev[a][b].resize(kGtPerStep * kGraphSteps, nullptr);
-        for (auto& ev : c->gt_ev[a][b]) CK(c, cudaEventCreate(&ev));
-    }
-    c->gt_cur = c->graph_timing ? c->gt_ev[a][b].data() : nullptr;
     const long long l0 = c->launches;
     CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int s = 0; s < kGraphSteps; ++s) {
@@ -1428,7 +1468,6 @@ fdtd_status build_graph(fdtd_ctx* c) {
     }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
-    c->gt_cur = nullptr;
     c->launches = l0;
     if (e != cudaSuccess) return fail(c, FDTD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&c->graph[a][b], g, 0);
@@ -1551,6 +1590,39 @@ fdtd_status stream_alloc(fdtd_ctx* c) {
         CK(c, cudaEventCreateWithFlags(&c->ev_out[s], cudaEventDisableTiming));
     }
     return FDTD_OK;
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+void time_launches_t(fdtd_ctx* c, cudaStream_t st, int which, int n, long long* counter) {
+    const Launch l{st, counter};
+    const Dom<T>* dd = (const Dom<T>*)c->d_doms;
+    StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.srcs = c->d_srcs;
+    a.mons = c->d_mons;
+    a.d_step = c->d_step;
+    a.d_ticket = c->d_ticket;
+    a.dft_on = c->dft_enabled;
+    a.dft_items = c->d_dft_items;
+    a.ndft = c->n_dft_items;
+    a.d_base = c->d_base;
+    a.offset = 0;
+    for (int r = 0; r < n; ++r) {
+        if (which == 0) {
+            for (int di = 0; di < (int)c->doms.size(); ++di) {
+                const DomainHost& h = c->doms[di];
+                launch_e_cell<T>(l, make_cell_args<T>(c, di, true), dd, (T)c->S, a, c->aniso, h.npole > 0 && h.bcell > 0);
+            }
+        } else if (which == 1) {
+            for (int di = 0; di < (int)c->doms.size(); ++di) launch_h_cell<T>(l, make_cell_args<T>(c, di, false), (T)c->S, a);
+        } else {
+            launch_dft<T>(l, dd, c->d_mons, c->d_dft_items, c->n_dft_items, 0, c->d_base, 0);
+        }
+    }
 }
 
 }  // namespace
@@ -1813,10 +1885,6 @@ fdtd_status fdtd_destroy(fdtd_ctx* ctx) {
     for (auto* v : {&ctx->ev_in, &ctx->ev_out})
         for (cudaEvent_t e : *v)
             if (e) cudaEventDestroy(e);
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b)
-            for (cudaEvent_t e : ctx->gt_ev[a][b])
-                if (e) cudaEventDestroy(e);
     for (void* p : ctx->owned) cudaFree(p);
     for (void* p : ctx->host_owned) cudaFreeHost(p);
     for (auto& s : ctx->slots) cudaFree(s.second.buf);
@@ -2722,41 +2790,48 @@ fdtd_status fdtd_launch_count(fdtd_ctx* ctx, int64_t* n) {
     return FDTD_OK;
 }
 
-fdtd_status fdtd_graph_timing(fdtd_ctx* ctx, int32_t enabled) {
+fdtd_status fdtd_time_half_steps(fdtd_ctx* ctx, int32_t which, int32_t n_launches, double* ms_per_launch) {
     GUARD(ctx);
-    if (enabled != 0 && enabled != 1) return fail(ctx, FDTD_EINVAL, "enabled must be 0 or 1");
-    if (ctx->graph_timing == enabled) return FDTD_OK;
-    drop_graphs(ctx);
-    ctx->graph_timing = enabled;
-    return FDTD_OK;
-}
-
-fdtd_status fdtd_graph_timing_read(fdtd_ctx* ctx, double* ms_e, double* ms_h, double* ms_dft, int32_t* steps) {
-    GUARD(ctx);
-    if (!ms_e || !ms_h || !ms_dft || !steps) return fail(ctx, FDTD_EINVAL, "NULL output");
-    *ms_e = *ms_h = *ms_dft = 0.0;
-    *steps = 0;
-    const int a = ctx->dft_enabled, b = ctx->energy_on;
-    if (!ctx->graph_timing || !ctx->graph[a][b] || ctx->gt_ev[a][b].empty()) return FDTD_OK;
+    NOT_STREAMED(ctx);
+    if (!ms_per_launch || which < 0 || which > 2 || n_launches < 1 || n_launches > 4096)
+        return fail(ctx, FDTD_EINVAL, "bad arguments");
+    *ms_per_launch = 0.0;
+    if (!ctx->cell_mode || ctx->energy_on || ctx->use_persistent)
+        return fail(ctx, FDTD_EINVAL, "per-cell launch mode (4) without an energy record only");
+    if (which == 2 && ctx->n_dft_items == 0) return fail(ctx, FDTD_EINVAL, "no DFT monitor");
+    if (!ctx->cap_stream) CK(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    const bool dft = ctx->dft_enabled && ctx->n_dft_items > 0;
-    const auto& ev = ctx->gt_ev[a][b];
-    double sum[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int s = 0; s < kGraphSteps; ++s)
-        for (int pair = 0; pair < (dft ? 4 : 2); ++pair) {
-            float t = 0.f;
-            const cudaError_t e = cudaEventElapsedTime(&t, ev[kGtPerStep * s + 2 * pair], ev[kGtPerStep * s + 2 * pair + 1]);
-            if (e == cudaErrorNotReady || e == cudaErrorInvalidResourceHandle) {
-                cudaGetLastError();   // the graph has not been replayed since it was built
-                return FDTD_OK;
-            }
-            CK(ctx, e);
-            sum[pair] += t;
-        }
-    *ms_e = sum[0];
-    *ms_h = sum[1];
-    *ms_dft = sum[2] + sum[3];
-    *steps = kGraphSteps;
+    launch_copy_int(L(ctx), ctx->d_step, ctx->d_base);   // phases / sources of the current step
+    CKL(ctx);
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    long long dummy = 0;
+    CK(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    if (ctx->dtype == FDTD_F32)
+        time_launches_t<float>(ctx, ctx->cap_stream, which, n_launches, &dummy);
+    else
+        time_launches_t<double>(ctx, ctx->cap_stream, which, n_launches, &dummy);
+    cudaGraph_t g = nullptr;
+    CK(ctx, cudaStreamEndCapture(ctx->cap_stream, &g));
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CK(ctx, e);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.f;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, ctx->stream);   // warm-up replay
+    if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGraphExecDestroy(ge);
+    CK(ctx, e);
+    ctx->launches += 2ll * n_launches * (which == 2 ? 1 : (long long)ctx->doms.size());
+    *ms_per_launch = (double)ms / n_launches;
     return FDTD_OK;
 }
 

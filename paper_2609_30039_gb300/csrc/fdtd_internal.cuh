@@ -268,6 +268,26 @@ struct CellArgs {
     int kz0, nzg;
 };
 
+// One domain's operands for the per-cell transposed kernels, passed by value: the adjoint fields,
+// the forward fields (material cotangent), eps^-1, the adjoint CPML memories of both half-steps
+// and the coefficient rows of both node kinds, the design box and its gradient buffer.
+template <typename T>
+struct AdjCellArgs {
+    T* A[6];
+    const T* F[6];
+    const T* ie[3];
+    T* apsiE[3][2];
+    T* apsiH[3][2];
+    const T* cE[3];
+    const T* cH[3];
+    int n[3], dlo[3], dhi[3], ns[3];
+    int per[3];
+    int dom;
+    int glo[3], ghi[3];   // design box (empty: lo = hi = 0)
+    double* grad;         // [3][design cells] or nullptr
+    int mlo[3], mhi[3];   // bounding box of the domain's monitor cells that carry adjoint sources
+};
+
 // One thread per cell over all cells of one domain (per-cell streaming launch mode).
 template <typename T>
 void launch_e_cell(const Launch& L, const CellArgs<T>& c, const Dom<T>* doms, T S, const StepArgs& a, int aniso,
@@ -295,6 +315,15 @@ void launch_adj_h(const Launch& L, const Dom<T>* doms, const Mon* mons, const Ti
                   int general);
 template <typename T>
 void launch_adj_flush(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S);
+// Per-cell transposed half-steps of one domain (one thread per cell, the forward per-cell grid).
+// poles: the domain has a pole box; mon: some monitor of the domain carries an adjoint source;
+// pole_grad: the domain collects pole-coefficient cotangents.
+template <typename T>
+void launch_adj_e_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, const Mon* mons, T S, int m,
+                       int pending, int poles, int mon, int pole_grad);
+template <typename T>
+void launch_adj_h_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, const Mon* mons, T S, int m,
+                       int mon);
 template <typename T>
 void launch_inject(const Launch& L, const Dom<T>* doms, const Mon* mons, const int* entries, int nentries,
                    long long nthreads, const long long* entry_begin, int step, int kind);

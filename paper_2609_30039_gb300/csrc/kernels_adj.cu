@@ -627,6 +627,399 @@ __global__ void k_inject(const Dom<T>* __restrict__ doms, const Mon* __restrict_
     d.A[m.comps[ci]][cidx(d.n, i, j, k)] += (T)acc;
 }
 
+// ---- per-cell transposed kernels -------------------------------------------------------------------
+// One thread per cell over the forward per-cell grid (x chunks of 32, y chunks of 8, z planes), so a
+// warp reads 128 contiguous bytes per array and every load of a thread is independent (the -1 / +1
+// neighbours come from L1 / L2).  The domain's operands arrive by value.  The algebra is that of
+// adj_e_column / adj_h_column: a gathered derivative cotangent is Dbar = ybar outside the CPML slabs
+// and ybar / kappa + c (psibar + ybar) in them, so a cell whose gather meets no slab node takes the
+// short form (differences of the cotangent fields scaled by S), decided per cell: warps diverge
+// only where a slab edge crosses them.  Poles, the material cotangent and monitor injection are
+// compiled in only where a domain needs them; pole-parameter cotangents keep the tile kernels.
+#ifndef GBFDTD_ADJ_CELL_BLOCKS_F32
+#define GBFDTD_ADJ_CELL_BLOCKS_F32 6
+#endif
+template <typename T, bool kHeavy>
+constexpr int adj_cell_blocks() {
+    return sizeof(T) == 4 ? (kHeavy ? 4 : GBFDTD_ADJ_CELL_BLOCKS_F32) : 3;
+}
+
+// Dbar of a derivative at node (i, j, k) whose coordinate along axis q is x and slab index sl
+// (-1 outside the slabs): coef is the axis' CPML row [b | c | 1/kappa], psi its memory cotangents.
+template <typename T>
+__device__ __forceinline__ T dbar_node(const T* coef, const T* psi, const int* n, const int* ns, int q, int i, int j,
+                                       int k, int x, int sl, T yb) {
+    if (sl < 0) return yb;
+    const T ps = psi[slab_off(n, ns, q, i, j, k, sl)];
+    return coef[2 * n[q] + x] * yb + coef[n[q] + x] * (ps + yb);
+}
+
+__device__ __forceinline__ bool in_box3(const int* lo, const int* hi, int i, int j, int k) {
+    return i >= lo[0] && i < hi[0] && j >= lo[1] && j < hi[1] && k >= lo[2] && k < hi[2];
+}
+
+// One E component a of the transposed E step at cell (i, j, k): completes the deferred own-cell
+// transpose of step m+1 (pending), adds the gathered cotangent gat and the monitor injection,
+// accumulates the material cotangent, and returns the new lagged value S eps^-1/(1 + eps^-1 G) Ebar.
+template <typename T, int a, bool kPoles, bool kGrad, bool kMon, bool kPG>
+__device__ __forceinline__ T adj_e_comp(const AdjCellArgs<T>& c, const Dom<T>* __restrict__ doms,
+                                        const Mon* __restrict__ mons, int i, int j, int k, long long id, T F, T ie,
+                                        T gat, T S, int m, int pending, bool disp, long long bo, const int* sl,
+                                        const long long* om, double* pacc) {
+    constexpr int q0 = (a + 1) % 3, q1 = (a + 2) % 3;
+    const int x[3] = {i, j, k};
+    T eb;
+    if (pending) {
+        if (kPoles && disp) {
+            const Dom<T>& d = doms[c.dom];
+            eb = (T(1) / ie - d.G) / S * F;
+            for (int p = 0; p < d.npole; ++p) {
+                T* pp = d.aade + ((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo;
+                T* pq = pp + d.bcell;
+                const T xp = *pp, xq = *pq;
+                eb += d.g0[p] * xp + d.g1[p] * xq;
+                *pp = d.M00[p] * xp + d.M10[p] * xq + (T(1) - d.M00[p]) / S * F;
+                *pq = d.M01[p] * xp + d.M11[p] * xq - d.M01[p] / S * F;
+            }
+        } else {
+            eb = F / (S * ie);
+        }
+        // own psibar_E of E_a's two derivatives: s = 0 along q0 (ybar = +F), s = 1 along q1 (-F)
+        if (sl[q0] >= 0) {
+            T* p = c.apsiE[a][0] + slab_off(c.n, c.ns, q0, i, j, k, sl[q0]);
+            *p = c.cE[q0][x[q0]] * (*p + F);
+        }
+        if (sl[q1] >= 0) {
+            T* p = c.apsiE[a][1] + slab_off(c.n, c.ns, q1, i, j, k, sl[q1]);
+            *p = c.cE[q1][x[q1]] * (*p - F);
+        }
+    } else {
+        eb = F;
+    }
+    eb += gat;
+    if (kMon && in_box3(c.mlo, c.mhi, i, j, k)) eb += (T)inject_at(doms[c.dom], mons, a, i, j, k, (long long)m * 2 + 0);
+    T et = eb, gdisp = T(0);
+    if (kPoles && disp) {
+        const Dom<T>& d = doms[c.dom];
+        for (int p = 0; p < d.npole; ++p) {
+            const T* pp = d.aade + ((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo;
+            et += d.g0[p] * pp[0] + d.g1[p] * pp[d.bcell];
+        }
+        gdisp = d.G;
+    }
+    const bool gcell = kGrad && in_box3(c.glo, c.ghi, i, j, k);
+    const bool pcell = kPG && disp;
+    if (gcell || pcell) {
+        // d E^{m+1} / d(eps^-1): S curl(H^{m+1/2}) of the forward state u^m (plus the pole terms);
+        // the design and pole boxes lie outside the CPML slabs, so the forward update used the
+        // plain curl
+        const T* Hq = c.F[3 + q1];
+        const T* Hb = c.F[3 + q0];
+        const T curl = (Hq[id] - Hq[id + om[q0]]) - (Hb[id] - Hb[id + om[q1]]);
+        double delta = (double)(S * curl);
+        const T e0 = c.F[a][id];
+        if (kPoles && disp) {
+            const Dom<T>& d = doms[c.dom];
+            for (int p = 0; p < d.npole; ++p) {
+                const T P = d.ade[((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo];
+                const T Q = d.ade[((long long)(a * d.npole + p) * 2 + 1) * d.bcell + bo];
+                delta += (double)(P - (d.M00[p] * P + d.M01[p] * Q) - T(2) * d.g0[p] * e0);
+            }
+        }
+        const double r = 1.0 / (1.0 + (double)ie * (double)gdisp);
+        if (gcell) {
+            const long long gi = ((long long)(k - c.glo[2]) * (c.ghi[1] - c.glo[1]) + (j - c.glo[1])) *
+                                     (c.ghi[0] - c.glo[0]) + (i - c.glo[0]);
+            const long long gn = (long long)(c.ghi[0] - c.glo[0]) * (c.ghi[1] - c.glo[1]) * (c.ghi[2] - c.glo[2]);
+            c.grad[a * gn + gi] += (double)et * delta * r * r;
+        }
+        if (pcell) {
+            // pole-coefficient cotangents (the algebra of adj_e_column): with u = xbar_P - rho et,
+            //   M00 += u P, M01 += u Q, M10 += xbar_Q P, M11 += xbar_Q Q, g0 += u es, g1 += xbar_Q es
+            const Dom<T>& d = doms[c.dom];
+            const double rho = (double)ie * r;
+            const double es = 2.0 * (double)e0 + rho * delta;
+            const double etr = (double)et * rho;
+            for (int p = 0; p < d.npole; ++p) {
+                const long long o0 = ((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo;
+                const long long o1 = o0 + d.bcell;
+                const double P = (double)d.ade[o0], Q = (double)d.ade[o1];
+                const double xq = (double)d.aade[o1];
+                const double u = (double)d.aade[o0] - etr;
+                double* pa = pacc + 6 * p;
+                pa[0] += u * P;
+                pa[1] += u * Q;
+                pa[2] += xq * P;
+                pa[3] += xq * Q;
+                pa[4] += u * es;
+                pa[5] += xq * es;
+            }
+        }
+    }
+    if (kPoles && disp) return S * ie / (T(1) + ie * gdisp) * et;
+    return S * ie * et;
+}
+
+// kPG (with kPoles): also sums the pole-coefficient cotangents of the domain (Sec. 3.1: pole parameters
+// through the transposed dispersion update): per thread, then one warp sum, a block sum in shared
+// memory and one FP64 atomic per block and coefficient into the domain's accumulator.
+template <typename T, bool kPoles, bool kGrad, bool kMon, bool kPG>
+__device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const Dom<T>* __restrict__ doms,
+                                                const Mon* __restrict__ mons, T S, int m, int pending, double* pacc) {
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const long long nxy = (long long)nx * ny;
+    const long long id = ((long long)k * ny + j) * nx + i;
+    bool hx_, hy_, hz_;   // the -1 neighbour exists (wraps on a periodic axis)
+    const long long om[3] = {nb_minus(i, nx, 1, c.per[0], &hx_), nb_minus(j, ny, nx, c.per[1], &hy_),
+                             nb_minus(k, nz, nxy, 0, &hz_)};
+    const T* Bx = c.A[3];
+    const T* By = c.A[4];
+    const T* Bz = c.A[5];
+    const T bx = Bx[id], by = By[id], bz = Bz[id];
+    const T by_zm = hz_ ? By[id + om[2]] : T(0), bx_zm = hz_ ? Bx[id + om[2]] : T(0);
+    const T bz_ym = hy_ ? Bz[id + om[1]] : T(0), bx_ym = hy_ ? Bx[id + om[1]] : T(0);
+    const T bz_xm = hx_ ? Bz[id + om[0]] : T(0), by_xm = hx_ ? By[id + om[0]] : T(0);
+    const T f0 = c.A[0][id], f1 = c.A[1][id], f2 = c.A[2][id];
+    const bool aniso = c.ie[1] != c.ie[0];
+    const T ie0 = c.ie[0][id];
+    const T ie1 = aniso ? c.ie[1][id] : ie0;
+    const T ie2 = aniso ? c.ie[2][id] : ie0;
+    // slab index of this node and of its -1 neighbour along each axis (-1: outside the slabs)
+    const int sl[3] = {c.ns[0] ? slab_of(i, c.dlo[0], c.dhi[0], nx) : -1,
+                       c.ns[1] ? slab_of(j, c.dlo[1], c.dhi[1], ny) : -1,
+                       c.ns[2] ? slab_of(k, c.dlo[2], c.dhi[2], nz) : -1};
+    const int sxm = (c.ns[0] && i > 0) ? slab_of(i - 1, c.dlo[0], c.dhi[0], nx) : -1;
+    const int sym = (c.ns[1] && j > 0) ? slab_of(j - 1, c.dlo[1], c.dhi[1], ny) : -1;
+    const int szm = (c.ns[2] && k > 0) ? slab_of(k - 1, c.dlo[2], c.dhi[2], nz) : -1;
+    // gathered transposes of the H update's derivatives: the q-derivative of H_c has ybar = -S Hbar_c
+    // for s = 0 of H_c and +S Hbar_c for s = 1; E_a gathers its two curl terms at this node and at
+    // -1.  Per axis, without a slab node among the two the Dbar are the ybar themselves.
+    T g0, g1, g2;
+    // z: H_y (s = 0) into E_x, H_x (s = 1) into E_y
+    if ((sl[2] & szm) < 0) {
+        g0 = S * (by - by_zm);
+        g1 = -(S * (bx - bx_zm));
+    } else {
+        const T tyz = dbar_node(c.cH[2], c.apsiH[1][0], c.n, c.ns, 2, i, j, k, k, sl[2], -S * by);
+        const T tyz_m = hz_ ? dbar_node(c.cH[2], c.apsiH[1][0], c.n, c.ns, 2, i, j, k - 1, k - 1, szm, -S * by_zm) : T(0);
+        const T txz = dbar_node(c.cH[2], c.apsiH[0][1], c.n, c.ns, 2, i, j, k, k, sl[2], S * bx);
+        const T txz_m = hz_ ? dbar_node(c.cH[2], c.apsiH[0][1], c.n, c.ns, 2, i, j, k - 1, k - 1, szm, S * bx_zm) : T(0);
+        g0 = tyz_m - tyz;
+        g1 = txz_m - txz;
+    }
+    // y: H_z (s = 1) into E_x, H_x (s = 0) into E_z
+    if ((sl[1] & sym) < 0) {
+        g0 -= S * (bz - bz_ym);
+        g2 = S * (bx - bx_ym);
+    } else {
+        const T tzy = dbar_node(c.cH[1], c.apsiH[2][1], c.n, c.ns, 1, i, j, k, j, sl[1], S * bz);
+        const T tzy_m = hy_ ? dbar_node(c.cH[1], c.apsiH[2][1], c.n, c.ns, 1, i, j - 1, k, j - 1, sym, S * bz_ym) : T(0);
+        const T txy = dbar_node(c.cH[1], c.apsiH[0][0], c.n, c.ns, 1, i, j, k, j, sl[1], -S * bx);
+        const T txy_m = hy_ ? dbar_node(c.cH[1], c.apsiH[0][0], c.n, c.ns, 1, i, j - 1, k, j - 1, sym, -S * bx_ym) : T(0);
+        g0 += tzy_m - tzy;
+        g2 = txy_m - txy;
+    }
+    // x: H_z (s = 0) into E_y, H_y (s = 1) into E_z
+    if ((sl[0] & sxm) < 0) {
+        g1 += S * (bz - bz_xm);
+        g2 -= S * (by - by_xm);
+    } else {
+        const T tzx = dbar_node(c.cH[0], c.apsiH[2][0], c.n, c.ns, 0, i, j, k, i, sl[0], -S * bz);
+        const T tzx_m = hx_ ? dbar_node(c.cH[0], c.apsiH[2][0], c.n, c.ns, 0, i - 1, j, k, i - 1, sxm, -S * bz_xm) : T(0);
+        const T tyx = dbar_node(c.cH[0], c.apsiH[1][1], c.n, c.ns, 0, i, j, k, i, sl[0], S * by);
+        const T tyx_m = hx_ ? dbar_node(c.cH[0], c.apsiH[1][1], c.n, c.ns, 0, i - 1, j, k, i - 1, sxm, S * by_xm) : T(0);
+        g1 += tzx_m - tzx;
+        g2 += tyx_m - tyx;
+    }
+    bool disp = false;
+    long long bo = 0;
+    if (kPoles) {
+        const Dom<T>& d = doms[c.dom];
+        disp = d.npole > 0 && in_ade_box(d, i, j, k) && d.mask[id];
+        if (disp) bo = ade_off(d, i, j, k);
+    }
+    // tangential E on a PEC plane (coordinate 0 of a non-periodic axis other than its own) is held
+    const bool pi = i == 0 && !c.per[0], pj = j == 0 && !c.per[1], pk = k == 0;
+    if (!(pj || pk))
+        c.A[0][id] = adj_e_comp<T, 0, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f0, ie0, g0, S, m, pending,
+                                                              disp, bo, sl, om, pacc);
+    if (!(pi || pk))
+        c.A[1][id] = adj_e_comp<T, 1, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f1, ie1, g1, S, m, pending,
+                                                              disp, bo, sl, om, pacc);
+    if (!(pi || pj))
+        c.A[2][id] = adj_e_comp<T, 2, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f2, ie2, g2, S, m, pending,
+                                                              disp, bo, sl, om, pacc);
+}
+
+template <typename T, bool kPoles, bool kGrad, bool kMon, bool kPG>
+__global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, kPoles || kGrad || kMon>())
+    k_adj_e_cell(const AdjCellArgs<T> c, const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, T S, int m,
+                 int pending) {
+    if (!kPG) {
+        adj_e_cell_body<T, kPoles, kGrad, kMon, false>(c, doms, mons, S, m, pending, nullptr);
+        return;
+    }
+    // every thread of the block reaches the reductions below (the domain, hence np, is the launch's)
+    const Dom<T>& d = doms[c.dom];
+    const int np = d.pgc ? d.npole : 0;
+    double acc[kMaxPole * 6];
+    for (int q = 0; q < np * 6; ++q) acc[q] = 0.0;
+    adj_e_cell_body<T, kPoles, kGrad, kMon, true>(c, doms, mons, S, m, pending, acc);
+    __shared__ double red[kTileX * kTileY / 32];
+    const int tid = threadIdx.y * kTileX + threadIdx.x;
+    for (int q = 0; q < np * 6; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[tid >> 5] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kTileX * kTileY / 32; ++w) t += red[w];
+            if (t != 0.0) atomicAdd(d.pgc + q, t);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, bool kMon>
+__global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
+    k_adj_h_cell(const AdjCellArgs<T> c, const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, T S, int m) {
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const long long nxy = (long long)nx * ny;
+    const long long id = ((long long)k * ny + j) * nx + i;
+    bool xe, ye, ze;   // the +1 neighbour exists (wraps on a periodic axis)
+    const long long ox = nb_plus(i, nx, 1, c.per[0], &xe);
+    const long long oy = nb_plus(j, ny, nx, c.per[1], &ye);
+    const long long oz = nb_plus(k, nz, nxy, 0, &ze);
+    const T* Fx = c.A[0];
+    const T* Fy = c.A[1];
+    const T* Fz = c.A[2];
+    const T fx = Fx[id], fy = Fy[id], fz = Fz[id];
+    const T fy_zp = ze ? Fy[id + oz] : T(0), fx_zp = ze ? Fx[id + oz] : T(0);
+    const T fz_yp = ye ? Fz[id + oy] : T(0), fx_yp = ye ? Fx[id + oy] : T(0);
+    const T fz_xp = xe ? Fz[id + ox] : T(0), fy_xp = xe ? Fy[id + ox] : T(0);
+    const T b0 = c.A[3][id], b1 = c.A[4][id], b2 = c.A[5][id];
+    const bool pi = i == 0 && !c.per[0], pj = j == 0 && !c.per[1], pk = k == 0;
+    const int sx = c.ns[0] ? slab_of(i, c.dlo[0], c.dhi[0], nx) : -1;
+    const int sy = c.ns[1] ? slab_of(j, c.dlo[1], c.dhi[1], ny) : -1;
+    const int sz = c.ns[2] ? slab_of(k, c.dlo[2], c.dhi[2], nz) : -1;
+    const int sxp = (c.ns[0] && i + 1 < nx) ? slab_of(i + 1, c.dlo[0], c.dhi[0], nx) : -1;
+    const int syp = (c.ns[1] && j + 1 < ny) ? slab_of(j + 1, c.dlo[1], c.dhi[1], ny) : -1;
+    const int szp = (c.ns[2] && k + 1 < nz) ? slab_of(k + 1, c.dlo[2], c.dhi[2], nz) : -1;
+    // transposes of the E update's derivatives: E_e's s = 0 derivative has ybar = +F_e, s = 1 has
+    // -F_e; H_c gathers them at this node and at +1.  PEC-held E nodes carry no cotangent (a +1 node
+    // reached by wrapping is no PEC node).  Per axis, away from PEC planes and without a slab node
+    // among the two, the Dbar are the ybar themselves.
+    const bool edge = pi || pj || pk;
+    T h0 = b0, h1 = b1, h2 = b2;
+    // z: E_y (s = 0) into H_x, E_x (s = 1) into H_y
+    if (!edge && (sz & szp) < 0) {
+        h0 += fy - fy_zp;
+        h1 += fx_zp - fx;
+    } else {
+        const T tyz_k = (pi || pk) ? T(0) : dbar_node(c.cE[2], c.apsiE[1][0], c.n, c.ns, 2, i, j, k, k, sz, fy);
+        const T tyz_n = (!ze || pi) ? T(0) : dbar_node(c.cE[2], c.apsiE[1][0], c.n, c.ns, 2, i, j, k + 1, k + 1, szp, fy_zp);
+        const T txz_k = (pj || pk) ? T(0) : dbar_node(c.cE[2], c.apsiE[0][1], c.n, c.ns, 2, i, j, k, k, sz, -fx);
+        const T txz_n = (!ze || pj) ? T(0) : dbar_node(c.cE[2], c.apsiE[0][1], c.n, c.ns, 2, i, j, k + 1, k + 1, szp, -fx_zp);
+        h0 += tyz_k - tyz_n;
+        h1 += txz_k - txz_n;
+    }
+    // y: E_z (s = 1) into H_x, E_x (s = 0) into H_z
+    if (!edge && (sy & syp) < 0) {
+        h0 += fz_yp - fz;
+        h2 += fx - fx_yp;
+    } else {
+        const T tzy = (pi || pj) ? T(0) : dbar_node(c.cE[1], c.apsiE[2][1], c.n, c.ns, 1, i, j, k, j, sy, -fz);
+        const T tzy_p = (!ye || pi) ? T(0) : dbar_node(c.cE[1], c.apsiE[2][1], c.n, c.ns, 1, i, j + 1, k, j + 1, syp, -fz_yp);
+        const T txy = (pk || pj) ? T(0) : dbar_node(c.cE[1], c.apsiE[0][0], c.n, c.ns, 1, i, j, k, j, sy, fx);
+        const T txy_p = (!ye || pk) ? T(0) : dbar_node(c.cE[1], c.apsiE[0][0], c.n, c.ns, 1, i, j + 1, k, j + 1, syp, fx_yp);
+        h0 += tzy - tzy_p;
+        h2 += txy - txy_p;
+    }
+    // x: E_z (s = 0) into H_y, E_y (s = 1) into H_z
+    if (!edge && (sx & sxp) < 0) {
+        h1 += fz - fz_xp;
+        h2 += fy_xp - fy;
+    } else {
+        const T tzx = (pi || pj) ? T(0) : dbar_node(c.cE[0], c.apsiE[2][0], c.n, c.ns, 0, i, j, k, i, sx, fz);
+        const T tzx_p = (!xe || pj) ? T(0) : dbar_node(c.cE[0], c.apsiE[2][0], c.n, c.ns, 0, i + 1, j, k, i + 1, sxp, fz_xp);
+        const T tyx = (pk || pi) ? T(0) : dbar_node(c.cE[0], c.apsiE[1][1], c.n, c.ns, 0, i, j, k, i, sx, -fy);
+        const T tyx_p = (!xe || pk) ? T(0) : dbar_node(c.cE[0], c.apsiE[1][1], c.n, c.ns, 0, i + 1, j, k, i + 1, sxp, -fy_xp);
+        h1 += tzx - tzx_p;
+        h2 += tyx - tyx_p;
+    }
+    // finish the H-side CPML transpose of step m (the E-side launch has read psibar_H)
+    if (sy >= 0) {
+        const long long o = slab_off(c.n, c.ns, 1, i, j, k, sy);
+        const T b = c.cH[1][j];
+        c.apsiH[0][0][o] = b * (c.apsiH[0][0][o] - S * b0);
+        c.apsiH[2][1][o] = b * (c.apsiH[2][1][o] + S * b2);
+    }
+    if (sz >= 0) {
+        const long long o = slab_off(c.n, c.ns, 2, i, j, k, sz);
+        const T b = c.cH[2][k];
+        c.apsiH[0][1][o] = b * (c.apsiH[0][1][o] + S * b0);
+        c.apsiH[1][0][o] = b * (c.apsiH[1][0][o] - S * b1);
+    }
+    if (sx >= 0) {
+        const long long o = slab_off(c.n, c.ns, 0, i, j, k, sx);
+        const T b = c.cH[0][i];
+        c.apsiH[1][1][o] = b * (c.apsiH[1][1][o] + S * b1);
+        c.apsiH[2][0][o] = b * (c.apsiH[2][0][o] - S * b2);
+    }
+    if (kMon && m >= 1 && in_box3(c.mlo, c.mhi, i, j, k)) {
+        const Dom<T>& d = doms[c.dom];
+        h0 += (T)inject_at(d, mons, 3, i, j, k, (long long)(m - 1) * 2 + 1);
+        h1 += (T)inject_at(d, mons, 4, i, j, k, (long long)(m - 1) * 2 + 1);
+        h2 += (T)inject_at(d, mons, 5, i, j, k, (long long)(m - 1) * 2 + 1);
+    }
+    c.A[3][id] = h0;
+    c.A[4][id] = h1;
+    c.A[5][id] = h2;
+}
+
+inline dim3 adj_cell_grid(const int* n) {
+    return dim3((unsigned)((n[0] + kTileX - 1) / kTileX), (unsigned)((n[1] + kTileY - 1) / kTileY), (unsigned)n[2]);
+}
+
+template <typename T>
+void launch_adj_e_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, const Mon* mons, T S, int m,
+                       int pending, int poles, int mon, int pole_grad) {
+    const dim3 g = adj_cell_grid(c.n), b(kTileX, kTileY);
+    const bool grad = c.grad != nullptr;
+    const int key = (poles && pole_grad ? 8 : 0) | (poles ? 4 : 0) | (grad ? 2 : 0) | (mon ? 1 : 0);
+    switch (key) {
+        case 0: k_adj_e_cell<T, false, false, false, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
+        case 1: k_adj_e_cell<T, false, false, true, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
+        case 2: k_adj_e_cell<T, false, true, false, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
+        case 3: k_adj_e_cell<T, false, true, true, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
+        case 4: k_adj_e_cell<T, true, false, false, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
+        case 5: k_adj_e_cell<T, true, false, true, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
+        case 6: k_adj_e_cell<T, true, true, false, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
+        case 7: k_adj_e_cell<T, true, true, true, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
+        case 12: k_adj_e_cell<T, true, false, false, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
+        case 13: k_adj_e_cell<T, true, false, true, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
+        case 14: k_adj_e_cell<T, true, true, false, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
+        default: k_adj_e_cell<T, true, true, true, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
+    }
+    ++*L.counter;
+}
+
+template <typename T>
+void launch_adj_h_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, const Mon* mons, T S, int m,
+                       int mon) {
+    const dim3 g = adj_cell_grid(c.n), b(kTileX, kTileY);
+    if (mon)
+        k_adj_h_cell<T, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m);
+    else
+        k_adj_h_cell<T, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m);
+    ++*L.counter;
+}
+
 template <typename T>
 void launch_adj_e(const Launch& L, const Dom<T>* doms, const Mon* mons, const Tile* tiles, int ntiles, T S, int m,
                   int pending, int general, int aniso, int pole_grad) {
@@ -678,7 +1071,11 @@ void launch_inject(const Launch& L, const Dom<T>* doms, const Mon* mons, const i
     template void launch_adj_h<T>(const Launch&, const Dom<T>*, const Mon*, const Tile*, int, T, int, int);     \
     template void launch_adj_flush<T>(const Launch&, const Dom<T>*, const Tile*, int, T);                       \
     template void launch_inject<T>(const Launch&, const Dom<T>*, const Mon*, const int*, int, long long,        \
-                                   const long long*, int, int);
+                                   const long long*, int, int);                                                 \
+    template void launch_adj_e_cell<T>(const Launch&, const AdjCellArgs<T>&, const Dom<T>*, const Mon*, T, int,  \
+                                       int, int, int, int);                                                     \
+    template void launch_adj_h_cell<T>(const Launch&, const AdjCellArgs<T>&, const Dom<T>*, const Mon*, T, int,  \
+                                       int);
 GBFDTD_INST(float)
 GBFDTD_INST(double)
 #undef GBFDTD_INST

@@ -115,9 +115,8 @@ _SIGS = {
     "fdtd_check_finite": [_ctx],
     "fdtd_synchronize": [_ctx, C.c_int32],
     "fdtd_set_wait_limit": [_ctx, C.c_int64, C.c_int32],
-    "fdtd_graph_timing": [_ctx, C.c_int32],
+    "fdtd_time_half_steps": [_ctx, C.c_int32, C.c_int32, C.POINTER(C.c_double)],
     "fdtd_measure_fp64_rate": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)],
-    "fdtd_graph_timing_read": [_ctx, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double), _i32p],
     "fdtd_launch_count": [_ctx, _i64p],
     "fdtd_count_nonfinite_noalloc": [_vp, C.c_int64, C.c_int32, _vp, _i64p],
     "fdtd_profile_begin": [_ctx, C.c_int32],
@@ -265,7 +264,6 @@ fdtd_set_adjoint_step_count = _wrap_simple("fdtd_set_adjoint_step_count")
 fdtd_check_finite = _wrap_simple("fdtd_check_finite")
 fdtd_synchronize = _wrap_simple("fdtd_synchronize")
 fdtd_set_wait_limit = _wrap_simple("fdtd_set_wait_limit")
-fdtd_graph_timing = _wrap_simple("fdtd_graph_timing")
 
 
 def fdtd_measure_fp64_rate(stream=0):
@@ -275,12 +273,11 @@ def fdtd_measure_fp64_rate(stream=0):
     return r.value, ms.value
 
 
-def fdtd_graph_timing_read(ctx):
-    """(E ms, H ms, DFT ms, steps) summed over the steps of the latest forward-graph replay."""
-    e, h, d, n = C.c_double(), C.c_double(), C.c_double(), C.c_int32()
-    _check(load().fdtd_graph_timing_read(ctx, C.byref(e), C.byref(h), C.byref(d), C.byref(n)),
-           "fdtd_graph_timing_read", ctx)
-    return e.value, h.value, d.value, n.value
+def fdtd_time_half_steps(ctx, which, n_launches=32):
+    """Milliseconds per launch of the E (0), H (1) or DFT-of-E (2) kernels, back to back in a graph."""
+    ms = C.c_double()
+    _check(load().fdtd_time_half_steps(ctx, int(which), int(n_launches), C.byref(ms)), "fdtd_time_half_steps", ctx)
+    return ms.value
 
 
 def _get_i64(name, ctx, *args):
