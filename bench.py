@@ -145,16 +145,20 @@ def alg_bytes_per_cell(sc, esz, kind):
     """Algorithmic bytes of one launch per cell (read once, write once; no temporal blocking):
     E update: E (3 R + 3 W) + H (3 R) + eps^-1 (1 R isotropic | 3 R) = 10 | 12 words;
     H update: H (3 R + 3 W) + E (3 R) = 9 words; each CPML slab membership adds 2 psi R + W
-    = 4 words per half-step (averaged over the grid)."""
+    = 4 words per half-step (averaged over the grid).
+    Transposed E (adj_e): the same 10 | 12 words on the cotangent fields; a slab membership adds the
+    two psibar_H read (gather) and the two psibar_E of the deferred own-cell part R + W = 6 words.
+    Transposed H (adj_h): 9 words; a membership adds two psibar_E read and two psibar_H R + W = 6."""
     n = sc.shape
     cells = n[0] * n[1] * n[2]
     memb = sum((sc.cpml[2 * q] + sc.cpml[2 * q + 1]) / n[q] for q in range(3))
     iso = sc.inv_eps is not None and len(sc.inv_eps) == 1
-    if kind == "e_update":
+    if kind in ("e_update", "adj_e"):
         words = 10 if iso else 12
     else:
         words = 9
-    return (words + 4 * memb) * esz, cells
+    per_memb = 6 if kind.startswith("adj") else 4
+    return (words + per_memb * memb) * esz, cells
 
 
 def run_ours(args):
@@ -292,9 +296,10 @@ def run_ours(args):
     if rank == 0 and not args.quick:
         out["e2e"] = e2e(ctx, sc, args, dev)
         out.update(extras(ctx, sc, args, dev))
+        spectra64 = out["fp64"].pop("_spectra")
         out["roofline_256"] = roofline_256(args, dev, peak)
         if not args.no_cpu:
-            cb, par = cpu_baseline(sc, args.cpu_seconds, spectra32, out["fp64"].pop("_spectra"))
+            cb, par = cpu_baseline(sc, args.cpu_seconds, spectra32, spectra64)
             out["cpu_baseline"] = cb
             if par:
                 out["parity"] = par
@@ -377,6 +382,25 @@ def extras(ctx, sc, args, dev):
     ms_adj = e0.elapsed_time(e1)
     res["adjoint"] = {"value": round(sc.cells * n_adj / (ms_adj * 1e-3) / 1e9, 3), "unit": "Gcell-steps/s",
                       "what": "transposed steps of the same grid (E and H transposes, CPML), no replay"}
+    if fdtd.fdtd_get_launch_mode(ctx.ctx) == 4:
+        # the transposed kernels back to back in a graph (CUDA events at its ends), as the forward ones
+        peak, _ = peaks()
+        kt = {"adj_e": fdtd.fdtd_time_half_steps(ctx.ctx, 3, 32), "adj_h": fdtd.fdtd_time_half_steps(ctx.ctx, 4, 32)}
+        dom = max(kt, key=kt.get)
+        bpc, ncell = alg_bytes_per_cell(sc, 4, dom)
+        ach = bpc * ncell / (kt[dom] * 1e-3) / 1e9
+        bae, _ = alg_bytes_per_cell(sc, 4, "adj_e")
+        bah, _ = alg_bytes_per_cell(sc, 4, "adj_h")
+        step_us = ms_adj * 1e3 / n_adj
+        res["adjoint"]["roofline"] = {
+            "kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4), "alg_bytes_per_launch": int(bpc * ncell),
+            "avg_launch_us": round(kt[dom] * 1e3, 3), "traffic": recorded_traffic(f"{dom}_mode4", 1),
+            "kernel_avg_us": {k: round(v * 1e3, 3) for k, v in kt.items()},
+            "step_us": round(step_us, 3), "step_effective_gbs": round((bae + bah) * ncell / (step_us * 1e-6) / 1e9, 1),
+            "timed_in": "graph of 32 back-to-back launches (CUDA events at its ends); step_us from the timed "
+                        "transposed steps above"}
+        fdtd.fdtd_adjoint_begin(ctx.ctx)
     # full checkpointed gradient: objective sum |F|^2 on the monitor plane, design = central 64^3
     from paper_2609_30039_gb300 import workloads as W
     sg = scene()

@@ -421,15 +421,17 @@ fdtd_status fdtd_profile_end(fdtd_ctx* ctx, double* ms_per_class, int64_t* launc
  * min(HBM bandwidth / bytes, this rate / FP64 instructions) per cell-step.  Synchronises. */
 fdtd_status fdtd_measure_fp64_rate(void* stream, double* fma_per_s, double* best_ms);
 
-/* Device time of one forward kernel class running back to back (instrumentation; no counterpart in
- * the paper): captures n_launches (1..4096) launches of the E update (which = 0), the H update (1)
- * or the DFT of E (2) -- the per-cell kernels of every domain, as one forward step launches them --
- * into a CUDA graph, replays it once to warm up and once between two CUDA events on the context's
- * stream, and writes the milliseconds per launch.  Only the graph is bracketed, so nothing sits
- * between the timed launches.  The launches act on the live state (fields, CPML memories, pole
- * states or DFT accumulators change as if the half-step ran 2 n_launches times at the current step
- * index): reset or restore the state afterwards.  Per-cell launch mode (4) without an energy record
- * only, and which = 2 needs a monitor (FDTD_EINVAL otherwise).  Synchronises. */
+/* Device time of one kernel class running back to back (instrumentation; no counterpart in the
+ * paper): captures n_launches (1..4096) launches of the E update (which = 0), the H update (1), the
+ * DFT of E (2), the transposed E half-step (3) or the transposed H half-step (4) -- the per-cell
+ * kernels of every domain, as one step launches them -- into a CUDA graph, replays it once to warm
+ * up and once between two CUDA events on the context's stream, and writes the milliseconds per
+ * launch.  Only the graph is bracketed, so nothing sits between the timed launches.  The launches
+ * act on the live state (forward or adjoint fields, CPML memories, pole states, DFT accumulators or
+ * the design gradient change as if the half-step ran 2 n_launches times at the current step index):
+ * reset or restore the state afterwards (fdtd_adjoint_begin for the adjoint state).  Per-cell launch
+ * mode (4) without an energy record only, and which = 2 needs a monitor (FDTD_EINVAL otherwise).
+ * Synchronises. */
 fdtd_status fdtd_time_half_steps(fdtd_ctx* ctx, int32_t which, int32_t n_launches, double* ms_per_launch);
 
 #ifdef __cplusplus

@@ -1352,6 +1352,16 @@ AdjCellArgs<T> make_adj_args(const fdtd_ctx* c, int di, int* mon) {
             a.apsiH[q][s2] = (T*)h.apsiH[q][s2];
         }
     }
+    for (int q = 0; q < 3; ++q) {
+        // E side gathers this node and -1: plain past the low slab's last node + 1 and before the
+        // high slab; H side gathers this node and +1 and must avoid PEC-held nodes (coordinate 0 of
+        // a non-periodic axis)
+        const int N = h.n[q], lo = h.ns[q] ? h.dlo[q] : 0, hi = h.ns[q] ? h.dhi[q] : 0;
+        a.elo[q] = lo > 0 ? lo + 1 : 0;
+        a.ehi[q] = N - hi;
+        a.hlo[q] = std::max(lo, h.per[q] ? 0 : 1);
+        a.hhi[q] = N - hi - (hi > 0 ? 1 : 0);
+    }
     a.dom = di;
     if (h.design && h.grad) {
         for (int q = 0; q < 3; ++q) {
@@ -1619,8 +1629,20 @@ void time_launches_t(fdtd_ctx* c, cudaStream_t st, int which, int n, long long* 
             }
         } else if (which == 1) {
             for (int di = 0; di < (int)c->doms.size(); ++di) launch_h_cell<T>(l, make_cell_args<T>(c, di, false), (T)c->S, a);
-        } else {
+        } else if (which == 2) {
             launch_dft<T>(l, dd, c->d_mons, c->d_dft_items, c->n_dft_items, 0, c->d_base, 0);
+        } else {
+            // transposed half-steps at adjoint index m = step count (no pending deferral)
+            for (int di = 0; di < (int)c->doms.size(); ++di) {
+                const DomainHost& h = c->doms[di];
+                int mon = 0;
+                const AdjCellArgs<T> aa = make_adj_args<T>(c, di, &mon);
+                const int m = (int)std::max(0ll, c->adj_step - 1);
+                if (which == 3)
+                    launch_adj_e_cell<T>(l, aa, dd, c->d_mons, (T)c->S, m, 1, h.npole > 0 && h.bcell > 0, mon, h.pgc_on);
+                else
+                    launch_adj_h_cell<T>(l, aa, dd, c->d_mons, (T)c->S, m, mon);
+            }
         }
     }
 }
@@ -2793,7 +2815,7 @@ fdtd_status fdtd_launch_count(fdtd_ctx* ctx, int64_t* n) {
 fdtd_status fdtd_time_half_steps(fdtd_ctx* ctx, int32_t which, int32_t n_launches, double* ms_per_launch) {
     GUARD(ctx);
     NOT_STREAMED(ctx);
-    if (!ms_per_launch || which < 0 || which > 2 || n_launches < 1 || n_launches > 4096)
+    if (!ms_per_launch || which < 0 || which > 4 || n_launches < 1 || n_launches > 4096)
         return fail(ctx, FDTD_EINVAL, "bad arguments");
     *ms_per_launch = 0.0;
     if (!ctx->cell_mode || ctx->energy_on || ctx->use_persistent)
@@ -2831,6 +2853,7 @@ fdtd_status fdtd_time_half_steps(fdtd_ctx* ctx, int32_t which, int32_t n_launche
     cudaGraphExecDestroy(ge);
     CK(ctx, e);
     ctx->launches += 2ll * n_launches * (which == 2 ? 1 : (long long)ctx->doms.size());
+    if (which >= 3) ctx->adj_pending = 1;   // the adjoint arrays now hold the lagged form
     *ms_per_launch = (double)ms / n_launches;
     return FDTD_OK;
 }

@@ -286,6 +286,9 @@ struct AdjCellArgs {
     int glo[3], ghi[3];   // design box (empty: lo = hi = 0)
     double* grad;         // [3][design cells] or nullptr
     int mlo[3], mhi[3];   // bounding box of the domain's monitor cells that carry adjoint sources
+    // coordinates [elo, ehi) / [hlo, hhi) per axis where the E-side (H-side) gather meets no slab
+    // node (and, H side, no PEC-held node): a cell inside on all three axes takes the plain form
+    int elo[3], ehi[3], hlo[3], hhi[3];
 };
 
 // One thread per cell over all cells of one domain (per-cell streaming launch mode).

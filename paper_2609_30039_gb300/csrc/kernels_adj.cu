@@ -637,11 +637,20 @@ __global__ void k_inject(const Dom<T>* __restrict__ doms, const Mon* __restrict_
 // only where a slab edge crosses them.  Poles, the material cotangent and monitor injection are
 // compiled in only where a domain needs them; pole-parameter cotangents keep the tile kernels.
 #ifndef GBFDTD_ADJ_CELL_BLOCKS_F32
-#define GBFDTD_ADJ_CELL_BLOCKS_F32 6
+#define GBFDTD_ADJ_CELL_BLOCKS_F32 8
 #endif
 template <typename T, bool kHeavy>
 constexpr int adj_cell_blocks() {
     return sizeof(T) == 4 ? (kHeavy ? 4 : GBFDTD_ADJ_CELL_BLOCKS_F32) : 3;
+}
+
+// Offset of cell (i, j, k) in the slab array of axis q at slab index s, written so that the part
+// depending only on the block's plane k (block-uniform) is computed in 64 bits once and the in-plane
+// part in 32 bits.
+__device__ __forceinline__ long long slab_off_c(const int* n, const int* ns, int q, int i, int j, int k, int s) {
+    if (q == 0) return (long long)k * (n[1] * ns[0]) + (j * ns[0] + s);
+    if (q == 1) return (long long)k * (ns[1] * n[0]) + (s * n[0] + i);
+    return (long long)s * ((long long)n[0] * n[1]) + (j * n[0] + i);
 }
 
 // Dbar of a derivative at node (i, j, k) whose coordinate along axis q is x and slab index sl
@@ -650,7 +659,7 @@ template <typename T>
 __device__ __forceinline__ T dbar_node(const T* coef, const T* psi, const int* n, const int* ns, int q, int i, int j,
                                        int k, int x, int sl, T yb) {
     if (sl < 0) return yb;
-    const T ps = psi[slab_off(n, ns, q, i, j, k, sl)];
+    const T ps = psi[slab_off_c(n, ns, q, i, j, k, sl)];
     return coef[2 * n[q] + x] * yb + coef[n[q] + x] * (ps + yb);
 }
 
@@ -658,9 +667,21 @@ __device__ __forceinline__ bool in_box3(const int* lo, const int* hi, int i, int
     return i >= lo[0] && i < hi[0] && j >= lo[1] && j < hi[1] && k >= lo[2] && k < hi[2];
 }
 
-// One E component a of the transposed E step at cell (i, j, k): completes the deferred own-cell
-// transpose of step m+1 (pending), adds the gathered cotangent gat and the monitor injection,
-// accumulates the material cotangent, and returns the new lagged value S eps^-1/(1 + eps^-1 G) Ebar.
+// 1 / x: a correctly rounded reciprocal in FP32 (a multiply by it replaces the IEEE division of
+// the deferred own-cell part), the exact quotient in FP64.
+__device__ __forceinline__ float recip_t(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip_t(double x) { return 1.0 / x; }
+
+// Slab index of coordinate x along an axis with CPML depths (lo, hi) over N nodes, or -1; an axis
+// without CPML (ns = 0) has none.
+__device__ __forceinline__ int slab_or_none(int x, int lo, int hi, int N, int ns) {
+    return ns ? slab_of(x, lo, hi, N) : -1;
+}
+
+// One E component a of the transposed E step at cell (i, j, k) (offset id of the whole array):
+// completes the deferred own-cell transpose of step m+1 (pending), adds the gathered cotangent gat
+// and the monitor injection, accumulates the material (and pole-coefficient) cotangents, and
+// returns the new lagged value S eps^-1 / (1 + eps^-1 G) Ebar.  om: offsets to the -1 neighbours.
 template <typename T, int a, bool kPoles, bool kGrad, bool kMon, bool kPG>
 __device__ __forceinline__ T adj_e_comp(const AdjCellArgs<T>& c, const Dom<T>* __restrict__ doms,
                                         const Mon* __restrict__ mons, int i, int j, int k, long long id, T F, T ie,
@@ -682,15 +703,15 @@ __device__ __forceinline__ T adj_e_comp(const AdjCellArgs<T>& c, const Dom<T>* _
                 *pq = d.M01[p] * xp + d.M11[p] * xq - d.M01[p] / S * F;
             }
         } else {
-            eb = F / (S * ie);
+            eb = F * recip_t(S * ie);
         }
         // own psibar_E of E_a's two derivatives: s = 0 along q0 (ybar = +F), s = 1 along q1 (-F)
         if (sl[q0] >= 0) {
-            T* p = c.apsiE[a][0] + slab_off(c.n, c.ns, q0, i, j, k, sl[q0]);
+            T* p = c.apsiE[a][0] + slab_off_c(c.n, c.ns, q0, i, j, k, sl[q0]);
             *p = c.cE[q0][x[q0]] * (*p + F);
         }
         if (sl[q1] >= 0) {
-            T* p = c.apsiE[a][1] + slab_off(c.n, c.ns, q1, i, j, k, sl[q1]);
+            T* p = c.apsiE[a][1] + slab_off_c(c.n, c.ns, q1, i, j, k, sl[q1]);
             *p = c.cE[q1][x[q1]] * (*p - F);
         }
     } else {
@@ -770,38 +791,74 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
     const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
     if (i >= nx || j >= ny) return;
     const long long nxy = (long long)nx * ny;
-    const long long id = ((long long)k * ny + j) * nx + i;
-    bool hx_, hy_, hz_;   // the -1 neighbour exists (wraps on a periodic axis)
-    const long long om[3] = {nb_minus(i, nx, 1, c.per[0], &hx_), nb_minus(j, ny, nx, c.per[1], &hy_),
-                             nb_minus(k, nz, nxy, 0, &hz_)};
-    const T* Bx = c.A[3];
-    const T* By = c.A[4];
-    const T* Bz = c.A[5];
-    const T bx = Bx[id], by = By[id], bz = Bz[id];
-    const T by_zm = hz_ ? By[id + om[2]] : T(0), bx_zm = hz_ ? Bx[id + om[2]] : T(0);
-    const T bz_ym = hy_ ? Bz[id + om[1]] : T(0), bx_ym = hy_ ? Bx[id + om[1]] : T(0);
-    const T bz_xm = hx_ ? Bz[id + om[0]] : T(0), by_xm = hx_ ? By[id + om[0]] : T(0);
-    const T f0 = c.A[0][id], f1 = c.A[1][id], f2 = c.A[2][id];
+    const long long pl = (long long)k * nxy;   // first cell of this z-plane (block-uniform)
+    const int ij = j * nx + i;                  // offset inside the plane
+    // -1 neighbours (wrapping on a periodic axis); in-plane offsets in 32 bits
+    const bool hx_ = i > 0 || c.per[0], hy_ = j > 0 || c.per[1], hz_ = k > 0;
+    const int ox = i > 0 ? -1 : nx - 1, oy = j > 0 ? -nx : (ny - 1) * nx;
+    const T* Bx = c.A[3] + pl;
+    const T* By = c.A[4] + pl;
+    const T* Bz = c.A[5] + pl;
+    const T bx = Bx[ij], by = By[ij], bz = Bz[ij];
+    const T by_zm = hz_ ? (By - nxy)[ij] : T(0), bx_zm = hz_ ? (Bx - nxy)[ij] : T(0);
+    const T bz_ym = hy_ ? Bz[ij + oy] : T(0), bx_ym = hy_ ? Bx[ij + oy] : T(0);
+    const T bz_xm = hx_ ? Bz[ij + ox] : T(0), by_xm = hx_ ? By[ij + ox] : T(0);
+    const T f0 = (c.A[0] + pl)[ij], f1 = (c.A[1] + pl)[ij], f2 = (c.A[2] + pl)[ij];
     const bool aniso = c.ie[1] != c.ie[0];
-    const T ie0 = c.ie[0][id];
-    const T ie1 = aniso ? c.ie[1][id] : ie0;
-    const T ie2 = aniso ? c.ie[2][id] : ie0;
-    // slab index of this node and of its -1 neighbour along each axis (-1: outside the slabs)
-    const int sl[3] = {c.ns[0] ? slab_of(i, c.dlo[0], c.dhi[0], nx) : -1,
-                       c.ns[1] ? slab_of(j, c.dlo[1], c.dhi[1], ny) : -1,
-                       c.ns[2] ? slab_of(k, c.dlo[2], c.dhi[2], nz) : -1};
-    const int sxm = (c.ns[0] && i > 0) ? slab_of(i - 1, c.dlo[0], c.dhi[0], nx) : -1;
-    const int sym = (c.ns[1] && j > 0) ? slab_of(j - 1, c.dlo[1], c.dhi[1], ny) : -1;
-    const int szm = (c.ns[2] && k > 0) ? slab_of(k - 1, c.dlo[2], c.dhi[2], nz) : -1;
+    const T ie0 = (c.ie[0] + pl)[ij];
+    const T ie1 = aniso ? (c.ie[1] + pl)[ij] : ie0;
+    const T ie2 = aniso ? (c.ie[2] + pl)[ij] : ie0;
+    const bool pi = i == 0 && !c.per[0], pj = j == 0 && !c.per[1], pk = k == 0;
+    const long long id = pl + ij;
+    const long long om[3] = {ox, oy, -nxy};
+    bool disp = false;
+    long long bo = 0;
+    if (kPoles) {
+        const Dom<T>& d = doms[c.dom];
+        disp = d.npole > 0 && in_ade_box(d, i, j, k) && d.mask[pl + ij];
+        if (disp) bo = ade_off(d, i, j, k);
+    }
+    // a warp (one x row of one plane) whose cells all gather no slab node takes the plain form: the
+    // derivative cotangents are S times differences of the H cotangent, and no psibar is touched
+    const unsigned am = __activemask();
+    const bool plain = (unsigned)(i - c.elo[0]) < (unsigned)(c.ehi[0] - c.elo[0]) &&
+                       (unsigned)(j - c.elo[1]) < (unsigned)(c.ehi[1] - c.elo[1]) &&
+                       (unsigned)(k - c.elo[2]) < (unsigned)(c.ehi[2] - c.elo[2]);
+    if (__all_sync(am, plain)) {
+        const int none[3] = {-1, -1, -1};
+        const T g0 = S * ((by - by_zm) - (bz - bz_ym));
+        const T g1 = S * ((bz - bz_xm) - (bx - bx_zm));
+        const T g2 = S * ((bx - bx_ym) - (by - by_xm));
+        if (!(pj || pk))
+            (c.A[0] + pl)[ij] = adj_e_comp<T, 0, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f0, ie0, g0, S,
+                                                                          m, pending, disp, bo, none, om, pacc);
+        if (!(pi || pk))
+            (c.A[1] + pl)[ij] = adj_e_comp<T, 1, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f1, ie1, g1, S,
+                                                                          m, pending, disp, bo, none, om, pacc);
+        if (!(pi || pj))
+            (c.A[2] + pl)[ij] = adj_e_comp<T, 2, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f2, ie2, g2, S,
+                                                                          m, pending, disp, bo, none, om, pacc);
+        return;
+    }
+    // slab index of this node along each axis (-1: outside the slabs); the -1 node lies in a slab
+    // only where this node is the first one past the low slab
+    const int sl[3] = {slab_or_none(i, c.dlo[0], c.dhi[0], nx, c.ns[0]), slab_or_none(j, c.dlo[1], c.dhi[1], ny, c.ns[1]),
+                       slab_or_none(k, c.dlo[2], c.dhi[2], nz, c.ns[2])};
+    // per axis, decided for the whole warp: a warp with any lane near a slab of that axis takes the
+    // general form, whose per-lane slab checks give the plain values elsewhere
+    const bool px_plain = __all_sync(am, sl[0] < 0 && !(i > 0 && i == c.dlo[0]));
+    const bool py_plain = __all_sync(am, sl[1] < 0 && !(j > 0 && j == c.dlo[1]));
+    const bool pz_plain = __all_sync(am, sl[2] < 0 && !(k > 0 && k == c.dlo[2]));
     // gathered transposes of the H update's derivatives: the q-derivative of H_c has ybar = -S Hbar_c
     // for s = 0 of H_c and +S Hbar_c for s = 1; E_a gathers its two curl terms at this node and at
     // -1.  Per axis, without a slab node among the two the Dbar are the ybar themselves.
     T g0, g1, g2;
     // z: H_y (s = 0) into E_x, H_x (s = 1) into E_y
-    if ((sl[2] & szm) < 0) {
+    if (pz_plain) {
         g0 = S * (by - by_zm);
         g1 = -(S * (bx - bx_zm));
     } else {
+        const int szm = k > 0 ? slab_or_none(k - 1, c.dlo[2], c.dhi[2], nz, c.ns[2]) : -1;
         const T tyz = dbar_node(c.cH[2], c.apsiH[1][0], c.n, c.ns, 2, i, j, k, k, sl[2], -S * by);
         const T tyz_m = hz_ ? dbar_node(c.cH[2], c.apsiH[1][0], c.n, c.ns, 2, i, j, k - 1, k - 1, szm, -S * by_zm) : T(0);
         const T txz = dbar_node(c.cH[2], c.apsiH[0][1], c.n, c.ns, 2, i, j, k, k, sl[2], S * bx);
@@ -810,10 +867,11 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
         g1 = txz_m - txz;
     }
     // y: H_z (s = 1) into E_x, H_x (s = 0) into E_z
-    if ((sl[1] & sym) < 0) {
+    if (py_plain) {
         g0 -= S * (bz - bz_ym);
         g2 = S * (bx - bx_ym);
     } else {
+        const int sym = j > 0 ? slab_or_none(j - 1, c.dlo[1], c.dhi[1], ny, c.ns[1]) : -1;
         const T tzy = dbar_node(c.cH[1], c.apsiH[2][1], c.n, c.ns, 1, i, j, k, j, sl[1], S * bz);
         const T tzy_m = hy_ ? dbar_node(c.cH[1], c.apsiH[2][1], c.n, c.ns, 1, i, j - 1, k, j - 1, sym, S * bz_ym) : T(0);
         const T txy = dbar_node(c.cH[1], c.apsiH[0][0], c.n, c.ns, 1, i, j, k, j, sl[1], -S * bx);
@@ -822,10 +880,11 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
         g2 = txy_m - txy;
     }
     // x: H_z (s = 0) into E_y, H_y (s = 1) into E_z
-    if ((sl[0] & sxm) < 0) {
+    if (px_plain) {
         g1 += S * (bz - bz_xm);
         g2 -= S * (by - by_xm);
     } else {
+        const int sxm = i > 0 ? slab_or_none(i - 1, c.dlo[0], c.dhi[0], nx, c.ns[0]) : -1;
         const T tzx = dbar_node(c.cH[0], c.apsiH[2][0], c.n, c.ns, 0, i, j, k, i, sl[0], -S * bz);
         const T tzx_m = hx_ ? dbar_node(c.cH[0], c.apsiH[2][0], c.n, c.ns, 0, i - 1, j, k, i - 1, sxm, -S * bz_xm) : T(0);
         const T tyx = dbar_node(c.cH[0], c.apsiH[1][1], c.n, c.ns, 0, i, j, k, i, sl[0], S * by);
@@ -833,24 +892,16 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
         g1 += tzx_m - tzx;
         g2 += tyx_m - tyx;
     }
-    bool disp = false;
-    long long bo = 0;
-    if (kPoles) {
-        const Dom<T>& d = doms[c.dom];
-        disp = d.npole > 0 && in_ade_box(d, i, j, k) && d.mask[id];
-        if (disp) bo = ade_off(d, i, j, k);
-    }
     // tangential E on a PEC plane (coordinate 0 of a non-periodic axis other than its own) is held
-    const bool pi = i == 0 && !c.per[0], pj = j == 0 && !c.per[1], pk = k == 0;
     if (!(pj || pk))
-        c.A[0][id] = adj_e_comp<T, 0, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f0, ie0, g0, S, m, pending,
-                                                              disp, bo, sl, om, pacc);
+        (c.A[0] + pl)[ij] = adj_e_comp<T, 0, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f0, ie0, g0, S, m,
+                                                                      pending, disp, bo, sl, om, pacc);
     if (!(pi || pk))
-        c.A[1][id] = adj_e_comp<T, 1, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f1, ie1, g1, S, m, pending,
-                                                              disp, bo, sl, om, pacc);
+        (c.A[1] + pl)[ij] = adj_e_comp<T, 1, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f1, ie1, g1, S, m,
+                                                                      pending, disp, bo, sl, om, pacc);
     if (!(pi || pj))
-        c.A[2][id] = adj_e_comp<T, 2, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f2, ie2, g2, S, m, pending,
-                                                              disp, bo, sl, om, pacc);
+        (c.A[2] + pl)[ij] = adj_e_comp<T, 2, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f2, ie2, g2, S, m,
+                                                                      pending, disp, bo, sl, om, pacc);
 }
 
 template <typename T, bool kPoles, bool kGrad, bool kMon, bool kPG>
@@ -890,37 +941,64 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
     const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
     if (i >= nx || j >= ny) return;
     const long long nxy = (long long)nx * ny;
-    const long long id = ((long long)k * ny + j) * nx + i;
-    bool xe, ye, ze;   // the +1 neighbour exists (wraps on a periodic axis)
-    const long long ox = nb_plus(i, nx, 1, c.per[0], &xe);
-    const long long oy = nb_plus(j, ny, nx, c.per[1], &ye);
-    const long long oz = nb_plus(k, nz, nxy, 0, &ze);
-    const T* Fx = c.A[0];
-    const T* Fy = c.A[1];
-    const T* Fz = c.A[2];
-    const T fx = Fx[id], fy = Fy[id], fz = Fz[id];
-    const T fy_zp = ze ? Fy[id + oz] : T(0), fx_zp = ze ? Fx[id + oz] : T(0);
-    const T fz_yp = ye ? Fz[id + oy] : T(0), fx_yp = ye ? Fx[id + oy] : T(0);
-    const T fz_xp = xe ? Fz[id + ox] : T(0), fy_xp = xe ? Fy[id + ox] : T(0);
-    const T b0 = c.A[3][id], b1 = c.A[4][id], b2 = c.A[5][id];
+    const long long pl = (long long)k * nxy;   // first cell of this z-plane (block-uniform)
+    const int ij = j * nx + i;
+    // +1 neighbours (wrapping on a periodic axis)
+    const bool xe = i + 1 < nx || c.per[0], ye = j + 1 < ny || c.per[1], ze = k + 1 < nz;
+    const int ox = i + 1 < nx ? 1 : -(nx - 1), oy = j + 1 < ny ? nx : -(ny - 1) * nx;
+    const T* Fx = c.A[0] + pl;
+    const T* Fy = c.A[1] + pl;
+    const T* Fz = c.A[2] + pl;
+    const T fx = Fx[ij], fy = Fy[ij], fz = Fz[ij];
+    const T fy_zp = ze ? (Fy + nxy)[ij] : T(0), fx_zp = ze ? (Fx + nxy)[ij] : T(0);
+    const T fz_yp = ye ? Fz[ij + oy] : T(0), fx_yp = ye ? Fx[ij + oy] : T(0);
+    const T fz_xp = xe ? Fz[ij + ox] : T(0), fy_xp = xe ? Fy[ij + ox] : T(0);
+    T* B0 = c.A[3] + pl;
+    T* B1 = c.A[4] + pl;
+    T* B2 = c.A[5] + pl;
+    const T b0 = B0[ij], b1 = B1[ij], b2 = B2[ij];
+    // a warp whose cells all gather no slab node and no PEC-held node takes the plain form
+    const unsigned am = __activemask();
+    const bool plain = (unsigned)(i - c.hlo[0]) < (unsigned)(c.hhi[0] - c.hlo[0]) &&
+                       (unsigned)(j - c.hlo[1]) < (unsigned)(c.hhi[1] - c.hlo[1]) &&
+                       (unsigned)(k - c.hlo[2]) < (unsigned)(c.hhi[2] - c.hlo[2]);
+    if (__all_sync(am, plain)) {
+        T h0 = b0 + (fy - fy_zp) + (fz_yp - fz);
+        T h1 = b1 + (fz - fz_xp) + (fx_zp - fx);
+        T h2 = b2 + (fx - fx_yp) + (fy_xp - fy);
+        if (kMon && m >= 1 && in_box3(c.mlo, c.mhi, i, j, k)) {
+            const Dom<T>& d = doms[c.dom];
+            h0 += (T)inject_at(d, mons, 3, i, j, k, (long long)(m - 1) * 2 + 1);
+            h1 += (T)inject_at(d, mons, 4, i, j, k, (long long)(m - 1) * 2 + 1);
+            h2 += (T)inject_at(d, mons, 5, i, j, k, (long long)(m - 1) * 2 + 1);
+        }
+        B0[ij] = h0;
+        B1[ij] = h1;
+        B2[ij] = h2;
+        return;
+    }
     const bool pi = i == 0 && !c.per[0], pj = j == 0 && !c.per[1], pk = k == 0;
-    const int sx = c.ns[0] ? slab_of(i, c.dlo[0], c.dhi[0], nx) : -1;
-    const int sy = c.ns[1] ? slab_of(j, c.dlo[1], c.dhi[1], ny) : -1;
-    const int sz = c.ns[2] ? slab_of(k, c.dlo[2], c.dhi[2], nz) : -1;
-    const int sxp = (c.ns[0] && i + 1 < nx) ? slab_of(i + 1, c.dlo[0], c.dhi[0], nx) : -1;
-    const int syp = (c.ns[1] && j + 1 < ny) ? slab_of(j + 1, c.dlo[1], c.dhi[1], ny) : -1;
-    const int szp = (c.ns[2] && k + 1 < nz) ? slab_of(k + 1, c.dlo[2], c.dhi[2], nz) : -1;
+    const bool edge = pi || pj || pk;
+    // slab index of this node along each axis; the +1 node lies in a slab only where this node is
+    // the last one before the high slab
+    const int sx = slab_or_none(i, c.dlo[0], c.dhi[0], nx, c.ns[0]);
+    const int sy = slab_or_none(j, c.dlo[1], c.dhi[1], ny, c.ns[1]);
+    const int sz = slab_or_none(k, c.dlo[2], c.dhi[2], nz, c.ns[2]);
+    // per axis, decided for the whole warp (see k_adj_e_cell)
+    const bool px_plain = __all_sync(am, !edge && sx < 0 && !(c.dhi[0] > 0 && i + 1 == nx - c.dhi[0]));
+    const bool py_plain = __all_sync(am, !edge && sy < 0 && !(c.dhi[1] > 0 && j + 1 == ny - c.dhi[1]));
+    const bool pz_plain = __all_sync(am, !edge && sz < 0 && !(c.dhi[2] > 0 && k + 1 == nz - c.dhi[2]));
     // transposes of the E update's derivatives: E_e's s = 0 derivative has ybar = +F_e, s = 1 has
     // -F_e; H_c gathers them at this node and at +1.  PEC-held E nodes carry no cotangent (a +1 node
     // reached by wrapping is no PEC node).  Per axis, away from PEC planes and without a slab node
     // among the two, the Dbar are the ybar themselves.
-    const bool edge = pi || pj || pk;
     T h0 = b0, h1 = b1, h2 = b2;
     // z: E_y (s = 0) into H_x, E_x (s = 1) into H_y
-    if (!edge && (sz & szp) < 0) {
+    if (pz_plain) {
         h0 += fy - fy_zp;
         h1 += fx_zp - fx;
     } else {
+        const int szp = k + 1 < nz ? slab_or_none(k + 1, c.dlo[2], c.dhi[2], nz, c.ns[2]) : -1;
         const T tyz_k = (pi || pk) ? T(0) : dbar_node(c.cE[2], c.apsiE[1][0], c.n, c.ns, 2, i, j, k, k, sz, fy);
         const T tyz_n = (!ze || pi) ? T(0) : dbar_node(c.cE[2], c.apsiE[1][0], c.n, c.ns, 2, i, j, k + 1, k + 1, szp, fy_zp);
         const T txz_k = (pj || pk) ? T(0) : dbar_node(c.cE[2], c.apsiE[0][1], c.n, c.ns, 2, i, j, k, k, sz, -fx);
@@ -929,10 +1007,11 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
         h1 += txz_k - txz_n;
     }
     // y: E_z (s = 1) into H_x, E_x (s = 0) into H_z
-    if (!edge && (sy & syp) < 0) {
+    if (py_plain) {
         h0 += fz_yp - fz;
         h2 += fx - fx_yp;
     } else {
+        const int syp = j + 1 < ny ? slab_or_none(j + 1, c.dlo[1], c.dhi[1], ny, c.ns[1]) : -1;
         const T tzy = (pi || pj) ? T(0) : dbar_node(c.cE[1], c.apsiE[2][1], c.n, c.ns, 1, i, j, k, j, sy, -fz);
         const T tzy_p = (!ye || pi) ? T(0) : dbar_node(c.cE[1], c.apsiE[2][1], c.n, c.ns, 1, i, j + 1, k, j + 1, syp, -fz_yp);
         const T txy = (pk || pj) ? T(0) : dbar_node(c.cE[1], c.apsiE[0][0], c.n, c.ns, 1, i, j, k, j, sy, fx);
@@ -941,10 +1020,11 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
         h2 += txy - txy_p;
     }
     // x: E_z (s = 0) into H_y, E_y (s = 1) into H_z
-    if (!edge && (sx & sxp) < 0) {
+    if (px_plain) {
         h1 += fz - fz_xp;
         h2 += fy_xp - fy;
     } else {
+        const int sxp = i + 1 < nx ? slab_or_none(i + 1, c.dlo[0], c.dhi[0], nx, c.ns[0]) : -1;
         const T tzx = (pi || pj) ? T(0) : dbar_node(c.cE[0], c.apsiE[2][0], c.n, c.ns, 0, i, j, k, i, sx, fz);
         const T tzx_p = (!xe || pj) ? T(0) : dbar_node(c.cE[0], c.apsiE[2][0], c.n, c.ns, 0, i + 1, j, k, i + 1, sxp, fz_xp);
         const T tyx = (pk || pi) ? T(0) : dbar_node(c.cE[0], c.apsiE[1][1], c.n, c.ns, 0, i, j, k, i, sx, -fy);
@@ -954,19 +1034,19 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
     }
     // finish the H-side CPML transpose of step m (the E-side launch has read psibar_H)
     if (sy >= 0) {
-        const long long o = slab_off(c.n, c.ns, 1, i, j, k, sy);
+        const long long o = slab_off_c(c.n, c.ns, 1, i, j, k, sy);
         const T b = c.cH[1][j];
         c.apsiH[0][0][o] = b * (c.apsiH[0][0][o] - S * b0);
         c.apsiH[2][1][o] = b * (c.apsiH[2][1][o] + S * b2);
     }
     if (sz >= 0) {
-        const long long o = slab_off(c.n, c.ns, 2, i, j, k, sz);
+        const long long o = slab_off_c(c.n, c.ns, 2, i, j, k, sz);
         const T b = c.cH[2][k];
         c.apsiH[0][1][o] = b * (c.apsiH[0][1][o] + S * b0);
         c.apsiH[1][0][o] = b * (c.apsiH[1][0][o] - S * b1);
     }
     if (sx >= 0) {
-        const long long o = slab_off(c.n, c.ns, 0, i, j, k, sx);
+        const long long o = slab_off_c(c.n, c.ns, 0, i, j, k, sx);
         const T b = c.cH[0][i];
         c.apsiH[1][1][o] = b * (c.apsiH[1][1][o] + S * b1);
         c.apsiH[2][0][o] = b * (c.apsiH[2][0][o] - S * b2);
@@ -977,9 +1057,9 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
         h1 += (T)inject_at(d, mons, 4, i, j, k, (long long)(m - 1) * 2 + 1);
         h2 += (T)inject_at(d, mons, 5, i, j, k, (long long)(m - 1) * 2 + 1);
     }
-    c.A[3][id] = h0;
-    c.A[4][id] = h1;
-    c.A[5][id] = h2;
+    B0[ij] = h0;
+    B1[ij] = h1;
+    B2[ij] = h2;
 }
 
 inline dim3 adj_cell_grid(const int* n) {

@@ -274,7 +274,8 @@ def fdtd_measure_fp64_rate(stream=0):
 
 
 def fdtd_time_half_steps(ctx, which, n_launches=32):
-    """Milliseconds per launch of the E (0), H (1) or DFT-of-E (2) kernels, back to back in a graph."""
+    """Milliseconds per launch of the E (0), H (1), DFT-of-E (2), transposed E (3) or transposed H (4)
+    kernels, back to back in a graph."""
     ms = C.c_double()
     _check(load().fdtd_time_half_steps(ctx, int(which), int(n_launches), C.byref(ms)), "fdtd_time_half_steps", ctx)
     return ms.value
