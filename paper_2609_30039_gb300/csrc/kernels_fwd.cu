@@ -613,6 +613,8 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
         if (!pz) c.F[2][id] = fma_t(S * iez, (yz1 - yz2), ez - sz);
         return;
     }
+    // in-slab CPML corrections (the coefficients are read per derivative: loading them once per axis
+    // measured slower here, unlike in k_h_cell)
     if (c.ns[2]) {
         const int sl = slab_of(kg, c.dlo[2], c.dhi[2], c.nzg);
         if (sl >= 0) {
@@ -701,28 +703,32 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
             c.F[5][id] = fma_t(-S, (yz1 - yz2), hz - mz);
             return;
         }
+        // in-slab CPML corrections; each axis' coefficients are loaded once for its two derivatives
         if (c.ns[2]) {
             const int sl = slab_of(kg, c.dlo[2], c.dhi[2], c.nzg);
             if (sl >= 0) {
                 const long long o = ((long long)sl * ny + j) * nx + i;
-                yx2 = cpml_cell(c.coef[2], c.nzg, kg, c.psi[0][1] + o, yx2);
-                yy1 = cpml_cell(c.coef[2], c.nzg, kg, c.psi[1][0] + o, yy1);
+                const T b = c.coef[2][kg], cc = c.coef[2][c.nzg + kg], kk = c.coef[2][2 * c.nzg + kg];
+                yx2 = cpml_rec(b, cc, kk, c.psi[0][1] + o, yx2);
+                yy1 = cpml_rec(b, cc, kk, c.psi[1][0] + o, yy1);
             }
         }
         if (c.ns[0]) {
             const int sl = slab_of(i, c.dlo[0], c.dhi[0], nx);
             if (sl >= 0) {
                 const long long o = ((long long)k * ny + j) * c.ns[0] + sl;
-                yy2 = cpml_cell(c.coef[0], nx, i, c.psi[1][1] + o, yy2);
-                yz1 = cpml_cell(c.coef[0], nx, i, c.psi[2][0] + o, yz1);
+                const T b = c.coef[0][i], cc = c.coef[0][nx + i], kk = c.coef[0][2 * nx + i];
+                yy2 = cpml_rec(b, cc, kk, c.psi[1][1] + o, yy2);
+                yz1 = cpml_rec(b, cc, kk, c.psi[2][0] + o, yz1);
             }
         }
         if (c.ns[1]) {
             const int sl = slab_of(j, c.dlo[1], c.dhi[1], ny);
             if (sl >= 0) {
                 const long long o = ((long long)k * c.ns[1] + sl) * nx + i;
-                yx1 = cpml_cell(c.coef[1], ny, j, c.psi[0][0] + o, yx1);
-                yz2 = cpml_cell(c.coef[1], ny, j, c.psi[2][1] + o, yz2);
+                const T b = c.coef[1][j], cc = c.coef[1][ny + j], kk = c.coef[1][2 * ny + j];
+                yx1 = cpml_rec(b, cc, kk, c.psi[0][0] + o, yx1);
+                yz2 = cpml_rec(b, cc, kk, c.psi[2][1] + o, yz2);
             }
         }
         T hx1 = fma_t(-S, (yx1 - yx2), hx);
