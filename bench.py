@@ -601,6 +601,9 @@ def main():
                     choices=["cpml128", "pec32", "batched", "adjoint256", "large640", "reversible256", "streamed", "poles"],
                     help="cpml128 is the benchmark line; the others measure the remaining workloads")
     ap.add_argument("--fd-cells", type=int, default=20)
+    ap.add_argument("--fp64-ref", action="store_true",
+                    help="--workload large640: also an FP64 gradient as the reference of both snapshot codecs")
+    ap.add_argument("--fp64-ref-slots", type=int, default=8)
     ap.add_argument("--stream-n", type=int, default=768, help="--workload streamed: grid edge")
     ap.add_argument("--slab", type=int, default=256, help="--workload streamed: owned planes per slab")
     ap.add_argument("--halo", type=int, default=32, help="--workload streamed: halo planes (steps per batch)")
@@ -969,6 +972,20 @@ def measure_large640(args):
         ctx.close()
     a, b = grads["fp32_snapshots"], grads["bf16_snapshots"]
     res["bf16_vs_fp32_snapshot_gradient_rel_l2"] = float(np.linalg.norm(b - a) / np.linalg.norm(a))
+    if args.fp64_ref:
+        # reference: the same checkpointed gradient in FP64 arithmetic with exact (native) snapshots;
+        # fewer slots keep the FP64 snapshots within HBM (more replay, same result: replay is exact)
+        slots64 = max(2, args.fp64_ref_slots)
+        ctx = fdtd.Context([sc], dtype="f64")
+        t0 = time.perf_counter()
+        (J64, _), g64, stats = ADJ.DesignAdjoint(ctx, slots=slots64).run(sc.n_steps, loss)
+        torch.cuda.synchronize()
+        res["fp64_reference"] = {"J": J64, "seconds": round(time.perf_counter() - t0, 2), "slots": slots64,
+                                 "forward_steps_incl_replay": stats["forward_steps"]}
+        r = g64[0].cpu().numpy()
+        ctx.close()
+        for name in ("fp32_snapshots", "bf16_snapshots"):
+            res[name]["gradient_rel_l2_vs_fp64"] = float(np.linalg.norm(grads[name] - r) / np.linalg.norm(r))
     print(json.dumps(res))
 
 

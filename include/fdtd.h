@@ -166,6 +166,21 @@ fdtd_status fdtd_dft_flux(fdtd_ctx* ctx, int32_t monitor, double* flux_host, int
  * launch mode. */
 fdtd_status fdtd_set_periodic(fdtd_ctx* ctx, int32_t domain, const int32_t periodic[3]);
 
+/* Bloch-periodic faces (Sec. 2.2: periodic pairs with a fixed Bloch phase; Sec. 3.1: transposed
+ * with conjugate seam factors).  phase[q] = k_q N_q (radians) for the x and y axes: a field continued
+ * across the seam of axis q picks up p_q = exp(i phase[q]), f(x + N_q) = p_q f(x), so the E update's
+ * backward differences read f(-1) = conj(p) f(N - 1) and the H update's forward differences
+ * f(N) = p f(0).  The domain's fields become complex: the field parts 0..5 hold the real parts and
+ * six more parts (ids 18 + 6 n_poles + c, c = 0..5, i.e. 18..23) the imaginary parts, forward
+ * (which = 0) and adjoint (which = 1; the adjoint is taken under <u, v> = sum conj(u) v).  A nonzero
+ * phase needs that axis periodic (fdtd_set_periodic first).  Scope: the domain has no CPML slabs
+ * (PEC z faces), no poles, no DFT monitor and no design box; soft sources add their (real) waveform
+ * to the real part; the context steps in launch mode 4 without an energy record, and autotuning, the
+ * backward step and kernel timing are not available.  FDTD_EINVAL otherwise.  The first call on a
+ * domain allocates the imaginary parts (zero) and frees every snapshot slot; later calls only
+ * change the phases.  Forward and transposed steps then run the Bloch kernels for this domain. */
+fdtd_status fdtd_set_bloch(fdtd_ctx* ctx, int32_t domain, const double phase[2]);
+
 /* Soft source (Sec. 2.4, Eq. (yee) s and m): after the update of `component` in forward
  * step n, every cell of the half-open box [lo, hi) gets += waveform[n] (no effect for
  * n >= n_steps).  waveform: host, copied, FP64.  *source_id may be NULL.  An electric source

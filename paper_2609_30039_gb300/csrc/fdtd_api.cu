@@ -53,6 +53,12 @@ struct DomainHost {
     int pgc_on = 0;                // collected by the transposed steps
     const void* tmaps = nullptr;   // this domain's kTmaMaps tensor maps in device memory
     int tma = 0;                   // maps encoded for the current field and eps^-1 pointers
+    // Bloch-periodic faces (Sec. 2.2): complex fields, the imaginary parts of the forward and
+    // adjoint fields in FI / AI, phase per period of the x and y seams
+    int bloch = 0;
+    double bphase[2] = {0.0, 0.0};
+    void* FI[6] = {};
+    void* AI[6] = {};
 };
 
 struct MonHost {
@@ -319,7 +325,7 @@ void pole_coef_deriv(const fdtd_pole& p, int wrt, double dc[6]) {
 }
 
 long long part_size(const DomainHost& d, int part) {
-    if (part < 6) return d.ncell;
+    if (part < 6 || part >= 18 + 6 * d.npole) return d.ncell;   // fields (real, then a Bloch domain's imaginary)
     if (part < 18) {
         const int a = ((part - 6) % 6) / 2, s = (part - 6) % 2;
         const int ax = (a + 1 + s) % 3;
@@ -328,10 +334,11 @@ long long part_size(const DomainHost& d, int part) {
     return d.bcell;
 }
 
-int part_count(const DomainHost& d) { return 18 + 6 * d.npole; }
+int part_count(const DomainHost& d) { return 18 + 6 * d.npole + (d.bloch ? 6 : 0); }
 
 void* part_ptr(const DomainHost& d, int which, int part, size_t esz) {
     if (part < 6) return which ? d.A[part] : d.F[part];
+    if (part >= 18 + 6 * d.npole) return which ? d.AI[part - 18 - 6 * d.npole] : d.FI[part - 18 - 6 * d.npole];
     if (part < 12) {
         const int a = (part - 6) / 2, s = (part - 6) % 2;
         return which ? d.apsiE[a][s] : d.psiE[a][s];
@@ -347,7 +354,7 @@ void* part_ptr(const DomainHost& d, int which, int part, size_t esz) {
 
 // Outermost extent of a part's array (slabs of the BF16 codec).
 long long part_planes(const DomainHost& d, int part) {
-    if (part < 6) return d.n[2];
+    if (part < 6 || part >= 18 + 6 * d.npole) return d.n[2];
     if (part < 18) {
         const int a = ((part - 6) % 6) / 2, s = (part - 6) % 2;
         const int ax = (a + 1 + s) % 3;
@@ -620,6 +627,17 @@ fdtd_status sync_srcs(fdtd_ctx* c) {
 }
 
 bool valid_dom(const fdtd_ctx* c, int d) { return d >= 0 && d < (int)c->doms.size(); }
+
+bool any_bloch(const fdtd_ctx* c) {
+    for (const auto& d : c->doms)
+        if (d.bloch) return true;
+    return false;
+}
+
+#define NOT_BLOCH(ctx, what)                                                                       \
+    do {                                                                                           \
+        if (any_bloch(ctx)) return fail((ctx), FDTD_EINVAL, std::string(what) + " is not available with Bloch domains"); \
+    } while (0)
 
 bool valid_box(const DomainHost& d, const int32_t lo[3], const int32_t hi[3]) {
     for (int q = 0; q < 3; ++q)
@@ -972,11 +990,25 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
     if ((nd > 0 || cell) && first) launch_copy_int(l, c->d_step, c->d_base);
     if (dstream && !first) cudaStreamWaitEvent(st, c->ev_de, 0);   // DFT of E^n done before E changes
     auto cell_args = [&](int di, bool e_side) { return make_cell_args<T>(c, di, e_side); };
+    auto bloch_args = [&](int di, bool e_side) {
+        const DomainHost& h = c->doms[di];
+        BlochArgs<T> b;
+        b.c = make_cell_args<T>(c, di, e_side);
+        for (int f = 0; f < 6; ++f) b.FI[f] = (T*)h.FI[f];
+        for (int q = 0; q < 2; ++q) {
+            b.pr[q] = (T)std::cos(h.bphase[q]);
+            b.pi[q] = (T)std::sin(h.bphase[q]);
+        }
+        return b;
+    };
     if (cell) {
         Prof p(c, FDTD_KERNEL_E);
         for (int di = 0; di < (int)c->doms.size(); ++di) {
             const DomainHost& h = c->doms[di];
-            launch_e_cell<T>(l, cell_args(di, true), dd, (T)c->S, a, c->aniso, h.npole > 0 && h.bcell > 0);
+            if (h.bloch)
+                launch_e_bloch<T>(l, bloch_args(di, true), (T)c->S, a);
+            else
+                launch_e_cell<T>(l, cell_args(di, true), dd, (T)c->S, a, c->aniso, h.npole > 0 && h.bcell > 0);
         }
     } else {
         fork_int();
@@ -1005,7 +1037,12 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
     if (cell) {
         {
             Prof p(c, FDTD_KERNEL_H);
-            for (int di = 0; di < (int)c->doms.size(); ++di) launch_h_cell<T>(l, cell_args(di, false), (T)c->S, a);
+            for (int di = 0; di < (int)c->doms.size(); ++di) {
+                if (c->doms[di].bloch)
+                    launch_h_bloch<T>(l, bloch_args(di, false), (T)c->S, a);
+                else
+                    launch_h_cell<T>(l, cell_args(di, false), (T)c->S, a);
+            }
         }
         if (last) launch_advance(l, c->d_step, offset + 1);
     } else {
@@ -1384,6 +1421,20 @@ AdjCellArgs<T> make_adj_args(const fdtd_ctx* c, int di, int* mon) {
     return a;
 }
 
+// Transposed-kernel arguments of a Bloch domain (its real-part arguments a).
+template <typename T>
+AdjBlochArgs<T> make_adj_bloch(const fdtd_ctx* c, int di, const AdjCellArgs<T>& a) {
+    const DomainHost& h = c->doms[di];
+    AdjBlochArgs<T> b;
+    b.c = a;
+    for (int f = 0; f < 6; ++f) b.AI[f] = (T*)h.AI[f];
+    for (int q = 0; q < 2; ++q) {
+        b.pr[q] = (T)std::cos(h.bphase[q]);
+        b.pi[q] = (T)std::sin(h.bphase[q]);
+    }
+    return b;
+}
+
 template <typename T>
 void adj_once(fdtd_ctx* c, int m) {
     const Launch l = L(c);
@@ -1400,14 +1451,21 @@ void adj_once(fdtd_ctx* c, int m) {
             Prof p(c, FDTD_KERNEL_ADJ_E);
             for (int di = 0; di < (int)c->doms.size(); ++di) {
                 const DomainHost& h = c->doms[di];
-                launch_adj_e_cell<T>(l, args[di], dd, c->d_mons, (T)c->S, m, c->adj_pending,
-                                     h.npole > 0 && h.bcell > 0, mon[di], h.pgc_on);
+                if (h.bloch)
+                    launch_adj_e_bloch<T>(l, make_adj_bloch<T>(c, di, args[di]), (T)c->S, c->adj_pending);
+                else
+                    launch_adj_e_cell<T>(l, args[di], dd, c->d_mons, (T)c->S, m, c->adj_pending,
+                                         h.npole > 0 && h.bcell > 0, mon[di], h.pgc_on);
             }
         }
         {
             Prof p(c, FDTD_KERNEL_ADJ_H);
-            for (int di = 0; di < (int)c->doms.size(); ++di)
-                launch_adj_h_cell<T>(l, args[di], dd, c->d_mons, (T)c->S, m, mon[di]);
+            for (int di = 0; di < (int)c->doms.size(); ++di) {
+                if (c->doms[di].bloch)
+                    launch_adj_h_bloch<T>(l, make_adj_bloch<T>(c, di, args[di]));
+                else
+                    launch_adj_h_cell<T>(l, args[di], dd, c->d_mons, (T)c->S, m, mon[di]);
+            }
         }
         return;
     }
@@ -1503,6 +1561,16 @@ fdtd_status flush_adjoint(fdtd_ctx* c) {
         launch_adj_flush<float>(L(c), (const Dom<float>*)c->d_doms, c->d_tiles, (int)c->tiles.size(), (float)c->S);
     else
         launch_adj_flush<double>(L(c), (const Dom<double>*)c->d_doms, c->d_tiles, (int)c->tiles.size(), c->S);
+    for (int di = 0; di < (int)c->doms.size(); ++di) {
+        if (!c->doms[di].bloch) continue;   // the imaginary E part of a Bloch domain
+        int mon = 0;
+        if (c->dtype == FDTD_F32)
+            launch_adj_flush_bloch<float>(L(c), make_adj_bloch<float>(c, di, make_adj_args<float>(c, di, &mon)),
+                                          (float)c->S);
+        else
+            launch_adj_flush_bloch<double>(L(c), make_adj_bloch<double>(c, di, make_adj_args<double>(c, di, &mon)),
+                                           c->S);
+    }
     CKL(c);
     c->adj_pending = 0;
     return FDTD_OK;
@@ -1952,6 +2020,41 @@ fdtd_status fdtd_set_periodic(fdtd_ctx* ctx, int32_t domain, const int32_t perio
     return sync_doms(ctx);
 }
 
+fdtd_status fdtd_set_bloch(fdtd_ctx* ctx, int32_t domain, const double phase[2]) {
+    GUARD(ctx);
+    NOT_STREAMED(ctx);
+    if (!ctx->cell_mode || ctx->energy_on)
+        return fail(ctx, FDTD_EINVAL, "Bloch domains step in launch mode 4 without an energy record");
+    if (!valid_dom(ctx, domain) || !phase || !std::isfinite(phase[0]) || !std::isfinite(phase[1]))
+        return fail(ctx, FDTD_EINVAL, "bad domain or phase");
+    DomainHost& d = ctx->doms[domain];
+    for (int q = 0; q < 2; ++q)
+        if (phase[q] != 0.0 && !d.per[q])
+            return fail(ctx, FDTD_EINVAL, "a Bloch phase needs a periodic axis (fdtd_set_periodic first)");
+    if (d.ns[0] || d.ns[1] || d.ns[2] || d.npole > 0 || !d.mons.empty() || d.design)
+        return fail(ctx, FDTD_EINVAL, "a Bloch domain has no CPML slabs, poles, DFT monitors or design box");
+    if (!d.bloch) {
+        // the state gains six parts: snapshots and the snapshot part table start afresh
+        fdtd_status st = fdtd_snapshots_free(ctx);
+        if (st != FDTD_OK) return st;
+        if (ctx->d_snapsegs) {
+            dfree(ctx, ctx->d_snapsegs);
+            ctx->d_snapsegs = nullptr;
+            ctx->n_snapsegs = 0;
+        }
+        for (int f = 0; f < 6; ++f) {
+            st = dmalloc(ctx, &d.FI[f], (size_t)d.ncell * ctx->esz);
+            if (st == FDTD_OK) st = dmalloc(ctx, &d.AI[f], (size_t)d.ncell * ctx->esz);
+            if (st != FDTD_OK) return st;
+        }
+        d.bloch = 1;
+    }
+    d.bphase[0] = phase[0];
+    d.bphase[1] = phase[1];
+    drop_graphs(ctx);   // captured launches hold the kernels and phases of the old configuration
+    return FDTD_OK;
+}
+
 fdtd_status fdtd_set_material(fdtd_ctx* ctx, int32_t domain, const fdtd_material* m) {
     GUARD(ctx);
     if (!valid_dom(ctx, domain) || !m) return fail(ctx, FDTD_EINVAL, "bad domain or material");
@@ -2038,6 +2141,7 @@ fdtd_status fdtd_add_dft_monitor(fdtd_ctx* ctx, int32_t domain, const int32_t lo
         component_mask == 0)
         return fail(ctx, FDTD_EINVAL, "bad monitor arguments");
     DomainHost& d = ctx->doms[domain];
+    if (d.bloch) return fail(ctx, FDTD_EINVAL, "a Bloch domain carries no DFT monitor");
     if (!valid_box(d, lo, hi)) return fail(ctx, FDTD_EINVAL, "monitor box outside the domain");
     if ((int)d.mons.size() >= kMaxMonPerDom) return fail(ctx, FDTD_EINVAL, "at most 8 monitors per domain");
     MonHost mh;
@@ -2120,6 +2224,7 @@ fdtd_status fdtd_dft_enable(fdtd_ctx* ctx, int32_t enabled) {
 fdtd_status fdtd_enable_energy(fdtd_ctx* ctx, int32_t capacity) {
     GUARD(ctx);
     NOT_STREAMED(ctx);
+    NOT_BLOCH(ctx, "the energy record");
     if (capacity < 1) return fail(ctx, FDTD_EINVAL, "capacity must be >= 1");
     for (auto& d : ctx->doms) {
         if (d.energy) dfree(ctx, d.energy);
@@ -2145,6 +2250,8 @@ fdtd_status fdtd_energy_read(fdtd_ctx* ctx, int32_t domain, double* host_dst, in
 fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
     GUARD(ctx);
     if (n_steps < 0) return fail(ctx, FDTD_EINVAL, "n_steps < 0");
+    if (any_bloch(ctx) && (!ctx->cell_mode || ctx->energy_on))
+        return fail(ctx, FDTD_EINVAL, "Bloch domains step in launch mode 4 without an energy record");
     if (ctx->step + n_steps >= (1ll << 30)) return fail(ctx, FDTD_EINVAL, "step count overflow");
     if (!ctx->mons.empty()) {
         bool changed = false;
@@ -2217,6 +2324,7 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
 fdtd_status fdtd_step_backward(fdtd_ctx* ctx, int32_t n_steps) {
     GUARD(ctx);
     NOT_STREAMED(ctx);
+    NOT_BLOCH(ctx, "the backward step");
     if (n_steps < 0) return fail(ctx, FDTD_EINVAL, "n_steps must be >= 0");
     for (const auto& d : ctx->doms) {
         if (d.ns[0] || d.ns[1] || d.ns[2] || d.npole > 0)
@@ -2255,6 +2363,7 @@ fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode) {
     GUARD(ctx);
     if (ctx->streamed && mode != 4) return fail(ctx, FDTD_EINVAL, "a host-streamed context steps per cell (mode 4)");
     if (mode < 0 || mode >= FDTD_LAUNCH_MODES) return fail(ctx, FDTD_EINVAL, "launch mode must be in [0, 4]");
+    if (mode != 4 && any_bloch(ctx)) return fail(ctx, FDTD_EINVAL, "Bloch domains step in launch mode 4");
     if (mode != ctx->cell_mode * 4) drop_graphs(ctx);   // graphs hold the launches of one mode
     ctx->use_persistent = mode >= 1 && mode <= 3;
     ctx->persist_variant = ctx->use_persistent ? mode - 1 : 0;
@@ -2277,6 +2386,7 @@ static fdtd_status restore_slot(fdtd_ctx* ctx, int32_t slot);
 fdtd_status fdtd_autotune(fdtd_ctx* ctx, int32_t n_steps, double* ms_per_mode) {
     GUARD(ctx);
     NOT_STREAMED(ctx);
+    NOT_BLOCH(ctx, "autotuning (Bloch domains step in launch mode 4)");
     if (n_steps < 1) return fail(ctx, FDTD_EINVAL, "n_steps must be >= 1");
     const int slot = 1 << 30;   // private slot id (public ids are below 2^30)
     const int energy = ctx->energy_on;
@@ -2589,6 +2699,7 @@ fdtd_status fdtd_set_design(fdtd_ctx* ctx, int32_t domain, const int32_t lo[3], 
     NOT_STREAMED(ctx);
     if (!valid_dom(ctx, domain)) return fail(ctx, FDTD_EINVAL, "bad domain");
     DomainHost& d = ctx->doms[domain];
+    if (d.bloch && grad) return fail(ctx, FDTD_EINVAL, "a Bloch domain carries no design box");
     if (!grad) {
         d.design = 0;
         d.grad = nullptr;
@@ -2820,6 +2931,7 @@ fdtd_status fdtd_time_half_steps(fdtd_ctx* ctx, int32_t which, int32_t n_launche
     *ms_per_launch = 0.0;
     if (!ctx->cell_mode || ctx->energy_on || ctx->use_persistent)
         return fail(ctx, FDTD_EINVAL, "per-cell launch mode (4) without an energy record only");
+    NOT_BLOCH(ctx, "kernel timing");
     if (which == 2 && ctx->n_dft_items == 0) return fail(ctx, FDTD_EINVAL, "no DFT monitor");
     if (!ctx->cap_stream) CK(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     CK(ctx, cudaStreamSynchronize(ctx->stream));

@@ -202,6 +202,21 @@ __host__ __device__ inline long long slab_off(const int* n, const int* ns, int q
     return ((long long)s * n[1] + j) * n[0] + i;
 }
 
+// Soft source increments of component `comp` at a cell (Eq. (yee): added after the update); D is a
+// domain descriptor or per-cell argument block listing the domain's sources.
+template <typename T, typename D>
+__device__ __forceinline__ T src_add_t(const D& d, const Src* __restrict__ srcs, int comp, int i, int j, int k,
+                                       int step) {
+    T add = T(0);
+    for (int s = 0; s < d.nsrc; ++s) {
+        const Src& sr = srcs[d.src[s]];
+        if (sr.comp != comp || step >= sr.n) continue;
+        if (i < sr.lo[0] || i >= sr.hi[0] || j < sr.lo[1] || j >= sr.hi[1] || k < sr.lo[2] || k >= sr.hi[2]) continue;
+        add += (T)sr.wave[step];
+    }
+    return add;
+}
+
 template <typename T>
 __device__ inline bool in_ade_box(const Dom<T>& d, int i, int j, int k) {
     return i >= d.blo[0] && i < d.bhi[0] && j >= d.blo[1] && j < d.bhi[1] && k >= d.blo[2] && k < d.bhi[2];
@@ -290,6 +305,33 @@ struct AdjCellArgs {
     // node (and, H side, no PEC-held node): a cell inside on all three axes takes the plain form
     int elo[3], ehi[3], hlo[3], hhi[3];
 };
+
+// A Bloch domain's operands (Sec. 2.2): the per-cell arguments of its real parts plus the
+// imaginary field arrays and the seam phases p_q = pr[q] + i pi[q] of the x and y faces.
+template <typename T>
+struct BlochArgs {
+    CellArgs<T> c;
+    T* FI[6];
+    T pr[2], pi[2];
+};
+template <typename T>
+struct AdjBlochArgs {
+    AdjCellArgs<T> c;
+    T* AI[6];
+    T pr[2], pi[2];
+};
+// Forward and transposed half-steps of a Bloch domain and the completion of a pending transposed
+// step of its imaginary E part (kernels_bloch.cu).
+template <typename T>
+void launch_e_bloch(const Launch& L, const BlochArgs<T>& b, T S, const StepArgs& a);
+template <typename T>
+void launch_h_bloch(const Launch& L, const BlochArgs<T>& b, T S, const StepArgs& a);
+template <typename T>
+void launch_adj_e_bloch(const Launch& L, const AdjBlochArgs<T>& b, T S, int pending);
+template <typename T>
+void launch_adj_h_bloch(const Launch& L, const AdjBlochArgs<T>& b);
+template <typename T>
+void launch_adj_flush_bloch(const Launch& L, const AdjBlochArgs<T>& b, T S);
 
 // One thread per cell over all cells of one domain (per-cell streaming launch mode).
 template <typename T>

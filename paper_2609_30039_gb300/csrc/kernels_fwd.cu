@@ -81,20 +81,6 @@ __device__ __forceinline__ T ade_update(const Dom<T>& d, int a, long long bo, T 
     return e1;
 }
 
-// Soft source increments of component `comp` at a cell (Eq. (yee): added after the update).
-template <typename T, typename D>
-__device__ __forceinline__ T src_add_t(const D& d, const Src* __restrict__ srcs, int comp, int i, int j, int k,
-                                       int step) {
-    T add = T(0);
-    for (int s = 0; s < d.nsrc; ++s) {
-        const Src& sr = srcs[d.src[s]];
-        if (sr.comp != comp || step >= sr.n) continue;
-        if (i < sr.lo[0] || i >= sr.hi[0] || j < sr.lo[1] || j >= sr.hi[1] || k < sr.lo[2] || k >= sr.hi[2]) continue;
-        add += (T)sr.wave[step];
-    }
-    return add;
-}
-
 template <typename T>
 __device__ __forceinline__ T src_add(const Dom<T>& d, const Src* __restrict__ srcs, int comp, int i, int j, int k,
                                      int step) {

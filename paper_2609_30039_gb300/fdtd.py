@@ -79,6 +79,7 @@ _SIGS = {
     "fdtd_version": [],
     "fdtd_set_material": [_ctx, C.c_int32, C.POINTER(fdtd_material)],
     "fdtd_set_periodic": [_ctx, C.c_int32, _i32p],
+    "fdtd_set_bloch": [_ctx, C.c_int32, C.POINTER(C.c_double)],
     "fdtd_dft_flux": [_ctx, C.c_int32, C.POINTER(C.c_double), C.c_int32],
     "fdtd_step_backward": [_ctx, C.c_int32],
     "fdtd_add_source": [_ctx, C.c_int32, C.c_int32, _i32p, _i32p, C.POINTER(C.c_double), C.c_int32, _i32p],
@@ -352,6 +353,11 @@ fdtd_step_backward = _wrap_simple("fdtd_step_backward")
 def fdtd_set_periodic(ctx, domain, periodic):
     arr = (C.c_int32 * 3)(*[int(v) for v in periodic])
     _check(load().fdtd_set_periodic(ctx, int(domain), arr), "fdtd_set_periodic", ctx)
+
+
+def fdtd_set_bloch(ctx, domain, phase):
+    ph = (C.c_double * 2)(float(phase[0]), float(phase[1]))
+    _check(load().fdtd_set_bloch(ctx, int(domain), ph), "fdtd_set_bloch", ctx)
 
 
 def fdtd_set_material(ctx, domain, material):

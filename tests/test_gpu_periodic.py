@@ -130,7 +130,7 @@ def test_flux_rejects_monitors_it_cannot_use():
 
 
 def test_fp32_slab_error_against_the_continuum_formula_is_the_printed_one():
-    # Sec. 5.1: the 8-cell slab of index 1.5 on a 25 nm mesh; the CUDA path's FP32 flux spectra
+    # Sec. 6.1: the 8-cell slab of index 1.5 on a 25 nm mesh; the CUDA path's FP32 flux spectra
     # deviate from Eq. (slab) by the discrete response the paper prints (tests/golden)
     import os
     golden = {}
@@ -168,7 +168,7 @@ def test_fp32_slab_error_against_the_continuum_formula_is_the_printed_one():
 
 
 def test_fp32_drude_slab_converges_at_the_printed_second_order_rate():
-    # Sec. 5.1 dispersive slabs on the CUDA path in FP32: the Drude slab of the oracle pin (0.1 um,
+    # Sec. 6.1 dispersive slabs on the CUDA path in FP32: the Drude slab of the oracle pin (0.1 um,
     # eps_inf 1, lambda_p 0.9 um, gamma 2 pi 0.05 per um of c t) against the continuum transfer
     # matrix; halving the mesh lowers the largest R / T / A error by the printed factor
     from tests.test_oracle_pins import _eps_continuum, _golden_dispersive, _slab_reference

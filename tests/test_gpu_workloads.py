@@ -88,7 +88,11 @@ def test_large_workload_snapshots_exact_replay_and_bf16_bound():
     assert torch.equal(grads["fp32"], grads["store_all"])
     a, b = grads["fp32"], grads["bf16"]
     err = float(torch.linalg.vector_norm(b - a) / torch.linalg.vector_norm(a))
-    assert err < 5e-2, err
+    # BF16 keeps 8 significant bits (relative rounding 2^-9 of each slab's max |x|); the replayed
+    # states inherit that perturbation, and the gradient moves by the same order (1.6e-3 measured at
+    # 640^3), so 5e-3 leaves a factor of ~3 and still catches a codec or replay slip
+    print(f"\nBF16 vs FP32 snapshot gradient rel-L2 {err:.3e}")
+    assert err < 5e-3, err
 
 
 def test_large_workload_gradient_matches_oracle_fp64_small():

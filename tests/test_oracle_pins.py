@@ -9,7 +9,7 @@ method (Sec. 2-3 of arxiv 2609.30039) or by the mathematics of the Yee scheme:
   * CPML special cases and reflection bound (Sec. 2.2);
   * the half-step DFT time offsets (Sec. 2.1, 2.4);
   * dot-product transpose identity and central finite differences with a quadratic
-    Taylor remainder for the discrete adjoint (Sec. 3.1, Eq. (adjoint); Sec. 5.2);
+    Taylor remainder for the discrete adjoint (Sec. 3.1, Eq. (adjoint); Sec. 6.2);
   * checkpoint replay is bitwise equal to store-all (Sec. 3.2);
   * plane-monitor flux (Sec. 2.4) through a slab in a periodic cell (Sec. 2.2) against an
     independent frequency-domain solve of the same 1-D lattice, energy balance R + T = 1, the
@@ -521,7 +521,7 @@ def test_backward_steps_refuse_lossy_domains():
         o.step_backward(1)
 
 
-# ---- dispersive slabs at normal incidence: second-order convergence (Sec. 5.1) -----------------
+# ---- dispersive slabs at normal incidence: second-order convergence (Sec. 6.1) -----------------
 def _golden_dispersive():
     import os
     rows = {}
@@ -616,7 +616,7 @@ def test_dispersive_slab_converges_at_second_order_like_the_paper(material):
 
 
 def test_slab_error_against_the_continuum_formula_is_the_printed_one():
-    # Sec. 5.1: the 8-cell slab of index 1.5 (0.2 um at 0.025 um) deviates from Eq. (slab) by its
+    # Sec. 6.1: the 8-cell slab of index 1.5 (0.2 um at 0.025 um) deviates from Eq. (slab) by its
     # discrete response.  The oracle's time-stepped spectra and the exact frequency-domain solve of
     # the same lattice reproduce the printed maximum errors (the lattice value moves by < 1.5%
     # between S = 0.5 and 0.99, the time step being one the paper does not print).
