@@ -524,6 +524,81 @@ int oracle_step_backward(oracle_t *o, int n) {
     return 0;
 }
 
+/* Absorbing-face variant of the reversible reconstruction (Sec. 3.2: the fields at the interface
+ * between interior and absorber are recorded so that the interior reconstruction stays lossless).
+ * The interior is the set of cells whose own node lies in no CPML slab along any axis; its E and H
+ * updates use no memory variable, so they can be undone exactly like a lossless domain's.  One
+ * backward step undoes forward step n = step - 1 on the interior only, in reverse order:
+ *   every E node outside the interior takes E^{n+1} from the record rec_e (three full-grid arrays;
+ *   only nodes outside the interior are read), then the interior H nodes
+ *   H^{n+1/2} = (H^{n+3/2} - m^n) + S curl E^{n+1};
+ *   every H node outside the interior takes H^{n+1/2} from rec_h, then the interior E nodes
+ *   E^n = (E^{n+1} - s^n) - S eps^-1 curl H^{n+1/2}.
+ * Cells outside the interior end up holding the recorded values (their memories and the absorber
+ * state are not reconstructed).  Poles: -1 (dispersion is not reversible). */
+static int in_interior(const oracle_t *o, int i, int j, int k) {
+    const int c[3] = {i, j, k};
+    for (int q = 0; q < 3; ++q) {
+        const int lo = o->cpml[2 * q], hi = o->cpml[2 * q + 1];
+        if (c[q] < lo || c[q] >= o->N[q] - hi) return 0;
+    }
+    return 1;
+}
+
+int oracle_step_backward_interior(oracle_t *o, const double *rex, const double *rey, const double *rez,
+                                  const double *rhx, const double *rhy, const double *rhz) {
+    if (o->npole > 0 || o->step < 1) return -1;
+    const int nx = o->N[0], ny = o->N[1], nz = o->N[2];
+    const double *re[3] = {rex, rey, rez}, *rh[3] = {rhx, rhy, rhz};
+    const long m = o->step - 1;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                if (!in_interior(o, i, j, k))
+                    for (int a = 0; a < 3; ++a) o->F[a][IDX(o, i, j, k)] = re[a][IDX(o, i, j, k)];
+    sub_sources(o, 1, m);
+    for (int a = 0; a < 3; ++a) {
+        int b = (a + 1) % 3, cax = (a + 2) % 3;
+        const double *Ec = o->F[cax], *Eb = o->F[b];
+        double *H = o->F[3 + a];
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    if (!in_interior(o, i, j, k)) continue;
+                    long id = IDX(o, i, j, k);
+                    int cb[3] = {i, j, k}; cb[b] += 1;
+                    int cc[3] = {i, j, k}; cc[cax] += 1;
+                    double d1 = at(o, Ec, cb[0], cb[1], cb[2]) - Ec[id];   /* dEc/dx_b */
+                    double d2 = at(o, Eb, cc[0], cc[1], cc[2]) - Eb[id];   /* dEb/dx_c */
+                    H[id] = H[id] + o->S * (d1 - d2);
+                }
+    }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                if (!in_interior(o, i, j, k))
+                    for (int a = 0; a < 3; ++a) o->F[3 + a][IDX(o, i, j, k)] = rh[a][IDX(o, i, j, k)];
+    sub_sources(o, 0, m);
+    for (int a = 0; a < 3; ++a) {
+        int b = (a + 1) % 3, cax = (a + 2) % 3;
+        const double *Hc = o->F[3 + cax], *Hb = o->F[3 + b];
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    int c[3] = {i, j, k};
+                    if (!in_interior(o, i, j, k) || is_pec_E(o, a, c)) continue;
+                    long id = IDX(o, i, j, k);
+                    int cb[3] = {i, j, k}; cb[b] -= 1;
+                    int cc[3] = {i, j, k}; cc[cax] -= 1;
+                    double d1 = Hc[id] - at(o, Hc, cb[0], cb[1], cb[2]);   /* dHc/dx_b */
+                    double d2 = Hb[id] - at(o, Hb, cc[0], cc[1], cc[2]);   /* dHb/dx_c */
+                    o->F[a][id] = o->F[a][id] - o->S * o->inv_eps[a][id] * (d1 - d2);
+                }
+    }
+    o->step = m;
+    return 0;
+}
+
 /* ---------------- access ---------------- */
 double *oracle_field(oracle_t *o, int comp) { return o->F[comp]; }
 double *oracle_psi(oracle_t *o, int magnetic, int comp, int which) {

@@ -66,6 +66,7 @@ def _load():
             "oracle_step": (None, [vp, C.c_int]),
             "oracle_set_threads": (None, [vp, C.c_int]),
             "oracle_step_backward": (C.c_int, [vp, C.c_int]),
+            "oracle_step_backward_interior": (C.c_int, [vp, _dp, _dp, _dp, _dp, _dp, _dp]),
             "oracle_field": (_dp, [vp, C.c_int]),
             "oracle_psi": (_dp, [vp, C.c_int, C.c_int, C.c_int]),
             "oracle_pole": (_dp, [vp, C.c_int, C.c_int, C.c_int]),
@@ -206,6 +207,19 @@ class Oracle:
         r = self.lib.oracle_step_backward(self.h, int(n))
         if r != 0:
             raise ValueError("backward stepping needs a domain without CPML layers and without poles")
+
+    def step_backward_interior(self, rec_e, rec_h):
+        """Undoes the last forward step on the interior (cells whose own node lies in no CPML slab),
+        the absorbing-face variant of the reversible reconstruction (Sec. 3.2): rec_e = (Ex, Ey, Ez)
+        of E^{n+1} and rec_h = (Hx, Hy, Hz) of H^{n+1/2}, full-grid arrays recorded by the forward
+        run, of which only the nodes outside the interior are read."""
+        e = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in rec_e]
+        h = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in rec_h]
+        for a in e + h:
+            assert a.size == self.n
+        r = self.lib.oracle_step_backward_interior(self.h, *[_d(a) for a in e + h])
+        if r != 0:
+            raise ValueError("interior backward steps need a domain without poles and a step count >= 1")
 
     @property
     def step_count(self):

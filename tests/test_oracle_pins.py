@@ -980,3 +980,69 @@ def test_thread_team_changes_no_bit():
     assert np.array_equal(runs[0][0], runs[1][0])
     assert np.array_equal(runs[0][1], runs[1][1])
     assert np.abs(runs[0][1]).max() > 0.0
+
+
+def _interior_mask(sc):
+    nx, ny, nz = sc.shape
+    m = np.zeros((nz, ny, nx), dtype=bool)
+    lo = [sc.cpml[2 * q] for q in range(3)]
+    hi = [sc.shape[q] - sc.cpml[2 * q + 1] for q in range(3)]
+    m[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = True
+    return m
+
+
+def _cpml_reversal_run(n_steps=30, seed=5):
+    sc = W.random_state_scene(shape=(14, 12, 16), d=3, n_poles=0, aniso=True)
+    sc.n_steps = n_steps
+    sc.sources = [W.Source(W.EZ, (6, 5, 7), (7, 7, 8), W.gaussian_pulse(n_steps, 8.0, periods=1, delay=2))]
+    o = oracle_from_scene(sc)
+    rng = np.random.default_rng(seed)
+    n = int(np.prod(sc.shape))
+    st = np.zeros(o.state_len)
+    st[:6 * n] = rng.standard_normal(6 * n)
+    pec = pec_mask_E(sc.shape)
+    for a in range(3):
+        st[a * n:(a + 1) * n][pec[a].ravel()] = 0.0
+    o.set_state(st)
+    states = [o.fields()]            # states[t] = (E^t, H^{t+1/2})
+    for _ in range(n_steps):
+        o.step(1)
+        states.append(o.fields())
+    return sc, o, states
+
+
+def test_interior_backward_steps_with_a_recorded_interface_rebuild_a_cpml_run():
+    # Sec. 3.2, absorbing-face variant: the fields at the interface between interior and absorber
+    # are recorded so that the interior reconstruction stays lossless.  With E^{n+1} and H^{n+1/2}
+    # recorded outside the interior, 30 backward steps of a CPML run (diagonal tensor, a source in
+    # the interior, random start) rebuild every interior E and H value to rounding, at every step
+    sc, o, states = _cpml_reversal_run()
+    inner = _interior_mask(sc)
+    worst = 0.0
+    for n in reversed(range(sc.n_steps)):
+        o.step_backward_interior(states[n + 1][:3], states[n][3:])
+        got = np.concatenate([f[inner] for f in o.fields()])
+        want = np.concatenate([f[inner] for f in states[n]])
+        worst = max(worst, float(np.linalg.norm(got - want) / np.linalg.norm(want)))
+    assert o.step_count == 0
+    assert worst <= 1e-12, worst
+
+
+def test_interior_backward_steps_need_the_interface_of_the_right_step():
+    # the same reversal with the E record one step late (E^{n+2} in place of E^{n+1}) or with no
+    # record at all (the absorber values left as they are) misses the interior state: the interface
+    # values enter the interior update
+    for late in (True, False):
+        sc, o, states = _cpml_reversal_run(n_steps=12)
+        inner = _interior_mask(sc)
+        for n in reversed(range(sc.n_steps)):
+            if late:
+                rec_e = states[min(n + 2, sc.n_steps)][:3]
+                rec_h = states[n][3:]
+            else:
+                cur = o.fields()
+                rec_e, rec_h = cur[:3], cur[3:]
+            o.step_backward_interior(rec_e, rec_h)
+        got = np.concatenate([f[inner] for f in o.fields()])
+        want = np.concatenate([f[inner] for f in states[0]])
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) > 1e-3
