@@ -230,11 +230,27 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps);
  * are rebuilt by stepping Eq. (yee) backward instead of replaying from checkpoints): undoes the
  * last n_steps forward steps, each in reverse order,
  *   H^{n+1/2} = (H^{n+3/2} - m^n) + S curl E^{n+1},  E^n = (E^{n+1} - s^n) - S eps^-1 curl H^{n+1/2}.
- * Every domain must be lossless: no CPML cells on any face and no poles (FDTD_EINVAL);
- * FDTD_ESTATE when n_steps exceeds the held step count.  DFT accumulators and energies are not
- * touched; the step count decreases by n_steps.  In floating point the reconstruction differs
+ * Domains must have no poles (FDTD_EINVAL).  A domain without CPML faces steps back whole.  A
+ * domain with CPML faces (the absorbing-face variant of Sec. 3.2) steps back its interior only --
+ * the cells whose own node lies in no CPML slab, whose updates use no memory variable -- with the
+ * fields at the interface between interior and absorber taken from the record of the forward run
+ * (fdtd_record_interface, which must cover these steps: FDTD_ESTATE otherwise); its absorber cells
+ * are left holding the recorded interface planes and otherwise whatever they held.  Launch mode 4
+ * only.  FDTD_ESTATE when n_steps exceeds the held step count.  DFT accumulators and energies are
+ * not touched; the step count decreases by n_steps.  In floating point the reconstruction differs
  * from the forward states by accumulated rounding.  Asynchronous. */
 fdtd_status fdtd_step_backward(fdtd_ctx* ctx, int32_t n_steps);
+
+/* Interface record of the absorbing-face reversible reconstruction (Sec. 3.2: the fields at the
+ * interface between interior and absorber are recorded so that the interior reconstruction stays
+ * lossless).  For every domain with CPML faces: allocates a device record of capacity + 1 slots
+ * (each slot: the three H components on the plane just below each low CPML face of the interior
+ * and the three E components on the plane just above each high one, full planes) and records the
+ * held state as slot 0; every later forward step n (up to t0 + capacity - 1, t0 = the step count
+ * now) records E^{n+1} and H^{n+3/2} into slot n + 1 - t0 (the record is captured into the
+ * forward graphs).  capacity = 0 frees the records.  Launch mode 4 without an energy record
+ * (FDTD_EINVAL otherwise); FDTD_ENOMEM if the record does not fit. */
+fdtd_status fdtd_record_interface(fdtd_ctx* ctx, int32_t capacity);
 
 /* Launch modes (no counterpart in the paper; they change scheduling, not arithmetic):
  * mode 0: per-half-step launches (replayed as CUDA graphs); mode 1: persistent

@@ -201,10 +201,13 @@ class DesignAdjoint:
 
 
 class ReversibleAdjoint(DesignAdjoint):
-    """The same gradient without checkpoints, for lossless nondispersive domains (Sec. 3.2:
-    the forward fields are rebuilt by stepping Eq. (yee) backward): one forward sweep, then for
-    m = n-1 .. 0 a backward step (u^(m+1) -> u^m) and the transposed step m.  Memory: the state
-    alone; work: one extra step per transposed step instead of the binomial replays."""
+    """The same gradient without checkpoints, for nondispersive domains (Sec. 3.2: the forward
+    fields are rebuilt by stepping Eq. (yee) backward): one forward sweep, then for m = n-1 .. 0 a
+    backward step (u^(m+1) -> u^m) and the transposed step m.  Lossless domains step back whole;
+    domains with CPML faces use the absorbing-face variant: the forward sweep records the fields at
+    the interface between interior and absorber, and the interior -- where every design box lies --
+    steps back from it.  Memory: the state plus the interface record; work: one extra step per
+    transposed step instead of the binomial replays."""
 
     def __init__(self, ctx: "F.Context"):
         super().__init__(ctx, slots=1)
@@ -212,6 +215,8 @@ class ReversibleAdjoint(DesignAdjoint):
     def run(self, n_steps: int, loss_of_spectra: Callable):
         ctx = self.ctx
         c = ctx.ctx
+        if any(any(sc.cpml) for sc in ctx.scenes):
+            F.fdtd_record_interface(c, n_steps)
         F.fdtd_step_forward(c, n_steps)
         specs = [ctx.dft(k) for k in range(len(ctx.monitors))]
         J, cots = loss_of_spectra(specs)
@@ -227,6 +232,8 @@ class ReversibleAdjoint(DesignAdjoint):
             F.fdtd_step_backward(c, 1)
             F.fdtd_step_adjoint(c, 1)
         F.fdtd_dft_enable(c, 1)
+        if any(any(sc.cpml) for sc in ctx.scenes):
+            F.fdtd_record_interface(c, 0)
         ctx.synchronize()
         return (J, specs), self.grads, {"forward_steps": n_steps, "backward_steps": n_steps,
                                         "adjoint_steps": n_steps}

@@ -59,6 +59,9 @@ struct DomainHost {
     double bphase[2] = {0.0, 0.0};
     void* FI[6] = {};
     void* AI[6] = {};
+    // interface record of the absorbing-face reversible reconstruction (Sec. 3.2), or nullptr
+    void* rec = nullptr;
+    IfaceArgs ia{};
 };
 
 struct MonHost {
@@ -941,8 +944,33 @@ CellArgs<T> make_cell_args(const fdtd_ctx* c, int di, bool e_side) {
     ca.dom = di;
     ca.kz0 = 0;
     ca.nzg = h.n[2];
+    for (int q = 0; q < 3; ++q) {
+        ca.alo[q] = 0;
+        ca.ahi[q] = h.n[q];
+    }
     return ca;
 }
+
+// The interface planes of a domain with absorbing faces (see IfacePlane) and their offsets in a slot.
+IfaceArgs iface_args(const DomainHost& h, int cap, long long t0) {
+    IfaceArgs ia{};
+    long long off = 0;
+    auto add = [&](int q, int x, int kind) {
+        const long long cells = h.ncell / h.n[q];
+        ia.p[ia.np++] = IfacePlane{q, x, kind, cells, off};
+        off += 3 * cells;
+    };
+    for (int q = 0; q < 3; ++q)
+        if (h.dlo[q] > 0) add(q, h.dlo[q] - 1, 0);   // H just below the interior's low face
+    for (int q = 0; q < 3; ++q)
+        if (h.dhi[q] > 0) add(q, h.n[q] - h.dhi[q], 1);   // E just above its high face
+    ia.slot = off;
+    ia.cap = cap;
+    ia.t0 = (int)t0;
+    return ia;
+}
+
+bool has_cpml(const DomainHost& h) { return h.ns[0] || h.ns[1] || h.ns[2]; }
 
 // One forward step as per-half-step launches on stream st.  offset: position of this step in the
 // launched batch (its DFT phase index is *d_base + offset); first / last: first and last step of
@@ -1044,6 +1072,9 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
                     launch_h_cell<T>(l, cell_args(di, false), (T)c->S, a);
             }
         }
+        // interface record of the reversible reconstruction: E^{n+1}, H^{n+3/2} into slot n + 1 - t0
+        for (const DomainHost& h : c->doms)
+            if (h.rec) launch_iface<T>(l, (T* const*)h.F, h.n, h.ia, (T*)h.rec, c->d_base, offset + 1, 3, 1);
         if (last) launch_advance(l, c->d_step, offset + 1);
     } else {
         fork_int();
@@ -1550,8 +1581,11 @@ fdtd_status build_graph(fdtd_ctx* c) {
     const bool cell = c->cell_mode && !c->energy_on;
     const long long per = cell ? 2 * ((long long)c->doms.size() + nd)
                                : 2 * ((c->tiles_int.empty() ? 0 : 1) + (c->tiles_gen.empty() ? 0 : 1) + nd);
-    // plus the step-base copy (DFT or per-cell) and, per-cell, the counter advance
-    c->graph_launches[a][b] = per * kGraphSteps + ((nd || cell) ? 1 : 0) + (cell ? 1 : 0);
+    // plus the step-base copy (DFT or per-cell) and, per-cell, the counter advance and the interface
+    // records
+    long long recs = 0;
+    for (const auto& h : c->doms) recs += (cell && h.rec) ? 1 : 0;
+    c->graph_launches[a][b] = (per + recs) * kGraphSteps + ((nd || cell) ? 1 : 0) + (cell ? 1 : 0);
     return FDTD_OK;
 }
 
@@ -2321,16 +2355,48 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
     return FDTD_OK;
 }
 
+fdtd_status fdtd_record_interface(fdtd_ctx* ctx, int32_t capacity) {
+    GUARD(ctx);
+    NOT_STREAMED(ctx);
+    NOT_BLOCH(ctx, "the interface record");
+    if (capacity < 0) return fail(ctx, FDTD_EINVAL, "capacity must be >= 0");
+    if (capacity > 0 && (!ctx->cell_mode || ctx->energy_on))
+        return fail(ctx, FDTD_EINVAL, "the interface record runs in launch mode 4 without an energy record");
+    drop_graphs(ctx);   // captured forward steps change (they record, or stop recording)
+    for (auto& d : ctx->doms) {
+        if (d.rec) {
+            dfree(ctx, d.rec);
+            d.rec = nullptr;
+        }
+        if (capacity == 0 || !has_cpml(d)) continue;
+        d.ia = iface_args(d, capacity, ctx->step);
+        fdtd_status st = dmalloc(ctx, &d.rec, (size_t)(capacity + 1) * d.ia.slot * ctx->esz);
+        if (st != FDTD_OK) return st;
+        // slot 0: the interface of the held state u^{t0}
+        if (ctx->dtype == FDTD_F32)
+            launch_iface<float>(L(ctx), (float* const*)d.F, d.n, d.ia, (float*)d.rec, nullptr, (int)ctx->step, 3, 1);
+        else
+            launch_iface<double>(L(ctx), (double* const*)d.F, d.n, d.ia, (double*)d.rec, nullptr, (int)ctx->step, 3, 1);
+        CKL(ctx);
+    }
+    return FDTD_OK;
+}
+
 fdtd_status fdtd_step_backward(fdtd_ctx* ctx, int32_t n_steps) {
     GUARD(ctx);
     NOT_STREAMED(ctx);
     NOT_BLOCH(ctx, "the backward step");
     if (n_steps < 0) return fail(ctx, FDTD_EINVAL, "n_steps must be >= 0");
     for (const auto& d : ctx->doms) {
-        if (d.ns[0] || d.ns[1] || d.ns[2] || d.npole > 0)
-            return fail(ctx, FDTD_EINVAL, "backward steps need lossless domains: no CPML layers and no poles");
+        if (d.npole > 0) return fail(ctx, FDTD_EINVAL, "backward steps need nondispersive domains (no poles)");
+        if (has_cpml(d) && !d.rec)
+            return fail(ctx, FDTD_EINVAL, "a domain with CPML faces steps backward only with an interface record "
+                                          "(fdtd_record_interface before the forward steps)");
+        if (d.rec && (ctx->step - n_steps < d.ia.t0 || ctx->step - d.ia.t0 > d.ia.cap))
+            return fail(ctx, FDTD_ESTATE, "the interface record does not cover these steps");
         if (d.ie[0] == nullptr) return fail(ctx, FDTD_EINVAL, "no material");
     }
+    if (!ctx->cell_mode) return fail(ctx, FDTD_EINVAL, "backward steps run in launch mode 4");
     if (n_steps > ctx->step) return fail(ctx, FDTD_ESTATE, "cannot step back past step 0");
     if (n_steps == 0) return FDTD_OK;
     const Launch l = L(ctx);
@@ -2343,14 +2409,36 @@ fdtd_status fdtd_step_backward(fdtd_ctx* ctx, int32_t n_steps) {
     a.d_base = ctx->d_base;
     launch_copy_int(l, ctx->d_step, ctx->d_base);
     for (int q = 0; q < n_steps; ++q) {
-        a.offset = -1 - q;   // undoes forward step (step - 1 - q)
+        a.offset = -1 - q;   // undoes forward step n = step - 1 - q
         for (int di = 0; di < (int)ctx->doms.size(); ++di) {
+            const DomainHost& d = ctx->doms[di];
+            if (!d.rec) {
+                if (ctx->dtype == FDTD_F32)
+                    launch_back_cell<float>(l, make_cell_args<float>(ctx, di, true),
+                                            make_cell_args<float>(ctx, di, false), (float)ctx->S, a, ctx->aniso);
+                else
+                    launch_back_cell<double>(l, make_cell_args<double>(ctx, di, true),
+                                             make_cell_args<double>(ctx, di, false), ctx->S, a, ctx->aniso);
+                continue;
+            }
+            // absorbing faces: the interior steps back, its interface planes come from the record
+            // (E^{n+1} from slot n + 1 - t0 before the H half, H^{n+1/2} from slot n - t0 before E)
+            auto back = [&](auto zero) {
+                using T = decltype(zero);
+                CellArgs<T> ce = make_cell_args<T>(ctx, di, true), ch = make_cell_args<T>(ctx, di, false);
+                for (int ax = 0; ax < 3; ++ax) {
+                    ce.alo[ax] = ch.alo[ax] = d.dlo[ax];
+                    ce.ahi[ax] = ch.ahi[ax] = d.n[ax] - d.dhi[ax];
+                }
+                launch_iface<T>(l, (T* const*)d.F, d.n, d.ia, (T*)d.rec, ctx->d_base, a.offset + 1, 2, 0);
+                launch_back_h<T>(l, ch, (T)ctx->S, a);
+                launch_iface<T>(l, (T* const*)d.F, d.n, d.ia, (T*)d.rec, ctx->d_base, a.offset, 1, 0);
+                launch_back_e<T>(l, ce, (T)ctx->S, a, ctx->aniso);
+            };
             if (ctx->dtype == FDTD_F32)
-                launch_back_cell<float>(l, make_cell_args<float>(ctx, di, true), make_cell_args<float>(ctx, di, false),
-                                        (float)ctx->S, a, ctx->aniso);
+                back(0.0f);
             else
-                launch_back_cell<double>(l, make_cell_args<double>(ctx, di, true),
-                                         make_cell_args<double>(ctx, di, false), ctx->S, a, ctx->aniso);
+                back(0.0);
         }
     }
     launch_advance(l, ctx->d_step, -n_steps);
@@ -2364,6 +2452,8 @@ fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode) {
     if (ctx->streamed && mode != 4) return fail(ctx, FDTD_EINVAL, "a host-streamed context steps per cell (mode 4)");
     if (mode < 0 || mode >= FDTD_LAUNCH_MODES) return fail(ctx, FDTD_EINVAL, "launch mode must be in [0, 4]");
     if (mode != 4 && any_bloch(ctx)) return fail(ctx, FDTD_EINVAL, "Bloch domains step in launch mode 4");
+    for (const auto& d : ctx->doms)
+        if (mode != 4 && d.rec) return fail(ctx, FDTD_EINVAL, "an interface record runs in launch mode 4");
     if (mode != ctx->cell_mode * 4) drop_graphs(ctx);   // graphs hold the launches of one mode
     ctx->use_persistent = mode >= 1 && mode <= 3;
     ctx->persist_variant = ctx->use_persistent ? mode - 1 : 0;

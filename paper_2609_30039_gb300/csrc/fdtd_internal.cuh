@@ -281,7 +281,39 @@ struct CellArgs {
     // planes (the CPML z profile, its memory index and the source boxes use global planes); a
     // resident domain has kz0 = 0, nzg = n[2]
     int kz0, nzg;
+    // cells [alo, ahi) the backward step updates (the whole domain, or the interior of a domain
+    // with absorbing faces, see launch_iface)
+    int alo[3], ahi[3];
 };
+
+// Interface planes of the absorbing-face reversible reconstruction (Sec. 3.2): the H nodes on the
+// plane just below each low face of the interior and the E nodes on the plane just above each high
+// face (the interior is the box of cells whose own node lies in no CPML slab).  One plane: axis q,
+// coordinate x along q, kind 0 = H (three components), 1 = E; its 3 * cells values start at `off`
+// inside a record slot.
+struct IfacePlane {
+    int q, x, kind;
+    long long cells, off;
+};
+struct IfaceArgs {
+    IfacePlane p[6];
+    int np;
+    long long slot;   // values per slot
+    int cap;          // last slot index
+    int t0;           // step count of slot 0
+};
+// Copies the planes of `kinds` (bit 0: H, bit 1: E) of every IfacePlane between the fields F and
+// record slot s = (d_base ? *d_base : 0) + bias - t0 (to_rec: fields -> record; else record ->
+// fields).  Slots outside [0, cap] are skipped.
+template <typename T>
+void launch_iface(const Launch& L, T* const* F, const int* n, const IfaceArgs& ia, T* rec, const int* d_base, int bias,
+                  int kinds, int to_rec);
+// The two halves of a backward step (reversible reconstruction) of one domain, each over the box
+// [alo, ahi) of its argument block; the step undone is *a.d_base + a.offset.
+template <typename T>
+void launch_back_h(const Launch& L, const CellArgs<T>& ch, T S, const StepArgs& a);
+template <typename T>
+void launch_back_e(const Launch& L, const CellArgs<T>& ce, T S, const StepArgs& a, int aniso);
 
 // One domain's operands for the per-cell transposed kernels, passed by value: the adjoint fields,
 // the forward fields (material cotangent), eps^-1, the adjoint CPML memories of both half-steps

@@ -586,6 +586,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
     const bool pi = i == 0 && !(kPer && c.per[0]), pj = j == 0 && !(kPer && c.per[1]), pk = k == 0;
     const bool px = pj || pk, py = pi || pk, pz = pi || pj;   // PEC-held
     if (kBack) {
+        if (i < c.alo[0] || i >= c.ahi[0] || j < c.alo[1] || j >= c.ahi[1] || k < c.alo[2] || k >= c.ahi[2]) return;
         T sx = T(0), sy = T(0), sz = T(0);
         if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && kg >= c.src_lo[2] &&
             kg < c.src_hi[2]) {
@@ -676,6 +677,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
         T yz1 = (xe ? Ey[id + ox] : T(0)) - eyk, yz2 = (ye ? Ex[id + oy] : T(0)) - exk;  // Hz: dEy/dx, dEx/dy
         const T hx = c.F[3][id], hy = c.F[4][id], hz = c.F[5][id];
         if (kBack) {
+            if (i < c.alo[0] || i >= c.ahi[0] || j < c.alo[1] || j >= c.ahi[1] || k < c.alo[2] || k >= c.ahi[2]) return;
             T mx = T(0), my = T(0), mz = T(0);
             if (i >= c.src_lo[0] && i < c.src_hi[0] && j >= c.src_lo[1] && j < c.src_hi[1] && kg >= c.src_lo[2] &&
                 kg < c.src_hi[2]) {
@@ -776,6 +778,73 @@ void launch_back_cell(const Launch& L, const CellArgs<T>& ce, const CellArgs<T>&
         (per ? k_e_cell<T, false, false, true, true> : k_e_cell<T, false, false, false, true>)<<<g, b, 0, L.stream>>>(
             ce, nullptr, -S, a);
     *L.counter += 2;
+}
+
+template <typename T>
+void launch_back_h(const Launch& L, const CellArgs<T>& ch, T S, const StepArgs& a) {
+    const dim3 g = cell_grid(ch.n), b(kTileX, kTileY);
+    if (ch.per[0] || ch.per[1])
+        k_h_cell<T, true, true><<<g, b, 0, L.stream>>>(ch, -S, a);
+    else
+        k_h_cell<T, false, true><<<g, b, 0, L.stream>>>(ch, -S, a);
+    ++*L.counter;
+}
+
+template <typename T>
+void launch_back_e(const Launch& L, const CellArgs<T>& ce, T S, const StepArgs& a, int aniso) {
+    const dim3 g = cell_grid(ce.n), b(kTileX, kTileY);
+    const bool per = ce.per[0] || ce.per[1];
+    if (aniso)
+        (per ? k_e_cell<T, true, false, true, true> : k_e_cell<T, true, false, false, true>)<<<g, b, 0, L.stream>>>(
+            ce, nullptr, -S, a);
+    else
+        (per ? k_e_cell<T, false, false, true, true> : k_e_cell<T, false, false, false, true>)<<<g, b, 0, L.stream>>>(
+            ce, nullptr, -S, a);
+    ++*L.counter;
+}
+
+// Interface planes <-> record slot (see IfaceArgs): blockIdx.y picks the plane, threads run over
+// its three components x cells.
+template <typename T>
+__global__ void __launch_bounds__(256) k_iface(const int n0, const int n1, const int n2, const IfaceArgs ia,
+                                               T* __restrict__ rec, const int* __restrict__ d_base, int bias, int kinds,
+                                               int to_rec, T* Ex, T* Ey, T* Ez, T* Hx, T* Hy, T* Hz) {
+    if (blockIdx.y >= (unsigned)ia.np) return;
+    const IfacePlane pl = ia.p[blockIdx.y];
+    if (!((kinds >> pl.kind) & 1)) return;   // kind 0 = H (bit 0), 1 = E (bit 1)
+    const long long s = (long long)(d_base ? *d_base : 0) + bias - ia.t0;
+    if (s < 0 || s > ia.cap) return;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * pl.cells) return;
+    const int comp = (int)(t / pl.cells);
+    const long long cell = t - (long long)comp * pl.cells;
+    // plane cell -> (i, j, k): the two other axes in increasing order, the first one fastest
+    int c[3];
+    const int nn[3] = {n0, n1, n2};
+    const int a0 = pl.q == 0 ? 1 : 0, a1 = pl.q == 2 ? 1 : 2;
+    c[pl.q] = pl.x;
+    c[a0] = (int)(cell % nn[a0]);
+    c[a1] = (int)(cell / nn[a0]);
+    const long long id = ((long long)c[2] * n1 + c[1]) * n0 + c[0];
+    T* fields[6] = {Ex, Ey, Ez, Hx, Hy, Hz};
+    T* f = fields[(pl.kind == 0 ? 3 : 0) + comp];
+    T* r = rec + s * ia.slot + pl.off + t;
+    if (to_rec)
+        *r = f[id];
+    else
+        f[id] = *r;
+}
+
+template <typename T>
+void launch_iface(const Launch& L, T* const* F, const int* n, const IfaceArgs& ia, T* rec, const int* d_base, int bias,
+                  int kinds, int to_rec) {
+    if (ia.np <= 0) return;
+    long long most = 0;
+    for (int q = 0; q < ia.np; ++q) most = most > 3 * ia.p[q].cells ? most : 3 * ia.p[q].cells;
+    const dim3 g((unsigned)((most + 255) / 256), (unsigned)ia.np);
+    k_iface<T><<<g, 256, 0, L.stream>>>(n[0], n[1], n[2], ia, rec, d_base, bias, kinds, to_rec, F[0], F[1], F[2], F[3],
+                                         F[4], F[5]);
+    ++*L.counter;
 }
 
 template <typename T>
@@ -1231,6 +1300,14 @@ template void launch_back_cell<float>(const Launch&, const CellArgs<float>&, con
                                       const StepArgs&, int);
 template void launch_back_cell<double>(const Launch&, const CellArgs<double>&, const CellArgs<double>&, double,
                                        const StepArgs&, int);
+template void launch_back_h<float>(const Launch&, const CellArgs<float>&, float, const StepArgs&);
+template void launch_back_h<double>(const Launch&, const CellArgs<double>&, double, const StepArgs&);
+template void launch_back_e<float>(const Launch&, const CellArgs<float>&, float, const StepArgs&, int);
+template void launch_back_e<double>(const Launch&, const CellArgs<double>&, double, const StepArgs&, int);
+template void launch_iface<float>(const Launch&, float* const*, const int*, const IfaceArgs&, float*, const int*, int,
+                                  int, int);
+template void launch_iface<double>(const Launch&, double* const*, const int*, const IfaceArgs&, double*, const int*,
+                                   int, int, int);
 template void launch_h_cell<float>(const Launch&, const CellArgs<float>&, float, const StepArgs&);
 template void launch_h_cell<double>(const Launch&, const CellArgs<double>&, double, const StepArgs&);
 template cudaError_t launch_steps<float>(const Launch&, const Dom<float>*, const Tile*, int, float, const StepArgs&, int,
