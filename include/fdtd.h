@@ -127,12 +127,32 @@ fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cp
  * hold exactly the values that a resident context (fdtd_create) computes, bit for bit.  The device
  * holds the three windows of min(nz, slab + 2 halo) planes plus the monitors, not the domain.
  * Requires 1 <= halo <= slab (FDTD_EINVAL).  Supported on a streamed context: stepping, sources,
- * DFT monitors and flux, periodic x / y, materials (pinned host), get/set of state parts (which =
- * 0; the copy may involve device or host memory), reset, step counters, fdtd_check_finite.  Not
- * supported (FDTD_EINVAL): the adjoint and design calls, snapshots, energy records, the backward
- * step, autotuning, profiling, and launch modes other than 4. */
+ * DFT monitors and flux, periodic x / y, materials (pinned host), get/set of state parts (the copy
+ * may involve device or host memory), reset, step counters, fdtd_check_finite, and the streamed
+ * transposed sweep (fdtd_stream_checkpoints, then fdtd_adjoint_begin / fdtd_step_adjoint with
+ * adjoint sources and a design box as on a resident context).  Not supported (FDTD_EINVAL):
+ * snapshots, energy records, the backward step, pole-parameter gradients, autotuning, profiling,
+ * and launch modes other than 4. */
 fdtd_status fdtd_create_streamed(const fdtd_grid* grid, const fdtd_cpml* cpml, const fdtd_material* material,
                                  int32_t slab, int32_t halo, void* stream, fdtd_ctx** out);
+
+/* Forward checkpoints of a host-streamed context (Sec. 4.2; the transposed sweep runs the slab
+ * tiling in reverse).  enabled = 1: from the held step t0 on, fdtd_step_forward runs its batches
+ * aligned to t0 + j * halo and keeps the whole forward state at every such batch start in pinned
+ * host memory owned by the context (existing checkpoints are dropped); 0 frees them.  The
+ * transposed sweep of a streamed context -- fdtd_adjoint_begin, then fdtd_step_adjoint -- then runs
+ * the batches last to first: per slab its window replays the batch from the checkpoint on the device
+ * (keeping each replayed window state, kb <= halo of them), takes the transposed steps from the
+ * adjoint state at the batch end (monitor cotangents injected over the whole window), completes them
+ * and writes its owned planes back; only owned design cells add to the material cotangent.  The
+ * owned planes then hold what the resident sweep computes (bit for bit in the adjoint state; the
+ * material cotangent to rounding order, each window summing its own steps first).  The adjoint
+ * state lives in two pinned host sets owned by the context (parts with which = 1 read the current
+ * one, always in natural form); fdtd_step_adjoint takes whole batches (FDTD_ESTATE otherwise).
+ * Device memory of the sweep: the adjoint window and halo replayed forward windows (fields and pole
+ * states of min(nz, slab + 2 halo) planes) besides the three stepping workspaces.  FDTD_EINVAL on a
+ * resident context. */
+fdtd_status fdtd_stream_checkpoints(fdtd_ctx* ctx, int32_t enabled);
 
 /* Frees everything the context owns.  NULL-safe.  Synchronises the stream. */
 fdtd_status fdtd_destroy(fdtd_ctx* ctx);

@@ -239,6 +239,37 @@ class ReversibleAdjoint(DesignAdjoint):
                                         "adjoint_steps": n_steps}
 
 
+class StreamedAdjoint(DesignAdjoint):
+    """The same gradient on a host-streamed context (Sec. 4.2: the transposed sweep runs the slab
+    tiling in reverse): one forward sweep that keeps its state at every batch start in pinned host
+    memory, then the transposed sweep batch by batch, last to first, each slab window replaying its
+    batch on the device from the checkpoint.  Device memory: the stepping workspaces, the adjoint
+    window and the replayed windows of one batch; host memory: the state, two adjoint state sets and
+    one checkpoint per batch."""
+
+    def __init__(self, ctx: "F.Context"):
+        super().__init__(ctx, slots=1)
+
+    def run(self, n_steps: int, loss_of_spectra: Callable):
+        ctx = self.ctx
+        c = ctx.ctx
+        F.fdtd_stream_checkpoints(c, 1)
+        F.fdtd_step_forward(c, n_steps)
+        specs = [ctx.dft(k) for k in range(len(ctx.monitors))]
+        J, cots = loss_of_spectra(specs)
+        keep = [ct.contiguous() if ct is not None else None for ct in cots]
+        for k, ct in enumerate(keep):
+            F.fdtd_set_adjoint_source(c, ctx.monitors[k][0], ct.data_ptr() if ct is not None else None)
+        for g in self.grads:
+            if g is not None:
+                g.zero_()
+        F.fdtd_adjoint_begin(c)
+        F.fdtd_step_adjoint(c, n_steps)
+        ctx.synchronize()
+        F.fdtd_stream_checkpoints(c, 0)
+        return (J, specs), self.grads, {"forward_steps": n_steps, "adjoint_steps": n_steps}
+
+
 def _make_function():
     import torch
 

@@ -165,6 +165,19 @@ struct fdtd_ctx {
     DftItem* d_sitems = nullptr;              // DFT items of the owned planes of every slab
     std::vector<int> sitem_begin, sitem_count;
     int stream_dirty = 1;
+    // streamed transposed sweep (Sec. 4.2: it runs the slab tiling in reverse): forward checkpoints
+    // at batch starts (step -> pinned buffer of every forward part, taken every sk steps from
+    // ck_t0), the adjoint state in two pinned host sets (the batch end is read, the batch start
+    // written), a device adjoint window and the kb replayed forward windows of a batch
+    int ck_on = 0;
+    long long ck_t0 = 0;
+    std::map<long long, void*> ck;
+    Workspace hadj[2];
+    int hadj_cur = 0;
+    int hadj_ready = 0;
+    Workspace aws;
+    std::vector<Workspace> rws;
+    void* d_adoms = nullptr;                  // descriptors (slab s, replay j) of the transposed windows
     // instrumentation
     int prof_on = 0;
     int prof_used = 0;
@@ -1150,6 +1163,46 @@ int ie_first(const DomainHost& h, int a) {
     return a;
 }
 
+// Descriptor of slab s's window in its workspace (local z extent and pole box).
+template <typename T>
+Dom<T> slab_dom(const fdtd_ctx* c, int s) {
+    const DomainHost& h = c->doms[0];
+    const long long nxy = (long long)h.n[0] * h.n[1];
+    const SlabWin w = slab_win(c, s);
+    const fdtd_ctx::Workspace& ws = c->ws[s % 3];
+    Dom<T> d;
+    fill_dom<T>(c, h, d);
+    d.n[2] = w.whi - w.wlo;
+    d.ncell = nxy * d.n[2];
+    for (int f = 0; f < 6; ++f) {
+        d.F[f] = (T*)ws.F[f];
+        d.A[f] = nullptr;
+    }
+    for (int a = 0; a < 3; ++a) {
+        d.ie[a] = (const T*)ws.ie[ie_first(h, a)];   // distinct arrays, distinct windows
+        for (int s2 = 0; s2 < 2; ++s2) {
+            d.psiE[a][s2] = (T*)ws.psiE[a][s2];
+            d.psiH[a][s2] = (T*)ws.psiH[a][s2];
+            d.apsiE[a][s2] = d.apsiH[a][s2] = nullptr;
+        }
+    }
+    d.mask = (const uint8_t*)ws.mask;
+    d.aade = nullptr;
+    d.ade = (T*)ws.ade;
+    d.grad = nullptr;
+    d.design = 0;
+    d.energy = nullptr;
+    if (w.zb1 > w.zb0) {
+        d.blo[2] = w.zb0 - w.wlo;
+        d.bhi[2] = w.zb1 - w.wlo;
+        d.bcell = (long long)(h.bhi[0] - h.blo[0]) * (h.bhi[1] - h.blo[1]) * (w.zb1 - w.zb0);
+    } else {
+        for (int q = 0; q < 3; ++q) d.blo[q] = d.bhi[q] = 0;
+        d.bcell = 0;
+    }
+    return d;
+}
+
 // Per-slab descriptors (workspace pointers, local pole box) and the DFT items of its owned planes.
 template <typename T>
 fdtd_status stream_prepare(fdtd_ctx* c) {
@@ -1173,37 +1226,7 @@ fdtd_status stream_prepare(fdtd_ctx* c) {
     c->sitem_count.assign(nsl, 0);
     for (int s = 0; s < nsl; ++s) {
         const SlabWin w = slab_win(c, s);
-        const fdtd_ctx::Workspace& ws = c->ws[s % 3];
-        Dom<T>& d = hd[s];
-        fill_dom<T>(c, h, d);
-        d.n[2] = w.whi - w.wlo;
-        d.ncell = nxy * d.n[2];
-        for (int f = 0; f < 6; ++f) {
-            d.F[f] = (T*)ws.F[f];
-            d.A[f] = nullptr;
-        }
-        for (int a = 0; a < 3; ++a) {
-            d.ie[a] = (const T*)ws.ie[ie_first(h, a)];   // distinct arrays, distinct windows
-            for (int s2 = 0; s2 < 2; ++s2) {
-                d.psiE[a][s2] = (T*)ws.psiE[a][s2];
-                d.psiH[a][s2] = (T*)ws.psiH[a][s2];
-                d.apsiE[a][s2] = d.apsiH[a][s2] = nullptr;
-            }
-        }
-        d.mask = (const uint8_t*)ws.mask;
-        d.aade = nullptr;
-        d.ade = (T*)ws.ade;
-        d.grad = nullptr;
-        d.design = 0;
-        d.energy = nullptr;
-        if (w.zb1 > w.zb0) {
-            d.blo[2] = w.zb0 - w.wlo;
-            d.bhi[2] = w.zb1 - w.wlo;
-            d.bcell = (long long)(h.bhi[0] - h.blo[0]) * (h.bhi[1] - h.blo[1]) * (w.zb1 - w.zb0);
-        } else {
-            for (int q = 0; q < 3; ++q) d.blo[q] = d.bhi[q] = 0;
-            d.bcell = 0;
-        }
+        hd[s] = slab_dom<T>(c, s);
         // DFT: monitor cells of the owned planes (cells are numbered x fastest, z slowest)
         c->sitem_begin[s] = (int)items.size();
         for (size_t mi = 0; mi < c->mons.size(); ++mi) {
@@ -1235,15 +1258,19 @@ fdtd_status stream_prepare(fdtd_ctx* c) {
     return FDTD_OK;
 }
 
-// Copies window or owned planes between the host state and workspace r (to_dev: host -> device
-// of the window; otherwise device -> host of the owned planes).
-fdtd_status stream_copy(fdtd_ctx* c, const SlabWin& w, int r, bool to_dev, cudaStream_t st) {
+// CPML memory (a, s) of the E (e = 0) or H (e = 1) update in a set of home arrays.
+void* home_psi(const fdtd_ctx::Workspace& hs, int e, int a, int s) { return e ? hs.psiH[a][s] : hs.psiE[a][s]; }
+
+// Copies the global planes [lo, hi) of a state (fields, CPML memories, pole states) between a set of
+// arrays in host layout (home: whole domain) and a device window (dev: planes [w.wlo, w.whi)), and,
+// with `materials`, the eps^-1 and pole-mask planes host -> device.
+fdtd_status window_copy(fdtd_ctx* c, const SlabWin& w, const fdtd_ctx::Workspace& home, const fdtd_ctx::Workspace& dev,
+                        int lo, int hi, bool to_dev, bool materials, cudaStream_t st) {
     const DomainHost& h = c->doms[0];
-    fdtd_ctx::Workspace& ws = c->ws[r];
+    const fdtd_ctx::Workspace& ws = dev;
     const size_t esz = c->esz;
     const long long nxy = (long long)h.n[0] * h.n[1];
     const int nz = h.n[2];
-    const int lo = to_dev ? w.wlo : w.zs, hi = to_dev ? w.whi : w.ze;   // global planes moved
     const cudaMemcpyKind kind = to_dev ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
     // planes [lo, hi) of an array of `per` elements per plane; the workspace holds the window
     auto planes = [&](void* home, void* dev, long long per, size_t el) -> cudaError_t {
@@ -1253,8 +1280,9 @@ fdtd_status stream_copy(fdtd_ctx* c, const SlabWin& w, int r, bool to_dev, cudaS
         const size_t bytes = (size_t)(hi - lo) * per * el;
         return to_dev ? cudaMemcpyAsync(dp, hp, bytes, kind, st) : cudaMemcpyAsync(hp, dp, bytes, kind, st);
     };
-    for (int f = 0; f < 6; ++f) CK(c, planes(h.F[f], ws.F[f], nxy, esz));
-    if (to_dev) {
+    for (int f = 0; f < 6; ++f)
+        if (home.F[f] && ws.F[f]) CK(c, planes(home.F[f], ws.F[f], nxy, esz));
+    if (to_dev && materials) {
         for (int a = 0; a < 3; ++a)
             if (ie_first(h, a) == a) CK(c, planes(const_cast<void*>(h.ie[a]), ws.ie[a], nxy, esz));
         if (h.npole > 0 && h.mask) CK(c, planes(const_cast<uint8_t*>(h.mask), ws.mask, nxy, 1));
@@ -1262,11 +1290,11 @@ fdtd_status stream_copy(fdtd_ctx* c, const SlabWin& w, int r, bool to_dev, cudaS
     for (int a = 0; a < 3; ++a)
         for (int s = 0; s < 2; ++s) {
             const long long per = psi_plane(h, a, s);
-            if (per == 0) continue;
-            void* home[2] = {h.psiE[a][s], h.psiH[a][s]};
-            void* dev[2] = {ws.psiE[a][s], ws.psiH[a][s]};
+            if (per == 0 || !home.psiE[a][s] || !ws.psiE[a][s]) continue;
+            void* hpsi[2] = {home_psi(home, 0, a, s), home_psi(home, 1, a, s)};
+            void* dpsi[2] = {ws.psiE[a][s], ws.psiH[a][s]};
             if ((a + 1 + s) % 3 != 2) {
-                for (int e = 0; e < 2; ++e) CK(c, planes(home[e], dev[e], per, esz));
+                for (int e = 0; e < 2; ++e) CK(c, planes(hpsi[e], dpsi[e], per, esz));
                 continue;
             }
             // z memories: CPML planes [0, dlo) are grid planes [0, dlo), planes [dlo, ns) are grid
@@ -1278,27 +1306,47 @@ fdtd_status stream_copy(fdtd_ctx* c, const SlabWin& w, int r, bool to_dev, cudaS
                 const long long p0 = part == 0 ? r0[0] : dlo + (r0[1] - (nz - dhi));
                 const size_t off = (size_t)p0 * per * esz, bytes = (size_t)(r1[part] - r0[part]) * per * esz;
                 for (int e = 0; e < 2; ++e) {
-                    char* hp = (char*)home[e] + off;
-                    char* dp = (char*)dev[e] + off;
+                    char* hp = (char*)hpsi[e] + off;
+                    char* dp = (char*)dpsi[e] + off;
                     CK(c, to_dev ? cudaMemcpyAsync(dp, hp, bytes, kind, st) : cudaMemcpyAsync(hp, dp, bytes, kind, st));
                 }
             }
         }
     // pole state: chunks [component][pole][P / Q] of the box, z slowest inside a chunk
-    if (w.zb1 > w.zb0) {
+    if (w.zb1 > w.zb0 && home.ade && ws.ade) {
         const long long bxy = (long long)(h.bhi[0] - h.blo[0]) * (h.bhi[1] - h.blo[1]);
         const long long lb = bxy * (w.zb1 - w.zb0);
         const int z0 = std::max(lo, w.zb0), z1 = std::min(hi, w.zb1);
         if (z1 > z0) {
             const size_t bytes = (size_t)(z1 - z0) * bxy * esz;
             for (int q = 0; q < 6 * h.npole; ++q) {
-                char* hp = (char*)h.ade + ((size_t)q * h.bcell + (size_t)(z0 - h.blo[2]) * bxy) * esz;
+                char* hp = (char*)home.ade + ((size_t)q * h.bcell + (size_t)(z0 - h.blo[2]) * bxy) * esz;
                 char* dp = (char*)ws.ade + ((size_t)q * lb + (size_t)(z0 - w.zb0) * bxy) * esz;
                 CK(c, to_dev ? cudaMemcpyAsync(dp, hp, bytes, kind, st) : cudaMemcpyAsync(hp, dp, bytes, kind, st));
             }
         }
     }
     return FDTD_OK;
+}
+
+// The domain's own host state as a set of home arrays.
+fdtd_ctx::Workspace host_state(const DomainHost& h) {
+    fdtd_ctx::Workspace hs;
+    for (int f = 0; f < 6; ++f) hs.F[f] = h.F[f];
+    for (int a = 0; a < 3; ++a)
+        for (int s2 = 0; s2 < 2; ++s2) {
+            hs.psiE[a][s2] = h.psiE[a][s2];
+            hs.psiH[a][s2] = h.psiH[a][s2];
+        }
+    hs.ade = h.ade;
+    return hs;
+}
+
+// Copies window or owned planes between the host state and workspace r (to_dev: host -> device
+// of the window, materials included; otherwise device -> host of the owned planes).
+fdtd_status stream_copy(fdtd_ctx* c, const SlabWin& w, int r, bool to_dev, cudaStream_t st) {
+    return window_copy(c, w, host_state(c->doms[0]), c->ws[r], to_dev ? w.wlo : w.zs, to_dev ? w.whi : w.ze, to_dev,
+                       true, st);
 }
 
 template <typename T>
@@ -1317,6 +1365,56 @@ CellArgs<T> stream_cell_args(const fdtd_ctx* c, int s, bool e_side) {
     ca.nzg = h.n[2];
     ca.dom = s;
     return ca;
+}
+
+// Bytes of the whole forward state of the streamed domain (every part).
+size_t state_bytes(const fdtd_ctx* c) {
+    size_t b = 0;
+    const DomainHost& h = c->doms[0];
+    for (int p = 0; p < part_count(h); ++p) b += (size_t)part_size(h, p) * c->esz;
+    return b;
+}
+
+// Keeps the host forward state (held at step `now`) as the checkpoint of that step, in pinned host
+// memory, once every copy of the previous batch has landed.
+fdtd_status ck_save(fdtd_ctx* c, long long now) {
+    CK(c, cudaStreamSynchronize(c->stream));
+    CK(c, cudaStreamSynchronize(c->d2h_stream));
+    void*& buf = c->ck[now];
+    if (!buf) {
+        cudaError_t e = cudaHostAlloc(&buf, state_bytes(c), cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->ck.erase(now);
+            return fail(c, FDTD_ENOMEM, "pinned host checkpoint allocation failed");
+        }
+    }
+    const DomainHost& h = c->doms[0];
+    size_t off = 0;
+    for (int p = 0; p < part_count(h); ++p) {
+        const size_t b = (size_t)part_size(h, p) * c->esz;
+        if (b) std::memcpy((char*)buf + off, part_ptr(h, 0, p, c->esz), b);
+        off += b;
+    }
+    return FDTD_OK;
+}
+
+// A checkpoint buffer seen as a set of home arrays (parts in id order, so the pole parts form one
+// contiguous block).
+fdtd_ctx::Workspace ck_view(const fdtd_ctx* c, void* buf) {
+    const DomainHost& h = c->doms[0];
+    fdtd_ctx::Workspace v;
+    size_t off = 0;
+    for (int p = 0; p < part_count(h); ++p) {
+        char* at = (char*)buf + off;
+        const long long n = part_size(h, p);
+        if (p < 6) v.F[p] = at;
+        else if (p < 12) v.psiE[(p - 6) / 2][(p - 6) % 2] = n ? at : nullptr;
+        else if (p < 18) v.psiH[(p - 12) / 2][(p - 12) % 2] = n ? at : nullptr;
+        else if (p == 18) v.ade = at;
+        off += (size_t)n * c->esz;
+    }
+    return v;
 }
 
 // n_steps forward steps of a host-streamed context, in batches of at most sk steps.
@@ -1355,7 +1453,18 @@ fdtd_status stream_forward(fdtd_ctx* c, int n_steps) {
     };
     int left = n_steps;
     while (left > 0) {
-        const int kb = std::min(left, c->sk);
+        int kb = std::min(left, c->sk);
+        if (c->ck_on) {
+            // batches aligned to the checkpoint grid; a batch start on it keeps the whole state
+            const long long now = c->step + (n_steps - left), rel = now - c->ck_t0;
+            if (rel >= 0) {
+                kb = (int)std::min<long long>(left, c->sk - rel % c->sk);
+                if (rel % c->sk == 0) {
+                    st = ck_save(c, now);
+                    if (st != FDTD_OK) return st;
+                }
+            }
+        }
         st = copy_in(0);
         if (st != FDTD_OK) return st;
         for (int s = 0; s < nsl; ++s) {
@@ -1431,12 +1540,16 @@ AdjCellArgs<T> make_adj_args(const fdtd_ctx* c, int di, int* mon) {
         a.hhi[q] = N - hi - (hi > 0 ? 1 : 0);
     }
     a.dom = di;
+    a.kz0 = 0;
+    a.nzg = h.n[2];
     if (h.design && h.grad) {
         for (int q = 0; q < 3; ++q) {
             a.glo[q] = h.glo[q];
             a.ghi[q] = h.ghi[q];
         }
         a.grad = h.grad;
+        a.gzg = h.glo[2];
+        a.gvol = (long long)(h.ghi[0] - h.glo[0]) * (h.ghi[1] - h.glo[1]) * (h.ghi[2] - h.glo[2]);
     }
     // bounding box of the monitor cells that carry an adjoint source
     *mon = 0;
@@ -1536,6 +1649,215 @@ void adj_once(fdtd_ctx* c, int m) {
     join_here();
 }
 
+// ---- host-streamed transposed sweep (Sec. 4.2) -------------------------------------------------
+// The transposed sweep runs the slab tiling in reverse.  Batches of kb <= sk steps (aligned to the
+// forward checkpoints) run last to first; for each slab its window replays the batch's forward steps
+// from the checkpoint at the batch start (keeping every replayed window state: the transposed step m
+// reads u^m for the material cotangent), then takes the kb transposed steps from the adjoint state
+// at the batch end (monitor cotangents injected over the whole window), completes the last one to
+// the natural form and writes its owned planes back; only owned design cells add to the material
+// cotangent.  A cut edge of a window acts as a PEC / open end and spoils one more plane per step, so
+// the owned planes come out exactly as the resident sweep computes them.  The adjoint state lives in
+// two pinned host sets (read at the batch end, written at the batch start).
+
+// Host adjoint sets, the device adjoint window, the replay windows and their descriptors.
+template <typename T>
+fdtd_status stream_adj_prepare(fdtd_ctx* c) {
+    if (c->hadj_ready) return FDTD_OK;
+    CK(c, cudaStreamSynchronize(c->stream));
+    const DomainHost& h = c->doms[0];
+    const long long nxy = (long long)h.n[0] * h.n[1];
+    const int nw = std::min(h.n[2], c->sw + 2 * c->sk);
+    for (int b = 0; b < 2; ++b) {
+        fdtd_ctx::Workspace& hs = c->hadj[b];
+        for (int f = 0; f < 6; ++f)
+            if (hmalloc(c, &hs.F[f], (size_t)h.ncell * c->esz) != FDTD_OK) return FDTD_ENOMEM;
+        for (int a = 0; a < 3; ++a)
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const long long n = part_size(h, 6 + 2 * a + s2);
+                if (n == 0) continue;
+                if (hmalloc(c, &hs.psiE[a][s2], (size_t)n * c->esz) != FDTD_OK ||
+                    hmalloc(c, &hs.psiH[a][s2], (size_t)n * c->esz) != FDTD_OK)
+                    return FDTD_ENOMEM;
+            }
+        if (h.npole > 0 && h.bcell > 0 && hmalloc(c, &hs.ade, (size_t)6 * h.npole * h.bcell * c->esz) != FDTD_OK)
+            return FDTD_ENOMEM;
+    }
+    const size_t fb = (size_t)nw * nxy * c->esz;
+    const size_t ab = (h.npole > 0 && h.bcell > 0)
+                          ? 6 * (size_t)h.npole * (h.bhi[0] - h.blo[0]) * (h.bhi[1] - h.blo[1]) *
+                                std::min(h.bhi[2] - h.blo[2], nw) * c->esz
+                          : 0;
+    for (int f = 0; f < 6; ++f)
+        if (dmalloc(c, &c->aws.F[f], fb) != FDTD_OK) return FDTD_ENOMEM;
+    for (int a = 0; a < 3; ++a)
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const long long per = psi_plane(h, a, s2);
+            if (per == 0) continue;
+            const size_t sb = (size_t)per * ((a + 1 + s2) % 3 == 2 ? h.ns[2] : nw) * c->esz;
+            if (dmalloc(c, &c->aws.psiE[a][s2], sb) || dmalloc(c, &c->aws.psiH[a][s2], sb)) return FDTD_ENOMEM;
+        }
+    if (ab && dmalloc(c, &c->aws.ade, ab) != FDTD_OK) return FDTD_ENOMEM;
+    c->rws.assign(c->sk, fdtd_ctx::Workspace());
+    for (auto& rw : c->rws) {
+        for (int f = 0; f < 6; ++f)
+            if (dmalloc(c, &rw.F[f], fb) != FDTD_OK) return FDTD_ENOMEM;
+        if (ab && dmalloc(c, &rw.ade, ab) != FDTD_OK) return FDTD_ENOMEM;
+    }
+    // descriptor (s, j): slab s's window with the replayed forward state j and the adjoint window
+    const int nsl = slab_count(c);
+    std::vector<Dom<T>> hd((size_t)nsl * c->sk);
+    for (int s2 = 0; s2 < nsl; ++s2)
+        for (int j = 0; j < c->sk; ++j) {
+            Dom<T> d = slab_dom<T>(c, s2);
+            for (int f = 0; f < 6; ++f) {
+                d.F[f] = (T*)c->rws[j].F[f];
+                d.A[f] = (T*)c->aws.F[f];
+            }
+            for (int a = 0; a < 3; ++a)
+                for (int q = 0; q < 2; ++q) {
+                    d.apsiE[a][q] = (T*)c->aws.psiE[a][q];
+                    d.apsiH[a][q] = (T*)c->aws.psiH[a][q];
+                }
+            d.ade = (T*)c->rws[j].ade;
+            d.aade = (T*)c->aws.ade;
+            hd[(size_t)s2 * c->sk + j] = d;
+        }
+    if (dmalloc(c, &c->d_adoms, sizeof(Dom<T>) * hd.size()) != FDTD_OK) return FDTD_ENOMEM;
+    CK(c, cudaMemcpy(c->d_adoms, hd.data(), sizeof(Dom<T>) * hd.size(), cudaMemcpyHostToDevice));
+    c->hadj_ready = 1;
+    return FDTD_OK;
+}
+
+// The domain's adjoint parts point at host set b (part access, the injection at the sweep start).
+fdtd_status stream_adj_bind(fdtd_ctx* c, int b) {
+    DomainHost& h = c->doms[0];
+    for (int f = 0; f < 6; ++f) h.A[f] = c->hadj[b].F[f];
+    for (int a = 0; a < 3; ++a)
+        for (int s2 = 0; s2 < 2; ++s2) {
+            h.apsiE[a][s2] = c->hadj[b].psiE[a][s2];
+            h.apsiH[a][s2] = c->hadj[b].psiH[a][s2];
+        }
+    h.aade = c->hadj[b].ade;
+    c->hadj_cur = b;
+    return sync_doms(c);
+}
+
+// Transposed-kernel arguments of slab s's window with replayed forward state j.
+template <typename T>
+AdjCellArgs<T> window_adj_args(const fdtd_ctx* c, int s, int j, int* mon) {
+    const DomainHost& h = c->doms[0];
+    const SlabWin w = slab_win(c, s);
+    const fdtd_ctx::Workspace& ws = c->ws[s % 3];
+    AdjCellArgs<T> a = make_adj_args<T>(c, 0, mon);
+    for (int f = 0; f < 6; ++f) {
+        a.A[f] = (T*)c->aws.F[f];
+        a.F[f] = (const T*)c->rws[j].F[f];
+    }
+    for (int q = 0; q < 3; ++q) {
+        a.ie[q] = (const T*)ws.ie[ie_first(h, q)];
+        for (int s2 = 0; s2 < 2; ++s2) {
+            a.apsiE[q][s2] = (T*)c->aws.psiE[q][s2];
+            a.apsiH[q][s2] = (T*)c->aws.psiH[q][s2];
+        }
+    }
+    a.n[2] = w.whi - w.wlo;
+    a.kz0 = w.wlo;
+    a.nzg = h.n[2];
+    a.dom = s * c->sk + j;
+    if (a.grad) {
+        // only owned design cells add to the material cotangent
+        const int z0 = std::max(h.glo[2], w.zs), z1 = std::min(h.ghi[2], w.ze);
+        if (z1 > z0) {
+            a.glo[2] = z0 - w.wlo;
+            a.ghi[2] = z1 - w.wlo;
+        } else {
+            a.grad = nullptr;
+            for (int q = 0; q < 3; ++q) a.glo[q] = a.ghi[q] = 0;
+        }
+    }
+    return a;
+}
+
+template <typename T>
+fdtd_status stream_adjoint(fdtd_ctx* c, int n_steps) {
+    fdtd_status st = stream_prepare<T>(c);
+    if (st != FDTD_OK) return st;
+    st = stream_adj_prepare<T>(c);
+    if (st != FDTD_OK) return st;
+    const DomainHost& h = c->doms[0];
+    const int nsl = slab_count(c);
+    const Launch l{c->stream, &c->launches};
+    const Dom<T>* sd = (const Dom<T>*)c->d_sdoms;
+    const Dom<T>* ad = (const Dom<T>*)c->d_adoms;
+    const long long nxy = (long long)h.n[0] * h.n[1];
+    StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.srcs = c->d_srcs;
+    a.mons = c->d_mons;
+    a.d_step = c->d_step;
+    a.d_ticket = c->d_ticket;
+    a.d_base = c->d_base;
+    int left = n_steps;
+    while (left > 0) {
+        const long long te = c->adj_step;
+        const long long tb = c->ck_t0 + ((te - 1 - c->ck_t0) / c->sk) * c->sk;
+        const int kb = (int)(te - tb);
+        auto it = c->ck.find(tb);
+        if (te <= c->ck_t0 || kb > left || it == c->ck.end())
+            return fail(c, FDTD_ESTATE, "a streamed transposed batch needs the forward checkpoint of step " +
+                                            std::to_string(tb) + " and all of its " + std::to_string(kb) + " steps");
+        const fdtd_ctx::Workspace ckv = ck_view(c, it->second);
+        const int cur = c->hadj_cur, nxt = 1 - cur;
+        for (int s2 = 0; s2 < nsl; ++s2) {
+            const int r = s2 % 3;
+            const SlabWin w = slab_win(c, s2);
+            const size_t wb = (size_t)(w.whi - w.wlo) * nxy * c->esz;
+            const size_t ab = (w.zb1 > w.zb0) ? 6 * (size_t)h.npole * (h.bhi[0] - h.blo[0]) * (h.bhi[1] - h.blo[1]) *
+                                                    (w.zb1 - w.zb0) * c->esz
+                                              : 0;
+            const int poles = h.npole > 0 && w.zb1 > w.zb0;
+            // forward window at the batch start, then its replay (the step index of the sources is
+            // the global one: the batch base tb plus the position in the batch)
+            st = window_copy(c, w, ckv, c->ws[r], w.wlo, w.whi, true, true, c->stream);
+            if (st != FDTD_OK) return st;
+            c->h_step_tmp = (int)tb;
+            CK(c, cudaMemcpyAsync(c->d_base, &c->h_step_tmp, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+            CK(c, cudaStreamSynchronize(c->stream));
+            const CellArgs<T> ce = stream_cell_args<T>(c, s2, true), ch = stream_cell_args<T>(c, s2, false);
+            for (int j = 0; j < kb; ++j) {
+                for (int f = 0; f < 6; ++f)
+                    CK(c, cudaMemcpyAsync(c->rws[j].F[f], c->ws[r].F[f], wb, cudaMemcpyDeviceToDevice, c->stream));
+                if (ab) CK(c, cudaMemcpyAsync(c->rws[j].ade, c->ws[r].ade, ab, cudaMemcpyDeviceToDevice, c->stream));
+                if (j + 1 == kb) break;
+                a.offset = j;
+                launch_e_cell<T>(l, ce, sd, (T)c->S, a, c->aniso, poles);
+                launch_h_cell<T>(l, ch, (T)c->S, a);
+            }
+            // adjoint window at the batch end, kb transposed steps, natural form, owned planes out
+            st = window_copy(c, w, c->hadj[cur], c->aws, w.wlo, w.whi, true, false, c->stream);
+            if (st != FDTD_OK) return st;
+            AdjCellArgs<T> aa;
+            for (int j = kb - 1; j >= 0; --j) {
+                int mon = 0;
+                aa = window_adj_args<T>(c, s2, j, &mon);
+                launch_adj_e_cell<T>(l, aa, ad, c->d_mons, (T)c->S, (int)(tb + j), j < kb - 1 ? 1 : 0, poles, mon, 0);
+                launch_adj_h_cell<T>(l, aa, ad, c->d_mons, (T)c->S, (int)(tb + j), mon);
+            }
+            launch_adj_flush_cell<T>(l, aa, ad, (T)c->S, poles);
+            st = window_copy(c, w, c->hadj[nxt], c->aws, w.zs, w.ze, false, false, c->stream);
+            if (st != FDTD_OK) return st;
+        }
+        CK(c, cudaStreamSynchronize(c->stream));
+        st = stream_adj_bind(c, nxt);
+        if (st != FDTD_OK) return st;
+        c->adj_step = tb;
+        left -= kb;
+    }
+    CKL(c);
+    return FDTD_OK;
+}
+
 constexpr int kGraphSteps = 32;
 
 void drop_graphs(fdtd_ctx* c) {
@@ -1591,10 +1913,24 @@ fdtd_status build_graph(fdtd_ctx* c) {
 
 fdtd_status flush_adjoint(fdtd_ctx* c) {
     if (!c->adj_pending) return FDTD_OK;
-    if (c->dtype == FDTD_F32)
+    if (c->cell_mode) {
+        // the per-cell form, with the arithmetic of the per-cell transposed kernels
+        for (int di = 0; di < (int)c->doms.size(); ++di) {
+            int mon = 0;
+            const DomainHost& h = c->doms[di];
+            const int poles = h.npole > 0 && h.bcell > 0;
+            if (c->dtype == FDTD_F32)
+                launch_adj_flush_cell<float>(L(c), make_adj_args<float>(c, di, &mon), (const Dom<float>*)c->d_doms,
+                                             (float)c->S, poles);
+            else
+                launch_adj_flush_cell<double>(L(c), make_adj_args<double>(c, di, &mon), (const Dom<double>*)c->d_doms,
+                                              c->S, poles);
+        }
+    } else if (c->dtype == FDTD_F32) {
         launch_adj_flush<float>(L(c), (const Dom<float>*)c->d_doms, c->d_tiles, (int)c->tiles.size(), (float)c->S);
-    else
+    } else {
         launch_adj_flush<double>(L(c), (const Dom<double>*)c->d_doms, c->d_tiles, (int)c->tiles.size(), c->S);
+    }
     for (int di = 0; di < (int)c->doms.size(); ++di) {
         if (!c->doms[di].bloch) continue;   // the imaginary E part of a Bloch domain
         int mon = 0;
@@ -2011,6 +2347,7 @@ fdtd_status fdtd_destroy(fdtd_ctx* ctx) {
             if (e) cudaEventDestroy(e);
     for (void* p : ctx->owned) cudaFree(p);
     for (void* p : ctx->host_owned) cudaFreeHost(p);
+    for (auto& kv : ctx->ck) cudaFreeHost(kv.second);
     for (auto& s : ctx->slots) cudaFree(s.second.buf);
     delete ctx;
     return FDTD_OK;
@@ -2355,6 +2692,18 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
     return FDTD_OK;
 }
 
+fdtd_status fdtd_stream_checkpoints(fdtd_ctx* ctx, int32_t enabled) {
+    GUARD(ctx);
+    if (!ctx->streamed) return fail(ctx, FDTD_EINVAL, "forward checkpoints in host memory belong to a streamed context");
+    if (enabled != 0 && enabled != 1) return fail(ctx, FDTD_EINVAL, "enabled must be 0 or 1");
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto& kv : ctx->ck) cudaFreeHost(kv.second);
+    ctx->ck.clear();
+    ctx->ck_on = enabled;
+    ctx->ck_t0 = ctx->step;
+    return FDTD_OK;
+}
+
 fdtd_status fdtd_record_interface(fdtd_ctx* ctx, int32_t capacity) {
     GUARD(ctx);
     NOT_STREAMED(ctx);
@@ -2608,8 +2957,9 @@ fdtd_status fdtd_get_part(fdtd_ctx* ctx, int32_t domain, int32_t which, int32_t 
     if (!valid_dom(ctx, domain) || (which != 0 && which != 1) || !dst) return fail(ctx, FDTD_EINVAL, "bad arguments");
     const DomainHost& d = ctx->doms[domain];
     if (part < 0 || part >= part_count(d)) return fail(ctx, FDTD_EINVAL, "bad part id");
-    if (which == 1 && ctx->streamed) return fail(ctx, FDTD_EINVAL, "a host-streamed context has no adjoint state");
-    if (which == 1) {
+    if (which == 1 && ctx->streamed && !ctx->hadj_ready)
+        return fail(ctx, FDTD_ESTATE, "a host-streamed context has an adjoint state after fdtd_adjoint_begin");
+    if (which == 1 && !ctx->streamed) {
         fdtd_status st = flush_adjoint(ctx);
         if (st != FDTD_OK) return st;
     }
@@ -2625,8 +2975,9 @@ fdtd_status fdtd_set_part(fdtd_ctx* ctx, int32_t domain, int32_t which, int32_t 
     if (!valid_dom(ctx, domain) || (which != 0 && which != 1) || !src) return fail(ctx, FDTD_EINVAL, "bad arguments");
     const DomainHost& d = ctx->doms[domain];
     if (part < 0 || part >= part_count(d)) return fail(ctx, FDTD_EINVAL, "bad part id");
-    if (which == 1 && ctx->streamed) return fail(ctx, FDTD_EINVAL, "a host-streamed context has no adjoint state");
-    if (which == 1) {
+    if (which == 1 && ctx->streamed && !ctx->hadj_ready)
+        return fail(ctx, FDTD_ESTATE, "a host-streamed context has an adjoint state after fdtd_adjoint_begin");
+    if (which == 1 && !ctx->streamed) {
         fdtd_status st = flush_adjoint(ctx);
         if (st != FDTD_OK) return st;
     }
@@ -2786,7 +3137,6 @@ fdtd_status fdtd_snapshots_free(fdtd_ctx* ctx) {
 
 fdtd_status fdtd_set_design(fdtd_ctx* ctx, int32_t domain, const int32_t lo[3], const int32_t hi[3], double* grad) {
     GUARD(ctx);
-    NOT_STREAMED(ctx);
     if (!valid_dom(ctx, domain)) return fail(ctx, FDTD_EINVAL, "bad domain");
     DomainHost& d = ctx->doms[domain];
     if (d.bloch && grad) return fail(ctx, FDTD_EINVAL, "a Bloch domain carries no design box");
@@ -2852,7 +3202,6 @@ fdtd_status fdtd_pole_grad(fdtd_ctx* ctx, int32_t domain, double* host_out) {
 
 fdtd_status fdtd_set_adjoint_source(fdtd_ctx* ctx, int32_t monitor_id, const void* cot) {
     GUARD(ctx);
-    NOT_STREAMED(ctx);
     if (monitor_id < 0 || monitor_id >= (int)ctx->mons.size()) return fail(ctx, FDTD_EINVAL, "bad monitor id");
     ctx->mons[monitor_id].m.cot = (const double2*)cot;
     return sync_mons(ctx);
@@ -2860,13 +3209,27 @@ fdtd_status fdtd_set_adjoint_source(fdtd_ctx* ctx, int32_t monitor_id, const voi
 
 fdtd_status fdtd_adjoint_begin(fdtd_ctx* ctx) {
     GUARD(ctx);
-    NOT_STREAMED(ctx);
-    for (auto& d : ctx->doms)
+    if (ctx->streamed) {
+        // the adjoint state lives in pinned host memory: set 0 of the two host sets, zeroed
+        fdtd_status st = ctx->dtype == FDTD_F32 ? stream_adj_prepare<float>(ctx) : stream_adj_prepare<double>(ctx);
+        if (st != FDTD_OK) return st;
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        st = stream_adj_bind(ctx, 0);
+        if (st != FDTD_OK) return st;
+        const DomainHost& d = ctx->doms[0];
         for (int p = 0; p < part_count(d); ++p) {
             void* ptr = part_ptr(d, 1, p, ctx->esz);
             const long long n = part_size(d, p);
-            if (ptr && n) CK(ctx, cudaMemsetAsync(ptr, 0, (size_t)n * ctx->esz, ctx->stream));
+            if (ptr && n) std::memset(ptr, 0, (size_t)n * ctx->esz);
         }
+    } else {
+        for (auto& d : ctx->doms)
+            for (int p = 0; p < part_count(d); ++p) {
+                void* ptr = part_ptr(d, 1, p, ctx->esz);
+                const long long n = part_size(d, p);
+                if (ptr && n) CK(ctx, cudaMemsetAsync(ptr, 0, (size_t)n * ctx->esz, ctx->stream));
+            }
+    }
     for (auto& d : ctx->doms)
         if (d.pgc_on) CK(ctx, cudaMemsetAsync(d.pgc, 0, sizeof(double) * 6 * kMaxPole, ctx->stream));
     ctx->adj_step = ctx->step;
@@ -2892,8 +3255,19 @@ fdtd_status fdtd_adjoint_begin(fdtd_ctx* ctx) {
 
 fdtd_status fdtd_step_adjoint(fdtd_ctx* ctx, int32_t n_steps) {
     GUARD(ctx);
-    NOT_STREAMED(ctx);
     if (n_steps < 0 || n_steps > ctx->adj_step) return fail(ctx, FDTD_EINVAL, "n_steps out of range");
+    if (ctx->streamed) {
+        if (!ctx->hadj_ready || !ctx->ck_on)
+            return fail(ctx, FDTD_ESTATE, "a streamed transposed sweep needs forward checkpoints "
+                                          "(fdtd_stream_checkpoints) and fdtd_adjoint_begin");
+        if (!ctx->mons.empty()) {
+            fdtd_status st = ensure_phase(ctx, ctx->adj_step + 2, nullptr);
+            if (st != FDTD_OK) return st;
+            st = sync_mons(ctx);
+            if (st != FDTD_OK) return st;
+        }
+        return ctx->dtype == FDTD_F32 ? stream_adjoint<float>(ctx, n_steps) : stream_adjoint<double>(ctx, n_steps);
+    }
     bool design = false;
     for (auto& d : ctx->doms) design = design || d.design;
     if (design && n_steps > 0 && (n_steps != 1 || ctx->step != ctx->adj_step - 1))

@@ -336,6 +336,12 @@ struct AdjCellArgs {
     // coordinates [elo, ehi) / [hlo, hhi) per axis where the E-side (H-side) gather meets no slab
     // node (and, H side, no PEC-held node): a cell inside on all three axes takes the plain form
     int elo[3], ehi[3], hlo[3], hhi[3];
+    // z window of a host-streamed slab (see CellArgs): local plane k is global plane k + kz0 of a
+    // domain of nzg planes (CPML z profile, plain ranges, monitors); resident: kz0 = 0, nzg = n[2].
+    // The design box [glo, ghi) is given in local planes; its gradient buffer is indexed as the
+    // whole box, whose first global plane is gzg and whose cell count is gvol.
+    int kz0, nzg, gzg;
+    long long gvol;
 };
 
 // A Bloch domain's operands (Sec. 2.2): the per-cell arguments of its real parts plus the
@@ -401,6 +407,10 @@ void launch_adj_e_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* d
 template <typename T>
 void launch_adj_h_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, const Mon* mons, T S, int m,
                        int mon);
+// Completes a pending transposed step (the deferred own-cell part of the E side) for every cell of
+// one domain or window, per cell; poles: the descriptor doms[c.dom] holds the pole box.
+template <typename T>
+void launch_adj_flush_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, T S, int poles);
 template <typename T>
 void launch_inject(const Launch& L, const Dom<T>* doms, const Mon* mons, const int* entries, int nentries,
                    long long nthreads, const long long* entry_begin, int step, int kind);

@@ -656,11 +656,11 @@ __device__ __forceinline__ long long slab_off_c(const int* n, const int* ns, int
 // Dbar of a derivative at node (i, j, k) whose coordinate along axis q is x and slab index sl
 // (-1 outside the slabs): coef is the axis' CPML row [b | c | 1/kappa], psi its memory cotangents.
 template <typename T>
-__device__ __forceinline__ T dbar_node(const T* coef, const T* psi, const int* n, const int* ns, int q, int i, int j,
-                                       int k, int x, int sl, T yb) {
+__device__ __forceinline__ T dbar_node(const T* coef, int N, const T* psi, const int* n, const int* ns, int q, int i,
+                                       int j, int k, int x, int sl, T yb) {
     if (sl < 0) return yb;
     const T ps = psi[slab_off_c(n, ns, q, i, j, k, sl)];
-    return coef[2 * n[q] + x] * yb + coef[n[q] + x] * (ps + yb);
+    return coef[2 * N + x] * yb + coef[N + x] * (ps + yb);
 }
 
 __device__ __forceinline__ bool in_box3(const int* lo, const int* hi, int i, int j, int k) {
@@ -688,7 +688,7 @@ __device__ __forceinline__ T adj_e_comp(const AdjCellArgs<T>& c, const Dom<T>* _
                                         T gat, T S, int m, int pending, bool disp, long long bo, const int* sl,
                                         const long long* om, double* pacc) {
     constexpr int q0 = (a + 1) % 3, q1 = (a + 2) % 3;
-    const int x[3] = {i, j, k};
+    const int x[3] = {i, j, k + c.kz0};   // coefficient rows are indexed by global coordinates
     T eb;
     if (pending) {
         if (kPoles && disp) {
@@ -718,7 +718,8 @@ __device__ __forceinline__ T adj_e_comp(const AdjCellArgs<T>& c, const Dom<T>* _
         eb = F;
     }
     eb += gat;
-    if (kMon && in_box3(c.mlo, c.mhi, i, j, k)) eb += (T)inject_at(doms[c.dom], mons, a, i, j, k, (long long)m * 2 + 0);
+    if (kMon && in_box3(c.mlo, c.mhi, i, j, k + c.kz0))
+        eb += (T)inject_at(doms[c.dom], mons, a, i, j, k + c.kz0, (long long)m * 2 + 0);
     T et = eb, gdisp = T(0);
     if (kPoles && disp) {
         const Dom<T>& d = doms[c.dom];
@@ -749,10 +750,9 @@ __device__ __forceinline__ T adj_e_comp(const AdjCellArgs<T>& c, const Dom<T>* _
         }
         const double r = 1.0 / (1.0 + (double)ie * (double)gdisp);
         if (gcell) {
-            const long long gi = ((long long)(k - c.glo[2]) * (c.ghi[1] - c.glo[1]) + (j - c.glo[1])) *
+            const long long gi = ((long long)(k + c.kz0 - c.gzg) * (c.ghi[1] - c.glo[1]) + (j - c.glo[1])) *
                                      (c.ghi[0] - c.glo[0]) + (i - c.glo[0]);
-            const long long gn = (long long)(c.ghi[0] - c.glo[0]) * (c.ghi[1] - c.glo[1]) * (c.ghi[2] - c.glo[2]);
-            c.grad[a * gn + gi] += (double)et * delta * r * r;
+            c.grad[a * c.gvol + gi] += (double)et * delta * r * r;
         }
         if (pcell) {
             // pole-coefficient cotangents (the algebra of adj_e_column): with u = xbar_P - rho et,
@@ -790,6 +790,7 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
     const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
     if (i >= nx || j >= ny) return;
+    const int kg = k + c.kz0;   // global plane (CPML z profile, monitors, plain ranges)
     const long long nxy = (long long)nx * ny;
     const long long pl = (long long)k * nxy;   // first cell of this z-plane (block-uniform)
     const int ij = j * nx + i;                  // offset inside the plane
@@ -823,7 +824,7 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
     const unsigned am = __activemask();
     const bool plain = (unsigned)(i - c.elo[0]) < (unsigned)(c.ehi[0] - c.elo[0]) &&
                        (unsigned)(j - c.elo[1]) < (unsigned)(c.ehi[1] - c.elo[1]) &&
-                       (unsigned)(k - c.elo[2]) < (unsigned)(c.ehi[2] - c.elo[2]);
+                       (unsigned)(kg - c.elo[2]) < (unsigned)(c.ehi[2] - c.elo[2]);
     if (__all_sync(am, plain)) {
         const int none[3] = {-1, -1, -1};
         const T g0 = S * ((by - by_zm) - (bz - bz_ym));
@@ -843,12 +844,12 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
     // slab index of this node along each axis (-1: outside the slabs); the -1 node lies in a slab
     // only where this node is the first one past the low slab
     const int sl[3] = {slab_or_none(i, c.dlo[0], c.dhi[0], nx, c.ns[0]), slab_or_none(j, c.dlo[1], c.dhi[1], ny, c.ns[1]),
-                       slab_or_none(k, c.dlo[2], c.dhi[2], nz, c.ns[2])};
+                       slab_or_none(kg, c.dlo[2], c.dhi[2], c.nzg, c.ns[2])};
     // per axis, decided for the whole warp: a warp with any lane near a slab of that axis takes the
     // general form, whose per-lane slab checks give the plain values elsewhere
     const bool px_plain = __all_sync(am, sl[0] < 0 && !(i > 0 && i == c.dlo[0]));
     const bool py_plain = __all_sync(am, sl[1] < 0 && !(j > 0 && j == c.dlo[1]));
-    const bool pz_plain = __all_sync(am, sl[2] < 0 && !(k > 0 && k == c.dlo[2]));
+    const bool pz_plain = __all_sync(am, sl[2] < 0 && !(k > 0 && kg == c.dlo[2]));
     // gathered transposes of the H update's derivatives: the q-derivative of H_c has ybar = -S Hbar_c
     // for s = 0 of H_c and +S Hbar_c for s = 1; E_a gathers its two curl terms at this node and at
     // -1.  Per axis, without a slab node among the two the Dbar are the ybar themselves.
@@ -858,11 +859,11 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
         g0 = S * (by - by_zm);
         g1 = -(S * (bx - bx_zm));
     } else {
-        const int szm = k > 0 ? slab_or_none(k - 1, c.dlo[2], c.dhi[2], nz, c.ns[2]) : -1;
-        const T tyz = dbar_node(c.cH[2], c.apsiH[1][0], c.n, c.ns, 2, i, j, k, k, sl[2], -S * by);
-        const T tyz_m = hz_ ? dbar_node(c.cH[2], c.apsiH[1][0], c.n, c.ns, 2, i, j, k - 1, k - 1, szm, -S * by_zm) : T(0);
-        const T txz = dbar_node(c.cH[2], c.apsiH[0][1], c.n, c.ns, 2, i, j, k, k, sl[2], S * bx);
-        const T txz_m = hz_ ? dbar_node(c.cH[2], c.apsiH[0][1], c.n, c.ns, 2, i, j, k - 1, k - 1, szm, S * bx_zm) : T(0);
+        const int szm = k > 0 ? slab_or_none(kg - 1, c.dlo[2], c.dhi[2], c.nzg, c.ns[2]) : -1;
+        const T tyz = dbar_node(c.cH[2], c.nzg, c.apsiH[1][0], c.n, c.ns, 2, i, j, k, kg, sl[2], -S * by);
+        const T tyz_m = hz_ ? dbar_node(c.cH[2], c.nzg, c.apsiH[1][0], c.n, c.ns, 2, i, j, k - 1, kg - 1, szm, -S * by_zm) : T(0);
+        const T txz = dbar_node(c.cH[2], c.nzg, c.apsiH[0][1], c.n, c.ns, 2, i, j, k, kg, sl[2], S * bx);
+        const T txz_m = hz_ ? dbar_node(c.cH[2], c.nzg, c.apsiH[0][1], c.n, c.ns, 2, i, j, k - 1, kg - 1, szm, S * bx_zm) : T(0);
         g0 = tyz_m - tyz;
         g1 = txz_m - txz;
     }
@@ -872,10 +873,10 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
         g2 = S * (bx - bx_ym);
     } else {
         const int sym = j > 0 ? slab_or_none(j - 1, c.dlo[1], c.dhi[1], ny, c.ns[1]) : -1;
-        const T tzy = dbar_node(c.cH[1], c.apsiH[2][1], c.n, c.ns, 1, i, j, k, j, sl[1], S * bz);
-        const T tzy_m = hy_ ? dbar_node(c.cH[1], c.apsiH[2][1], c.n, c.ns, 1, i, j - 1, k, j - 1, sym, S * bz_ym) : T(0);
-        const T txy = dbar_node(c.cH[1], c.apsiH[0][0], c.n, c.ns, 1, i, j, k, j, sl[1], -S * bx);
-        const T txy_m = hy_ ? dbar_node(c.cH[1], c.apsiH[0][0], c.n, c.ns, 1, i, j - 1, k, j - 1, sym, -S * bx_ym) : T(0);
+        const T tzy = dbar_node(c.cH[1], c.n[1], c.apsiH[2][1], c.n, c.ns, 1, i, j, k, j, sl[1], S * bz);
+        const T tzy_m = hy_ ? dbar_node(c.cH[1], c.n[1], c.apsiH[2][1], c.n, c.ns, 1, i, j - 1, k, j - 1, sym, S * bz_ym) : T(0);
+        const T txy = dbar_node(c.cH[1], c.n[1], c.apsiH[0][0], c.n, c.ns, 1, i, j, k, j, sl[1], -S * bx);
+        const T txy_m = hy_ ? dbar_node(c.cH[1], c.n[1], c.apsiH[0][0], c.n, c.ns, 1, i, j - 1, k, j - 1, sym, -S * bx_ym) : T(0);
         g0 += tzy_m - tzy;
         g2 = txy_m - txy;
     }
@@ -885,10 +886,10 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
         g2 -= S * (by - by_xm);
     } else {
         const int sxm = i > 0 ? slab_or_none(i - 1, c.dlo[0], c.dhi[0], nx, c.ns[0]) : -1;
-        const T tzx = dbar_node(c.cH[0], c.apsiH[2][0], c.n, c.ns, 0, i, j, k, i, sl[0], -S * bz);
-        const T tzx_m = hx_ ? dbar_node(c.cH[0], c.apsiH[2][0], c.n, c.ns, 0, i - 1, j, k, i - 1, sxm, -S * bz_xm) : T(0);
-        const T tyx = dbar_node(c.cH[0], c.apsiH[1][1], c.n, c.ns, 0, i, j, k, i, sl[0], S * by);
-        const T tyx_m = hx_ ? dbar_node(c.cH[0], c.apsiH[1][1], c.n, c.ns, 0, i - 1, j, k, i - 1, sxm, S * by_xm) : T(0);
+        const T tzx = dbar_node(c.cH[0], c.n[0], c.apsiH[2][0], c.n, c.ns, 0, i, j, k, i, sl[0], -S * bz);
+        const T tzx_m = hx_ ? dbar_node(c.cH[0], c.n[0], c.apsiH[2][0], c.n, c.ns, 0, i - 1, j, k, i - 1, sxm, -S * bz_xm) : T(0);
+        const T tyx = dbar_node(c.cH[0], c.n[0], c.apsiH[1][1], c.n, c.ns, 0, i, j, k, i, sl[0], S * by);
+        const T tyx_m = hx_ ? dbar_node(c.cH[0], c.n[0], c.apsiH[1][1], c.n, c.ns, 0, i - 1, j, k, i - 1, sxm, S * by_xm) : T(0);
         g1 += tzx_m - tzx;
         g2 += tyx_m - tyx;
     }
@@ -940,6 +941,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
     const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
     if (i >= nx || j >= ny) return;
+    const int kg = k + c.kz0;   // global plane (CPML z profile, monitors, plain ranges)
     const long long nxy = (long long)nx * ny;
     const long long pl = (long long)k * nxy;   // first cell of this z-plane (block-uniform)
     const int ij = j * nx + i;
@@ -961,16 +963,16 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
     const unsigned am = __activemask();
     const bool plain = (unsigned)(i - c.hlo[0]) < (unsigned)(c.hhi[0] - c.hlo[0]) &&
                        (unsigned)(j - c.hlo[1]) < (unsigned)(c.hhi[1] - c.hlo[1]) &&
-                       (unsigned)(k - c.hlo[2]) < (unsigned)(c.hhi[2] - c.hlo[2]);
+                       (unsigned)(kg - c.hlo[2]) < (unsigned)(c.hhi[2] - c.hlo[2]) && k > 0;
     if (__all_sync(am, plain)) {
         T h0 = b0 + (fy - fy_zp) + (fz_yp - fz);
         T h1 = b1 + (fz - fz_xp) + (fx_zp - fx);
         T h2 = b2 + (fx - fx_yp) + (fy_xp - fy);
-        if (kMon && m >= 1 && in_box3(c.mlo, c.mhi, i, j, k)) {
+        if (kMon && m >= 1 && in_box3(c.mlo, c.mhi, i, j, kg)) {
             const Dom<T>& d = doms[c.dom];
-            h0 += (T)inject_at(d, mons, 3, i, j, k, (long long)(m - 1) * 2 + 1);
-            h1 += (T)inject_at(d, mons, 4, i, j, k, (long long)(m - 1) * 2 + 1);
-            h2 += (T)inject_at(d, mons, 5, i, j, k, (long long)(m - 1) * 2 + 1);
+            h0 += (T)inject_at(d, mons, 3, i, j, kg, (long long)(m - 1) * 2 + 1);
+            h1 += (T)inject_at(d, mons, 4, i, j, kg, (long long)(m - 1) * 2 + 1);
+            h2 += (T)inject_at(d, mons, 5, i, j, kg, (long long)(m - 1) * 2 + 1);
         }
         B0[ij] = h0;
         B1[ij] = h1;
@@ -983,11 +985,11 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
     // the last one before the high slab
     const int sx = slab_or_none(i, c.dlo[0], c.dhi[0], nx, c.ns[0]);
     const int sy = slab_or_none(j, c.dlo[1], c.dhi[1], ny, c.ns[1]);
-    const int sz = slab_or_none(k, c.dlo[2], c.dhi[2], nz, c.ns[2]);
+    const int sz = slab_or_none(kg, c.dlo[2], c.dhi[2], c.nzg, c.ns[2]);
     // per axis, decided for the whole warp (see k_adj_e_cell)
     const bool px_plain = __all_sync(am, !edge && sx < 0 && !(c.dhi[0] > 0 && i + 1 == nx - c.dhi[0]));
     const bool py_plain = __all_sync(am, !edge && sy < 0 && !(c.dhi[1] > 0 && j + 1 == ny - c.dhi[1]));
-    const bool pz_plain = __all_sync(am, !edge && sz < 0 && !(c.dhi[2] > 0 && k + 1 == nz - c.dhi[2]));
+    const bool pz_plain = __all_sync(am, !edge && sz < 0 && !(c.dhi[2] > 0 && kg + 1 == c.nzg - c.dhi[2]));
     // transposes of the E update's derivatives: E_e's s = 0 derivative has ybar = +F_e, s = 1 has
     // -F_e; H_c gathers them at this node and at +1.  PEC-held E nodes carry no cotangent (a +1 node
     // reached by wrapping is no PEC node).  Per axis, away from PEC planes and without a slab node
@@ -998,11 +1000,11 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
         h0 += fy - fy_zp;
         h1 += fx_zp - fx;
     } else {
-        const int szp = k + 1 < nz ? slab_or_none(k + 1, c.dlo[2], c.dhi[2], nz, c.ns[2]) : -1;
-        const T tyz_k = (pi || pk) ? T(0) : dbar_node(c.cE[2], c.apsiE[1][0], c.n, c.ns, 2, i, j, k, k, sz, fy);
-        const T tyz_n = (!ze || pi) ? T(0) : dbar_node(c.cE[2], c.apsiE[1][0], c.n, c.ns, 2, i, j, k + 1, k + 1, szp, fy_zp);
-        const T txz_k = (pj || pk) ? T(0) : dbar_node(c.cE[2], c.apsiE[0][1], c.n, c.ns, 2, i, j, k, k, sz, -fx);
-        const T txz_n = (!ze || pj) ? T(0) : dbar_node(c.cE[2], c.apsiE[0][1], c.n, c.ns, 2, i, j, k + 1, k + 1, szp, -fx_zp);
+        const int szp = k + 1 < nz ? slab_or_none(kg + 1, c.dlo[2], c.dhi[2], c.nzg, c.ns[2]) : -1;
+        const T tyz_k = (pi || pk) ? T(0) : dbar_node(c.cE[2], c.nzg, c.apsiE[1][0], c.n, c.ns, 2, i, j, k, kg, sz, fy);
+        const T tyz_n = (!ze || pi) ? T(0) : dbar_node(c.cE[2], c.nzg, c.apsiE[1][0], c.n, c.ns, 2, i, j, k + 1, kg + 1, szp, fy_zp);
+        const T txz_k = (pj || pk) ? T(0) : dbar_node(c.cE[2], c.nzg, c.apsiE[0][1], c.n, c.ns, 2, i, j, k, kg, sz, -fx);
+        const T txz_n = (!ze || pj) ? T(0) : dbar_node(c.cE[2], c.nzg, c.apsiE[0][1], c.n, c.ns, 2, i, j, k + 1, kg + 1, szp, -fx_zp);
         h0 += tyz_k - tyz_n;
         h1 += txz_k - txz_n;
     }
@@ -1012,10 +1014,10 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
         h2 += fx - fx_yp;
     } else {
         const int syp = j + 1 < ny ? slab_or_none(j + 1, c.dlo[1], c.dhi[1], ny, c.ns[1]) : -1;
-        const T tzy = (pi || pj) ? T(0) : dbar_node(c.cE[1], c.apsiE[2][1], c.n, c.ns, 1, i, j, k, j, sy, -fz);
-        const T tzy_p = (!ye || pi) ? T(0) : dbar_node(c.cE[1], c.apsiE[2][1], c.n, c.ns, 1, i, j + 1, k, j + 1, syp, -fz_yp);
-        const T txy = (pk || pj) ? T(0) : dbar_node(c.cE[1], c.apsiE[0][0], c.n, c.ns, 1, i, j, k, j, sy, fx);
-        const T txy_p = (!ye || pk) ? T(0) : dbar_node(c.cE[1], c.apsiE[0][0], c.n, c.ns, 1, i, j + 1, k, j + 1, syp, fx_yp);
+        const T tzy = (pi || pj) ? T(0) : dbar_node(c.cE[1], c.n[1], c.apsiE[2][1], c.n, c.ns, 1, i, j, k, j, sy, -fz);
+        const T tzy_p = (!ye || pi) ? T(0) : dbar_node(c.cE[1], c.n[1], c.apsiE[2][1], c.n, c.ns, 1, i, j + 1, k, j + 1, syp, -fz_yp);
+        const T txy = (pk || pj) ? T(0) : dbar_node(c.cE[1], c.n[1], c.apsiE[0][0], c.n, c.ns, 1, i, j, k, j, sy, fx);
+        const T txy_p = (!ye || pk) ? T(0) : dbar_node(c.cE[1], c.n[1], c.apsiE[0][0], c.n, c.ns, 1, i, j + 1, k, j + 1, syp, fx_yp);
         h0 += tzy - tzy_p;
         h2 += txy - txy_p;
     }
@@ -1025,10 +1027,10 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
         h2 += fy_xp - fy;
     } else {
         const int sxp = i + 1 < nx ? slab_or_none(i + 1, c.dlo[0], c.dhi[0], nx, c.ns[0]) : -1;
-        const T tzx = (pi || pj) ? T(0) : dbar_node(c.cE[0], c.apsiE[2][0], c.n, c.ns, 0, i, j, k, i, sx, fz);
-        const T tzx_p = (!xe || pj) ? T(0) : dbar_node(c.cE[0], c.apsiE[2][0], c.n, c.ns, 0, i + 1, j, k, i + 1, sxp, fz_xp);
-        const T tyx = (pk || pi) ? T(0) : dbar_node(c.cE[0], c.apsiE[1][1], c.n, c.ns, 0, i, j, k, i, sx, -fy);
-        const T tyx_p = (!xe || pk) ? T(0) : dbar_node(c.cE[0], c.apsiE[1][1], c.n, c.ns, 0, i + 1, j, k, i + 1, sxp, -fy_xp);
+        const T tzx = (pi || pj) ? T(0) : dbar_node(c.cE[0], c.n[0], c.apsiE[2][0], c.n, c.ns, 0, i, j, k, i, sx, fz);
+        const T tzx_p = (!xe || pj) ? T(0) : dbar_node(c.cE[0], c.n[0], c.apsiE[2][0], c.n, c.ns, 0, i + 1, j, k, i + 1, sxp, fz_xp);
+        const T tyx = (pk || pi) ? T(0) : dbar_node(c.cE[0], c.n[0], c.apsiE[1][1], c.n, c.ns, 0, i, j, k, i, sx, -fy);
+        const T tyx_p = (!xe || pk) ? T(0) : dbar_node(c.cE[0], c.n[0], c.apsiE[1][1], c.n, c.ns, 0, i + 1, j, k, i + 1, sxp, -fy_xp);
         h1 += tzx - tzx_p;
         h2 += tyx - tyx_p;
     }
@@ -1041,7 +1043,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
     }
     if (sz >= 0) {
         const long long o = slab_off_c(c.n, c.ns, 2, i, j, k, sz);
-        const T b = c.cH[2][k];
+        const T b = c.cH[2][kg];
         c.apsiH[0][1][o] = b * (c.apsiH[0][1][o] + S * b0);
         c.apsiH[1][0][o] = b * (c.apsiH[1][0][o] - S * b1);
     }
@@ -1051,15 +1053,78 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
         c.apsiH[1][1][o] = b * (c.apsiH[1][1][o] + S * b1);
         c.apsiH[2][0][o] = b * (c.apsiH[2][0][o] - S * b2);
     }
-    if (kMon && m >= 1 && in_box3(c.mlo, c.mhi, i, j, k)) {
+    if (kMon && m >= 1 && in_box3(c.mlo, c.mhi, i, j, kg)) {
         const Dom<T>& d = doms[c.dom];
-        h0 += (T)inject_at(d, mons, 3, i, j, k, (long long)(m - 1) * 2 + 1);
-        h1 += (T)inject_at(d, mons, 4, i, j, k, (long long)(m - 1) * 2 + 1);
-        h2 += (T)inject_at(d, mons, 5, i, j, k, (long long)(m - 1) * 2 + 1);
+        h0 += (T)inject_at(d, mons, 3, i, j, kg, (long long)(m - 1) * 2 + 1);
+        h1 += (T)inject_at(d, mons, 4, i, j, kg, (long long)(m - 1) * 2 + 1);
+        h2 += (T)inject_at(d, mons, 5, i, j, kg, (long long)(m - 1) * 2 + 1);
     }
     B0[ij] = h0;
     B1[ij] = h1;
     B2[ij] = h2;
+}
+
+// Completes a pending transposed step cell by cell (the algebra of e_deferred): for every E
+// component not held by a PEC plane, Ebar = F / (S eps^-1) (or the pole form in dispersive cells,
+// which also advances the pole cotangents) and the own psibar_E of its two derivatives.
+template <typename T, bool kPoles>
+__global__ void __launch_bounds__(kTileX* kTileY) k_adj_flush_cell(const AdjCellArgs<T> c,
+                                                                   const Dom<T>* __restrict__ doms, T S) {
+    const int nx = c.n[0], ny = c.n[1];
+    const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const int kg = k + c.kz0;
+    const long long id = ((long long)k * ny + j) * nx + i;
+    const int sl[3] = {slab_or_none(i, c.dlo[0], c.dhi[0], nx, c.ns[0]), slab_or_none(j, c.dlo[1], c.dhi[1], ny, c.ns[1]),
+                       slab_or_none(kg, c.dlo[2], c.dhi[2], c.nzg, c.ns[2])};
+    const int x[3] = {i, j, kg};
+    bool disp = false;
+    long long bo = 0;
+    if (kPoles) {
+        const Dom<T>& d = doms[c.dom];
+        disp = d.npole > 0 && in_ade_box(d, i, j, k) && d.mask[id];
+        if (disp) bo = ade_off(d, i, j, k);
+    }
+    const bool pi = i == 0 && !c.per[0], pj = j == 0 && !c.per[1], pk = k == 0;
+    const bool pec[3] = {pj || pk, pi || pk, pi || pj};
+    for (int a = 0; a < 3; ++a) {
+        if (pec[a]) continue;
+        const T ie = c.ie[a][id];
+        const T F = c.A[a][id];
+        T eb;
+        if (kPoles && disp) {
+            const Dom<T>& d = doms[c.dom];
+            eb = (T(1) / ie - d.G) / S * F;
+            for (int p = 0; p < d.npole; ++p) {
+                T* pp = d.aade + ((long long)(a * d.npole + p) * 2 + 0) * d.bcell + bo;
+                T* pq = pp + d.bcell;
+                const T xp = *pp, xq = *pq;
+                eb += d.g0[p] * xp + d.g1[p] * xq;
+                *pp = d.M00[p] * xp + d.M10[p] * xq + (T(1) - d.M00[p]) / S * F;
+                *pq = d.M01[p] * xp + d.M11[p] * xq - d.M01[p] / S * F;
+            }
+        } else {
+            eb = F * recip_t(S * ie);
+        }
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int ax = (a + 1 + s2) % 3;
+            if (sl[ax] < 0) continue;
+            T* p = c.apsiE[a][s2] + slab_off_c(c.n, c.ns, ax, i, j, k, sl[ax]);
+            *p = c.cE[ax][x[ax]] * (*p + (s2 == 0 ? F : -F));
+        }
+        c.A[a][id] = eb;
+    }
+}
+
+template <typename T>
+void launch_adj_flush_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, T S, int poles) {
+    const dim3 g((unsigned)((c.n[0] + kTileX - 1) / kTileX), (unsigned)((c.n[1] + kTileY - 1) / kTileY),
+                 (unsigned)c.n[2]);
+    if (poles)
+        k_adj_flush_cell<T, true><<<g, dim3(kTileX, kTileY), 0, L.stream>>>(c, doms, S);
+    else
+        k_adj_flush_cell<T, false><<<g, dim3(kTileX, kTileY), 0, L.stream>>>(c, doms, S);
+    ++*L.counter;
 }
 
 inline dim3 adj_cell_grid(const int* n) {
@@ -1155,7 +1220,8 @@ void launch_inject(const Launch& L, const Dom<T>* doms, const Mon* mons, const i
     template void launch_adj_e_cell<T>(const Launch&, const AdjCellArgs<T>&, const Dom<T>*, const Mon*, T, int,  \
                                        int, int, int, int);                                                     \
     template void launch_adj_h_cell<T>(const Launch&, const AdjCellArgs<T>&, const Dom<T>*, const Mon*, T, int,  \
-                                       int);
+                                       int);                                                                    \
+    template void launch_adj_flush_cell<T>(const Launch&, const AdjCellArgs<T>&, const Dom<T>*, T, int);
 GBFDTD_INST(float)
 GBFDTD_INST(double)
 #undef GBFDTD_INST

@@ -83,6 +83,7 @@ _SIGS = {
     "fdtd_dft_flux": [_ctx, C.c_int32, C.POINTER(C.c_double), C.c_int32],
     "fdtd_step_backward": [_ctx, C.c_int32],
     "fdtd_record_interface": [_ctx, C.c_int32],
+    "fdtd_stream_checkpoints": [_ctx, C.c_int32],
     "fdtd_add_source": [_ctx, C.c_int32, C.c_int32, _i32p, _i32p, C.POINTER(C.c_double), C.c_int32, _i32p],
     "fdtd_add_dft_monitor": [_ctx, C.c_int32, _i32p, _i32p, C.c_uint32, C.c_int32, C.POINTER(C.c_double),
                              _i32p],
@@ -350,6 +351,7 @@ def fdtd_dft_flux(ctx, monitor, n_freq):
 
 fdtd_step_backward = _wrap_simple("fdtd_step_backward")
 fdtd_record_interface = _wrap_simple("fdtd_record_interface")
+fdtd_stream_checkpoints = _wrap_simple("fdtd_stream_checkpoints")
 
 
 def fdtd_set_periodic(ctx, domain, periodic):

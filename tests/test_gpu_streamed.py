@@ -110,15 +110,23 @@ def test_streamed_reset_and_dft_reset_repeat_the_run():
 def test_streamed_context_rejects_what_it_does_not_hold():
     sc = _rich_scene(steps=8)
     ctx = fdtd.Context([sc], dtype="f32", streamed=(8, 4))
-    for call in (lambda: fdtd.fdtd_adjoint_begin(ctx.ctx),
-                 lambda: fdtd.fdtd_step_adjoint(ctx.ctx, 1),
-                 lambda: fdtd.fdtd_state_save(ctx.ctx, 0, 0),
+    for call in (lambda: fdtd.fdtd_state_save(ctx.ctx, 0, 0),
                  lambda: fdtd.fdtd_set_launch_mode(ctx.ctx, 0),
-                 lambda: fdtd.fdtd_step_backward(ctx.ctx, 1),
-                 lambda: ctx.part(0, 0, which=1)):
+                 lambda: fdtd.fdtd_step_backward(ctx.ctx, 1)):
         with pytest.raises(fdtd.FdtdError) as e:
             call()
         assert e.value.status == fdtd.FDTD_EINVAL
+    # the adjoint state exists after fdtd_adjoint_begin, and a transposed sweep needs the forward
+    # checkpoints of its batches
+    for call in (lambda: ctx.part(0, 0, which=1), lambda: fdtd.fdtd_step_adjoint(ctx.ctx, 0)):
+        with pytest.raises(fdtd.FdtdError) as e:
+            call()
+        assert e.value.status == fdtd.FDTD_ESTATE
+    ctx.step(4)
+    fdtd.fdtd_adjoint_begin(ctx.ctx)
+    with pytest.raises(fdtd.FdtdError) as e:
+        fdtd.fdtd_step_adjoint(ctx.ctx, 2)
+    assert e.value.status == fdtd.FDTD_ESTATE
     fdtd.fdtd_set_launch_mode(ctx.ctx, 4)
     # materials on the device, a halo wider than the slab, no halo
     with pytest.raises(fdtd.FdtdError):
@@ -153,3 +161,61 @@ def test_streamed_device_footprint_is_the_windows():
     used_res = f1 - torch.cuda.mem_get_info()[0]
     res.close()
     assert used_st < 0.3 * used_res, (used_st, used_res)
+
+
+# ---- the streamed transposed sweep (Sec. 4.2: it runs the slab tiling in reverse) ----------------
+def _adjoint_scene(steps):
+    sc = _rich_scene(steps=steps)
+    sc.design = ((6, 5, 8), (15, 12, 30))   # outside the CPML slabs, across several slab edges
+    return sc
+
+
+def _loss(specs):
+    F = specs[0]
+    return float((F.abs() ** 2).sum()), [torch.view_as_real(2.0 * F).contiguous()] + [None] * (len(specs) - 1)
+
+
+@pytest.mark.parametrize("slab,halo,steps,dtype", [
+    (8, 3, 37, "f32"),    # five slabs, batches of 3 with a ragged last batch
+    (9, 6, 20, "f64"),
+    (64, 16, 25, "f32"),  # one slab holds the domain
+])
+def test_streamed_transposed_sweep_equals_the_resident_one(slab, halo, steps, dtype):
+    from paper_2609_30039_gb300 import adjoint as ADJ
+    sc = _adjoint_scene(steps)
+    res = fdtd.Context([sc], dtype=dtype)
+    (J_r, _), g_r, _ = ADJ.DesignAdjoint(res, slots=6).run(sc.n_steps, _loss)
+    adj_r = [res.part(0, p, which=1).clone() for p in range(res.part_count(0))]
+    st = fdtd.Context([sc], dtype=dtype, streamed=(slab, halo))
+    (J_s, _), g_s, _ = ADJ.StreamedAdjoint(st).run(sc.n_steps, _loss)
+    adj_s = [st.part(0, p, which=1).clone() for p in range(st.part_count(0))]
+    assert J_s == J_r
+    assert float(g_r[0].abs().max()) > 0.0
+    # the owned planes of every window hold what the resident sweep computes, bit for bit: the
+    # adjoint state at step 0 and the material cotangent (each cell sums its steps in the same order)
+    for p, (x, y) in enumerate(zip(adj_s, adj_r)):
+        assert torch.equal(x.cpu(), y.cpu()), f"adjoint part {p} differs: {float((x.cpu() - y.cpu()).abs().max())}"
+    assert torch.equal(g_s[0], g_r[0]), float((g_s[0] - g_r[0]).abs().max())
+    res.close()
+    st.close()
+
+
+def test_streamed_gradient_matches_the_oracle_fp64():
+    from oracle.oracle import gradient_replay
+    from paper_2609_30039_gb300 import adjoint as ADJ
+    sc = _adjoint_scene(24)
+    o = oracle_from_scene(sc)
+
+    def obj(orc):
+        F = orc.dft(0)
+        return float((np.abs(F) ** 2).sum()), {0: 2.0 * F}
+
+    J_ref = gradient_replay(o, sc.n_steps, obj)
+    g_ref = np.stack([o.grad(a) for a in range(3)])
+    st = fdtd.Context([sc], dtype="f64", streamed=(8, 3))
+    (J, _), g, _ = ADJ.StreamedAdjoint(st).run(sc.n_steps, _loss)
+    assert abs(J - J_ref) <= 1e-12 * abs(J_ref)
+    err = rel(g[0].cpu().numpy().reshape(g_ref.shape), g_ref)
+    print(f"\nstreamed FP64 gradient vs oracle: {err:.3e}")
+    assert err < 1e-10, err
+    st.close()
