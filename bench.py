@@ -598,7 +598,8 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0,
                     help="n: run only a short n^3 FP32 forward (ncu captures on a case larger than L2)")
     ap.add_argument("--workload", default="cpml128",
-                    choices=["cpml128", "pec32", "batched", "adjoint256", "large640", "reversible256", "streamed", "poles"],
+                    choices=["cpml128", "pec32", "batched", "adjoint256", "large640", "reversible256", "streamed", "poles",
+                             "streamed_grad"],
                     help="cpml128 is the benchmark line; the others measure the remaining workloads")
     ap.add_argument("--fd-cells", type=int, default=20)
     ap.add_argument("--fp64-ref", action="store_true",
@@ -632,7 +633,7 @@ def main():
     elif args.workload != "cpml128" and args.impl == "ours":
         {"pec32": measure_pec32, "batched": measure_batched, "adjoint256": measure_adjoint256,
          "large640": measure_large640, "reversible256": measure_reversible256,
-         "streamed": measure_streamed, "poles": measure_poles}[args.workload](args)
+         "streamed": measure_streamed, "poles": measure_poles, "streamed_grad": measure_streamed_grad}[args.workload](args)
     elif args.impl == "reference":
         run_reference(args)
     else:
@@ -1034,6 +1035,79 @@ def measure_streamed(args):
         ctx.close()
     res["streamed_over_resident_time"] = round(res["resident_gcell_steps_s"] / res["streamed_gcell_steps_s"], 3)
     res["bitwise_equal_fields_and_spectra"] = all(torch.equal(a, b) for a, b in zip(out["streamed"], out["resident"]))
+    print(json.dumps(res))
+
+
+def measure_streamed_grad(args):
+    """Host-streamed gradient (Sec. 4.2, the transposed sweep in reverse) against the resident
+    checkpointed one on an n^3 FP32 domain (10-cell CPML, blocky eps in a central design box, an Ez
+    sheet, a plane monitor): time, device bytes held, host checkpoint bytes, and bitwise agreement of
+    the two gradients."""
+    import numpy as np
+    import torch
+    from paper_2609_30039_gb300 import adjoint as ADJ
+    from paper_2609_30039_gb300 import build as B
+    from paper_2609_30039_gb300 import fdtd
+    from paper_2609_30039_gb300 import workloads as W
+    B.build()
+    n = args.stream_n if args.stream_n != 768 else 512
+    steps = args.steps * 8 if args.steps != 10 else 64
+    sc = W.cpml_blocks(n=n, d=CPML, n_steps=steps)
+    q = n // 4
+    sc.design = ((q, q, (7 * n) // 16), (n - q, n - q, (9 * n) // 16))
+
+    def loss(specs):
+        F = specs[0]
+        return float((F.abs() ** 2).sum()), [torch.view_as_real(2.0 * F).contiguous()]
+
+    _warm_loss(loss, torch.device("cuda"))
+    res = {"workload": f"cpml_blocks_{n}^3 FP32 with a {n // 2}x{n // 2}x{n // 8} design box, {steps} steps",
+           "slab": args.slab, "halo": args.halo, "cells": sc.cells}
+    grads = {}
+    for kind in ("resident", "streamed"):
+        torch.cuda.synchronize()
+        f0 = torch.cuda.mem_get_info()[0]
+        ctx = fdtd.Context([sc], dtype="f32", streamed=(args.slab, args.halo) if kind == "streamed" else None)
+        runner = ADJ.StreamedAdjoint(ctx) if kind == "streamed" else ADJ.DesignAdjoint(ctx, slots=8)
+        # the first run allocates (device slots, pinned host checkpoints); the second is timed
+        for rep in ("first", "second"):
+            fdtd.fdtd_reset(ctx.ctx)
+            fdtd.fdtd_dft_reset(ctx.ctx)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            (J, _), g, _ = runner.run(steps, loss)
+            torch.cuda.synchronize()
+            res[f"{kind}_seconds" + ("_first_run" if rep == "first" else "")] = round(time.perf_counter() - t0, 3)
+        res[f"{kind}_device_bytes"] = int(f0 - torch.cuda.mem_get_info()[0])
+        grads[kind] = g[0].clone()
+        if kind == "streamed":
+            state = sum(fdtd.fdtd_part_size(ctx.ctx, 0, p) for p in range(ctx.part_count(0))) * 4
+            res["host_checkpoint_bytes"] = int(state * (-(-steps // args.halo)))
+            # the two halves of a run: forward with checkpoints, then the transposed sweep
+            fdtd.fdtd_reset(ctx.ctx)
+            fdtd.fdtd_dft_reset(ctx.ctx)
+            fdtd.fdtd_stream_checkpoints(ctx.ctx, 1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fdtd.fdtd_step_forward(ctx.ctx, steps)
+            ctx.synchronize()
+            t1 = time.perf_counter()
+            fdtd.fdtd_adjoint_begin(ctx.ctx)
+            fdtd.fdtd_step_adjoint(ctx.ctx, steps)
+            ctx.synchronize()
+            t2 = time.perf_counter()
+            fdtd.fdtd_reset(ctx.ctx)
+            fdtd.fdtd_stream_checkpoints(ctx.ctx, 0)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            fdtd.fdtd_step_forward(ctx.ctx, steps)
+            ctx.synchronize()
+            res["streamed_forward_seconds"] = round(t1 - t0, 3)
+            res["streamed_transposed_seconds"] = round(t2 - t1, 3)
+            res["streamed_forward_without_checkpoints_seconds"] = round(time.perf_counter() - t3, 3)
+        ctx.close()
+    res["streamed_over_resident_time"] = round(res["streamed_seconds"] / res["resident_seconds"], 3)
+    res["gradients_bitwise_equal"] = bool(torch.equal(grads["resident"], grads["streamed"]))
     print(json.dumps(res))
 
 

@@ -139,7 +139,11 @@ fdtd_status fdtd_create_streamed(const fdtd_grid* grid, const fdtd_cpml* cpml, c
 /* Forward checkpoints of a host-streamed context (Sec. 4.2; the transposed sweep runs the slab
  * tiling in reverse).  enabled = 1: from the held step t0 on, fdtd_step_forward runs its batches
  * aligned to t0 + j * halo and keeps the whole forward state at every such batch start in pinned
- * host memory owned by the context (existing checkpoints are dropped); 0 frees them.  The
+ * host memory owned by the context (existing checkpoints are dropped, their buffers reused); each
+ * batch writes the next checkpoint with the copies of its owned planes.  enabled = 0 stops taking
+ * checkpoints and frees every checkpoint buffer; enabled = 2 stops taking them but keeps the
+ * buffers for the next enabled = 1 (a gradient loop then pins its host memory once); other values:
+ * FDTD_EINVAL.  fdtd_destroy frees them in any case.  The
  * transposed sweep of a streamed context -- fdtd_adjoint_begin, then fdtd_step_adjoint -- then runs
  * the batches last to first: per slab its window replays the batch from the checkpoint on the device
  * (keeping each replayed window state, kb <= halo of them), takes the transposed steps from the

@@ -245,7 +245,8 @@ class StreamedAdjoint(DesignAdjoint):
     memory, then the transposed sweep batch by batch, last to first, each slab window replaying its
     batch on the device from the checkpoint.  Device memory: the stepping workspaces, the adjoint
     window and the replayed windows of one batch; host memory: the state, two adjoint state sets and
-    one checkpoint per batch."""
+    one checkpoint per batch, whose pinned buffers are kept for the next run until release() or the
+    context's close."""
 
     def __init__(self, ctx: "F.Context"):
         super().__init__(ctx, slots=1)
@@ -266,8 +267,13 @@ class StreamedAdjoint(DesignAdjoint):
         F.fdtd_adjoint_begin(c)
         F.fdtd_step_adjoint(c, n_steps)
         ctx.synchronize()
-        F.fdtd_stream_checkpoints(c, 0)
+        # checkpoints off; their pinned buffers stay for the next run (freed with the context)
+        F.fdtd_stream_checkpoints(c, 2)
         return (J, specs), self.grads, {"forward_steps": n_steps, "adjoint_steps": n_steps}
+
+    def release(self):
+        """Frees the pinned host checkpoint buffers kept between runs."""
+        F.fdtd_stream_checkpoints(self.ctx.ctx, 0)
 
 
 def _make_function():

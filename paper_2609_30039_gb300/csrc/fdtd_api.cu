@@ -172,6 +172,7 @@ struct fdtd_ctx {
     int ck_on = 0;
     long long ck_t0 = 0;
     std::map<long long, void*> ck;
+    std::vector<void*> ck_pool;               // pinned checkpoint buffers kept for the next run
     Workspace hadj[2];
     int hadj_cur = 0;
     int hadj_ready = 0;
@@ -1375,20 +1376,33 @@ size_t state_bytes(const fdtd_ctx* c) {
     return b;
 }
 
+// The pinned host buffer of the checkpoint of step `now` (taken from the kept buffers, else
+// allocated).
+fdtd_status ck_alloc(fdtd_ctx* c, long long now) {
+    void*& buf = c->ck[now];
+    if (buf) return FDTD_OK;
+    if (!c->ck_pool.empty()) {
+        buf = c->ck_pool.back();
+        c->ck_pool.pop_back();
+        return FDTD_OK;
+    }
+    cudaError_t e = cudaHostAlloc(&buf, state_bytes(c), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->ck.erase(now);
+        return fail(c, FDTD_ENOMEM, "pinned host checkpoint allocation failed");
+    }
+    return FDTD_OK;
+}
+
 // Keeps the host forward state (held at step `now`) as the checkpoint of that step, in pinned host
 // memory, once every copy of the previous batch has landed.
 fdtd_status ck_save(fdtd_ctx* c, long long now) {
     CK(c, cudaStreamSynchronize(c->stream));
     CK(c, cudaStreamSynchronize(c->d2h_stream));
-    void*& buf = c->ck[now];
-    if (!buf) {
-        cudaError_t e = cudaHostAlloc(&buf, state_bytes(c), cudaHostAllocDefault);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            c->ck.erase(now);
-            return fail(c, FDTD_ENOMEM, "pinned host checkpoint allocation failed");
-        }
-    }
+    fdtd_status st = ck_alloc(c, now);
+    if (st != FDTD_OK) return st;
+    void* buf = c->ck[now];
     const DomainHost& h = c->doms[0];
     size_t off = 0;
     for (int p = 0; p < part_count(h); ++p) {
@@ -1452,16 +1466,25 @@ fdtd_status stream_forward(fdtd_ctx* c, int n_steps) {
         return FDTD_OK;
     };
     int left = n_steps;
+    long long ck_next = -1;   // the checkpoint this batch's copy-outs also write (its end step), or -1
     while (left > 0) {
         int kb = std::min(left, c->sk);
+        const long long ck_written = ck_next;
+        ck_next = -1;
         if (c->ck_on) {
-            // batches aligned to the checkpoint grid; a batch start on it keeps the whole state
+            // batches aligned to the checkpoint grid; the state at every batch start on it is kept:
+            // the first one copied from the host state, later ones written by the previous batch
             const long long now = c->step + (n_steps - left), rel = now - c->ck_t0;
             if (rel >= 0) {
                 kb = (int)std::min<long long>(left, c->sk - rel % c->sk);
-                if (rel % c->sk == 0) {
+                if (rel % c->sk == 0 && now != ck_written) {
                     st = ck_save(c, now);
                     if (st != FDTD_OK) return st;
+                }
+                if (left > kb) {
+                    st = ck_alloc(c, now + kb);
+                    if (st != FDTD_OK) return st;
+                    ck_next = now + kb;
                 }
             }
         }
@@ -1494,6 +1517,11 @@ fdtd_status stream_forward(fdtd_ctx* c, int n_steps) {
             if (s + 1 < nsl) CK(c, cudaStreamWaitEvent(c->d2h_stream, c->ev_in[s + 1], 0));
             st = stream_copy(c, w, r, false, c->d2h_stream);
             if (st != FDTD_OK) return st;
+            if (ck_next >= 0) {
+                // the owned planes at the batch end are also the next checkpoint's
+                st = window_copy(c, w, ck_view(c, c->ck[ck_next]), c->ws[r], w.zs, w.ze, false, false, c->d2h_stream);
+                if (st != FDTD_OK) return st;
+            }
             CK(c, cudaEventRecord(c->ev_out[s], c->d2h_stream));
             CK(c, cudaEventRecord(c->ws_free[r], c->d2h_stream));
         }
@@ -1821,9 +1849,7 @@ fdtd_status stream_adjoint(fdtd_ctx* c, int n_steps) {
             // the global one: the batch base tb plus the position in the batch)
             st = window_copy(c, w, ckv, c->ws[r], w.wlo, w.whi, true, true, c->stream);
             if (st != FDTD_OK) return st;
-            c->h_step_tmp = (int)tb;
-            CK(c, cudaMemcpyAsync(c->d_base, &c->h_step_tmp, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-            CK(c, cudaStreamSynchronize(c->stream));
+            launch_set_int(l, c->d_base, (int)tb);
             const CellArgs<T> ce = stream_cell_args<T>(c, s2, true), ch = stream_cell_args<T>(c, s2, false);
             for (int j = 0; j < kb; ++j) {
                 for (int f = 0; f < 6; ++f)
@@ -2348,6 +2374,7 @@ fdtd_status fdtd_destroy(fdtd_ctx* ctx) {
     for (void* p : ctx->owned) cudaFree(p);
     for (void* p : ctx->host_owned) cudaFreeHost(p);
     for (auto& kv : ctx->ck) cudaFreeHost(kv.second);
+    for (void* p : ctx->ck_pool) cudaFreeHost(p);
     for (auto& s : ctx->slots) cudaFree(s.second.buf);
     delete ctx;
     return FDTD_OK;
@@ -2695,11 +2722,16 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
 fdtd_status fdtd_stream_checkpoints(fdtd_ctx* ctx, int32_t enabled) {
     GUARD(ctx);
     if (!ctx->streamed) return fail(ctx, FDTD_EINVAL, "forward checkpoints in host memory belong to a streamed context");
-    if (enabled != 0 && enabled != 1) return fail(ctx, FDTD_EINVAL, "enabled must be 0 or 1");
+    if (enabled < 0 || enabled > 2) return fail(ctx, FDTD_EINVAL, "enabled must be 0, 1 or 2");
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    for (auto& kv : ctx->ck) cudaFreeHost(kv.second);
+    CK(ctx, cudaStreamSynchronize(ctx->d2h_stream));
+    for (auto& kv : ctx->ck) ctx->ck_pool.push_back(kv.second);
     ctx->ck.clear();
-    ctx->ck_on = enabled;
+    if (enabled == 0) {
+        for (void* p : ctx->ck_pool) cudaFreeHost(p);
+        ctx->ck_pool.clear();
+    }
+    ctx->ck_on = enabled == 1;
     ctx->ck_t0 = ctx->step;
     return FDTD_OK;
 }

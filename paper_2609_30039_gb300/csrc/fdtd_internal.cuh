@@ -262,6 +262,7 @@ template <typename T>
 void launch_dft(const Launch& L, const Dom<T>* doms, const Mon* mons, const DftItem* items, int nitems, int kind,
                 const int* d_base, int offset);
 void launch_copy_int(const Launch& L, const int* src, int* dst);
+void launch_set_int(const Launch& L, int* dst, int v);
 // One domain's operands for the per-cell kernels, passed by value (kernel parameter space) so
 // the first field loads need no descriptor load before them.  psi / coef: the CPML memories and
 // coefficient rows of the half-step (E or H).

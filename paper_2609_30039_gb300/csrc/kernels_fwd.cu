@@ -144,6 +144,8 @@ __global__ void __launch_bounds__(kTileX* kTileY)
 
 __global__ void k_copy_int(const int* __restrict__ src, int* __restrict__ dst) { *dst = *src; }
 
+__global__ void k_set_int(int* __restrict__ dst, int v) { *dst = v; }
+
 // Blocks per SM the per-launch kernels are compiled for.  Interior tiles run the plain register
 // path at full occupancy (8 blocks of 256 threads in FP32, at most 32 registers): the warps in
 // flight are what keeps enough loads outstanding to approach the DRAM bandwidth.
@@ -1273,6 +1275,11 @@ void launch_dft(const Launch& L, const Dom<T>* doms, const Mon* mons, const DftI
 
 void launch_copy_int(const Launch& L, const int* src, int* dst) {
     k_copy_int<<<1, 1, 0, L.stream>>>(src, dst);
+    ++*L.counter;
+}
+
+void launch_set_int(const Launch& L, int* dst, int v) {
+    k_set_int<<<1, 1, 0, L.stream>>>(dst, v);
     ++*L.counter;
 }
 

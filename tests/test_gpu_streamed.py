@@ -219,3 +219,23 @@ def test_streamed_gradient_matches_the_oracle_fp64():
     print(f"\nstreamed FP64 gradient vs oracle: {err:.3e}")
     assert err < 1e-10, err
     st.close()
+
+
+def test_streamed_gradient_repeats_with_the_kept_checkpoint_buffers():
+    from paper_2609_30039_gb300 import adjoint as ADJ
+    sc = _adjoint_scene(20)
+    st = fdtd.Context([sc], dtype="f32", streamed=(8, 3))
+    runner = ADJ.StreamedAdjoint(st)
+    (J1, _), g, _ = runner.run(sc.n_steps, _loss)
+    g1 = g[0].clone()
+    # a second run from step 0 reuses the pinned buffers of the first and gives the same result
+    fdtd.fdtd_reset(st.ctx)
+    fdtd.fdtd_dft_reset(st.ctx)
+    (J2, _), g, _ = runner.run(sc.n_steps, _loss)
+    assert J2 == J1
+    assert torch.equal(g[0], g1)
+    with pytest.raises(fdtd.FdtdError) as e:
+        fdtd.fdtd_stream_checkpoints(st.ctx, 3)
+    assert e.value.status == fdtd.FDTD_EINVAL
+    runner.release()
+    st.close()
