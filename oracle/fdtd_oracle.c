@@ -22,7 +22,9 @@
  *                 profiles; PEC holds tangential E at zero on the boundary node;
  *                 periodic pairs wrap the difference operators (oracle-only).
  *   - Sec. 2.3    real permittivity per Yee E position (diagonal), Drude/Lorentz
- *                 poles integrated with the trapezoidal ADE.
+ *                 poles integrated with the trapezoidal ADE; or (tensor mode, no
+ *                 poles) a symmetric eps^{-1} tensor per grid node applied to the
+ *                 curl through the node assembly S = D^{-1/2} (1/8 sum R^T eps^-1 R) D^{-1/2}.
  *   - Sec. 2.4    DFT monitors over a box of cells (plane, patch or point) with the
  *                 half-step magnetic phase.
  *   - Sec. 3.1, Eq. (adjoint): reverse recursion, transposed curls, the CPML
@@ -107,7 +109,9 @@ typedef struct oracle {
     double *A[6];
     double *apsiE[3][2], *apsiH[3][2];
     double *aP[3][MAXP], *aQ[3][MAXP];
-    int design_on; int dlo[3], dhi[3]; long dcell; double *grad[3];
+    int design_on; int dlo[3], dhi[3]; long dcell; double *grad[6];
+    /* tensor mode (Sec. 2.3): eps^-1 per node, components xx yy zz xy xz yz; D per E edge */
+    int tensor_on; double *tinv[6]; double *tD[3]; double *tscr[3], *tacc[3];
     /* scratch */
     double *tmpE[3], *curl[3], *tmpH[3];
     int threads;                  /* OpenMP team size of the cell loops (1: serial) */
@@ -199,6 +203,7 @@ void oracle_destroy(oracle_t *o) {
     for (int q = 0; q < 3; ++q) {
         free(o->eb[q]); free(o->ec[q]); free(o->ek[q]); free(o->hb[q]); free(o->hc[q]); free(o->hk[q]);
         free(o->inv_eps[q]); free(o->tmpE[q]); free(o->curl[q]); free(o->tmpH[q]); free(o->grad[q]);
+        free(o->grad[3 + q]); free(o->tinv[q]); free(o->tinv[3 + q]); free(o->tD[q]); free(o->tscr[q]); free(o->tacc[q]);
         for (int s = 0; s < 2; ++s) { free(o->psiE[q][s]); free(o->psiH[q][s]); free(o->apsiE[q][s]); free(o->apsiH[q][s]); }
         for (int p = 0; p < o->npole; ++p) { free(o->P[q][p]); free(o->Q[q][p]); free(o->aP[q][p]); free(o->aQ[q][p]); }
     }
@@ -284,6 +289,7 @@ int oracle_add_dft_box(oracle_t *o, const int *lo, const int *hi, unsigned mask,
 }
 
 void oracle_enable_energy(oracle_t *o, long cap) {
+    if (o->tensor_on) return;   /* the energy below is the diagonal one */
     free(o->energy);
     o->energy = zalloc(cap); o->energy_cap = cap; o->energy_on = 1;
 }
@@ -324,6 +330,107 @@ static int is_pec_E(const oracle_t *o, int a, const int c[3]) {
     return 0;
 }
 
+/* ---------------- symmetric tensors at the nodes, Sec. 2.3 ----------------
+ * Grid node n = (i, j, k) carries eps^-1_n (symmetric, 3 x 3).  For a choice c in {0,1}^3,
+ * R_{n,c} picks one E edge per axis next to the node: along axis q the edge whose coordinate is
+ * n_q - 1 + c_q (the E_q array index; it wraps on a periodic axis and is absent below 0 on a
+ * non-periodic one), the other two coordinates those of the node.  The assembly is
+ *   A = 1/8 sum_n sum_c R_{n,c}^T eps^-1_n R_{n,c},   D = 1/8 sum_n sum_c R_{n,c}^T R_{n,c},
+ * D diagonal (the same sum with the identity tensor), and the E update applies
+ *   S_t = D^{-1/2} A D^{-1/2}
+ * to the curl: E^{n+1} = E^n + S S_t C.  PEC-held edges are not unknowns: the operator reads them
+ * as zero and leaves them alone.  With eps^-1 <= I at every node, A <= D, so ||S_t|| <= 1 and the
+ * vacuum time step stays admissible. */
+static int tcomp(int u, int v) {
+    if (u == v) return u;
+    if (u + v == 1) return 3;   /* xy */
+    if (u + v == 2) return 4;   /* xz */
+    return 5;                   /* yz */
+}
+
+/* Coordinate along axis q of the edge that choice bit cq picks at node coordinate x, or -1. */
+static int edge_coord(const oracle_t *o, int q, int x, int cq) {
+    int e = x - 1 + cq;
+    if (e < 0) { if (!o->periodic[q]) return -1; e += o->N[q]; }
+    return e;
+}
+
+/* Edge ids (or -1) of choice c at node (i, j, k), per axis. */
+static void node_edges(const oracle_t *o, int i, int j, int k, int c, long id[3]) {
+    const int n[3] = {i, j, k};
+    for (int a = 0; a < 3; ++a) {
+        int e[3] = {i, j, k};
+        e[a] = edge_coord(o, a, n[a], (c >> a) & 1);
+        id[a] = -1;
+        if (e[a] < 0 || is_pec_E(o, a, e)) continue;
+        id[a] = IDX(o, e[0], e[1], e[2]);
+    }
+}
+
+/* out = S_t in (full arrays of the three E components). */
+static void tensor_apply(oracle_t *o, double *const in[3], double *const out[3]) {
+    const int nx = o->N[0], ny = o->N[1], nz = o->N[2];
+    for (int a = 0; a < 3; ++a) memset(o->tacc[a], 0, sizeof(double) * (size_t)o->ncell);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                long n = IDX(o, i, j, k);
+                for (int c = 0; c < 8; ++c) {
+                    long id[3];
+                    node_edges(o, i, j, k, c, id);
+                    double v[3], u[3];
+                    for (int a = 0; a < 3; ++a) v[a] = id[a] >= 0 ? in[a][id[a]] / sqrt(o->tD[a][id[a]]) : 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        u[a] = 0.0;
+                        for (int b = 0; b < 3; ++b) u[a] += o->tinv[tcomp(a, b)][n] * v[b];
+                    }
+                    for (int a = 0; a < 3; ++a)
+                        if (id[a] >= 0) o->tacc[a][id[a]] += u[a] / 8.0;
+                }
+            }
+    for (int a = 0; a < 3; ++a)
+        for (long e = 0; e < o->ncell; ++e) out[a][e] = o->tD[a][e] > 0.0 ? o->tacc[a][e] / sqrt(o->tD[a][e]) : 0.0;
+}
+
+/* Tensor mode on (t6 = six full node arrays xx yy zz xy xz yz) or off (t6 = NULL).
+ * -1 with poles or an energy record (neither is defined here for tensors). */
+int oracle_set_tensor(oracle_t *o, const double *t6) {
+    if (!t6) { o->tensor_on = 0; return 0; }
+    if (o->npole > 0 || o->energy_on) return -1;
+    const int nx = o->N[0], ny = o->N[1], nz = o->N[2];
+    for (int q = 0; q < 6; ++q) {
+        if (!o->tinv[q]) o->tinv[q] = zalloc(o->ncell);
+        memcpy(o->tinv[q], t6 + (long)q * o->ncell, sizeof(double) * (size_t)o->ncell);
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (!o->tD[a]) { o->tD[a] = zalloc(o->ncell); o->tscr[a] = zalloc(o->ncell); o->tacc[a] = zalloc(o->ncell); }
+        memset(o->tD[a], 0, sizeof(double) * (size_t)o->ncell);
+    }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                for (int c = 0; c < 8; ++c) {
+                    long id[3];
+                    node_edges(o, i, j, k, c, id);
+                    for (int a = 0; a < 3; ++a)
+                        if (id[a] >= 0) o->tD[a][id[a]] += 1.0 / 8.0;
+                }
+    o->tensor_on = 1;
+    return 0;
+}
+
+/* The assembled operator on three arrays (in tensor mode; -1 otherwise). */
+int oracle_tensor_apply(oracle_t *o, const double *inx, const double *iny, const double *inz, double *outx,
+                        double *outy, double *outz) {
+    if (!o->tensor_on) return -1;
+    double *in[3] = {(double *)inx, (double *)iny, (double *)inz}, *out[3] = {outx, outy, outz};
+    tensor_apply(o, in, out);
+    return 0;
+}
+
+/* The diagonal D of the assembly for E component a (tensor mode; NULL otherwise). */
+double *oracle_tensor_D(oracle_t *o, int a) { return o->tensor_on ? o->tD[a] : NULL; }
+
 /* E-phase of Eq. (yee): reads E, H, psiE, P, Q; writes Enew (pre-source), psiE_out,
  * P/Q outputs and the CPML-corrected curl.  Output arrays may alias inputs
  * because every cell reads only its own E/psi/P/Q and the (unchanged) H. */
@@ -358,7 +465,9 @@ static void e_phase(oracle_t *o, double *const Eout[3], double *const psiout[3][
                     psiout[a][1][id] = ps2;
                     o->curl[a][id] = cu;
                     double E = o->F[a][id];
-                    if (o->npole > 0 && o->mask[id]) {
+                    if (o->tensor_on) {
+                        Eout[a][id] = E;   /* updated below, once every curl is known */
+                    } else if (o->npole > 0 && o->mask[id]) {
                         double eps = 1.0 / o->inv_eps[a][id];
                         double G = 0.0, num = eps * E + o->S * cu;
                         for (int p = 0; p < o->npole; ++p) {
@@ -382,6 +491,19 @@ static void e_phase(oracle_t *o, double *const Eout[3], double *const psiout[3][
                         }
                     }
                 }
+    }
+    if (o->tensor_on) {
+        /* E^{n+1} = E^n + S S_t C over the whole curl field */
+        tensor_apply(o, o->curl, o->tscr);
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < nz; ++k)
+                for (int j = 0; j < ny; ++j)
+                    for (int i = 0; i < nx; ++i) {
+                        int c[3] = {i, j, k};
+                        if (is_pec_E(o, a, c)) continue;
+                        long id = IDX(o, i, j, k);
+                        Eout[a][id] = o->F[a][id] + o->S * o->tscr[a][id];
+                    }
     }
 }
 
@@ -480,7 +602,7 @@ static void sub_sources(oracle_t *o, int magnetic, long n) {
 int oracle_step_backward(oracle_t *o, int n) {
     for (int q = 0; q < 3; ++q)
         if (o->cpml[2 * q] || o->cpml[2 * q + 1]) return -1;
-    if (o->npole > 0) return -1;
+    if (o->npole > 0 || o->tensor_on) return -1;
     const int nx = o->N[0], ny = o->N[1], nz = o->N[2];
     for (int s = 0; s < n && o->step > 0; ++s) {
         const long m = o->step - 1;
@@ -547,7 +669,7 @@ static int in_interior(const oracle_t *o, int i, int j, int k) {
 
 int oracle_step_backward_interior(oracle_t *o, const double *rex, const double *rey, const double *rez,
                                   const double *rhx, const double *rhy, const double *rhz) {
-    if (o->npole > 0 || o->step < 1) return -1;
+    if (o->npole > 0 || o->tensor_on || o->step < 1) return -1;
     const int nx = o->N[0], ny = o->N[1], nz = o->N[2];
     const double *re[3] = {rex, rey, rez}, *rh[3] = {rhx, rhy, rhz};
     const long m = o->step - 1;
@@ -665,7 +787,7 @@ void oracle_set_adjoint_source(oracle_t *o, int mon, const double *cot) {
 int oracle_set_design(oracle_t *o, const int *lo, const int *hi) {
     for (int q = 0; q < 3; ++q) { o->dlo[q] = lo[q]; o->dhi[q] = hi[q]; }
     o->dcell = (long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
-    for (int a = 0; a < 3; ++a) { free(o->grad[a]); o->grad[a] = zalloc(o->dcell); }
+    for (int a = 0; a < 6; ++a) { free(o->grad[a]); o->grad[a] = zalloc(o->dcell); }
     o->design_on = 1;
     return 0;
 }
@@ -677,7 +799,7 @@ void oracle_adj_reset(oracle_t *o) {
     state_ptrs(o, v, 1);
     int nv = 18 + 6 * o->npole;
     for (int s = 0; s < nv; ++s) memset(v[s], 0, sizeof(double) * (size_t)o->ncell);
-    if (o->design_on) for (int a = 0; a < 3; ++a) memset(o->grad[a], 0, sizeof(double) * (size_t)o->dcell);
+    if (o->design_on) for (int a = 0; a < 6; ++a) memset(o->grad[a], 0, sizeof(double) * (size_t)o->dcell);
     memset(o->pgc, 0, sizeof(o->pgc));
 }
 
@@ -793,6 +915,34 @@ void oracle_adjoint_step(oracle_t *o, long m) {
     }
     /* reverse of: DFT-E at t = m + 1 */
     inject(o, 0, (double)(m + 1));
+    if (o->tensor_on) {
+        /* E^{m+1} = E^m + S S_t C: Cbar = S S_t^T Ebar = S S_t Ebar (S_t is symmetric), and
+         * d/d eps^-1_n[u][v] of Ebar^T S S_t C is S/8 sum_c (R_c D^-1/2 Ebar)_u (R_c D^-1/2 C)_v,
+         * summed over [u][v] and [v][u] for an off-diagonal component */
+        tensor_apply(o, o->A, o->tscr);
+        if (o->design_on)
+            for (int k = o->dlo[2]; k < o->dhi[2]; ++k)
+                for (int j = o->dlo[1]; j < o->dhi[1]; ++j)
+                    for (int i = o->dlo[0]; i < o->dhi[0]; ++i) {
+                        long did = ((long)(k - o->dlo[2]) * (o->dhi[1] - o->dlo[1]) + (j - o->dlo[1])) *
+                                       (o->dhi[0] - o->dlo[0]) + (i - o->dlo[0]);
+                        for (int c = 0; c < 8; ++c) {
+                            long id[3];
+                            node_edges(o, i, j, k, c, id);
+                            double wb[3], wc[3];
+                            for (int a = 0; a < 3; ++a) {
+                                double r = id[a] >= 0 ? 1.0 / sqrt(o->tD[a][id[a]]) : 0.0;
+                                wb[a] = id[a] >= 0 ? r * o->A[a][id[a]] : 0.0;
+                                wc[a] = id[a] >= 0 ? r * o->curl[a][id[a]] : 0.0;
+                            }
+                            for (int u = 0; u < 3; ++u)
+                                for (int v = u; v < 3; ++v) {
+                                    double t = u == v ? wb[u] * wc[u] : wb[u] * wc[v] + wb[v] * wc[u];
+                                    o->grad[tcomp(u, v)][did] += o->S * t / 8.0;
+                                }
+                        }
+                    }
+    }
     /* reverse of the E-phase */
     for (int a = 0; a < 3; ++a) {
         int b = (a + 1) % 3, cax = (a + 2) % 3;
@@ -854,6 +1004,9 @@ void oracle_adjoint_step(oracle_t *o, long m) {
                             double eps_b = Etb * (Eold - Et) / den;
                             o->grad[a][did] += -eps * eps * eps_b;
                         }
+                    } else if (o->tensor_on) {
+                        Eold_b = Etb;
+                        curl_b = o->S * o->tscr[a][id];
                     } else {
                         /* Et = E + S inv_eps curl */
                         Eold_b = Etb;

@@ -7,7 +7,7 @@ this module only compiles it with gcc, marshals arguments and exposes numpy view
 
 Paper passages followed (arxiv 2609.30039): Sec. 2.1 Eq. (yee) and the half-step time
 bookkeeping; Sec. 2.2 CPML and PEC; Sec. 2.3 diagonal permittivity and trapezoidal
-Drude/Lorentz poles; Sec. 2.4 plane DFT monitors; Sec. 3.1 Eq. (adjoint) and the CPML /
+Drude/Lorentz poles, symmetric node tensors with the node assembly and their admission rule; Sec. 2.4 plane DFT monitors; Sec. 3.1 Eq. (adjoint) and the CPML /
 pole transposes; Sec. 3.2 checkpoint replay (here a plain two-level store-all replay) and the
 reversible reconstruction (backward steps of Eq. (yee)).
 """
@@ -89,6 +89,9 @@ def _load():
             "oracle_adjoint_step": (None, [vp, C.c_long]),
             "oracle_pole_grad": (None, [vp, _dp]),
             "oracle_pole_coef_grad": (None, [vp, _dp]),
+            "oracle_set_tensor": (C.c_int, [vp, _dp]),
+            "oracle_tensor_apply": (C.c_int, [vp, _dp, _dp, _dp, _dp, _dp, _dp]),
+            "oracle_tensor_D": (_dp, [vp, C.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -158,6 +161,35 @@ class Oracle:
                                      kinds.ctypes.data_as(_ip), _d(deps), _d(w), _d(g),
                                      mk.ctypes.data_as(C.POINTER(C.c_ubyte)) if mk is not None else None)
         self.npole = npole
+
+    def set_tensor(self, t6):
+        """Tensor mode (Sec. 2.3): t6 = the six components (xx, yy, zz, xy, xz, yz) of eps^-1 at
+        every grid node, shape (6, nz, ny, nx); the E update then applies the node assembly
+        S_t = D^{-1/2} (1/8 sum R^T eps^-1 R) D^{-1/2} to the curl.  None switches it off.  Not
+        with poles or an energy record."""
+        if t6 is None:
+            self.lib.oracle_set_tensor(self.h, None)
+            self.tensor = False
+            return
+        t = np.ascontiguousarray(t6, dtype=np.float64).reshape(-1)
+        assert t.size == 6 * self.n
+        if self.lib.oracle_set_tensor(self.h, _d(t)) != 0:
+            raise ValueError("tensor mode excludes poles and the energy record")
+        self.tensor = True
+
+    def tensor_apply(self, v):
+        """S_t applied to three E-component arrays (tensor mode)."""
+        nx, ny, nz = self.shape
+        vin = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in v]
+        out = [np.zeros(self.n) for _ in range(3)]
+        r = self.lib.oracle_tensor_apply(self.h, *[_d(a) for a in vin], *[_d(a) for a in out])
+        assert r == 0
+        return [a.reshape(nz, ny, nx) for a in out]
+
+    def tensor_D(self, a):
+        """The diagonal of D = 1/8 sum R^T R on the edges of E component a (tensor mode)."""
+        nx, ny, nz = self.shape
+        return self._view(self.lib.oracle_tensor_D(self.h, int(a))).reshape(nz, ny, nx).copy()
 
     def add_source(self, comp, lo, hi, wave):
         wave = np.ascontiguousarray(wave, dtype=np.float64)
@@ -294,6 +326,9 @@ class Oracle:
         self._design = (tuple(lo), tuple(hi))
 
     def grad(self, comp):
+        """dJ/d eps^-1 over the design box: comp 0..2 the diagonal components of the cells; in
+        tensor mode 0..5 the node components xx, yy, zz, xy, xz, yz (an off-diagonal one counts
+        once, as one symmetric parameter)."""
         lo, hi = self._design
         n = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])
         return self._view(self.lib.oracle_grad(self.h, int(comp)), n).reshape(
@@ -336,6 +371,42 @@ class Oracle:
         out = np.zeros(6 * max(n, 1))
         self.lib.oracle_pole_coef_grad(self.h, _d(out))
         return out[: 6 * n].reshape(n, 6)
+
+
+TENSOR_TOL = 1e-6
+
+
+def tensor_rejected(t6, shape, cpml):
+    """The admission rule of Sec. 2.3, node by node: eps^-1 (components xx, yy, zz, xy, xz, yz,
+    shape (6, nz, ny, nx)) must be symmetric positive definite with every eigenvalue of eps at or
+    above one (eigenvalues of eps^-1 in (0, 1], up to a relative TENSOR_TOL), and inside the CPML
+    slab of an axis q (node coordinate < lo_q or >= N_q - hi_q; cpml = (xlo, xhi, ylo, yhi, zlo,
+    zhi)) the face normal e_q must be a principal axis (the off-diagonal entries of row q are zero
+    up to TENSOR_TOL times the largest diagonal entry) whose eigenvalue is not strictly between the
+    other two.  Returns a boolean (nz, ny, nx) array, True where the node is rejected."""
+    nx, ny, nz = shape
+    t = np.asarray(t6, dtype=np.float64).reshape(6, nz, ny, nx)
+    idx = [[0, 3, 4], [3, 1, 5], [4, 5, 2]]
+    M = np.stack([np.stack([t[idx[a][b]] for b in range(3)], axis=-1) for a in range(3)], axis=-2)
+    lam = np.linalg.eigvalsh(M)
+    bad = (lam[..., 0] <= 0.0) | (lam[..., 2] > 1.0 + TENSOR_TOL)
+    coords = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    pos = [coords[2], coords[1], coords[0]]
+    scale = np.max(np.abs(np.stack([t[0], t[1], t[2]])), axis=0)
+    for q in range(3):
+        lo, hi = cpml[2 * q], cpml[2 * q + 1]
+        if lo == 0 and hi == 0:
+            continue
+        n = shape[q]
+        inslab = (pos[q] < lo) | (pos[q] >= n - hi)
+        b, c = (q + 1) % 3, (q + 2) % 3
+        off = np.maximum(np.abs(M[..., q, b]), np.abs(M[..., q, c])) > TENSOR_TOL * scale
+        sub = np.stack([np.stack([M[..., b, b], M[..., b, c]], -1), np.stack([M[..., c, b], M[..., c, c]], -1)], -2)
+        mu = np.linalg.eigvalsh(sub)
+        tol = TENSOR_TOL * (np.abs(mu[..., 0]) + np.abs(mu[..., 1]))
+        inter = (M[..., q, q] - mu[..., 0] > tol) & (mu[..., 1] - M[..., q, q] > tol)
+        bad |= inslab & (off | inter)
+    return bad
 
 
 def gradient_replay(orc: Oracle, n_steps: int, objective, segment: int = 0):

@@ -62,6 +62,9 @@ class Scene:
     energy: bool = False
     name: str = ""
     periodic: Tuple[int, int, int] = (0, 0, 0)   # periodic x / y (z must be 0)
+    # symmetric eps^-1 tensor per grid node (Sec. 2.3 node assembly), shape (6, nz, ny, nx), components
+    # xx, yy, zz, xy, xz, yz; replaces inv_eps in the E update (no poles)
+    tensor: Optional[np.ndarray] = None
 
     @property
     def cells(self) -> int:
@@ -93,6 +96,28 @@ def gaussian_pulse(n_steps: int, wavelength: float = 20.0, courant: float = COUR
     t0 = delay * tau
     t = np.arange(n_steps, dtype=np.float64) + 1.0
     return np.sin(w0 * (t - t0)) * np.exp(-0.5 * ((t - t0) / tau) ** 2)
+
+
+def rotation(axis: int, angle: float) -> np.ndarray:
+    """Rotation matrix about coordinate axis 0, 1 or 2 by angle (radians)."""
+    c, s = math.cos(angle), math.sin(angle)
+    b, d = (axis + 1) % 3, (axis + 2) % 3
+    R = np.eye(3)
+    R[b, b], R[b, d], R[d, b], R[d, d] = c, -s, s, c
+    return R
+
+
+def inv_tensor6(eps: np.ndarray) -> np.ndarray:
+    """The six components (xx, yy, zz, xy, xz, yz) of eps^-1 for a symmetric 3 x 3 eps, or for an
+    array of them with the matrix axes last."""
+    inv = np.linalg.inv(np.asarray(eps, dtype=np.float64))
+    return np.stack([inv[..., 0, 0], inv[..., 1, 1], inv[..., 2, 2], inv[..., 0, 1], inv[..., 0, 2], inv[..., 1, 2]])
+
+
+def principal_eps(principal, R=None) -> np.ndarray:
+    """eps = R diag(principal) R^T (principal axes rotated by R)."""
+    D = np.diag(np.asarray(principal, dtype=np.float64))
+    return D if R is None else R @ D @ R.T
 
 
 def omegas_for(wavelengths, courant: float = COURANT) -> np.ndarray:

@@ -10,6 +10,8 @@ def oracle_from_scene(sc, with_sources=True, with_monitors=True, periodic=None):
     o = Oracle(sc.shape, sc.courant, periodic=periodic, cpml=sc.cpml, m=sc.cpml_m,
                kappa_max=sc.kappa_max, alpha_max=sc.alpha_max, sigma_max=sc.sigma_max)
     o.set_material(sc.inv_eps3(), poles=sc.poles, mask=sc.pole_mask)
+    if getattr(sc, "tensor", None) is not None:
+        o.set_tensor(sc.tensor)
     if with_sources:
         for s in sc.sources:
             o.add_source(s.comp, s.lo, s.hi, s.wave)
