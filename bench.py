@@ -148,13 +148,20 @@ def alg_bytes_per_cell(sc, esz, kind):
     = 4 words per half-step (averaged over the grid).
     Transposed E (adj_e): the same 10 | 12 words on the cotangent fields; a slab membership adds the
     two psibar_H read (gather) and the two psibar_E of the deferred own-cell part R + W = 6 words.
-    Transposed H (adj_h): 9 words; a membership adds two psibar_E read and two psibar_H R + W = 6."""
+    Transposed H (adj_h): 9 words; a membership adds two psibar_E read and two psibar_H R + W = 6.
+    Tensor domains (Sec. 2.3), the E side in two launches: tensor_e = curl (H 3 R, curl 3 W) + apply
+    (curl 3 R, eps^-1 6 R, E 3 R + 3 W) = 21 words; tensor_adj_e = transposed E (E array 3 R, Ebar
+    3 R + 3 W, Hbar 3 R) + apply (Ebar 3 R, eps^-1 6 R, E array 3 W) = 24 words."""
     n = sc.shape
     cells = n[0] * n[1] * n[2]
     memb = sum((sc.cpml[2 * q] + sc.cpml[2 * q + 1]) / n[q] for q in range(3))
     iso = sc.inv_eps is not None and len(sc.inv_eps) == 1
     if kind in ("e_update", "adj_e"):
         words = 10 if iso else 12
+    elif kind == "tensor_e":
+        words = 21
+    elif kind == "tensor_adj_e":
+        words = 24
     else:
         words = 9
     per_memb = 6 if kind.startswith("adj") else 4
@@ -599,7 +606,7 @@ def main():
                     help="n: run only a short n^3 FP32 forward (ncu captures on a case larger than L2)")
     ap.add_argument("--workload", default="cpml128",
                     choices=["cpml128", "pec32", "batched", "adjoint256", "large640", "reversible256", "streamed", "poles",
-                             "streamed_grad"],
+                             "streamed_grad", "tensor"],
                     help="cpml128 is the benchmark line; the others measure the remaining workloads")
     ap.add_argument("--fd-cells", type=int, default=20)
     ap.add_argument("--fp64-ref", action="store_true",
@@ -633,7 +640,8 @@ def main():
     elif args.workload != "cpml128" and args.impl == "ours":
         {"pec32": measure_pec32, "batched": measure_batched, "adjoint256": measure_adjoint256,
          "large640": measure_large640, "reversible256": measure_reversible256,
-         "streamed": measure_streamed, "poles": measure_poles, "streamed_grad": measure_streamed_grad}[args.workload](args)
+         "streamed": measure_streamed, "poles": measure_poles, "streamed_grad": measure_streamed_grad,
+         "tensor": measure_tensor}[args.workload](args)
     elif args.impl == "reference":
         run_reference(args)
     else:
@@ -1108,6 +1116,57 @@ def measure_streamed_grad(args):
         ctx.close()
     res["streamed_over_resident_time"] = round(res["streamed_seconds"] / res["resident_seconds"], 3)
     res["gradients_bitwise_equal"] = bool(torch.equal(grads["resident"], grads["streamed"]))
+    print(json.dumps(res))
+
+
+def measure_tensor(args):
+    """Symmetric node tensors (Sec. 2.3) at n^3 FP32 on tensor_blocks (rotated random tensors in the 8^3
+    blocks of the central cube, 10-cell CPML): forward and transposed Gcell-steps/s beside the
+    diagonal path on the cpml_blocks grid of the same size (both per-cell launches, state larger
+    than L2), with each step's effective bandwidth from the algorithmic bytes per cell-step
+    (alg_bytes_per_cell), and the FP32 spectra against an FP64 GPU run of the same steps."""
+    import torch
+    from paper_2609_30039_gb300 import build as B
+    from paper_2609_30039_gb300 import fdtd
+    from paper_2609_30039_gb300 import workloads as W
+    B.build()
+    n = args.profile_case or 256
+    steps = 200
+    peak, _ = peaks()
+    res = {"workload": f"tensor_blocks_{n}^3 FP32 (principal eps in [1, 4], random axes, 8^3 blocks), "
+                       f"{steps} timed steps each way", "peak_gbs": peak}
+    specs = {}
+    for kind, sc in (("tensor", W.tensor_blocks(n=n, n_steps=steps + 10)),
+                     ("diagonal", W.cpml_blocks(n=n, n_steps=steps + 10))):
+        cells = sc.cells
+        ctx = fdtd.Context([sc], dtype="f32")
+        fdtd.fdtd_set_launch_mode(ctx.ctx, 4)
+        ctx.step(10)
+        t = _timed(lambda: ctx.step(steps), ctx.stream)
+        specs[kind] = ctx.dft(0).cpu()
+        fdtd.fdtd_adjoint_begin(ctx.ctx)
+        fdtd.fdtd_step_adjoint(ctx.ctx, 10)
+        ta = _timed(lambda: fdtd.fdtd_step_adjoint(ctx.ctx, steps), ctx.stream)
+        ek, ak = ("tensor_e", "tensor_adj_e") if kind == "tensor" else ("e_update", "adj_e")
+        bf = alg_bytes_per_cell(sc, 4, ek)[0] + alg_bytes_per_cell(sc, 4, "h_update")[0]
+        ba = alg_bytes_per_cell(sc, 4, ak)[0] + alg_bytes_per_cell(sc, 4, "adj_h")[0]
+        gbs_f = bf * cells * steps / t / 1e9
+        gbs_a = ba * cells * steps / ta / 1e9
+        res[kind] = {"forward_gcell_steps_s": round(cells * steps / t / 1e9, 3),
+                     "transposed_gcell_steps_s": round(cells * steps / ta / 1e9, 3),
+                     "forward_bytes_per_cell_step": round(bf, 1), "transposed_bytes_per_cell_step": round(ba, 1),
+                     "forward_effective_gbs": round(gbs_f, 1), "forward_frac": round(gbs_f / peak, 4),
+                     "transposed_effective_gbs": round(gbs_a, 1), "transposed_frac": round(gbs_a / peak, 4)}
+        ctx.close()
+        if kind == "tensor":
+            c64 = fdtd.Context([sc], dtype="f64")
+            c64.step(10 + steps)
+            ref = c64.dft(0).cpu()
+            res[kind]["fp32_vs_fp64_spectra_rel_l2"] = float((specs[kind].to(torch.complex128) - ref).abs().norm()
+                                                             / ref.abs().norm())
+            c64.close()
+    res["tensor_over_diagonal_forward_time"] = round(
+        res["diagonal"]["forward_gcell_steps_s"] / res["tensor"]["forward_gcell_steps_s"], 3)
     print(json.dumps(res))
 
 

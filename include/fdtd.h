@@ -205,6 +205,26 @@ fdtd_status fdtd_set_periodic(fdtd_ctx* ctx, int32_t domain, const int32_t perio
  * change the phases.  Forward and transposed steps then run the Bloch kernels for this domain. */
 fdtd_status fdtd_set_bloch(fdtd_ctx* ctx, int32_t domain, const double phase[2]);
 
+/* Symmetric permittivity tensors at the grid nodes (Sec. 2.3).  inv_eps[6]: the components xx, yy,
+ * zz, xy, xz, yz of eps^-1 at every node (node (i, j, k) at offset (k ny + j) nx + i, the context's
+ * dtype; device or host memory, copied into memory the context owns).  The domain's E update then
+ * applies the node assembly S_t = D^{-1/2} (1/8 sum_n sum_c R_{n,c}^T eps^-1_n R_{n,c}) D^{-1/2} to
+ * the CPML-corrected curl, E += S S_t curl, where R_{n,c} picks one E edge per axis next to node n
+ * (the q-edge of coordinate n_q - 1 + c_q, for the 2^3 choices c) and D is the same sum with the
+ * identity tensor (1 on an edge with two end nodes, 1/2 on one whose upper node lies beyond a
+ * non-periodic high face); the diagonal eps^-1 of fdtd_create is no longer read.  The transposed
+ * steps apply S_t to Ebar (it is symmetric), and a design box (fdtd_set_design) then collects
+ * d J / d eps^-1 of its nodes, six components per node.  Admission rule (FDTD_ETENSOR, the domain is
+ * then left without tensors): every node positive definite with each eigenvalue of eps at least one
+ * (relative tolerance 1e-6), and at a node inside the CPML slab of an axis q, e_q is a principal axis
+ * (eps^-1_qb = eps^-1_qc = 0 up to 1e-6 of the largest diagonal entry) whose eigenvalue is not
+ * strictly between the two others.  Scope: no poles, no Bloch phase, no energy record, no interface
+ * record, resident contexts (FDTD_EINVAL otherwise); the context switches to launch mode 4, and
+ * other launch modes, autotuning, the backward step and kernel timing are refused while a domain
+ * holds tensors.  inv_eps = NULL returns the domain to its diagonal eps^-1.  Every call removes the
+ * domain's design box (its gradient buffer has the other layout): set the box afterwards. */
+fdtd_status fdtd_set_tensor(fdtd_ctx* ctx, int32_t domain, const void* const inv_eps[6]);
+
 /* Soft source (Sec. 2.4, Eq. (yee) s and m): after the update of `component` in forward
  * step n, every cell of the half-open box [lo, hi) gets += waveform[n] (no effect for
  * n >= n_steps).  waveform: host, copied, FP64.  *source_id may be NULL.  An electric source
@@ -360,7 +380,9 @@ fdtd_status fdtd_snapshots_free(fdtd_ctx* ctx);
 /* ---- discrete adjoint (Sec. 3.1, Eq. (adjoint)) ----
  * Design box of a domain: the material cotangent d J / d(eps^-1_a) of every cell of [lo, hi)
  * is accumulated (+=) into grad_device (FP64, borrowed, layout [3][box cells, x fastest]) by
- * every adjoint step.  The box must lie outside the CPML slabs.  grad_device = NULL removes it. */
+ * every adjoint step.  In a tensor domain (fdtd_set_tensor) the box is one of nodes and the layout
+ * [6][box nodes], components xx, yy, zz, xy, xz, yz (an off-diagonal component is one symmetric
+ * parameter).  The box must lie outside the CPML slabs.  grad_device = NULL removes it. */
 fdtd_status fdtd_set_design(fdtd_ctx* ctx, int32_t domain, const int32_t lo[3], const int32_t hi[3],
                             double* grad_device);
 

@@ -173,7 +173,9 @@ class DesignAdjoint:
                 continue
             lo, hi = sc.design
             n = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])
-            g = torch.zeros(3 * n, dtype=torch.float64, device=ctx.device)
+            # [3][cells] of the diagonal eps^-1, or [6][nodes] of a tensor domain (Sec. 2.3)
+            ncomp = 6 if getattr(sc, "tensor", None) is not None else 3
+            g = torch.zeros(ncomp * n, dtype=torch.float64, device=ctx.device)
             F.fdtd_set_design(ctx.ctx, d, lo, hi, g.data_ptr())
             self.grads.append(g)
 

@@ -62,6 +62,12 @@ struct DomainHost {
     // interface record of the absorbing-face reversible reconstruction (Sec. 3.2), or nullptr
     void* rec = nullptr;
     IfaceArgs ia{};
+    // symmetric node tensors (Sec. 2.3): eps^-1 xx yy zz xy xz yz at the nodes, the curl of the E
+    // update and the E cotangent of the transposed sweep (device, owned)
+    int tensor = 0;
+    void* tn[6] = {};
+    void* tcur[3] = {};
+    void* teb[3] = {};
 };
 
 struct MonHost {
@@ -651,6 +657,17 @@ bool any_bloch(const fdtd_ctx* c) {
     return false;
 }
 
+bool any_tensor(const fdtd_ctx* c) {
+    for (const auto& d : c->doms)
+        if (d.tensor) return true;
+    return false;
+}
+
+#define NOT_TENSOR(ctx, what)                                                                      \
+    do {                                                                                           \
+        if (any_tensor(ctx)) return fail((ctx), FDTD_EINVAL, std::string(what) + " is not available with tensor domains"); \
+    } while (0)
+
 #define NOT_BLOCH(ctx, what)                                                                       \
     do {                                                                                           \
         if (any_bloch(ctx)) return fail((ctx), FDTD_EINVAL, std::string(what) + " is not available with Bloch domains"); \
@@ -961,8 +978,25 @@ CellArgs<T> make_cell_args(const fdtd_ctx* c, int di, bool e_side) {
     for (int q = 0; q < 3; ++q) {
         ca.alo[q] = 0;
         ca.ahi[q] = h.n[q];
+        ca.cur[q] = (T*)h.tcur[q];
     }
     return ca;
+}
+
+// Tensor-operator operands of domain di: operand v, output out (three E-edge arrays each).
+template <typename T>
+TensorArgs<T> tensor_args(const fdtd_ctx* c, int di, void* const* v, void* const* out) {
+    const DomainHost& h = c->doms[di];
+    TensorArgs<T> t;
+    std::memset(&t, 0, sizeof(t));
+    for (int q = 0; q < 6; ++q) t.t[q] = (const T*)h.tn[q];
+    for (int a = 0; a < 3; ++a) {
+        t.v[a] = (const T*)v[a];
+        t.out[a] = (T*)out[a];
+        t.n[a] = h.n[a];
+        t.per[a] = h.per[a];
+    }
+    return t;
 }
 
 // The interface planes of a domain with absorbing faces (see IfacePlane) and their offsets in a slot.
@@ -1047,10 +1081,16 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
         Prof p(c, FDTD_KERNEL_E);
         for (int di = 0; di < (int)c->doms.size(); ++di) {
             const DomainHost& h = c->doms[di];
-            if (h.bloch)
+            if (h.bloch) {
                 launch_e_bloch<T>(l, bloch_args(di, true), (T)c->S, a);
-            else
+            } else if (h.tensor) {
+                // the curl (CPML memories advanced), then E += S S_t curl and the sources
+                const CellArgs<T> ce = cell_args(di, true);
+                launch_e_curl<T>(l, ce);
+                launch_tensor_apply<T>(l, tensor_args<T>(c, di, h.tcur, h.F), ce, (T)c->S, a, 1);
+            } else {
                 launch_e_cell<T>(l, cell_args(di, true), dd, (T)c->S, a, c->aniso, h.npole > 0 && h.bcell > 0);
+            }
         }
     } else {
         fork_int();
@@ -1570,6 +1610,7 @@ AdjCellArgs<T> make_adj_args(const fdtd_ctx* c, int di, int* mon) {
     a.dom = di;
     a.kz0 = 0;
     a.nzg = h.n[2];
+    for (int q = 0; q < 3; ++q) a.Eb[q] = (T*)h.teb[q];
     if (h.design && h.grad) {
         for (int q = 0; q < 3; ++q) {
             a.glo[q] = h.glo[q];
@@ -1623,11 +1664,34 @@ void adj_once(fdtd_ctx* c, int m) {
             Prof p(c, FDTD_KERNEL_ADJ_E);
             for (int di = 0; di < (int)c->doms.size(); ++di) {
                 const DomainHost& h = c->doms[di];
-                if (h.bloch)
+                if (h.bloch) {
                     launch_adj_e_bloch<T>(l, make_adj_bloch<T>(c, di, args[di]), (T)c->S, c->adj_pending);
-                else
+                } else if (h.tensor) {
+                    // Ebar^{m+1} into Eb, the node-tensor cotangent, then the curl cotangent S S_t Ebar
+                    // into the E array for the H side
+                    launch_adj_e_cell<T>(l, args[di], dd, c->d_mons, (T)c->S, m, c->adj_pending, 0, mon[di], 0, 1);
+                    if (h.design && h.grad) {
+                        TensorGradArgs<T> g;
+                        std::memset(&g, 0, sizeof(g));
+                        for (int q = 0; q < 3; ++q) {
+                            g.Eb[q] = (const T*)h.teb[q];
+                            g.H[q] = (const T*)h.F[3 + q];
+                            g.n[q] = h.n[q];
+                            g.per[q] = h.per[q];
+                            g.glo[q] = h.glo[q];
+                            g.ghi[q] = h.ghi[q];
+                        }
+                        g.gvol = (long long)(h.ghi[0] - h.glo[0]) * (h.ghi[1] - h.glo[1]) * (h.ghi[2] - h.glo[2]);
+                        g.grad = h.grad;
+                        launch_tensor_grad<T>(l, tensor_args<T>(c, di, h.teb, h.A), g, (T)c->S);
+                    }
+                    CellArgs<T> none;
+                    std::memset(&none, 0, sizeof(none));
+                    launch_tensor_apply<T>(l, tensor_args<T>(c, di, h.teb, h.A), none, (T)c->S, StepArgs{}, 0);
+                } else {
                     launch_adj_e_cell<T>(l, args[di], dd, c->d_mons, (T)c->S, m, c->adj_pending,
-                                         h.npole > 0 && h.bcell > 0, mon[di], h.pgc_on);
+                                         h.npole > 0 && h.bcell > 0, mon[di], h.pgc_on, 0);
+                }
             }
         }
         {
@@ -1867,10 +1931,11 @@ fdtd_status stream_adjoint(fdtd_ctx* c, int n_steps) {
             for (int j = kb - 1; j >= 0; --j) {
                 int mon = 0;
                 aa = window_adj_args<T>(c, s2, j, &mon);
-                launch_adj_e_cell<T>(l, aa, ad, c->d_mons, (T)c->S, (int)(tb + j), j < kb - 1 ? 1 : 0, poles, mon, 0);
+                launch_adj_e_cell<T>(l, aa, ad, c->d_mons, (T)c->S, (int)(tb + j), j < kb - 1 ? 1 : 0, poles, mon, 0,
+                                     0);
                 launch_adj_h_cell<T>(l, aa, ad, c->d_mons, (T)c->S, (int)(tb + j), mon);
             }
-            launch_adj_flush_cell<T>(l, aa, ad, (T)c->S, poles);
+            launch_adj_flush_cell<T>(l, aa, ad, (T)c->S, poles, 0);
             st = window_copy(c, w, c->hadj[nxt], c->aws, w.zs, w.ze, false, false, c->stream);
             if (st != FDTD_OK) return st;
         }
@@ -1947,10 +2012,10 @@ fdtd_status flush_adjoint(fdtd_ctx* c) {
             const int poles = h.npole > 0 && h.bcell > 0;
             if (c->dtype == FDTD_F32)
                 launch_adj_flush_cell<float>(L(c), make_adj_args<float>(c, di, &mon), (const Dom<float>*)c->d_doms,
-                                             (float)c->S, poles);
+                                             (float)c->S, poles, h.tensor);
             else
                 launch_adj_flush_cell<double>(L(c), make_adj_args<double>(c, di, &mon), (const Dom<double>*)c->d_doms,
-                                              c->S, poles);
+                                              c->S, poles, h.tensor);
         }
     } else if (c->dtype == FDTD_F32) {
         launch_adj_flush<float>(L(c), (const Dom<float>*)c->d_doms, c->d_tiles, (int)c->tiles.size(), (float)c->S);
@@ -2103,7 +2168,8 @@ void time_launches_t(fdtd_ctx* c, cudaStream_t st, int which, int n, long long* 
                 const AdjCellArgs<T> aa = make_adj_args<T>(c, di, &mon);
                 const int m = (int)std::max(0ll, c->adj_step - 1);
                 if (which == 3)
-                    launch_adj_e_cell<T>(l, aa, dd, c->d_mons, (T)c->S, m, 1, h.npole > 0 && h.bcell > 0, mon, h.pgc_on);
+                    launch_adj_e_cell<T>(l, aa, dd, c->d_mons, (T)c->S, m, 1, h.npole > 0 && h.bcell > 0, mon, h.pgc_on,
+                                         0);
                 else
                     launch_adj_h_cell<T>(l, aa, dd, c->d_mons, (T)c->S, m, mon);
             }
@@ -2418,6 +2484,70 @@ fdtd_status fdtd_set_periodic(fdtd_ctx* ctx, int32_t domain, const int32_t perio
     return sync_doms(ctx);
 }
 
+fdtd_status fdtd_set_tensor(fdtd_ctx* ctx, int32_t domain, const void* const inv_eps[6]) {
+    GUARD(ctx);
+    NOT_STREAMED(ctx);
+    if (!valid_dom(ctx, domain)) return fail(ctx, FDTD_EINVAL, "bad domain");
+    DomainHost& d = ctx->doms[domain];
+    // a design box's buffer holds [3][cells] for the diagonal eps^-1 and [6][nodes] for tensors: a
+    // change between the two removes the box, so that no launch writes past a buffer of the other form
+    auto drop_design = [&]() -> fdtd_status {
+        if (!d.design) return FDTD_OK;
+        d.design = 0;
+        d.grad = nullptr;
+        return sync_doms(ctx);
+    };
+    if (!inv_eps) {
+        if (d.tensor) {
+            drop_graphs(ctx);   // captured steps change
+            fdtd_status st = drop_design();
+            if (st != FDTD_OK) return st;
+        }
+        d.tensor = 0;
+        return FDTD_OK;
+    }
+    for (int q = 0; q < 6; ++q)
+        if (!inv_eps[q]) return fail(ctx, FDTD_EINVAL, "a tensor needs its six component arrays");
+    if (d.bloch || d.npole > 0) return fail(ctx, FDTD_EINVAL, "a tensor domain has no poles and no Bloch phase");
+    if (ctx->energy_on || d.rec)
+        return fail(ctx, FDTD_EINVAL, "tensor domains take no energy record and no interface record");
+    const size_t bytes = (size_t)d.ncell * ctx->esz;
+    fdtd_status st = FDTD_OK;
+    if (!d.tn[0]) {
+        for (int q = 0; q < 6 && st == FDTD_OK; ++q) st = dmalloc(ctx, &d.tn[q], bytes);
+        for (int q = 0; q < 3 && st == FDTD_OK; ++q) st = dmalloc(ctx, &d.tcur[q], bytes);
+        for (int q = 0; q < 3 && st == FDTD_OK; ++q) st = dmalloc(ctx, &d.teb[q], bytes);
+        if (st != FDTD_OK) return st;
+    }
+    drop_graphs(ctx);   // captured steps change
+    st = drop_design();
+    if (st != FDTD_OK) return st;
+    d.tensor = 0;
+    for (int q = 0; q < 6; ++q) CK(ctx, cudaMemcpyAsync(d.tn[q], inv_eps[q], bytes, cudaMemcpyDefault, ctx->stream));
+    // the admission rule, node by node
+    CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(unsigned long long), ctx->stream));
+    if (ctx->dtype == FDTD_F32)
+        launch_tensor_admission<float>(L(ctx), tensor_args<float>(ctx, domain, d.tcur, d.tcur), d.dlo, d.dhi, d.ns,
+                                       ctx->d_flag);
+    else
+        launch_tensor_admission<double>(L(ctx), tensor_args<double>(ctx, domain, d.tcur, d.tcur), d.dlo, d.dhi, d.ns,
+                                        ctx->d_flag);
+    CKL(ctx);
+    unsigned long long bad = 0;
+    CK(ctx, cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (bad)
+        return fail(ctx, FDTD_ETENSOR,
+                    "domain " + std::to_string(domain) + ": " + std::to_string(bad) +
+                        " nodes hold a tensor the admission rule rejects (eps below one, not positive definite, or "
+                        "inside a CPML face whose normal is no principal axis or has the intermediate eigenvalue)");
+    ctx->cell_mode = 1;
+    ctx->use_persistent = 0;
+    ctx->persist_variant = 0;
+    d.tensor = 1;
+    return FDTD_OK;
+}
+
 fdtd_status fdtd_set_bloch(fdtd_ctx* ctx, int32_t domain, const double phase[2]) {
     GUARD(ctx);
     NOT_STREAMED(ctx);
@@ -2429,8 +2559,8 @@ fdtd_status fdtd_set_bloch(fdtd_ctx* ctx, int32_t domain, const double phase[2])
     for (int q = 0; q < 2; ++q)
         if (phase[q] != 0.0 && !d.per[q])
             return fail(ctx, FDTD_EINVAL, "a Bloch phase needs a periodic axis (fdtd_set_periodic first)");
-    if (d.ns[0] || d.ns[1] || d.ns[2] || d.npole > 0 || !d.mons.empty() || d.design)
-        return fail(ctx, FDTD_EINVAL, "a Bloch domain has no CPML slabs, poles, DFT monitors or design box");
+    if (d.ns[0] || d.ns[1] || d.ns[2] || d.npole > 0 || !d.mons.empty() || d.design || d.tensor)
+        return fail(ctx, FDTD_EINVAL, "a Bloch domain has no CPML slabs, poles, DFT monitors, design box or tensors");
     if (!d.bloch) {
         // the state gains six parts: snapshots and the snapshot part table start afresh
         fdtd_status st = fdtd_snapshots_free(ctx);
@@ -2623,6 +2753,7 @@ fdtd_status fdtd_enable_energy(fdtd_ctx* ctx, int32_t capacity) {
     GUARD(ctx);
     NOT_STREAMED(ctx);
     NOT_BLOCH(ctx, "the energy record");
+    NOT_TENSOR(ctx, "the energy record");
     if (capacity < 1) return fail(ctx, FDTD_EINVAL, "capacity must be >= 1");
     for (auto& d : ctx->doms) {
         if (d.energy) dfree(ctx, d.energy);
@@ -2740,6 +2871,7 @@ fdtd_status fdtd_record_interface(fdtd_ctx* ctx, int32_t capacity) {
     GUARD(ctx);
     NOT_STREAMED(ctx);
     NOT_BLOCH(ctx, "the interface record");
+    NOT_TENSOR(ctx, "the interface record");
     if (capacity < 0) return fail(ctx, FDTD_EINVAL, "capacity must be >= 0");
     if (capacity > 0 && (!ctx->cell_mode || ctx->energy_on))
         return fail(ctx, FDTD_EINVAL, "the interface record runs in launch mode 4 without an energy record");
@@ -2767,6 +2899,7 @@ fdtd_status fdtd_step_backward(fdtd_ctx* ctx, int32_t n_steps) {
     GUARD(ctx);
     NOT_STREAMED(ctx);
     NOT_BLOCH(ctx, "the backward step");
+    NOT_TENSOR(ctx, "the backward step");
     if (n_steps < 0) return fail(ctx, FDTD_EINVAL, "n_steps must be >= 0");
     for (const auto& d : ctx->doms) {
         if (d.npole > 0) return fail(ctx, FDTD_EINVAL, "backward steps need nondispersive domains (no poles)");
@@ -2833,6 +2966,7 @@ fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode) {
     if (ctx->streamed && mode != 4) return fail(ctx, FDTD_EINVAL, "a host-streamed context steps per cell (mode 4)");
     if (mode < 0 || mode >= FDTD_LAUNCH_MODES) return fail(ctx, FDTD_EINVAL, "launch mode must be in [0, 4]");
     if (mode != 4 && any_bloch(ctx)) return fail(ctx, FDTD_EINVAL, "Bloch domains step in launch mode 4");
+    if (mode != 4 && any_tensor(ctx)) return fail(ctx, FDTD_EINVAL, "tensor domains step in launch mode 4");
     for (const auto& d : ctx->doms)
         if (mode != 4 && d.rec) return fail(ctx, FDTD_EINVAL, "an interface record runs in launch mode 4");
     if (mode != ctx->cell_mode * 4) drop_graphs(ctx);   // graphs hold the launches of one mode
@@ -2858,6 +2992,7 @@ fdtd_status fdtd_autotune(fdtd_ctx* ctx, int32_t n_steps, double* ms_per_mode) {
     GUARD(ctx);
     NOT_STREAMED(ctx);
     NOT_BLOCH(ctx, "autotuning (Bloch domains step in launch mode 4)");
+    NOT_TENSOR(ctx, "autotuning (tensor domains step in launch mode 4)");
     if (n_steps < 1) return fail(ctx, FDTD_EINVAL, "n_steps must be >= 1");
     const int slot = 1 << 30;   // private slot id (public ids are below 2^30)
     const int energy = ctx->energy_on;
@@ -3428,6 +3563,7 @@ fdtd_status fdtd_time_half_steps(fdtd_ctx* ctx, int32_t which, int32_t n_launche
     if (!ctx->cell_mode || ctx->energy_on || ctx->use_persistent)
         return fail(ctx, FDTD_EINVAL, "per-cell launch mode (4) without an energy record only");
     NOT_BLOCH(ctx, "kernel timing");
+    NOT_TENSOR(ctx, "kernel timing");
     if (which == 2 && ctx->n_dft_items == 0) return fail(ctx, FDTD_EINVAL, "no DFT monitor");
     if (!ctx->cap_stream) CK(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     CK(ctx, cudaStreamSynchronize(ctx->stream));

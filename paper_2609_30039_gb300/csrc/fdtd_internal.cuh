@@ -285,6 +285,8 @@ struct CellArgs {
     // cells [alo, ahi) the backward step updates (the whole domain, or the interior of a domain
     // with absorbing faces, see launch_iface)
     int alo[3], ahi[3];
+    // curl output of the E side of a tensor domain (launch_e_curl), else unused
+    T* cur[3];
 };
 
 // Interface planes of the absorbing-face reversible reconstruction (Sec. 3.2): the H nodes on the
@@ -343,6 +345,32 @@ struct AdjCellArgs {
     // whole box, whose first global plane is gzg and whose cell count is gvol.
     int kz0, nzg, gzg;
     long long gvol;
+    // tensor domain (Sec. 2.3 node assembly): the E cotangent Ebar (the E array then carries the
+    // curl cotangent S S_t Ebar between the E and H launches), else nullptr
+    T* Eb[3];
+};
+
+// Operands of the node-assembled tensor operator S_t = D^{-1/2} (1/8 sum R^T eps^-1 R) D^{-1/2}
+// (Sec. 2.3) of one domain: eps^-1 at the nodes (xx, yy, zz, xy, xz, yz; node (i, j, k) at offset
+// (k ny + j) nx + i), the E-edge operand v and the output.
+template <typename T>
+struct TensorArgs {
+    const T* t[6];
+    const T* v[3];
+    T* out[3];
+    int n[3], per[3];
+};
+
+// Node-tensor cotangent over a design box of nodes: the E cotangent Ebar^{m+1}, the forward H of
+// u^m (whose plain curl is the curl the update used), and the FP64 gradient [6][box nodes].
+template <typename T>
+struct TensorGradArgs {
+    const T* Eb[3];
+    const T* H[3];
+    int n[3], per[3];
+    int glo[3], ghi[3];
+    long long gvol;
+    double* grad;
 };
 
 // A Bloch domain's operands (Sec. 2.2): the per-cell arguments of its real parts plus the
@@ -378,6 +406,23 @@ void launch_e_cell(const Launch& L, const CellArgs<T>& c, const Dom<T>* doms, T 
                    int poles);
 template <typename T>
 void launch_h_cell(const Launch& L, const CellArgs<T>& c, T S, const StepArgs& a);
+// Curl of the E update of a tensor domain (CPML memories advanced, no E update, no sources) into
+// c.cur; PEC-held edges are not written.
+template <typename T>
+void launch_e_curl(const Launch& L, const CellArgs<T>& c);
+// Tensor operator (kernels_tensor.cu), one thread per cell, every non-PEC E edge: forward (fwd = 1)
+// out += S S_t v plus the soft sources of c (the E update of a tensor domain, out = E, v = its curl);
+// transposed (fwd = 0) out = S S_t v, zero on PEC-held edges (the curl cotangent from Ebar).
+template <typename T>
+void launch_tensor_apply(const Launch& L, const TensorArgs<T>& t, const CellArgs<T>& c, T S, const StepArgs& a,
+                         int fwd);
+// d J / d eps^-1 of every node of the design box, += over one transposed step.
+template <typename T>
+void launch_tensor_grad(const Launch& L, const TensorArgs<T>& t, const TensorGradArgs<T>& g, T S);
+// Counts the nodes the Sec. 2.3 admission rule rejects into *d_bad.
+template <typename T>
+void launch_tensor_admission(const Launch& L, const TensorArgs<T>& t, const int* dlo, const int* dhi, const int* ns,
+                             unsigned long long* d_bad);
 // One backward step (reversible reconstruction) of a lossless domain: ce / ch hold the E / H
 // half-step's sources; the step index is *a.d_base + a.offset.
 template <typename T>
@@ -401,17 +446,20 @@ template <typename T>
 void launch_adj_flush(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S);
 // Per-cell transposed half-steps of one domain (one thread per cell, the forward per-cell grid).
 // poles: the domain has a pole box; mon: some monitor of the domain carries an adjoint source;
-// pole_grad: the domain collects pole-coefficient cotangents.
+// pole_grad: the domain collects pole-coefficient cotangents; tensor: the domain is a tensor domain
+// (Ebar lives in c.Eb, no poles, the material cotangent comes from launch_tensor_grad).
 template <typename T>
 void launch_adj_e_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, const Mon* mons, T S, int m,
-                       int pending, int poles, int mon, int pole_grad);
+                       int pending, int poles, int mon, int pole_grad, int tensor);
 template <typename T>
 void launch_adj_h_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, const Mon* mons, T S, int m,
                        int mon);
 // Completes a pending transposed step (the deferred own-cell part of the E side) for every cell of
-// one domain or window, per cell; poles: the descriptor doms[c.dom] holds the pole box.
+// one domain or window, per cell; poles: the descriptor doms[c.dom] holds the pole box; tensor: Ebar
+// comes from c.Eb.
 template <typename T>
-void launch_adj_flush_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, T S, int poles);
+void launch_adj_flush_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, T S, int poles,
+                           int tensor);
 template <typename T>
 void launch_inject(const Launch& L, const Dom<T>* doms, const Mon* mons, const int* entries, int nentries,
                    long long nthreads, const long long* entry_begin, int step, int kind);

@@ -682,7 +682,10 @@ __device__ __forceinline__ int slab_or_none(int x, int lo, int hi, int N, int ns
 // completes the deferred own-cell transpose of step m+1 (pending), adds the gathered cotangent gat
 // and the monitor injection, accumulates the material (and pole-coefficient) cotangents, and
 // returns the new lagged value S eps^-1 / (1 + eps^-1 G) Ebar.  om: offsets to the -1 neighbours.
-template <typename T, int a, bool kPoles, bool kGrad, bool kMon, bool kPG>
+// kTen (a tensor domain, Sec. 2.3): Ebar of step m+1 is kept in c.Eb (the pending part only advances
+// the psibar_E with F, the curl cotangent the apply kernel left in the E array) and the return value
+// is Ebar itself, which the caller stores into c.Eb.
+template <typename T, int a, bool kPoles, bool kGrad, bool kMon, bool kPG, bool kTen = false>
 __device__ __forceinline__ T adj_e_comp(const AdjCellArgs<T>& c, const Dom<T>* __restrict__ doms,
                                         const Mon* __restrict__ mons, int i, int j, int k, long long id, T F, T ie,
                                         T gat, T S, int m, int pending, bool disp, long long bo, const int* sl,
@@ -691,7 +694,9 @@ __device__ __forceinline__ T adj_e_comp(const AdjCellArgs<T>& c, const Dom<T>* _
     const int x[3] = {i, j, k + c.kz0};   // coefficient rows are indexed by global coordinates
     T eb;
     if (pending) {
-        if (kPoles && disp) {
+        if (kTen) {
+            eb = c.Eb[a][id];
+        } else if (kPoles && disp) {
             const Dom<T>& d = doms[c.dom];
             eb = (T(1) / ie - d.G) / S * F;
             for (int p = 0; p < d.npole; ++p) {
@@ -777,6 +782,7 @@ __device__ __forceinline__ T adj_e_comp(const AdjCellArgs<T>& c, const Dom<T>* _
             }
         }
     }
+    if (kTen) return et;
     if (kPoles && disp) return S * ie / (T(1) + ie * gdisp) * et;
     return S * ie * et;
 }
@@ -784,7 +790,7 @@ __device__ __forceinline__ T adj_e_comp(const AdjCellArgs<T>& c, const Dom<T>* _
 // kPG (with kPoles): also sums the pole-coefficient cotangents of the domain (Sec. 3.1: pole parameters
 // through the transposed dispersion update): per thread, then one warp sum, a block sum in shared
 // memory and one FP64 atomic per block and coefficient into the domain's accumulator.
-template <typename T, bool kPoles, bool kGrad, bool kMon, bool kPG>
+template <typename T, bool kPoles, bool kGrad, bool kMon, bool kPG, bool kTen>
 __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const Dom<T>* __restrict__ doms,
                                                 const Mon* __restrict__ mons, T S, int m, int pending, double* pacc) {
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
@@ -806,9 +812,13 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
     const T bz_xm = hx_ ? Bz[ij + ox] : T(0), by_xm = hx_ ? By[ij + ox] : T(0);
     const T f0 = (c.A[0] + pl)[ij], f1 = (c.A[1] + pl)[ij], f2 = (c.A[2] + pl)[ij];
     const bool aniso = c.ie[1] != c.ie[0];
-    const T ie0 = (c.ie[0] + pl)[ij];
-    const T ie1 = aniso ? (c.ie[1] + pl)[ij] : ie0;
-    const T ie2 = aniso ? (c.ie[2] + pl)[ij] : ie0;
+    const T ie0 = kTen ? T(1) : (c.ie[0] + pl)[ij];
+    const T ie1 = kTen ? T(1) : (aniso ? (c.ie[1] + pl)[ij] : ie0);
+    const T ie2 = kTen ? T(1) : (aniso ? (c.ie[2] + pl)[ij] : ie0);
+    // where the new E cotangents go: the lagged form into the E array, a tensor domain's Ebar into Eb
+    T* const E0 = kTen ? c.Eb[0] : c.A[0];
+    T* const E1 = kTen ? c.Eb[1] : c.A[1];
+    T* const E2 = kTen ? c.Eb[2] : c.A[2];
     const bool pi = i == 0 && !c.per[0], pj = j == 0 && !c.per[1], pk = k == 0;
     const long long id = pl + ij;
     const long long om[3] = {ox, oy, -nxy};
@@ -831,13 +841,13 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
         const T g1 = S * ((bz - bz_xm) - (bx - bx_zm));
         const T g2 = S * ((bx - bx_ym) - (by - by_xm));
         if (!(pj || pk))
-            (c.A[0] + pl)[ij] = adj_e_comp<T, 0, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f0, ie0, g0, S,
+            (E0 + pl)[ij] = adj_e_comp<T, 0, kPoles, kGrad, kMon, kPG, kTen>(c, doms, mons, i, j, k, id, f0, ie0, g0, S,
                                                                           m, pending, disp, bo, none, om, pacc);
         if (!(pi || pk))
-            (c.A[1] + pl)[ij] = adj_e_comp<T, 1, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f1, ie1, g1, S,
+            (E1 + pl)[ij] = adj_e_comp<T, 1, kPoles, kGrad, kMon, kPG, kTen>(c, doms, mons, i, j, k, id, f1, ie1, g1, S,
                                                                           m, pending, disp, bo, none, om, pacc);
         if (!(pi || pj))
-            (c.A[2] + pl)[ij] = adj_e_comp<T, 2, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f2, ie2, g2, S,
+            (E2 + pl)[ij] = adj_e_comp<T, 2, kPoles, kGrad, kMon, kPG, kTen>(c, doms, mons, i, j, k, id, f2, ie2, g2, S,
                                                                           m, pending, disp, bo, none, om, pacc);
         return;
     }
@@ -895,22 +905,22 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
     }
     // tangential E on a PEC plane (coordinate 0 of a non-periodic axis other than its own) is held
     if (!(pj || pk))
-        (c.A[0] + pl)[ij] = adj_e_comp<T, 0, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f0, ie0, g0, S, m,
+        (E0 + pl)[ij] = adj_e_comp<T, 0, kPoles, kGrad, kMon, kPG, kTen>(c, doms, mons, i, j, k, id, f0, ie0, g0, S, m,
                                                                       pending, disp, bo, sl, om, pacc);
     if (!(pi || pk))
-        (c.A[1] + pl)[ij] = adj_e_comp<T, 1, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f1, ie1, g1, S, m,
+        (E1 + pl)[ij] = adj_e_comp<T, 1, kPoles, kGrad, kMon, kPG, kTen>(c, doms, mons, i, j, k, id, f1, ie1, g1, S, m,
                                                                       pending, disp, bo, sl, om, pacc);
     if (!(pi || pj))
-        (c.A[2] + pl)[ij] = adj_e_comp<T, 2, kPoles, kGrad, kMon, kPG>(c, doms, mons, i, j, k, id, f2, ie2, g2, S, m,
+        (E2 + pl)[ij] = adj_e_comp<T, 2, kPoles, kGrad, kMon, kPG, kTen>(c, doms, mons, i, j, k, id, f2, ie2, g2, S, m,
                                                                       pending, disp, bo, sl, om, pacc);
 }
 
-template <typename T, bool kPoles, bool kGrad, bool kMon, bool kPG>
+template <typename T, bool kPoles, bool kGrad, bool kMon, bool kPG, bool kTen = false>
 __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, kPoles || kGrad || kMon>())
     k_adj_e_cell(const AdjCellArgs<T> c, const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, T S, int m,
                  int pending) {
     if (!kPG) {
-        adj_e_cell_body<T, kPoles, kGrad, kMon, false>(c, doms, mons, S, m, pending, nullptr);
+        adj_e_cell_body<T, kPoles, kGrad, kMon, false, kTen>(c, doms, mons, S, m, pending, nullptr);
         return;
     }
     // every thread of the block reaches the reductions below (the domain, hence np, is the launch's)
@@ -918,7 +928,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, kPoles || k
     const int np = d.pgc ? d.npole : 0;
     double acc[kMaxPole * 6];
     for (int q = 0; q < np * 6; ++q) acc[q] = 0.0;
-    adj_e_cell_body<T, kPoles, kGrad, kMon, true>(c, doms, mons, S, m, pending, acc);
+    adj_e_cell_body<T, kPoles, kGrad, kMon, true, false>(c, doms, mons, S, m, pending, acc);
     __shared__ double red[kTileX * kTileY / 32];
     const int tid = threadIdx.y * kTileX + threadIdx.x;
     for (int q = 0; q < np * 6; ++q) {
@@ -1067,7 +1077,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
 // Completes a pending transposed step cell by cell (the algebra of e_deferred): for every E
 // component not held by a PEC plane, Ebar = F / (S eps^-1) (or the pole form in dispersive cells,
 // which also advances the pole cotangents) and the own psibar_E of its two derivatives.
-template <typename T, bool kPoles>
+template <typename T, bool kPoles, bool kTen = false>
 __global__ void __launch_bounds__(kTileX* kTileY) k_adj_flush_cell(const AdjCellArgs<T> c,
                                                                    const Dom<T>* __restrict__ doms, T S) {
     const int nx = c.n[0], ny = c.n[1];
@@ -1089,10 +1099,12 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_adj_flush_cell(const AdjCell
     const bool pec[3] = {pj || pk, pi || pk, pi || pj};
     for (int a = 0; a < 3; ++a) {
         if (pec[a]) continue;
-        const T ie = c.ie[a][id];
+        const T ie = kTen ? T(1) : c.ie[a][id];
         const T F = c.A[a][id];
         T eb;
-        if (kPoles && disp) {
+        if (kTen) {
+            eb = c.Eb[a][id];
+        } else if (kPoles && disp) {
             const Dom<T>& d = doms[c.dom];
             eb = (T(1) / ie - d.G) / S * F;
             for (int p = 0; p < d.npole; ++p) {
@@ -1117,10 +1129,13 @@ __global__ void __launch_bounds__(kTileX* kTileY) k_adj_flush_cell(const AdjCell
 }
 
 template <typename T>
-void launch_adj_flush_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, T S, int poles) {
+void launch_adj_flush_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, T S, int poles,
+                           int tensor) {
     const dim3 g((unsigned)((c.n[0] + kTileX - 1) / kTileX), (unsigned)((c.n[1] + kTileY - 1) / kTileY),
                  (unsigned)c.n[2]);
-    if (poles)
+    if (tensor)
+        k_adj_flush_cell<T, false, true><<<g, dim3(kTileX, kTileY), 0, L.stream>>>(c, doms, S);
+    else if (poles)
         k_adj_flush_cell<T, true><<<g, dim3(kTileX, kTileY), 0, L.stream>>>(c, doms, S);
     else
         k_adj_flush_cell<T, false><<<g, dim3(kTileX, kTileY), 0, L.stream>>>(c, doms, S);
@@ -1133,8 +1148,17 @@ inline dim3 adj_cell_grid(const int* n) {
 
 template <typename T>
 void launch_adj_e_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* doms, const Mon* mons, T S, int m,
-                       int pending, int poles, int mon, int pole_grad) {
+                       int pending, int poles, int mon, int pole_grad, int tensor) {
     const dim3 g = adj_cell_grid(c.n), b(kTileX, kTileY);
+    if (tensor) {
+        // a tensor domain has no poles; its material cotangent comes from launch_tensor_grad
+        if (mon)
+            k_adj_e_cell<T, false, false, true, false, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending);
+        else
+            k_adj_e_cell<T, false, false, false, false, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending);
+        ++*L.counter;
+        return;
+    }
     const bool grad = c.grad != nullptr;
     const int key = (poles && pole_grad ? 8 : 0) | (poles ? 4 : 0) | (grad ? 2 : 0) | (mon ? 1 : 0);
     switch (key) {
@@ -1218,10 +1242,10 @@ void launch_inject(const Launch& L, const Dom<T>* doms, const Mon* mons, const i
     template void launch_inject<T>(const Launch&, const Dom<T>*, const Mon*, const int*, int, long long,        \
                                    const long long*, int, int);                                                 \
     template void launch_adj_e_cell<T>(const Launch&, const AdjCellArgs<T>&, const Dom<T>*, const Mon*, T, int,  \
-                                       int, int, int, int);                                                     \
+                                       int, int, int, int, int);                                                \
     template void launch_adj_h_cell<T>(const Launch&, const AdjCellArgs<T>&, const Dom<T>*, const Mon*, T, int,  \
                                        int);                                                                    \
-    template void launch_adj_flush_cell<T>(const Launch&, const AdjCellArgs<T>&, const Dom<T>*, T, int);
+    template void launch_adj_flush_cell<T>(const Launch&, const AdjCellArgs<T>&, const Dom<T>*, T, int, int);
 GBFDTD_INST(float)
 GBFDTD_INST(double)
 #undef GBFDTD_INST

@@ -560,7 +560,9 @@ __device__ __forceinline__ T cpml_cell(const T* coef, int N, int x, T* psi, T D)
 
 // kBack: the backward step of the reversible reconstruction (Sec. 3.2) for a lossless domain,
 // E^n = (E^{n+1} - s^n) - S eps^-1 curl H^{n+1/2}, called with S negated (no CPML, no poles).
-template <typename T, bool kAniso, bool kPoles, bool kPer, bool kBack = false>
+// kCurl: the first half of a tensor domain's E update (Sec. 2.3): the CPML-corrected curl of every
+// non-PEC edge into c.cur (the memories advance as usual); launch_tensor_apply then applies S_t.
+template <typename T, bool kAniso, bool kPoles, bool kPer, bool kBack = false, bool kCurl = false>
 __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
     k_e_cell(const CellArgs<T> c, const Dom<T>* __restrict__ doms, T S, const StepArgs a) {
     const int nx = c.n[0], ny = c.n[1];
@@ -627,6 +629,12 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
             if (!px) yx1 = cpml_cell(c.coef[1], ny, j, c.psi[0][0] + o, yx1);
             if (!pz) yz2 = cpml_cell(c.coef[1], ny, j, c.psi[2][1] + o, yz2);
         }
+    }
+    if (kCurl) {
+        if (!px) c.cur[0][id] = yx1 - yx2;
+        if (!py) c.cur[1][id] = yy1 - yy2;
+        if (!pz) c.cur[2][id] = yz1 - yz2;
+        return;
     }
     bool disp = false;
     if (kPoles) {
@@ -760,6 +768,16 @@ void launch_e_cell(const Launch& L, const CellArgs<T>& c, const Dom<T>* doms, T 
         launch_e_cell_t<T, true>(L, c, doms, S, a, aniso, poles);
     else
         launch_e_cell_t<T, false>(L, c, doms, S, a, aniso, poles);
+    ++*L.counter;
+}
+
+template <typename T>
+void launch_e_curl(const Launch& L, const CellArgs<T>& c) {
+    const dim3 g = cell_grid(c.n), b(kTileX, kTileY);
+    if (c.per[0] || c.per[1])
+        k_e_cell<T, false, false, true, false, true><<<g, b, 0, L.stream>>>(c, nullptr, T(0), StepArgs{});
+    else
+        k_e_cell<T, false, false, false, false, true><<<g, b, 0, L.stream>>>(c, nullptr, T(0), StepArgs{});
     ++*L.counter;
 }
 
@@ -1315,6 +1333,8 @@ template void launch_iface<float>(const Launch&, float* const*, const int*, cons
                                   int, int);
 template void launch_iface<double>(const Launch&, double* const*, const int*, const IfaceArgs&, double*, const int*,
                                    int, int, int);
+template void launch_e_curl<float>(const Launch&, const CellArgs<float>&);
+template void launch_e_curl<double>(const Launch&, const CellArgs<double>&);
 template void launch_h_cell<float>(const Launch&, const CellArgs<float>&, float, const StepArgs&);
 template void launch_h_cell<double>(const Launch&, const CellArgs<double>&, double, const StepArgs&);
 template cudaError_t launch_steps<float>(const Launch&, const Dom<float>*, const Tile*, int, float, const StepArgs&, int,

@@ -80,6 +80,7 @@ _SIGS = {
     "fdtd_set_material": [_ctx, C.c_int32, C.POINTER(fdtd_material)],
     "fdtd_set_periodic": [_ctx, C.c_int32, _i32p],
     "fdtd_set_bloch": [_ctx, C.c_int32, C.POINTER(C.c_double)],
+    "fdtd_set_tensor": [_ctx, C.c_int32, C.POINTER(C.c_void_p)],
     "fdtd_dft_flux": [_ctx, C.c_int32, C.POINTER(C.c_double), C.c_int32],
     "fdtd_step_backward": [_ctx, C.c_int32],
     "fdtd_record_interface": [_ctx, C.c_int32],
@@ -364,6 +365,16 @@ def fdtd_set_bloch(ctx, domain, phase):
     _check(load().fdtd_set_bloch(ctx, int(domain), ph), "fdtd_set_bloch", ctx)
 
 
+def fdtd_set_tensor(ctx, domain, components):
+    """components: six arrays (device tensors or host arrays of the context's dtype, contiguous) of
+    eps^-1 xx, yy, zz, xy, xz, yz at the nodes, or None to return to the diagonal eps^-1."""
+    if components is None:
+        _check(load().fdtd_set_tensor(ctx, int(domain), None), "fdtd_set_tensor", ctx)
+        return
+    ptrs = (C.c_void_p * 6)(*[int(t.data_ptr()) if hasattr(t, "data_ptr") else int(t.ctypes.data) for t in components])
+    _check(load().fdtd_set_tensor(ctx, int(domain), ptrs), "fdtd_set_tensor", ctx)
+
+
 def fdtd_set_material(ctx, domain, material):
     _check(load().fdtd_set_material(ctx, int(domain), C.byref(material)), "fdtd_set_material", ctx)
 
@@ -469,6 +480,9 @@ class Context:
         for d, sc in enumerate(self.scenes):
             if any(sc.periodic):
                 fdtd_set_periodic(self.ctx, d, sc.periodic)
+            if getattr(sc, "tensor", None) is not None:
+                t = torch.from_numpy(np.ascontiguousarray(sc.tensor, dtype=self.npdtype)).to(self.device)
+                fdtd_set_tensor(self.ctx, d, [t[q] for q in range(6)])
             for s in sc.sources:
                 self.sources.append(fdtd_add_source(self.ctx, d, s.comp, s.lo, s.hi, s.wave))
             for m in sc.monitors:

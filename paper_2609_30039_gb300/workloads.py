@@ -155,6 +155,30 @@ def cpml_blocks(n: int = 128, d: int = 10, n_steps: int = 2000, block: int = 8, 
                  inv_eps=[inv], sources=[src], monitors=[mon], name=f"cpml_blocks_{n}^3")
 
 
+def tensor_blocks(n: int = 256, d: int = 10, n_steps: int = 200, block: int = 8, seed_index: int = 6,
+                  wavelengths=(18.0, 20.0, 22.0)) -> Scene:
+    """The cpml_blocks box with anisotropic blocks (Sec. 2.3 tensors at the nodes): every 8^3 block of
+    the central cube holds eps with principal values uniform in [1, 4] (indices up to 2, like the
+    birefringent media of the paper's validation) along random principal axes; vacuum elsewhere,
+    so every CPML node holds the identity (admitted)."""
+    rng = _rng(seed_index)
+    sc = cpml_blocks(n=n, d=d, n_steps=n_steps, block=block, seed_index=seed_index, wavelengths=wavelengths)
+    lo, hi = n // 4, n - n // 4
+    nb = -(-(hi - lo) // block)
+    Q, _ = np.linalg.qr(rng.standard_normal((nb ** 3, 3, 3)))
+    lam = rng.uniform(1.0, 4.0, size=(nb ** 3, 3))
+    blocks = inv_tensor6(np.einsum("nij,nj,nkj->nik", Q, lam, Q)).reshape(6, nb, nb, nb)
+    t = np.zeros((6, n, n, n))
+    t[0] = t[1] = t[2] = 1.0
+    for q in range(6):
+        big = np.repeat(np.repeat(np.repeat(blocks[q], block, 0), block, 1), block, 2)
+        t[q, lo:hi, lo:hi, lo:hi] = big[: hi - lo, : hi - lo, : hi - lo]
+    sc.inv_eps = None
+    sc.tensor = t
+    sc.name = f"tensor_blocks_{n}^3"
+    return sc
+
+
 def density_to_eps(rho: np.ndarray) -> np.ndarray:
     """Design map eps_r = 1 + 11 sigmoid(8 (rho - 0.5)) (the workload's material producer)."""
     return 1.0 + 11.0 / (1.0 + np.exp(-8.0 * (rho - 0.5)))
