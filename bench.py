@@ -55,14 +55,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
-FORWARD_KERNEL_SOURCES = ("kernels_fwd.cu", "fdtd_internal.cuh", "tma_ptx.cuh")
+KERNEL_SOURCES = {"forward": ("kernels_fwd.cu", "fdtd_internal.cuh", "tma_ptx.cuh"),
+                  "adjoint": ("kernels_adj.cu", "fdtd_internal.cuh")}
 
 
-def source_sha():
-    """Hash of the sources that define the forward kernels (the ones the roofline reports)."""
+def source_sha(family="forward"):
+    """Hash of the sources that define one family of kernels (forward or transposed)."""
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2609_30039_gb300", "csrc")
-    for f in FORWARD_KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[family]:
         with open(os.path.join(cs, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -70,13 +71,14 @@ def source_sha():
 
 def recorded_traffic(kernel, steps_per_launch):
     """DRAM bytes per launch from the committed ncu summary (bytes per time step x steps per
-    launch), if the summary was taken from the current kernel source."""
+    launch), if the summary was taken from the current source of the kernel's family."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
         ent = d.get(kernel)
-        if ent and ent.get("source_sha") == source_sha():
+        fam = "adjoint" if kernel.startswith("adj") else "forward"
+        if ent and ent.get("source_sha") == source_sha(fam):
             return int(ent["dram_bytes_per_step"] * steps_per_launch)
     except Exception:
         pass
@@ -606,13 +608,14 @@ def main():
                     help="n: run only a short n^3 FP32 forward (ncu captures on a case larger than L2)")
     ap.add_argument("--workload", default="cpml128",
                     choices=["cpml128", "pec32", "batched", "adjoint256", "large640", "reversible256", "streamed", "poles",
-                             "streamed_grad", "tensor"],
+                             "streamed_grad", "tensor", "small_batch"],
                     help="cpml128 is the benchmark line; the others measure the remaining workloads")
     ap.add_argument("--fd-cells", type=int, default=20)
     ap.add_argument("--fp64-ref", action="store_true",
                     help="--workload large640: also an FP64 gradient as the reference of both snapshot codecs")
     ap.add_argument("--fp64-ref-slots", type=int, default=8)
     ap.add_argument("--stream-n", type=int, default=768, help="--workload streamed: grid edge")
+    ap.add_argument("--grad-n", type=int, default=512, help="--workload streamed_grad: grid edge")
     ap.add_argument("--slab", type=int, default=256, help="--workload streamed: owned planes per slab")
     ap.add_argument("--halo", type=int, default=32, help="--workload streamed: halo planes (steps per batch)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="precision of --profile-case")
@@ -641,7 +644,7 @@ def main():
         {"pec32": measure_pec32, "batched": measure_batched, "adjoint256": measure_adjoint256,
          "large640": measure_large640, "reversible256": measure_reversible256,
          "streamed": measure_streamed, "poles": measure_poles, "streamed_grad": measure_streamed_grad,
-         "tensor": measure_tensor}[args.workload](args)
+         "tensor": measure_tensor, "small_batch": measure_small_batch}[args.workload](args)
     elif args.impl == "reference":
         run_reference(args)
     else:
@@ -1058,7 +1061,7 @@ def measure_streamed_grad(args):
     from paper_2609_30039_gb300 import fdtd
     from paper_2609_30039_gb300 import workloads as W
     B.build()
-    n = args.stream_n if args.stream_n != 768 else 512
+    n = args.grad_n
     steps = args.steps * 8 if args.steps != 10 else 64
     sc = W.cpml_blocks(n=n, d=CPML, n_steps=steps)
     q = n // 4
@@ -1116,6 +1119,57 @@ def measure_streamed_grad(args):
         ctx.close()
     res["streamed_over_resident_time"] = round(res["streamed_seconds"] / res["resident_seconds"], 3)
     res["gradients_bitwise_equal"] = bool(torch.equal(grads["resident"], grads["streamed"]))
+    print(json.dumps(res))
+
+
+def measure_small_batch(args):
+    """Many small domains in one context (the paper's tensor batch: cohorts of identical small
+    cases, Sec. 4): B cpml_blocks cases of 32^3 (6-cell CPML, 4^3 blocks, each its own seed), 800
+    steps, FP32, for B = 8 and 64.  The autotuner times every launch mode on the batch (per-half-step
+    tile launches, the persistent kernels, per-cell launches per domain); the batch is then timed in
+    the fastest mode and in the per-cell mode, against the same cases run one context after another."""
+    import torch
+    from paper_2609_30039_gb300 import build as B
+    from paper_2609_30039_gb300 import fdtd
+    from paper_2609_30039_gb300 import workloads as W
+    B.build()
+    steps, n = 800, 32
+    names = ["tiles", "persistent", "persistent+prefetch", "persistent+TMA", "per-cell"]
+    res = {"workload": f"{n}^3 cpml_blocks cases (CPML 6), {steps} steps, FP32"}
+    for nb in (8, 64):
+        scs = [W.cpml_blocks(n=n, d=6, n_steps=steps, block=4, region=(8, 24), seed_index=20 + b,
+                             wavelengths=(10.0, 12.0, 14.0)) for b in range(nb)]
+        ctx = fdtd.Context(scs, dtype="f32")
+        ctx.step(64)
+        tune = fdtd.fdtd_autotune(ctx.ctx, 64)
+        best = fdtd.fdtd_get_launch_mode(ctx.ctx)
+        out = {"autotune_ms_per_64_steps": dict(zip(names, [round(v, 3) for v in tune])), "chosen": names[best]}
+        for mode in sorted({best, 4}):
+            fdtd.fdtd_set_launch_mode(ctx.ctx, mode)
+            fdtd.fdtd_reset(ctx.ctx)
+            fdtd.fdtd_dft_reset(ctx.ctx)
+            ctx.step(steps)
+            fdtd.fdtd_reset(ctx.ctx)
+            fdtd.fdtd_dft_reset(ctx.ctx)
+            t = _timed(lambda: ctx.step(steps), ctx.stream)
+            out[f"batch_{names[mode]}_cases_per_s"] = round(nb / t, 2)
+        ctx.close()
+        one = [fdtd.Context([sc], dtype="f32") for sc in scs[: min(nb, 8)]]
+        for c in one:
+            fdtd.fdtd_set_launch_mode(c.ctx, 4)
+            c.step(steps)
+            fdtd.fdtd_reset(c.ctx)
+            fdtd.fdtd_dft_reset(c.ctx)
+
+        def seq():
+            for c in one:
+                c.step(steps)
+
+        t = _timed(seq, one[0].stream)
+        out["one_context_per_case_cases_per_s"] = round(len(one) / t, 2)
+        for c in one:
+            c.close()
+        res[f"B{nb}"] = out
     print(json.dumps(res))
 
 
