@@ -946,6 +946,26 @@ def measure_reversible256(args):
     a, b = grads["reversible"], grads["checkpointed_32"]
     res["reversible_vs_checkpointed_gradient_rel_l2"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
     res["speedup"] = round(res["checkpointed_32"]["seconds"] / res["reversible"]["seconds"], 3)
+    # the absorbing-face variant (Sec. 3.2): the adjoint-design workload with CPML on every face;
+    # the interior steps backward from the recorded interface planes
+    sa = W.adjoint_design(n=n)
+    ab = {"workload": f"adjoint_design_{n}^3 (CPML 12 on every face), {sa.n_steps} steps, FP32"}
+    ag = {}
+    for name, make in (("reversible_interface", lambda c: ADJ.ReversibleAdjoint(c)),
+                       ("checkpointed_32", lambda c: ADJ.DesignAdjoint(c, slots=32))):
+        ctx = fdtd.Context([sa], dtype="f32")
+        runner = make(ctx)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        (J, _), g, stats = runner.run(sa.n_steps, loss)
+        torch.cuda.synchronize()
+        ab[name] = {"J": J, "seconds": round(time.perf_counter() - t0, 3), **{k: int(v) for k, v in stats.items()}}
+        ag[name] = g[0].cpu().numpy().copy()
+        ctx.close()
+    a, b = ag["reversible_interface"], ag["checkpointed_32"]
+    ab["reversible_vs_checkpointed_gradient_rel_l2"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    ab["speedup"] = round(ab["checkpointed_32"]["seconds"] / ab["reversible_interface"]["seconds"], 3)
+    res["absorbing_faces"] = ab
     print(json.dumps(res))
 
 
