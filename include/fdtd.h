@@ -111,7 +111,9 @@ typedef struct {
  * grids/cpml/materials have n_domains entries.  Checks Eq. (cfl) (FDTD_ECFL), the tensor
  * admission rule in every CPML cell (FDTD_ETENSOR: with a diagonal tensor the face normal is
  * a principal axis; the normal eigenvalue must not lie strictly between the other two), and
- * the memory plan against cudaMemGetInfo before allocating (FDTD_ENOMEM).  Synchronises the
+ * the memory plan against cudaMemGetInfo before allocating (FDTD_ENOMEM).  Grid limits
+ * (FDTD_EINVAL): 2 <= nx, ny <= 65535, nz >= 2, fewer than 2^40 cells, fewer than 2^31 cells per
+ * z-plane and per CPML memory array (slab depth times the two other extents).  Synchronises the
  * stream.  *out is set only on FDTD_OK. */
 fdtd_status fdtd_create(int32_t n_domains, const fdtd_grid* grids, const fdtd_cpml* cpml,
                         const fdtd_material* materials, void* stream, fdtd_ctx** out);

@@ -1260,7 +1260,6 @@ fdtd_status stream_prepare(fdtd_ctx* c) {
                 }
     }
     const int nsl = slab_count(c);
-    const long long nxy = (long long)h.n[0] * h.n[1];
     std::vector<Dom<T>> hd(nsl);
     std::vector<DftItem> items;
     c->sitem_begin.assign(nsl, 0);
@@ -2223,6 +2222,15 @@ static fdtd_status create_impl(int32_t n_domains, const fdtd_grid* grids, const 
             const int n = q == 0 ? g.nx : (q == 1 ? g.ny : g.nz);
             if (p.cells[2 * q] < 0 || p.cells[2 * q + 1] < 0 || p.cells[2 * q] + p.cells[2 * q + 1] > n - 2)
                 return bail(FDTD_EINVAL);
+        }
+        // the per-cell kernels index within a z-plane and within a CPML memory array in 32 bits
+        const long long nn[3] = {g.nx, g.ny, g.nz};
+        bool fits = nn[0] * nn[1] < (1ll << 31);
+        for (int q = 0; q < 3; ++q)
+            fits = fits && (long long)(p.cells[2 * q] + p.cells[2 * q + 1]) * nn[(q + 1) % 3] * nn[(q + 2) % 3] < (1ll << 31);
+        if (!fits) {
+            c->err = "a z-plane or a CPML memory array holds 2^31 or more cells";
+            return bail(FDTD_EINVAL);
         }
         if ((p.cells[0] | p.cells[1] | p.cells[2] | p.cells[3] | p.cells[4] | p.cells[5]) &&
             (!(p.m >= 0) || !(p.kappa_max >= 1) || !(p.alpha_max >= 0)))

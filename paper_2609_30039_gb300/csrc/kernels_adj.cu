@@ -647,10 +647,10 @@ constexpr int adj_cell_blocks() {
 // Offset of cell (i, j, k) in the slab array of axis q at slab index s, written so that the part
 // depending only on the block's plane k (block-uniform) is computed in 64 bits once and the in-plane
 // part in 32 bits.
-__device__ __forceinline__ long long slab_off_c(const int* n, const int* ns, int q, int i, int j, int k, int s) {
-    if (q == 0) return (long long)k * (n[1] * ns[0]) + (j * ns[0] + s);
-    if (q == 1) return (long long)k * (ns[1] * n[0]) + (s * n[0] + i);
-    return (long long)s * ((long long)n[0] * n[1]) + (j * n[0] + i);
+__device__ __forceinline__ int slab_off_c(const int* n, const int* ns, int q, int i, int j, int k, int s) {
+    if (q == 0) return k * (n[1] * ns[0]) + (j * ns[0] + s);
+    if (q == 1) return k * (ns[1] * n[0]) + (s * n[0] + i);
+    return s * (n[0] * n[1]) + (j * n[0] + i);
 }
 
 // Dbar of a derivative at node (i, j, k) whose coordinate along axis q is x and slab index sl
@@ -794,7 +794,10 @@ template <typename T, bool kPoles, bool kGrad, bool kMon, bool kPG, bool kTen>
 __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const Dom<T>* __restrict__ doms,
                                                 const Mon* __restrict__ mons, T S, int m, int pending, double* pacc) {
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
-    const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
+    // a warp covers 16 x 2 cells (two half-rows of 64 / 128 aligned bytes): a row's x slabs fill two
+    // of its warps instead of half of them
+    const int i = blockIdx.x * 16 + (threadIdx.x & 15), j = blockIdx.y * 16 + threadIdx.y * 2 + (threadIdx.x >> 4);
+    const int k = blockIdx.z;
     if (i >= nx || j >= ny) return;
     const int kg = k + c.kz0;   // global plane (CPML z profile, monitors, plain ranges)
     const long long nxy = (long long)nx * ny;
@@ -949,7 +952,8 @@ template <typename T, bool kMon>
 __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
     k_adj_h_cell(const AdjCellArgs<T> c, const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, T S, int m) {
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
-    const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
+    const int i = blockIdx.x * 16 + (threadIdx.x & 15), j = blockIdx.y * 16 + threadIdx.y * 2 + (threadIdx.x >> 4);
+    const int k = blockIdx.z;
     if (i >= nx || j >= ny) return;
     const int kg = k + c.kz0;   // global plane (CPML z profile, monitors, plain ranges)
     const long long nxy = (long long)nx * ny;
@@ -1046,19 +1050,19 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
     }
     // finish the H-side CPML transpose of step m (the E-side launch has read psibar_H)
     if (sy >= 0) {
-        const long long o = slab_off_c(c.n, c.ns, 1, i, j, k, sy);
+        const int o = slab_off_c(c.n, c.ns, 1, i, j, k, sy);
         const T b = c.cH[1][j];
         c.apsiH[0][0][o] = b * (c.apsiH[0][0][o] - S * b0);
         c.apsiH[2][1][o] = b * (c.apsiH[2][1][o] + S * b2);
     }
     if (sz >= 0) {
-        const long long o = slab_off_c(c.n, c.ns, 2, i, j, k, sz);
+        const int o = slab_off_c(c.n, c.ns, 2, i, j, k, sz);
         const T b = c.cH[2][kg];
         c.apsiH[0][1][o] = b * (c.apsiH[0][1][o] + S * b0);
         c.apsiH[1][0][o] = b * (c.apsiH[1][0][o] - S * b1);
     }
     if (sx >= 0) {
-        const long long o = slab_off_c(c.n, c.ns, 0, i, j, k, sx);
+        const int o = slab_off_c(c.n, c.ns, 0, i, j, k, sx);
         const T b = c.cH[0][i];
         c.apsiH[1][1][o] = b * (c.apsiH[1][1][o] + S * b1);
         c.apsiH[2][0][o] = b * (c.apsiH[2][0][o] - S * b2);
@@ -1142,8 +1146,9 @@ void launch_adj_flush_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T
     ++*L.counter;
 }
 
+// blocks of 32 x 8 threads covering 16 x 16 cells of a plane (warps of 16 x 2 cells)
 inline dim3 adj_cell_grid(const int* n) {
-    return dim3((unsigned)((n[0] + kTileX - 1) / kTileX), (unsigned)((n[1] + kTileY - 1) / kTileY), (unsigned)n[2]);
+    return dim3((unsigned)((n[0] + 15) / 16), (unsigned)((n[1] + 15) / 16), (unsigned)n[2]);
 }
 
 template <typename T>

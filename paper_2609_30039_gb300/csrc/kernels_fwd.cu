@@ -566,7 +566,8 @@ template <typename T, bool kAniso, bool kPoles, bool kPer, bool kBack = false, b
 __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
     k_e_cell(const CellArgs<T> c, const Dom<T>* __restrict__ doms, T S, const StepArgs a) {
     const int nx = c.n[0], ny = c.n[1];
-    const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
+    const int i = blockIdx.x * 16 + (threadIdx.x & 15), j = blockIdx.y * 16 + threadIdx.y * 2 + (threadIdx.x >> 4);
+    const int k = blockIdx.z;
     const int kg = k + c.kz0;   // global plane (CPML z profile, sources)
     if (i >= nx || j >= ny) return;
     const long long nxy = (long long)nx * ny;
@@ -669,7 +670,8 @@ template <typename T, bool kPer, bool kBack = false>
 __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
     k_h_cell(const CellArgs<T> c, T S, const StepArgs a) {
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
-    const int i = blockIdx.x * kTileX + threadIdx.x, j = blockIdx.y * kTileY + threadIdx.y, k = blockIdx.z;
+    const int i = blockIdx.x * 16 + (threadIdx.x & 15), j = blockIdx.y * 16 + threadIdx.y * 2 + (threadIdx.x >> 4);
+    const int k = blockIdx.z;
     const int kg = k + c.kz0;   // global plane (CPML z profile, sources)
     if (i < nx && j < ny) {
         const long long nxy = (long long)nx * ny;
@@ -747,7 +749,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
 
 // grid: (x chunks of kTileX, y chunks of kTileY, z planes)
 inline dim3 cell_grid(const int* n) {
-    return dim3((unsigned)((n[0] + kTileX - 1) / kTileX), (unsigned)((n[1] + kTileY - 1) / kTileY), (unsigned)n[2]);
+    return dim3((unsigned)((n[0] + 15) / 16), (unsigned)((n[1] + 15) / 16), (unsigned)n[2]);
 }
 
 template <typename T, bool kPer>
