@@ -55,7 +55,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = {"forward": ("kernels_fwd.cu", "fdtd_internal.cuh", "tma_ptx.cuh"),
+KERNEL_SOURCES = {"forward": ("kernels_fwd.cu", "fdtd_internal.cuh"),
                   "adjoint": ("kernels_adj.cu", "fdtd_internal.cuh")}
 
 
@@ -264,7 +264,8 @@ def run_ours(args):
                       "e_plus_h_us_per_step": round(eh, 3), "step_us": round(step_us, 3),
                       "e_plus_h_fits_step": bool(eh <= step_us * 1.02)}
     else:
-        # no graph replays (a persistent launch mode): the whole step is the kernel
+        # tile launches (mode 0): the interior and shell launches of a half-step overlap on two
+        # streams, so the whole step is taken as the unit
         dom, avg_ms = "step", step_us * 1e-3
         alg_bytes = (bE + bH) * ncell
         achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
@@ -281,9 +282,9 @@ def run_ours(args):
                    "l2": "flushed between timed iterations (256 MiB write); the ~75 MB state stays L2-resident "
                          "within an iteration", "parallelism": f"{world} independent replica(s), no collective"},
         "gpu_launches": int(launches),
-        "launch_mode": {"chosen": ["per-half-step graphs", "persistent", "persistent+prefetch", "persistent+TMA",
-                                   "per-cell graphs"][mode],
-                        "autotune_ms_per_200_steps": [round(v, 3) for v in tune_ms] if tune_ms else "fixed"},
+        "launch_mode": {"chosen": {0: "tile graphs", 4: "per-cell graphs"}[mode],
+                        "autotune_ms_per_200_steps": {"tile graphs": round(tune_ms[0], 3),
+                                                      "per-cell graphs": round(tune_ms[4], 3)} if tune_ms else "fixed"},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                      "alg_bytes_per_launch": int(alg_bytes), "avg_launch_us": round(avg_ms * 1e3, 3),
@@ -622,9 +623,8 @@ def main():
     ap.add_argument("--cpml", type=int, default=CPML, help="CPML depth of --profile-case (0: PEC box)")
     ap.add_argument("--adjoint", action="store_true", help="--profile-case: also time as many transposed steps")
     ap.add_argument("--launch-mode", type=int, default=None,
-                    help="0 per half-step tile launches, 1 persistent, 2 persistent with prefetch, 3 persistent "
-                         "with TMA staging, 4 per-cell launches; default: autotuned (the bench line), 4 "
-                         "(--profile-case)")
+                    choices=[0, 4], help="0 per-half-step tile launches over all domains, 4 per-cell launches; "
+                                         "default: autotuned (the bench line), 4 (--profile-case)")
     ap.add_argument("--dry-run", action="store_true",
                     help="host-only check of the launch path: N gloo ranks, no GPU work, one JSON line")
     args = ap.parse_args()
@@ -803,7 +803,8 @@ def measure_batched(args):
     out = {"workload": f"lorentz_batch: {len(all_scs)} domains, {total_cells} cells, {T} steps, FP32",
            "gcell_steps_s": round(total_cells * T / t / 1e9, 3), "seconds": round(t, 4),
            "n_gpus": world, "scaling": "strong (fixed batch, domains sharded over ranks)",
-           "launch_mode": mode, "autotune_ms_per_64_steps": [round(v, 3) for v in tune_ms]}
+           "launch_mode": mode, "autotune_ms_per_64_steps": {"tiles": round(tune_ms[0], 3),
+                                                              "per-cell": round(tune_ms[4], 3)}}
     if rank == 0 and not args.no_cpu:
         obuild()
         o = oracle_from_scene(scs[small])
@@ -1145,16 +1146,16 @@ def measure_streamed_grad(args):
 def measure_small_batch(args):
     """Many small domains in one context (the paper's tensor batch: cohorts of identical small
     cases, Sec. 4): B cpml_blocks cases of 32^3 (6-cell CPML, 4^3 blocks, each its own seed), 800
-    steps, FP32, for B = 8 and 64.  The autotuner times every launch mode on the batch (per-half-step
-    tile launches, the persistent kernels, per-cell launches per domain); the batch is then timed in
-    the fastest mode and in the per-cell mode, against the same cases run one context after another."""
+    steps, FP32, for B = 8 and 64.  The autotuner times both launch modes on the batch (per-half-step
+    tile launches over all domains, per-cell launches per domain); the batch is then timed in the
+    faster mode and in the per-cell mode, against the same cases run one context after another."""
     import torch
     from paper_2609_30039_gb300 import build as B
     from paper_2609_30039_gb300 import fdtd
     from paper_2609_30039_gb300 import workloads as W
     B.build()
     steps, n = 800, 32
-    names = ["tiles", "persistent", "persistent+prefetch", "persistent+TMA", "per-cell"]
+    names = {0: "tiles", 4: "per-cell"}
     res = {"workload": f"{n}^3 cpml_blocks cases (CPML 6), {steps} steps, FP32"}
     for nb in (8, 64):
         scs = [W.cpml_blocks(n=n, d=6, n_steps=steps, block=4, region=(8, 24), seed_index=20 + b,
@@ -1163,7 +1164,7 @@ def measure_small_batch(args):
         ctx.step(64)
         tune = fdtd.fdtd_autotune(ctx.ctx, 64)
         best = fdtd.fdtd_get_launch_mode(ctx.ctx)
-        out = {"autotune_ms_per_64_steps": dict(zip(names, [round(v, 3) for v in tune])), "chosen": names[best]}
+        out = {"autotune_ms_per_64_steps": {names[q]: round(tune[q], 3) for q in names}, "chosen": names[best]}
         for mode in sorted({best, 4}):
             fdtd.fdtd_set_launch_mode(ctx.ctx, mode)
             fdtd.fdtd_reset(ctx.ctx)

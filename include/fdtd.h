@@ -23,9 +23,9 @@
  *     nodes at coordinate N do not exist.
  *   - Component ids: 0..2 = Ex, Ey, Ez; 3..5 = Hx, Hy, Hz.
  *   - Every function returns an fdtd_status; nothing throws across the ABI.  On error the
- *     context keeps a message (fdtd_last_error).  After FDTD_ECUDA, or FDTD_ETIMEOUT reporting a
- *     device-side wait that ran out, the context is poisoned: every later call except
- *     fdtd_destroy / fdtd_last_error returns FDTD_ESTATE.
+ *     context keeps a message (fdtd_last_error).  After FDTD_ECUDA the context is poisoned:
+ *     every later call except fdtd_destroy / fdtd_last_error returns FDTD_ESTATE.  No kernel of
+ *     the library waits on another block or kernel, so no device-side wait can run out.
  *   - All device work is enqueued on the stream given to fdtd_create (a cudaStream_t passed
  *     as void*; NULL = legacy default stream).  Calls are asynchronous unless stated.
  *     A context is not thread-safe.
@@ -55,7 +55,7 @@ typedef enum {
     FDTD_ECUDA = 5,      /* a CUDA call failed; the context is poisoned */
     FDTD_ESTATE = 6,     /* call not valid in the current state (see each function) */
     FDTD_ENONFINITE = 7, /* NaN/Inf found by fdtd_check_finite */
-    FDTD_ETIMEOUT = 8    /* a bounded host wait, or a bounded device-side wait, ran out */
+    FDTD_ETIMEOUT = 8    /* a bounded host wait ran out (fdtd_synchronize) */
 } fdtd_status;
 
 enum { FDTD_F32 = 0, FDTD_F64 = 1 };          /* storage and arithmetic type of fields */
@@ -299,25 +299,23 @@ fdtd_status fdtd_step_backward(fdtd_ctx* ctx, int32_t n_steps);
 fdtd_status fdtd_record_interface(fdtd_ctx* ctx, int32_t capacity);
 
 /* Launch modes (no counterpart in the paper; they change scheduling, not arithmetic):
- * mode 0: per-half-step launches (replayed as CUDA graphs); mode 1: persistent
- * cooperative launches (4 blocks per SM in FP32); mode 2: persistent launches whose interior
- * tiles load the next z-plane ahead into registers (3 blocks per SM); mode 3: persistent
- * launches whose interior tiles stage whole z-planes in shared memory with tiled bulk tensor
- * copies (TMA), several planes ahead.  Mode 3 applies to domains whose rows (nx elements) are
- * a multiple of 16 bytes and whose fields and eps^-1 arrays are 16-byte aligned; other domains
- * run the mode-1 code.  Mode 4 (default): per-half-step launches (CUDA graphs) of per-cell
- * kernels, one thread per cell over every cell of a domain (with an energy record it runs the
- * mode-0 code).
- * All modes compute the same values bitwise.  FDTD_EINVAL for another mode. */
+ * mode 0: per-half-step launches over one tile work list of every domain (interior and shell
+ * tiles on two streams), replayed as CUDA graphs: the fastest form for batches of many domains.
+ * Mode 4 (default): per-half-step launches (CUDA graphs) of per-cell kernels, one thread per cell
+ * over every cell of a domain, one launch per domain (with an energy record it runs the mode-0
+ * code): the fastest form for one or a few domains.  Both compute the same values bitwise.
+ * Modes 1-3 (persistent multi-step kernels with grid barriers) are not available: FDTD_EINVAL,
+ * as for any other value. */
 #define FDTD_LAUNCH_MODES 5
 fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode);
 fdtd_status fdtd_get_launch_mode(fdtd_ctx* ctx, int32_t* mode);
 
-/* Autotuner (no counterpart in the paper): times each launch mode for n_steps forward steps on
- * the current state, with DFT recording as configured and energy recording off, and keeps the
- * fastest.  The state, step count, DFT accumulators and energies are left as they were (state
+/* Autotuner (no counterpart in the paper): times launch modes 0 and 4 for n_steps forward steps
+ * on the current state, with DFT recording as configured and energy recording off, and keeps the
+ * faster.  The state, step count, DFT accumulators and energies are left as they were (state
  * and accumulators are copied aside and restored after every trial).  ms_per_mode
- * (FDTD_LAUNCH_MODES entries, may be NULL) receives the measured milliseconds.  Needs device
+ * (FDTD_LAUNCH_MODES entries indexed by mode, may be NULL) receives the measured milliseconds
+ * of modes 0 and 4 and -1 for the others.  Needs device
  * memory for one native snapshot plus the accumulators (FDTD_ENOMEM otherwise).  Synchronises
  * the stream. */
 fdtd_status fdtd_autotune(fdtd_ctx* ctx, int32_t n_steps, double* ms_per_mode);
@@ -431,22 +429,8 @@ fdtd_status fdtd_check_finite(fdtd_ctx* ctx);
 
 /* Synchronises the context's stream, polling at most timeout_ms milliseconds
  * (FDTD_ETIMEOUT if the work has not finished by then; the work itself is not cancelled, and the
- * context stays usable).  Once the stream has drained it reads the persistent kernel's sticky error
- * word: if a device-side wait of a persistent launch (a grid barrier, or a staged plane copy of
- * launch mode 3) gave up, it returns FDTD_ETIMEOUT and poisons the context.  Every later
- * persistent launch of the context returns at its first instruction once the word is set, so no
- * further step runs on a state that is no longer the result of the requested steps.
- * fdtd_dft_read to host memory and fdtd_check_finite read the same word after they synchronise. */
+ * context stays usable).  A CUDA error reported by the stream poisons the context (FDTD_ECUDA). */
 fdtd_status fdtd_synchronize(fdtd_ctx* ctx, int32_t timeout_ms);
-
-/* Wait bound of the persistent launches (modes 1-3; no counterpart in the paper): a grid-barrier
- * wait gives up after `polls` polls of ~64 ns each (default 2^26, a few seconds), records the
- * error and leaves the launch.  extra_arrivals (0 or 1; default 0) is a test hook: with 1 every
- * barrier waits for one block more than the launch has, so no barrier can complete and every
- * block gives up after at most `polls` polls -- the bounded failure path, exercised without any
- * block that hangs or faults.  Synchronises the stream.  FDTD_EINVAL for polls < 1 or another
- * extra_arrivals. */
-fdtd_status fdtd_set_wait_limit(fdtd_ctx* ctx, int64_t polls, int32_t extra_arrivals);
 
 /* Number of kernel launches this context has enqueued since creation (instrumentation). */
 fdtd_status fdtd_launch_count(fdtd_ctx* ctx, int64_t* n);
@@ -482,8 +466,7 @@ enum {
     FDTD_KERNEL_STEP = 4,     /* device step counter */
     FDTD_KERNEL_ADJ_E = 5,    /* transposed step, E side */
     FDTD_KERNEL_ADJ_H = 6,    /* transposed step, H side */
-    FDTD_KERNEL_PERSISTENT = 7, /* persistent launch of several forward steps (E and H) */
-    FDTD_KERNEL_CLASSES = 8
+    FDTD_KERNEL_CLASSES = 8   /* (class 7 is unused) */
 };
 /* Starts recording an event pair around every kernel launch (at most max_launches launches,
  * later ones are not timed).  Adds two event records per launch to the stream. */

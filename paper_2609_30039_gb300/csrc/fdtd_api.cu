@@ -51,8 +51,6 @@ struct DomainHost {
     int per[3] = {0, 0, 0};        // periodic axes (x, y)
     double* pgc = nullptr;         // pole-coefficient cotangents [npole][6] (device, owned)
     int pgc_on = 0;                // collected by the transposed steps
-    const void* tmaps = nullptr;   // this domain's kTmaMaps tensor maps in device memory
-    int tma = 0;                   // maps encoded for the current field and eps^-1 pointers
     // Bloch-periodic faces (Sec. 2.2): complex fields, the imaginary parts of the forward and
     // adjoint fields in FI / AI, phase per period of the x and y seams
     int bloch = 0;
@@ -68,6 +66,10 @@ struct DomainHost {
     void* tn[6] = {};
     void* tcur[3] = {};
     void* teb[3] = {};
+    // objective injection of one transposed step over the box of the monitors that carry adjoint
+    // sources ([6][box cells]: E of step m, H of step m - 1; device, owned; grown with the box)
+    void* inj = nullptr;
+    long long inj_cap = 0;
 };
 
 struct MonHost {
@@ -113,14 +115,7 @@ struct fdtd_ctx {
     Src* d_srcs = nullptr;          // every source of every domain
     int* d_step = nullptr;
     unsigned* d_ticket = nullptr;   // completion ticket of the last H launch of a step
-    GridSync* d_sync = nullptr;     // barrier / ticket of the persistent step kernel
-    Tile* d_tiles_lpt = nullptr;    // general tiles first, then interior (persistent kernel)
-    int n_lpt = 0;
-    int use_persistent = 0;
     int cell_mode = 1;              // per-half-step launches of the per-cell streaming kernels
-    int persist_variant = 0;        // 0 register path, 1 register prefetch, 2 TMA-staged interior
-    void* d_tmaps = nullptr;        // kTmaMaps CUtensorMap per domain
-    int persist_grid = 0;
     int h_step_tmp = 0;
     long long step = 0;
     long long adj_step = 0;
@@ -442,65 +437,6 @@ void fill_dom(const fdtd_ctx* c, const DomainHost& h, Dom<T>& d) {
     for (int i = 0; i < d.nsrc; ++i) d.src[i] = h.srcs[i];
     d.energy = c->energy_on ? h.energy : nullptr;
     d.energy_cap = h.energy_cap;
-    d.tmaps = h.tmaps;
-    d.tma = h.tma;
-}
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).
-PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-        else
-            cudaGetLastError();
-    }
-    return fn;
-}
-
-// Plane-box tensor maps of one domain (Ex..Hz, eps^-1 x y z), each a 3-D view (nx, ny, nz) with a
-// kTmaBoxX x kTmaBoxY x 1 box.  False when the domain cannot use them: a row of nx elements that
-// is not a multiple of 16 bytes, an operand not 16-byte aligned, or an encoding the driver refuses.
-bool encode_tmaps(const fdtd_ctx* c, const DomainHost& h, CUtensorMap* out) {
-    PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encoder();
-    if (!enc || !kTmaFits) return false;
-    const size_t esz = c->esz;
-    if (((size_t)h.n[0] * esz) % 16 != 0) return false;
-    const void* ptr[kTmaMaps] = {h.F[0], h.F[1], h.F[2], h.F[3], h.F[4], h.F[5], h.ie[0], h.ie[1], h.ie[2]};
-    const cuuint64_t dim[3] = {(cuuint64_t)h.n[0], (cuuint64_t)h.n[1], (cuuint64_t)h.n[2]};
-    const cuuint64_t str[2] = {(cuuint64_t)h.n[0] * esz, (cuuint64_t)h.n[0] * h.n[1] * esz};
-    const cuuint32_t box[3] = {(cuuint32_t)kTmaBoxX, (cuuint32_t)kTmaBoxY, 1u};
-    const cuuint32_t es[3] = {1u, 1u, 1u};
-    for (int b = 0; b < kTmaMaps; ++b) {
-        if (!ptr[b] || ((uintptr_t)ptr[b] & 15u)) return false;
-        const CUresult r = enc(&out[b], esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
-                               const_cast<void*>(ptr[b]), dim, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return false;
-    }
-    return true;
-}
-
-// (Re-)encodes every domain's maps for the current pointers and uploads them.
-fdtd_status sync_tmaps(fdtd_ctx* c) {
-    if (!c->d_tmaps) return FDTD_OK;
-    std::vector<CUtensorMap> maps(c->doms.size() * kTmaMaps);
-    for (size_t di = 0; di < c->doms.size(); ++di) {
-        DomainHost& h = c->doms[di];
-        h.tmaps = (const char*)c->d_tmaps + di * kTmaMaps * sizeof(CUtensorMap);
-        h.tma = encode_tmaps(c, h, &maps[di * kTmaMaps]) ? 1 : 0;
-    }
-    CK(c, cudaMemcpyAsync(c->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
-                          c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
-    return FDTD_OK;
 }
 
 template <typename T>
@@ -518,8 +454,6 @@ fdtd_status sync_doms(fdtd_ctx* c) {
     // any descriptor change (materials, sources, monitors, design) invalidates them
     drop_graphs(c);
     c->stream_dirty = 1;
-    fdtd_status st = sync_tmaps(c);
-    if (st != FDTD_OK) return st;
     return c->dtype == FDTD_F32 ? sync_doms_t<float>(c) : sync_doms_t<double>(c);
 }
 
@@ -879,39 +813,11 @@ void tile_flags(fdtd_ctx* c, Tile& t) {
 
 fdtd_status upload_tiles(fdtd_ctx* c) {
     drop_graphs(c);
-    // work list of the persistent kernel: general tiles first (the slower class), then interior
-    std::vector<Tile> lpt;
-    for (auto& t : c->tiles_gen) {
-        tile_flags(c, t);
-        t.flags |= kTileGeneral;
-        lpt.push_back(t);
-    }
-    for (auto& t : c->tiles_int) {
-        tile_flags(c, t);
-        lpt.push_back(t);
-    }
     CK(c, cudaStreamSynchronize(c->stream));
-    if (!lpt.empty()) {
-        if (c->d_tiles_lpt && c->n_lpt < (int)lpt.size()) {
-            dfree(c, c->d_tiles_lpt);
-            c->d_tiles_lpt = nullptr;
-        }
-        if (!c->d_tiles_lpt) {
-            fdtd_status st = dmalloc(c, (void**)&c->d_tiles_lpt, sizeof(Tile) * lpt.size());
-            if (st != FDTD_OK) return st;
-        }
-        CK(c, cudaMemcpyAsync(c->d_tiles_lpt, lpt.data(), sizeof(Tile) * lpt.size(), cudaMemcpyHostToDevice,
-                              c->stream));
-    }
-    c->n_lpt = (int)lpt.size();
     std::vector<Tile>* lists[3] = {&c->tiles, &c->tiles_gen, &c->tiles_int};
     Tile** dst[3] = {&c->d_tiles, &c->d_tiles_gen, &c->d_tiles_int};
     for (int li = 0; li < 3; ++li) {
-        for (auto& t : *lists[li]) {
-            const int g = t.flags & kTileGeneral;
-            tile_flags(c, t);
-            t.flags |= g;
-        }
+        for (auto& t : *lists[li]) tile_flags(c, t);
         const std::vector<Tile>& up = *lists[li];
         if (up.empty()) continue;
         if (!*dst[li]) {
@@ -1033,8 +939,6 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
     a.d_step = c->d_step;
     a.d_ticket = c->d_ticket;
     a.dft_on = c->dft_enabled;
-    a.dft_items = c->d_dft_items;
-    a.ndft = c->n_dft_items;
     a.d_base = c->d_base;
     a.offset = offset;
     const int ng = (int)c->tiles_gen.size(), ni = (int)c->tiles_int.size();
@@ -1485,8 +1389,6 @@ fdtd_status stream_forward(fdtd_ctx* c, int n_steps) {
     a.d_step = c->d_step;
     a.d_ticket = c->d_ticket;
     a.dft_on = c->dft_enabled;
-    a.dft_items = nullptr;
-    a.ndft = 0;
     a.d_base = c->d_base;
     a.offset = 0;
     // the host state may have been written on the caller's stream (set_part, reset)
@@ -1619,7 +1521,7 @@ AdjCellArgs<T> make_adj_args(const fdtd_ctx* c, int di, int* mon) {
         a.gzg = h.glo[2];
         a.gvol = (long long)(h.ghi[0] - h.glo[0]) * (h.ghi[1] - h.glo[1]) * (h.ghi[2] - h.glo[2]);
     }
-    // bounding box of the monitor cells that carry an adjoint source
+    // bounding box of the monitor cells that carry an adjoint source, and its injection scratch
     *mon = 0;
     for (int mi : h.mons) {
         const Mon& m = c->mons[mi].m;
@@ -1629,6 +1531,10 @@ AdjCellArgs<T> make_adj_args(const fdtd_ctx* c, int di, int* mon) {
             a.mhi[q] = *mon ? std::max(a.mhi[q], m.hi[q]) : m.hi[q];
         }
         *mon = 1;
+    }
+    if (*mon) {
+        a.mvol = (long long)(a.mhi[0] - a.mlo[0]) * (a.mhi[1] - a.mlo[1]) * (a.mhi[2] - a.mlo[2]);
+        a.inj = (const T*)h.inj;
     }
     return a;
 }
@@ -1647,6 +1553,37 @@ AdjBlochArgs<T> make_adj_bloch(const fdtd_ctx* c, int di, const AdjCellArgs<T>& 
     return b;
 }
 
+// Sizes every domain's injection scratch for the box of its monitors that carry adjoint sources
+// (before transposed steps are launched: the launches themselves cannot fail).
+fdtd_status prepare_inj(fdtd_ctx* c) {
+    for (DomainHost& h : c->doms) {
+        bool any = false;
+        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        for (int mi : h.mons) {
+            const Mon& m = c->mons[mi].m;
+            if (!m.cot) continue;
+            for (int q = 0; q < 3; ++q) {
+                lo[q] = any ? std::min(lo[q], m.lo[q]) : m.lo[q];
+                hi[q] = any ? std::max(hi[q], m.hi[q]) : m.hi[q];
+            }
+            any = true;
+        }
+        if (!any) continue;
+        const long long need = 6ll * (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+        if (need <= h.inj_cap) continue;
+        if (h.inj) {
+            CK(c, cudaStreamSynchronize(c->stream));
+            dfree(c, h.inj);
+            h.inj = nullptr;
+            h.inj_cap = 0;
+        }
+        fdtd_status st = dmalloc(c, &h.inj, (size_t)need * c->esz);
+        if (st != FDTD_OK) return st;
+        h.inj_cap = need;
+    }
+    return FDTD_OK;
+}
+
 template <typename T>
 void adj_once(fdtd_ctx* c, int m) {
     const Launch l = L(c);
@@ -1659,6 +1596,12 @@ void adj_once(fdtd_ctx* c, int m) {
         std::vector<AdjCellArgs<T>> args(c->doms.size());
         std::vector<int> mon(c->doms.size(), 0);
         for (int di = 0; di < (int)c->doms.size(); ++di) args[di] = make_adj_args<T>(c, di, &mon[di]);
+        // the E-DFT cotangents of step m and the H-DFT ones of step m - 1 over each monitor box, one
+        // launch per domain; the H-side launches read the second half of the scratch
+        for (int di = 0; di < (int)c->doms.size(); ++di)
+            if (mon[di])
+                launch_inject_box<T>(l, dd + di, c->d_mons, args[di].mlo, args[di].mhi, 2ll * m,
+                                     m >= 1 ? 2ll * (m - 1) + 1 : -1ll, (T*)c->doms[di].inj);
         {
             Prof p(c, FDTD_KERNEL_ADJ_E);
             for (int di = 0; di < (int)c->doms.size(); ++di) {
@@ -1693,6 +1636,8 @@ void adj_once(fdtd_ctx* c, int m) {
                 }
             }
         }
+        for (int di = 0; di < (int)c->doms.size(); ++di)
+            if (mon[di]) args[di].inj += 3 * args[di].mvol;
         {
             Prof p(c, FDTD_KERNEL_ADJ_H);
             for (int di = 0; di < (int)c->doms.size(); ++di) {
@@ -1930,8 +1875,12 @@ fdtd_status stream_adjoint(fdtd_ctx* c, int n_steps) {
             for (int j = kb - 1; j >= 0; --j) {
                 int mon = 0;
                 aa = window_adj_args<T>(c, s2, j, &mon);
+                if (mon)
+                    launch_inject_box<T>(l, (const Dom<T>*)c->d_doms, c->d_mons, aa.mlo, aa.mhi, 2ll * (tb + j),
+                                         tb + j >= 1 ? 2ll * (tb + j - 1) + 1 : -1ll, (T*)h.inj);
                 launch_adj_e_cell<T>(l, aa, ad, c->d_mons, (T)c->S, (int)(tb + j), j < kb - 1 ? 1 : 0, poles, mon, 0,
                                      0);
+                if (mon) aa.inj += 3 * aa.mvol;
                 launch_adj_h_cell<T>(l, aa, ad, c->d_mons, (T)c->S, (int)(tb + j), mon);
             }
             launch_adj_flush_cell<T>(l, aa, ad, (T)c->S, poles, 0);
@@ -2036,18 +1985,6 @@ fdtd_status flush_adjoint(fdtd_ctx* c) {
     return FDTD_OK;
 }
 
-// Reads the sticky error word of the persistent kernel after the stream has drained (the caller
-// synchronised it).  A wait that ran out poisons the context: its state is no longer the
-// result of the requested steps.
-fdtd_status device_error(fdtd_ctx* c) {
-    int err = 0;
-    CK(c, cudaMemcpy(&err, &c->d_sync->err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (!err) return FDTD_OK;
-    c->poisoned = 1;
-    if (err == 1) return fail(c, FDTD_ETIMEOUT, "a grid barrier of the persistent step kernel ran out");
-    return fail(c, FDTD_ETIMEOUT, "a staged plane copy of the persistent step kernel never completed");
-}
-
 fdtd_status set_device_step(fdtd_ctx* c, long long s) {
     c->h_step_tmp = (int)s;
     CK(c, cudaMemcpyAsync(c->d_step, &c->h_step_tmp, sizeof(int), cudaMemcpyHostToDevice, c->stream));
@@ -2145,8 +2082,6 @@ void time_launches_t(fdtd_ctx* c, cudaStream_t st, int which, int n, long long* 
     a.d_step = c->d_step;
     a.d_ticket = c->d_ticket;
     a.dft_on = c->dft_enabled;
-    a.dft_items = c->d_dft_items;
-    a.ndft = c->n_dft_items;
     a.d_base = c->d_base;
     a.offset = 0;
     for (int r = 0; r < n; ++r) {
@@ -2267,16 +2202,7 @@ static fdtd_status create_impl(int32_t n_domains, const fdtd_grid* grids, const 
     e = cudaMalloc((void**)&c->d_base, 64);
     if (e != cudaSuccess) return bail(FDTD_ECUDA);
     c->owned.push_back(c->d_base);
-    e = cudaMalloc((void**)&c->d_sync, sizeof(GridSync));
-    if (e != cudaSuccess) return bail(FDTD_ECUDA);
-    c->owned.push_back(c->d_sync);
     if (cudaMemsetAsync(c->d_ticket, 0, 64, c->stream) != cudaSuccess) return bail(FDTD_ECUDA);
-    {
-        // the only place the sticky error word is cleared
-        GridSync gs0{};
-        gs0.spin_limit = kDefaultSpinLimit;
-        if (cudaMemcpy(c->d_sync, &gs0, sizeof(gs0), cudaMemcpyHostToDevice) != cudaSuccess) return bail(FDTD_ECUDA);
-    }
 
     // domain geometry, pole boxes and the memory plan
     c->doms.resize(n_domains);
@@ -2385,8 +2311,6 @@ static fdtd_status create_impl(int32_t n_domains, const fdtd_grid* grids, const 
     }
     const size_t domb = (c->dtype == FDTD_F32 ? sizeof(Dom<float>) : sizeof(Dom<double>)) * n_domains;
     if (dmalloc(c, &c->d_doms, domb) != FDTD_OK) return bail(FDTD_ENOMEM);
-    if (!streamed && dmalloc(c, &c->d_tmaps, sizeof(CUtensorMap) * kTmaMaps * n_domains) != FDTD_OK)
-        return bail(FDTD_ENOMEM);
     build_tiles(c);
     for (int di = 0; di < n_domains; ++di) {
         const DomainHost& d = c->doms[di];
@@ -2550,8 +2474,6 @@ fdtd_status fdtd_set_tensor(fdtd_ctx* ctx, int32_t domain, const void* const inv
                         " nodes hold a tensor the admission rule rejects (eps below one, not positive definite, or "
                         "inside a CPML face whose normal is no principal axis or has the intermediate eigenvalue)");
     ctx->cell_mode = 1;
-    ctx->use_persistent = 0;
-    ctx->persist_variant = 0;
     d.tensor = 1;
     return FDTD_OK;
 }
@@ -2737,10 +2659,7 @@ fdtd_status fdtd_dft_read(fdtd_ctx* ctx, int32_t monitor_id, void* dst, size_t b
     const Mon& m = ctx->mons[monitor_id].m;
     CK(ctx, cudaMemcpyAsync(dst, m.acc, (size_t)n * 16, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                             ctx->stream));
-    if (!dst_on_device) {
-        CK(ctx, cudaStreamSynchronize(ctx->stream));
-        return device_error(ctx);
-    }
+    if (!dst_on_device) CK(ctx, cudaStreamSynchronize(ctx->stream));
     return FDTD_OK;
 }
 
@@ -2806,37 +2725,6 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
         return FDTD_OK;
     }
     int left = n_steps;
-    if (ctx->use_persistent && n_steps > 0) {
-        StepArgs a;
-        a.srcs = ctx->d_srcs;
-        a.mons = ctx->d_mons;
-        a.d_step = ctx->d_step;
-        a.d_ticket = ctx->d_ticket;
-        a.dft_on = ctx->dft_enabled;
-        a.dft_items = ctx->d_dft_items;
-        a.ndft = ctx->n_dft_items;
-        a.d_base = nullptr;   // the persistent kernel counts its steps itself
-        a.offset = 0;
-        const int nt = ctx->n_lpt;
-        const Launch l{ctx->stream, &ctx->launches};
-        while (left > 0) {
-            const int chunk = left > 512 ? 512 : left;
-            cudaError_t e;
-            {
-                Prof p(ctx, FDTD_KERNEL_PERSISTENT);
-                if (ctx->dtype == FDTD_F32)
-                    e = launch_steps<float>(l, (const Dom<float>*)ctx->d_doms, ctx->d_tiles_lpt, nt, (float)ctx->S, a,
-                                            chunk, ctx->aniso, ctx->energy_on, ctx->persist_variant, ctx->d_sync,
-                                            &ctx->persist_grid);
-                else
-                    e = launch_steps<double>(l, (const Dom<double>*)ctx->d_doms, ctx->d_tiles_lpt, nt, ctx->S, a, chunk,
-                                             ctx->aniso, ctx->energy_on, ctx->persist_variant, ctx->d_sync,
-                                             &ctx->persist_grid);
-            }
-            if (e != cudaSuccess) return fail(ctx, FDTD_ECUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
-            left -= chunk;
-        }
-    }
     if (ctx->use_graphs && !ctx->prof_on && left >= kGraphSteps) {
         fdtd_status st = build_graph(ctx);
         if (st != FDTD_OK) return st;
@@ -2972,14 +2860,12 @@ fdtd_status fdtd_step_backward(fdtd_ctx* ctx, int32_t n_steps) {
 fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode) {
     GUARD(ctx);
     if (ctx->streamed && mode != 4) return fail(ctx, FDTD_EINVAL, "a host-streamed context steps per cell (mode 4)");
-    if (mode < 0 || mode >= FDTD_LAUNCH_MODES) return fail(ctx, FDTD_EINVAL, "launch mode must be in [0, 4]");
+    if (mode != 0 && mode != 4) return fail(ctx, FDTD_EINVAL, "launch mode must be 0 or 4");
     if (mode != 4 && any_bloch(ctx)) return fail(ctx, FDTD_EINVAL, "Bloch domains step in launch mode 4");
     if (mode != 4 && any_tensor(ctx)) return fail(ctx, FDTD_EINVAL, "tensor domains step in launch mode 4");
     for (const auto& d : ctx->doms)
         if (mode != 4 && d.rec) return fail(ctx, FDTD_EINVAL, "an interface record runs in launch mode 4");
     if (mode != ctx->cell_mode * 4) drop_graphs(ctx);   // graphs hold the launches of one mode
-    ctx->use_persistent = mode >= 1 && mode <= 3;
-    ctx->persist_variant = ctx->use_persistent ? mode - 1 : 0;
     ctx->cell_mode = mode == 4;
     return FDTD_OK;
 }
@@ -2987,12 +2873,12 @@ fdtd_status fdtd_set_launch_mode(fdtd_ctx* ctx, int32_t mode) {
 fdtd_status fdtd_get_launch_mode(fdtd_ctx* ctx, int32_t* mode) {
     GUARD(ctx);
     if (!mode) return FDTD_EINVAL;
-    *mode = ctx->cell_mode ? 4 : (ctx->use_persistent ? 1 + ctx->persist_variant : 0);
+    *mode = ctx->cell_mode ? 4 : 0;
     return FDTD_OK;
 }
 
-// Times every launch mode for n_steps on the live state (saved to a private snapshot first and
-// restored after each trial, DFT accumulation off) and keeps the fastest.
+// Times launch modes 0 and 4 for n_steps on the live state (saved to a private snapshot first and
+// restored after each trial) and keeps the faster.
 static fdtd_status save_slot(fdtd_ctx* ctx, int32_t slot, int32_t codec);
 static fdtd_status restore_slot(fdtd_ctx* ctx, int32_t slot);
 
@@ -3008,7 +2894,9 @@ fdtd_status fdtd_autotune(fdtd_ctx* ctx, int32_t n_steps, double* ms_per_mode) {
     ctx->energy_on = 0;
     fdtd_status st = FDTD_OK;
     double best = 1e30;
-    int best_mode = 1;
+    int best_mode = 4;
+    if (ms_per_mode)
+        for (int q = 0; q < FDTD_LAUNCH_MODES; ++q) ms_per_mode[q] = -1.0;
     // the trials run with DFT recording as configured (its cost shapes the ranking); the monitor
     // accumulators are copied aside first and put back after every trial
     std::vector<std::pair<void*, size_t>> saved;
@@ -3031,9 +2919,10 @@ fdtd_status fdtd_autotune(fdtd_ctx* ctx, int32_t n_steps, double* ms_per_mode) {
     if (st == FDTD_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = fail(ctx, FDTD_ECUDA, "cudaEventCreate failed");
     if (st == FDTD_OK) st = save_slot(ctx, slot, FDTD_CODEC_NATIVE);
-    for (int mode = 0; mode < FDTD_LAUNCH_MODES && st == FDTD_OK; ++mode) {
+    for (int mode : {0, 4}) {
+        if (st != FDTD_OK) break;
         fdtd_set_launch_mode(ctx, mode);
-        // warm-up: graph capture, first-touch of the persistent kernel, caches
+        // warm-up: graph capture, caches
         st = fdtd_step_forward(ctx, n_steps < kGraphSteps ? n_steps : kGraphSteps);
         if (st == FDTD_OK) st = restore_slot(ctx, slot);
         if (st != FDTD_OK) break;
@@ -3441,6 +3330,8 @@ fdtd_status fdtd_step_adjoint(fdtd_ctx* ctx, int32_t n_steps) {
             st = sync_mons(ctx);
             if (st != FDTD_OK) return st;
         }
+        fdtd_status st = prepare_inj(ctx);
+        if (st != FDTD_OK) return st;
         return ctx->dtype == FDTD_F32 ? stream_adjoint<float>(ctx, n_steps) : stream_adjoint<double>(ctx, n_steps);
     }
     bool design = false;
@@ -3457,6 +3348,10 @@ fdtd_status fdtd_step_adjoint(fdtd_ctx* ctx, int32_t n_steps) {
             st = sync_mons(ctx);
             if (st != FDTD_OK) return st;
         }
+    }
+    {
+        fdtd_status st = prepare_inj(ctx);
+        if (st != FDTD_OK) return st;
     }
     for (int s = 0; s < n_steps; ++s) {
         const int m = (int)ctx->adj_step - 1;
@@ -3526,8 +3421,6 @@ fdtd_status fdtd_check_finite(fdtd_ctx* ctx) {
     unsigned long long bad = 0;
     CK(ctx, cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    fdtd_status st = device_error(ctx);
-    if (st != FDTD_OK) return st;
     if (bad) return fail(ctx, FDTD_ENONFINITE, "non-finite values in the forward state");
     return FDTD_OK;
 }
@@ -3537,23 +3430,12 @@ fdtd_status fdtd_synchronize(fdtd_ctx* ctx, int32_t timeout_ms) {
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaStreamQuery(ctx->stream);
-        if (e == cudaSuccess) return device_error(ctx);
+        if (e == cudaSuccess) return FDTD_OK;
         if (e != cudaErrorNotReady) return fail(ctx, FDTD_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
         const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
         if (ms.count() >= timeout_ms) return fail(ctx, FDTD_ETIMEOUT, "stream not finished within the timeout");
         std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
-}
-
-fdtd_status fdtd_set_wait_limit(fdtd_ctx* ctx, int64_t polls, int32_t extra_arrivals) {
-    GUARD(ctx);
-    if (polls < 1 || extra_arrivals < 0 || extra_arrivals > 1) return fail(ctx, FDTD_EINVAL, "bad wait limit");
-    const long long lim = polls;
-    const int extra = extra_arrivals;
-    CK(ctx, cudaStreamSynchronize(ctx->stream));   // no launch in flight reads the words being changed
-    CK(ctx, cudaMemcpy(&ctx->d_sync->spin_limit, &lim, sizeof(lim), cudaMemcpyHostToDevice));
-    CK(ctx, cudaMemcpy(&ctx->d_sync->extra, &extra, sizeof(extra), cudaMemcpyHostToDevice));
-    return FDTD_OK;
 }
 
 fdtd_status fdtd_launch_count(fdtd_ctx* ctx, int64_t* n) {
@@ -3568,11 +3450,15 @@ fdtd_status fdtd_time_half_steps(fdtd_ctx* ctx, int32_t which, int32_t n_launche
     if (!ms_per_launch || which < 0 || which > 4 || n_launches < 1 || n_launches > 4096)
         return fail(ctx, FDTD_EINVAL, "bad arguments");
     *ms_per_launch = 0.0;
-    if (!ctx->cell_mode || ctx->energy_on || ctx->use_persistent)
+    if (!ctx->cell_mode || ctx->energy_on)
         return fail(ctx, FDTD_EINVAL, "per-cell launch mode (4) without an energy record only");
     NOT_BLOCH(ctx, "kernel timing");
     NOT_TENSOR(ctx, "kernel timing");
     if (which == 2 && ctx->n_dft_items == 0) return fail(ctx, FDTD_EINVAL, "no DFT monitor");
+    if (which >= 3) {
+        fdtd_status st = prepare_inj(ctx);   // the transposed kernels read the injection scratch
+        if (st != FDTD_OK) return st;
+    }
     if (!ctx->cap_stream) CK(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     launch_copy_int(L(ctx), ctx->d_step, ctx->d_base);   // phases / sources of the current step

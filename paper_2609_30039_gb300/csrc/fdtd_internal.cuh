@@ -29,15 +29,6 @@ constexpr int kTileY = 8;
 #endif
 constexpr int kIntX = GBFDTD_INT_X;
 constexpr int kIntY = kTileX * kTileY / kIntX;
-// Plane box of the TMA-staged interior tiles: one array, one z-plane, kTmaBoxX x kTmaBoxY
-// elements.  x starts at the tile's first column minus one, rounded down to a 16-byte
-// boundary (at most 4 elements earlier), so kIntX + 4 columns cover the tile, its -1 / +1 halo
-// and the round-down; kIntY + 1 rows cover the tile and its -1 (E update) or +1 (H update) halo
-// row.  A box row is at most 256 elements, so the widest interior tiles cannot be staged.
-constexpr int kTmaBoxX = kIntX + 4;
-constexpr int kTmaBoxY = kIntY + 1;
-constexpr bool kTmaFits = kTmaBoxX <= 256;
-constexpr int kTmaMaps = 9;   // Ex Ey Ez Hx Hy Hz, eps^-1 x y z
 
 template <typename T>
 struct Dom {
@@ -72,8 +63,6 @@ struct Dom {
     int src[kMaxSrcPerDom];
     double* energy;            // per-step energy or nullptr
     int energy_cap;
-    const void* tmaps;         // kTmaMaps CUtensorMap (device memory) or nullptr
-    int tma;                   // 1 if the maps are valid (the TMA-staged interior path may run)
 };
 
 // A running DFT monitor (Sec. 2.4).  acc / cot: [ncomp][nf][ncell] double2.
@@ -119,22 +108,9 @@ enum : int {
     kTileSrcH = 2,   // ... of a magnetic soft source
     kTileMonE = 4,   // holds a cell of a monitor recording an E component (objective injection)
     kTileMonH = 8,   // ... an H component
-    kTileGeneral = 16 // needs the CPML / PEC / pole code path
+    kTileGeneral = 16 // needs the CPML / PEC / pole code path (the transposed tile kernels)
 };
 
-// State of the grid-wide barrier and tile ticket of the persistent step kernel.  arrive, gen and
-// ticket are cleared before every launch; err is sticky: it is cleared only when the context is
-// created, so an error of one launch stops every later launch at its first instruction and stays
-// visible until the host reads it.
-struct GridSync {
-    unsigned arrive;
-    unsigned gen;
-    int err;                  // 1: a barrier wait ran out; 2: a staged plane copy never completed
-    int extra;                // added to the arrivals a barrier waits for (0; a test hook, see fdtd.h)
-    unsigned long long ticket;
-    long long spin_limit;     // polls (~64 ns each) a barrier wait may take before it gives up
-};
-constexpr long long kDefaultSpinLimit = 1ll << 26;   // a few seconds
 // Columns of a tile: lane tx maps to x in [xs[0], xs[1]) then [xs[2], xs[3]) (two segments let
 // one warp cover both opposite CPML slabs), thread row ty to y likewise with ys; at most
 // kTileX x kTileY columns.  z runs over [z0, z1).
@@ -242,8 +218,6 @@ struct StepArgs {
     int* d_step;
     unsigned* d_ticket;
     int dft_on;
-    const DftItem* dft_items;   // DFT work items of every monitor (persistent kernel)
-    int ndft;
     const int* d_base;          // per-cell mode: first step of the launched batch ...
     int offset;                 // ... and this step's position in it (step = *d_base + offset)
 };
@@ -348,6 +322,10 @@ struct AdjCellArgs {
     // tensor domain (Sec. 2.3 node assembly): the E cotangent Ebar (the E array then carries the
     // curl cotangent S S_t Ebar between the E and H launches), else nullptr
     T* Eb[3];
+    // objective injection over the monitor box [mlo, mhi) (global coordinates): [3][mvol] values of
+    // this half-step's components (launch_inject_box), or nullptr without monitors
+    const T* inj;
+    long long mvol;
 };
 
 // Operands of the node-assembled tensor operator S_t = D^{-1/2} (1/8 sum R^T eps^-1 R) D^{-1/2}
@@ -428,11 +406,6 @@ void launch_tensor_admission(const Launch& L, const TensorArgs<T>& t, const int*
 template <typename T>
 void launch_back_cell(const Launch& L, const CellArgs<T>& ce, const CellArgs<T>& ch, T S, const StepArgs& a,
                       int aniso);
-// Persistent cooperative launch advancing nsteps forward steps over all tiles (general first).
-// variant: 0 register path, 1 one-plane register prefetch, 2 TMA-staged interior tiles.
-template <typename T>
-cudaError_t launch_steps(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
-                         int nsteps, int aniso, int energy, int variant, GridSync* gs, int* grid_used);
 
 // Adjoint kernels (kernels_adj.cu)
 template <typename T>
@@ -463,6 +436,14 @@ void launch_adj_flush_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T
 template <typename T>
 void launch_inject(const Launch& L, const Dom<T>* doms, const Mon* mons, const int* entries, int nentries,
                    long long nthreads, const long long* entry_begin, int step, int kind);
+// The objective injection of one transposed step m for every cell of the box [lo, hi) of the
+// domain *dom: inj[c][box cell, x fastest] = dJ/df of component c, for the E components (c < 3)
+// at phase index pidx_e = 2 m (the E-DFT of step m) and for the H components (c >= 3) at pidx_h =
+// 2 (m - 1) + 1 (the H-DFT of step m - 1; skipped for pidx_h < 0), summed over the domain's
+// monitors in FP64 and rounded to T once, as the per-cell transposed kernels add it.
+template <typename T>
+void launch_inject_box(const Launch& L, const Dom<T>* dom, const Mon* mons, const int* lo, const int* hi,
+                       long long pidx_e, long long pidx_h, T* inj);
 
 // Auxiliary kernels (kernels_aux.cu)
 // Flux through the H plane of a two-plane monitor; slots: accumulator slots of Ex, Ey, Hx, Hy.

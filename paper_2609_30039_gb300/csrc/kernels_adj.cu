@@ -627,6 +627,20 @@ __global__ void k_inject(const Dom<T>* __restrict__ doms, const Mon* __restrict_
     d.A[m.comps[ci]][cidx(d.n, i, j, k)] += (T)acc;
 }
 
+// Injection values of one half-step over a box of cells (see launch_inject_box): the sum over the
+// domain's monitors of inject_at, rounded to T once, exactly the value the per-cell kernels add.
+template <typename T>
+__global__ void k_inject_box(const Dom<T>* __restrict__ dom, const Mon* __restrict__ mons, int3 lo, int3 hi,
+                             long long pidx_e, long long pidx_h, T* __restrict__ inj) {
+    const long long bx = hi.x - lo.x, by = hi.y - lo.y, vol = bx * by * (hi.z - lo.z);
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= vol) return;
+    const int i = lo.x + (int)(t % bx), j = lo.y + (int)((t / bx) % by), k = lo.z + (int)(t / (bx * by));
+    for (int c = 0; c < 3; ++c) inj[c * vol + t] = (T)inject_at(*dom, mons, c, i, j, k, pidx_e);
+    if (pidx_h >= 0)
+        for (int c = 3; c < 6; ++c) inj[c * vol + t] = (T)inject_at(*dom, mons, c, i, j, k, pidx_h);
+}
+
 // ---- per-cell transposed kernels -------------------------------------------------------------------
 // One thread per cell over the forward per-cell grid (x chunks of 32, y chunks of 8, z planes), so a
 // warp reads 128 contiguous bytes per array and every load of a thread is independent (the -1 / +1
@@ -665,6 +679,11 @@ __device__ __forceinline__ T dbar_node(const T* coef, int N, const T* psi, const
 
 __device__ __forceinline__ bool in_box3(const int* lo, const int* hi, int i, int j, int k) {
     return i >= lo[0] && i < hi[0] && j >= lo[1] && j < hi[1] && k >= lo[2] && k < hi[2];
+}
+
+// Offset of cell (i, j, k) inside the box [lo, hi), x fastest.
+__device__ __forceinline__ long long box_cell(const int* lo, const int* hi, int i, int j, int k) {
+    return ((long long)(k - lo[2]) * (hi[1] - lo[1]) + (j - lo[1])) * (hi[0] - lo[0]) + (i - lo[0]);
 }
 
 // 1 / x: a correctly rounded reciprocal in FP32 (a multiply by it replaces the IEEE division of
@@ -723,8 +742,7 @@ __device__ __forceinline__ T adj_e_comp(const AdjCellArgs<T>& c, const Dom<T>* _
         eb = F;
     }
     eb += gat;
-    if (kMon && in_box3(c.mlo, c.mhi, i, j, k + c.kz0))
-        eb += (T)inject_at(doms[c.dom], mons, a, i, j, k + c.kz0, (long long)m * 2 + 0);
+    if (kMon && in_box3(c.mlo, c.mhi, i, j, k + c.kz0)) eb += c.inj[a * c.mvol + box_cell(c.mlo, c.mhi, i, j, k + c.kz0)];
     T et = eb, gdisp = T(0);
     if (kPoles && disp) {
         const Dom<T>& d = doms[c.dom];
@@ -919,7 +937,7 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
 }
 
 template <typename T, bool kPoles, bool kGrad, bool kMon, bool kPG, bool kTen = false>
-__global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, kPoles || kGrad || kMon>())
+__global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, kPoles || kGrad>())
     k_adj_e_cell(const AdjCellArgs<T> c, const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, T S, int m,
                  int pending) {
     if (!kPG) {
@@ -983,10 +1001,10 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
         T h1 = b1 + (fz - fz_xp) + (fx_zp - fx);
         T h2 = b2 + (fx - fx_yp) + (fy_xp - fy);
         if (kMon && m >= 1 && in_box3(c.mlo, c.mhi, i, j, kg)) {
-            const Dom<T>& d = doms[c.dom];
-            h0 += (T)inject_at(d, mons, 3, i, j, kg, (long long)(m - 1) * 2 + 1);
-            h1 += (T)inject_at(d, mons, 4, i, j, kg, (long long)(m - 1) * 2 + 1);
-            h2 += (T)inject_at(d, mons, 5, i, j, kg, (long long)(m - 1) * 2 + 1);
+            const long long bo = box_cell(c.mlo, c.mhi, i, j, kg);
+            h0 += c.inj[bo];
+            h1 += c.inj[c.mvol + bo];
+            h2 += c.inj[2 * c.mvol + bo];
         }
         B0[ij] = h0;
         B1[ij] = h1;
@@ -1068,10 +1086,10 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
         c.apsiH[2][0][o] = b * (c.apsiH[2][0][o] - S * b2);
     }
     if (kMon && m >= 1 && in_box3(c.mlo, c.mhi, i, j, kg)) {
-        const Dom<T>& d = doms[c.dom];
-        h0 += (T)inject_at(d, mons, 3, i, j, kg, (long long)(m - 1) * 2 + 1);
-        h1 += (T)inject_at(d, mons, 4, i, j, kg, (long long)(m - 1) * 2 + 1);
-        h2 += (T)inject_at(d, mons, 5, i, j, kg, (long long)(m - 1) * 2 + 1);
+        const long long bo = box_cell(c.mlo, c.mhi, i, j, kg);
+        h0 += c.inj[bo];
+        h1 += c.inj[c.mvol + bo];
+        h2 += c.inj[2 * c.mvol + bo];
     }
     B0[ij] = h0;
     B1[ij] = h1;
@@ -1230,6 +1248,18 @@ void launch_adj_flush(const Launch& L, const Dom<T>* doms, const Tile* tiles, in
 }
 
 template <typename T>
+void launch_inject_box(const Launch& L, const Dom<T>* dom, const Mon* mons, const int* lo, const int* hi,
+                       long long pidx_e, long long pidx_h, T* inj) {
+    const long long vol = (long long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+    if (vol <= 0) return;
+    const int bs = 256;
+    k_inject_box<T><<<(unsigned)((vol + bs - 1) / bs), bs, 0, L.stream>>>(dom, mons, make_int3(lo[0], lo[1], lo[2]),
+                                                                           make_int3(hi[0], hi[1], hi[2]), pidx_e,
+                                                                           pidx_h, inj);
+    ++*L.counter;
+}
+
+template <typename T>
 void launch_inject(const Launch& L, const Dom<T>* doms, const Mon* mons, const int* entries, int nentries,
                    long long nthreads, const long long* entry_begin, int step, int kind) {
     if (nentries <= 0 || nthreads <= 0) return;
@@ -1246,6 +1276,8 @@ void launch_inject(const Launch& L, const Dom<T>* doms, const Mon* mons, const i
     template void launch_adj_flush<T>(const Launch&, const Dom<T>*, const Tile*, int, T);                       \
     template void launch_inject<T>(const Launch&, const Dom<T>*, const Mon*, const int*, int, long long,        \
                                    const long long*, int, int);                                                 \
+    template void launch_inject_box<T>(const Launch&, const Dom<T>*, const Mon*, const int*, const int*,         \
+                                       long long, long long, T*);                                               \
     template void launch_adj_e_cell<T>(const Launch&, const AdjCellArgs<T>&, const Dom<T>*, const Mon*, T, int,  \
                                        int, int, int, int, int);                                                \
     template void launch_adj_h_cell<T>(const Launch&, const AdjCellArgs<T>&, const Dom<T>*, const Mon*, T, int,  \

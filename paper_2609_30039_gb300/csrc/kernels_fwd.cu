@@ -9,7 +9,6 @@
 // flags mark the tiles that hold source or monitor cells), so a forward step is two kernels per
 // tile class and a CUDA graph of them replays without host work.
 #include "fdtd_internal.cuh"
-#include "tma_ptx.cuh"
 
 namespace gbfdtd {
 
@@ -157,162 +156,9 @@ constexpr int min_blocks(bool general) {
     return general ? (sizeof(T) == 4 ? 4 : 2) : (sizeof(T) == 4 ? GBFDTD_INT_BLOCKS_F32 : 4);
 }
 
-#ifndef GBFDTD_TMA_STAGES_F32
-#define GBFDTD_TMA_STAGES_F32 4
-#endif
-#ifndef GBFDTD_TMA_BLOCKS_F32
-#define GBFDTD_TMA_BLOCKS_F32 4
-#endif
-// the persistent kernel holds both code paths; the prefetch variant (1) needs more registers,
-// the TMA variant (2) ~51 KB (FP32) / ~71 KB (FP64) of shared memory per block
-template <typename T, int kVar>
-constexpr int min_blocks_persistent() {
-    return sizeof(T) == 4 ? (kVar == 1 ? 3 : (kVar == 2 ? GBFDTD_TMA_BLOCKS_F32 : 4)) : 2;
-}
-
 // E half-step (Eq. (yee) first half) of a tile.  kGen = false: the tile touches no CPML slab,
 // PEC plane, domain edge or dispersive cell, so none of that code is compiled in.  Every load of
 // a plane is issued before any store of it; H_x, H_y of plane k-1 stay in registers.
-// Interior E tile with a one-plane software pipeline: the operands of plane k+1 are loaded
-// before plane k is computed and stored, so every thread keeps two planes of loads in flight.
-template <typename T, bool kAniso>
-__device__ __forceinline__ void tile_e_int(const Dom<T>* __restrict__ doms, const Tile& t, T S, const StepArgs& a,
-                                           int step) {
-    const Dom<T>& d = doms[t.dom];
-    const int nx = d.n[0], ny = d.n[1];
-    int i, j;
-    tile_coords(t, i, j);
-    if (i < 0 || j < 0) return;
-    const bool fsrc = t.flags & kTileSrcE;
-    const long long nxy = (long long)nx * ny;
-    T* Ex = d.F[0];
-    T* Ey = d.F[1];
-    T* Ez = d.F[2];
-    const T* Hx = d.F[3];
-    const T* Hy = d.F[4];
-    const T* Hz = d.F[5];
-    const T* ie0 = d.ie[0];
-    const T* ie1 = d.ie[1];
-    const T* ie2 = d.ie[2];
-    long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
-    T hxz = Hx[id - nxy], hyz = Hy[id - nxy];
-    // operands of the current plane
-    T hx = Hx[id], hy = Hy[id], hz = Hz[id];
-    T hz_ym = Hz[id - nx], hx_ym = Hx[id - nx], hz_xm = Hz[id - 1], hy_xm = Hy[id - 1];
-    T ex = Ex[id], ey = Ey[id], ez = Ez[id];
-    T iex = ie0[id], iey = kAniso ? ie1[id] : iex, iez = kAniso ? ie2[id] : iex;
-    for (int k = t.z0; k < t.z1; ++k, id += nxy) {
-        // prefetch plane k+1 (the tile never ends at the domain's last plane)
-        const long long nid = id + nxy;
-        const bool more = k + 1 < t.z1;
-        T nhx = T(0), nhy = T(0), nhz = T(0), nhz_ym = T(0), nhx_ym = T(0), nhz_xm = T(0), nhy_xm = T(0);
-        T nex = T(0), ney = T(0), nez = T(0), niex = T(0), niey = T(0), niez = T(0);
-        if (more) {
-            nhx = Hx[nid];
-            nhy = Hy[nid];
-            nhz = Hz[nid];
-            nhz_ym = Hz[nid - nx];
-            nhx_ym = Hx[nid - nx];
-            nhz_xm = Hz[nid - 1];
-            nhy_xm = Hy[nid - 1];
-            nex = Ex[nid];
-            ney = Ey[nid];
-            nez = Ez[nid];
-            niex = ie0[nid];
-            niey = kAniso ? ie1[nid] : niex;
-            niez = kAniso ? ie2[nid] : niex;
-        }
-        ex = fma_t(S * iex, ((hz - hz_ym) - (hy - hyz)), ex);
-        ey = fma_t(S * iey, ((hx - hxz) - (hz - hz_xm)), ey);
-        ez = fma_t(S * iez, ((hy - hy_xm) - (hx - hx_ym)), ez);
-        if (fsrc) {
-            ex += src_add(d, a.srcs, 0, i, j, k, step);
-            ey += src_add(d, a.srcs, 1, i, j, k, step);
-            ez += src_add(d, a.srcs, 2, i, j, k, step);
-        }
-        Ex[id] = ex;
-        Ey[id] = ey;
-        Ez[id] = ez;
-        hxz = hx;
-        hyz = hy;
-        hx = nhx; hy = nhy; hz = nhz;
-        hz_ym = nhz_ym; hx_ym = nhx_ym; hz_xm = nhz_xm; hy_xm = nhy_xm;
-        ex = nex; ey = ney; ez = nez;
-        iex = niex; iey = niey; iez = niez;
-    }
-}
-
-// Interior H tile with the same one-plane pipeline (E_x, E_y of plane k+1 are operands of
-// plane k and are carried).
-template <typename T, bool kEnergy>
-__device__ __forceinline__ void tile_h_int(const Dom<T>* __restrict__ doms, const Tile& t, T S, const StepArgs& a,
-                                           int step) {
-    const Dom<T>& d = doms[t.dom];
-    const int nx = d.n[0], ny = d.n[1];
-    int i, j;
-    tile_coords(t, i, j);
-    const bool fsrc = t.flags & kTileSrcH;
-    double w = 0.0;
-    if (i >= 0 && j >= 0) {
-        const long long nxy = (long long)nx * ny;
-        const T* Ex = d.F[0];
-        const T* Ey = d.F[1];
-        const T* Ez = d.F[2];
-        T* Hx = d.F[3];
-        T* Hy = d.F[4];
-        T* Hz = d.F[5];
-        long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
-        T exk = Ex[id], eyk = Ey[id];
-        T exn = Ex[id + nxy], eyn = Ey[id + nxy];
-        T ez = Ez[id], ez_yp = Ez[id + nx], ez_xp = Ez[id + 1], ey_xp = Ey[id + 1], ex_yp = Ex[id + nx];
-        T hx = Hx[id], hy = Hy[id], hz = Hz[id];
-        for (int k = t.z0; k < t.z1; ++k, id += nxy) {
-            const long long nid = id + nxy;
-            const bool more = k + 1 < t.z1;
-            T nexn = T(0), neyn = T(0), nez = T(0), nez_yp = T(0), nez_xp = T(0), ney_xp = T(0), nex_yp = T(0);
-            T nhx = T(0), nhy = T(0), nhz = T(0);
-            if (more) {
-                nexn = Ex[nid + nxy];
-                neyn = Ey[nid + nxy];
-                nez = Ez[nid];
-                nez_yp = Ez[nid + nx];
-                nez_xp = Ez[nid + 1];
-                ney_xp = Ey[nid + 1];
-                nex_yp = Ex[nid + nx];
-                nhx = Hx[nid];
-                nhy = Hy[nid];
-                nhz = Hz[nid];
-            }
-            T hx1 = fma_t(-S, ((ez_yp - ez) - (eyn - eyk)), hx);
-            T hy1 = fma_t(-S, ((exn - exk) - (ez_xp - ez)), hy);
-            T hz1 = fma_t(-S, ((ey_xp - eyk) - (ex_yp - exk)), hz);
-            if (fsrc) {
-                hx1 += src_add(d, a.srcs, 3, i, j, k, step);
-                hy1 += src_add(d, a.srcs, 4, i, j, k, step);
-                hz1 += src_add(d, a.srcs, 5, i, j, k, step);
-            }
-            Hx[id] = hx1;
-            Hy[id] = hy1;
-            Hz[id] = hz1;
-            if (kEnergy) {
-                w += 0.5 * ((double)hx * hx1 + (double)hy * hy1 + (double)hz * hz1);
-                w += 0.5 * ((double)exk * exk / (double)d.ie[0][id] + (double)eyk * eyk / (double)d.ie[1][id] +
-                            (double)ez * ez / (double)d.ie[2][id]);
-            }
-            exk = exn;
-            eyk = eyn;
-            exn = nexn;
-            eyn = neyn;
-            ez = nez; ez_yp = nez_yp; ez_xp = nez_xp; ey_xp = ney_xp; ex_yp = nex_yp;
-            hx = nhx; hy = nhy; hz = nhz;
-        }
-    }
-    if (kEnergy) {
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        if ((threadIdx.x & 31) == 0 && d.energy && step < d.energy_cap) atomicAdd(d.energy + step, w);
-    }
-}
-
 template <typename T, bool kGen, bool kAniso>
 __device__ __forceinline__ void tile_e(const Dom<T>* __restrict__ doms, const Tile& t, T S, const StepArgs& a,
                                        int step) {
@@ -879,382 +725,6 @@ void launch_h_cell(const Launch& L, const CellArgs<T>& c, T S, const StepArgs& a
     ++*L.counter;
 }
 
-// ---- TMA-staged interior tiles ---------------------------------------------------------------
-// One elected thread copies every operand array of a z-plane of the tile (a kTmaBoxX x kTmaBoxY
-// box per array, see fdtd_internal.cuh) into a ring of kStages shared-memory stages with tiled
-// bulk tensor copies; each stage completes on its own mbarrier.  While the block computes plane
-// k, planes k+1 .. k+kStages-1 are in flight, so the memory-level parallelism no longer depends
-// on registers or on the number of resident warps.  A stage is refilled only after a block
-// barrier has shown that every thread is done with it.  `seq` counts the planes this block has
-// staged so far: stage = seq % kStages and the mbarrier phase parity = (seq / kStages) & 1.
-template <typename T>
-constexpr int tma_stages() {
-    return sizeof(T) == 4 ? GBFDTD_TMA_STAGES_F32 : 3;
-}
-template <typename T>
-constexpr int tma_box_bytes() {
-    return kTmaBoxX * kTmaBoxY * (int)sizeof(T);
-}
-template <typename T>
-constexpr int tma_slot_elems() {   // one box slot, padded to 128 bytes
-    return ((tma_box_bytes<T>() + 127) / 128 * 128) / (int)sizeof(T);
-}
-template <typename T>
-constexpr int tma_smem_bytes() {   // stages, their mbarriers, and the alignment slack
-    return tma_stages<T>() * kTmaMaps * tma_slot_elems<T>() * (int)sizeof(T) + 8 * tma_stages<T>() + 128;
-}
-
-struct TmaRing {
-    unsigned smem;   // shared address of stage 0, slot 0
-    unsigned bar0;   // shared address of the first mbarrier (8 bytes each)
-    unsigned seq;    // planes staged so far by this block
-};
-
-// Copies plane z of `nbox` arrays (maps 0 .. nbox-1) into the stage of sequence number g.
-template <typename T>
-__device__ __forceinline__ void tma_issue_plane(const TmaRing& r, const void* maps, int nbox, unsigned g, int x, int y,
-                                                int z) {
-    constexpr int NS = tma_stages<T>();
-    const unsigned s = g % NS;
-    const unsigned bar = r.bar0 + 8u * s;
-    const unsigned base = r.smem + s * (unsigned)(kTmaMaps * tma_slot_elems<T>() * sizeof(T));
-    mbar_arrive_expect(bar, (unsigned)(nbox * tma_box_bytes<T>()));
-    const char* m = (const char*)maps;
-    for (int b = 0; b < nbox; ++b)
-        tma_load_3d(base + (unsigned)(b * tma_slot_elems<T>() * sizeof(T)), m + 128 * b, x, y, z, bar);
-}
-
-// After a wait ran out: give the copies issued but not yet seen complete (sequence numbers
-// [from, to)) a bounded chance to land before the block leaves.
-template <typename T>
-__device__ __forceinline__ void tma_drain(const TmaRing& r, unsigned from, unsigned to) {
-    constexpr int NS = tma_stages<T>();
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        for (unsigned g = from; g < to; ++g) mbar_wait(r.bar0 + 8u * (g % NS), (g / NS) & 1u);
-    __syncthreads();
-}
-
-// E half-step of an interior tile with staged planes.  Box origin (bx, y0 - 1, k): the thread of
-// column (i, j) = (x0 + tx, y0 + ty) finds its cell at box row ty + 1, column i - bx, and the
-// -x / -y neighbours one element / one row before it.  Returns false if a stage never completed.
-template <typename T, bool kAniso>
-__device__ __forceinline__ bool tile_e_tma(const Dom<T>& d, const Tile& t, T S, const StepArgs& a, int step,
-                                           TmaRing& r) {
-    constexpr int NS = tma_stages<T>();
-    constexpr int P = tma_slot_elems<T>();
-    const int nx = d.n[0], ny = d.n[1];
-    const int tid = threadIdx.y * kTileX + threadIdx.x;
-    const int tx = tid % kIntX, ty = tid / kIntX;   // interior tiles are kIntX x kIntY columns
-    const int i = t.xs[0] + tx, j = t.ys[0] + ty;
-    const bool act = i < t.xs[1] && j < t.ys[1];
-    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
-    const int bx = (t.xs[0] - 1) & ~3, by = t.ys[0] - 1;
-    const int np = t.z1 - t.z0;
-    const int nbox = kAniso ? 9 : 7;
-    const bool fsrc = t.flags & kTileSrcE;
-    const long long nxy = (long long)nx * ny;
-    const unsigned g0 = r.seq;
-    if (lead) {
-        fence_proxy_async_global();
-        for (int p = 0; p < NS && p < np; ++p) tma_issue_plane<T>(r, d.tmaps, nbox, g0 + p, bx, by, t.z0 + p);
-    }
-    T hxz = T(0), hyz = T(0);
-    long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
-    if (act) {
-        hxz = d.F[3][id - nxy];
-        hyz = d.F[4][id - nxy];
-    }
-    const int c = (ty + 1) * kTmaBoxX + (i - bx);
-    const T* stage0 = (const T*)__cvta_shared_to_generic(r.smem);
-    for (int p = 0; p < np; ++p, id += nxy) {
-        const unsigned g = g0 + p;
-        const bool got = mbar_wait(r.bar0 + 8u * (g % NS), (g / NS) & 1u);
-        if (act && got) {
-            const T* st = stage0 + (size_t)(g % NS) * kTmaMaps * P;
-            const T* sEx = st;
-            const T* sEy = st + P;
-            const T* sEz = st + 2 * P;
-            const T* sHx = st + 3 * P;
-            const T* sHy = st + 4 * P;
-            const T* sHz = st + 5 * P;
-            const T hx = sHx[c], hy = sHy[c], hz = sHz[c];
-            const T iex = st[6 * P + c];
-            const T iey = kAniso ? st[7 * P + c] : iex;
-            const T iez = kAniso ? st[8 * P + c] : iex;
-            const int k = t.z0 + p;
-            T ex = fma_t(S * iex, ((hz - sHz[c - kTmaBoxX]) - (hy - hyz)), sEx[c]);
-            T ey = fma_t(S * iey, ((hx - hxz) - (hz - sHz[c - 1])), sEy[c]);
-            T ez = fma_t(S * iez, ((hy - sHy[c - 1]) - (hx - sHx[c - kTmaBoxX])), sEz[c]);
-            if (fsrc) {
-                ex += src_add(d, a.srcs, 0, i, j, k, step);
-                ey += src_add(d, a.srcs, 1, i, j, k, step);
-                ez += src_add(d, a.srcs, 2, i, j, k, step);
-            }
-            d.F[0][id] = ex;
-            d.F[1][id] = ey;
-            d.F[2][id] = ez;
-            hxz = hx;
-            hyz = hy;
-        }
-        if (__syncthreads_or(!got)) {
-            tma_drain<T>(r, g, g0 + (np < p + NS ? np : p + NS));   // planes issued so far
-            r.seq = g0 + np;
-            return false;
-        }
-        if (lead && p + NS < np) tma_issue_plane<T>(r, d.tmaps, nbox, g + NS, bx, by, t.z0 + p + NS);
-    }
-    r.seq = g0 + np;
-    return true;
-}
-
-// H half-step of an interior tile with staged planes.  Box origin (bx, y0, k): the cell sits at
-// box row ty, column i - bx; the +x / +y neighbours one element / one row after it.  Planes
-// z0 .. z1 are staged (plane k+1 supplies E_x, E_y of the z-differences), six arrays each.
-template <typename T, bool kEnergy>
-__device__ __forceinline__ bool tile_h_tma(const Dom<T>& d, const Tile& t, T S, const StepArgs& a, int step,
-                                           TmaRing& r) {
-    constexpr int NS = tma_stages<T>();
-    constexpr int P = tma_slot_elems<T>();
-    const int nx = d.n[0], ny = d.n[1];
-    const int tid = threadIdx.y * kTileX + threadIdx.x;
-    const int tx = tid % kIntX, ty = tid / kIntX;   // interior tiles are kIntX x kIntY columns
-    const int i = t.xs[0] + tx, j = t.ys[0] + ty;
-    const bool act = i < t.xs[1] && j < t.ys[1];
-    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
-    const int bx = t.xs[0] & ~3, by = t.ys[0];
-    const int nz = t.z1 - t.z0;       // planes computed
-    const int np = nz + 1;            // planes staged
-    const bool fsrc = t.flags & kTileSrcH;
-    const long long nxy = (long long)nx * ny;
-    const unsigned g0 = r.seq;
-    if (lead) {
-        fence_proxy_async_global();
-        for (int p = 0; p < NS && p < np; ++p) tma_issue_plane<T>(r, d.tmaps, 6, g0 + p, bx, by, t.z0 + p);
-    }
-    const int c = ty * kTmaBoxX + (i - bx);
-    const T* stage0 = (const T*)__cvta_shared_to_generic(r.smem);
-    long long id = (long long)t.z0 * nxy + (long long)j * nx + i;
-    double w = 0.0;
-    bool ok = true;
-    for (int p = 0; p < nz; ++p, id += nxy) {
-        const unsigned g = g0 + p;
-        bool got = mbar_wait(r.bar0 + 8u * (g % NS), (g / NS) & 1u);
-        got = got && mbar_wait(r.bar0 + 8u * ((g + 1) % NS), ((g + 1) / NS) & 1u);
-        if (act && got) {
-            const T* st = stage0 + (size_t)(g % NS) * kTmaMaps * P;
-            const T* sn = stage0 + (size_t)((g + 1) % NS) * kTmaMaps * P;
-            const T* sEx = st;
-            const T* sEy = st + P;
-            const T* sEz = st + 2 * P;
-            const T exk = sEx[c], eyk = sEy[c], ez = sEz[c];
-            const T hx = st[3 * P + c], hy = st[4 * P + c], hz = st[5 * P + c];
-            const T exn = sn[c], eyn = sn[P + c];
-            const int k = t.z0 + p;
-            T hx1 = fma_t(-S, ((sEz[c + kTmaBoxX] - ez) - (eyn - eyk)), hx);
-            T hy1 = fma_t(-S, ((exn - exk) - (sEz[c + 1] - ez)), hy);
-            T hz1 = fma_t(-S, ((sEy[c + 1] - eyk) - (sEx[c + kTmaBoxX] - exk)), hz);
-            if (fsrc) {
-                hx1 += src_add(d, a.srcs, 3, i, j, k, step);
-                hy1 += src_add(d, a.srcs, 4, i, j, k, step);
-                hz1 += src_add(d, a.srcs, 5, i, j, k, step);
-            }
-            d.F[3][id] = hx1;
-            d.F[4][id] = hy1;
-            d.F[5][id] = hz1;
-            if (kEnergy) {
-                w += 0.5 * ((double)hx * hx1 + (double)hy * hy1 + (double)hz * hz1);
-                w += 0.5 * ((double)exk * exk / (double)d.ie[0][id] + (double)eyk * eyk / (double)d.ie[1][id] +
-                            (double)ez * ez / (double)d.ie[2][id]);
-            }
-        }
-        if (__syncthreads_or(!got)) {
-            tma_drain<T>(r, g, g0 + (np < p + NS ? np : p + NS));   // planes issued so far
-            ok = false;
-            break;
-        }
-        if (lead && p + NS < np) tma_issue_plane<T>(r, d.tmaps, 6, g + NS, bx, by, t.z0 + p + NS);
-    }
-    r.seq = g0 + np;
-    if (kEnergy) {
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        if ((threadIdx.x & 31) == 0 && d.energy && step < d.energy_cap) atomicAdd(d.energy + step, w);
-    }
-    return ok;
-}
-
-// ---- persistent step kernel ---------------------------------------------------------------
-// One cooperative launch runs nsteps forward steps: in each half-step the blocks claim tiles from
-// a shared ticket (general tiles first, so the slower ones start early), then meet at a
-// grid-wide barrier.  The barrier wait is bounded (gs->spin_limit polls); if it runs out the
-// block records an error and every block leaves the loop (a cooperative launch guarantees all
-// blocks are resident, so this only guards against a fault elsewhere).  A block whose wait ran
-// out leaves its arrival counted, so the blocks still inside reach no later barrier either: each
-// of them also gives up after at most spin_limit polls, and the launch ends in bounded time.
-
-__device__ __forceinline__ bool grid_sync(GridSync* gs, unsigned nblocks) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        volatile unsigned* vgen = &gs->gen;
-        const unsigned g = *vgen;
-        const long long limit = *((volatile long long*)&gs->spin_limit);
-        const unsigned need = nblocks + (unsigned)*((volatile int*)&gs->extra);
-        __threadfence();
-        if (atomicAdd(&gs->arrive, 1u) == need - 1) {
-            gs->arrive = 0u;
-            __threadfence();
-            atomicAdd(&gs->gen, 1u);
-        } else {
-            long long it = 0;
-            while (*vgen == g) {
-                if (++it > limit) {
-                    atomicExch(&gs->err, 1);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        s_ok = *((volatile int*)&gs->err) == 0;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-__device__ __forceinline__ int claim_tile(GridSync* gs, unsigned long long base) {
-    __shared__ int s_t;
-    if (threadIdx.x == 0 && threadIdx.y == 0) s_t = (int)(atomicAdd(&gs->ticket, 1ull) - base);
-    __syncthreads();
-    const int t = s_t;
-    __syncthreads();
-    return t;
-}
-
-template <typename T, bool kAniso, bool kEnergy, int kVar>
-__global__ void __launch_bounds__(kTileX* kTileY, min_blocks_persistent<T, kVar>())
-    k_steps(const Dom<T>* __restrict__ doms, const Tile* __restrict__ tiles, int ntiles, T S, const StepArgs a,
-            int nsteps, GridSync* gs) {
-    extern __shared__ unsigned char smem_dyn[];
-    TmaRing ring{0u, 0u, 0u};
-    if (kVar == 2) {
-        constexpr int NS = tma_stages<T>();
-        const unsigned base = (smem_u32(smem_dyn) + 127u) & ~127u;
-        ring.smem = base;
-        ring.bar0 = base + (unsigned)(NS * kTmaMaps * tma_slot_elems<T>() * sizeof(T));
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            for (int q = 0; q < NS; ++q) mbar_init(ring.bar0 + 8u * q, 1u);
-            mbar_init_fence();
-        }
-        __syncthreads();
-    }
-    // an earlier launch of this context gave up a wait: do nothing (the error stays set)
-    if (*((volatile int*)&gs->err) != 0) return;
-    const int step0 = *a.d_step;
-    // each phase claims the field tiles, then the DFT items of the field the phase leaves alone:
-    // the E phase of step s records H of step s-1, the H phase E of step s; a tail phase records
-    // H of the last step
-    const int ndft = a.dft_on ? a.ndft : 0;
-    const int nwork = ntiles + ndft;
-    const unsigned long long per_phase = (unsigned long long)nwork + gridDim.x;
-    unsigned long long base = 0;
-    bool ok = true;
-    for (int s = 0; s < nsteps; ++s) {
-        const int step = step0 + s;
-        while (ok) {
-            const int t = claim_tile(gs, base);
-            if (t >= nwork) break;
-            if (t >= ntiles) {
-                if (s > 0) dft_item(doms, a.mons, a.dft_items[t - ntiles], 1, step - 1);
-                continue;
-            }
-            const Tile tl = tiles[t];
-            if (tl.flags & kTileGeneral)
-                tile_e<T, true, true>(doms, tl, S, a, step);
-            else if (kVar == 1)
-                tile_e_int<T, kAniso>(doms, tl, S, a, step);
-            else if (kVar == 2 && doms[tl.dom].tma)
-                ok = tile_e_tma<T, kAniso>(doms[tl.dom], tl, S, a, step, ring);
-            else
-                tile_e<T, false, kAniso>(doms, tl, S, a, step);
-        }
-        if (!ok && threadIdx.x == 0 && threadIdx.y == 0) atomicExch(&gs->err, 2);
-        if (kVar == 2) fence_proxy_async_global();   // these stores are TMA sources of the next phase
-        base += per_phase;
-        if (!grid_sync(gs, gridDim.x)) return;
-        while (ok) {
-            const int t = claim_tile(gs, base);
-            if (t >= nwork) break;
-            if (t >= ntiles) {
-                dft_item(doms, a.mons, a.dft_items[t - ntiles], 0, step);
-                continue;
-            }
-            const Tile tl = tiles[t];
-            if (tl.flags & kTileGeneral)
-                tile_h<T, true, kEnergy>(doms, tl, S, a, step);
-            else if (kVar == 1)
-                tile_h_int<T, kEnergy>(doms, tl, S, a, step);
-            else if (kVar == 2 && doms[tl.dom].tma)
-                ok = tile_h_tma<T, kEnergy>(doms[tl.dom], tl, S, a, step, ring);
-            else
-                tile_h<T, false, kEnergy>(doms, tl, S, a, step);
-        }
-        if (!ok && threadIdx.x == 0 && threadIdx.y == 0) atomicExch(&gs->err, 2);
-        if (kVar == 2) fence_proxy_async_global();
-        base += per_phase;
-        if (!grid_sync(gs, gridDim.x)) return;
-    }
-    while (ndft > 0 && nsteps > 0) {
-        const int t = claim_tile(gs, base);
-        if (t >= ndft) break;
-        dft_item(doms, a.mons, a.dft_items[t], 1, step0 + nsteps - 1);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *a.d_step = step0 + nsteps;
-}
-
-template <typename T, int kVar>
-static cudaError_t steps_fn(int aniso, int energy, void** fn) {
-    if (aniso)
-        *fn = energy ? (void*)k_steps<T, true, true, kVar> : (void*)k_steps<T, true, false, kVar>;
-    else
-        *fn = energy ? (void*)k_steps<T, false, true, kVar> : (void*)k_steps<T, false, false, kVar>;
-    const int smem = kVar == 2 ? tma_smem_bytes<T>() : 0;
-    return smem > 48 * 1024 ? cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) : cudaSuccess;
-}
-
-template <typename T>
-cudaError_t launch_steps(const Launch& L, const Dom<T>* doms, const Tile* tiles, int ntiles, T S, const StepArgs& a,
-                         int nsteps, int aniso, int energy, int variant, GridSync* gs, int* grid_used) {
-    void* fn = nullptr;
-    cudaError_t e;
-    if (variant == 2)
-        e = steps_fn<T, 2>(aniso, energy, &fn);
-    else if (variant == 1)
-        e = steps_fn<T, 1>(aniso, energy, &fn);
-    else
-        e = steps_fn<T, 0>(aniso, energy, &fn);
-    if (e != cudaSuccess) return e;
-    const int smem = variant == 2 ? tma_smem_bytes<T>() : 0;
-    int dev = 0, sms = 0, per = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kTileX * kTileY, smem);
-    if (e != cudaSuccess) return e;
-    if (per < 1) return cudaErrorInvalidConfiguration;
-    int grid = sms * per;
-    if (grid > ntiles) grid = ntiles;
-    if (grid < 1) grid = 1;
-    // clear the barrier and the ticket, not the sticky error word or the limits
-    e = cudaMemsetAsync(&gs->arrive, 0, 2 * sizeof(unsigned), L.stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(&gs->ticket, 0, sizeof(unsigned long long), L.stream);
-    if (e != cudaSuccess) return e;
-    StepArgs aa = a;
-    void* args[] = {(void*)&doms, (void*)&tiles, (void*)&ntiles, (void*)&S, (void*)&aa, (void*)&nsteps, (void*)&gs};
-    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTileX, kTileY), args, (size_t)smem, L.stream);
-    ++*L.counter;
-    if (grid_used) *grid_used = grid;
-    return e;
-}
-
 __global__ void k_advance(int* d_step, int delta) { *d_step += delta; }
 
 // ---- host launchers --------------------------------------------------------------------------
@@ -1339,9 +809,5 @@ template void launch_e_curl<float>(const Launch&, const CellArgs<float>&);
 template void launch_e_curl<double>(const Launch&, const CellArgs<double>&);
 template void launch_h_cell<float>(const Launch&, const CellArgs<float>&, float, const StepArgs&);
 template void launch_h_cell<double>(const Launch&, const CellArgs<double>&, double, const StepArgs&);
-template cudaError_t launch_steps<float>(const Launch&, const Dom<float>*, const Tile*, int, float, const StepArgs&, int,
-                                         int, int, int, GridSync*, int*);
-template cudaError_t launch_steps<double>(const Launch&, const Dom<double>*, const Tile*, int, double,
-                                          const StepArgs&, int, int, int, int, GridSync*, int*);
 
 }  // namespace gbfdtd

@@ -27,8 +27,9 @@ STATUS_NAMES = ["FDTD_OK", "FDTD_EINVAL", "FDTD_ECFL", "FDTD_ETENSOR", "FDTD_ENO
 FDTD_F32, FDTD_F64 = 0, 1
 FDTD_LORENTZ, FDTD_DRUDE = 0, 1
 FDTD_CODEC_NATIVE, FDTD_CODEC_BF16 = 0, 1
-LAUNCH_MODES = 5   # FDTD_LAUNCH_MODES: per-half-step tiles, persistent, +register prefetch, +TMA staging, per-cell
-KERNEL_CLASSES = ["e_update", "h_update", "source", "dft", "step", "adj_e", "adj_h", "persistent"]
+LAUNCH_MODES = 5   # FDTD_LAUNCH_MODES: entries of the autotuner's array, indexed by mode
+MODES = (0, 4)     # the launch modes: per-half-step tile launches over all domains, per-cell launches
+KERNEL_CLASSES = ["e_update", "h_update", "source", "dft", "step", "adj_e", "adj_h", "unused"]
 
 
 class fdtd_grid(C.Structure):
@@ -118,7 +119,6 @@ _SIGS = {
     "fdtd_set_adjoint_step_count": [_ctx, C.c_int64],
     "fdtd_check_finite": [_ctx],
     "fdtd_synchronize": [_ctx, C.c_int32],
-    "fdtd_set_wait_limit": [_ctx, C.c_int64, C.c_int32],
     "fdtd_time_half_steps": [_ctx, C.c_int32, C.c_int32, C.POINTER(C.c_double)],
     "fdtd_measure_fp64_rate": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "fdtd_launch_count": [_ctx, _i64p],
@@ -253,7 +253,8 @@ def fdtd_get_launch_mode(ctx):
 
 
 def fdtd_autotune(ctx, n_steps):
-    """Times the launch modes on the live state, keeps the fastest; returns ms per mode."""
+    """Times launch modes 0 and 4 on the live state, keeps the faster; returns ms per mode index
+    (-1 for the mode numbers that are not available)."""
     ms = (C.c_double * LAUNCH_MODES)()
     _check(load().fdtd_autotune(ctx, int(n_steps), ms), "fdtd_autotune", ctx)
     return [float(v) for v in ms]
@@ -267,7 +268,6 @@ fdtd_step_adjoint = _wrap_simple("fdtd_step_adjoint")
 fdtd_set_adjoint_step_count = _wrap_simple("fdtd_set_adjoint_step_count")
 fdtd_check_finite = _wrap_simple("fdtd_check_finite")
 fdtd_synchronize = _wrap_simple("fdtd_synchronize")
-fdtd_set_wait_limit = _wrap_simple("fdtd_set_wait_limit")
 
 
 def fdtd_measure_fp64_rate(stream=0):

@@ -525,10 +525,10 @@ def test_nonfinite_detection_and_adjoint_state_rules():
 
 
 @pytest.mark.parametrize("which,dtype", [("blocks", "f32"), ("batch", "f32"), ("blocks", "f64"), ("rows42", "f32")])
-def test_persistent_and_per_launch_paths_bitwise_equal(which, dtype):
-    # every launch mode (per-half-step, persistent, register prefetch, TMA-staged planes) runs the
-    # same arithmetic per cell, so the states and spectra must agree bit for bit; 42-cell rows
-    # (168 B, not a multiple of 16 B) cannot be staged by TMA and take the register path
+def test_tile_and_per_cell_launch_modes_bitwise_equal(which, dtype):
+    # both launch modes (tile launches over all domains, per-cell launches per domain) run the
+    # same arithmetic per cell, so the states and spectra must agree bit for bit (42-cell rows: a
+    # row width that is no multiple of a warp)
     if which == "blocks":
         scs = [small_blocks(40, 6, 150)]
     elif which == "rows42":
@@ -536,7 +536,7 @@ def test_persistent_and_per_launch_paths_bitwise_equal(which, dtype):
     else:
         scs = _tiny_batch(3, 150)
     outs = []
-    for mode in range(fdtd.LAUNCH_MODES):
+    for mode in fdtd.MODES:
         ctx = fdtd.Context(scs, dtype=dtype)
         fdtd.fdtd_set_launch_mode(ctx.ctx, mode)
         ctx.step(70)
@@ -580,8 +580,8 @@ def test_autotune_keeps_state_and_spectra():
     ctx = fdtd.Context([sc], dtype="f32")
     ctx.step(30)
     ms = fdtd.fdtd_autotune(ctx.ctx, 12)
-    assert len(ms) == fdtd.LAUNCH_MODES and all(m > 0 for m in ms)
-    assert fdtd.fdtd_get_launch_mode(ctx.ctx) in range(fdtd.LAUNCH_MODES)
+    assert [m > 0 for m in ms] == [q in fdtd.MODES for q in range(fdtd.LAUNCH_MODES)]
+    assert fdtd.fdtd_get_launch_mode(ctx.ctx) in fdtd.MODES
     assert ctx.step_count == 30
     ctx.step(30)
     for p in range(ctx.part_count(0)):

@@ -16,7 +16,7 @@ from tests.test_gpu_parity import _gpu_loss, _oracle_objective, _random_parts, _
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("mode", list(range(5)))
+@pytest.mark.parametrize("mode", list(fdtd.MODES))
 def test_periodic_cell_fp64_matches_oracle_in_every_launch_mode(mode):
     sc = W.periodic_cell(n_steps=90)
     o = oracle_from_scene(sc)
@@ -33,7 +33,7 @@ def test_periodic_cell_fp64_matches_oracle_in_every_launch_mode(mode):
 def test_periodic_cell_launch_modes_bitwise_equal_fp32():
     sc = W.periodic_cell(n_steps=80)
     outs = []
-    for mode in range(fdtd.LAUNCH_MODES):
+    for mode in fdtd.MODES:
         ctx = fdtd.Context([sc], dtype="f32")
         fdtd.fdtd_set_launch_mode(ctx.ctx, mode)
         ctx.step(80)
