@@ -167,7 +167,11 @@ def alg_bytes_per_cell(sc, esz, kind):
     else:
         words = 9
     per_memb = 6 if kind.startswith("adj") else 4
-    return (words + per_memb * memb) * esz, cells
+    extra = 0.0
+    if kind == "e_update" and sc.poles and sc.pole_mask is not None:
+        # each pole's (P, Q) read and written in the dispersive cells: 4 words, x 3 components
+        extra = 12.0 * len(sc.poles) * float((sc.pole_mask != 0).mean())
+    return (words + per_memb * memb + extra) * esz, cells
 
 
 def run_ours(args):
@@ -800,8 +804,14 @@ def measure_batched(args):
         dist.barrier()
         t = sharding.max_over_ranks(t, dist, torch.device("cuda", local))
     small = min(range(len(scs)), key=lambda d: scs[d].cells)
+    # algorithmic bytes of a step over the whole batch (E with the poles' P, Q in dispersive cells, H)
+    step_bytes = sum((alg_bytes_per_cell(sc, 4, "e_update")[0] + alg_bytes_per_cell(sc, 4, "h_update")[0]) * sc.cells
+                     for sc in scs)
+    peak, _ = peaks()
     out = {"workload": f"lorentz_batch: {len(all_scs)} domains, {total_cells} cells, {T} steps, FP32",
            "gcell_steps_s": round(total_cells * T / t / 1e9, 3), "seconds": round(t, 4),
+           "step_effective_gbs": round(step_bytes * T / t / 1e9, 1),
+           "step_frac_of_measured_copy": round(step_bytes * T / t / 1e9 / peak, 4),
            "n_gpus": world, "scaling": "strong (fixed batch, domains sharded over ranks)",
            "launch_mode": mode, "autotune_ms_per_64_steps": {"tiles": round(tune_ms[0], 3),
                                                               "per-cell": round(tune_ms[4], 3)}}

@@ -116,6 +116,12 @@ struct fdtd_ctx {
     int* d_step = nullptr;
     unsigned* d_ticket = nullptr;   // completion ticket of the last H launch of a step
     int cell_mode = 1;              // per-half-step launches of the per-cell streaming kernels
+    // per-cell mode with several domains: one launch per half-step over all of them, from argument
+    // blocks in device memory (E side, H side) and the prefix sums of the domains' block counts
+    void* d_cargs[2] = {nullptr, nullptr};
+    int* d_bbeg = nullptr;
+    int multi_blocks = 0;
+    int cargs_dirty = 1;
     int h_step_tmp = 0;
     long long step = 0;
     long long adj_step = 0;
@@ -454,6 +460,7 @@ fdtd_status sync_doms(fdtd_ctx* c) {
     // any descriptor change (materials, sources, monitors, design) invalidates them
     drop_graphs(c);
     c->stream_dirty = 1;
+    c->cargs_dirty = 1;
     return c->dtype == FDTD_F32 ? sync_doms_t<float>(c) : sync_doms_t<double>(c);
 }
 
@@ -889,6 +896,51 @@ CellArgs<T> make_cell_args(const fdtd_ctx* c, int di, bool e_side) {
     return ca;
 }
 
+// Whether the per-cell mode runs every domain in one launch per half-step: several domains, none
+// of them a Bloch or tensor domain or one with an interface record.
+bool multi_cells(const fdtd_ctx* c) {
+    if (c->doms.size() < 2 || c->streamed) return false;
+    for (const DomainHost& h : c->doms)
+        if (h.bloch || h.tensor || h.rec) return false;
+    return true;
+}
+
+// Uploads the argument blocks of every domain and the block prefix sums (outside graph capture).
+template <typename T>
+fdtd_status sync_cell_args_t(fdtd_ctx* c) {
+    const int nd = (int)c->doms.size();
+    std::vector<CellArgs<T>> ae(nd), ah(nd);
+    std::vector<int> beg(nd + 1, 0);
+    for (int di = 0; di < nd; ++di) {
+        ae[di] = make_cell_args<T>(c, di, true);
+        ah[di] = make_cell_args<T>(c, di, false);
+        const DomainHost& h = c->doms[di];
+        beg[di + 1] = beg[di] + ((h.n[0] + 15) / 16) * ((h.n[1] + 15) / 16) * h.n[2];
+    }
+    for (int s2 = 0; s2 < 2; ++s2) {
+        if (!c->d_cargs[s2]) {
+            fdtd_status st = dmalloc(c, &c->d_cargs[s2], sizeof(CellArgs<T>) * nd);
+            if (st != FDTD_OK) return st;
+        }
+        CK(c, cudaMemcpyAsync(c->d_cargs[s2], s2 ? ah.data() : ae.data(), sizeof(CellArgs<T>) * nd,
+                              cudaMemcpyHostToDevice, c->stream));
+    }
+    if (!c->d_bbeg) {
+        fdtd_status st = dmalloc(c, (void**)&c->d_bbeg, sizeof(int) * (nd + 1));
+        if (st != FDTD_OK) return st;
+    }
+    CK(c, cudaMemcpyAsync(c->d_bbeg, beg.data(), sizeof(int) * (nd + 1), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));   // the host vectors go out of scope
+    c->multi_blocks = beg[nd];
+    c->cargs_dirty = 0;
+    return FDTD_OK;
+}
+
+fdtd_status sync_cell_args(fdtd_ctx* c) {
+    if (!c->cell_mode || !c->cargs_dirty || !multi_cells(c)) return FDTD_OK;
+    return c->dtype == FDTD_F32 ? sync_cell_args_t<float>(c) : sync_cell_args_t<double>(c);
+}
+
 // Tensor-operator operands of domain di: operand v, output out (three E-edge arrays each).
 template <typename T>
 TensorArgs<T> tensor_args(const fdtd_ctx* c, int di, void* const* v, void* const* out) {
@@ -981,7 +1033,19 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
         }
         return b;
     };
-    if (cell) {
+    // one launch per half-step over every domain of a batch (per-cell mode)
+    const bool multi = cell && multi_cells(c) && !c->cargs_dirty;
+    int any_poles = 0, any_per = 0;
+    if (multi)
+        for (const DomainHost& h : c->doms) {
+            any_poles |= h.npole > 0 && h.bcell > 0;
+            any_per |= h.per[0] | h.per[1];
+        }
+    if (multi) {
+        Prof p(c, FDTD_KERNEL_E);
+        launch_e_cells<T>(l, (const CellArgs<T>*)c->d_cargs[0], c->d_bbeg, (int)c->doms.size(), c->multi_blocks, dd,
+                          (T)c->S, a, c->aniso, any_poles, any_per);
+    } else if (cell) {
         Prof p(c, FDTD_KERNEL_E);
         for (int di = 0; di < (int)c->doms.size(); ++di) {
             const DomainHost& h = c->doms[di];
@@ -1021,7 +1085,11 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
     }
     if (dstream && !first) cudaStreamWaitEvent(st, c->ev_dh, 0);   // DFT of H^{n-1/2} done
     if (cell) {
-        {
+        if (multi) {
+            Prof p(c, FDTD_KERNEL_H);
+            launch_h_cells<T>(l, (const CellArgs<T>*)c->d_cargs[1], c->d_bbeg, (int)c->doms.size(), c->multi_blocks,
+                              (T)c->S, a, any_per);
+        } else {
             Prof p(c, FDTD_KERNEL_H);
             for (int di = 0; di < (int)c->doms.size(); ++di) {
                 if (c->doms[di].bloch)
@@ -2725,6 +2793,10 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
         return FDTD_OK;
     }
     int left = n_steps;
+    {
+        fdtd_status st = sync_cell_args(ctx);   // a batch's argument blocks, before any capture
+        if (st != FDTD_OK) return st;
+    }
     if (ctx->use_graphs && !ctx->prof_on && left >= kGraphSteps) {
         fdtd_status st = build_graph(ctx);
         if (st != FDTD_OK) return st;

@@ -384,6 +384,17 @@ void launch_e_cell(const Launch& L, const CellArgs<T>& c, const Dom<T>* doms, T 
                    int poles);
 template <typename T>
 void launch_h_cell(const Launch& L, const CellArgs<T>& c, T S, const StepArgs& a);
+// The per-cell updates of every domain of a batch in one launch each: args holds one argument block
+// per domain (device memory), bbeg the prefix sums of the domains' block counts (ceil(nx / 16)
+// ceil(ny / 16) nz each; ndom + 1 entries, nblocks = bbeg[ndom]).  The same arithmetic per cell as
+// launch_e_cell / launch_h_cell.  aniso / poles / per: some domain is anisotropic, dispersive,
+// periodic.
+template <typename T>
+void launch_e_cells(const Launch& L, const CellArgs<T>* args, const int* bbeg, int ndom, int nblocks,
+                    const Dom<T>* doms, T S, const StepArgs& a, int aniso, int poles, int per);
+template <typename T>
+void launch_h_cells(const Launch& L, const CellArgs<T>* args, const int* bbeg, int ndom, int nblocks, T S,
+                    const StepArgs& a, int per);
 // Curl of the E update of a tensor domain (CPML memories advanced, no E update, no sources) into
 // c.cur; PEC-held edges are not written.
 template <typename T>

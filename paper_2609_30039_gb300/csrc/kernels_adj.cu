@@ -944,9 +944,20 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, kPoles || k
         adj_e_cell_body<T, kPoles, kGrad, kMon, false, kTen>(c, doms, mons, S, m, pending, nullptr);
         return;
     }
-    // every thread of the block reaches the reductions below (the domain, hence np, is the launch's)
     const Dom<T>& d = doms[c.dom];
     const int np = d.pgc ? d.npole : 0;
+    // a block of 16 x 16 cells of one plane that meets no pole-box cell has no pole-coefficient
+    // cotangent to add (a block-uniform test): it runs the plain body and skips the reductions
+    {
+        const int i0 = blockIdx.x * 16, j0 = blockIdx.y * 16, k = blockIdx.z;
+        const bool meets = np > 0 && i0 < d.bhi[0] && i0 + 16 > d.blo[0] && j0 < d.bhi[1] && j0 + 16 > d.blo[1] &&
+                           k >= d.blo[2] && k < d.bhi[2];
+        if (!meets) {
+            adj_e_cell_body<T, kPoles, kGrad, kMon, false, kTen>(c, doms, mons, S, m, pending, nullptr);
+            return;
+        }
+    }
+    // every thread of the block reaches the reductions below (the domain, hence np, is the launch's)
     double acc[kMaxPole * 6];
     for (int q = 0; q < np * 6; ++q) acc[q] = 0.0;
     adj_e_cell_body<T, kPoles, kGrad, kMon, true, false>(c, doms, mons, S, m, pending, acc);

@@ -408,12 +408,10 @@ __device__ __forceinline__ T cpml_cell(const T* coef, int N, int x, T* psi, T D)
 // E^n = (E^{n+1} - s^n) - S eps^-1 curl H^{n+1/2}, called with S negated (no CPML, no poles).
 // kCurl: the first half of a tensor domain's E update (Sec. 2.3): the CPML-corrected curl of every
 // non-PEC edge into c.cur (the memories advance as usual); launch_tensor_apply then applies S_t.
-template <typename T, bool kAniso, bool kPoles, bool kPer, bool kBack = false, bool kCurl = false>
-__global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
-    k_e_cell(const CellArgs<T> c, const Dom<T>* __restrict__ doms, T S, const StepArgs a) {
+template <typename T, bool kAniso, bool kPoles, bool kPer, bool kBack, bool kCurl>
+__device__ __forceinline__ void e_cell_body(const CellArgs<T>& c, const Dom<T>* __restrict__ doms, T S,
+                                            const StepArgs& a, int i, int j, int k) {
     const int nx = c.n[0], ny = c.n[1];
-    const int i = blockIdx.x * 16 + (threadIdx.x & 15), j = blockIdx.y * 16 + threadIdx.y * 2 + (threadIdx.x >> 4);
-    const int k = blockIdx.z;
     const int kg = k + c.kz0;   // global plane (CPML z profile, sources)
     if (i >= nx || j >= ny) return;
     const long long nxy = (long long)nx * ny;
@@ -511,13 +509,62 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
     if (!pz) c.F[2][id] = ez;
 }
 
+// Block (bx, by, bz) of a domain's per-cell grid: blocks of 32 x 8 threads cover 16 x 16 cells of a
+// z-plane, a warp 16 x 2 cells (two aligned half-rows): a row's x slabs fill two of its warps.
+__device__ __forceinline__ void cell_of(int bx, int by, int& i, int& j) {
+    i = bx * 16 + (threadIdx.x & 15);
+    j = by * 16 + threadIdx.y * 2 + (threadIdx.x >> 4);
+}
+
+template <typename T, bool kAniso, bool kPoles, bool kPer, bool kBack = false, bool kCurl = false>
+__global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
+    k_e_cell(const CellArgs<T> c, const Dom<T>* __restrict__ doms, T S, const StepArgs a) {
+    int i, j;
+    cell_of(blockIdx.x, blockIdx.y, i, j);
+    e_cell_body<T, kAniso, kPoles, kPer, kBack, kCurl>(c, doms, S, a, i, j, blockIdx.z);
+}
+
+// Domain of block b of a multi-domain launch: the last d with bbeg[d] <= b (bbeg: prefix sums of the
+// domains' block counts); its argument block is copied into shared memory once per block.
+template <typename T>
+__device__ __forceinline__ int multi_cell(const CellArgs<T>* __restrict__ args, const int* __restrict__ bbeg, int ndom,
+                                          CellArgs<T>& sc, int& i, int& j, int& k) {
+    const int b = blockIdx.x;
+    int lo = 0, hi = ndom - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bbeg[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const int tid = threadIdx.y * kTileX + threadIdx.x;
+    const int* src = (const int*)(args + lo);
+    int* dst = (int*)&sc;
+    for (int w = tid; w < (int)(sizeof(CellArgs<T>) / sizeof(int)); w += kTileX * kTileY) dst[w] = src[w];
+    __syncthreads();
+    const int local = b - bbeg[lo];
+    const int gx = (sc.n[0] + 15) >> 4, gy = (sc.n[1] + 15) >> 4;
+    cell_of(local % gx, (local / gx) % gy, i, j);
+    k = local / (gx * gy);
+    return lo;
+}
+
+// Every domain of a batch in one launch (per-cell launch mode with several domains): the same body as
+// k_e_cell, the domain's operands read from its argument block.
+template <typename T, bool kAniso, bool kPoles, bool kPer>
+__global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T, kPoles>())
+    k_e_cells(const CellArgs<T>* __restrict__ args, const int* __restrict__ bbeg, int ndom,
+              const Dom<T>* __restrict__ doms, T S, const StepArgs a) {
+    __shared__ CellArgs<T> sc;
+    int i, j, k;
+    multi_cell(args, bbeg, ndom, sc, i, j, k);
+    e_cell_body<T, kAniso, kPoles, kPer, false, false>(sc, doms, S, a, i, j, k);
+}
+
+
 // kBack: backward H step, H^{n+1/2} = (H^{n+3/2} - m^n) + S curl E^{n+1}, called with S negated.
-template <typename T, bool kPer, bool kBack = false>
-__global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
-    k_h_cell(const CellArgs<T> c, T S, const StepArgs a) {
+template <typename T, bool kPer, bool kBack>
+__device__ __forceinline__ void h_cell_body(const CellArgs<T>& c, T S, const StepArgs& a, int i, int j, int k) {
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
-    const int i = blockIdx.x * 16 + (threadIdx.x & 15), j = blockIdx.y * 16 + threadIdx.y * 2 + (threadIdx.x >> 4);
-    const int k = blockIdx.z;
     const int kg = k + c.kz0;   // global plane (CPML z profile, sources)
     if (i < nx && j < ny) {
         const long long nxy = (long long)nx * ny;
@@ -593,6 +640,23 @@ __global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
     }
 }
 
+template <typename T, bool kPer, bool kBack = false>
+__global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>()) k_h_cell(const CellArgs<T> c, T S, const StepArgs a) {
+    int i, j;
+    cell_of(blockIdx.x, blockIdx.y, i, j);
+    h_cell_body<T, kPer, kBack>(c, S, a, i, j, blockIdx.z);
+}
+
+template <typename T, bool kPer>
+__global__ void __launch_bounds__(kTileX* kTileY, cell_blocks<T>())
+    k_h_cells(const CellArgs<T>* __restrict__ args, const int* __restrict__ bbeg, int ndom, T S, const StepArgs a) {
+    __shared__ CellArgs<T> sc;
+    int i, j, k;
+    multi_cell(args, bbeg, ndom, sc, i, j, k);
+    h_cell_body<T, kPer, false>(sc, S, a, i, j, k);
+}
+
+
 // grid: (x chunks of kTileX, y chunks of kTileY, z planes)
 inline dim3 cell_grid(const int* n) {
     return dim3((unsigned)((n[0] + 15) / 16), (unsigned)((n[1] + 15) / 16), (unsigned)n[2]);
@@ -616,6 +680,39 @@ void launch_e_cell(const Launch& L, const CellArgs<T>& c, const Dom<T>* doms, T 
         launch_e_cell_t<T, true>(L, c, doms, S, a, aniso, poles);
     else
         launch_e_cell_t<T, false>(L, c, doms, S, a, aniso, poles);
+    ++*L.counter;
+}
+
+template <typename T>
+void launch_e_cells(const Launch& L, const CellArgs<T>* args, const int* bbeg, int ndom, int nblocks,
+                    const Dom<T>* doms, T S, const StepArgs& a, int aniso, int poles, int per) {
+    const dim3 b(kTileX, kTileY);
+    if (per) {
+        if (poles)
+            (aniso ? k_e_cells<T, true, true, true> : k_e_cells<T, false, true, true>)<<<nblocks, b, 0, L.stream>>>(
+                args, bbeg, ndom, doms, S, a);
+        else
+            (aniso ? k_e_cells<T, true, false, true> : k_e_cells<T, false, false, true>)<<<nblocks, b, 0, L.stream>>>(
+                args, bbeg, ndom, doms, S, a);
+    } else {
+        if (poles)
+            (aniso ? k_e_cells<T, true, true, false> : k_e_cells<T, false, true, false>)<<<nblocks, b, 0, L.stream>>>(
+                args, bbeg, ndom, doms, S, a);
+        else
+            (aniso ? k_e_cells<T, true, false, false> : k_e_cells<T, false, false, false>)<<<nblocks, b, 0, L.stream>>>(
+                args, bbeg, ndom, doms, S, a);
+    }
+    ++*L.counter;
+}
+
+template <typename T>
+void launch_h_cells(const Launch& L, const CellArgs<T>* args, const int* bbeg, int ndom, int nblocks, T S,
+                    const StepArgs& a, int per) {
+    const dim3 b(kTileX, kTileY);
+    if (per)
+        k_h_cells<T, true><<<nblocks, b, 0, L.stream>>>(args, bbeg, ndom, S, a);
+    else
+        k_h_cells<T, false><<<nblocks, b, 0, L.stream>>>(args, bbeg, ndom, S, a);
     ++*L.counter;
 }
 
@@ -805,6 +902,14 @@ template void launch_iface<float>(const Launch&, float* const*, const int*, cons
                                   int, int);
 template void launch_iface<double>(const Launch&, double* const*, const int*, const IfaceArgs&, double*, const int*,
                                    int, int, int);
+template void launch_e_cells<float>(const Launch&, const CellArgs<float>*, const int*, int, int, const Dom<float>*,
+                                    float, const StepArgs&, int, int, int);
+template void launch_e_cells<double>(const Launch&, const CellArgs<double>*, const int*, int, int,
+                                     const Dom<double>*, double, const StepArgs&, int, int, int);
+template void launch_h_cells<float>(const Launch&, const CellArgs<float>*, const int*, int, int, float,
+                                    const StepArgs&, int);
+template void launch_h_cells<double>(const Launch&, const CellArgs<double>*, const int*, int, int, double,
+                                     const StepArgs&, int);
 template void launch_e_curl<float>(const Launch&, const CellArgs<float>&);
 template void launch_e_curl<double>(const Launch&, const CellArgs<double>&);
 template void launch_h_cell<float>(const Launch&, const CellArgs<float>&, float, const StepArgs&);
