@@ -300,10 +300,10 @@ fdtd_status fdtd_record_interface(fdtd_ctx* ctx, int32_t capacity);
 
 /* Launch modes (no counterpart in the paper; they change scheduling, not arithmetic):
  * mode 0: per-half-step launches over one tile work list of every domain (interior and shell
- * tiles on two streams), replayed as CUDA graphs: the fastest form for batches of many domains.
- * Mode 4 (default): per-half-step launches (CUDA graphs) of per-cell kernels, one thread per cell
- * over every cell of a domain, one launch per domain (with an energy record it runs the mode-0
- * code): the fastest form for one or a few domains.  Both compute the same values bitwise.
+ * tiles on two streams), replayed as CUDA graphs; the path of the energy record.
+ * Mode 4 (default): per-half-step launches (CUDA graphs) of per-cell kernels, one thread per cell;
+ * with several domains one launch per half-step covers every cell of every domain (with an energy
+ * record it runs the mode-0 code).  Both compute the same values bitwise.
  * Modes 1-3 (persistent multi-step kernels with grid barriers) are not available: FDTD_EINVAL,
  * as for any other value. */
 #define FDTD_LAUNCH_MODES 5
