@@ -1660,7 +1660,11 @@ void adj_once(fdtd_ctx* c, int m) {
     for (const auto& h : c->doms) pgrad |= h.pgc_on;
     if (c->cell_mode) {
         // per-cell launch mode: one launch per domain and half-step, E side first (the H side
-        // reads the lagged E cotangent it leaves)
+        // reads the lagged E cotangent it leaves).  The per-cell transposed kernels are launched
+        // programmatically (they start while the kernel before them finishes; not under per-launch
+        // profiling): these eager launches otherwise leave the GPU idle between half-steps.
+        Launch lp = l;
+        lp.pdl = !c->prof_on;
         std::vector<AdjCellArgs<T>> args(c->doms.size());
         std::vector<int> mon(c->doms.size(), 0);
         for (int di = 0; di < (int)c->doms.size(); ++di) args[di] = make_adj_args<T>(c, di, &mon[di]);
@@ -1699,7 +1703,7 @@ void adj_once(fdtd_ctx* c, int m) {
                     std::memset(&none, 0, sizeof(none));
                     launch_tensor_apply<T>(l, tensor_args<T>(c, di, h.teb, h.A), none, (T)c->S, StepArgs{}, 0);
                 } else {
-                    launch_adj_e_cell<T>(l, args[di], dd, c->d_mons, (T)c->S, m, c->adj_pending,
+                    launch_adj_e_cell<T>(lp, args[di], dd, c->d_mons, (T)c->S, m, c->adj_pending,
                                          h.npole > 0 && h.bcell > 0, mon[di], h.pgc_on, 0);
                 }
             }
@@ -1712,7 +1716,7 @@ void adj_once(fdtd_ctx* c, int m) {
                 if (c->doms[di].bloch)
                     launch_adj_h_bloch<T>(l, make_adj_bloch<T>(c, di, args[di]));
                 else
-                    launch_adj_h_cell<T>(l, args[di], dd, c->d_mons, (T)c->S, m, mon[di]);
+                    launch_adj_h_cell<T>(lp, args[di], dd, c->d_mons, (T)c->S, m, mon[di]);
             }
         }
         return;

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "fdtd.h"
 
 namespace gbfdtd {
@@ -207,7 +209,40 @@ __device__ inline long long ade_off(const Dom<T>& d, int i, int j, int k) {
 struct Launch {
     cudaStream_t stream;
     long long* counter;   // launches enqueued
+    // programmatic dependent launch: the kernel may start while the previous kernel of the stream
+    // finishes (only kernels that call pdl_wait before reading what an earlier kernel writes)
+    bool pdl = false;
 };
+
+// Programmatic dependent launch (sm_90+): pdl_wait returns once the grids this one depends on have
+// completed and their writes are visible (at once for a kernel launched without the attribute);
+// pdl_trigger lets the next kernel of the stream start launching once every block of this grid has
+// issued it or exited.  A kernel launched with the attribute calls pdl_wait before it reads anything
+// an earlier kernel writes (argument blocks uploaded by copies may come first) and pdl_trigger after
+// it, so a dependent launch begins only after this grid's prerequisites, hence every earlier kernel
+// of the stream, have completed, and its waiting blocks only hold SM slots.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch kernel k on L.stream, with the programmatic-serialization attribute when L.pdl is set.
+template <typename... KArgs, typename... Args>
+inline void launch_k(const Launch& L, void (*k)(KArgs...), dim3 g, dim3 b, Args&&... args) {
+    if (!L.pdl) {
+        k<<<g, b, 0, L.stream>>>(std::forward<Args>(args)...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 
 // Forward kernels (kernels_fwd.cu)
 // Step context shared by the fused forward kernels: sources, monitors, the device step counter

@@ -824,6 +824,8 @@ __device__ __forceinline__ void adj_e_cell_body(const AdjCellArgs<T>& c, const D
     // -1 neighbours (wrapping on a periodic axis); in-plane offsets in 32 bits
     const bool hx_ = i > 0 || c.per[0], hy_ = j > 0 || c.per[1], hz_ = k > 0;
     const int ox = i > 0 ? -1 : nx - 1, oy = j > 0 ? -nx : (ny - 1) * nx;
+    pdl_wait();
+    pdl_trigger();
     const T* Bx = c.A[3] + pl;
     const T* By = c.A[4] + pl;
     const T* Bz = c.A[5] + pl;
@@ -991,6 +993,8 @@ __global__ void __launch_bounds__(kTileX* kTileY, adj_cell_blocks<T, false>())
     // +1 neighbours (wrapping on a periodic axis)
     const bool xe = i + 1 < nx || c.per[0], ye = j + 1 < ny || c.per[1], ze = k + 1 < nz;
     const int ox = i + 1 < nx ? 1 : -(nx - 1), oy = j + 1 < ny ? nx : -(ny - 1) * nx;
+    pdl_wait();
+    pdl_trigger();
     const T* Fx = c.A[0] + pl;
     const T* Fy = c.A[1] + pl;
     const T* Fz = c.A[2] + pl;
@@ -1187,27 +1191,27 @@ void launch_adj_e_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* d
     if (tensor) {
         // a tensor domain has no poles; its material cotangent comes from launch_tensor_grad
         if (mon)
-            k_adj_e_cell<T, false, false, true, false, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending);
+            launch_k(L, k_adj_e_cell<T, false, false, true, false, true>, g, b, c, doms, mons, S, m, pending);
         else
-            k_adj_e_cell<T, false, false, false, false, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending);
+            launch_k(L, k_adj_e_cell<T, false, false, false, false, true>, g, b, c, doms, mons, S, m, pending);
         ++*L.counter;
         return;
     }
     const bool grad = c.grad != nullptr;
     const int key = (poles && pole_grad ? 8 : 0) | (poles ? 4 : 0) | (grad ? 2 : 0) | (mon ? 1 : 0);
     switch (key) {
-        case 0: k_adj_e_cell<T, false, false, false, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
-        case 1: k_adj_e_cell<T, false, false, true, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
-        case 2: k_adj_e_cell<T, false, true, false, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
-        case 3: k_adj_e_cell<T, false, true, true, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
-        case 4: k_adj_e_cell<T, true, false, false, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
-        case 5: k_adj_e_cell<T, true, false, true, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
-        case 6: k_adj_e_cell<T, true, true, false, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
-        case 7: k_adj_e_cell<T, true, true, true, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
-        case 12: k_adj_e_cell<T, true, false, false, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
-        case 13: k_adj_e_cell<T, true, false, true, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
-        case 14: k_adj_e_cell<T, true, true, false, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
-        default: k_adj_e_cell<T, true, true, true, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m, pending); break;
+        case 0: launch_k(L, k_adj_e_cell<T, false, false, false, false>, g, b, c, doms, mons, S, m, pending); break;
+        case 1: launch_k(L, k_adj_e_cell<T, false, false, true, false>, g, b, c, doms, mons, S, m, pending); break;
+        case 2: launch_k(L, k_adj_e_cell<T, false, true, false, false>, g, b, c, doms, mons, S, m, pending); break;
+        case 3: launch_k(L, k_adj_e_cell<T, false, true, true, false>, g, b, c, doms, mons, S, m, pending); break;
+        case 4: launch_k(L, k_adj_e_cell<T, true, false, false, false>, g, b, c, doms, mons, S, m, pending); break;
+        case 5: launch_k(L, k_adj_e_cell<T, true, false, true, false>, g, b, c, doms, mons, S, m, pending); break;
+        case 6: launch_k(L, k_adj_e_cell<T, true, true, false, false>, g, b, c, doms, mons, S, m, pending); break;
+        case 7: launch_k(L, k_adj_e_cell<T, true, true, true, false>, g, b, c, doms, mons, S, m, pending); break;
+        case 12: launch_k(L, k_adj_e_cell<T, true, false, false, true>, g, b, c, doms, mons, S, m, pending); break;
+        case 13: launch_k(L, k_adj_e_cell<T, true, false, true, true>, g, b, c, doms, mons, S, m, pending); break;
+        case 14: launch_k(L, k_adj_e_cell<T, true, true, false, true>, g, b, c, doms, mons, S, m, pending); break;
+        default: launch_k(L, k_adj_e_cell<T, true, true, true, true>, g, b, c, doms, mons, S, m, pending); break;
     }
     ++*L.counter;
 }
@@ -1217,9 +1221,9 @@ void launch_adj_h_cell(const Launch& L, const AdjCellArgs<T>& c, const Dom<T>* d
                        int mon) {
     const dim3 g = adj_cell_grid(c.n), b(kTileX, kTileY);
     if (mon)
-        k_adj_h_cell<T, true><<<g, b, 0, L.stream>>>(c, doms, mons, S, m);
+        launch_k(L, k_adj_h_cell<T, true>, g, b, c, doms, mons, S, m);
     else
-        k_adj_h_cell<T, false><<<g, b, 0, L.stream>>>(c, doms, mons, S, m);
+        launch_k(L, k_adj_h_cell<T, false>, g, b, c, doms, mons, S, m);
     ++*L.counter;
 }
 
