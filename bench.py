@@ -242,9 +242,9 @@ def run_ours(args):
     value = world * cells * T_STEPS / (ms_per_step * 1e-3) / 1e9
 
     # roofline of the dominant kernel: each kernel class of the timed solve, on the benchmark state
-    # right after the timed solves, as a graph of 32 back-to-back launches with CUDA events on the
+    # right after the timed solves, as a graph of back-to-back launches with CUDA events on the
     # context's stream at the graph's two ends only (events between launches would add a drain per
-    # launch); E + H must fit in the timed step (the DFT runs beside them on its own stream)
+    # launch); E + H must fit in the timed step
     peak, peak_kind = peaks()
     bE, ncell = alg_bytes_per_cell(sc, 4, "e_update")
     bH, _ = alg_bytes_per_cell(sc, 4, "h_update")
@@ -252,9 +252,13 @@ def run_ours(args):
     roof_extra = {}
     if mode == 4:
         step_ms = {"e_update": fdtd.fdtd_time_half_steps(ctx.ctx, 0, 32),
-                   "h_update": fdtd.fdtd_time_half_steps(ctx.ctx, 1, 32),
-                   "dft": fdtd.fdtd_time_half_steps(ctx.ctx, 2, 32)}
-        step_ms["dft"] *= 2.0   # the DFT of E and the DFT of H of one step
+                   "h_update": fdtd.fdtd_time_half_steps(ctx.ctx, 1, 32)}
+        try:
+            # monitor rings: one fold of 32 steps of samples per batch, per step its 32nd part
+            step_ms["dft_fold"] = fdtd.fdtd_time_half_steps(ctx.ctx, 5, 8) / 32.0
+        except fdtd.FdtdError:
+            # the DFT of E and the DFT of H of one step
+            step_ms["dft"] = 2.0 * fdtd.fdtd_time_half_steps(ctx.ctx, 2, 32)
         dom = max(("e_update", "h_update"), key=lambda k: step_ms[k])
         avg_ms = step_ms[dom]
         bpc = bE if dom == "e_update" else bH

@@ -240,7 +240,12 @@ fdtd_status fdtd_add_source(fdtd_ctx* ctx, int32_t domain, int32_t component, co
  * F_c(f, cell) += field_c(cell) * exp(+i omega_dt[f] t) with t = n+1 for E components and
  * t = n+3/2 for H components in forward step n.  Accumulators are complex FP64, layout
  * [ncomp][n_freq][box cells (x fastest)], components in increasing id among component_mask
- * (bit c = component c).  omega_dt: host, copied.  *monitor_id receives the id. */
+ * (bit c = component c).  omega_dt: host, copied.  *monitor_id receives the id.
+ * In launch mode 4 without an energy record, a resident context whose monitors sit at most one per
+ * domain (and in no tensor domain) keeps a device ring of one batch (32 steps) of samples per
+ * monitor (32 * ncomp * box cells field values, at most 512 MiB for all monitors): the update
+ * kernels store the samples and one launch per batch adds them to the accumulators in step order,
+ * bit for bit the values per-step accumulation gives.  Otherwise the DFT runs per half-step. */
 fdtd_status fdtd_add_dft_monitor(fdtd_ctx* ctx, int32_t domain, const int32_t lo[3], const int32_t hi[3],
                                  uint32_t component_mask, int32_t n_freq, const double* omega_dt,
                                  int32_t* monitor_id);
@@ -485,8 +490,9 @@ fdtd_status fdtd_measure_fp64_rate(void* stream, double* fma_per_s, double* best
 
 /* Device time of one kernel class running back to back (instrumentation; no counterpart in the
  * paper): captures n_launches (1..4096) launches of the E update (which = 0), the H update (1), the
- * DFT of E (2), the transposed E half-step (3) or the transposed H half-step (4) -- the per-cell
- * kernels of every domain, as one step launches them -- into a CUDA graph, replays it once to warm
+ * DFT of E (2), the transposed E half-step (3), the transposed H half-step (4) or the fold of one
+ * 32-step batch of monitor-ring samples into the DFT (5; FDTD_EINVAL without monitor rings) -- the
+ * per-cell kernels of every domain, as one step launches them -- into a CUDA graph, replays it once to warm
  * up and once between two CUDA events on the context's stream, and writes the milliseconds per
  * launch.  Only the graph is bracketed, so nothing sits between the timed launches.  The launches
  * act on the live state (forward or adjoint fields, CPML memories, pole states, DFT accumulators or

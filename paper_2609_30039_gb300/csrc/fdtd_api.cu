@@ -18,6 +18,12 @@
 
 using namespace gbfdtd;
 
+// Forward steps per captured CUDA graph, and per launched batch of the per-cell mode (the monitor
+// rings hold one batch of samples).
+constexpr int kGraphSteps = 32;
+// Device bytes the monitor rings of a context may take; beyond, the DFT runs per step.
+constexpr long long kRingMaxBytes = 512ll << 20;
+
 namespace {
 
 struct DomainHost {
@@ -127,6 +133,7 @@ struct fdtd_ctx {
     long long adj_step = 0;
     int adj_pending = 0;
     int dft_enabled = 1;
+    int ring_on = 0;   // monitor rings in use (per-cell mode: DFT once per batch, see ensure_ring)
     int energy_on = 0;
     int phase_cap = 0;
     long long launches = 0;
@@ -893,7 +900,56 @@ CellArgs<T> make_cell_args(const fdtd_ctx* c, int di, bool e_side) {
         ca.ahi[q] = h.n[q];
         ca.cur[q] = (T*)h.tcur[q];
     }
+    // the ring of the domain's monitor: component f's plane of slot 0 (E side E, H side H only)
+    if (c->ring_on && h.mons.size() == 1) {
+        const Mon& m = c->mons[h.mons[0]].m;
+        for (int q = 0; q < 3; ++q) {
+            ca.slo[q] = m.lo[q];
+            ca.shi[q] = m.hi[q];
+        }
+        ca.sstride = (long long)m.ncomp * m.ncell;
+        for (int ci = 0; ci < m.ncomp; ++ci)
+            if ((m.comps[ci] < 3) == e_side) ca.smp[m.comps[ci]] = (T*)m.ring + (long long)ci * m.ncell;
+    }
     return ca;
+}
+
+// Whether the per-cell mode folds the DFT once per batch from monitor rings: a resident context
+// whose monitors sit one per domain in domains the per-cell update kernels step (no tensor domain),
+// within kRingMaxBytes of rings.
+bool ring_wanted(const fdtd_ctx* c) {
+    if (c->streamed || c->mons.empty()) return false;
+    for (const DomainHost& h : c->doms)
+        if (h.mons.size() > 1 || (!h.mons.empty() && (h.tensor || h.bloch))) return false;
+    const long long esize = c->dtype == FDTD_F32 ? 4 : 8;
+    long long bytes = 0;
+    for (const MonHost& mh : c->mons) bytes += (long long)kGraphSteps * mh.m.ncomp * mh.m.ncell * esize;
+    return bytes <= kRingMaxBytes;
+}
+
+
+// Brings the rings in line with the configuration (outside graph capture): allocates a missing ring,
+// and drops the captured graphs and argument blocks when the rings come into or out of use.
+fdtd_status ensure_ring(fdtd_ctx* c) {
+    const int want = ring_wanted(c) ? 1 : 0;
+    const long long esize = c->dtype == FDTD_F32 ? 4 : 8;
+    bool alloc = false;
+    if (want)
+        for (MonHost& mh : c->mons)
+            if (!mh.m.ring) {
+                fdtd_status st = dmalloc(c, &mh.m.ring, (size_t)(kGraphSteps * mh.m.ncomp * mh.m.ncell * esize));
+                if (st != FDTD_OK) return st;
+                alloc = true;
+            }
+    if (want == c->ring_on && !alloc) return FDTD_OK;
+    c->ring_on = want;
+    if (alloc) {
+        fdtd_status st = sync_mons(c);   // the device monitor records carry the ring pointers
+        if (st != FDTD_OK) return st;
+    }
+    drop_graphs(c);
+    c->cargs_dirty = 1;
+    return FDTD_OK;
 }
 
 // Whether the per-cell mode runs every domain in one launch per half-step: several domains, none
@@ -979,8 +1035,9 @@ IfaceArgs iface_args(const DomainHost& h, int cap, long long t0) {
 bool has_cpml(const DomainHost& h) { return h.ns[0] || h.ns[1] || h.ns[2]; }
 
 // One forward step as per-half-step launches on stream st.  offset: position of this step in the
-// launched batch (its DFT phase index is *d_base + offset); first / last: first and last step of
-// the batch (no wait on DFT work of an earlier batch; the DFT stream is joined back at the end).
+// launched batch of at most kGraphSteps steps (its DFT phase index is *d_base + offset, its monitor
+// ring slot offset); first / last: first and last step of the batch (no wait on DFT work of an
+// earlier batch; the DFT stream is joined back at the end; the rings are folded after the last).
 template <typename T>
 void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) {
     const Launch l{st, &c->launches};
@@ -1000,9 +1057,16 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
     // ones.  Under per-launch profiling they run one after the other on st.
     const bool fork = c->aux_stream && !c->prof_on && ng > 0 && ni > 0;
     const Launch la{fork ? c->aux_stream : st, &c->launches};
-    // The DFT of E (step n) runs on its own stream beside the H update, the DFT of H beside the
-    // next E update; a half-step waits only for the DFT of the field it overwrites.
-    const int nd = c->dft_enabled ? c->n_dft_items : 0;
+    // per-cell mode (no energy record): the kernels take their step from the batch base, and
+    // the step counter advances once, after the batch's last step
+    const bool cell = c->cell_mode && !c->energy_on;
+    // With monitor rings the per-cell updates store the monitor samples and one launch after the
+    // batch's last step folds them into the DFT.  Otherwise the DFT of E (step n) runs on its own
+    // stream beside the H update, the DFT of H beside the next E update; a half-step waits only for
+    // the DFT of the field it overwrites.
+    const bool ring = cell && c->ring_on && c->dft_enabled && c->n_dft_items > 0;
+    a.ring = ring ? 1 : 0;
+    const int nd = (c->dft_enabled && !ring) ? c->n_dft_items : 0;
     const bool dstream = nd > 0 && !c->prof_on;
     const Launch ld{dstream ? c->dft_stream : st, &c->launches};
     const unsigned adv = (unsigned)(ng + ni);
@@ -1016,9 +1080,6 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
         cudaEventRecord(c->ev_join, c->aux_stream);
         cudaStreamWaitEvent(st, c->ev_join, 0);
     };
-    // per-cell mode (no energy record): the kernels take their step from the batch base, and
-    // the step counter advances once, after the batch's last step
-    const bool cell = c->cell_mode && !c->energy_on;
     if ((nd > 0 || cell) && first) launch_copy_int(l, c->d_step, c->d_base);
     if (dstream && !first) cudaStreamWaitEvent(st, c->ev_de, 0);   // DFT of E^n done before E changes
     auto cell_args = [&](int di, bool e_side) { return make_cell_args<T>(c, di, e_side); };
@@ -1101,6 +1162,10 @@ void step_once(fdtd_ctx* c, cudaStream_t st, int offset, bool first, bool last) 
         // interface record of the reversible reconstruction: E^{n+1}, H^{n+3/2} into slot n + 1 - t0
         for (const DomainHost& h : c->doms)
             if (h.rec) launch_iface<T>(l, (T* const*)h.F, h.n, h.ia, (T*)h.rec, c->d_base, offset + 1, 3, 1);
+        if (last && ring) {
+            Prof p(c, FDTD_KERNEL_DFT);
+            launch_dft_ring<T>(l, c->d_mons, c->d_dft_items, c->n_dft_items, c->d_base, offset + 1);
+        }
         if (last) launch_advance(l, c->d_step, offset + 1);
     } else {
         fork_int();
@@ -1969,7 +2034,6 @@ fdtd_status stream_adjoint(fdtd_ctx* c, int n_steps) {
     return FDTD_OK;
 }
 
-constexpr int kGraphSteps = 32;
 
 void drop_graphs(fdtd_ctx* c) {
     bool any = false;
@@ -2000,6 +2064,7 @@ fdtd_status build_graph(fdtd_ctx* c) {
     }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    const long long captured = c->launches - l0;   // kernel launches of one replay
     c->launches = l0;
     if (e != cudaSuccess) return fail(c, FDTD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&c->graph[a][b], g, 0);
@@ -2008,17 +2073,7 @@ fdtd_status build_graph(fdtd_ctx* c) {
         c->graph[a][b] = nullptr;
         return fail(c, FDTD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
-    // launches of one step: E and H for each non-empty tile class, the two DFT launches, and
-    // one step-base copy per graph
-    const int nd = c->dft_enabled && c->n_dft_items > 0;
-    const bool cell = c->cell_mode && !c->energy_on;
-    const long long per = cell ? 2 * ((long long)c->doms.size() + nd)
-                               : 2 * ((c->tiles_int.empty() ? 0 : 1) + (c->tiles_gen.empty() ? 0 : 1) + nd);
-    // plus the step-base copy (DFT or per-cell) and, per-cell, the counter advance and the interface
-    // records
-    long long recs = 0;
-    for (const auto& h : c->doms) recs += (cell && h.rec) ? 1 : 0;
-    c->graph_launches[a][b] = (per + recs) * kGraphSteps + ((nd || cell) ? 1 : 0) + (cell ? 1 : 0);
+    c->graph_launches[a][b] = captured;
     return FDTD_OK;
 }
 
@@ -2156,6 +2211,8 @@ void time_launches_t(fdtd_ctx* c, cudaStream_t st, int which, int n, long long* 
     a.dft_on = c->dft_enabled;
     a.d_base = c->d_base;
     a.offset = 0;
+    // the updates store their monitor samples as in a step (into slot 0)
+    a.ring = c->ring_on && c->dft_enabled && c->n_dft_items > 0 ? 1 : 0;
     for (int r = 0; r < n; ++r) {
         if (which == 0) {
             for (int di = 0; di < (int)c->doms.size(); ++di) {
@@ -2166,6 +2223,8 @@ void time_launches_t(fdtd_ctx* c, cudaStream_t st, int which, int n, long long* 
             for (int di = 0; di < (int)c->doms.size(); ++di) launch_h_cell<T>(l, make_cell_args<T>(c, di, false), (T)c->S, a);
         } else if (which == 2) {
             launch_dft<T>(l, dd, c->d_mons, c->d_dft_items, c->n_dft_items, 0, c->d_base, 0);
+        } else if (which == 5) {
+            launch_dft_ring<T>(l, c->d_mons, c->d_dft_items, c->n_dft_items, c->d_base, kGraphSteps);
         } else {
             // transposed half-steps at adjoint index m = step count (no pending deferral)
             for (int di = 0; di < (int)c->doms.size(); ++di) {
@@ -2798,7 +2857,9 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
     }
     int left = n_steps;
     {
-        fdtd_status st = sync_cell_args(ctx);   // a batch's argument blocks, before any capture
+        fdtd_status st = ensure_ring(ctx);   // monitor rings, before the argument blocks and any capture
+        if (st != FDTD_OK) return st;
+        st = sync_cell_args(ctx);   // a batch's argument blocks, before any capture
         if (st != FDTD_OK) return st;
     }
     if (ctx->use_graphs && !ctx->prof_on && left >= kGraphSteps) {
@@ -2811,11 +2872,15 @@ fdtd_status fdtd_step_forward(fdtd_ctx* ctx, int32_t n_steps) {
             left -= kGraphSteps;
         }
     }
-    for (int s = 0; s < left; ++s) {
-        if (ctx->dtype == FDTD_F32)
-            step_once<float>(ctx, ctx->stream, s, s == 0, s == left - 1);
-        else
-            step_once<double>(ctx, ctx->stream, s, s == 0, s == left - 1);
+    // the rest in eager batches of at most kGraphSteps steps (a monitor ring holds one batch)
+    for (int b0 = 0; b0 < left; b0 += kGraphSteps) {
+        const int nb = std::min(kGraphSteps, left - b0);
+        for (int s = 0; s < nb; ++s) {
+            if (ctx->dtype == FDTD_F32)
+                step_once<float>(ctx, ctx->stream, s, s == 0, s == nb - 1);
+            else
+                step_once<double>(ctx, ctx->stream, s, s == 0, s == nb - 1);
+        }
     }
     CKL(ctx);
     ctx->step += n_steps;
@@ -3523,7 +3588,7 @@ fdtd_status fdtd_launch_count(fdtd_ctx* ctx, int64_t* n) {
 fdtd_status fdtd_time_half_steps(fdtd_ctx* ctx, int32_t which, int32_t n_launches, double* ms_per_launch) {
     GUARD(ctx);
     NOT_STREAMED(ctx);
-    if (!ms_per_launch || which < 0 || which > 4 || n_launches < 1 || n_launches > 4096)
+    if (!ms_per_launch || which < 0 || which > 5 || n_launches < 1 || n_launches > 4096)
         return fail(ctx, FDTD_EINVAL, "bad arguments");
     *ms_per_launch = 0.0;
     if (!ctx->cell_mode || ctx->energy_on)
@@ -3531,6 +3596,21 @@ fdtd_status fdtd_time_half_steps(fdtd_ctx* ctx, int32_t which, int32_t n_launche
     NOT_BLOCH(ctx, "kernel timing");
     NOT_TENSOR(ctx, "kernel timing");
     if (which == 2 && ctx->n_dft_items == 0) return fail(ctx, FDTD_EINVAL, "no DFT monitor");
+    if (which <= 2 || which == 5) {
+        fdtd_status st = ensure_ring(ctx);
+        if (st != FDTD_OK) return st;
+    }
+    if (which == 5) {
+        if (!ctx->ring_on || ctx->n_dft_items == 0)
+            return fail(ctx, FDTD_EINVAL, "no monitor ring (the DFT runs per step in this configuration)");
+        bool changed = false;   // phases of the kGraphSteps steps the fold reads
+        fdtd_status st = ensure_phase(ctx, ctx->step + kGraphSteps + 2, &changed);
+        if (st != FDTD_OK) return st;
+        if (changed) {
+            st = sync_mons(ctx);
+            if (st != FDTD_OK) return st;
+        }
+    }
     if (which >= 3) {
         fdtd_status st = prepare_inj(ctx);   // the transposed kernels read the injection scratch
         if (st != FDTD_OK) return st;
@@ -3566,7 +3646,7 @@ fdtd_status fdtd_time_half_steps(fdtd_ctx* ctx, int32_t which, int32_t n_launche
     if (e1) cudaEventDestroy(e1);
     cudaGraphExecDestroy(ge);
     CK(ctx, e);
-    ctx->launches += 2ll * n_launches * (which == 2 ? 1 : (long long)ctx->doms.size());
+    ctx->launches += 2ll * n_launches * ((which == 2 || which == 5) ? 1 : (long long)ctx->doms.size());
     if (which >= 3) ctx->adj_pending = 1;   // the adjoint arrays now hold the lagged form
     *ms_per_launch = (double)ms / n_launches;
     return FDTD_OK;

@@ -82,6 +82,9 @@ struct Mon {
     const double2* cot;
     const double2* phase;
     int cap;
+    // per-cell mode: field samples of one launched batch of steps, [step of the batch][ncomp][ncell]
+    // in the field type, written by the update kernels and folded into acc once per batch
+    void* ring;
 };
 
 // A DFT work item: cells [begin, min(begin + 256, end)) of monitor `mon` (one thread per cell),
@@ -255,6 +258,7 @@ struct StepArgs {
     int dft_on;
     const int* d_base;          // per-cell mode: first step of the launched batch ...
     int offset;                 // ... and this step's position in it (step = *d_base + offset)
+    int ring = 0;               // per-cell mode: the updates store monitor samples into slot offset
 };
 
 template <typename T>
@@ -270,6 +274,11 @@ void launch_advance(const Launch& L, int* d_step, int delta);
 template <typename T>
 void launch_dft(const Launch& L, const Dom<T>* doms, const Mon* mons, const DftItem* items, int nitems, int kind,
                 const int* d_base, int offset);
+// Folds the samples of steps *d_base .. *d_base + cnt - 1 in every monitor's ring into its DFT
+// accumulators, in step order with the per-step kernel's FP64 fused multiply-adds (bit for bit the
+// accumulators cnt launches of launch_dft of each kind would leave).
+template <typename T>
+void launch_dft_ring(const Launch& L, const Mon* mons, const DftItem* items, int nitems, const int* d_base, int cnt);
 void launch_copy_int(const Launch& L, const int* src, int* dst);
 void launch_set_int(const Launch& L, int* dst, int v);
 // One domain's operands for the per-cell kernels, passed by value (kernel parameter space) so
@@ -296,6 +305,12 @@ struct CellArgs {
     int alo[3], ahi[3];
     // curl output of the E side of a tensor domain (launch_e_curl), else unused
     T* cur[3];
+    // monitor samples (StepArgs::ring): the box [slo, shi) of the domain's monitor, and for each
+    // field component in it the ring plane of slot 0 (nullptr: not monitored); slot s starts
+    // s * sstride values further
+    T* smp[6];
+    int slo[3], shi[3];
+    long long sstride;
 };
 
 // Interface planes of the absorbing-face reversible reconstruction (Sec. 3.2): the H nodes on the

@@ -122,8 +122,8 @@ __device__ __forceinline__ void dft_item(const Dom<T>* __restrict__ doms, const 
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     if (f0 + q >= nf) break;
-                    x[q].x += v * p[q].x;
-                    x[q].y += v * p[q].y;
+                    x[q].x = fma_t(v, p[q].x, x[q].x);
+                    x[q].y = fma_t(v, p[q].y, x[q].y);
                     acc[(long long)(f0 + q) * m.ncell] = x[q];
                 }
             }
@@ -139,6 +139,70 @@ __global__ void __launch_bounds__(kTileX* kTileY)
     k_dft(const Dom<T>* __restrict__ doms, const Mon* __restrict__ mons, const DftItem* __restrict__ items, int kind,
           const int* __restrict__ d_base, int offset) {
     dft_item(doms, mons, items[blockIdx.x], kind, *d_base + offset);
+}
+
+// DFT of a batch of cnt steps from the monitor rings (per-cell mode): block (x, y) takes work item
+// x for the monitor's y-th component (one thread per monitor cell), so the FP64 work of a batch
+// spreads over items x components blocks; each accumulator takes the samples of steps base,
+// base + 1, ... in order with the fused multiply-adds of dft_item, so it ends bit for bit where cnt
+// per-step launches of each kind would leave it, with one accumulator load and store per batch
+// instead of per step.
+template <typename T>
+__global__ void __launch_bounds__(kTileX* kTileY)
+    k_dft_ring(const Mon* __restrict__ mons, const DftItem* __restrict__ items, const int* __restrict__ d_base,
+               int cnt) {
+    const DftItem& it = items[blockIdx.x];
+    const Mon& m = mons[it.mon];
+    const int ci = blockIdx.y;
+    const long long cell = it.begin + threadIdx.y * kTileX + threadIdx.x;
+    if (ci >= m.ncomp || cell >= it.end) return;
+    const int base = *d_base, nf = m.nf;
+    const long long slot = (long long)m.ncomp * m.ncell;
+    {
+        const int kind = m.comps[ci] >= 3 ? 1 : 0;
+        const T* r = (const T*)m.ring + (long long)ci * m.ncell + cell;
+        double2* acc = m.acc + (long long)ci * nf * m.ncell + cell;
+        for (int f0 = 0; f0 < nf; f0 += 4) {
+            double2 x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = acc[(long long)(f0 + q < nf ? f0 + q : f0) * m.ncell];
+            for (int t = 0; t < cnt; ++t) {
+                const double v = (double)r[t * slot];
+                const double2* ph = m.phase + ((long long)(base + t) * 2 + kind) * nf + f0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (f0 + q >= nf) break;
+                    const double2 p = ph[q];
+                    x[q].x = fma_t(v, p.x, x[q].x);
+                    x[q].y = fma_t(v, p.y, x[q].y);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (f0 + q >= nf) break;
+                acc[(long long)(f0 + q) * m.ncell] = x[q];
+            }
+        }
+    }
+}
+
+// Monitor samples: plane kg (global; block-uniform in the per-cell kernels) crosses the domain's
+// monitor box and the step stores samples, then cell (i, j) lies in the box; the sample of a
+// component goes to slot a.offset of its ring at sample_off.
+template <typename T>
+__device__ __forceinline__ bool in_sample_plane(const CellArgs<T>& c, const StepArgs& a, int kg) {
+    return (unsigned)(kg - c.slo[2]) < (unsigned)(c.shi[2] - c.slo[2]) && a.ring;
+}
+template <typename T>
+__device__ __forceinline__ bool in_sample_rect(const CellArgs<T>& c, int i, int j) {
+    return (unsigned)(i - c.slo[0]) < (unsigned)(c.shi[0] - c.slo[0]) &&
+           (unsigned)(j - c.slo[1]) < (unsigned)(c.shi[1] - c.slo[1]);
+}
+template <typename T>
+__device__ __forceinline__ long long sample_off(const CellArgs<T>& c, const StepArgs& a, int i, int j, int kg) {
+    return (long long)a.offset * c.sstride +
+           ((long long)(kg - c.slo[2]) * (c.shi[1] - c.slo[1]) + (j - c.slo[1])) * (c.shi[0] - c.slo[0]) +
+           (i - c.slo[0]);
 }
 
 __global__ void k_copy_int(const int* __restrict__ src, int* __restrict__ dst) { *dst = *src; }
@@ -507,6 +571,13 @@ __device__ __forceinline__ void e_cell_body(const CellArgs<T>& c, const Dom<T>* 
     if (!px) c.F[0][id] = ex;
     if (!py) c.F[1][id] = ey;
     if (!pz) c.F[2][id] = ez;
+    if (in_sample_plane(c, a, kg) && in_sample_rect(c, i, j)) {
+        // the DFT sample of E^{n+1} (a PEC-held component keeps its value)
+        const long long o = sample_off(c, a, i, j, kg);
+        if (c.smp[0]) c.smp[0][o] = ex;
+        if (c.smp[1]) c.smp[1][o] = ey;
+        if (c.smp[2]) c.smp[2][o] = ez;
+    }
 }
 
 // Block (bx, by, bz) of a domain's per-cell grid: blocks of 32 x 8 threads cover 16 x 16 cells of a
@@ -637,6 +708,13 @@ __device__ __forceinline__ void h_cell_body(const CellArgs<T>& c, T S, const Ste
         c.F[3][id] = hx1;
         c.F[4][id] = hy1;
         c.F[5][id] = hz1;
+        if (in_sample_plane(c, a, kg) && in_sample_rect(c, i, j)) {
+            // the DFT sample of H^{n+3/2}
+            const long long o = sample_off(c, a, i, j, kg);
+            if (c.smp[3]) c.smp[3][o] = hx1;
+            if (c.smp[4]) c.smp[4][o] = hy1;
+            if (c.smp[5]) c.smp[5][o] = hz1;
+        }
     }
 }
 
@@ -860,6 +938,14 @@ void launch_dft(const Launch& L, const Dom<T>* doms, const Mon* mons, const DftI
     ++*L.counter;
 }
 
+template <typename T>
+void launch_dft_ring(const Launch& L, const Mon* mons, const DftItem* items, int nitems, const int* d_base, int cnt) {
+    if (nitems <= 0 || cnt <= 0) return;
+    // one grid row per component slot (6 at most; rows past a monitor's components return at once)
+    k_dft_ring<T><<<dim3(nitems, 6), dim3(kTileX, kTileY), 0, L.stream>>>(mons, items, d_base, cnt);
+    ++*L.counter;
+}
+
 void launch_copy_int(const Launch& L, const int* src, int* dst) {
     k_copy_int<<<1, 1, 0, L.stream>>>(src, dst);
     ++*L.counter;
@@ -886,6 +972,8 @@ template void launch_dft<float>(const Launch&, const Dom<float>*, const Mon*, co
                                 int);
 template void launch_dft<double>(const Launch&, const Dom<double>*, const Mon*, const DftItem*, int, int, const int*,
                                  int);
+template void launch_dft_ring<float>(const Launch&, const Mon*, const DftItem*, int, const int*, int);
+template void launch_dft_ring<double>(const Launch&, const Mon*, const DftItem*, int, const int*, int);
 template void launch_e_cell<float>(const Launch&, const CellArgs<float>&, const Dom<float>*, float, const StepArgs&,
                                    int, int);
 template void launch_e_cell<double>(const Launch&, const CellArgs<double>&, const Dom<double>*, double,

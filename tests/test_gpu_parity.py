@@ -552,6 +552,39 @@ def test_tile_and_per_cell_launch_modes_bitwise_equal(which, dtype):
             assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_monitor_ring_fold_matches_per_step_dft(dtype):
+    # the per-cell mode stores monitor samples during a batch of steps and folds them into the DFT
+    # once per batch; a second monitor in the same domain turns the rings off (one DFT launch per
+    # half-step): the shared monitor's spectra must agree bit for bit, over batches of 32 steps
+    # (graphs) and of 1 to 31 (eager remainders)
+    sc = small_blocks(40, 6, 150)
+    sc2 = small_blocks(40, 6, 150)
+    sc2.monitors.append(W.Monitor((4, 4, 4), (12, 12, 5), (W.EX, W.HZ), sc2.monitors[0].omegas))
+    specs = []
+    for s, prof in ((sc, False), (sc2, False), (sc, True)):
+        ctx = fdtd.Context([s], dtype=dtype)
+        fdtd.fdtd_set_launch_mode(ctx.ctx, 4)
+        if prof:
+            # per-launch profiling steps without graphs: eager batches of at most 32 steps
+            fdtd.fdtd_profile_begin(ctx.ctx, 4096)
+        for n in (70, 1, 31, 48):
+            ctx.step(n)
+        if prof:
+            fdtd.fdtd_profile_end(ctx.ctx)
+        specs.append(ctx.dft(0).clone())
+        if s is sc and not prof:
+            # the fold of one batch can be timed on its own; the per-step form has no rings
+            assert fdtd.fdtd_time_half_steps(ctx.ctx, 5, 2) > 0
+        elif s is sc2:
+            with pytest.raises(fdtd.FdtdError):
+                fdtd.fdtd_time_half_steps(ctx.ctx, 5, 2)
+        ctx.close()
+    assert torch.equal(specs[0], specs[1])
+    assert torch.equal(specs[0], specs[2])
+    assert float(specs[0].abs().max()) > 0
+
+
 def test_bf16_snapshot_denormal_slab_stays_finite():
     # a slab whose largest value is an FP32 denormal (the leading edge of a wave far from the
     # source) must round-trip without NaN
