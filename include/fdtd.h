@@ -25,7 +25,9 @@
  *   - Every function returns an fdtd_status; nothing throws across the ABI.  On error the
  *     context keeps a message (fdtd_last_error).  After FDTD_ECUDA the context is poisoned:
  *     every later call except fdtd_destroy / fdtd_last_error returns FDTD_ESTATE.  No kernel of
- *     the library waits on another block or kernel, so no device-side wait can run out.
+ *     the library spins on a flag of another block or kernel; the only device-side wait is the
+ *     griddepcontrol wait of the programmatically launched transposed kernels, which the hardware
+ *     ends when the kernels launched before them on the stream complete, so none can run out.
  *   - All device work is enqueued on the stream given to fdtd_create (a cudaStream_t passed
  *     as void*; NULL = legacy default stream).  Calls are asynchronous unless stated.
  *     A context is not thread-safe.

@@ -591,8 +591,9 @@ class Context:
         return fdtd_launch_count(self.ctx)
 
     def synchronize(self, timeout_ms: int = 600000):
-        """Waits for the context's work and reports a device-side wait that gave up (FdtdError
-        with FDTD_ETIMEOUT; the context is then poisoned)."""
+        """Waits at most timeout_ms for the context's work (FdtdError with FDTD_ETIMEOUT if it has
+        not finished; the work goes on and the context stays usable; a CUDA error the stream reports
+        poisons the context: FDTD_ECUDA)."""
         fdtd_synchronize(self.ctx, int(timeout_ms))
 
     def close(self):
