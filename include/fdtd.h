@@ -247,7 +247,8 @@ fdtd_status fdtd_add_source(fdtd_ctx* ctx, int32_t domain, int32_t component, co
  * domain (and in no tensor domain) keeps a device ring of one batch (32 steps) of samples per
  * monitor (32 * ncomp * box cells field values, at most 512 MiB for all monitors): the update
  * kernels store the samples and one launch per batch adds them to the accumulators in step order,
- * bit for bit the values per-step accumulation gives.  Otherwise the DFT runs per half-step. */
+ * bit for bit the values per-step accumulation gives.  Otherwise (or when a ring does not fit in
+ * device memory) the DFT runs per half-step. */
 fdtd_status fdtd_add_dft_monitor(fdtd_ctx* ctx, int32_t domain, const int32_t lo[3], const int32_t hi[3],
                                  uint32_t component_mask, int32_t n_freq, const double* omega_dt,
                                  int32_t* monitor_id);

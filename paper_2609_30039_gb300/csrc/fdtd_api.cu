@@ -931,13 +931,17 @@ bool ring_wanted(const fdtd_ctx* c) {
 // Brings the rings in line with the configuration (outside graph capture): allocates a missing ring,
 // and drops the captured graphs and argument blocks when the rings come into or out of use.
 fdtd_status ensure_ring(fdtd_ctx* c) {
-    const int want = ring_wanted(c) ? 1 : 0;
+    int want = ring_wanted(c) ? 1 : 0;
     const long long esize = c->dtype == FDTD_F32 ? 4 : 8;
     bool alloc = false;
     if (want)
         for (MonHost& mh : c->mons)
             if (!mh.m.ring) {
                 fdtd_status st = dmalloc(c, &mh.m.ring, (size_t)(kGraphSteps * mh.m.ncomp * mh.m.ncell * esize));
+                if (st == FDTD_ENOMEM) {   // no room for a ring: the DFT runs per half-step instead
+                    want = 0;
+                    break;
+                }
                 if (st != FDTD_OK) return st;
                 alloc = true;
             }
