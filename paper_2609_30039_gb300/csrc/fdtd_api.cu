@@ -11,9 +11,6 @@
 #include <thread>
 #include <vector>
 
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include "fdtd_internal.cuh"
 
 using namespace gbfdtd;
